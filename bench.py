@@ -1,0 +1,388 @@
+"""Benchmark: proximal message passing iterations/s on the 10k-bus workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one iteration of the whole hot path (every line prox in every
+contingency, every device prox including the inner ADMM of ramp-limited
+generators and batteries, node averages, price updates, FP64 residuals and
+the adaptive penalty) over the 10,000-bus, T = 96, K = 50 synthetic instance.
+``value`` is iterations/s with the state resident in HBM; under torchrun
+each rank solves its own instance (independent problems, weak scaling, no
+data-path collective) and ``value`` sums all ranks.  ``e2e`` is the same
+metric through the C ABI with host buffers: network upload, the K
+iterations and the solution download are inside the timed region.
+
+``--impl reference`` times the FP64 oracle on the host cores instead; each
+step is one oracle iteration on a bounded sample of the instance (the 10k
+network with fewer contingencies and time steps), converted to full-workload
+iterations/s by the paper's variable count 4 J T (K+1) per iteration.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ADMM iterations/s"
+UNIT = "iter/s"
+WORKLOAD = "dcopf-10k-bus-T96-K50"
+KERNEL_SRC = os.path.join(ROOT, "paper_2410_17203_gb300", "csrc", "opf_kernels.cu")
+PROFILE = os.path.join(ROOT, "profiles", "iteration_kernel_10k.txt")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def byte_model(d):
+    """Algorithmic bytes of one iteration: every carried FP32 state element read
+    once and written once -- lines p, theta1, theta2, v1, v2; nodes u, pbar,
+    theta_bar (each [K+1][.][T]); device power [S][T] (read and written)."""
+    Kp, T = d["K"] + 1, d["T"]
+    return 8 * Kp * T * (5 * d["L"] + 3 * d["N"]) + 8 * d["S"] * T
+
+
+def variables_per_iter(d):
+    """The paper's problem-size convention 4 J T (K+1) (p, theta, u, v)."""
+    return 4 * d["J"] * d["T"] * (d["K"] + 1)
+
+
+def peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per iteration from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    try:
+        kv = {}
+        for line in open(PROFILE):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256") != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_iteration"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        load = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+
+def sample_case(case, k_s, T_s):
+    """The instance with its first k_s contingencies and first T_s steps."""
+    import numpy as np
+    c = dict(case)
+    c["outaged"] = np.asarray(case["outaged"][:k_s], np.int32)
+    c["T"] = T_s
+    for k in ("gen_pmin", "gen_pmax", "load_p"):
+        c[k] = np.ascontiguousarray(case[k][:, :T_s])
+    if T_s <= 1:
+        c["gen_ramp"] = -np.ones(len(case["gen_node"]))
+    return c
+
+
+def oracle_child(cfg, k_s, T_s, steps, warmup):
+    """Runs in a child process with single-threaded BLAS: times the oracle."""
+    from gridgen import case_dims, make_case
+    from oracle import Oracle, OracleOptions
+    c = sample_case(make_case(cfg), k_s, T_s)
+    o = Oracle(c, OracleOptions(adapt_every=10, eps=0.0))
+    for _ in range(warmup):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step()
+    dt = time.perf_counter() - t0
+    d = case_dims(c)
+    return {"seconds": dt, "steps": steps, "vars_per_iter": variables_per_iter(d),
+            "K_sample": k_s, "T_sample": T_s}
+
+
+def run_oracle(cfg, k_s, T_s, steps, warmup):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle-child",
+           json.dumps(dict(cfg=cfg, k_s=k_s, T_s=T_s, steps=steps, warmup=warmup))]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle child failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_value(res, full_vars):
+    """Full-workload iterations/s from the sample's variable-update rate."""
+    upd = res["vars_per_iter"] * res["steps"] / res["seconds"]
+    return upd / full_vars
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args):
+    from gridgen import CONFIGS, case_dims, make_case
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    full = make_case(args.config)
+    d = case_dims(full)
+    # per-step budget: the whole run in about two minutes
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    # oracle cost is about 0.4 s per (contingency, 96 steps) at 10k on one core
+    unit = 0.4 * d["T"] / 96.0 * (d["N"] / 10000.0)
+    k_s = max(0, min(d["K"], int(per_step / unit) - 1))
+    T_s = d["T"] if k_s > 0 else max(1, min(d["T"], int(d["T"] * per_step / unit)))
+    res = run_oracle(args.config, k_s, T_s, args.steps, args.warmup)
+    v = oracle_value(res, variables_per_iter(d))
+    sample = (f"{args.config} network, contingencies 0..{k_s}, steps 0..{T_s - 1}; "
+              f"value scaled by 4JT(K+1) variables per iteration")
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds"] / res["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "N": d["N"], "L": d["L"], "T": d["T"], "K": d["K"],
+                       "S": d["S"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours_arm(args):
+    import numpy as np
+    import torch
+
+    from gridgen import case_dims, make_case
+    from paper_2410_17203_gb300 import (Solver, opf_create, opf_destroy, opf_get_info, opf_iterate,
+                                        opf_residuals, opf_solution)
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    case = make_case(args.config, seed=None if ws == 1 else 1000 + rank)
+    d = case_dims(case)
+    B = byte_model(d)
+    stream = torch.cuda.Stream(device=dev)
+    opts = dict(adapt_every=10, eps=0.0)
+    s = Solver(case, opts, stream=stream.cuda_stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    with torch.cuda.stream(stream):
+        opf_iterate(s.h, args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(local) if rank == 0 else None
+    time.sleep(0.4 if clocks else 0.0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    opf_iterate(s.h, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    res = opf_residuals(s.h)
+    info = s.get_info()
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ws * args.steps / (ms_max / 1e3)
+    s.close()
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Kp, L, N, S, T = d["K"] + 1, d["L"], d["N"], d["S"], d["T"]
+        p_dev = np.zeros((S, T), np.float32)
+        price = np.zeros((N, T), np.float32)
+        h2d = sum(np.asarray(v).nbytes for k, v in case.items() if isinstance(v, np.ndarray))
+        d2h = p_dev.nbytes + price.nbytes + 6 * 8
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        h = opf_create(case, opts, stream=stream.cuda_stream)
+        opf_iterate(h, args.steps)
+        r = opf_residuals(h)
+        opf_solution(h, False, True, p_dev=p_dev, price=price)
+        opf_destroy(h)
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": ws * args.steps / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "includes": "opf_create (host network upload, device arena), K iterations, "
+                           "residuals + solution download, opf_destroy"}
+
+    # time to the 1e-4 tolerance of Eq. (converge), adaptive penalty on
+    ttt = None
+    if args.ttt and rank == 0:
+        h = opf_create(case, dict(adapt_every=10, eps=1e-4), stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = 0
+        while done < args.ttt_max:
+            opf_iterate(h, 1000)
+            done += 1000
+            inf = opf_get_info(h)
+            if inf["converged"]:
+                break
+        dt = time.perf_counter() - t0
+        inf = opf_get_info(h)
+        ttt = {"eps": 1e-4, "converged": bool(inf["converged"]), "iterations": int(inf["iterations"]),
+               "seconds": dt, "residuals": [float(x) for x in opf_residuals(h)[:2]],
+               "tolerance": inf["tolerance"]}
+        opf_destroy(h)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        k_s = 10
+        r = run_oracle(args.config, k_s, d["T"], 2, 1)
+        cpu = {"value": oracle_value(r, variables_per_iter(d)), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.config} network with contingencies 0..{k_s} (of {d['K']}), 2 timed "
+                         f"iterations after 1 warm-up; value scaled by 4JT(K+1) variables per iteration"}
+
+    if rank == 0:
+        peak, src = peak_hbm()
+        achieved = B * args.steps / (ms / 1e3) / 1e9
+        traffic = profiled_traffic()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": d["N"], "L": d["L"], "T": d["T"], "K": d["K"],
+                       "S": d["S"], "J": d["J"], "parallelism": f"independent instance per GPU x{ws}",
+                       "l2": "inputs larger than L2 (state %.2f GB)" % (info["device_bytes"] / 1e9),
+                       "adapt_every": 10},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": src,
+                         "traffic": (traffic * args.steps if traffic else None),
+                         "algorithmic_bytes_per_iteration": B,
+                         "kernel": "opfk::iteration_kernel (one cooperative launch of K iterations)"},
+            "variable_updates_per_s": value * variables_per_iter(d),
+            "e2e": e2e,
+            "gpu_launches": 1,
+            "clocks": ck,
+            "residuals": [float(x) for x in res],
+            "rho": [info["rho_p"], info["rho_theta"]],
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        if ttt:
+            line["time_to_tolerance"] = ttt
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="10k")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ttt", action="store_true", help="also time the solve to eps = 1e-4")
+    ap.add_argument("--ttt-max", type=int, default=30000)
+    ap.add_argument("--_oracle-child", dest="oracle_child", default=None)
+    args = ap.parse_args()
+    if args.oracle_child:
+        kw = json.loads(args.oracle_child)
+        print(json.dumps(oracle_child(**kw)))
+        return 0
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

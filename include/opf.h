@@ -1,0 +1,205 @@
+/*
+ * opf.h -- C ABI of the GB300 proximal message passing solver for
+ * contingency-constrained DC optimal power flow.
+ *
+ * The solver runs the message-passing form of ADMM (Section 3.2): per
+ * iteration, the prox of every line in every contingency (step 1), the prox
+ * of every generator, load and battery shared by all contingencies (step 2),
+ * the node averages and the scaled price updates (step 3), then the primal and
+ * dual residuals of Section 3.3, the stopping test of Eq. (converge) and the
+ * adaptive penalty of Section 3.5.  Ramp-limited generators and batteries use
+ * the inner ADMM of Appendix D for their prox.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an opf_status and never aborts the process.
+ *   - Input arrays are read during the call only; the library copies them.
+ *   - Output buffers are owned by the caller.  Where a function takes an
+ *     `on_device` flag, 0 means host pointers and 1 means device pointers of
+ *     the current CUDA device.
+ *   - Arrays are row-major; the time step t is always the innermost index.
+ *     K is the number of contingencies, Kp = K + 1 (contingency 0 is the base
+ *     case), L lines, N nodes, S = n_gens + n_loads + n_stor single-terminal
+ *     devices ordered generators, then loads, then batteries.
+ *   - Power p > 0 flows from a device into its node (Section 2).  A line's
+ *     power is reported at its second terminal (the `to` node); its first
+ *     terminal carries -p.
+ *   - All GPU work is enqueued on the stream given in opf_options; functions
+ *     that return data synchronize that stream.
+ */
+#ifndef OPF_H_
+#define OPF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OPF_ABI_VERSION 1
+
+typedef struct opf_ctx opf_ctx; /* opaque, created by opf_create, freed by opf_destroy */
+
+typedef enum {
+  OPF_OK = 0,
+  OPF_EINVAL = 1,     /* bad argument or inconsistent network data */
+  OPF_ENOMEM = 2,     /* a host or device allocation failed */
+  OPF_ECUDA = 3,      /* a CUDA runtime call failed (message in opf_last_error) */
+  OPF_ETIMEOUT = 4,   /* a grid-wide barrier of the iteration kernel ran out of its
+                         spin budget; the iterate is incomplete (see OPF_ESTATE) */
+  OPF_ENONFINITE = 5, /* a residual became NaN or infinite; iteration stopped */
+  OPF_ESTATE = 6      /* the state is unusable after an earlier OPF_ETIMEOUT;
+                         call opf_reset or opf_set_state before iterating again */
+} opf_status;
+
+/*
+ * Network data (Section 2.1 device models, Section 2.3 contingencies).
+ * Node ids are 0-based.  Every node needs at least one terminal.
+ */
+typedef struct {
+  int32_t n_nodes;
+
+  /* AC lines under the DC approximation: I{p1 + p2 = 0} + I{|p2| <= u}
+   * + I{p2 = b (theta1 - theta2)}.  Terminal 1 sits at line_from, terminal 2
+   * at line_to.  b > 0, u >= 0. */
+  int32_t n_lines;
+  const int32_t *line_from, *line_to;
+  const double *line_b, *line_u;
+
+  /* Generators: a p^2 + b p + I{pmin_t <= p_t <= pmax_t}; gen_pmin/gen_pmax
+   * are [n_gens][T].  gen_ramp[g] >= 0 adds |p_{t+1} - p_t| <= ramp (for T > 1);
+   * a negative value means no ramp limit. */
+  int32_t n_gens;
+  const int32_t *gen_node;
+  const double *gen_a, *gen_b, *gen_pmin, *gen_pmax, *gen_ramp;
+
+  /* Loads: load_p [n_loads][T] is the consumption (>= 0).  load_voll < 0 makes
+   * the load fixed (p = -load_p); otherwise the load is curtailable on
+   * [-load_p, 0] at cost voll * (p + load_p). */
+  int32_t n_loads;
+  const int32_t *load_node;
+  const double *load_p, *load_voll;
+
+  /* Batteries (Section 2.1): power limit P, duration dur (energy limit
+   * dur * P), charge efficiency eff in (0, 1], discharge cost cost >= 0;
+   * empty at the start and at the end of the horizon. */
+  int32_t n_stor;
+  const int32_t *stor_node;
+  const double *stor_P, *stor_dur, *stor_eff, *stor_cost;
+} opf_network;
+
+/* Contingencies k = 1..K: in contingency k the line outaged_line[k-1] has
+ * u = b = 0 (Section 2.3, N-1 example); -1 keeps the base-case parameters. */
+typedef struct {
+  int32_t K;
+  const int32_t *outaged_line;
+} opf_contingencies;
+
+/* Algorithm options.  opf_default_options fills the paper's defaults
+ * (Section 5.2): rho_p = rho_theta = 1, mu = 2, gamma = 1.1, adapt every 10
+ * iterations, 10 inner iterations (Section 4.5), eps = 1e-4 tested every 10. */
+typedef struct {
+  double rho_p, rho_theta;  /* initial penalties (> 0) */
+  double eps;               /* Eq. (converge) tolerance; <= 0 disables stopping */
+  double mu, gamma;         /* adaptive penalty: threshold and factor (Section 3.5) */
+  int32_t adapt_every;      /* penalty update cadence; 0 disables adaptation */
+  int32_t inner_iters;      /* Appendix D iterations per iterative prox (>= 1) */
+  int32_t check_every;      /* stopping test cadence; 0 disables stopping */
+  int32_t reserved0;
+  int64_t barrier_timeout_cycles; /* spin budget of one grid barrier in SM clock
+                                     cycles; <= 0 selects the default (~2e9) */
+  void *cuda_stream;        /* cudaStream_t to enqueue on; NULL = default stream */
+} opf_options;
+
+/* Solver state, the iterate s = (p, theta, u, v) of Section 4.4 plus the
+ * inner ADMM duals.  Each pointer may be NULL to skip that array.
+ *   p_line, th1, th2, v1, v2: [Kp][L][T]  line terminal-2 power, terminal
+ *                                          angles and phase duals
+ *   p_dev:  [S][T]                         single-terminal device power
+ *   u:      [Kp][N][T]                     scaled power-balance duals (per node)
+ *   inner:  [inner_len]                    inner ADMM (lambda, beta) of the
+ *           iterative proxes, layout documented at opf_get_info. */
+typedef struct {
+  float *p_line, *th1, *th2, *v1, *v2;
+  float *p_dev;
+  float *u;
+  float *inner;
+} opf_state;
+
+typedef struct {
+  int64_t iterations;       /* iterations run since create / reset */
+  int32_t converged;        /* 1 once Eq. (converge) held at a test */
+  int32_t status;           /* sticky device status (an opf_status value) */
+  double rho_p, rho_theta;  /* current penalties */
+  double tolerance;         /* eps * sqrt(2 J T Kp) */
+  int32_t N, L, S, T, K, J; /* sizes; J = 2L + S terminals */
+  int32_t n_ramp, n_stor;   /* devices using the inner ADMM */
+  /* inner_len = n_ramp * 2 * (4T - 2) + n_stor * 2 * (8T + 4).  Layout: for
+   * each ramp-limited generator in generator order, lambda then beta over the
+   * rows [p <= pmax (T), -p <= -pmin (T), ramp up (T-1), ramp down (T-1)];
+   * then for each battery, lambda then beta over the rows [p + c - delta = 0
+   * (T), soc dynamics (T), s_1 = 0, s_{T+1} = 0, c <= P (T), -c <= 0 (T),
+   * delta <= P (T), -delta <= 0 (T), s <= dur P (T+1), -s <= 0 (T+1)]. */
+  int64_t inner_len;
+  int64_t device_bytes;     /* device memory held by the context */
+} opf_info;
+
+/* Fill `opt` with the defaults listed above. */
+void opf_default_options(opf_options *opt);
+
+/* Validate the network, build the node-ordered incidence (CSR by node), upload
+ * parameters and allocate the device state, zero-initialised (Section 3.4).
+ * `opt` may be NULL for the defaults.  On success *out owns the context. */
+opf_status opf_create(const opf_network *net, int32_t horizon_T,
+                      const opf_contingencies *ctg, const opf_options *opt,
+                      opf_ctx **out);
+
+/* Enqueue up to n_iters message-passing iterations (Section 3.2) as one
+ * persistent cooperative kernel launch.  rho > 0 first sets rho_p = rho_theta
+ * = rho, rescaling the scaled duals (Section 3.5); rho <= 0 keeps the current
+ * (possibly adapted) penalties.  Stops early after a passed stopping test.
+ * Asynchronous: device errors surface at the next synchronizing call. */
+opf_status opf_iterate(opf_ctx *ctx, int32_t n_iters, double rho);
+
+/* Residuals of the last iteration run (Section 3.3), FP64:
+ * out[0] = ||r_primal||, out[1] = ||r_dual||, out[2] = primal power part,
+ * out[3] = primal phase part, out[4] = dual power part, out[5] = dual phase part.
+ * Synchronizes; returns the sticky device status. */
+opf_status opf_residuals(opf_ctx *ctx, double out[6]);
+
+/* Solution at the current iterate.  Any pointer may be NULL.
+ *   objective   host double: sum of device costs (line costs are indicators)
+ *   p_dev       [S][T]      device power
+ *   p_line      [Kp][L][T]  line terminal-2 power
+ *   theta_node  [Kp][N][T]  node angles theta_bar
+ *   price       [N][T]      nodal prices -rho_p * sum_k u_k
+ * Synchronizes. */
+opf_status opf_solution(opf_ctx *ctx, int32_t on_device, double *objective, float *p_dev,
+                        float *p_line, float *theta_node, float *price);
+
+/* Export / import the full state (warm start, checkpoint and resume,
+ * Section 3.4).  Import recomputes the node averages from p and theta and
+ * projects v onto v_bar = 0 per node (Appendix C); it clears a sticky
+ * OPF_ETIMEOUT / OPF_ESTATE.  Arrays left NULL on import are zeroed. */
+opf_status opf_get_state(opf_ctx *ctx, int32_t on_device, const opf_state *dst);
+opf_status opf_set_state(opf_ctx *ctx, int32_t on_device, const opf_state *src);
+
+/* Zero the state (cold start), restore the initial penalties and counters. */
+opf_status opf_reset(opf_ctx *ctx);
+
+opf_status opf_get_info(opf_ctx *ctx, opf_info *info);
+
+/* Free all resources; NULL is ignored. */
+void opf_destroy(opf_ctx *ctx);
+
+const char *opf_status_str(opf_status s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *opf_last_error(void);
+
+int32_t opf_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OPF_H_ */

@@ -402,6 +402,47 @@ class Oracle:
                     inner_matrix(Qd, rho, omega, self.stor_A[eff], T))
         self._factored_rho = rho
 
+    # -- state import (the C ABI's export layout: include/opf.h opf_state)
+    def load_state(self, st, rho_p=None, rho_theta=None, it=None):
+        """Set the iterate from a state dict with keys p_line, th1, th2, v1, v2
+        ``[K+1, L, T]``, p_dev ``[S, T]``, u ``[K+1, N, T]`` and optionally
+        ``inner`` (ramp generators then batteries, each lambda then beta over
+        the rows of ``ramp_rows`` / ``storage_rows``)."""
+        net = self.net
+        L = net.L
+        f = lambda x: np.asarray(x, dtype=np.float64)
+        self.p[:, :L] = -f(st["p_line"])
+        self.p[:, L:2 * L] = f(st["p_line"])
+        self.p[:, net.sl_dev] = f(st["p_dev"])[None]
+        self.th[:, :L] = f(st["th1"])
+        self.th[:, L:] = f(st["th2"])
+        self.v[:, :L] = f(st["v1"])
+        self.v[:, L:] = f(st["v2"])
+        self.u[:] = f(st["u"])
+        if rho_p is not None:
+            self.rho_p = float(rho_p)
+        if rho_theta is not None:
+            self.rho_th = float(rho_theta)
+        if it is not None:
+            self.it = int(it)
+        inner = st.get("inner")
+        if inner is not None:
+            x = f(inner)
+            o = 0
+            if len(self.ramp_idx):
+                m = self.ramp_A.shape[0]
+                for r in range(len(self.ramp_idx)):
+                    self.ramp_lam[r] = x[o:o + m]
+                    self.ramp_beta[r] = x[o + m:o + 2 * m]
+                    o += 2 * m
+            if net.B:
+                m = self.stor_h.shape[1]
+                for b in range(net.B):
+                    self.stor_lam[b] = x[o:o + m]
+                    self.stor_beta[b] = x[o + m:o + 2 * m]
+                    o += 2 * m
+            assert o == len(x)
+
     # -- state access
     def line_p(self):
         """Terminal-2 power of every line, ``[K+1, L, T]``."""

@@ -1,0 +1,324 @@
+"""ctypes binding of the C ABI in ``include/opf.h`` (argument marshalling only).
+
+Every function keeps the C name.  Errors raise :class:`OpfError` carrying the
+``opf_status`` code.  Host arrays are NumPy; device buffers are anything with a
+``data_ptr()`` (PyTorch tensors) and are passed with ``on_device=True``.
+There is no fallback: if the CUDA library is not built, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libopfmp.so")
+
+OPF_OK, OPF_EINVAL, OPF_ENOMEM, OPF_ECUDA, OPF_ETIMEOUT, OPF_ENONFINITE, OPF_ESTATE = range(7)
+
+F32P = C.POINTER(C.c_float)
+F64P = C.POINTER(C.c_double)
+I32P = C.POINTER(C.c_int32)
+
+
+class OpfError(RuntimeError):
+    def __init__(self, status, where, msg=""):
+        self.status = int(status)
+        super().__init__(f"{where}: {_status_str(status)} ({status}) {msg}".rstrip())
+
+
+class opf_network(C.Structure):
+    _fields_ = [
+        ("n_nodes", C.c_int32),
+        ("n_lines", C.c_int32), ("line_from", I32P), ("line_to", I32P),
+        ("line_b", F64P), ("line_u", F64P),
+        ("n_gens", C.c_int32), ("gen_node", I32P), ("gen_a", F64P), ("gen_b", F64P),
+        ("gen_pmin", F64P), ("gen_pmax", F64P), ("gen_ramp", F64P),
+        ("n_loads", C.c_int32), ("load_node", I32P), ("load_p", F64P), ("load_voll", F64P),
+        ("n_stor", C.c_int32), ("stor_node", I32P), ("stor_P", F64P), ("stor_dur", F64P),
+        ("stor_eff", F64P), ("stor_cost", F64P),
+    ]
+
+
+class opf_contingencies(C.Structure):
+    _fields_ = [("K", C.c_int32), ("outaged_line", I32P)]
+
+
+class opf_options(C.Structure):
+    _fields_ = [
+        ("rho_p", C.c_double), ("rho_theta", C.c_double), ("eps", C.c_double),
+        ("mu", C.c_double), ("gamma", C.c_double),
+        ("adapt_every", C.c_int32), ("inner_iters", C.c_int32), ("check_every", C.c_int32),
+        ("reserved0", C.c_int32),
+        ("barrier_timeout_cycles", C.c_int64),
+        ("cuda_stream", C.c_void_p),
+    ]
+
+
+class opf_state(C.Structure):
+    _fields_ = [("p_line", C.c_void_p), ("th1", C.c_void_p), ("th2", C.c_void_p),
+                ("v1", C.c_void_p), ("v2", C.c_void_p), ("p_dev", C.c_void_p),
+                ("u", C.c_void_p), ("inner", C.c_void_p)]
+
+
+class opf_info(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int64), ("converged", C.c_int32), ("status", C.c_int32),
+        ("rho_p", C.c_double), ("rho_theta", C.c_double), ("tolerance", C.c_double),
+        ("N", C.c_int32), ("L", C.c_int32), ("S", C.c_int32), ("T", C.c_int32),
+        ("K", C.c_int32), ("J", C.c_int32), ("n_ramp", C.c_int32), ("n_stor", C.c_int32),
+        ("inner_len", C.c_int64), ("device_bytes", C.c_int64),
+    ]
+
+
+EXPORTS = ["opf_default_options", "opf_create", "opf_iterate", "opf_residuals", "opf_solution",
+           "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info", "opf_destroy",
+           "opf_status_str", "opf_last_error", "opf_abi_version"]
+
+_lib = None
+
+
+def load_library(path=None):
+    """Load the CUDA library (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"CUDA library not built: {p} (run __graft_entry__.build())")
+    lib = C.CDLL(p)
+    lib.opf_default_options.argtypes = [C.POINTER(opf_options)]
+    lib.opf_default_options.restype = None
+    lib.opf_create.argtypes = [C.POINTER(opf_network), C.c_int32, C.POINTER(opf_contingencies),
+                               C.POINTER(opf_options), C.POINTER(C.c_void_p)]
+    lib.opf_iterate.argtypes = [C.c_void_p, C.c_int32, C.c_double]
+    lib.opf_residuals.argtypes = [C.c_void_p, F64P]
+    lib.opf_solution.argtypes = [C.c_void_p, C.c_int32, F64P, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]
+    lib.opf_get_state.argtypes = [C.c_void_p, C.c_int32, C.POINTER(opf_state)]
+    lib.opf_set_state.argtypes = [C.c_void_p, C.c_int32, C.POINTER(opf_state)]
+    lib.opf_reset.argtypes = [C.c_void_p]
+    lib.opf_get_info.argtypes = [C.c_void_p, C.POINTER(opf_info)]
+    lib.opf_destroy.argtypes = [C.c_void_p]
+    lib.opf_destroy.restype = None
+    lib.opf_status_str.argtypes = [C.c_int]
+    lib.opf_status_str.restype = C.c_char_p
+    lib.opf_last_error.argtypes = []
+    lib.opf_last_error.restype = C.c_char_p
+    lib.opf_abi_version.argtypes = []
+    lib.opf_abi_version.restype = C.c_int32
+    for name in ("opf_create", "opf_iterate", "opf_residuals", "opf_solution", "opf_get_state",
+                 "opf_set_state", "opf_reset", "opf_get_info"):
+        getattr(lib, name).restype = C.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _status_str(s):
+    try:
+        return load_library().opf_status_str(int(s)).decode()
+    except OSError:
+        return "status"
+
+
+def _check(status, where):
+    if status != OPF_OK:
+        raise OpfError(status, where, opf_last_error())
+
+
+def opf_status_str(status):
+    return load_library().opf_status_str(int(status)).decode()
+
+
+def opf_last_error():
+    return load_library().opf_last_error().decode()
+
+
+def opf_abi_version():
+    return int(load_library().opf_abi_version())
+
+
+def opf_default_options(**overrides):
+    o = opf_options()
+    load_library().opf_default_options(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None and a.size else C.POINTER(ctype)()
+
+
+def opf_create(case, options=None, stream=None):
+    """Create a solver context from a case dict (see ``gridgen``).  Returns the handle."""
+    lib = load_library()
+    T = int(case["T"])
+    keep = {}
+
+    def f64(name, shape=None):
+        a = np.ascontiguousarray(np.asarray(case[name], dtype=np.float64))
+        keep[name] = a
+        return _ptr(a, C.c_double)
+
+    def i32(name):
+        a = np.ascontiguousarray(np.asarray(case[name], dtype=np.int32))
+        keep[name] = a
+        return _ptr(a, C.c_int32)
+
+    net = opf_network(
+        n_nodes=int(case["n_nodes"]),
+        n_lines=len(case["line_from"]), line_from=i32("line_from"), line_to=i32("line_to"),
+        line_b=f64("line_b"), line_u=f64("line_u"),
+        n_gens=len(case["gen_node"]), gen_node=i32("gen_node"), gen_a=f64("gen_a"),
+        gen_b=f64("gen_b"), gen_pmin=f64("gen_pmin"), gen_pmax=f64("gen_pmax"),
+        gen_ramp=f64("gen_ramp"),
+        n_loads=len(case["load_node"]), load_node=i32("load_node"), load_p=f64("load_p"),
+        load_voll=f64("load_voll"),
+        n_stor=len(case["stor_node"]), stor_node=i32("stor_node"), stor_P=f64("stor_P"),
+        stor_dur=f64("stor_dur"), stor_eff=f64("stor_eff"), stor_cost=f64("stor_cost"),
+    )
+    out = np.ascontiguousarray(np.asarray(case["outaged"], dtype=np.int32))
+    ctg = opf_contingencies(K=len(out), outaged_line=_ptr(out, C.c_int32))
+    if options is None:
+        options = opf_default_options()
+    elif isinstance(options, dict):
+        options = opf_default_options(**options)
+    if stream is not None:
+        options.cuda_stream = C.c_void_p(int(stream))
+    h = C.c_void_p()
+    _check(lib.opf_create(C.byref(net), T, C.byref(ctg), C.byref(options), C.byref(h)),
+           "opf_create")
+    return h
+
+
+def opf_destroy(h):
+    if h:
+        load_library().opf_destroy(h)
+
+
+def opf_iterate(h, n_iters, rho=0.0):
+    _check(load_library().opf_iterate(h, int(n_iters), float(rho)), "opf_iterate")
+
+
+def opf_residuals(h, raise_on_status=True):
+    """Residuals of the last iteration (6 FP64 values) and the device status."""
+    out = np.zeros(6)
+    st = load_library().opf_residuals(h, out.ctypes.data_as(F64P))
+    if raise_on_status:
+        _check(st, "opf_residuals")
+        return out
+    return out, st
+
+
+def opf_get_info(h):
+    info = opf_info()
+    _check(load_library().opf_get_info(h, C.byref(info)), "opf_get_info")
+    return {name: getattr(info, name) for name, _ in opf_info._fields_}
+
+
+def _addr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def opf_solution(h, on_device=False, objective=True, p_dev=None, p_line=None, theta_node=None,
+                 price=None):
+    """Fill the given output buffers (NumPy float32 on host, tensors on device).
+
+    Returns the objective (float) or None."""
+    obj = C.c_double(0.0)
+    st = load_library().opf_solution(
+        h, int(bool(on_device)), C.byref(obj) if objective else F64P(),
+        _addr(p_dev), _addr(p_line), _addr(theta_node), _addr(price))
+    _check(st, "opf_solution")
+    return obj.value if objective else None
+
+
+STATE_FIELDS = ("p_line", "th1", "th2", "v1", "v2", "p_dev", "u", "inner")
+
+
+def state_shapes(info):
+    Kp, L, N, S, T = info["K"] + 1, info["L"], info["N"], info["S"], info["T"]
+    return dict(p_line=(Kp, L, T), th1=(Kp, L, T), th2=(Kp, L, T), v1=(Kp, L, T),
+                v2=(Kp, L, T), p_dev=(S, T), u=(Kp, N, T), inner=(info["inner_len"],))
+
+
+def opf_get_state(h, on_device=False, out=None):
+    """Export the state into ``out`` (dict of buffers) or new host arrays."""
+    info = opf_get_info(h)
+    if out is None:
+        if on_device:
+            raise ValueError("pass device buffers in `out` for on_device=True")
+        out = {k: np.zeros(s, np.float32) for k, s in state_shapes(info).items()}
+    st = opf_state(**{k: _addr(out.get(k)) for k in STATE_FIELDS})
+    _check(load_library().opf_get_state(h, int(bool(on_device)), C.byref(st)), "opf_get_state")
+    return out
+
+
+def opf_set_state(h, state, on_device=False):
+    """Import a state dict (missing keys are zeroed on the device)."""
+    keep = {}
+    ptrs = {}
+    for k in STATE_FIELDS:
+        x = state.get(k)
+        if x is None:
+            ptrs[k] = None
+            continue
+        if not on_device:
+            x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+            keep[k] = x
+        ptrs[k] = _addr(x)
+    st = opf_state(**ptrs)
+    _check(load_library().opf_set_state(h, int(bool(on_device)), C.byref(st)), "opf_set_state")
+
+
+def opf_reset(h):
+    _check(load_library().opf_reset(h), "opf_reset")
+
+
+class Solver:
+    """Owner of one context (calls opf_destroy when collected)."""
+
+    def __init__(self, case, options=None, stream=None):
+        self.h = opf_create(case, options, stream)
+        self.info = opf_get_info(self.h)
+
+    def iterate(self, n, rho=0.0):
+        opf_iterate(self.h, n, rho)
+
+    def residuals(self):
+        return opf_residuals(self.h)
+
+    def get_info(self):
+        return opf_get_info(self.h)
+
+    def state(self):
+        return opf_get_state(self.h)
+
+    def set_state(self, st):
+        opf_set_state(self.h, st)
+
+    def solution(self):
+        i = self.info
+        Kp, L, N, S, T = i["K"] + 1, i["L"], i["N"], i["S"], i["T"]
+        out = dict(p_dev=np.zeros((S, T), np.float32), p_line=np.zeros((Kp, L, T), np.float32),
+                   theta_node=np.zeros((Kp, N, T), np.float32), price=np.zeros((N, T), np.float32))
+        out["objective"] = opf_solution(self.h, False, True, **out)
+        return out
+
+    def close(self):
+        if self.h:
+            opf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,775 @@
+// Host side of the C ABI declared in include/opf.h: input validation, the
+// CSR-by-node incidence (Section 4.3 scatter/gather as node-ordered lists),
+// device memory (one arena per context) and the entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "opf.h"
+#include "opf_internal.h"
+
+using opfk::DevScalars;
+using opfk::Params;
+
+namespace {
+
+thread_local std::string g_err;
+
+opf_status fail(opf_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+opf_status cuda_fail(cudaError_t e, const char *what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? OPF_ENOMEM : OPF_ECUDA;
+}
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr int kMaxT = 2048;
+
+// bump allocator over one cudaMalloc
+struct Arena {
+  size_t off = 0;
+  char *base = nullptr;
+  template <class T>
+  T *take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace
+
+struct opf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  opf_options opt{};
+  int N = 0, L = 0, T = 0, K = 0, Kp = 0, S = 0, G = 0, D = 0, B = 0;
+  int n_closed = 0, n_ramp = 0, n_stor = 0;
+  int grid = 0;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  Params P{};
+  float *price_stage = nullptr;
+  // host copies used for the objective and the inner-state layout
+  std::vector<double> gen_a, gen_b, load_voll, load_p, stor_cost;
+  std::vector<int> ramp_gen;  // generator index of each ramp device
+  double tol = 0.0;
+  int host_status = 0;        // sticky status seen by the host
+};
+
+extern "C" {
+
+void opf_default_options(opf_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->rho_p = 1.0;
+  o->rho_theta = 1.0;
+  o->eps = 1e-4;
+  o->mu = 2.0;
+  o->gamma = 1.1;
+  o->adapt_every = 10;
+  o->inner_iters = 10;
+  o->check_every = 10;
+  o->barrier_timeout_cycles = 0;
+  o->cuda_stream = nullptr;
+}
+
+const char *opf_status_str(opf_status s) {
+  switch (s) {
+    case OPF_OK: return "ok";
+    case OPF_EINVAL: return "invalid argument";
+    case OPF_ENOMEM: return "out of memory";
+    case OPF_ECUDA: return "CUDA error";
+    case OPF_ETIMEOUT: return "grid barrier timeout";
+    case OPF_ENONFINITE: return "non-finite residual";
+    case OPF_ESTATE: return "state unusable after an earlier device error";
+  }
+  return "unknown status";
+}
+
+const char *opf_last_error(void) { return g_err.c_str(); }
+
+int32_t opf_abi_version(void) { return OPF_ABI_VERSION; }
+
+}  // extern "C"
+
+namespace {
+
+bool finite_all(const double *a, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+opf_status validate(const opf_network *net, int T, const opf_contingencies *ctg,
+                    const opf_options &o) {
+  if (!net) return fail(OPF_EINVAL, "network is NULL");
+  if (T < 1 || T > kMaxT) return fail(OPF_EINVAL, "horizon T must be in [1, 2048]");
+  if (net->n_nodes < 1) return fail(OPF_EINVAL, "n_nodes must be >= 1");
+  if (net->n_lines < 0 || net->n_gens < 0 || net->n_loads < 0 || net->n_stor < 0)
+    return fail(OPF_EINVAL, "negative device count");
+  const int N = net->n_nodes;
+  auto bad_nodes = [N](const int32_t *a, int n) {
+    for (int i = 0; i < n; ++i)
+      if (a[i] < 0 || a[i] >= N) return true;
+    return false;
+  };
+  const size_t nT = (size_t)T;
+  if (net->n_lines) {
+    if (!net->line_from || !net->line_to || !net->line_b || !net->line_u)
+      return fail(OPF_EINVAL, "line arrays missing");
+    if (bad_nodes(net->line_from, net->n_lines) || bad_nodes(net->line_to, net->n_lines))
+      return fail(OPF_EINVAL, "line node id out of range");
+    for (int l = 0; l < net->n_lines; ++l) {
+      if (net->line_from[l] == net->line_to[l]) return fail(OPF_EINVAL, "line connects a node to itself");
+      if (!(net->line_b[l] > 0.0) || !std::isfinite(net->line_b[l]))
+        return fail(OPF_EINVAL, "line susceptance must be finite and > 0");
+      if (!(net->line_u[l] >= 0.0) || !std::isfinite(net->line_u[l]))
+        return fail(OPF_EINVAL, "line limit must be finite and >= 0");
+    }
+  }
+  if (net->n_gens) {
+    if (!net->gen_node || !net->gen_a || !net->gen_b || !net->gen_pmin || !net->gen_pmax || !net->gen_ramp)
+      return fail(OPF_EINVAL, "generator arrays missing");
+    if (bad_nodes(net->gen_node, net->n_gens)) return fail(OPF_EINVAL, "generator node id out of range");
+    if (!finite_all(net->gen_a, net->n_gens) || !finite_all(net->gen_b, net->n_gens) ||
+        !finite_all(net->gen_ramp, net->n_gens) || !finite_all(net->gen_pmin, net->n_gens * nT) ||
+        !finite_all(net->gen_pmax, net->n_gens * nT))
+      return fail(OPF_EINVAL, "non-finite generator data");
+    for (int g = 0; g < net->n_gens; ++g) {
+      if (net->gen_a[g] < 0) return fail(OPF_EINVAL, "generator quadratic cost must be >= 0");
+      for (int t = 0; t < T; ++t)
+        if (net->gen_pmin[g * nT + t] > net->gen_pmax[g * nT + t])
+          return fail(OPF_EINVAL, "generator pmin > pmax");
+    }
+  }
+  if (net->n_loads) {
+    if (!net->load_node || !net->load_p || !net->load_voll) return fail(OPF_EINVAL, "load arrays missing");
+    if (bad_nodes(net->load_node, net->n_loads)) return fail(OPF_EINVAL, "load node id out of range");
+    if (!finite_all(net->load_p, net->n_loads * nT) || !finite_all(net->load_voll, net->n_loads))
+      return fail(OPF_EINVAL, "non-finite load data");
+  }
+  if (net->n_stor) {
+    if (!net->stor_node || !net->stor_P || !net->stor_dur || !net->stor_eff || !net->stor_cost)
+      return fail(OPF_EINVAL, "battery arrays missing");
+    if (bad_nodes(net->stor_node, net->n_stor)) return fail(OPF_EINVAL, "battery node id out of range");
+    for (int b = 0; b < net->n_stor; ++b) {
+      if (!(net->stor_P[b] >= 0) || !(net->stor_dur[b] >= 0) || !(net->stor_eff[b] > 0) ||
+          !(net->stor_eff[b] <= 1) || !(net->stor_cost[b] >= 0) || !std::isfinite(net->stor_P[b]) ||
+          !std::isfinite(net->stor_dur[b]) || !std::isfinite(net->stor_cost[b]))
+        return fail(OPF_EINVAL, "battery data out of range");
+    }
+  }
+  if (ctg && ctg->K < 0) return fail(OPF_EINVAL, "K must be >= 0");
+  if (ctg && ctg->K > 0) {
+    if (!ctg->outaged_line) return fail(OPF_EINVAL, "outaged_line is NULL");
+    for (int k = 0; k < ctg->K; ++k)
+      if (ctg->outaged_line[k] < -1 || ctg->outaged_line[k] >= net->n_lines)
+        return fail(OPF_EINVAL, "outaged line index out of range");
+  }
+  if (!(o.rho_p > 0) || !(o.rho_theta > 0) || !std::isfinite(o.rho_p) || !std::isfinite(o.rho_theta))
+    return fail(OPF_EINVAL, "penalties must be finite and > 0");
+  if (!(o.mu > 0) || !(o.gamma >= 1) || o.inner_iters < 1 || o.adapt_every < 0 || o.check_every < 0 ||
+      !std::isfinite(o.eps))
+    return fail(OPF_EINVAL, "invalid options");
+  return OPF_OK;
+}
+
+// The arena layout; called once with a null base to size it.
+void carve(opf_ctx *c, Arena &a) {
+  Params &p = c->P;
+  const size_t KLT = (size_t)c->Kp * c->L * c->T, KNT = (size_t)c->Kp * c->N * c->T;
+  const size_t NT = (size_t)c->N * c->T, ST = (size_t)c->S * c->T;
+  const int T = c->T, Tp = c->T + 1;
+  // state first (zeroed on reset)
+  p.P = a.take<float>(KLT);
+  p.TH1 = a.take<float>(KLT);
+  p.TH2 = a.take<float>(KLT);
+  p.V1 = a.take<float>(KLT);
+  p.V2 = a.take<float>(KLT);
+  p.DP = a.take<float>(KLT);
+  p.U = a.take<float>(KNT);
+  p.PBAR = a.take<float>(KNT);
+  p.THBAR = a.take<float>(KNT);
+  p.SPBAR = a.take<float>(NT);
+  p.SU = a.take<float>(NT);
+  p.PD = a.take<float>(ST);
+  p.DPD = a.take<float>(ST);
+  p.ramp_lam = a.take<float>((size_t)c->n_ramp * opfk::RG_N * T);
+  p.ramp_beta = a.take<float>((size_t)c->n_ramp * opfk::RG_N * T);
+  p.ramp_m = a.take<float>((size_t)c->n_ramp * T);
+  p.ramp_rho = a.take<float>(c->n_ramp);
+  p.stor_lam = a.take<float>((size_t)c->n_stor * opfk::SG_N * Tp);
+  p.stor_beta = a.take<float>((size_t)c->n_stor * opfk::SG_N * Tp);
+  p.stor_m = a.take<float>((size_t)c->n_stor * Tp);
+  p.stor_rho = a.take<float>(c->n_stor);
+  p.stor_delta = a.take<float>((size_t)c->n_stor * T);
+  p.sc = a.take<DevScalars>(1);
+  // parameters
+  p.line_n1 = a.take<int>(c->L);
+  p.line_n2 = a.take<int>(c->L);
+  p.line_b = a.take<float>(c->L);
+  p.line_u = a.take<float>(c->L);
+  p.out_line = a.take<int>(c->Kp);
+  p.lcsr_ptr = a.take<int>(c->N + 1);
+  p.lcsr_idx = a.take<int>(2 * (size_t)c->L);
+  p.dcsr_ptr = a.take<int>(c->N + 1);
+  p.dcsr_idx = a.take<int>(c->S);
+  p.cnt_p = a.take<float>(c->N);
+  p.cnt_th = a.take<float>(c->N);
+  p.dev_node = a.take<int>(c->S);
+  p.dev_a = a.take<float>(c->S);
+  p.dev_b = a.take<float>(c->S);
+  p.dev_lo = a.take<float>(ST);
+  p.dev_hi = a.take<float>(ST);
+  p.closed_ids = a.take<int>(c->n_closed);
+  p.ramp_ids = a.take<int>(c->n_ramp);
+  p.ramp_R = a.take<float>(c->n_ramp);
+  p.stor_ids = a.take<int>(c->n_stor);
+  p.stor_eff = a.take<float>(c->n_stor);
+  p.stor_P = a.take<float>(c->n_stor);
+  p.stor_dur = a.take<float>(c->n_stor);
+  p.stor_cost = a.take<float>(c->n_stor);
+  // scratch
+  p.partials = a.take<double>((size_t)2 * c->grid * opfk::NSLOT);
+  p.bar_count = a.take<unsigned>(4);  // count, gen, err (as int), pad
+  p.bar_gen = p.bar_count ? p.bar_count + 1 : nullptr;
+  p.err = p.bar_count ? reinterpret_cast<int *>(p.bar_count + 2) : nullptr;
+  c->price_stage = a.take<float>(NT);
+}
+
+size_t state_bytes(const opf_ctx *c) {
+  // everything carved before the scalars block, plus the scalars
+  return (size_t)(reinterpret_cast<const char *>(c->P.sc) - c->arena);
+}
+
+opf_status init_scalars(opf_ctx *c) {
+  DevScalars sc{};
+  sc.rho_p = c->opt.rho_p;
+  sc.rho_th = c->opt.rho_theta;
+  sc.su = 1.0;
+  sc.sv = 1.0;
+  sc.v_fresh = 1;
+  CK(cudaMemcpyAsync(c->P.sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return OPF_OK;
+}
+
+opf_status read_scalars(opf_ctx *c, DevScalars *sc) {
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(sc, c->P.sc, sizeof(*sc), cudaMemcpyDeviceToHost));
+  if (sc->status) c->host_status = sc->status;
+  return OPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies *ctg,
+                      const opf_options *opt_in, opf_ctx **out) {
+  if (!out) return fail(OPF_EINVAL, "out is NULL");
+  *out = nullptr;
+  opf_options opt;
+  opf_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.barrier_timeout_cycles <= 0) opt.barrier_timeout_cycles = 2000000000LL;
+  opf_status st = validate(net, T, ctg, opt);
+  if (st != OPF_OK) return st;
+
+  auto *c = new (std::nothrow) opf_ctx();
+  if (!c) return fail(OPF_ENOMEM, "host allocation failed");
+  c->opt = opt;
+  c->stream = (cudaStream_t)opt.cuda_stream;
+  c->N = net->n_nodes;
+  c->L = net->n_lines;
+  c->T = T;
+  c->K = ctg ? ctg->K : 0;
+  c->Kp = c->K + 1;
+  c->G = net->n_gens;
+  c->D = net->n_loads;
+  c->B = net->n_stor;
+  c->S = c->G + c->D + c->B;
+  const int N = c->N, L = c->L, S = c->S, G = c->G, D = c->D;
+  const size_t nT = (size_t)T;
+
+  // node-ordered incidence; every node needs a terminal
+  std::vector<int> lcnt(N, 0), dcnt(N, 0);
+  for (int l = 0; l < L; ++l) {
+    lcnt[net->line_from[l]]++;
+    lcnt[net->line_to[l]]++;
+  }
+  std::vector<int> dev_node(S);
+  for (int g = 0; g < G; ++g) dev_node[g] = net->gen_node[g];
+  for (int d = 0; d < D; ++d) dev_node[G + d] = net->load_node[d];
+  for (int b = 0; b < c->B; ++b) dev_node[G + D + b] = net->stor_node[b];
+  for (int d = 0; d < S; ++d) dcnt[dev_node[d]]++;
+  for (int n = 0; n < N; ++n)
+    if (lcnt[n] + dcnt[n] == 0) {
+      delete c;
+      return fail(OPF_EINVAL, "node " + std::to_string(n) + " has no terminal");
+    }
+  std::vector<int> lptr(N + 1, 0), dptr(N + 1, 0);
+  for (int n = 0; n < N; ++n) {
+    lptr[n + 1] = lptr[n] + lcnt[n];
+    dptr[n + 1] = dptr[n] + dcnt[n];
+  }
+  std::vector<int> lidx(2 * (size_t)L), didx(S);
+  {
+    std::vector<int> lp(lptr.begin(), lptr.end() - 1), dp(dptr.begin(), dptr.end() - 1);
+    for (int l = 0; l < L; ++l) {
+      lidx[lp[net->line_from[l]]++] = 2 * l;      // terminal 1
+      lidx[lp[net->line_to[l]]++] = 2 * l + 1;    // terminal 2
+    }
+    for (int d = 0; d < S; ++d) didx[dp[dev_node[d]]++] = d;
+  }
+  std::vector<float> cnt_p(N), cnt_th(N);
+  for (int n = 0; n < N; ++n) {
+    cnt_p[n] = (float)(lcnt[n] + dcnt[n]);
+    cnt_th[n] = (float)lcnt[n];
+  }
+
+  // device classes and closed-form parameters
+  std::vector<float> dev_a(S, 0.f), dev_b(S, 0.f), lo(S * nT, 0.f), hi(S * nT, 0.f);
+  std::vector<int> closed, ramp, stor;
+  std::vector<float> rampR;
+  for (int g = 0; g < G; ++g) {
+    dev_a[g] = (float)net->gen_a[g];
+    dev_b[g] = (float)net->gen_b[g];
+    for (size_t t = 0; t < nT; ++t) {
+      lo[g * nT + t] = (float)net->gen_pmin[g * nT + t];
+      hi[g * nT + t] = (float)net->gen_pmax[g * nT + t];
+    }
+    if (net->gen_ramp[g] >= 0 && T > 1) {
+      ramp.push_back(g);
+      rampR.push_back((float)net->gen_ramp[g]);
+      c->ramp_gen.push_back(g);
+    } else {
+      closed.push_back(g);
+    }
+  }
+  for (int d = 0; d < D; ++d) {
+    const bool fixed = net->load_voll[d] < 0;
+    dev_a[G + d] = 0.f;
+    dev_b[G + d] = fixed ? 0.f : (float)net->load_voll[d];
+    for (size_t t = 0; t < nT; ++t) {
+      const float P = (float)net->load_p[d * nT + t];
+      lo[(G + d) * nT + t] = -P;
+      hi[(G + d) * nT + t] = fixed ? -P : 0.f;
+    }
+    closed.push_back(G + d);
+  }
+  std::vector<float> seff, sP, sdur, scost;
+  for (int b = 0; b < c->B; ++b) {
+    stor.push_back(G + D + b);
+    seff.push_back((float)net->stor_eff[b]);
+    sP.push_back((float)net->stor_P[b]);
+    sdur.push_back((float)net->stor_dur[b]);
+    scost.push_back((float)net->stor_cost[b]);
+  }
+  c->n_closed = (int)closed.size();
+  c->n_ramp = (int)ramp.size();
+  c->n_stor = (int)stor.size();
+
+  // host copies for the objective
+  c->gen_a.assign(net->gen_a, net->gen_a + G);
+  c->gen_b.assign(net->gen_b, net->gen_b + G);
+  c->load_voll.assign(net->load_voll, net->load_voll + D);
+  c->load_p.assign(net->load_p, net->load_p + D * nT);
+  c->stor_cost.assign(net->stor_cost, net->stor_cost + c->B);
+
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  if (opfk_max_grid(T, &c->grid) != 0) {
+    delete c;
+    return fail(OPF_ECUDA, "occupancy query for the iteration kernel failed");
+  }
+  Arena a;
+  carve(c, a);
+  c->arena_bytes = a.off + 256;
+  e = cudaMalloc(&c->arena, c->arena_bytes);
+  if (e != cudaSuccess) {
+    opf_status s = cuda_fail(e, "cudaMalloc(arena)");
+    delete c;
+    return s;
+  }
+  a = Arena();
+  a.base = c->arena;
+  carve(c, a);
+
+  Params &p = c->P;
+  p.N = N;
+  p.L = L;
+  p.T = T;
+  p.Kp = c->Kp;
+  p.S = S;
+  p.n_closed = c->n_closed;
+  p.n_ramp = c->n_ramp;
+  p.n_stor = c->n_stor;
+  p.eps = opt.eps;
+  p.mu = opt.mu;
+  p.gamma = opt.gamma;
+  p.adapt_every = opt.adapt_every;
+  p.check_every = opt.check_every;
+  p.inner_iters = opt.inner_iters;
+  p.barrier_budget = opt.barrier_timeout_cycles;
+  c->tol = opt.eps * std::sqrt(2.0 * (2.0 * L + S) * T * c->Kp);
+  p.tol = c->tol;
+
+  std::vector<int> n1(L), n2(L), outl(c->Kp, -1);
+  std::vector<float> lb(L), lu(L);
+  for (int l = 0; l < L; ++l) {
+    n1[l] = net->line_from[l];
+    n2[l] = net->line_to[l];
+    lb[l] = (float)net->line_b[l];
+    lu[l] = (float)net->line_u[l];
+  }
+  for (int k = 0; k < c->K; ++k) outl[k + 1] = ctg->outaged_line[k];
+
+  opf_status s = OPF_OK;
+  auto up = [&](const void *dst, const auto &v) {
+    if (s != OPF_OK || v.empty()) return;
+    cudaError_t ee = cudaMemcpyAsync(const_cast<void *>(dst), v.data(), v.size() * sizeof(v[0]),
+                                     cudaMemcpyHostToDevice, c->stream);
+    if (ee != cudaSuccess) s = cuda_fail(ee, "cudaMemcpyAsync(parameters)");
+  };
+  e = cudaMemsetAsync(c->arena, 0, c->arena_bytes, c->stream);
+  if (e != cudaSuccess) s = cuda_fail(e, "cudaMemsetAsync(arena)");
+  up(p.line_n1, n1);
+  up(p.line_n2, n2);
+  up(p.line_b, lb);
+  up(p.line_u, lu);
+  up(p.out_line, outl);
+  up(p.lcsr_ptr, lptr);
+  up(p.lcsr_idx, lidx);
+  up(p.dcsr_ptr, dptr);
+  up(p.dcsr_idx, didx);
+  up(p.cnt_p, cnt_p);
+  up(p.cnt_th, cnt_th);
+  up(p.dev_node, dev_node);
+  up(p.dev_a, dev_a);
+  up(p.dev_b, dev_b);
+  up(p.dev_lo, lo);
+  up(p.dev_hi, hi);
+  up(p.closed_ids, closed);
+  up(p.ramp_ids, ramp);
+  up(p.ramp_R, rampR);
+  up(p.stor_ids, stor);
+  up(p.stor_eff, seff);
+  up(p.stor_P, sP);
+  up(p.stor_dur, sdur);
+  up(p.stor_cost, scost);
+  if (s == OPF_OK) s = init_scalars(c);
+  if (s != OPF_OK) {
+    cudaFree(c->arena);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return OPF_OK;
+}
+
+void opf_destroy(opf_ctx *c) {
+  if (!c) return;
+  if (c->arena) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->arena);
+  }
+  delete c;
+}
+
+opf_status opf_iterate(opf_ctx *c, int32_t n_iters, double rho) {
+  if (!c) return fail(OPF_EINVAL, "ctx is NULL");
+  if (c->host_status == OPF_ETIMEOUT || c->host_status == OPF_ESTATE)
+    return fail(OPF_ESTATE, "state unusable after a barrier timeout; call opf_reset or opf_set_state");
+  if (n_iters < 0) return fail(OPF_EINVAL, "n_iters must be >= 0");
+  if (rho > 0) {
+    if (!std::isfinite(rho)) return fail(OPF_EINVAL, "rho must be finite");
+    if (opfk_set_rho_launch(c->P.sc, rho, c->stream) != 0) return fail(OPF_ECUDA, "set_rho launch failed");
+  }
+  if (n_iters == 0) return OPF_OK;
+  CK(cudaMemsetAsync(c->P.bar_count, 0, 4 * sizeof(unsigned), c->stream));
+  Params p = c->P;
+  p.n_iters = n_iters;
+  char msg[256];
+  int grid = c->grid;
+  if (opfk_iteration_launch(p, c->stream, &grid, msg, sizeof(msg)) != 0) return fail(OPF_ECUDA, msg);
+  return OPF_OK;
+}
+
+opf_status opf_residuals(opf_ctx *c, double out[6]) {
+  if (!c || !out) return fail(OPF_EINVAL, "NULL argument");
+  DevScalars sc;
+  opf_status s = read_scalars(c, &sc);
+  if (s != OPF_OK) return s;
+  for (int j = 0; j < 6; ++j) out[j] = sc.res[j];
+  return (opf_status)sc.status;
+}
+
+opf_status opf_get_info(opf_ctx *c, opf_info *info) {
+  if (!c || !info) return fail(OPF_EINVAL, "NULL argument");
+  DevScalars sc;
+  opf_status s = read_scalars(c, &sc);
+  if (s != OPF_OK) return s;
+  std::memset(info, 0, sizeof(*info));
+  info->iterations = sc.it;
+  info->converged = sc.converged;
+  info->status = c->host_status;
+  info->rho_p = sc.rho_p;
+  info->rho_theta = sc.rho_th;
+  info->tolerance = c->tol;
+  info->N = c->N;
+  info->L = c->L;
+  info->S = c->S;
+  info->T = c->T;
+  info->K = c->K;
+  info->J = 2 * c->L + c->S;
+  info->n_ramp = c->n_ramp;
+  info->n_stor = c->n_stor;
+  info->inner_len = (int64_t)c->n_ramp * 2 * (4 * (int64_t)c->T - 2) +
+                    (int64_t)c->n_stor * 2 * (8 * (int64_t)c->T + 4);
+  info->device_bytes = (int64_t)c->arena_bytes;
+  return OPF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// copy `n` floats from device `src` to a caller buffer (host or device)
+opf_status copy_out(float *dst, const float *src, size_t n, int on_device, cudaStream_t s) {
+  if (!dst || n == 0) return OPF_OK;
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  return OPF_OK;
+}
+
+opf_status copy_in(float *dst, const float *src, size_t n, int on_device, cudaStream_t s) {
+  if (n == 0) return OPF_OK;
+  if (!src) {
+    CK(cudaMemsetAsync(dst, 0, n * sizeof(float), s));
+    return OPF_OK;
+  }
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  return OPF_OK;
+}
+
+// Build the list of (canonical index -> (array, device index)) pairs.
+struct InnerEntry {
+  int arr;     // 0 ramp_lam, 1 ramp_beta, 2 stor_lam, 3 stor_beta, -1 always zero
+  size_t idx;
+};
+
+std::vector<InnerEntry> inner_layout(const opf_ctx *c) {
+  const int T = c->T, Tp = T + 1;
+  std::vector<InnerEntry> v;
+  for (int r = 0; r < c->n_ramp; ++r) {
+    const size_t base = (size_t)r * opfk::RG_N * T;
+    std::vector<size_t> rows;
+    for (int t = 0; t < T; ++t) rows.push_back(base + opfk::RG_UP * T + t);
+    for (int t = 0; t < T; ++t) rows.push_back(base + opfk::RG_LO * T + t);
+    for (int t = 0; t < T - 1; ++t) rows.push_back(base + opfk::RG_RU * T + t);
+    for (int t = 0; t < T - 1; ++t) rows.push_back(base + opfk::RG_RD * T + t);
+    for (size_t x : rows) v.push_back({0, x});
+    for (size_t x : rows) v.push_back({1, x});
+  }
+  for (int b = 0; b < c->n_stor; ++b) {
+    const size_t base = (size_t)b * opfk::SG_N * Tp;
+    std::vector<std::pair<size_t, bool>> rows;  // (device index, equality row)
+    for (int t = 0; t < T; ++t) rows.push_back({base + opfk::SG_E1 * Tp + t, true});
+    for (int t = 0; t < T; ++t) rows.push_back({base + opfk::SG_E2 * Tp + t, true});
+    rows.push_back({base + opfk::SG_E3 * Tp + 0, true});
+    rows.push_back({base + opfk::SG_E3 * Tp + 1, true});
+    for (int t = 0; t < T; ++t) rows.push_back({base + opfk::SG_CU * Tp + t, false});
+    for (int t = 0; t < T; ++t) rows.push_back({base + opfk::SG_CL * Tp + t, false});
+    for (int t = 0; t < T; ++t) rows.push_back({base + opfk::SG_DU * Tp + t, false});
+    for (int t = 0; t < T; ++t) rows.push_back({base + opfk::SG_DL * Tp + t, false});
+    for (int t = 0; t < Tp; ++t) rows.push_back({base + opfk::SG_SU * Tp + t, false});
+    for (int t = 0; t < Tp; ++t) rows.push_back({base + opfk::SG_SL * Tp + t, false});
+    for (auto &x : rows) v.push_back({2, x.first});
+    for (auto &x : rows) v.push_back({x.second ? -1 : 3, x.first});
+  }
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+opf_status opf_solution(opf_ctx *c, int32_t on_device, double *objective, float *p_dev, float *p_line,
+                        float *theta_node, float *price) {
+  if (!c) return fail(OPF_EINVAL, "ctx is NULL");
+  const size_t T = c->T;
+  opf_status s;
+  if ((s = copy_out(p_dev, c->P.PD, (size_t)c->S * T, on_device, c->stream)) != OPF_OK) return s;
+  if ((s = copy_out(p_line, c->P.P, (size_t)c->Kp * c->L * T, on_device, c->stream)) != OPF_OK) return s;
+  if ((s = copy_out(theta_node, c->P.THBAR, (size_t)c->Kp * c->N * T, on_device, c->stream)) != OPF_OK) return s;
+  if (price) {
+    float *dst = on_device ? price : c->price_stage;
+    if (opfk_price_launch(c->P, dst, c->stream) != 0) return fail(OPF_ECUDA, "price kernel launch failed");
+    if (!on_device) CK(cudaMemcpyAsync(price, c->price_stage, (size_t)c->N * T * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (objective) {
+    std::vector<float> pd((size_t)c->S * T), dl((size_t)c->n_stor * T);
+    CK(cudaMemcpyAsync(pd.data(), c->P.PD, pd.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    if (!dl.empty())
+      CK(cudaMemcpyAsync(dl.data(), c->P.stor_delta, dl.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double f = 0.0;
+    for (int g = 0; g < c->G; ++g)
+      for (size_t t = 0; t < T; ++t) {
+        const double x = pd[g * T + t];
+        f += c->gen_a[g] * x * x + c->gen_b[g] * x;
+      }
+    for (int d = 0; d < c->D; ++d) {
+      if (c->load_voll[d] < 0) continue;
+      for (size_t t = 0; t < T; ++t) f += c->load_voll[d] * ((double)pd[(c->G + d) * T + t] + c->load_p[d * T + t]);
+    }
+    for (int b = 0; b < c->n_stor; ++b)
+      for (size_t t = 0; t < T; ++t) f += c->stor_cost[b] * (double)dl[b * T + t];
+    *objective = f;
+  }
+  DevScalars sc;
+  if ((s = read_scalars(c, &sc)) != OPF_OK) return s;
+  return (opf_status)sc.status;
+}
+
+opf_status opf_get_state(opf_ctx *c, int32_t on_device, const opf_state *dst) {
+  if (!c || !dst) return fail(OPF_EINVAL, "NULL argument");
+  const size_t KLT = (size_t)c->Kp * c->L * c->T, KNT = (size_t)c->Kp * c->N * c->T;
+  opf_status s;
+  if ((s = copy_out(dst->p_line, c->P.P, KLT, on_device, c->stream)) != OPF_OK) return s;
+  if ((s = copy_out(dst->th1, c->P.TH1, KLT, on_device, c->stream)) != OPF_OK) return s;
+  if ((s = copy_out(dst->th2, c->P.TH2, KLT, on_device, c->stream)) != OPF_OK) return s;
+  if ((s = copy_out(dst->p_dev, c->P.PD, (size_t)c->S * c->T, on_device, c->stream)) != OPF_OK) return s;
+  float *tmp = nullptr;
+  if ((dst->v1 || dst->v2 || dst->u) && !on_device) CK(cudaMalloc(&tmp, std::max(2 * KLT, KNT) * sizeof(float) + 16));
+  if (dst->v1 || dst->v2) {
+    float *a = on_device ? dst->v1 : (dst->v1 ? tmp : nullptr);
+    float *b = on_device ? dst->v2 : (dst->v2 ? tmp + KLT : nullptr);
+    if (opfk_export_v_launch(c->P, a, b, c->stream) != 0) { cudaFree(tmp); return fail(OPF_ECUDA, "export_v launch failed"); }
+    if (!on_device) {
+      if (dst->v1) cudaMemcpyAsync(dst->v1, tmp, KLT * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+      if (dst->v2) cudaMemcpyAsync(dst->v2, tmp + KLT, KLT * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+      cudaStreamSynchronize(c->stream);
+    }
+  }
+  if (dst->u) {
+    float *a = on_device ? dst->u : tmp;
+    if (opfk_export_u_launch(c->P, a, c->stream) != 0) { cudaFree(tmp); return fail(OPF_ECUDA, "export_u launch failed"); }
+    if (!on_device) {
+      cudaMemcpyAsync(dst->u, tmp, KNT * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+      cudaStreamSynchronize(c->stream);
+    }
+  }
+  if (tmp) cudaFree(tmp);
+  if (dst->inner) {
+    auto lay = inner_layout(c);
+    const size_t nr = (size_t)c->n_ramp * opfk::RG_N * c->T, ns = (size_t)c->n_stor * opfk::SG_N * (c->T + 1);
+    std::vector<float> rl(nr), rb(nr), sl(ns), sb(ns);
+    if (nr) {
+      CK(cudaMemcpyAsync(rl.data(), c->P.ramp_lam, nr * 4, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaMemcpyAsync(rb.data(), c->P.ramp_beta, nr * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (ns) {
+      CK(cudaMemcpyAsync(sl.data(), c->P.stor_lam, ns * 4, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaMemcpyAsync(sb.data(), c->P.stor_beta, ns * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<float> flat(lay.size());
+    for (size_t i = 0; i < lay.size(); ++i) {
+      const auto &e = lay[i];
+      flat[i] = e.arr == 0 ? rl[e.idx] : e.arr == 1 ? rb[e.idx] : e.arr == 2 ? sl[e.idx] : e.arr == 3 ? sb[e.idx] : 0.f;
+    }
+    if (on_device) {
+      CK(cudaMemcpyAsync(dst->inner, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    } else {
+      std::memcpy(dst->inner, flat.data(), flat.size() * 4);
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return OPF_OK;
+}
+
+opf_status opf_set_state(opf_ctx *c, int32_t on_device, const opf_state *src) {
+  if (!c || !src) return fail(OPF_EINVAL, "NULL argument");
+  const size_t KLT = (size_t)c->Kp * c->L * c->T, KNT = (size_t)c->Kp * c->N * c->T;
+  DevScalars sc;
+  opf_status s;
+  if ((s = read_scalars(c, &sc)) != OPF_OK) return s;
+  if ((s = copy_in(c->P.P, src->p_line, KLT, on_device, c->stream)) != OPF_OK) return s;
+  if ((s = copy_in(c->P.TH1, src->th1, KLT, on_device, c->stream)) != OPF_OK) return s;
+  if ((s = copy_in(c->P.TH2, src->th2, KLT, on_device, c->stream)) != OPF_OK) return s;
+  if ((s = copy_in(c->P.V1, src->v1, KLT, on_device, c->stream)) != OPF_OK) return s;
+  if ((s = copy_in(c->P.V2, src->v2, KLT, on_device, c->stream)) != OPF_OK) return s;
+  if ((s = copy_in(c->P.PD, src->p_dev, (size_t)c->S * c->T, on_device, c->stream)) != OPF_OK) return s;
+  if ((s = copy_in(c->P.U, src->u, KNT, on_device, c->stream)) != OPF_OK) return s;
+  // inner duals: scaled for the current penalty, factors to be rebuilt
+  const float rho_dev = (float)(c->Kp * sc.rho_p);
+  const size_t nr = (size_t)c->n_ramp * opfk::RG_N * c->T, ns = (size_t)c->n_stor * opfk::SG_N * (c->T + 1);
+  std::vector<float> rl(nr, 0.f), rb(nr, 0.f), sl(ns, 0.f), sb(ns, 0.f);
+  if (src->inner) {
+    auto lay = inner_layout(c);
+    std::vector<float> flat(lay.size());
+    if (on_device) {
+      CK(cudaMemcpy(flat.data(), src->inner, flat.size() * 4, cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(flat.data(), src->inner, flat.size() * 4);
+    }
+    for (size_t i = 0; i < lay.size(); ++i) {
+      const auto &e = lay[i];
+      if (e.arr == 0) rl[e.idx] = flat[i];
+      else if (e.arr == 1) rb[e.idx] = flat[i];
+      else if (e.arr == 2) sl[e.idx] = flat[i];
+      else if (e.arr == 3) sb[e.idx] = flat[i];
+    }
+  }
+  std::vector<float> rr(c->n_ramp, src->inner ? -rho_dev : 0.f), sr(c->n_stor, src->inner ? -rho_dev : 0.f);
+  if (nr) {
+    CK(cudaMemcpyAsync(c->P.ramp_lam, rl.data(), nr * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->P.ramp_beta, rb.data(), nr * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->P.ramp_rho, rr.data(), rr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  }
+  if (ns) {
+    CK(cudaMemcpyAsync(c->P.stor_lam, sl.data(), ns * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->P.stor_beta, sb.data(), ns * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->P.stor_rho, sr.data(), sr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  }
+  if (opfk_project_v_launch(c->P, c->stream) != 0) return fail(OPF_ECUDA, "project_v launch failed");
+  if (opfk_node_average_launch(c->P, c->stream) != 0) return fail(OPF_ECUDA, "node_average launch failed");
+  sc.su = 1.0;
+  sc.sv = 1.0;
+  sc.v_fresh = 1;
+  sc.status = 0;
+  sc.converged = 0;
+  sc.dual_valid = 0;
+  CK(cudaMemcpyAsync(c->P.sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->host_status = 0;
+  return OPF_OK;
+}
+
+opf_status opf_reset(opf_ctx *c) {
+  if (!c) return fail(OPF_EINVAL, "ctx is NULL");
+  CK(cudaMemsetAsync(c->arena, 0, state_bytes(c), c->stream));
+  c->host_status = 0;
+  return init_scalars(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+include/opf.h declares, the ctypes structures match the C layout, and the host
+side rejects invalid networks before touching the device."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "opf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2410_17203_gb300 import build, binding
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    return binding.load_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(opf_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2410_17203_gb300 import binding
+    assert set(names) == set(binding.EXPORTS)
+
+
+def test_abi_version_and_status_strings(lib):
+    from paper_2410_17203_gb300 import binding as b
+    assert b.opf_abi_version() == 1
+    for s in range(7):
+        assert b.opf_status_str(s) not in ("", "unknown status")
+    assert b.opf_status_str(99) == "unknown status"
+
+
+def test_default_options_are_the_papers(lib):
+    from paper_2410_17203_gb300 import opf_default_options
+    o = opf_default_options()
+    assert (o.rho_p, o.rho_theta, o.mu, o.gamma) == (1.0, 1.0, 2.0, 1.1)
+    assert (o.adapt_every, o.inner_iters, o.check_every, o.eps) == (10, 10, 10, 1e-4)
+
+
+def test_ctypes_layout_matches_c(lib, tmp_path):
+    """Compile a probe against opf.h with gcc and compare sizes and offsets."""
+    from paper_2410_17203_gb300 import binding as b
+    structs = {"opf_network": b.opf_network, "opf_contingencies": b.opf_contingencies,
+               "opf_options": b.opf_options, "opf_state": b.opf_state, "opf_info": b.opf_info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "opf.h"', "int main(void){"]
+    for sname, cls in structs.items():
+        lines.append(f'printf("{sname} %zu\\n", sizeof({sname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{sname}.{f} %zu\\n", offsetof({sname}, {f}));')
+    lines.append("return 0;}")
+    c = tmp_path / "probe.c"
+    c.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n") if l)
+    for sname, cls in structs.items():
+        assert int(got[sname]) == __import__("ctypes").sizeof(cls), sname
+        for f, _ in cls._fields_:
+            assert int(got[f"{sname}.{f}"]) == getattr(cls, f).offset, f"{sname}.{f}"
+
+
+def _bad(case, **changes):
+    c = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in case.items()}
+    for k, v in changes.items():
+        if callable(v):
+            v(c)
+        else:
+            c[k] = v
+    return c
+
+
+@pytest.mark.parametrize("mutate, what", [
+    (lambda c: c["line_from"].__setitem__(0, 30), "line node id out of range"),
+    (lambda c: c["line_to"].__setitem__(2, c["line_from"][2]), "itself"),
+    (lambda c: c["line_b"].__setitem__(1, 0.0), "susceptance"),
+    (lambda c: c["line_u"].__setitem__(1, -1.0), "line limit"),
+    (lambda c: c["gen_pmin"].__setitem__((0, 0), 9.0), "pmin > pmax"),
+    (lambda c: c["gen_a"].__setitem__(0, -0.1), "quadratic cost"),
+    (lambda c: c["load_p"].__setitem__((3, 0), np.nan), "non-finite load"),
+    (lambda c: c["gen_node"].__setitem__(0, -1), "generator node id"),
+    (lambda c: c.__setitem__("outaged", np.array([40], np.int32)), "outaged line"),
+    (lambda c: c.__setitem__("T", 0), "horizon"),
+    (lambda c: c.__setitem__("T", 4096), "horizon"),
+])
+def test_invalid_networks_are_rejected_on_the_host(lib, mutate, what):
+    from gridgen import make_case
+    from paper_2410_17203_gb300 import OpfError, opf_create
+    case = make_case("tiny")
+    if what == "horizon":
+        bad = _bad(case)
+        mutate(bad)
+        T = bad["T"]
+        bad.update(T=max(T, 1))
+        # the arrays stay T=1; only the declared horizon is wrong
+        bad["T"] = T
+    else:
+        bad = _bad(case)
+        mutate(bad)
+    with pytest.raises(OpfError) as e:
+        opf_create(bad)
+    assert e.value.status == 1
+    assert what.split()[0].lower() in str(e.value).lower()
+
+
+def test_isolated_node_is_rejected(lib):
+    from gridgen import make_case
+    from paper_2410_17203_gb300 import OpfError, opf_create
+    case = make_case("tiny")
+    case["n_nodes"] = 31          # node 30 has no terminal
+    with pytest.raises(OpfError, match="no terminal"):
+        opf_create(case)
+
+
+@pytest.mark.parametrize("opt", [dict(rho_p=0.0), dict(rho_theta=-1.0), dict(inner_iters=0),
+                                 dict(gamma=0.5), dict(adapt_every=-1)])
+def test_invalid_options_are_rejected(lib, opt):
+    from gridgen import make_case
+    from paper_2410_17203_gb300 import OpfError, opf_create
+    with pytest.raises(OpfError) as e:
+        opf_create(make_case("tiny"), opt)
+    assert e.value.status == 1
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    from paper_2410_17203_gb300 import binding
+    with pytest.raises(OSError):
+        binding.load_library(str(tmp_path / "missing.so"))

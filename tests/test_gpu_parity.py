@@ -1,0 +1,213 @@
+"""GPU path vs the FP64 oracle, element by element (normwise per state array).
+
+All calls go through the C ABI (ctypes binding).  Sizes span several CTAs and
+ragged tails; the cases cover the 128-bit path (T % 4 == 0) and the scalar
+path, outages, K = 0, T = 1, fixed and curtailable loads, ramp-limited
+generators and batteries (Appendix D inner ADMM), with and without the
+adaptive penalty.
+"""
+import numpy as np
+import pytest
+
+from gridgen import make_case, scale_case
+from helpers import compare_residuals, compare_states, oracle_arrays, rel_err
+from oracle import Oracle, OracleOptions
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2410_17203_gb300 import load_library
+    load_library()
+
+
+def run_both(case, n, **opts):
+    from paper_2410_17203_gb300 import Solver
+    s = Solver(case, dict(opts))
+    s.iterate(n)
+    st = s.state()
+    res = s.residuals()
+    info = s.get_info()
+    s.close()
+    o = Oracle(case, OracleOptions(**opts))
+    o.iterate(n, stop=opts.get("eps", 1e-4) > 0)
+    return st, res, info, o
+
+
+CASES = {
+    "tiny": lambda: make_case("tiny"),
+    "mixed_T24": lambda: make_case(scale_case(150, 24, 6, seed=21)),
+    "scalar_T7": lambda: make_case(scale_case(90, 7, 3, seed=22, fixed_frac=0.3)),
+    "K0_fixed": lambda: make_case(scale_case(70, 8, 0, seed=23, fixed_frac=0.5, stor_per_node=0.0)),
+    "T1_outages": lambda: make_case(scale_case(120, 1, 9, seed=24, fixed_frac=0.2)),
+    "dup_noout": lambda: dict(make_case(scale_case(60, 12, 0, seed=25)),
+                              outaged=np.array([-1, -1], np.int32)),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("n", [1, 10, 100])
+def test_iterates_match_oracle_no_adaptation(name, n):
+    case = CASES[name]()
+    st, res, info, o = run_both(case, n, adapt_every=0, eps=0.0, rho_theta=5.0)
+    compare_states(st, o)
+    scale = max(np.linalg.norm(a) for a in oracle_arrays(o).values())
+    compare_residuals(res, o.res, scale)
+    assert info["iterations"] == n
+
+
+@pytest.mark.parametrize("name", ["tiny", "mixed_T24", "scalar_T7"])
+def test_iterates_and_penalties_match_with_adaptation(name):
+    case = CASES[name]()
+    n = 100
+    st, res, info, o = run_both(case, n, adapt_every=10, eps=0.0)
+    # the sequence of penalty decisions must agree
+    assert info["rho_p"] == pytest.approx(o.rho_p, rel=1e-12)
+    assert info["rho_theta"] == pytest.approx(o.rho_th, rel=1e-12)
+    compare_states(st, o)
+
+
+def test_split_launches_equal_one_launch():
+    """Iterations split over several launches (deferred v, pending rescale,
+    dual residual history carried on the device) give the same iterate."""
+    from paper_2410_17203_gb300 import Solver
+    case = CASES["mixed_T24"]()
+    a = Solver(case, dict(adapt_every=10, eps=0.0))
+    a.iterate(60)
+    b = Solver(case, dict(adapt_every=10, eps=0.0))
+    for n in (7, 3, 10, 1, 29, 10):
+        b.iterate(n)
+    sa, sb = a.state(), b.state()
+    for k in sa:
+        np.testing.assert_array_equal(sa[k], sb[k], err_msg=k)
+    np.testing.assert_array_equal(a.residuals(), b.residuals())
+
+
+def test_state_import_then_step_matches_oracle():
+    """Warm start (Section 3.4): an oracle state imported through the C ABI
+    continues exactly like the oracle does from that state."""
+    from paper_2410_17203_gb300 import Solver
+    case = CASES["mixed_T24"]()
+    o = Oracle(case, OracleOptions(adapt_every=0, eps=0.0, rho_theta=5.0))
+    o.iterate(40, stop=False)
+    ref = oracle_arrays(o)
+    st = {k: v.astype(np.float32) for k, v in ref.items()}
+    inner = []
+    for r in range(len(o.ramp_idx)):
+        inner += [o.ramp_lam[r], o.ramp_beta[r]]
+    for b in range(o.net.B):
+        inner += [o.stor_lam[b], o.stor_beta[b]]
+    st["inner"] = np.concatenate(inner).astype(np.float32)
+    s = Solver(case, dict(adapt_every=0, eps=0.0, rho_theta=5.0))
+    s.set_state(st)
+    back = s.state()
+    for k in ref:
+        assert rel_err(back[k], ref[k]) < 1e-6, k
+    assert rel_err(back["inner"], st["inner"]) < 1e-6
+    # continue both from the (FP32-rounded) state
+    o2 = Oracle(case, OracleOptions(adapt_every=0, eps=0.0, rho_theta=5.0))
+    o2.load_state(st)
+    s.iterate(5)
+    o2.iterate(5, stop=False)
+    compare_states(s.state(), o2)
+
+
+def test_solution_outputs_match_oracle():
+    from paper_2410_17203_gb300 import Solver
+    case = CASES["mixed_T24"]()
+    s = Solver(case, dict(adapt_every=10, eps=0.0))
+    s.iterate(80)
+    sol = s.solution()
+    o = Oracle(case, OracleOptions(adapt_every=10, eps=0.0))
+    o.iterate(80, stop=False)
+    assert rel_err(sol["p_dev"], o.dev_p()) < 1e-5
+    assert rel_err(sol["p_line"], o.line_p()) < 1e-5
+    assert rel_err(sol["theta_node"], o.thbar()) < 1e-5
+    assert rel_err(sol["price"], o.prices()) < 1e-5
+    assert sol["objective"] == pytest.approx(o.objective(), rel=1e-5)
+
+
+def test_phase_dual_stays_zero_mean_per_node():
+    """v_bar = 0 at every node and contingency (Section 3.2 invariant)."""
+    from paper_2410_17203_gb300 import Solver
+    case = CASES["mixed_T24"]()
+    s = Solver(case, dict(adapt_every=10, eps=0.0))
+    s.iterate(37)
+    st = s.state()
+    N = case["n_nodes"]
+    Kp, L, T = st["v1"].shape
+    acc = np.zeros((Kp, N, T))
+    cnt = np.zeros(N)
+    np.add.at(acc, (slice(None), case["line_from"]), st["v1"].astype(np.float64))
+    np.add.at(acc, (slice(None), case["line_to"]), st["v2"].astype(np.float64))
+    scale = np.abs(st["v1"]).max() + np.abs(st["v2"]).max()
+    assert np.abs(acc).max() <= 1e-5 * scale * 8
+
+
+def test_converged_objective_matches_oracle():
+    """Both sides run to the Eq. (converge) tolerance; objectives within 1e-4."""
+    from paper_2410_17203_gb300 import Solver
+    case = make_case("tiny")
+    opts = dict(adapt_every=0, rho_theta=10.0, eps=1e-4)
+    s = Solver(case, opts)
+    s.iterate(50000)
+    info = s.get_info()
+    res = s.residuals()
+    assert info["converged"] == 1
+    assert max(res[0], res[1]) <= info["tolerance"]
+    sol = s.solution()
+    o = Oracle(case, OracleOptions(**opts))
+    o.iterate(50000)
+    assert o.converged
+    assert sol["objective"] == pytest.approx(o.objective(), rel=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# failure detection without a GPU fault
+# ---------------------------------------------------------------------------
+
+def test_barrier_timeout_is_reported_and_recoverable():
+    from paper_2410_17203_gb300 import OpfError, Solver, opf_iterate, opf_reset, opf_residuals
+    case = CASES["mixed_T24"]()
+    s = Solver(case, dict(barrier_timeout_cycles=1, eps=0.0))
+    opf_iterate(s.h, 3)
+    res, st = opf_residuals(s.h, raise_on_status=False)
+    assert st == 4                                   # OPF_ETIMEOUT
+    with pytest.raises(OpfError) as e:
+        opf_iterate(s.h, 1)
+    assert e.value.status == 6                       # OPF_ESTATE
+    opf_reset(s.h)
+    assert s.get_info()["iterations"] == 0
+
+
+def test_nonfinite_state_is_reported():
+    from paper_2410_17203_gb300 import Solver, opf_residuals
+    case = CASES["mixed_T24"]()
+    s = Solver(case, dict(eps=0.0))
+    st = s.state()
+    st["u"][0, 3, 2] = np.nan
+    s.set_state(st)
+    s.iterate(5)
+    _, status = opf_residuals(s.h, raise_on_status=False)
+    assert status == 5                               # OPF_ENONFINITE
+    assert s.get_info()["iterations"] == 1
+
+
+def test_empty_and_degenerate_shapes():
+    """One bus and no lines (no phase terminals), K = 0, T = 1."""
+    from paper_2410_17203_gb300 import Solver
+    rng = np.random.default_rng(3)
+    G, D, T = 3, 2, 1
+    case = dict(n_nodes=1, T=T, line_from=np.zeros(0, np.int32), line_to=np.zeros(0, np.int32),
+                line_b=np.zeros(0), line_u=np.zeros(0), gen_node=np.zeros(G, np.int32),
+                gen_a=rng.uniform(0.01, 0.1, G), gen_b=rng.uniform(10, 40, G),
+                gen_pmin=np.zeros((G, T)), gen_pmax=np.full((G, T), 2.0), gen_ramp=-np.ones(G),
+                load_node=np.zeros(D, np.int32), load_p=np.full((D, T), 0.8),
+                load_voll=-np.ones(D), stor_node=np.zeros(0, np.int32), stor_P=np.zeros(0),
+                stor_dur=np.zeros(0), stor_eff=np.zeros(0), stor_cost=np.zeros(0),
+                outaged=np.zeros(0, np.int32))
+    st, res, info, o = run_both(case, 30, adapt_every=10, eps=0.0)
+    compare_states(st, o, keys=["p_dev", "u"])
