@@ -58,12 +58,12 @@ struct opf_ctx {
   cudaStream_t stream = nullptr;
   opf_options opt{};
   int N = 0, L = 0, T = 0, K = 0, Kp = 0, S = 0, G = 0, D = 0, B = 0;
-  int n_closed = 0, n_ramp = 0, n_stor = 0;
+  int n_closed = 0, n_cnode = 0, n_ramp = 0, n_stor = 0;
   int grid = 0;
   char *arena = nullptr;
   size_t arena_bytes = 0;
   Params P{};
-  float *price_stage = nullptr;
+  size_t state_bytes = 0;     // leading part of the arena zeroed by opf_reset
   // host copies used for the objective and the inner-state layout
   std::vector<double> gen_a, gen_b, load_voll, load_p, stor_cost;
   std::vector<int> ramp_gen;  // generator index of each ramp device
@@ -175,6 +175,12 @@ opf_status validate(const opf_network *net, int T, const opf_contingencies *ctg,
     }
   }
   if (ctg && ctg->K < 0) return fail(OPF_EINVAL, "K must be >= 0");
+  {
+    // item indices of the iteration kernel are 32-bit
+    const double kp = 1.0 + (ctg ? ctg->K : 0);
+    if (kp * std::max(net->n_lines, net->n_nodes) * T >= 2147483647.0)
+      return fail(OPF_EINVAL, "(K+1) * max(lines, nodes) * T must stay below 2^31");
+  }
   if (ctg && ctg->K > 0) {
     if (!ctg->outaged_line) return fail(OPF_EINVAL, "outaged_line is NULL");
     for (int k = 0; k < ctg->K; ++k)
@@ -189,6 +195,38 @@ opf_status validate(const opf_network *net, int T, const opf_contingencies *ctg,
   return OPF_OK;
 }
 
+// Reverse Cuthill-McKee order of the node graph (lines as edges): order[new]
+// = old.  Neighbours of a node end up with nearby numbers, so the two ends of
+// a line are processed close together and its second read hits L2.
+std::vector<int> rcm_order(int N, const std::vector<int> &ptr, const std::vector<int> &adj) {
+  std::vector<int> deg(N), order, bydeg(N);
+  order.reserve(N);
+  for (int n = 0; n < N; ++n) deg[n] = ptr[n + 1] - ptr[n];
+  for (int n = 0; n < N; ++n) bydeg[n] = n;
+  std::stable_sort(bydeg.begin(), bydeg.end(), [&](int a, int b) { return deg[a] < deg[b]; });
+  std::vector<char> seen(N, 0);
+  std::vector<int> nb;
+  for (int s : bydeg) {
+    if (seen[s]) continue;
+    seen[s] = 1;
+    size_t head = order.size();
+    order.push_back(s);
+    while (head < order.size()) {
+      const int v = order[head++];
+      nb.clear();
+      for (int j = ptr[v]; j < ptr[v + 1]; ++j)
+        if (!seen[adj[j]]) {
+          seen[adj[j]] = 1;
+          nb.push_back(adj[j]);
+        }
+      std::stable_sort(nb.begin(), nb.end(), [&](int a, int b) { return deg[a] < deg[b]; });
+      order.insert(order.end(), nb.begin(), nb.end());
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  return order;
+}
+
 // The arena layout; called once with a null base to size it.
 void carve(opf_ctx *c, Arena &a) {
   Params &p = c->P;
@@ -196,28 +234,28 @@ void carve(opf_ctx *c, Arena &a) {
   const size_t NT = (size_t)c->N * c->T, ST = (size_t)c->S * c->T;
   const int T = c->T, Tp = c->T + 1;
   // state first (zeroed on reset)
-  p.P = a.take<float>(KLT);
-  p.TH1 = a.take<float>(KLT);
-  p.TH2 = a.take<float>(KLT);
-  p.V1 = a.take<float>(KLT);
-  p.V2 = a.take<float>(KLT);
-  p.DP = a.take<float>(KLT);
-  p.U = a.take<float>(KNT);
-  p.PBAR = a.take<float>(KNT);
-  p.THBAR = a.take<float>(KNT);
-  p.SPBAR = a.take<float>(NT);
-  p.SU = a.take<float>(NT);
+  for (int b = 0; b < 2; ++b) {
+    p.P[b] = a.take<float>(KLT);
+    p.TH1[b] = a.take<float>(KLT);
+    p.TH2[b] = a.take<float>(KLT);
+    p.V1[b] = a.take<float>(KLT);
+    p.V2[b] = a.take<float>(KLT);
+    p.U[b] = a.take<float>(KNT);
+    p.PBAR[b] = a.take<float>(KNT);
+    p.THBAR[b] = a.take<float>(KNT);
+  }
   p.PD = a.take<float>(ST);
   p.DPD = a.take<float>(ST);
   p.ramp_lam = a.take<float>((size_t)c->n_ramp * opfk::RG_N * T);
   p.ramp_beta = a.take<float>((size_t)c->n_ramp * opfk::RG_N * T);
-  p.ramp_m = a.take<float>((size_t)c->n_ramp * T);
+  p.ramp_q = a.take<float>((size_t)c->n_ramp * T);
   p.ramp_rho = a.take<float>(c->n_ramp);
   p.stor_lam = a.take<float>((size_t)c->n_stor * opfk::SG_N * Tp);
   p.stor_beta = a.take<float>((size_t)c->n_stor * opfk::SG_N * Tp);
-  p.stor_m = a.take<float>((size_t)c->n_stor * Tp);
+  p.stor_q = a.take<float>((size_t)c->n_stor * Tp);
   p.stor_rho = a.take<float>(c->n_stor);
   p.stor_delta = a.take<float>((size_t)c->n_stor * T);
+  c->state_bytes = a.off;
   p.sc = a.take<DevScalars>(1);
   // parameters
   p.line_n1 = a.take<int>(c->L);
@@ -226,17 +264,22 @@ void carve(opf_ctx *c, Arena &a) {
   p.line_u = a.take<float>(c->L);
   p.out_line = a.take<int>(c->Kp);
   p.lcsr_ptr = a.take<int>(c->N + 1);
-  p.lcsr_idx = a.take<int>(2 * (size_t)c->L);
+  p.lcsr = a.take<int2>(2 * (size_t)c->L);
   p.dcsr_ptr = a.take<int>(c->N + 1);
   p.dcsr_idx = a.take<int>(c->S);
   p.cnt_p = a.take<float>(c->N);
   p.cnt_th = a.take<float>(c->N);
+  p.rcnt_p = a.take<float>(c->N);
+  p.rcnt_th = a.take<float>(c->N);
   p.dev_node = a.take<int>(c->S);
+  p.dev_type = a.take<int>(c->S);
+  p.cnode_ids = a.take<int>(c->n_cnode);
+  p.cnode_ptr = a.take<int>(c->n_cnode + 1);
+  p.cnode_dev = a.take<int>(c->n_closed);
   p.dev_a = a.take<float>(c->S);
   p.dev_b = a.take<float>(c->S);
   p.dev_lo = a.take<float>(ST);
   p.dev_hi = a.take<float>(ST);
-  p.closed_ids = a.take<int>(c->n_closed);
   p.ramp_ids = a.take<int>(c->n_ramp);
   p.ramp_R = a.take<float>(c->n_ramp);
   p.stor_ids = a.take<int>(c->n_stor);
@@ -244,17 +287,15 @@ void carve(opf_ctx *c, Arena &a) {
   p.stor_P = a.take<float>(c->n_stor);
   p.stor_dur = a.take<float>(c->n_stor);
   p.stor_cost = a.take<float>(c->n_stor);
+  p.node_perm = a.take<int>(c->N);
+  p.line_perm = a.take<int>(c->L);
   // scratch
   p.partials = a.take<double>((size_t)2 * c->grid * opfk::NSLOT);
-  p.bar_count = a.take<unsigned>(4);  // count, gen, err (as int), pad
+  // barrier count, generation, error word, pad, then two 64-bit work counters
+  p.bar_count = a.take<unsigned>(8);
   p.bar_gen = p.bar_count ? p.bar_count + 1 : nullptr;
   p.err = p.bar_count ? reinterpret_cast<int *>(p.bar_count + 2) : nullptr;
-  c->price_stage = a.take<float>(NT);
-}
-
-size_t state_bytes(const opf_ctx *c) {
-  // everything carved before the scalars block, plus the scalars
-  return (size_t)(reinterpret_cast<const char *>(c->P.sc) - c->arena);
+  p.work = p.bar_count ? reinterpret_cast<unsigned long long *>(p.bar_count + 4) : nullptr;
 }
 
 opf_status init_scalars(opf_ctx *c) {
@@ -275,6 +316,14 @@ opf_status read_scalars(opf_ctx *c, DevScalars *sc) {
   if (sc->status) c->host_status = sc->status;
   return OPF_OK;
 }
+
+// device scratch for exports to host memory (not on the iteration path)
+struct DevTmp {
+  float *p = nullptr;
+  ~DevTmp() {
+    if (p) cudaFree(p);
+  }
+};
 
 }  // namespace
 
@@ -307,45 +356,77 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   const int N = c->N, L = c->L, S = c->S, G = c->G, D = c->D;
   const size_t nT = (size_t)T;
 
-  // node-ordered incidence; every node needs a terminal
+  // every node needs a terminal
+  std::vector<int> dev_node(S);
+  for (int g = 0; g < G; ++g) dev_node[g] = net->gen_node[g];
+  for (int d = 0; d < D; ++d) dev_node[G + d] = net->load_node[d];
+  for (int b = 0; b < c->B; ++b) dev_node[G + D + b] = net->stor_node[b];
   std::vector<int> lcnt(N, 0), dcnt(N, 0);
   for (int l = 0; l < L; ++l) {
     lcnt[net->line_from[l]]++;
     lcnt[net->line_to[l]]++;
   }
-  std::vector<int> dev_node(S);
-  for (int g = 0; g < G; ++g) dev_node[g] = net->gen_node[g];
-  for (int d = 0; d < D; ++d) dev_node[G + d] = net->load_node[d];
-  for (int b = 0; b < c->B; ++b) dev_node[G + D + b] = net->stor_node[b];
   for (int d = 0; d < S; ++d) dcnt[dev_node[d]]++;
   for (int n = 0; n < N; ++n)
     if (lcnt[n] + dcnt[n] == 0) {
       delete c;
       return fail(OPF_EINVAL, "node " + std::to_string(n) + " has no terminal");
     }
+
+  // node renumbering (RCM) and line order (by owner = lower internal end)
+  std::vector<int> aptr(N + 1, 0), adj(2 * (size_t)L);
+  for (int n = 0; n < N; ++n) aptr[n + 1] = aptr[n] + lcnt[n];
+  {
+    std::vector<int> fill(aptr.begin(), aptr.end() - 1);
+    for (int l = 0; l < L; ++l) {
+      adj[fill[net->line_from[l]]++] = net->line_to[l];
+      adj[fill[net->line_to[l]]++] = net->line_from[l];
+    }
+  }
+  std::vector<int> node_perm = rcm_order(N, aptr, adj), node_inv(N);
+  for (int i = 0; i < N; ++i) node_inv[node_perm[i]] = i;
+  std::vector<int> line_perm(L), line_inv(L);
+  for (int l = 0; l < L; ++l) line_perm[l] = l;
+  auto key = [&](int l) {
+    const int a = node_inv[net->line_from[l]], b = node_inv[net->line_to[l]];
+    return std::make_pair(std::min(a, b), std::max(a, b));
+  };
+  std::stable_sort(line_perm.begin(), line_perm.end(), [&](int x, int y) { return key(x) < key(y); });
+  for (int i = 0; i < L; ++i) line_inv[line_perm[i]] = i;
+
+  // CSR by internal node: incident lines (2*l + end, other node) and devices
   std::vector<int> lptr(N + 1, 0), dptr(N + 1, 0);
   for (int n = 0; n < N; ++n) {
-    lptr[n + 1] = lptr[n] + lcnt[n];
-    dptr[n + 1] = dptr[n] + dcnt[n];
+    lptr[n + 1] = lptr[n] + lcnt[node_perm[n]];
+    dptr[n + 1] = dptr[n] + dcnt[node_perm[n]];
   }
-  std::vector<int> lidx(2 * (size_t)L), didx(S);
+  std::vector<int2> lcsr(2 * (size_t)L);
+  std::vector<int> didx(S), n1(L), n2(L);
   {
     std::vector<int> lp(lptr.begin(), lptr.end() - 1), dp(dptr.begin(), dptr.end() - 1);
-    for (int l = 0; l < L; ++l) {
-      lidx[lp[net->line_from[l]]++] = 2 * l;      // terminal 1
-      lidx[lp[net->line_to[l]]++] = 2 * l + 1;    // terminal 2
+    for (int li = 0; li < L; ++li) {
+      const int l = line_perm[li];
+      const int a = node_inv[net->line_from[l]], b = node_inv[net->line_to[l]];
+      n1[li] = a;
+      n2[li] = b;
+      lcsr[lp[a]++] = make_int2(2 * li, b);       // terminal 1 at a
+      lcsr[lp[b]++] = make_int2(2 * li + 1, a);   // terminal 2 at b
     }
-    for (int d = 0; d < S; ++d) didx[dp[dev_node[d]]++] = d;
+    for (int d = 0; d < S; ++d) didx[dp[node_inv[dev_node[d]]]++] = d;
   }
-  std::vector<float> cnt_p(N), cnt_th(N);
+  std::vector<float> cnt_p(N), cnt_th(N), rcnt_p(N), rcnt_th(N);
+  std::vector<int> dev_node_int(S);
   for (int n = 0; n < N; ++n) {
-    cnt_p[n] = (float)(lcnt[n] + dcnt[n]);
-    cnt_th[n] = (float)lcnt[n];
+    cnt_p[n] = (float)(lcnt[node_perm[n]] + dcnt[node_perm[n]]);
+    cnt_th[n] = (float)lcnt[node_perm[n]];
+    rcnt_p[n] = (float)(1.0 / cnt_p[n]);
+    rcnt_th[n] = cnt_th[n] > 0 ? (float)(1.0 / cnt_th[n]) : 0.f;
   }
+  for (int d = 0; d < S; ++d) dev_node_int[d] = node_inv[dev_node[d]];
 
   // device classes and closed-form parameters
   std::vector<float> dev_a(S, 0.f), dev_b(S, 0.f), lo(S * nT, 0.f), hi(S * nT, 0.f);
-  std::vector<int> closed, ramp, stor;
+  std::vector<int> dev_type(S, 0), ramp, stor;
   std::vector<float> rampR;
   for (int g = 0; g < G; ++g) {
     dev_a[g] = (float)net->gen_a[g];
@@ -357,31 +438,41 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
     if (net->gen_ramp[g] >= 0 && T > 1) {
       ramp.push_back(g);
       rampR.push_back((float)net->gen_ramp[g]);
-      c->ramp_gen.push_back(g);
-    } else {
-      closed.push_back(g);
+      dev_type[g] = 1;
     }
   }
   for (int d = 0; d < D; ++d) {
     const bool fixed = net->load_voll[d] < 0;
-    dev_a[G + d] = 0.f;
     dev_b[G + d] = fixed ? 0.f : (float)net->load_voll[d];
     for (size_t t = 0; t < nT; ++t) {
       const float P = (float)net->load_p[d * nT + t];
       lo[(G + d) * nT + t] = -P;
       hi[(G + d) * nT + t] = fixed ? -P : 0.f;
     }
-    closed.push_back(G + d);
   }
   std::vector<float> seff, sP, sdur, scost;
   for (int b = 0; b < c->B; ++b) {
     stor.push_back(G + D + b);
+    dev_type[G + D + b] = 1;
     seff.push_back((float)net->stor_eff[b]);
     sP.push_back((float)net->stor_P[b]);
     sdur.push_back((float)net->stor_dur[b]);
     scost.push_back((float)net->stor_cost[b]);
   }
-  c->n_closed = (int)closed.size();
+  // closed-form devices grouped by internal node (phase D sums pbar + u over
+  // k once per node)
+  std::vector<int> cnode_ids, cnode_ptr(1, 0), cnode_dev;
+  for (int n = 0; n < N; ++n) {
+    const size_t before = cnode_dev.size();
+    for (int j = dptr[n]; j < dptr[n + 1]; ++j)
+      if (dev_type[didx[j]] == 0) cnode_dev.push_back(didx[j]);
+    if (cnode_dev.size() > before) {
+      cnode_ids.push_back(n);
+      cnode_ptr.push_back((int)cnode_dev.size());
+    }
+  }
+  c->n_closed = (int)cnode_dev.size();
+  c->n_cnode = (int)cnode_ids.size();
   c->n_ramp = (int)ramp.size();
   c->n_stor = (int)stor.size();
 
@@ -420,7 +511,11 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   p.T = T;
   p.Kp = c->Kp;
   p.S = S;
-  p.n_closed = c->n_closed;
+  p.n_cnode = c->n_cnode;
+  // one stage group: all line proxes, then all node sums (staging the
+  // contingencies to keep new line rows in L2 cost more in grid barriers than
+  // it saved in DRAM traffic at 10k buses)
+  p.G = c->Kp;
   p.n_ramp = c->n_ramp;
   p.n_stor = c->n_stor;
   p.eps = opt.eps;
@@ -433,15 +528,13 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   c->tol = opt.eps * std::sqrt(2.0 * (2.0 * L + S) * T * c->Kp);
   p.tol = c->tol;
 
-  std::vector<int> n1(L), n2(L), outl(c->Kp, -1);
+  std::vector<int> outl(c->Kp, -1);
   std::vector<float> lb(L), lu(L);
-  for (int l = 0; l < L; ++l) {
-    n1[l] = net->line_from[l];
-    n2[l] = net->line_to[l];
-    lb[l] = (float)net->line_b[l];
-    lu[l] = (float)net->line_u[l];
+  for (int li = 0; li < L; ++li) {
+    lb[li] = (float)net->line_b[line_perm[li]];
+    lu[li] = (float)net->line_u[line_perm[li]];
   }
-  for (int k = 0; k < c->K; ++k) outl[k + 1] = ctg->outaged_line[k];
+  for (int k = 0; k < c->K; ++k) outl[k + 1] = ctg->outaged_line[k] >= 0 ? line_inv[ctg->outaged_line[k]] : -1;
 
   opf_status s = OPF_OK;
   auto up = [&](const void *dst, const auto &v) {
@@ -458,17 +551,22 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   up(p.line_u, lu);
   up(p.out_line, outl);
   up(p.lcsr_ptr, lptr);
-  up(p.lcsr_idx, lidx);
+  up(p.lcsr, lcsr);
   up(p.dcsr_ptr, dptr);
   up(p.dcsr_idx, didx);
   up(p.cnt_p, cnt_p);
   up(p.cnt_th, cnt_th);
-  up(p.dev_node, dev_node);
+  up(p.rcnt_p, rcnt_p);
+  up(p.rcnt_th, rcnt_th);
+  up(p.dev_node, dev_node_int);
+  up(p.dev_type, dev_type);
+  up(p.cnode_ids, cnode_ids);
+  up(p.cnode_ptr, cnode_ptr);
+  up(p.cnode_dev, cnode_dev);
   up(p.dev_a, dev_a);
   up(p.dev_b, dev_b);
   up(p.dev_lo, lo);
   up(p.dev_hi, hi);
-  up(p.closed_ids, closed);
   up(p.ramp_ids, ramp);
   up(p.ramp_R, rampR);
   up(p.stor_ids, stor);
@@ -476,6 +574,8 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   up(p.stor_P, sP);
   up(p.stor_dur, sdur);
   up(p.stor_cost, scost);
+  up(p.node_perm, node_perm);
+  up(p.line_perm, line_perm);
   if (s == OPF_OK) s = init_scalars(c);
   if (s != OPF_OK) {
     cudaFree(c->arena);
@@ -505,12 +605,11 @@ opf_status opf_iterate(opf_ctx *c, int32_t n_iters, double rho) {
     if (opfk_set_rho_launch(c->P.sc, rho, c->stream) != 0) return fail(OPF_ECUDA, "set_rho launch failed");
   }
   if (n_iters == 0) return OPF_OK;
-  CK(cudaMemsetAsync(c->P.bar_count, 0, 4 * sizeof(unsigned), c->stream));
+  CK(cudaMemsetAsync(c->P.bar_count, 0, 8 * sizeof(unsigned), c->stream));
   Params p = c->P;
   p.n_iters = n_iters;
   char msg[256];
-  int grid = c->grid;
-  if (opfk_iteration_launch(p, c->stream, &grid, msg, sizeof(msg)) != 0) return fail(OPF_ECUDA, msg);
+  if (opfk_iteration_launch(p, c->stream, c->grid, msg, sizeof(msg)) != 0) return fail(OPF_ECUDA, msg);
   return OPF_OK;
 }
 
@@ -553,24 +652,7 @@ opf_status opf_get_info(opf_ctx *c, opf_info *info) {
 
 namespace {
 
-// copy `n` floats from device `src` to a caller buffer (host or device)
-opf_status copy_out(float *dst, const float *src, size_t n, int on_device, cudaStream_t s) {
-  if (!dst || n == 0) return OPF_OK;
-  CK(cudaMemcpyAsync(dst, src, n * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-  return OPF_OK;
-}
-
-opf_status copy_in(float *dst, const float *src, size_t n, int on_device, cudaStream_t s) {
-  if (n == 0) return OPF_OK;
-  if (!src) {
-    CK(cudaMemsetAsync(dst, 0, n * sizeof(float), s));
-    return OPF_OK;
-  }
-  CK(cudaMemcpyAsync(dst, src, n * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-  return OPF_OK;
-}
-
-// Build the list of (canonical index -> (array, device index)) pairs.
+// canonical inner-state entry -> (device array, index)
 struct InnerEntry {
   int arr;     // 0 ramp_lam, 1 ramp_beta, 2 stor_lam, 3 stor_beta, -1 always zero
   size_t idx;
@@ -608,6 +690,16 @@ std::vector<InnerEntry> inner_layout(const opf_ctx *c) {
   return v;
 }
 
+// Destination for an export: the caller's device buffer, or a device staging
+// area that is copied to the caller's host buffer afterwards.
+float *stage(float *user, int on_device, float *tmp) { return user ? (on_device ? user : tmp) : nullptr; }
+
+opf_status alloc_tmp(DevTmp &t, size_t n) {
+  if (n == 0) return OPF_OK;
+  CK(cudaMalloc(&t.p, n * sizeof(float)));
+  return OPF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -615,21 +707,39 @@ extern "C" {
 opf_status opf_solution(opf_ctx *c, int32_t on_device, double *objective, float *p_dev, float *p_line,
                         float *theta_node, float *price) {
   if (!c) return fail(OPF_EINVAL, "ctx is NULL");
-  const size_t T = c->T;
+  DevScalars sc;
   opf_status s;
-  if ((s = copy_out(p_dev, c->P.PD, (size_t)c->S * T, on_device, c->stream)) != OPF_OK) return s;
-  if ((s = copy_out(p_line, c->P.P, (size_t)c->Kp * c->L * T, on_device, c->stream)) != OPF_OK) return s;
-  if ((s = copy_out(theta_node, c->P.THBAR, (size_t)c->Kp * c->N * T, on_device, c->stream)) != OPF_OK) return s;
-  if (price) {
-    float *dst = on_device ? price : c->price_stage;
-    if (opfk_price_launch(c->P, dst, c->stream) != 0) return fail(OPF_ECUDA, "price kernel launch failed");
-    if (!on_device) CK(cudaMemcpyAsync(price, c->price_stage, (size_t)c->N * T * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if ((s = read_scalars(c, &sc)) != OPF_OK) return s;
+  const int cur = (int)(sc.it & 1);
+  const size_t T = c->T, KLT = (size_t)c->Kp * c->L * T, KNT = (size_t)c->Kp * c->N * T, NT = (size_t)c->N * T;
+  if (p_dev)
+    CK(cudaMemcpyAsync(p_dev, c->P.PD, (size_t)c->S * T * sizeof(float),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  DevTmp tmp;
+  if (!on_device && (p_line || theta_node || price)) {
+    if ((s = alloc_tmp(tmp, (p_line ? KLT : 0) + (theta_node ? KNT : 0) + (price ? NT : 0))) != OPF_OK)
+      return s;
+  }
+  float *tl = tmp.p, *tt = tmp.p ? tmp.p + (p_line ? KLT : 0) : nullptr;
+  float *tp = tt ? tt + (theta_node ? KNT : 0) : nullptr;
+  if (p_line && opfk_export_lines_launch(c->P, cur, stage(p_line, on_device, tl), nullptr, nullptr,
+                                         nullptr, nullptr, c->stream) != 0)
+    return fail(OPF_ECUDA, "export launch failed");
+  if ((theta_node || price) &&
+      opfk_export_nodes_launch(c->P, cur, nullptr, stage(theta_node, on_device, tt),
+                               stage(price, on_device, tp), c->stream) != 0)
+    return fail(OPF_ECUDA, "export launch failed");
+  if (!on_device) {
+    if (p_line) CK(cudaMemcpyAsync(p_line, tl, KLT * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (theta_node) CK(cudaMemcpyAsync(theta_node, tt, KNT * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (price) CK(cudaMemcpyAsync(price, tp, NT * 4, cudaMemcpyDeviceToHost, c->stream));
   }
   if (objective) {
     std::vector<float> pd((size_t)c->S * T), dl((size_t)c->n_stor * T);
     CK(cudaMemcpyAsync(pd.data(), c->P.PD, pd.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     if (!dl.empty())
-      CK(cudaMemcpyAsync(dl.data(), c->P.stor_delta, dl.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaMemcpyAsync(dl.data(), c->P.stor_delta, dl.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                         c->stream));
     CK(cudaStreamSynchronize(c->stream));
     double f = 0.0;
     for (int g = 0; g < c->G; ++g)
@@ -639,46 +749,52 @@ opf_status opf_solution(opf_ctx *c, int32_t on_device, double *objective, float 
       }
     for (int d = 0; d < c->D; ++d) {
       if (c->load_voll[d] < 0) continue;
-      for (size_t t = 0; t < T; ++t) f += c->load_voll[d] * ((double)pd[(c->G + d) * T + t] + c->load_p[d * T + t]);
+      for (size_t t = 0; t < T; ++t)
+        f += c->load_voll[d] * ((double)pd[(c->G + d) * T + t] + c->load_p[d * T + t]);
     }
     for (int b = 0; b < c->n_stor; ++b)
       for (size_t t = 0; t < T; ++t) f += c->stor_cost[b] * (double)dl[b * T + t];
     *objective = f;
   }
-  DevScalars sc;
-  if ((s = read_scalars(c, &sc)) != OPF_OK) return s;
+  CK(cudaStreamSynchronize(c->stream));
   return (opf_status)sc.status;
 }
 
 opf_status opf_get_state(opf_ctx *c, int32_t on_device, const opf_state *dst) {
   if (!c || !dst) return fail(OPF_EINVAL, "NULL argument");
-  const size_t KLT = (size_t)c->Kp * c->L * c->T, KNT = (size_t)c->Kp * c->N * c->T;
+  DevScalars sc;
   opf_status s;
-  if ((s = copy_out(dst->p_line, c->P.P, KLT, on_device, c->stream)) != OPF_OK) return s;
-  if ((s = copy_out(dst->th1, c->P.TH1, KLT, on_device, c->stream)) != OPF_OK) return s;
-  if ((s = copy_out(dst->th2, c->P.TH2, KLT, on_device, c->stream)) != OPF_OK) return s;
-  if ((s = copy_out(dst->p_dev, c->P.PD, (size_t)c->S * c->T, on_device, c->stream)) != OPF_OK) return s;
-  float *tmp = nullptr;
-  if ((dst->v1 || dst->v2 || dst->u) && !on_device) CK(cudaMalloc(&tmp, std::max(2 * KLT, KNT) * sizeof(float) + 16));
-  if (dst->v1 || dst->v2) {
-    float *a = on_device ? dst->v1 : (dst->v1 ? tmp : nullptr);
-    float *b = on_device ? dst->v2 : (dst->v2 ? tmp + KLT : nullptr);
-    if (opfk_export_v_launch(c->P, a, b, c->stream) != 0) { cudaFree(tmp); return fail(OPF_ECUDA, "export_v launch failed"); }
-    if (!on_device) {
-      if (dst->v1) cudaMemcpyAsync(dst->v1, tmp, KLT * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
-      if (dst->v2) cudaMemcpyAsync(dst->v2, tmp + KLT, KLT * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
-      cudaStreamSynchronize(c->stream);
-    }
+  if ((s = read_scalars(c, &sc)) != OPF_OK) return s;
+  const int cur = (int)(sc.it & 1);
+  const size_t KLT = (size_t)c->Kp * c->L * c->T, KNT = (size_t)c->Kp * c->N * c->T;
+  if (dst->p_dev)
+    CK(cudaMemcpyAsync(dst->p_dev, c->P.PD, (size_t)c->S * c->T * sizeof(float),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  float *lines[5] = {dst->p_line, dst->th1, dst->th2, dst->v1, dst->v2};
+  DevTmp tmp;
+  if (!on_device) {
+    size_t n = dst->u ? KNT : 0;
+    for (float *x : lines) n += x ? KLT : 0;
+    if ((s = alloc_tmp(tmp, n)) != OPF_OK) return s;
   }
-  if (dst->u) {
-    float *a = on_device ? dst->u : tmp;
-    if (opfk_export_u_launch(c->P, a, c->stream) != 0) { cudaFree(tmp); return fail(OPF_ECUDA, "export_u launch failed"); }
-    if (!on_device) {
-      cudaMemcpyAsync(dst->u, tmp, KNT * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
-      cudaStreamSynchronize(c->stream);
-    }
+  float *stg[5];
+  float *cursor = tmp.p;
+  for (int j = 0; j < 5; ++j) {
+    stg[j] = lines[j] ? (on_device ? lines[j] : cursor) : nullptr;
+    if (lines[j] && !on_device) cursor += KLT;
   }
-  if (tmp) cudaFree(tmp);
+  float *ustg = dst->u ? (on_device ? dst->u : cursor) : nullptr;
+  if (lines[0] || lines[1] || lines[2] || lines[3] || lines[4]) {
+    if (opfk_export_lines_launch(c->P, cur, stg[0], stg[1], stg[2], stg[3], stg[4], c->stream) != 0)
+      return fail(OPF_ECUDA, "export launch failed");
+  }
+  if (ustg && opfk_export_nodes_launch(c->P, cur, ustg, nullptr, nullptr, c->stream) != 0)
+    return fail(OPF_ECUDA, "export launch failed");
+  if (!on_device) {
+    for (int j = 0; j < 5; ++j)
+      if (lines[j]) CK(cudaMemcpyAsync(lines[j], stg[j], KLT * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (dst->u) CK(cudaMemcpyAsync(dst->u, ustg, KNT * 4, cudaMemcpyDeviceToHost, c->stream));
+  }
   if (dst->inner) {
     auto lay = inner_layout(c);
     const size_t nr = (size_t)c->n_ramp * opfk::RG_N * c->T, ns = (size_t)c->n_stor * opfk::SG_N * (c->T + 1);
@@ -699,6 +815,7 @@ opf_status opf_get_state(opf_ctx *c, int32_t on_device, const opf_state *dst) {
     }
     if (on_device) {
       CK(cudaMemcpyAsync(dst->inner, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
     } else {
       std::memcpy(dst->inner, flat.data(), flat.size() * 4);
     }
@@ -710,17 +827,42 @@ opf_status opf_get_state(opf_ctx *c, int32_t on_device, const opf_state *dst) {
 opf_status opf_set_state(opf_ctx *c, int32_t on_device, const opf_state *src) {
   if (!c || !src) return fail(OPF_EINVAL, "NULL argument");
   const size_t KLT = (size_t)c->Kp * c->L * c->T, KNT = (size_t)c->Kp * c->N * c->T;
+  const size_t ST = (size_t)c->S * c->T;
   DevScalars sc;
   opf_status s;
   if ((s = read_scalars(c, &sc)) != OPF_OK) return s;
-  if ((s = copy_in(c->P.P, src->p_line, KLT, on_device, c->stream)) != OPF_OK) return s;
-  if ((s = copy_in(c->P.TH1, src->th1, KLT, on_device, c->stream)) != OPF_OK) return s;
-  if ((s = copy_in(c->P.TH2, src->th2, KLT, on_device, c->stream)) != OPF_OK) return s;
-  if ((s = copy_in(c->P.V1, src->v1, KLT, on_device, c->stream)) != OPF_OK) return s;
-  if ((s = copy_in(c->P.V2, src->v2, KLT, on_device, c->stream)) != OPF_OK) return s;
-  if ((s = copy_in(c->P.PD, src->p_dev, (size_t)c->S * c->T, on_device, c->stream)) != OPF_OK) return s;
-  if ((s = copy_in(c->P.U, src->u, KNT, on_device, c->stream)) != OPF_OK) return s;
-  // inner duals: scaled for the current penalty, factors to be rebuilt
+  const int cur = (int)(sc.it & 1);
+  const float *lines[5] = {src->p_line, src->th1, src->th2, src->v1, src->v2};
+  const float *dsrc[5], *usrc = src->u;
+  DevTmp tmp;
+  if (!on_device) {
+    size_t n = src->u ? KNT : 0;
+    for (const float *x : lines) n += x ? KLT : 0;
+    if ((s = alloc_tmp(tmp, n)) != OPF_OK) return s;
+    float *cursor = tmp.p;
+    for (int j = 0; j < 5; ++j) {
+      dsrc[j] = nullptr;
+      if (lines[j]) {
+        CK(cudaMemcpyAsync(cursor, lines[j], KLT * 4, cudaMemcpyHostToDevice, c->stream));
+        dsrc[j] = cursor;
+        cursor += KLT;
+      }
+    }
+    if (src->u) {
+      CK(cudaMemcpyAsync(cursor, src->u, KNT * 4, cudaMemcpyHostToDevice, c->stream));
+      usrc = cursor;
+    }
+  } else {
+    for (int j = 0; j < 5; ++j) dsrc[j] = lines[j];
+  }
+  if (opfk_import_launch(c->P, cur, dsrc[0], dsrc[1], dsrc[2], dsrc[3], dsrc[4], usrc, c->stream) != 0)
+    return fail(OPF_ECUDA, "import launch failed");
+  if (src->p_dev)
+    CK(cudaMemcpyAsync(c->P.PD, src->p_dev, ST * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->stream));
+  else
+    CK(cudaMemsetAsync(c->P.PD, 0, ST * 4, c->stream));
+  // inner duals: scaled for the current penalty; factors rebuilt on first use
   const float rho_dev = (float)(c->Kp * sc.rho_p);
   const size_t nr = (size_t)c->n_ramp * opfk::RG_N * c->T, ns = (size_t)c->n_stor * opfk::SG_N * (c->T + 1);
   std::vector<float> rl(nr, 0.f), rb(nr, 0.f), sl(ns, 0.f), sb(ns, 0.f);
@@ -751,14 +893,13 @@ opf_status opf_set_state(opf_ctx *c, int32_t on_device, const opf_state *src) {
     CK(cudaMemcpyAsync(c->P.stor_beta, sb.data(), ns * 4, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->P.stor_rho, sr.data(), sr.size() * 4, cudaMemcpyHostToDevice, c->stream));
   }
-  if (opfk_project_v_launch(c->P, c->stream) != 0) return fail(OPF_ECUDA, "project_v launch failed");
-  if (opfk_node_average_launch(c->P, c->stream) != 0) return fail(OPF_ECUDA, "node_average launch failed");
+  if (opfk_project_v_launch(c->P, cur, c->stream) != 0) return fail(OPF_ECUDA, "project_v launch failed");
+  if (opfk_node_average_launch(c->P, cur, c->stream) != 0) return fail(OPF_ECUDA, "node_average launch failed");
   sc.su = 1.0;
   sc.sv = 1.0;
   sc.v_fresh = 1;
   sc.status = 0;
   sc.converged = 0;
-  sc.dual_valid = 0;
   CK(cudaMemcpyAsync(c->P.sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->host_status = 0;
@@ -767,7 +908,7 @@ opf_status opf_set_state(opf_ctx *c, int32_t on_device, const opf_state *src) {
 
 opf_status opf_reset(opf_ctx *c) {
   if (!c) return fail(OPF_EINVAL, "ctx is NULL");
-  CK(cudaMemsetAsync(c->arena, 0, state_bytes(c), c->stream));
+  CK(cudaMemsetAsync(c->arena, 0, c->state_bytes, c->stream));
   c->host_status = 0;
   return init_scalars(c);
 }

@@ -1,14 +1,22 @@
 // Internal layout shared by the host side (opf_api.cu) and the kernels
 // (opf_kernels.cu).  Not part of the public ABI.
 //
-// Device memory layout (structure of arrays, time innermost so that every
-// row of T floats is one contiguous, 16-byte aligned segment when T % 4 == 0):
-//   lines   P, TH1, TH2, V1, V2, DP       [Kp][L][T]   float
-//   nodes   U, PBAR, THBAR                [Kp][N][T]   float
-//           SPBAR, SU (sums over k)       [N][T]       float
-//   devices PD                            [S][T]       float
-//   inner ADMM state of ramp generators   lam, beta [n_ramp][4][T],  m [n_ramp][T]
-//   inner ADMM state of batteries         lam, beta [n_stor][9][T+1], m [n_stor][T+1]
+// Numbering: nodes are renumbered by reverse Cuthill-McKee and lines sorted by
+// their lower-numbered end (the line's "owner"), so that the two ends of a
+// line are processed close together in time; the C ABI converts to and from
+// the caller's numbering on import and export.  Devices keep the caller's
+// order (generators, loads, batteries).
+//
+// Device memory layout (structure of arrays, time innermost so that every row
+// of T floats is one contiguous, 16-byte aligned segment when T % 4 == 0):
+//   lines   P, TH1, TH2, V1, V2             2 x [Kp][L][T] float (double buffer)
+//   nodes   U, PBAR, THBAR                  2 x [Kp][N][T] float (double buffer)
+//   devices PD, DPD                         [S][T]         float
+//   inner ADMM state of ramp generators     lam, beta [n_ramp][4][T],  q [n_ramp][T]
+//   inner ADMM state of batteries           lam, beta [n_stor][9][T+1], q [n_stor][T+1]
+// Buffer (it & 1) holds the state after `it` iterations; an iteration reads
+// the old buffers and writes the other ones, because both ends of a line
+// evaluate its prox from the old line and node values.
 // V1/V2 hold the phase duals one step behind: the update v += theta - theta_bar
 // of iteration i is folded into the line pass of iteration i+1, which already
 // reads theta and theta_bar (so v is read and written once per iteration).
@@ -19,9 +27,8 @@
 
 namespace opfk {
 
-// residual partial-sum slots (FP64)
-// SL_NF counts non-finite node duals: the prox clamps (fminf/fmaxf) would
-// otherwise turn a NaN input into a finite bound.
+// residual partial-sum slots.  SL_NF counts non-finite node values: the prox
+// clamps (fminf/fmaxf) would otherwise turn a NaN input into a finite bound.
 enum { SL_PP = 0, SL_PT = 1, SL_DP = 2, SL_DT = 3, SL_NF = 4, NSLOT = 5 };
 
 // Scalars that persist on the device between launches.
@@ -33,7 +40,7 @@ struct DevScalars {
   int converged;
   int status;            // sticky opf_status from the device (0 = ok)
   int v_fresh;           // 1: V1/V2 already hold the current v (after import / reset)
-  int dual_valid;        // 1: res[1], res[4], res[5] belong to the last iteration
+  int pad;
 };
 
 // Battery group offsets inside lam/beta rows of stride Tp = T + 1.
@@ -44,37 +51,44 @@ enum { RG_UP = 0, RG_LO = 1, RG_RU = 2, RG_RD = 3, RG_N = 4 };
 
 struct Params {
   int N, L, T, Kp, S;
-  int n_closed, n_ramp, n_stor;
-  // lines
-  const int *line_n1, *line_n2;
+  int n_cnode, n_ramp, n_stor;
+  int G;  // contingencies per stage group: stage s runs line proxes of group s
+          // and node sums of group s-1, whose new line rows are still in L2
+  // lines (internal numbering)
+  const int *line_n1, *line_n2;  // internal node of terminal 1 (from) and terminal 2 (to)
   const float *line_b, *line_u;
-  const int *out_line;  // [Kp], -1 = no outage (k = 0 always -1)
-  float *P, *TH1, *TH2, *V1, *V2;
-  float *DP;   // [Kp][L][T] line power change of the iteration (written on residual iterations)
-  // nodes
-  float *U, *PBAR, *THBAR, *SPBAR, *SU;
-  const int *lcsr_ptr, *lcsr_idx;  // line terminals of each node: 2*l + end (end 1 = terminal 2)
+  const int *out_line;  // [Kp], internal index of the outaged line, -1 = none
+  float *P[2], *TH1[2], *TH2[2], *V1[2], *V2[2];  // double-buffered
+  // nodes (internal numbering), double-buffered
+  float *U[2], *PBAR[2], *THBAR[2];
+  // incident lines of each node: x = 2*l + end (end 1: the node is terminal 2), y = other node
+  const int *lcsr_ptr;
+  const int2 *lcsr;
   const int *dcsr_ptr, *dcsr_idx;  // devices of each node
-  const float *cnt_p, *cnt_th;  // terminals per node: all (power), line terminals (phase)
-  // devices (closed-form prox: clip((rho X - b)/(2a + rho), lo, hi))
-  float *PD;
-  float *DPD;  // [S][T] device power change (residual iterations)
-  const int *dev_node;
+  const float *cnt_p, *cnt_th;     // terminals per node: all (power), line terminals (phase)
+  const float *rcnt_p, *rcnt_th;   // their reciprocals (0 for a node without line terminals)
+  // devices: type 0 = closed-form prox clip((rho X - b)/(2a + rho), lo, hi), 1 = inner ADMM
+  float *PD, *DPD;
+  const int *dev_node, *dev_type;
+  // nodes with closed-form devices, and those devices per node
+  const int *cnode_ids, *cnode_ptr, *cnode_dev;
   const float *dev_a, *dev_b;
   const float *dev_lo, *dev_hi;  // [S][T]
-  const int *closed_ids;
   // ramp-limited generators
   const int *ramp_ids;
   const float *ramp_R;
-  float *ramp_lam, *ramp_beta, *ramp_m, *ramp_rho;
+  float *ramp_lam, *ramp_beta, *ramp_q, *ramp_rho;
   // batteries
   const int *stor_ids;
   const float *stor_eff, *stor_P, *stor_dur, *stor_cost;
-  float *stor_lam, *stor_beta, *stor_m, *stor_rho, *stor_delta;  // delta [n_stor][T]
+  float *stor_lam, *stor_beta, *stor_q, *stor_rho, *stor_delta;  // delta [n_stor][T]
+  // numbering maps (internal -> caller) for import / export
+  const int *node_perm, *line_perm;
   // scratch
-  double *partials;        // [2][grid][NSLOT]
+  double *partials;  // [2][grid][NSLOT]
   unsigned *bar_count, *bar_gen;
   int *err;
+  unsigned long long *work;  // [2] phase-N work counters, by iteration parity
   DevScalars *sc;
   // options
   double eps, mu, gamma, tol;
@@ -87,13 +101,19 @@ struct Params {
 
 // Launch wrappers implemented in opf_kernels.cu (host callable).
 extern "C++" {
-int opfk_iteration_launch(const opfk::Params &p, void *stream, int *grid_used, char *msg, int msglen);
+int opfk_iteration_launch(const opfk::Params &p, void *stream, int grid, char *msg, int msglen);
 int opfk_max_grid(int T, int *grid);
-int opfk_node_average_launch(const opfk::Params &p, void *stream);
-int opfk_export_v_launch(const opfk::Params &p, float *v1, float *v2, void *stream);
-int opfk_price_launch(const opfk::Params &p, float *price, void *stream);
-int opfk_project_v_launch(const opfk::Params &p, void *stream);
-int opfk_export_u_launch(const opfk::Params &p, float *u, void *stream);
+// State import / export between internal and caller numbering; `cur` selects
+// the node buffer holding the current state.
+int opfk_import_launch(const opfk::Params &p, int cur, const float *p_line, const float *th1,
+                       const float *th2, const float *v1, const float *v2, const float *u,
+                       void *stream);
+int opfk_node_average_launch(const opfk::Params &p, int cur, void *stream);
+int opfk_project_v_launch(const opfk::Params &p, int cur, void *stream);
+int opfk_export_lines_launch(const opfk::Params &p, int cur, float *p_line, float *th1, float *th2,
+                             float *v1, float *v2, void *stream);
+int opfk_export_nodes_launch(const opfk::Params &p, int cur, float *u, float *theta_node,
+                             float *price, void *stream);
 int opfk_set_rho_launch(opfk::DevScalars *sc, double rho, void *stream);
 }
 

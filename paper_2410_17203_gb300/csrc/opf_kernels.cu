@@ -4,29 +4,30 @@
 // form of ADMM (Section 3.2).  Each iteration has three phases separated by
 // grid-wide barriers with a bounded spin:
 //
-//   A  prox phase (Section 3.2 steps 1-2, Section 4.2):
-//        - every (contingency k, line l, time chunk) applies the line prox to
-//          (p~ - u, theta_bar - v) gathered from its two end nodes, and folds in
-//          the deferred phase-dual update v += theta - theta_bar of the
-//          previous iteration;
-//        - every generator / load applies its closed-form prox with weight
-//          (K+1) rho_p to p_d - avg_k(pbar + u);
-//        - ramp-limited generators and batteries run the inner ADMM of
-//          Appendix D, one warp per device, lanes over time steps, with the
-//          x-update as a tridiagonal solve done by a warp-wide scan;
-//   B  node phase (Eq. average-op, Section 3.2 step 3, Section 3.3): every
-//      (node, time chunk) walks the node's terminals in CSR-by-node order,
-//      for each contingency forms pbar, theta_bar and u += pbar with plain
-//      register sums (no atomics), accumulates sum_k pbar and sum_k u for the
-//      next step A, and the FP64 residual partial sums;
-//   C  every CTA reduces the per-CTA FP64 partials in the same order and takes
-//      the same stopping / adaptive-penalty decision (Section 3.5), so no third
-//      barrier is needed.
+//   D  step 2, the devices shared by all contingencies: one thread per
+//      (node with generators or loads, time chunk) sums pbar + u over k and
+//      applies the closed-form prox with weight (K+1) rho_p to
+//      p_d - avg_k(pbar + u) for every such device at the node; one warp per
+//      ramp-limited generator or battery runs the inner ADMM of Appendix D,
+//      lanes over time steps, each x-update a tridiagonal solve done by a
+//      warp-wide scan;
+//   N  one item per (contingency k, node n, chunk of time steps), taken in
+//      contingency-major order.  The item evaluates the closed-form prox of
+//      every incident line (step 1) from the previous line and node values at
+//      both ends -- both ends compute the same prox, the lower-numbered end
+//      stores it -- and forms pbar, theta_bar and u += pbar (step 3) as plain
+//      register sums over the node's terminals (no atomics), with the residual
+//      partial sums of Section 3.3 (one-pass Welford sums for theta~ and for
+//      the change of p~);
+//   C  every CTA reduces the per-CTA partial sums in the same order (FP64) and
+//      takes the same stopping / adaptive-penalty decision (Section 3.5).
 //
-// Memory layout and the deferred v update are described in opf_internal.h.
+// Memory layout, numbering and the deferred v update: opf_internal.h.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
+
+#include <algorithm>
 
 #include "opf_internal.h"
 
@@ -36,57 +37,6 @@ constexpr int BLOCK = 256;
 constexpr int WARPS = BLOCK / 32;
 constexpr int ST_TIMEOUT = 4;    // opf_status values used on the device
 constexpr int ST_NONFINITE = 5;
-
-// ---------------------------------------------------------------------------
-// small vector helpers: VW consecutive time steps per thread (4 -> 128-bit I/O)
-// ---------------------------------------------------------------------------
-template <int VW>
-struct FV {
-  float v[VW];
-};
-
-template <int VW>
-__device__ __forceinline__ FV<VW> ldv(const float *p) {
-  FV<VW> r;
-  if constexpr (VW == 4) {
-    float4 t = *reinterpret_cast<const float4 *>(p);
-    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
-  } else {
-    r.v[0] = *p;
-  }
-  return r;
-}
-
-// streaming load/store (read or written once per phase: evict first)
-template <int VW>
-__device__ __forceinline__ FV<VW> ldv_cs(const float *p) {
-  FV<VW> r;
-  if constexpr (VW == 4) {
-    float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
-    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
-  } else {
-    r.v[0] = __ldcs(p);
-  }
-  return r;
-}
-
-template <int VW>
-__device__ __forceinline__ void stv(float *p, const FV<VW> &r) {
-  if constexpr (VW == 4) {
-    *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
-  } else {
-    *p = r.v[0];
-  }
-}
-
-template <int VW>
-__device__ __forceinline__ void stv_cs(float *p, const FV<VW> &r) {
-  if constexpr (VW == 4) {
-    __stcs(reinterpret_cast<float4 *>(p), make_float4(r.v[0], r.v[1], r.v[2], r.v[3]));
-  } else {
-    __stcs(p, r.v[0]);
-  }
-}
 
 // ---------------------------------------------------------------------------
 // grid barrier with a bounded spin.  On timeout the CTA records ST_TIMEOUT in
@@ -211,7 +161,7 @@ __device__ void warp_tri_solve(const float *__restrict__ q, float off, float *bu
 // x-update matrix (2a + rho + 2 omega) I + 2 omega D'D is tridiagonal.
 // ---------------------------------------------------------------------------
 __device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf,
-                          float *sm, bool resid, int lane) {
+                          const float *pbar_o, const float *u_o, float *sm, int lane) {
   const int T = p.T;
   const int d = p.ramp_ids[r];
   const int n = p.dev_node[d];
@@ -219,7 +169,7 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf
   const float om = rho;
   float *lam = p.ramp_lam + (size_t)r * RG_N * T;
   float *bet = p.ramp_beta + (size_t)r * RG_N * T;
-  float *mf = p.ramp_m + (size_t)r * T;
+  float *mf = p.ramp_q + (size_t)r * T;
   const float *lo = p.dev_lo + (size_t)d * T;
   const float *hi = p.dev_hi + (size_t)d * T;
   float *pd = p.PD + (size_t)d * T;
@@ -238,7 +188,12 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf
   }
   for (int t = lane; t < T; t += 32) {
     size_t o = (size_t)n * T + t;
-    X[t] = pd[t] - (p.SPBAR[o] + su * p.SU[o]) / kpf;
+    float sp = 0.f, sq = 0.f;
+    for (int k = 0; k < p.Kp; ++k) {
+      sp += pbar_o[(size_t)k * p.N * T + o];
+      sq += u_o[(size_t)k * p.N * T + o];
+    }
+    X[t] = pd[t] - (sp + su * sq) / kpf;   // p_d - avg_k(pbar + u)
   }
   __syncwarp();
   for (int itn = 0; itn < p.inner_iters; ++itn) {
@@ -281,7 +236,7 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf
   }
   for (int t = lane; t < T; t += 32) {
     const float pn = Z[t];
-    if (resid) p.DPD[(size_t)d * T + t] = pn - pd[t];
+    p.DPD[(size_t)d * T + t] = pn - pd[t];
     pd[t] = pn;
   }
   __syncwarp();
@@ -294,7 +249,7 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf
 // system of size T + 1 in the state of charge s.
 // ---------------------------------------------------------------------------
 __device__ void stor_prox(const Params &p, int sidx, float rho, float su, float kpf,
-                          float *sm, bool resid, int lane) {
+                          const float *pbar_o, const float *u_o, float *sm, int lane) {
   const int T = p.T, Tp = T + 1;
   const int d = p.stor_ids[sidx];
   const int n = p.dev_node[d];
@@ -303,7 +258,7 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float su, float 
   const float om = rho;
   float *lam = p.stor_lam + (size_t)sidx * SG_N * Tp;
   float *bet = p.stor_beta + (size_t)sidx * SG_N * Tp;
-  float *mf = p.stor_m + (size_t)sidx * Tp;
+  float *mf = p.stor_q + (size_t)sidx * Tp;
   float *pd = p.PD + (size_t)d * T;
   float *dl_out = p.stor_delta + (size_t)sidx * T;
   float *X = sm, *TAU = sm + Tp, *S = sm + 2 * Tp;
@@ -329,7 +284,12 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float su, float 
   }
   for (int t = lane; t < T; t += 32) {
     size_t o = (size_t)n * T + t;
-    X[t] = pd[t] - (p.SPBAR[o] + su * p.SU[o]) / kpf;
+    float sp = 0.f, sq = 0.f;
+    for (int k = 0; k < p.Kp; ++k) {
+      sp += pbar_o[(size_t)k * p.N * T + o];
+      sq += u_o[(size_t)k * p.N * T + o];
+    }
+    X[t] = pd[t] - (sp + su * sq) / kpf;   // p_d - avg_k(pbar + u)
   }
   __syncwarp();
 #define LAM(g, t) lam[(g) * Tp + (t)]
@@ -393,10 +353,241 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float su, float 
 #undef BET
   for (int t = lane; t < T; t += 32) {
     const float pn = TAU[t];
-    if (resid) p.DPD[(size_t)d * T + t] = pn - pd[t];
+    p.DPD[(size_t)d * T + t] = pn - pd[t];
     pd[t] = pn;
   }
   __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// the persistent iteration kernel
+// ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// line prox (Section 2.1 f^ac, Section 4.2), both terminals, one lane value.
+// Inputs are the line's stored state (p at terminal 2, angles, deferred phase
+// duals) and the previous node values at its two ends.  A single call site
+// in the kernel, so both ends of a line obtain bit-identical results.
+// ---------------------------------------------------------------------------
+// VW consecutive time steps per thread (4 -> 128-bit accesses when T % 4 == 0)
+// ---------------------------------------------------------------------------
+template <int VW>
+struct FV {
+  float v[VW];
+};
+
+template <int VW>
+__device__ __forceinline__ FV<VW> ldv(const float *p) {
+  FV<VW> r;
+  if constexpr (VW == 4) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else {
+    r.v[0] = *p;
+  }
+  return r;
+}
+
+// streaming load (read once per iteration: evict first)
+template <int VW>
+__device__ __forceinline__ FV<VW> ldv_cs(const float *p) {
+  FV<VW> r;
+  if constexpr (VW == 4) {
+    const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else {
+    r.v[0] = __ldcs(p);
+  }
+  return r;
+}
+
+template <int VW>
+__device__ __forceinline__ void stv(float *p, const FV<VW> &r) {
+  if constexpr (VW == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  } else {
+    *p = r.v[0];
+  }
+}
+
+// streaming store (not read again in this iteration: evict first)
+template <int VW>
+__device__ __forceinline__ void stv_cs(float *p, const FV<VW> &r) {
+  if constexpr (VW == 4) {
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(r.v[0], r.v[1], r.v[2], r.v[3]));
+  } else {
+    __stcs(p, r.v[0]);
+  }
+}
+
+// one-pass sum of squared deviations from the mean (Welford)
+template <int VW>
+struct Welf {
+  float n;
+  float mean[VW], m2[VW];
+  __device__ __forceinline__ void reset() {
+    n = 0.f;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) { mean[e] = 0.f; m2[e] = 0.f; }
+  }
+  __device__ __forceinline__ void add(const float *x) {
+    n += 1.f;
+    const float r = __frcp_rn(n);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const float d = x[e] - mean[e];
+      mean[e] = fmaf(d, r, mean[e]);
+      m2[e] = fmaf(d, x[e] - mean[e], m2[e]);
+    }
+  }
+};
+
+// x / c given r = 1/c rounded to nearest: one FMA correction step gives the
+// correctly rounded quotient for these well-scaled operands (a plain x * r
+// would carry the rounding bias of r into every node average, iteration
+// after iteration).
+__device__ __forceinline__ float div_rn(float x, float c, float r) {
+  const float q = x * r;
+  return fmaf(fmaf(-q, c, x), r, q);
+}
+
+// Index (a, b, c) of a row-major [.][B][C] item space, advanced by a fixed
+// stride with carries instead of 64-bit divisions per item.
+struct Idx3 {
+  int a, b, c;
+  __device__ __forceinline__ void set(unsigned x, int B, int C) {
+    c = (int)(x % (unsigned)C);
+    const unsigned q = x / (unsigned)C;
+    b = (int)(q % (unsigned)B);
+    a = (int)(q / (unsigned)B);
+  }
+  __device__ __forceinline__ void step(const Idx3 &d, int B, int C) {
+    c += d.c;
+    if (c >= C) { c -= C; ++b; }
+    b += d.b;
+    if (b >= B) { b -= B; ++a; }
+    a += d.a;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// line prox item (Section 3.2 step 1, Section 2.1 f^ac, Section 4.2): one
+// (contingency k, line l, VW time steps).  x = p~ - u and y = theta_bar - v at
+// both terminals from the previous iterate; the deferred phase-dual update
+// v += theta - theta_bar of the previous iteration is applied on the way.
+// ---------------------------------------------------------------------------
+template <int VW>
+__device__ __forceinline__ void line_item(const Params &p, int old, int nw, int k, int l, int toff, float frp,
+                                          float frt, float fsu, float fsv, bool v_fresh) {
+  const int T = p.T, L = p.L, N = p.N;
+  const int n1 = p.line_n1[l], n2 = p.line_n2[l];
+  const bool act = p.out_line[k] != l;
+  const size_t ol = ((size_t)k * L + l) * T + toff;
+  const size_t o1 = ((size_t)k * N + n1) * T + toff, o2 = ((size_t)k * N + n2) * T + toff;
+  // p stays cached: the node sums of the next stage read both its old and new value
+  FV<VW> P = ldv<VW>(p.P[old] + ol), A1 = ldv_cs<VW>(p.TH1[old] + ol), A2 = ldv_cs<VW>(p.TH2[old] + ol);
+  FV<VW> V1 = ldv_cs<VW>(p.V1[old] + ol), V2 = ldv_cs<VW>(p.V2[old] + ol);
+  const FV<VW> U1 = ldv<VW>(p.U[old] + o1), U2 = ldv<VW>(p.U[old] + o2);
+  const FV<VW> B1 = ldv<VW>(p.PBAR[old] + o1), B2 = ldv<VW>(p.PBAR[old] + o2);
+  const FV<VW> G1 = ldv<VW>(p.THBAR[old] + o1), G2 = ldv<VW>(p.THBAR[old] + o2);
+  float tb = 1.f, den = 1.f, ulim = 0.f;
+  if (act) {
+    const float bb = p.line_b[l];
+    ulim = p.line_u[l];
+    tb = 2.f * bb;
+    den = 2.f * frp + frt / (tb * bb);   // denominator as derived in the oracle
+  }
+  const float rden = __frcp_rn(den), rtb = __frcp_rn(tb);
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    const float x1 = -P.v[e] - B1.v[e] - fsu * U1.v[e];     // p~ - u at terminal 1
+    const float x2 = P.v[e] - B2.v[e] - fsu * U2.v[e];      // p~ - u at terminal 2
+    const float v1 = v_fresh ? fsv * V1.v[e] : fsv * (V1.v[e] + (A1.v[e] - G1.v[e]));
+    const float v2 = v_fresh ? fsv * V2.v[e] : fsv * (V2.v[e] + (A2.v[e] - G2.v[e]));
+    const float y1 = G1.v[e] - v1, y2 = G2.v[e] - v2;       // theta_bar - v
+    if (act) {
+      const float num = frp * (x2 - x1) + div_rn(frt * (y1 - y2), tb, rtb);
+      const float pn = fminf(fmaxf(div_rn(num, den, rden), -ulim), ulim);
+      const float mid = 0.5f * (y1 + y2);
+      const float h = div_rn(pn, tb, rtb);
+      P.v[e] = pn;
+      A1.v[e] = mid + h;
+      A2.v[e] = mid - h;
+    } else {  // outaged line: the terminals decouple
+      P.v[e] = 0.f;
+      A1.v[e] = y1;
+      A2.v[e] = y2;
+    }
+    V1.v[e] = v1;
+    V2.v[e] = v2;
+  }
+  // p and the angles are read back by the next stage's node sums; v is not
+  stv<VW>(p.P[nw] + ol, P);
+  stv<VW>(p.TH1[nw] + ol, A1);
+  stv<VW>(p.TH2[nw] + ol, A2);
+  stv_cs<VW>(p.V1[nw] + ol, V1);
+  stv_cs<VW>(p.V2[nw] + ol, V2);
+}
+
+// ---------------------------------------------------------------------------
+// node item (Section 3.2 step 3, Eq. average-op, Section 3.3): one
+// (contingency k, node n, VW time steps).  Sums the node's terminals in CSR
+// order (no atomics), forms pbar, theta_bar, u += pbar, and the residual
+// partial sums: ||pbar||^2, ||theta~||^2 and ||p~ - p~_prev||^2 by one-pass
+// Welford sums over the terminals, ||theta_bar - theta_bar_prev||^2.
+// ---------------------------------------------------------------------------
+template <int VW>
+__device__ __forceinline__ void node_item(const Params &p, int old, int nw, int k, int n, int toff, float fsu,
+                                          float *acc) {
+  const int T = p.T, L = p.L, N = p.N;
+  const float cp = p.cnt_p[n], ct = p.cnt_th[n], rcp = p.rcnt_p[n], rct = p.rcnt_th[n];
+  FV<VW> sp, st;
+  Welf<VW> wdp, wth;
+  wdp.reset();
+  wth.reset();
+#pragma unroll
+  for (int e = 0; e < VW; ++e) { sp.v[e] = 0.f; st.v[e] = 0.f; }
+  for (int j = p.dcsr_ptr[n]; j < p.dcsr_ptr[n + 1]; ++j) {
+    const size_t od = (size_t)p.dcsr_idx[j] * T + toff;
+    const FV<VW> pd = ldv<VW>(p.PD + od), dpd = ldv<VW>(p.DPD + od);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) sp.v[e] += pd.v[e];
+    wdp.add(dpd.v);
+  }
+  const size_t kb = (size_t)k * L * T + toff;
+  for (int j = p.lcsr_ptr[n]; j < p.lcsr_ptr[n + 1]; ++j) {
+    const int code = p.lcsr[j].x;
+    const size_t ol = kb + (size_t)(code >> 1) * T;
+    const FV<VW> pn = ldv<VW>(p.P[nw] + ol), po = ldv<VW>(p.P[old] + ol);
+    const FV<VW> th = ldv<VW>(((code & 1) ? p.TH2[nw] : p.TH1[nw]) + ol);
+    float dpo[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      sp.v[e] += (code & 1) ? pn.v[e] : -pn.v[e];
+      st.v[e] += th.v[e];
+      dpo[e] = (code & 1) ? pn.v[e] - po.v[e] : po.v[e] - pn.v[e];
+    }
+    wdp.add(dpo);
+    wth.add(th.v);
+  }
+  const size_t on = ((size_t)k * N + n) * T + toff;
+  const FV<VW> uo = ldv<VW>(p.U[old] + on), go = ldv<VW>(p.THBAR[old] + on);
+  FV<VW> pb, tbar, un;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    pb.v[e] = div_rn(sp.v[e], cp, rcp);                      // Eq. (average-op)
+    tbar.v[e] = ct > 0.f ? div_rn(st.v[e], ct, rct) : 0.f;
+    un.v[e] = fsu * uo.v[e] + pb.v[e];                       // u += pbar
+    const float dt = tbar.v[e] - go.v[e];
+    acc[SL_PP] += cp * pb.v[e] * pb.v[e];
+    acc[SL_PT] += wth.m2[e];
+    acc[SL_DP] += wdp.m2[e];
+    acc[SL_DT] += ct * dt * dt;
+    if (!isfinite(un.v[e]) || !isfinite(tbar.v[e])) acc[SL_NF] += 1.f;
+  }
+  // the new node rows are read in the next iteration only
+  stv_cs<VW>(p.U[nw] + on, un);
+  stv_cs<VW>(p.PBAR[nw] + on, pb);
+  stv_cs<VW>(p.THBAR[nw] + on, tbar);
 }
 
 // ---------------------------------------------------------------------------
@@ -406,242 +597,124 @@ template <int VW>
 __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
   extern __shared__ float smem[];
   __shared__ double red[WARPS][NSLOT];
-  __shared__ double dec[8];
+  __shared__ double sd[10];   // thread 0: rho_p, rho_th, su, sv, res[6]
+  __shared__ float sf[5];     // broadcast: rho_p, rho_th, su, sv, (K+1) rho_p
+  __shared__ int s_code;
   __shared__ int s_flag;
 
-  const int T = p.T, TV = T / VW, Kp = p.Kp, L = p.L, N = p.N;
+  const int T = p.T, Kp = p.Kp, L = p.L, N = p.N, TV = T / VW, G = p.G;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gwarp = blockIdx.x * WARPS + wib, nwarp = gridDim.x * WARPS;
   const long long gthr = (long long)blockIdx.x * BLOCK + threadIdx.x;
   const long long nthr = (long long)gridDim.x * BLOCK;
   float *wsm = smem + wib * 3 * (T + 1);
+  const int S = (Kp + G - 1) / G;  // stage groups
 
   const DevScalars sc0 = *p.sc;
-  double rho_p = sc0.rho_p, rho_th = sc0.rho_th, su = sc0.su, sv = sc0.sv;
-  double res[6];
-#pragma unroll
-  for (int j = 0; j < 6; ++j) res[j] = sc0.res[j];
+  if (threadIdx.x == 0) {
+    sd[0] = sc0.rho_p; sd[1] = sc0.rho_th; sd[2] = sc0.su; sd[3] = sc0.sv;
+    for (int j = 0; j < 6; ++j) sd[4 + j] = sc0.res[j];
+  }
   long long it = sc0.it;
-  int v_fresh = sc0.v_fresh, converged = sc0.converged, status = 0, dual_valid = sc0.dual_valid;
+  int v_fresh = sc0.v_fresh, converged = sc0.converged, status = 0;
   const float kpf = (float)Kp;
   const int n_inner = p.n_stor + p.n_ramp;
-  const long long n_closed_items = (long long)p.n_closed * TV;
-  const long long n_line_items = (long long)Kp * L * TV;
+  const long long n_cnode_items = (long long)p.n_cnode * T;
+  const int line_per_k = L * TV, node_per_k = N * TV;
 
   // a sticky device error (timeout, non-finite) leaves the state as it is
   const int n_iters = sc0.status ? 0 : p.n_iters;
   for (int i = 0; i < n_iters; ++i) {
     const long long itn = it + 1;
-    const bool last = (i == n_iters - 1);
+    const int old = (int)(it & 1), nw = old ^ 1;
     const bool adapt_now = p.adapt_every > 0 && (itn % p.adapt_every) == 0;
     const bool check_now = p.eps > 0 && p.check_every > 0 && (itn % p.check_every) == 0;
-    const bool resid = adapt_now || check_now || last;
-    const int par = (int)(itn & 1);
-    const float frp = (float)rho_p, frt = (float)rho_th;
-    const float fsu = (float)su, fsv = (float)sv;
-    const float rho_dev = (float)(Kp * rho_p);
-    // per-thread partial sums in FP32; FP64 from the block reduction on
+    if (threadIdx.x == 0) {
+      sf[0] = (float)sd[0]; sf[1] = (float)sd[1]; sf[2] = (float)sd[2]; sf[3] = (float)sd[3];
+      sf[4] = (float)(Kp * sd[0]);
+    }
+    __syncthreads();
+    const float frp = sf[0], frt = sf[1], fsu = sf[2], fsv = sf[3], rho_dev = sf[4];
+    const float *Uo = p.U[old], *Bo = p.PBAR[old];
+    const size_t NT = (size_t)N * T;
     float acc[NSLOT] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    bool ok = true;
 
-    // ---------------- phase A: proxes ----------------
+    // ---------------- phase D: device proxes (step 2) ----------------
     for (int w = gwarp; w < n_inner; w += nwarp) {
       if (w < p.n_stor)
-        stor_prox(p, w, rho_dev, fsu, kpf, wsm, resid, lane);
+        stor_prox(p, w, rho_dev, fsu, kpf, Bo, Uo, wsm, lane);
       else
-        ramp_prox(p, w - p.n_stor, rho_dev, fsu, kpf, wsm, resid, lane);
+        ramp_prox(p, w - p.n_stor, rho_dev, fsu, kpf, Bo, Uo, wsm, lane);
     }
-    for (long long item = gthr; item < n_closed_items + n_line_items; item += nthr) {
-      if (item < n_closed_items) {
-        const int ci = (int)(item / TV), tc = (int)(item % TV);
-        const int d = p.closed_ids[ci];
-        const int nd = p.dev_node[d];
-        const size_t od = (size_t)d * T + tc * VW, on = (size_t)nd * T + tc * VW;
-        FV<VW> pd = ldv<VW>(p.PD + od);
-        const FV<VW> sp = ldv<VW>(p.SPBAR + on), sum_u = ldv<VW>(p.SU + on);
-        const FV<VW> lo = ldv<VW>(p.dev_lo + od), hi = ldv<VW>(p.dev_hi + od);
-        const float a = p.dev_a[d], b = p.dev_b[d];
-        const float den = 2.f * a + rho_dev;
-        FV<VW> dpd;
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-          const float x = pd.v[e] - (sp.v[e] + fsu * sum_u.v[e]) / kpf;
-          const float pn = fminf(fmaxf((rho_dev * x - b) / den, lo.v[e]), hi.v[e]);
-          dpd.v[e] = pn - pd.v[e];
-          pd.v[e] = pn;
+    {
+      const float rkp = __frcp_rn(kpf);
+      Idx3 ix, dx;
+      ix.set((unsigned)gthr, 1 << 30, T);
+      dx.set((unsigned)nthr, 1 << 30, T);
+      for (unsigned item = (unsigned)gthr; item < (unsigned)n_cnode_items; item += (unsigned)nthr,
+                    ix.step(dx, 1 << 30, T)) {
+        const int ci = ix.b, t = ix.c;
+        const size_t on = (size_t)p.cnode_ids[ci] * T + t;
+        float sp = 0.f, sq = 0.f;
+        for (int k = 0; k < Kp; ++k) {            // sum_k pbar and sum_k u at the node
+          sp += Bo[k * NT + on];
+          sq += Uo[k * NT + on];
         }
-        stv<VW>(p.PD + od, pd);
-        if (resid) stv<VW>(p.DPD + od, dpd);
-      } else {
-        const long long li = item - n_closed_items;
-        const int k = (int)(li / ((long long)L * TV));
-        const long long rem = li - (long long)k * L * TV;
-        const int l = (int)(rem / TV), tc = (int)(rem % TV);
-        const int n1 = p.line_n1[l], n2 = p.line_n2[l];
-        const bool act = p.out_line[k] != l;
-        const size_t ol = ((size_t)k * L + l) * T + tc * VW;
-        const size_t o1 = ((size_t)k * N + n1) * T + tc * VW;
-        const size_t o2 = ((size_t)k * N + n2) * T + tc * VW;
-        FV<VW> P = ldv_cs<VW>(p.P + ol), A1 = ldv_cs<VW>(p.TH1 + ol), A2 = ldv_cs<VW>(p.TH2 + ol);
-        FV<VW> V1 = ldv_cs<VW>(p.V1 + ol), V2 = ldv_cs<VW>(p.V2 + ol);
-        const FV<VW> U1 = ldv<VW>(p.U + o1), U2 = ldv<VW>(p.U + o2);
-        const FV<VW> B1 = ldv<VW>(p.PBAR + o1), B2 = ldv<VW>(p.PBAR + o2);
-        const FV<VW> G1 = ldv<VW>(p.THBAR + o1), G2 = ldv<VW>(p.THBAR + o2);
-        // line prox (Section 4.2 closed form, denominator as derived in the oracle)
-        float tb = 1.f, den = 1.f, ulim = 0.f;
-        if (act) {
-          const float bb = p.line_b[l];
-          ulim = p.line_u[l];
-          tb = 2.f * bb;
-          den = 2.f * frp + frt / (tb * bb);
+        const float xs = div_rn(sp + fsu * sq, kpf, rkp);   // avg_k(pbar + u)
+        for (int j = p.cnode_ptr[ci]; j < p.cnode_ptr[ci + 1]; ++j) {
+          const int d = p.cnode_dev[j];
+          const size_t od = (size_t)d * T + t;
+          const float pd = p.PD[od];
+          const float x = pd - xs;                  // p_d - avg_k(pbar + u)
+          const float den = 2.f * p.dev_a[d] + rho_dev;
+          const float pn = fminf(fmaxf(div_rn(rho_dev * x - p.dev_b[d], den, __frcp_rn(den)), p.dev_lo[od]),
+                                 p.dev_hi[od]);
+          p.DPD[od] = pn - pd;
+          p.PD[od] = pn;
         }
-        FV<VW> DPv;
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-          const float x1 = -P.v[e] - B1.v[e] - fsu * U1.v[e];
-          const float x2 = P.v[e] - B2.v[e] - fsu * U2.v[e];
-          const float v1 = v_fresh ? fsv * V1.v[e] : fsv * (V1.v[e] + (A1.v[e] - G1.v[e]));
-          const float v2 = v_fresh ? fsv * V2.v[e] : fsv * (V2.v[e] + (A2.v[e] - G2.v[e]));
-          const float y1 = G1.v[e] - v1, y2 = G2.v[e] - v2;
-          float pn, t1, t2;
-          if (act) {
-            const float num = frp * (x2 - x1) + frt * (y1 - y2) / tb;
-            pn = fminf(fmaxf(num / den, -ulim), ulim);
-            const float mid = 0.5f * (y1 + y2);
-            const float h = pn / tb;
-            t1 = mid + h;
-            t2 = mid - h;
-          } else {
-            pn = 0.f;
-            t1 = y1;
-            t2 = y2;
-          }
-          DPv.v[e] = pn - P.v[e];
-          P.v[e] = pn;
-          A1.v[e] = t1;
-          A2.v[e] = t2;
-          V1.v[e] = v1;
-          V2.v[e] = v2;
-        }
-        stv_cs<VW>(p.P + ol, P);
-        stv_cs<VW>(p.TH1 + ol, A1);
-        stv_cs<VW>(p.TH2 + ol, A2);
-        stv_cs<VW>(p.V1 + ol, V1);
-        stv_cs<VW>(p.V2 + ol, V2);
-        if (resid) stv_cs<VW>(p.DP + ol, DPv);
       }
     }
     if (!grid_barrier(p, &s_flag)) { status = ST_TIMEOUT; break; }
 
-    // ---------------- phase B: node averages, prices, residual partials ----------------
-    for (long long item = gthr; item < (long long)N * TV; item += nthr) {
-      const int n = (int)(item / TV), tc = (int)(item % TV);
-      const int l0 = p.lcsr_ptr[n], l1 = p.lcsr_ptr[n + 1];
-      const int d0 = p.dcsr_ptr[n], d1 = p.dcsr_ptr[n + 1];
-      const float cp = p.cnt_p[n], ct = p.cnt_th[n];
-      FV<VW> devsum;
-#pragma unroll
-      for (int e = 0; e < VW; ++e) devsum.v[e] = 0.f;
-      for (int j = d0; j < d1; ++j) {
-        const FV<VW> x = ldv<VW>(p.PD + (size_t)p.dcsr_idx[j] * T + tc * VW);
-#pragma unroll
-        for (int e = 0; e < VW; ++e) devsum.v[e] += x.v[e];
+    // ------- stages: node sums of group s-1 first (their inputs were written
+    // by the previous stage), then line proxes of group s
+    for (int s = 0; s <= S && ok; ++s) {
+      if (s > 0) {
+        const int kb0 = (s - 1) * G, kb1 = min(Kp, s * G);
+        const unsigned nb = (unsigned)((kb1 - kb0) * node_per_k);
+        Idx3 ix, dx;
+        ix.set((unsigned)gthr, N, TV);
+        dx.set((unsigned)nthr, N, TV);
+        for (unsigned item = (unsigned)gthr; item < nb; item += (unsigned)nthr, ix.step(dx, N, TV))
+          node_item<VW>(p, old, nw, kb0 + ix.a, ix.b, ix.c * VW, fsu, acc);
       }
-      FV<VW> sumpb, sumu;
-#pragma unroll
-      for (int e = 0; e < VW; ++e) { sumpb.v[e] = 0.f; sumu.v[e] = 0.f; }
-      for (int k = 0; k < Kp; ++k) {
-        FV<VW> sp = devsum, st;
-#pragma unroll
-        for (int e = 0; e < VW; ++e) st.v[e] = 0.f;
-        const size_t kb = (size_t)k * L * T + tc * VW;
-        for (int j = l0; j < l1; ++j) {
-          const int code = p.lcsr_idx[j];
-          const size_t ol = kb + (size_t)(code >> 1) * T;
-          const FV<VW> pl = ldv<VW>(p.P + ol);
-          const FV<VW> th = ldv<VW>(((code & 1) ? p.TH2 : p.TH1) + ol);
-#pragma unroll
-          for (int e = 0; e < VW; ++e) {
-            sp.v[e] += (code & 1) ? pl.v[e] : -pl.v[e];
-            st.v[e] += th.v[e];
-          }
-        }
-        const size_t on = ((size_t)k * N + n) * T + tc * VW;
-        FV<VW> u = ldv<VW>(p.U + on), pb, tbar, dpb;
-        FV<VW> pb_old, tb_old;
-        if (resid) {
-          pb_old = ldv<VW>(p.PBAR + on);
-          tb_old = ldv<VW>(p.THBAR + on);
-        }
-        float a_pp = 0.f, a_pt = 0.f, a_dp = 0.f, a_dt = 0.f, a_nf = 0.f;
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-          pb.v[e] = sp.v[e] / cp;                              // Eq. (average-op)
-          tbar.v[e] = ct > 0.f ? st.v[e] / ct : 0.f;
-          u.v[e] = fsu * u.v[e] + pb.v[e];                      // u += pbar
-          sumpb.v[e] += pb.v[e];
-          sumu.v[e] += u.v[e];
-          a_pp += cp * pb.v[e] * pb.v[e];
-          if (!isfinite(u.v[e]) || !isfinite(tbar.v[e])) a_nf += 1.f;
-          if (resid) {
-            dpb.v[e] = pb.v[e] - pb_old.v[e];
-            const float ddt = tbar.v[e] - tb_old.v[e];
-            a_dt += ct * ddt * ddt;
-          }
-        }
-        // second pass over the terminals (rows are L1-resident): theta~ and p~ change
-        for (int j = l0; j < l1; ++j) {
-          const int code = p.lcsr_idx[j];
-          const size_t ol = kb + (size_t)(code >> 1) * T;
-          const FV<VW> th = ldv<VW>(((code & 1) ? p.TH2 : p.TH1) + ol);
-#pragma unroll
-          for (int e = 0; e < VW; ++e) {
-            const float r = th.v[e] - tbar.v[e];
-            a_pt += r * r;
-          }
-          if (resid) {
-            const FV<VW> dl = ldv<VW>(p.DP + ol);
-#pragma unroll
-            for (int e = 0; e < VW; ++e) {
-              const float r = ((code & 1) ? dl.v[e] : -dl.v[e]) - dpb.v[e];
-              a_dp += r * r;
-            }
-          }
-        }
-        if (resid) {
-          for (int j = d0; j < d1; ++j) {
-            const FV<VW> dd = ldv<VW>(p.DPD + (size_t)p.dcsr_idx[j] * T + tc * VW);
-#pragma unroll
-            for (int e = 0; e < VW; ++e) {
-              const float r = dd.v[e] - dpb.v[e];
-              a_dp += r * r;
-            }
-          }
-        }
-        acc[SL_PP] += a_pp;
-        acc[SL_PT] += a_pt;
-        acc[SL_DP] += a_dp;
-        acc[SL_DT] += a_dt;
-        acc[SL_NF] += a_nf;
-        stv<VW>(p.U + on, u);
-        stv<VW>(p.PBAR + on, pb);
-        stv<VW>(p.THBAR + on, tbar);
+      if (s < S) {
+        const int ka0 = s * G, ka1 = min(Kp, (s + 1) * G);
+        const unsigned na = (unsigned)((ka1 - ka0) * line_per_k);
+        Idx3 ix, dx;
+        ix.set((unsigned)gthr, L, TV);
+        dx.set((unsigned)nthr, L, TV);
+        for (unsigned item = (unsigned)gthr; item < na; item += (unsigned)nthr, ix.step(dx, L, TV))
+          line_item<VW>(p, old, nw, ka0 + ix.a, ix.b, ix.c * VW, frp, frt, fsu, fsv, v_fresh);
       }
-      stv<VW>(p.SPBAR + (size_t)n * T + tc * VW, sumpb);
-      stv<VW>(p.SU + (size_t)n * T + tc * VW, sumu);
+      if (!grid_barrier(p, &s_flag)) { status = ST_TIMEOUT; ok = false; }
     }
-    // block reduction of the partials in FP64
+    if (!ok) break;
+
+    // block reduction of the partial sums: FP32 within a warp, FP64 across
 #pragma unroll
     for (int s = 0; s < NSLOT; ++s) {
-      double v = (double)acc[s];
+      float v = acc[s];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) red[wib][s] = v;
+      if (lane == 0) red[wib][s] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x < NSLOT) {
       double v = 0.0;
       for (int w = 0; w < WARPS; ++w) v += red[w][threadIdx.x];
-      p.partials[((size_t)par * gridDim.x + blockIdx.x) * NSLOT + threadIdx.x] = v;
+      p.partials[((size_t)(itn & 1) * gridDim.x + blockIdx.x) * NSLOT + threadIdx.x] = v;
     }
     if (!grid_barrier(p, &s_flag)) { status = ST_TIMEOUT; break; }
 
@@ -650,7 +723,7 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
       double tot[NSLOT];
 #pragma unroll
       for (int s = 0; s < NSLOT; ++s) tot[s] = 0.0;
-      const double *base = p.partials + (size_t)par * gridDim.x * NSLOT;
+      const double *base = p.partials + (size_t)(itn & 1) * gridDim.x * NSLOT;
       for (int b = lane; b < (int)gridDim.x; b += 32) {
         double v[NSLOT];
 #pragma unroll
@@ -666,18 +739,19 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
         tot[s] = v;
       }
       if (lane == 0) {
+        const double rho_p = sd[0], rho_th = sd[1];
         const double r_pp = sqrt(fmax(tot[SL_PP], 0.0));
         const double r_pt = sqrt(fmax(tot[SL_PT], 0.0));
         const double r_dp = rho_p * sqrt(fmax(tot[SL_DP], 0.0));
         const double r_dt = rho_th * sqrt(fmax(tot[SL_DT], 0.0));
         const double rp = sqrt(r_pp * r_pp + r_pt * r_pt);
         const double rd = sqrt(r_dp * r_dp + r_dt * r_dt);
-        double stop = 0.0, st = 0.0, nrp = rho_p, nrt = rho_th;
-        if (!isfinite(rp) || (resid && !isfinite(rd)) || tot[SL_NF] != 0.0) {
-          st = ST_NONFINITE;
-          stop = 1.0;
+        int code = 0;
+        double nrp = rho_p, nrt = rho_th;
+        if (!isfinite(rp) || !isfinite(rd) || tot[SL_NF] != 0.0) {
+          code = 1 | (ST_NONFINITE << 2);
         } else {
-          if (check_now && fmax(rp, rd) <= p.tol) stop = 2.0;
+          if (check_now && fmax(rp, rd) <= p.tol) code = 2;
           if (adapt_now) {
             if (r_pp > p.mu * r_dp) nrp = rho_p * p.gamma;
             else if (r_dp > p.mu * r_pp) nrp = rho_p / p.gamma;
@@ -685,27 +759,18 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
             else if (r_dt > p.mu * r_pt) nrt = rho_th / p.gamma;
           }
         }
-        dec[0] = rp; dec[1] = resid ? rd : res[1];
-        dec[2] = r_pp; dec[3] = r_pt;
-        dec[4] = resid ? r_dp : res[4]; dec[5] = resid ? r_dt : res[5];
-        dec[6] = stop + 4.0 * st;
-        red[0][0] = nrp;
-        red[0][1] = nrt;
+        sd[4] = rp; sd[5] = rd; sd[6] = r_pp; sd[7] = r_pt; sd[8] = r_dp; sd[9] = r_dt;
+        sd[2] = rho_p / nrp;   // pending rescale of u and v (Section 3.5)
+        sd[3] = rho_th / nrt;
+        sd[0] = nrp;
+        sd[1] = nrt;
+        s_code = code;
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 6; ++j) res[j] = dec[j];
-    const int code = (int)dec[6];
-    const double nrp = red[0][0], nrt = red[0][1];
-    __syncthreads();  // red is rewritten in the next iteration
-    su = rho_p / nrp;
-    sv = rho_th / nrt;
-    rho_p = nrp;
-    rho_th = nrt;
+    const int code = s_code;
     it = itn;
     v_fresh = 0;
-    dual_valid = resid ? 1 : 0;
     if ((code & 3) == 2) converged = 1;
     if (code >= 4) status = code >> 2;
     if (code != 0) break;
@@ -713,55 +778,75 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
 
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     DevScalars sc = sc0;
-    sc.rho_p = rho_p;
-    sc.rho_th = rho_th;
-    sc.su = su;
-    sc.sv = sv;
-    for (int j = 0; j < 6; ++j) sc.res[j] = res[j];
+    sc.rho_p = sd[0];
+    sc.rho_th = sd[1];
+    sc.su = sd[2];
+    sc.sv = sd[3];
+    for (int j = 0; j < 6; ++j) sc.res[j] = sd[4 + j];
     sc.it = it;
     sc.converged = converged;
-    int e = *(volatile int *)p.err;
+    const int e = *(volatile int *)p.err;
     sc.status = status ? status : (e ? e : sc0.status);
     sc.v_fresh = v_fresh;
-    sc.dual_valid = dual_valid;
     *p.sc = sc;
   }
 }
 
 // ---------------------------------------------------------------------------
-// auxiliary kernels: averages after a state import, deferred-v export,
-// prices, v projection on import
+// import / export between internal and caller numbering
 // ---------------------------------------------------------------------------
-__global__ void node_average_kernel(Params p) {
+__global__ void import_kernel(Params p, int cur, const float *pl, const float *a1, const float *a2,
+                              const float *v1, const float *v2, const float *u) {
+  const int T = p.T, L = p.L, N = p.N;
+  const long long nl = (long long)p.Kp * L * T, nn = (long long)p.Kp * N * T;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nl + nn;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i < nl) {
+      const int k = (int)(i / ((long long)L * T));
+      const long long rem = i - (long long)k * L * T;
+      const int l = (int)(rem / T), t = (int)(rem % T);
+      const size_t src = ((size_t)k * L + p.line_perm[l]) * T + t;
+      p.P[cur][i] = pl ? pl[src] : 0.f;
+      p.TH1[cur][i] = a1 ? a1[src] : 0.f;
+      p.TH2[cur][i] = a2 ? a2[src] : 0.f;
+      p.V1[cur][i] = v1 ? v1[src] : 0.f;
+      p.V2[cur][i] = v2 ? v2[src] : 0.f;
+    } else {
+      const long long j = i - nl;
+      const int k = (int)(j / ((long long)N * T));
+      const long long rem = j - (long long)k * N * T;
+      const int n = (int)(rem / T), t = (int)(rem % T);
+      p.U[cur][j] = u ? u[((size_t)k * N + p.node_perm[n]) * T + t] : 0.f;
+    }
+  }
+}
+
+// node averages from the stored terminal values (after import)
+__global__ void node_average_kernel(Params p, int cur) {
   const int T = p.T, N = p.N, L = p.L;
   for (long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x; item < (long long)N * T;
        item += (long long)gridDim.x * blockDim.x) {
     const int n = (int)(item / T), t = (int)(item % T);
     float devsum = 0.f;
     for (int j = p.dcsr_ptr[n]; j < p.dcsr_ptr[n + 1]; ++j) devsum += p.PD[(size_t)p.dcsr_idx[j] * T + t];
-    float sumpb = 0.f, sumu = 0.f;
     for (int k = 0; k < p.Kp; ++k) {
       float sp = devsum, st = 0.f;
       for (int j = p.lcsr_ptr[n]; j < p.lcsr_ptr[n + 1]; ++j) {
-        const int code = p.lcsr_idx[j];
+        const int code = p.lcsr[j].x;
         const size_t ol = ((size_t)k * L + (code >> 1)) * T + t;
-        sp += (code & 1) ? p.P[ol] : -p.P[ol];
-        st += (code & 1) ? p.TH2[ol] : p.TH1[ol];
+        sp += (code & 1) ? p.P[cur][ol] : -p.P[cur][ol];
+        st += (code & 1) ? p.TH2[cur][ol] : p.TH1[cur][ol];
       }
       const size_t on = ((size_t)k * N + n) * T + t;
       const float pb = sp / p.cnt_p[n];
-      p.PBAR[on] = pb;
-      p.THBAR[on] = p.cnt_th[n] > 0.f ? st / p.cnt_th[n] : 0.f;
-      sumpb += pb;
-      sumu += p.U[on];
+      p.PBAR[cur][on] = pb;
+      p.THBAR[cur][on] = p.cnt_th[n] > 0.f ? st / p.cnt_th[n] : 0.f;
     }
-    p.SPBAR[(size_t)n * T + t] = sumpb;
-    p.SU[(size_t)n * T + t] = sumu;
   }
 }
 
 // v projected onto v_bar = 0 per node and contingency (Appendix C)
-__global__ void project_v_kernel(Params p) {
+__global__ void project_v_kernel(Params p, int cur) {
   const int T = p.T, N = p.N, L = p.L;
   for (long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
        item < (long long)p.Kp * N * T; item += (long long)gridDim.x * blockDim.x) {
@@ -772,56 +857,64 @@ __global__ void project_v_kernel(Params p) {
     if (l1 == l0) continue;
     float s = 0.f;
     for (int j = l0; j < l1; ++j) {
-      const int code = p.lcsr_idx[j];
+      const int code = p.lcsr[j].x;
       const size_t ol = ((size_t)k * L + (code >> 1)) * T + t;
-      s += (code & 1) ? p.V2[ol] : p.V1[ol];
+      s += (code & 1) ? p.V2[cur][ol] : p.V1[cur][ol];
     }
     const float m = s / p.cnt_th[n];
     for (int j = l0; j < l1; ++j) {
-      const int code = p.lcsr_idx[j];
+      const int code = p.lcsr[j].x;
       const size_t ol = ((size_t)k * L + (code >> 1)) * T + t;
-      if (code & 1) p.V2[ol] -= m; else p.V1[ol] -= m;
+      if (code & 1) p.V2[cur][ol] -= m; else p.V1[cur][ol] -= m;
     }
   }
 }
 
-// current v = sv * (V + theta - theta_bar) (deferred update), or sv * V when fresh
-__global__ void export_v_kernel(Params p, float *v1, float *v2) {
+// lines to caller numbering; v = sv (V + theta - theta_bar) unless fresh
+__global__ void export_lines_kernel(Params p, int cur, float *pl, float *a1, float *a2, float *v1,
+                                    float *v2) {
   const DevScalars sc = *p.sc;
   const float sv = (float)sc.sv;
   const int T = p.T, N = p.N, L = p.L;
-  for (long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-       item < (long long)p.Kp * L * T; item += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(item / ((long long)L * T));
-    const long long rem = item - (long long)k * L * T;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)p.Kp * L * T;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i / ((long long)L * T));
+    const long long rem = i - (long long)k * L * T;
     const int l = (int)(rem / T), t = (int)(rem % T);
-    const size_t ol = item;
-    float a = p.V1[ol], b = p.V2[ol];
-    if (!sc.v_fresh) {
-      a += p.TH1[ol] - p.THBAR[((size_t)k * N + p.line_n1[l]) * T + t];
-      b += p.TH2[ol] - p.THBAR[((size_t)k * N + p.line_n2[l]) * T + t];
+    const size_t dst = ((size_t)k * L + p.line_perm[l]) * T + t;
+    if (pl) pl[dst] = p.P[cur][i];
+    if (a1) a1[dst] = p.TH1[cur][i];
+    if (a2) a2[dst] = p.TH2[cur][i];
+    if (v1 || v2) {
+      float x = p.V1[cur][i], y = p.V2[cur][i];
+      if (!sc.v_fresh) {
+        x += p.TH1[cur][i] - p.THBAR[cur][((size_t)k * N + p.line_n1[l]) * T + t];
+        y += p.TH2[cur][i] - p.THBAR[cur][((size_t)k * N + p.line_n2[l]) * T + t];
+      }
+      if (v1) v1[dst] = sv * x;
+      if (v2) v2[dst] = sv * y;
     }
-    if (v1) v1[ol] = sv * a;
-    if (v2) v2[ol] = sv * b;
   }
 }
 
-__global__ void export_u_kernel(Params p, float *u) {
-  const float su = (float)p.sc->su;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)p.Kp * p.N * p.T;
-       i += (long long)gridDim.x * blockDim.x)
-    u[i] = su * p.U[i];
-}
-
-// price_{n,t} = -rho_p * sum_k u_{k,n,t} with the pending rescale applied
-__global__ void price_kernel(Params p, float *price) {
+// nodes to caller numbering: u (pending rescale applied), theta_bar, and the
+// prices -rho_p sum_k u_k
+__global__ void export_nodes_kernel(Params p, int cur, float *u, float *theta, float *price) {
   const DevScalars sc = *p.sc;
-  const double f = -sc.rho_p * sc.su;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)p.N * p.T;
+  const int T = p.T, N = p.N;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)N * T;
        i += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(i / T), t = (int)(i % T);
+    const size_t ext = (size_t)p.node_perm[n] * T + t;
     double s = 0.0;
-    for (int k = 0; k < p.Kp; ++k) s += p.U[(size_t)k * p.N * p.T + i];
-    price[i] = (float)(f * s);
+    for (int k = 0; k < p.Kp; ++k) {
+      const size_t o = (size_t)k * N * T + i;
+      const float uu = p.U[cur][o];
+      if (u) u[(size_t)k * N * T + ext] = (float)(sc.su * uu);
+      if (theta) theta[(size_t)k * N * T + ext] = p.THBAR[cur][o];
+      s += uu;
+    }
+    if (price) price[ext] = (float)(-sc.rho_p * sc.su * s);
   }
 }
 
@@ -840,38 +933,30 @@ static size_t iteration_smem(int T) { return (size_t)WARPS * 3 * (T + 1) * sizeo
 
 using namespace opfk;
 
+template <int VW>
+static cudaError_t occupancy(int *nb, size_t sm) {
+  if (sm > 48 * 1024) cudaFuncSetAttribute(iteration_kernel<VW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, iteration_kernel<VW>, BLOCK, sm);
+}
+
 int opfk_max_grid(int T, int *grid) {
   int dev = 0, sms = 0, nb = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  cudaError_t e;
-  if (T % 4 == 0)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, iteration_kernel<4>, BLOCK, iteration_smem(T));
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, iteration_kernel<1>, BLOCK, iteration_smem(T));
+  const size_t sm = iteration_smem(T);
+  const cudaError_t e = (T % 4 == 0) ? occupancy<4>(&nb, sm) : occupancy<1>(&nb, sm);
   if (e != cudaSuccess || nb < 1) return -1;
   *grid = nb * sms;
   return 0;
 }
 
-int opfk_iteration_launch(const Params &p, void *stream, int *grid_used, char *msg, int msglen) {
+int opfk_iteration_launch(const Params &p, void *stream, int grid, char *msg, int msglen) {
   cudaStream_t s = (cudaStream_t)stream;
-  int grid = *grid_used;
-  size_t sm = iteration_smem(p.T);
-  if (sm > 48 * 1024) {
-    cudaError_t e = (p.T % 4 == 0)
-        ? cudaFuncSetAttribute(iteration_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-        : cudaFuncSetAttribute(iteration_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) {
-      snprintf(msg, msglen, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-      return -1;
-    }
-  }
+  const size_t sm = iteration_smem(p.T);
   Params pp = p;
   void *args[] = {&pp};
-  cudaError_t e = (p.T % 4 == 0)
-      ? cudaLaunchCooperativeKernel((void *)iteration_kernel<4>, dim3(grid), dim3(BLOCK), args, sm, s)
-      : cudaLaunchCooperativeKernel((void *)iteration_kernel<1>, dim3(grid), dim3(BLOCK), args, sm, s);
+  void *fn = (p.T % 4 == 0) ? (void *)iteration_kernel<4> : (void *)iteration_kernel<1>;
+  const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BLOCK), args, sm, s);
   if (e != cudaSuccess) {
     snprintf(msg, msglen, "cudaLaunchCooperativeKernel: %s", cudaGetErrorString(e));
     return -1;
@@ -886,28 +971,34 @@ static int aux_grid(long long work) {
   return (int)g;
 }
 
-int opfk_node_average_launch(const Params &p, void *stream) {
-  node_average_kernel<<<aux_grid((long long)p.N * p.T), 256, 0, (cudaStream_t)stream>>>(p);
+int opfk_import_launch(const Params &p, int cur, const float *pl, const float *a1, const float *a2,
+                       const float *v1, const float *v2, const float *u, void *stream) {
+  const long long work = (long long)p.Kp * (p.L + p.N) * p.T;
+  import_kernel<<<aux_grid(work), 256, 0, (cudaStream_t)stream>>>(p, cur, pl, a1, a2, v1, v2, u);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int opfk_project_v_launch(const Params &p, void *stream) {
-  project_v_kernel<<<aux_grid((long long)p.Kp * p.N * p.T), 256, 0, (cudaStream_t)stream>>>(p);
+int opfk_node_average_launch(const Params &p, int cur, void *stream) {
+  node_average_kernel<<<aux_grid((long long)p.N * p.T), 256, 0, (cudaStream_t)stream>>>(p, cur);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int opfk_export_v_launch(const Params &p, float *v1, float *v2, void *stream) {
-  export_v_kernel<<<aux_grid((long long)p.Kp * p.L * p.T), 256, 0, (cudaStream_t)stream>>>(p, v1, v2);
+int opfk_project_v_launch(const Params &p, int cur, void *stream) {
+  project_v_kernel<<<aux_grid((long long)p.Kp * p.N * p.T), 256, 0, (cudaStream_t)stream>>>(p, cur);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int opfk_export_u_launch(const Params &p, float *u, void *stream) {
-  export_u_kernel<<<aux_grid((long long)p.Kp * p.N * p.T), 256, 0, (cudaStream_t)stream>>>(p, u);
+int opfk_export_lines_launch(const Params &p, int cur, float *pl, float *a1, float *a2, float *v1,
+                             float *v2, void *stream) {
+  export_lines_kernel<<<aux_grid((long long)p.Kp * p.L * p.T), 256, 0, (cudaStream_t)stream>>>(
+      p, cur, pl, a1, a2, v1, v2);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int opfk_price_launch(const Params &p, float *price, void *stream) {
-  price_kernel<<<aux_grid((long long)p.N * p.T), 256, 0, (cudaStream_t)stream>>>(p, price);
+int opfk_export_nodes_launch(const Params &p, int cur, float *u, float *theta, float *price,
+                             void *stream) {
+  export_nodes_kernel<<<aux_grid((long long)p.N * p.T), 256, 0, (cudaStream_t)stream>>>(p, cur, u, theta,
+                                                                                         price);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
