@@ -59,6 +59,7 @@ struct opf_ctx {
   opf_options opt{};
   int N = 0, L = 0, T = 0, K = 0, Kp = 0, S = 0, G = 0, D = 0, B = 0;
   int n_closed = 0, n_cnode = 0, n_ramp = 0, n_stor = 0;
+  size_t n_tcode = 0;  // padded terminal-code list length
   int grid = 0;
   char *arena = nullptr;
   size_t arena_bytes = 0;
@@ -271,6 +272,9 @@ void carve(opf_ctx *c, Arena &a) {
   p.cnt_th = a.take<float>(c->N);
   p.rcnt_p = a.take<float>(c->N);
   p.rcnt_th = a.take<float>(c->N);
+  p.ndesc = a.take<int4>(c->N);
+  p.ncnt = a.take<float4>(c->N);
+  p.tcode = a.take<int>(c->n_tcode);
   p.dev_node = a.take<int>(c->S);
   p.dev_type = a.take<int>(c->S);
   p.cnode_ids = a.take<int>(c->n_cnode);
@@ -492,6 +496,14 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
     delete c;
     return fail(OPF_ECUDA, "occupancy query for the iteration kernel failed");
   }
+  // terminal codes per node, padded to a multiple of 4
+  std::vector<int> tcode, tptr(N + 1, 0);
+  for (int n = 0; n < N; ++n) {
+    for (int j = lptr[n]; j < lptr[n + 1]; ++j) tcode.push_back(lcsr[j].x);
+    while (tcode.size() % 4) tcode.push_back(-1);
+    tptr[n + 1] = (int)tcode.size();
+  }
+  c->n_tcode = tcode.size();
   Arena a;
   carve(c, a);
   c->arena_bytes = a.off + 256;
@@ -558,6 +570,17 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   up(p.cnt_th, cnt_th);
   up(p.rcnt_p, rcnt_p);
   up(p.rcnt_th, rcnt_th);
+  {
+    std::vector<int4> nd(N);
+    std::vector<float4> nc(N);
+    for (int n = 0; n < N; ++n) {
+      nd[n] = make_int4(tptr[n], tptr[n + 1], dptr[n], dptr[n + 1]);
+      nc[n] = make_float4(cnt_p[n], cnt_th[n], rcnt_p[n], rcnt_th[n]);
+    }
+    up(p.ndesc, nd);
+    up(p.ncnt, nc);
+  }
+  up(p.tcode, tcode);
   up(p.dev_node, dev_node_int);
   up(p.dev_type, dev_type);
   up(p.cnode_ids, cnode_ids);

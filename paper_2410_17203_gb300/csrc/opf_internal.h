@@ -67,6 +67,10 @@ struct Params {
   const int *dcsr_ptr, *dcsr_idx;  // devices of each node
   const float *cnt_p, *cnt_th;     // terminals per node: all (power), line terminals (phase)
   const float *rcnt_p, *rcnt_th;   // their reciprocals (0 for a node without line terminals)
+  const int4 *ndesc;               // per node: tcode begin, end, dcsr begin, end
+  const float4 *ncnt;              // per node: cnt_p, cnt_th, rcnt_p, rcnt_th
+  const int *tcode;                // line terminals 2*l + end per node, each node's list
+                                   // padded to a multiple of 4 with -1 (int4 loads)
   // devices: type 0 = closed-form prox clip((rho X - b)/(2a + rho), lo, hi), 1 = inner ADMM
   float *PD, *DPD;
   const int *dev_node, *dev_type;

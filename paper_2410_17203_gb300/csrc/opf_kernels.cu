@@ -35,6 +35,7 @@ namespace opfk {
 
 constexpr int BLOCK = 256;
 constexpr int WARPS = BLOCK / 32;
+constexpr int LGRAB = 8;         // 32-item groups of line items a warp takes per counter access
 constexpr int ST_TIMEOUT = 4;    // opf_status values used on the device
 constexpr int ST_NONFINITE = 5;
 
@@ -74,6 +75,13 @@ __device__ __forceinline__ bool grid_barrier(const Params &p, int *s_flag) {
   }
   __syncthreads();
   return *s_flag != 0;
+}
+
+// shared floats per warp: 3 (T+1) for the inner-ADMM work arrays, plus room
+// for one device's (lam, beta) while the horizon is short enough
+__host__ __device__ inline int warp_smem_floats(int T) {
+  const int work = 3 * (T + 1), state = 2 * SG_N * (T + 1);
+  return T <= 128 ? work + state : work;
 }
 
 // ---------------------------------------------------------------------------
@@ -155,20 +163,68 @@ __device__ void warp_tri_solve(const float *__restrict__ q, float off, float *bu
   __syncwarp();
 }
 
+// sum over contingencies k of pbar and u at one (node, t) offset o, with 8
+// independent loads in flight per step
+__device__ __forceinline__ void ksum(const float *pbar_o, const float *u_o, size_t o, size_t stride, int Kp,
+                                     float &sp, float &sq) {
+  float a[8], b[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) { a[j] = 0.f; b[j] = 0.f; }
+  int k = 0;
+  for (; k + 8 <= Kp; k += 8) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      a[j] += pbar_o[(size_t)(k + j) * stride + o];
+      b[j] += u_o[(size_t)(k + j) * stride + o];
+    }
+  }
+  for (; k < Kp; ++k) {
+    a[0] += pbar_o[(size_t)k * stride + o];
+    b[0] += u_o[(size_t)k * stride + o];
+  }
+  sp = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  sq = ((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + (b[6] + b[7]));
+}
+
+// The warp's inner-ADMM state (lam, beta) lives in shared memory during the
+// inner iterations when it fits (lam_sh != nullptr), else in global memory.
+__device__ __forceinline__ void stage_in(float *&lam, float *&bet, float *lam_sh, int n, int lane) {
+  if (!lam_sh) return;
+  float *bsh = lam_sh + n;
+  for (int i = lane; i < n; i += 32) {
+    lam_sh[i] = lam[i];
+    bsh[i] = bet[i];
+  }
+  __syncwarp();
+  lam = lam_sh;
+  bet = bsh;
+}
+
+__device__ __forceinline__ void stage_out(float *lam_g, float *bet_g, const float *lam_sh, int n, int lane) {
+  if (!lam_sh) return;
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    lam_g[i] = lam_sh[i];
+    bet_g[i] = lam_sh[n + i];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Appendix D inner ADMM, ramp-limited generator (one warp, lanes over t).
 // Rows: p_t <= pmax_t, -p_t <= -pmin_t, p_{t+1} - p_t <= R, p_t - p_{t+1} <= R.
 // x-update matrix (2a + rho + 2 omega) I + 2 omega D'D is tridiagonal.
 // ---------------------------------------------------------------------------
 __device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf,
-                          const float *pbar_o, const float *u_o, float *sm, int lane) {
+                          const float *pbar_o, const float *u_o, float *sm, float *state_sh, int lane) {
   const int T = p.T;
   const int d = p.ramp_ids[r];
   const int n = p.dev_node[d];
   const float a = p.dev_a[d], b = p.dev_b[d], R = p.ramp_R[r];
   const float om = rho;
-  float *lam = p.ramp_lam + (size_t)r * RG_N * T;
-  float *bet = p.ramp_beta + (size_t)r * RG_N * T;
+  float *const lam_g = p.ramp_lam + (size_t)r * RG_N * T;
+  float *const bet_g = p.ramp_beta + (size_t)r * RG_N * T;
+  float *lam = lam_g, *bet = bet_g;
+  stage_in(lam, bet, state_sh, RG_N * T, lane);
   float *mf = p.ramp_q + (size_t)r * T;
   const float *lo = p.dev_lo + (size_t)d * T;
   const float *hi = p.dev_hi + (size_t)d * T;
@@ -187,12 +243,8 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf
     __syncwarp();
   }
   for (int t = lane; t < T; t += 32) {
-    size_t o = (size_t)n * T + t;
-    float sp = 0.f, sq = 0.f;
-    for (int k = 0; k < p.Kp; ++k) {
-      sp += pbar_o[(size_t)k * p.N * T + o];
-      sq += u_o[(size_t)k * p.N * T + o];
-    }
+    float sp, sq;
+    ksum(pbar_o, u_o, (size_t)n * T + t, (size_t)p.N * T, p.Kp, sp, sq);
     X[t] = pd[t] - (sp + su * sq) / kpf;   // p_d - avg_k(pbar + u)
   }
   __syncwarp();
@@ -234,6 +286,7 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf
     }
     __syncwarp();
   }
+  stage_out(lam_g, bet_g, state_sh, RG_N * T, lane);
   for (int t = lane; t < T; t += 32) {
     const float pn = Z[t];
     p.DPD[(size_t)d * T + t] = pn - pd[t];
@@ -249,15 +302,17 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf
 // system of size T + 1 in the state of charge s.
 // ---------------------------------------------------------------------------
 __device__ void stor_prox(const Params &p, int sidx, float rho, float su, float kpf,
-                          const float *pbar_o, const float *u_o, float *sm, int lane) {
+                          const float *pbar_o, const float *u_o, float *sm, float *state_sh, int lane) {
   const int T = p.T, Tp = T + 1;
   const int d = p.stor_ids[sidx];
   const int n = p.dev_node[d];
   const float eta = p.stor_eff[sidx], Pm = p.stor_P[sidx], Em = p.stor_dur[sidx] * Pm;
   const float q = p.stor_cost[sidx];
   const float om = rho;
-  float *lam = p.stor_lam + (size_t)sidx * SG_N * Tp;
-  float *bet = p.stor_beta + (size_t)sidx * SG_N * Tp;
+  float *const lam_g = p.stor_lam + (size_t)sidx * SG_N * Tp;
+  float *const bet_g = p.stor_beta + (size_t)sidx * SG_N * Tp;
+  float *lam = lam_g, *bet = bet_g;
+  stage_in(lam, bet, state_sh, SG_N * Tp, lane);
   float *mf = p.stor_q + (size_t)sidx * Tp;
   float *pd = p.PD + (size_t)d * T;
   float *dl_out = p.stor_delta + (size_t)sidx * T;
@@ -283,12 +338,8 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float su, float 
     __syncwarp();
   }
   for (int t = lane; t < T; t += 32) {
-    size_t o = (size_t)n * T + t;
-    float sp = 0.f, sq = 0.f;
-    for (int k = 0; k < p.Kp; ++k) {
-      sp += pbar_o[(size_t)k * p.N * T + o];
-      sq += u_o[(size_t)k * p.N * T + o];
-    }
+    float sp, sq;
+    ksum(pbar_o, u_o, (size_t)n * T + t, (size_t)p.N * T, p.Kp, sp, sq);
     X[t] = pd[t] - (sp + su * sq) / kpf;   // p_d - avg_k(pbar + u)
   }
   __syncwarp();
@@ -351,6 +402,7 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float su, float 
   }
 #undef LAM
 #undef BET
+  stage_out(lam_g, bet_g, state_sh, SG_N * Tp, lane);
   for (int t = lane; t < T; t += 32) {
     const float pn = TAU[t];
     p.DPD[(size_t)d * T + t] = pn - pd[t];
@@ -359,14 +411,6 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float su, float 
   __syncwarp();
 }
 
-// ---------------------------------------------------------------------------
-// the persistent iteration kernel
-// ---------------------------------------------------------------------------
-// ---------------------------------------------------------------------------
-// line prox (Section 2.1 f^ac, Section 4.2), both terminals, one lane value.
-// Inputs are the line's stored state (p at terminal 2, angles, deferred phase
-// duals) and the previous node values at its two ends.  A single call site
-// in the kernel, so both ends of a line obtain bit-identical results.
 // ---------------------------------------------------------------------------
 // VW consecutive time steps per thread (4 -> 128-bit accesses when T % 4 == 0)
 // ---------------------------------------------------------------------------
@@ -378,7 +422,11 @@ struct FV {
 template <int VW>
 __device__ __forceinline__ FV<VW> ldv(const float *p) {
   FV<VW> r;
-  if constexpr (VW == 4) {
+  if constexpr (VW == 8) {
+    const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
+    r.v[0] = a.x; r.v[1] = a.y; r.v[2] = a.z; r.v[3] = a.w;
+    r.v[4] = b.x; r.v[5] = b.y; r.v[6] = b.z; r.v[7] = b.w;
+  } else if constexpr (VW == 4) {
     const float4 t = *reinterpret_cast<const float4 *>(p);
     r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
   } else {
@@ -402,7 +450,10 @@ __device__ __forceinline__ FV<VW> ldv_cs(const float *p) {
 
 template <int VW>
 __device__ __forceinline__ void stv(float *p, const FV<VW> &r) {
-  if constexpr (VW == 4) {
+  if constexpr (VW == 8) {
+    *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    *reinterpret_cast<float4 *>(p + 4) = make_float4(r.v[4], r.v[5], r.v[6], r.v[7]);
+  } else if constexpr (VW == 4) {
     *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
   } else {
     *p = r.v[0];
@@ -412,7 +463,10 @@ __device__ __forceinline__ void stv(float *p, const FV<VW> &r) {
 // streaming store (not read again in this iteration: evict first)
 template <int VW>
 __device__ __forceinline__ void stv_cs(float *p, const FV<VW> &r) {
-  if constexpr (VW == 4) {
+  if constexpr (VW == 8) {
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(r.v[0], r.v[1], r.v[2], r.v[3]));
+    __stcs(reinterpret_cast<float4 *>(p + 4), make_float4(r.v[4], r.v[5], r.v[6], r.v[7]));
+  } else if constexpr (VW == 4) {
     __stcs(reinterpret_cast<float4 *>(p), make_float4(r.v[0], r.v[1], r.v[2], r.v[3]));
   } else {
     __stcs(p, r.v[0]);
@@ -533,20 +587,26 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
 // (contingency k, node n, VW time steps).  Sums the node's terminals in CSR
 // order (no atomics), forms pbar, theta_bar, u += pbar, and the residual
 // partial sums: ||pbar||^2, ||theta~||^2 and ||p~ - p~_prev||^2 by one-pass
-// Welford sums over the terminals, ||theta_bar - theta_bar_prev||^2.
+// Welford sums over the terminals, ||theta_bar - theta_bar_prev||^2.  The
+// terminal codes come four at a time so that a node's row loads issue
+// together.
 // ---------------------------------------------------------------------------
 template <int VW>
 __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int k, int n, int toff, float fsu,
                                           float *acc) {
   const int T = p.T, L = p.L, N = p.N;
-  const float cp = p.cnt_p[n], ct = p.cnt_th[n], rcp = p.rcnt_p[n], rct = p.rcnt_th[n];
+  const int4 nd = p.ndesc[n];
+  const float4 nc = p.ncnt[n];
+  const float cp = nc.x, ct = nc.y, rcp = nc.z, rct = nc.w;
+  const size_t on = ((size_t)k * N + n) * T + toff;
+  const FV<VW> uo = ldv<VW>(p.U[old] + on), go = ldv<VW>(p.THBAR[old] + on);
   FV<VW> sp, st;
   Welf<VW> wdp, wth;
   wdp.reset();
   wth.reset();
 #pragma unroll
   for (int e = 0; e < VW; ++e) { sp.v[e] = 0.f; st.v[e] = 0.f; }
-  for (int j = p.dcsr_ptr[n]; j < p.dcsr_ptr[n + 1]; ++j) {
+  for (int j = nd.z; j < nd.w; ++j) {
     const size_t od = (size_t)p.dcsr_idx[j] * T + toff;
     const FV<VW> pd = ldv<VW>(p.PD + od), dpd = ldv<VW>(p.DPD + od);
 #pragma unroll
@@ -554,23 +614,35 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
     wdp.add(dpd.v);
   }
   const size_t kb = (size_t)k * L * T + toff;
-  for (int j = p.lcsr_ptr[n]; j < p.lcsr_ptr[n + 1]; ++j) {
-    const int code = p.lcsr[j].x;
-    const size_t ol = kb + (size_t)(code >> 1) * T;
-    const FV<VW> pn = ldv<VW>(p.P[nw] + ol), po = ldv<VW>(p.P[old] + ol);
-    const FV<VW> th = ldv<VW>(((code & 1) ? p.TH2[nw] : p.TH1[nw]) + ol);
-    float dpo[VW];
+  for (int j = nd.x; j < nd.y; j += 4) {
+    const int4 c4 = *reinterpret_cast<const int4 *>(p.tcode + j);
+    const int code[4] = {c4.x, c4.y, c4.z, c4.w};
+    FV<VW> pn[4], po[4], th[4];
 #pragma unroll
-    for (int e = 0; e < VW; ++e) {
-      sp.v[e] += (code & 1) ? pn.v[e] : -pn.v[e];
-      st.v[e] += th.v[e];
-      dpo[e] = (code & 1) ? pn.v[e] - po.v[e] : po.v[e] - pn.v[e];
+    for (int q = 0; q < 4; ++q) {
+      if (code[q] >= 0) {
+        const size_t ol = kb + (size_t)(code[q] >> 1) * T;
+        pn[q] = ldv<VW>(p.P[nw] + ol);
+        po[q] = ldv<VW>(p.P[old] + ol);
+        th[q] = ldv<VW>(((code[q] & 1) ? p.TH2[nw] : p.TH1[nw]) + ol);
+      }
     }
-    wdp.add(dpo);
-    wth.add(th.v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (code[q] >= 0) {
+        const bool t2 = code[q] & 1;
+        float dpo[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          sp.v[e] += t2 ? pn[q].v[e] : -pn[q].v[e];
+          st.v[e] += th[q].v[e];
+          dpo[e] = t2 ? pn[q].v[e] - po[q].v[e] : po[q].v[e] - pn[q].v[e];
+        }
+        wdp.add(dpo);
+        wth.add(th[q].v);
+      }
+    }
   }
-  const size_t on = ((size_t)k * N + n) * T + toff;
-  const FV<VW> uo = ldv<VW>(p.U[old] + on), go = ldv<VW>(p.THBAR[old] + on);
   FV<VW> pb, tbar, un;
 #pragma unroll
   for (int e = 0; e < VW; ++e) {
@@ -607,7 +679,10 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
   const int gwarp = blockIdx.x * WARPS + wib, nwarp = gridDim.x * WARPS;
   const long long gthr = (long long)blockIdx.x * BLOCK + threadIdx.x;
   const long long nthr = (long long)gridDim.x * BLOCK;
-  float *wsm = smem + wib * 3 * (T + 1);
+  // per warp: 3 (T+1) work floats, then the inner-ADMM state if it fits
+  const int wfl = warp_smem_floats(T);
+  float *wsm = smem + (size_t)wib * wfl;
+  float *state_sh = (wfl > 3 * (T + 1)) ? wsm + 3 * (T + 1) : nullptr;
   const int S = (Kp + G - 1) / G;  // stage groups
 
   const DevScalars sc0 = *p.sc;
@@ -620,7 +695,8 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
   const float kpf = (float)Kp;
   const int n_inner = p.n_stor + p.n_ramp;
   const long long n_cnode_items = (long long)p.n_cnode * T;
-  const int line_per_k = L * TV, node_per_k = N * TV;
+  const int line_per_k = L * TV;
+  (void)G;
 
   // a sticky device error (timeout, non-finite) leaves the state as it is
   const int n_iters = sc0.status ? 0 : p.n_iters;
@@ -638,14 +714,16 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
     const float *Uo = p.U[old], *Bo = p.PBAR[old];
     const size_t NT = (size_t)N * T;
     float acc[NSLOT] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    bool ok = true;
 
-    // ---------------- phase D: device proxes (step 2) ----------------
+    // ------- phase 1: steps 1 and 2, both from the previous iterate -------
+    // Device proxes first (the inner-ADMM warps are latency-bound), then the
+    // line proxes, taken in contingency-major order from a counter so that
+    // warps that had devices take fewer lines.
     for (int w = gwarp; w < n_inner; w += nwarp) {
       if (w < p.n_stor)
-        stor_prox(p, w, rho_dev, fsu, kpf, Bo, Uo, wsm, lane);
+        stor_prox(p, w, rho_dev, fsu, kpf, Bo, Uo, wsm, state_sh, lane);
       else
-        ramp_prox(p, w - p.n_stor, rho_dev, fsu, kpf, Bo, Uo, wsm, lane);
+        ramp_prox(p, w - p.n_stor, rho_dev, fsu, kpf, Bo, Uo, wsm, state_sh, lane);
     }
     {
       const float rkp = __frcp_rn(kpf);
@@ -656,11 +734,8 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
                     ix.step(dx, 1 << 30, T)) {
         const int ci = ix.b, t = ix.c;
         const size_t on = (size_t)p.cnode_ids[ci] * T + t;
-        float sp = 0.f, sq = 0.f;
-        for (int k = 0; k < Kp; ++k) {            // sum_k pbar and sum_k u at the node
-          sp += Bo[k * NT + on];
-          sq += Uo[k * NT + on];
-        }
+        float sp, sq;
+        ksum(Bo, Uo, on, NT, Kp, sp, sq);          // sum_k pbar and sum_k u at the node
         const float xs = div_rn(sp + fsu * sq, kpf, rkp);   // avg_k(pbar + u)
         for (int j = p.cnode_ptr[ci]; j < p.cnode_ptr[ci + 1]; ++j) {
           const int d = p.cnode_dev[j];
@@ -675,32 +750,34 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
         }
       }
     }
+    {
+      const unsigned na = (unsigned)Kp * (unsigned)line_per_k;
+      unsigned long long *wctr = p.work + (itn & 1);
+      for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = (unsigned)atomicAdd(wctr, (unsigned long long)(32 * LGRAB));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= na) break;
+        Idx3 ix, dx;
+        ix.set(base + lane, L, TV);
+        dx.set(32u, L, TV);
+#pragma unroll 1
+        for (int g = 0; g < LGRAB; ++g, ix.step(dx, L, TV)) {
+          if (base + g * 32 + lane < na) line_item<VW>(p, old, nw, ix.a, ix.b, ix.c * VW, frp, frt, fsu, fsv, v_fresh);
+        }
+      }
+    }
     if (!grid_barrier(p, &s_flag)) { status = ST_TIMEOUT; break; }
 
-    // ------- stages: node sums of group s-1 first (their inputs were written
-    // by the previous stage), then line proxes of group s
-    for (int s = 0; s <= S && ok; ++s) {
-      if (s > 0) {
-        const int kb0 = (s - 1) * G, kb1 = min(Kp, s * G);
-        const unsigned nb = (unsigned)((kb1 - kb0) * node_per_k);
-        Idx3 ix, dx;
-        ix.set((unsigned)gthr, N, TV);
-        dx.set((unsigned)nthr, N, TV);
-        for (unsigned item = (unsigned)gthr; item < nb; item += (unsigned)nthr, ix.step(dx, N, TV))
-          node_item<VW>(p, old, nw, kb0 + ix.a, ix.b, ix.c * VW, fsu, acc);
-      }
-      if (s < S) {
-        const int ka0 = s * G, ka1 = min(Kp, (s + 1) * G);
-        const unsigned na = (unsigned)((ka1 - ka0) * line_per_k);
-        Idx3 ix, dx;
-        ix.set((unsigned)gthr, L, TV);
-        dx.set((unsigned)nthr, L, TV);
-        for (unsigned item = (unsigned)gthr; item < na; item += (unsigned)nthr, ix.step(dx, L, TV))
-          line_item<VW>(p, old, nw, ka0 + ix.a, ix.b, ix.c * VW, frp, frt, fsu, fsv, v_fresh);
-      }
-      if (!grid_barrier(p, &s_flag)) { status = ST_TIMEOUT; ok = false; }
+    // ------- phase 2: step 3, node sums of the new terminal values -------
+    {
+      const unsigned nn = (unsigned)Kp * (unsigned)(N * TV);
+      Idx3 ix, dx;
+      ix.set((unsigned)gthr, N, TV);
+      dx.set((unsigned)nthr, N, TV);
+      for (unsigned item = (unsigned)gthr; item < nn; item += (unsigned)nthr, ix.step(dx, N, TV))
+        node_item<VW>(p, old, nw, ix.a, ix.b, ix.c * VW, fsu, acc);
     }
-    if (!ok) break;
 
     // block reduction of the partial sums: FP32 within a warp, FP64 across
 #pragma unroll
@@ -760,6 +837,9 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
           }
         }
         sd[4] = rp; sd[5] = rd; sd[6] = r_pp; sd[7] = r_pt; sd[8] = r_dp; sd[9] = r_dt;
+        // this iteration's work counter is next used two iterations on,
+        // after at least one more grid barrier
+        if (blockIdx.x == 0) p.work[itn & 1] = 0ull;
         sd[2] = rho_p / nrp;   // pending rescale of u and v (Section 3.5)
         sd[3] = rho_th / nrt;
         sd[0] = nrp;
@@ -927,7 +1007,7 @@ __global__ void set_rho_kernel(DevScalars *sc, double rho) {
   *sc = s;
 }
 
-static size_t iteration_smem(int T) { return (size_t)WARPS * 3 * (T + 1) * sizeof(float); }
+static size_t iteration_smem(int T) { return (size_t)WARPS * warp_smem_floats(T) * sizeof(float); }
 
 }  // namespace opfk
 
