@@ -232,7 +232,7 @@ std::vector<int> rcm_order(int N, const std::vector<int> &ptr, const std::vector
 void carve(opf_ctx *c, Arena &a) {
   Params &p = c->P;
   const size_t KLT = (size_t)c->Kp * c->L * c->T, KNT = (size_t)c->Kp * c->N * c->T;
-  const size_t NT = (size_t)c->N * c->T, ST = (size_t)c->S * c->T;
+  const size_t ST = (size_t)c->S * c->T;
   const int T = c->T, Tp = c->T + 1;
   // state first (zeroed on reset)
   for (int b = 0; b < 2; ++b) {
@@ -524,10 +524,6 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   p.Kp = c->Kp;
   p.S = S;
   p.n_cnode = c->n_cnode;
-  // one stage group: all line proxes, then all node sums (staging the
-  // contingencies to keep new line rows in L2 cost more in grid barriers than
-  // it saved in DRAM traffic at 10k buses)
-  p.G = c->Kp;
   p.n_ramp = c->n_ramp;
   p.n_stor = c->n_stor;
   p.eps = opt.eps;

@@ -27,6 +27,9 @@
 
 namespace opfk {
 
+// threads per CTA of the persistent iteration kernel
+constexpr int BLOCK = 256;
+
 // residual partial-sum slots.  SL_NF counts non-finite node values: the prox
 // clamps (fminf/fmaxf) would otherwise turn a NaN input into a finite bound.
 enum { SL_PP = 0, SL_PT = 1, SL_DP = 2, SL_DT = 3, SL_NF = 4, NSLOT = 5 };
@@ -52,8 +55,6 @@ enum { RG_UP = 0, RG_LO = 1, RG_RU = 2, RG_RD = 3, RG_N = 4 };
 struct Params {
   int N, L, T, Kp, S;
   int n_cnode, n_ramp, n_stor;
-  int G;  // contingencies per stage group: stage s runs line proxes of group s
-          // and node sums of group s-1, whose new line rows are still in L2
   // lines (internal numbering)
   const int *line_n1, *line_n2;  // internal node of terminal 1 (from) and terminal 2 (to)
   const float *line_b, *line_u;

@@ -33,7 +33,6 @@
 
 namespace opfk {
 
-constexpr int BLOCK = 256;
 constexpr int WARPS = BLOCK / 32;
 constexpr int LGRAB = 8;         // 32-item groups of line items a warp takes per counter access
 constexpr int ST_TIMEOUT = 4;    // opf_status values used on the device
@@ -674,7 +673,7 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
   __shared__ int s_code;
   __shared__ int s_flag;
 
-  const int T = p.T, Kp = p.Kp, L = p.L, N = p.N, TV = T / VW, G = p.G;
+  const int T = p.T, Kp = p.Kp, L = p.L, N = p.N, TV = T / VW;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gwarp = blockIdx.x * WARPS + wib, nwarp = gridDim.x * WARPS;
   const long long gthr = (long long)blockIdx.x * BLOCK + threadIdx.x;
@@ -683,7 +682,6 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
   const int wfl = warp_smem_floats(T);
   float *wsm = smem + (size_t)wib * wfl;
   float *state_sh = (wfl > 3 * (T + 1)) ? wsm + 3 * (T + 1) : nullptr;
-  const int S = (Kp + G - 1) / G;  // stage groups
 
   const DevScalars sc0 = *p.sc;
   if (threadIdx.x == 0) {
@@ -696,7 +694,6 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
   const int n_inner = p.n_stor + p.n_ramp;
   const long long n_cnode_items = (long long)p.n_cnode * T;
   const int line_per_k = L * TV;
-  (void)G;
 
   // a sticky device error (timeout, non-finite) leaves the state as it is
   const int n_iters = sc0.status ? 0 : p.n_iters;
