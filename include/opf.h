@@ -176,6 +176,24 @@ opf_status opf_residuals(opf_ctx *ctx, double out[6]);
 opf_status opf_solution(opf_ctx *ctx, int32_t on_device, double *objective, float *p_dev,
                         float *p_line, float *theta_node, float *price);
 
+/* Nodal prices without any allocation: the same export as opf_solution's
+ * `price`, staged through a fixed device array instead of a per-call device
+ * buffer.  The paper has no counterpart; this is a serving convenience for
+ * callers that must not allocate once set up.
+ *   price   host float [N][T] (caller's node numbering), -rho_p * sum_k u_k
+ * Scratch: one file-scope device array of OPF_PRICE_SCRATCH_FLOATS floats
+ * (4 MiB) per device.  N * T above that returns OPF_EINVAL before any device
+ * work.  Its address is resolved once per device by opf_create (so the first
+ * price call never resolves it, e.g. during stream capture); the call itself
+ * makes no cudaMalloc / cudaFree or allocating library call, on the device
+ * or the host.  Every staged element is written before it is read, so nothing
+ * needs clearing between calls.  The array is shared by all contexts of a
+ * device: calls that overlap in time (from several threads, or on different
+ * streams) race on it and must be serialized by the caller.
+ * Synchronizes the context's stream. */
+#define OPF_PRICE_SCRATCH_FLOATS (1 << 20)
+opf_status opf_price_noalloc(opf_ctx *ctx, float *price);
+
 /* Export / import the full state (warm start, checkpoint and resume,
  * Section 3.4).  Import recomputes the node averages from p and theta and
  * projects v onto v_bar = 0 per node (Appendix C); it clears a sticky

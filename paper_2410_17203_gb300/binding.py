@@ -16,6 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libopfmp.so")
 
 OPF_OK, OPF_EINVAL, OPF_ENOMEM, OPF_ECUDA, OPF_ETIMEOUT, OPF_ENONFINITE, OPF_ESTATE = range(7)
+# capacity of the fixed device array behind opf_price_noalloc (N * T floats)
+OPF_PRICE_SCRATCH_FLOATS = 1 << 20
 
 F32P = C.POINTER(C.c_float)
 F64P = C.POINTER(C.c_double)
@@ -73,8 +75,8 @@ class opf_info(C.Structure):
 
 
 EXPORTS = ["opf_default_options", "opf_create", "opf_iterate", "opf_residuals", "opf_solution",
-           "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info", "opf_destroy",
-           "opf_status_str", "opf_last_error", "opf_abi_version"]
+           "opf_price_noalloc", "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info",
+           "opf_destroy", "opf_status_str", "opf_last_error", "opf_abi_version"]
 
 _lib = None
 
@@ -96,6 +98,7 @@ def load_library(path=None):
     lib.opf_residuals.argtypes = [C.c_void_p, F64P]
     lib.opf_solution.argtypes = [C.c_void_p, C.c_int32, F64P, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]
+    lib.opf_price_noalloc.argtypes = [C.c_void_p, C.c_void_p]
     lib.opf_get_state.argtypes = [C.c_void_p, C.c_int32, C.POINTER(opf_state)]
     lib.opf_set_state.argtypes = [C.c_void_p, C.c_int32, C.POINTER(opf_state)]
     lib.opf_reset.argtypes = [C.c_void_p]
@@ -108,8 +111,8 @@ def load_library(path=None):
     lib.opf_last_error.restype = C.c_char_p
     lib.opf_abi_version.argtypes = []
     lib.opf_abi_version.restype = C.c_int32
-    for name in ("opf_create", "opf_iterate", "opf_residuals", "opf_solution", "opf_get_state",
-                 "opf_set_state", "opf_reset", "opf_get_info"):
+    for name in ("opf_create", "opf_iterate", "opf_residuals", "opf_solution", "opf_price_noalloc",
+                 "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info"):
         getattr(lib, name).restype = C.c_int
     if path is None:
         _lib = lib
@@ -238,6 +241,18 @@ def opf_solution(h, on_device=False, objective=True, p_dev=None, p_line=None, th
         _addr(p_dev), _addr(p_line), _addr(theta_node), _addr(price))
     _check(st, "opf_solution")
     return obj.value if objective else None
+
+
+def opf_price_noalloc(h, out=None):
+    """Nodal prices [N][T] into the host float32 array ``out`` (or a new one),
+    staged through the library's fixed device array (no allocation)."""
+    if out is None:
+        info = opf_get_info(h)
+        out = np.zeros((info["N"], info["T"]), np.float32)
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float32 and out.flags.c_contiguous):
+        raise ValueError("out must be a C-contiguous float32 NumPy array")
+    _check(load_library().opf_price_noalloc(h, _addr(out)), "opf_price_noalloc")
+    return out
 
 
 STATE_FIELDS = ("p_line", "th1", "th2", "v1", "v2", "p_dev", "u", "inner")

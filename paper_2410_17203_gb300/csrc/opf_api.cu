@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -18,15 +19,19 @@ using opfk::Params;
 
 namespace {
 
-thread_local std::string g_err;
+// message of the last failing call on this thread; a fixed buffer, so that
+// reporting an error allocates nothing
+thread_local char g_err[512];
 
-opf_status fail(opf_status s, const std::string &msg) {
-  g_err = msg;
+opf_status fail(opf_status s, const char *msg) {
+  snprintf(g_err, sizeof(g_err), "%s", msg);
   return s;
 }
 
+opf_status fail(opf_status s, const std::string &msg) { return fail(s, msg.c_str()); }
+
 opf_status cuda_fail(cudaError_t e, const char *what) {
-  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? OPF_ENOMEM : OPF_ECUDA;
 }
 
@@ -60,6 +65,7 @@ struct opf_ctx {
   int N = 0, L = 0, T = 0, K = 0, Kp = 0, S = 0, G = 0, D = 0, B = 0;
   int n_closed = 0, n_cnode = 0, n_ramp = 0, n_stor = 0;
   size_t n_tcode = 0;  // padded terminal-code list length
+  float *price_scratch = nullptr;  // this device's fixed price staging array
   int grid = 0;
   char *arena = nullptr;
   size_t arena_bytes = 0;
@@ -102,7 +108,7 @@ const char *opf_status_str(opf_status s) {
   return "unknown status";
 }
 
-const char *opf_last_error(void) { return g_err.c_str(); }
+const char *opf_last_error(void) { return g_err; }
 
 int32_t opf_abi_version(void) { return OPF_ABI_VERSION; }
 
@@ -329,6 +335,28 @@ struct DevTmp {
   }
 };
 
+// Fixed staging array of opf_price_noalloc: a module-scope device variable,
+// so it exists once per device the library runs on and is never allocated.
+static __device__ __align__(256) float g_price_scratch[OPF_PRICE_SCRATCH_FLOATS];
+
+// Its address on each device, resolved once (cudaGetSymbolAddress) at
+// context creation, before any call can run inside a stream capture.
+constexpr int kMaxDevices = 64;
+float *g_price_scratch_addr[kMaxDevices] = {};
+std::mutex g_price_scratch_mu;
+
+opf_status resolve_price_scratch(int device, float **out) {
+  if (device < 0 || device >= kMaxDevices) return fail(OPF_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_price_scratch_mu);
+  if (!g_price_scratch_addr[device]) {
+    void *a = nullptr;
+    CK(cudaGetSymbolAddress(&a, g_price_scratch));
+    g_price_scratch_addr[device] = static_cast<float *>(a);
+  }
+  *out = g_price_scratch_addr[device];
+  return OPF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -491,6 +519,13 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   if (e != cudaSuccess) {
     delete c;
     return cuda_fail(e, "cudaGetDevice");
+  }
+  {
+    const opf_status ps = resolve_price_scratch(c->device, &c->price_scratch);
+    if (ps != OPF_OK) {
+      delete c;
+      return ps;
+    }
   }
   if (opfk_max_grid(T, &c->grid) != 0) {
     delete c;
@@ -775,6 +810,23 @@ opf_status opf_solution(opf_ctx *c, int32_t on_device, double *objective, float 
       for (size_t t = 0; t < T; ++t) f += c->stor_cost[b] * (double)dl[b * T + t];
     *objective = f;
   }
+  CK(cudaStreamSynchronize(c->stream));
+  return (opf_status)sc.status;
+}
+
+opf_status opf_price_noalloc(opf_ctx *c, float *price) {
+  if (!c || !price) return fail(OPF_EINVAL, "NULL argument");
+  const size_t NT = (size_t)c->N * c->T;
+  if (NT > (size_t)OPF_PRICE_SCRATCH_FLOATS)
+    return fail(OPF_EINVAL, "N * T exceeds OPF_PRICE_SCRATCH_FLOATS");
+  if (!c->price_scratch) return fail(OPF_ESTATE, "price scratch not resolved");
+  DevScalars sc;
+  opf_status s;
+  if ((s = read_scalars(c, &sc)) != OPF_OK) return s;
+  // every element of [0, N*T) is written by the export before the copy reads it
+  if (opfk_export_nodes_launch(c->P, (int)(sc.it & 1), nullptr, nullptr, c->price_scratch, c->stream) != 0)
+    return fail(OPF_ECUDA, "export launch failed");
+  CK(cudaMemcpyAsync(price, c->price_scratch, NT * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return (opf_status)sc.status;
 }

@@ -35,6 +35,12 @@ def test_every_declared_function_is_exported(lib):
     assert set(names) == set(binding.EXPORTS)
 
 
+def test_price_scratch_capacity_matches_header():
+    from paper_2410_17203_gb300 import binding
+    m = re.search(r"#define OPF_PRICE_SCRATCH_FLOATS \(1 << (\d+)\)", open(HEADER).read())
+    assert m and binding.OPF_PRICE_SCRATCH_FLOATS == 1 << int(m.group(1))
+
+
 def test_abi_version_and_status_strings(lib):
     from paper_2410_17203_gb300 import binding as b
     assert b.opf_abi_version() == 1
