@@ -10,7 +10,7 @@ here is pinned by ``-m "not gpu"`` tests against closed forms, brute force,
 analytic small grids or identities that the paper states.
 """
 from .mp import (  # noqa: F401
-    Oracle, OracleOptions, Network,
+    Oracle, OracleOptions, Network, Shard,
     prox_gen, prox_line, prox_fixed_load,
     ramp_rows, storage_rows, inner_admm, inner_matrix,
     node_mean, average, residual,

@@ -252,7 +252,7 @@ class Network:
     terminals: the ``2L`` line terminals (the first ``2L`` power terminals).
     """
 
-    def __init__(self, case):
+    def __init__(self, case, k_ids=None):
         self.case = case
         self.T = int(case["T"])
         self.N = int(case["n_nodes"])
@@ -266,7 +266,9 @@ class Network:
         self.G, self.D, self.B = len(self.gen_node), len(self.load_node), len(self.stor_node)
         self.outaged = np.asarray(case["outaged"], np.int64)
         self.K = len(self.outaged)
-        self.Kp = self.K + 1
+        # contingencies held here: all of 0..K, or a shard of them (k_ids)
+        self.k_ids = np.arange(self.K + 1) if k_ids is None else np.asarray(k_ids, np.int64)
+        self.Kp = len(self.k_ids)
         L, G, D, B = self.L, self.G, self.D, self.B
         self.sl_t1 = slice(0, L)
         self.sl_t2 = slice(L, 2 * L)
@@ -287,9 +289,9 @@ class Network:
         # contingency k: line outaged[k-1] has u = b = 0 (Section 2.3, N-1
         # example); an index of -1 keeps the base-case parameters
         self.active = np.ones((self.Kp, L), bool)
-        for k, l in enumerate(self.outaged):
-            if l >= 0:
-                self.active[k + 1, l] = False
+        for i, k in enumerate(self.k_ids):
+            if k > 0 and self.outaged[k - 1] >= 0:
+                self.active[i, self.outaged[k - 1]] = False
         self.line_b = np.asarray(case["line_b"], float)
         self.line_u = np.asarray(case["line_u"], float)
         self.gen_a = np.asarray(case["gen_a"], float)
@@ -338,12 +340,31 @@ def residual(net, z, phase=False):
 # the iteration
 # ---------------------------------------------------------------------------
 
+class Shard:
+    """A slice of the contingencies for one of several cooperating processes.
+
+    ``k_ids`` are the global contingency indices held locally and
+    ``allreduce(x)`` returns the elementwise sum of ``x`` over all processes.
+    The only quantities that couple contingencies are the sums over ``k``
+    feeding the non-contingency proxes (Section 3.2) and the residual norms
+    (Section 3.3), so those are the two places that call it.
+    """
+
+    def __init__(self, k_ids, K, allreduce):
+        self.k_ids = np.asarray(k_ids, np.int64)
+        self.Kp_total = K + 1
+        self.allreduce = allreduce
+
+
 class Oracle:
     """Proximal message passing (Section 3.2) with residuals (Section 3.3) and
-    the adaptive penalty (Section 3.5), over all contingencies and time steps."""
+    the adaptive penalty (Section 3.5), over all contingencies and time steps
+    (or over a ``Shard`` of the contingencies)."""
 
-    def __init__(self, case, opts=None):
-        self.net = Network(case)
+    def __init__(self, case, opts=None, shard=None):
+        self.shard = shard
+        self.net = Network(case, None if shard is None else shard.k_ids)
+        self.Kp_total = self.net.Kp if shard is None else shard.Kp_total
         self.opts = opts or OracleOptions()
         net = self.net
         Kp, J, N, T, L = net.Kp, net.J, net.N, net.T, net.L
@@ -386,7 +407,7 @@ class Oracle:
 
     # -- cached inner factorizations (Appendix D: reused while rho, omega fixed)
     def _factor(self):
-        rho = self.net.Kp * self.rho_p
+        rho = self.Kp_total * self.rho_p
         if self._factored_rho == rho:
             return
         net, T = self.net, self.net.T
@@ -460,7 +481,10 @@ class Oracle:
 
     def prices(self):
         """Nodal prices ``-rho_p sum_k u_k`` (stationarity of step 2 at a fixed point)."""
-        return -self.rho_p * self.u.sum(axis=0)
+        s = self.u.sum(axis=0)
+        if self.shard is not None:
+            s = self.shard.allreduce(s)
+        return -self.rho_p * s
 
     def objective(self):
         """Sum of device costs at the current iterate (line costs are indicators)."""
@@ -506,8 +530,8 @@ class Oracle:
         # step 2: non-contingency devices, one schedule shared by all k:
         # prox with weight (K+1) rho_p at p_d - avg_k(pbar_kd + u_kd)
         sd = net.sl_dev
-        X = p[0, sd] - np.mean(pbar[:, sd] + uj[:, sd], axis=0)
-        rho_d = Kp * rp
+        X = p[0, sd] - self._kmean(pbar[:, sd] + uj[:, sd])
+        rho_d = self.Kp_total * rp
         self._factor()
         pd = np.empty_like(X)
         G, D, B = net.G, net.D, net.B
@@ -553,10 +577,10 @@ class Oracle:
         v_new = v + (th_new - thbar_new)
 
         # residuals (Section 3.3), with the penalties used in this iteration
-        r_pp = np.linalg.norm(pbar_new)
-        r_pt = np.linalg.norm(th_new - thbar_new)
-        r_dp = rp * np.linalg.norm((p_new - pbar_new) - ptil_old)
-        r_dt = rt * np.linalg.norm(thbar_new - thbar_old)
+        r_pp = self._norm(pbar_new)
+        r_pt = self._norm(th_new - thbar_new)
+        r_dp = rp * self._norm((p_new - pbar_new) - ptil_old)
+        r_dt = rt * self._norm(thbar_new - thbar_old)
         self.res = np.array([np.hypot(r_pp, r_pt), np.hypot(r_dp, r_dt), r_pp, r_pt, r_dp, r_dt])
 
         self.p, self.th, self.u, self.v = p_new, th_new, u_new, v_new
@@ -565,6 +589,19 @@ class Oracle:
         # adaptive penalty (Section 3.5), every adapt_every iterations
         if o.adapt_every and self.it % o.adapt_every == 0:
             self._adapt(r_pp, r_pt, r_dp, r_dt)
+
+    # -- the two couplings across contingencies (reduced over a shard's peers)
+    def _kmean(self, a):
+        """``(1/(K+1)) sum_k a_k`` over all contingencies."""
+        if self.shard is None:
+            return np.mean(a, axis=0)
+        return self.shard.allreduce(np.sum(a, axis=0)) / self.Kp_total
+
+    def _norm(self, x):
+        """Euclidean norm over all contingencies."""
+        if self.shard is None:
+            return np.linalg.norm(x)
+        return float(np.sqrt(self.shard.allreduce(np.array([np.sum(x * x)]))[0]))
 
     def _adapt(self, r_pp, r_pt, r_dp, r_dt):
         o = self.opts
@@ -595,7 +632,7 @@ class Oracle:
     def tolerance(self):
         """Right-hand side of Eq. (converge): ``eps sqrt(2 J T (K+1))``."""
         n = self.net
-        return self.opts.eps * np.sqrt(2.0 * n.J * n.T * n.Kp)
+        return self.opts.eps * np.sqrt(2.0 * n.J * n.T * self.Kp_total)
 
     def iterate(self, n_iters, stop=True):
         """Run up to ``n_iters`` iterations; with ``stop`` the Eq. (converge) test

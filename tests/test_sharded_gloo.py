@@ -1,0 +1,86 @@
+"""Contingency sharding over two processes (gloo, CPU).
+
+The iteration couples contingencies only through the sums over k that feed
+the non-contingency proxes (Section 3.2) and through the residual norms
+(Section 3.3).  Two ranks each hold half of the contingencies, all-reduce
+exactly those quantities, and must reproduce the single-process iteration:
+the same states (to FP64 rounding of the split sums), residuals and
+penalty decisions.  This is the exchange a contingency-sharded multi-GPU
+run performs once per iteration.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from gridgen import make_case, scale_case
+
+
+def _case():
+    return make_case(scale_case(60, 6, 5, seed=31))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir, n_iter):
+    import torch
+    import torch.distributed as dist
+    from oracle import Oracle, OracleOptions, Shard
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        case = _case()
+        K = len(case["outaged"])
+        k_ids = np.array_split(np.arange(K + 1), world)[rank]
+
+        def allreduce(x):
+            t = torch.from_numpy(np.ascontiguousarray(x, np.float64)).clone()
+            dist.all_reduce(t)
+            return t.numpy()
+
+        o = Oracle(case, OracleOptions(adapt_every=10, eps=0.0), shard=Shard(k_ids, K, allreduce))
+        res = []
+        for _ in range(n_iter):
+            o.step()
+            res.append(o.res.copy())
+        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), k_ids=k_ids, p=o.p, th=o.th, u=o.u, v=o.v,
+                 res=np.array(res), rho=np.array([o.rho_p, o.rho_th]),
+                 hist=np.array(o.rho_history, float), prices=o.prices())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_contingency_shards_reproduce_the_iteration(tmp_path):
+    import torch.multiprocessing as mp
+    from oracle import Oracle, OracleOptions
+
+    n_iter = 30
+    port = _free_port()
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path), n_iter), nprocs=2, join=True,
+                       start_method="spawn")
+    parts = [np.load(tmp_path / f"rank{r}.npz") for r in range(2)]
+
+    ref = Oracle(_case(), OracleOptions(adapt_every=10, eps=0.0))
+    res = []
+    for _ in range(n_iter):
+        ref.step()
+        res.append(ref.res.copy())
+    res = np.array(res)
+
+    for name in ("p", "th", "u", "v"):
+        full = getattr(ref, name)
+        got = np.concatenate([q[name] for q in parts], axis=0)
+        assert got.shape == full.shape
+        np.testing.assert_allclose(got, full, rtol=1e-10, atol=1e-12 * np.abs(full).max(), err_msg=name)
+    for q in parts:
+        np.testing.assert_allclose(q["res"], res, rtol=1e-10)
+        assert q["rho"].tolist() == [ref.rho_p, ref.rho_th]
+        assert q["hist"].tolist() == [list(h) for h in ref.rho_history]
+        np.testing.assert_allclose(q["prices"], ref.prices(), rtol=1e-10, atol=1e-12)
+    assert np.concatenate([q["k_ids"] for q in parts]).tolist() == list(range(ref.net.Kp))
