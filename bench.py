@@ -35,7 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "ADMM iterations/s"
 UNIT = "iter/s"
 WORKLOAD = "dcopf-10k-bus-T96-K50"
-KERNEL_SRC = os.path.join(ROOT, "paper_2410_17203_gb300", "csrc", "opf_kernels.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2410_17203_gb300", "csrc", f)
+              for f in ("opf_kernels.cu", "opf_internal.h")]
 PROFILE = os.path.join(ROOT, "profiles", "iteration_kernel_10k.txt")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -62,8 +63,11 @@ def peak_hbm():
 
 
 def kernel_hash():
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for p in KERNEL_SRC:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic():

@@ -65,6 +65,11 @@ CONFIGS = {
     # 10,000 buses, 15,000 lines, T=96 (four days, daily period 24), 50 outages.
     "10k": dict(n_nodes=10000, n_lines=15000, n_gens=2500, n_loads=7500, n_stor=500, T=96,
                 K=50, seed=2, topology="geometric", fixed_frac=0.0, ramp=True),
+    # the 10k network with 12 outages: per-contingency work of the 10k
+    # instance at a quarter of its state (~1.1 GB, still far above L2), the
+    # size on which kernel counters are captured
+    "10k-K12": dict(n_nodes=10000, n_lines=15000, n_gens=2500, n_loads=7500, n_stor=500, T=96,
+                    K=12, seed=2, topology="geometric", fixed_frac=0.0, ramp=True),
 }
 
 
