@@ -63,7 +63,7 @@ struct opf_ctx {
   cudaStream_t stream = nullptr;
   opf_options opt{};
   int N = 0, L = 0, T = 0, K = 0, Kp = 0, S = 0, G = 0, D = 0, B = 0;
-  int n_closed = 0, n_cnode = 0, n_ramp = 0, n_stor = 0;
+  int n_closed = 0, n_dnode = 0, n_ramp = 0, n_stor = 0;
   size_t n_tcode = 0;  // padded terminal-code list length
   float *price_scratch = nullptr;  // this device's fixed price staging array
   int grid = 0;
@@ -283,9 +283,10 @@ void carve(opf_ctx *c, Arena &a) {
   p.tcode = a.take<int>(c->n_tcode);
   p.dev_node = a.take<int>(c->S);
   p.dev_type = a.take<int>(c->S);
-  p.cnode_ids = a.take<int>(c->n_cnode);
-  p.cnode_ptr = a.take<int>(c->n_cnode + 1);
-  p.cnode_dev = a.take<int>(c->n_closed);
+  p.dnode_ids = a.take<int>(c->n_dnode);
+  p.dnode_ptr = a.take<int>(c->n_dnode + 1);
+  p.dnode_dev = a.take<int>(c->n_closed);
+  p.dnode_keep = a.take<int>(c->n_dnode);
   p.dev_a = a.take<float>(c->S);
   p.dev_b = a.take<float>(c->S);
   p.dev_lo = a.take<float>(ST);
@@ -300,9 +301,11 @@ void carve(opf_ctx *c, Arena &a) {
   p.node_perm = a.take<int>(c->N);
   p.line_perm = a.take<int>(c->L);
   // scratch
+  p.XS = a.take<float>((size_t)c->N * T);
   p.partials = a.take<double>((size_t)2 * c->grid * opfk::NSLOT);
-  // barrier count, generation, error word, pad, then two 64-bit work counters
-  p.bar_count = a.take<unsigned>(8);
+  // barrier count, generation, error word, pad, then four 64-bit work
+  // counters (line items and device items, by iteration parity)
+  p.bar_count = a.take<unsigned>(opfk::SYNC_WORDS);
   p.bar_gen = p.bar_count ? p.bar_count + 1 : nullptr;
   p.err = p.bar_count ? reinterpret_cast<int *>(p.bar_count + 2) : nullptr;
   p.work = p.bar_count ? reinterpret_cast<unsigned long long *>(p.bar_count + 4) : nullptr;
@@ -491,20 +494,22 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
     sdur.push_back((float)net->stor_dur[b]);
     scost.push_back((float)net->stor_cost[b]);
   }
-  // closed-form devices grouped by internal node (phase D sums pbar + u over
-  // k once per node)
-  std::vector<int> cnode_ids, cnode_ptr(1, 0), cnode_dev;
+  // nodes with devices (avg_k(pbar + u) is formed once per node), their
+  // closed-form devices, and whether inner-ADMM devices need the average
+  std::vector<int> dnode_ids, dnode_ptr(1, 0), dnode_dev, dnode_keep;
   for (int n = 0; n < N; ++n) {
-    const size_t before = cnode_dev.size();
-    for (int j = dptr[n]; j < dptr[n + 1]; ++j)
-      if (dev_type[didx[j]] == 0) cnode_dev.push_back(didx[j]);
-    if (cnode_dev.size() > before) {
-      cnode_ids.push_back(n);
-      cnode_ptr.push_back((int)cnode_dev.size());
+    if (dptr[n + 1] == dptr[n]) continue;
+    int keep = 0;
+    for (int j = dptr[n]; j < dptr[n + 1]; ++j) {
+      if (dev_type[didx[j]] == 0) dnode_dev.push_back(didx[j]);
+      else keep = 1;
     }
+    dnode_ids.push_back(n);
+    dnode_ptr.push_back((int)dnode_dev.size());
+    dnode_keep.push_back(keep);
   }
-  c->n_closed = (int)cnode_dev.size();
-  c->n_cnode = (int)cnode_ids.size();
+  c->n_closed = (int)dnode_dev.size();
+  c->n_dnode = (int)dnode_ids.size();
   c->n_ramp = (int)ramp.size();
   c->n_stor = (int)stor.size();
 
@@ -558,7 +563,7 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   p.T = T;
   p.Kp = c->Kp;
   p.S = S;
-  p.n_cnode = c->n_cnode;
+  p.n_dnode = c->n_dnode;
   p.n_ramp = c->n_ramp;
   p.n_stor = c->n_stor;
   p.eps = opt.eps;
@@ -614,9 +619,10 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   up(p.tcode, tcode);
   up(p.dev_node, dev_node_int);
   up(p.dev_type, dev_type);
-  up(p.cnode_ids, cnode_ids);
-  up(p.cnode_ptr, cnode_ptr);
-  up(p.cnode_dev, cnode_dev);
+  up(p.dnode_ids, dnode_ids);
+  up(p.dnode_ptr, dnode_ptr);
+  up(p.dnode_dev, dnode_dev);
+  up(p.dnode_keep, dnode_keep);
   up(p.dev_a, dev_a);
   up(p.dev_b, dev_b);
   up(p.dev_lo, lo);
@@ -659,7 +665,7 @@ opf_status opf_iterate(opf_ctx *c, int32_t n_iters, double rho) {
     if (opfk_set_rho_launch(c->P.sc, rho, c->stream) != 0) return fail(OPF_ECUDA, "set_rho launch failed");
   }
   if (n_iters == 0) return OPF_OK;
-  CK(cudaMemsetAsync(c->P.bar_count, 0, 8 * sizeof(unsigned), c->stream));
+  CK(cudaMemsetAsync(c->P.bar_count, 0, opfk::SYNC_WORDS * sizeof(unsigned), c->stream));
   Params p = c->P;
   p.n_iters = n_iters;
   char msg[256];

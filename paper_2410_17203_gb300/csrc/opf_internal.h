@@ -29,6 +29,9 @@ namespace opfk {
 
 // threads per CTA of the persistent iteration kernel
 constexpr int BLOCK = 256;
+// 32-bit words of grid-synchronisation state (barrier count and generation,
+// error word, pad, eight 64-bit work counters), zeroed before each launch
+constexpr int SYNC_WORDS = 20;
 
 // residual partial-sum slots.  SL_NF counts non-finite node values: the prox
 // clamps (fminf/fmaxf) would otherwise turn a NaN input into a finite bound.
@@ -54,7 +57,7 @@ enum { RG_UP = 0, RG_LO = 1, RG_RU = 2, RG_RD = 3, RG_N = 4 };
 
 struct Params {
   int N, L, T, Kp, S;
-  int n_cnode, n_ramp, n_stor;
+  int n_dnode, n_ramp, n_stor;
   // lines (internal numbering)
   const int *line_n1, *line_n2;  // internal node of terminal 1 (from) and terminal 2 (to)
   const float *line_b, *line_u;
@@ -75,8 +78,10 @@ struct Params {
   // devices: type 0 = closed-form prox clip((rho X - b)/(2a + rho), lo, hi), 1 = inner ADMM
   float *PD, *DPD;
   const int *dev_node, *dev_type;
-  // nodes with closed-form devices, and those devices per node
-  const int *cnode_ids, *cnode_ptr, *cnode_dev;
+  // nodes with devices; per node its closed-form devices and whether it has
+  // inner-ADMM devices, whose input avg_k(pbar + u) is then kept in XS
+  const int *dnode_ids, *dnode_ptr, *dnode_dev, *dnode_keep;
+  float *XS;  // [N][T], avg_k(pbar + u) of the previous iterate at kept nodes
   const float *dev_a, *dev_b;
   const float *dev_lo, *dev_hi;  // [S][T]
   // ramp-limited generators
@@ -93,7 +98,8 @@ struct Params {
   double *partials;  // [2][grid][NSLOT]
   unsigned *bar_count, *bar_gen;
   int *err;
-  unsigned long long *work;  // [2] phase-N work counters, by iteration parity
+  unsigned long long *work;  // [8] counters by iteration parity: line items, inner devices,
+                             // node averages taken, node averages done
   DevScalars *sc;
   // options
   double eps, mu, gamma, tol;

@@ -34,7 +34,8 @@
 namespace opfk {
 
 constexpr int WARPS = BLOCK / 32;
-constexpr int LGRAB = 8;         // 32-item groups of line items a warp takes per counter access
+constexpr int LGRAB = 8;
+constexpr int DEV_WARPS = 2;     // warps per CTA that take device proxes before lines         // 32-item groups of line items a warp takes per counter access
 constexpr int ST_TIMEOUT = 4;    // opf_status values used on the device
 constexpr int ST_NONFINITE = 5;
 
@@ -185,6 +186,42 @@ __device__ __forceinline__ void ksum(const float *pbar_o, const float *u_o, size
   sq = ((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + (b[6] + b[7]));
 }
 
+// The same sums for four consecutive time steps (o 16-byte aligned): one
+// 128-bit load per row, two rows of each array in flight per step.
+__device__ __forceinline__ void ksum4(const float *pbar_o, const float *u_o, size_t o, size_t stride, int Kp,
+                                      float4 &sp, float4 &sq) {
+  float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+  int k = 0;
+  for (; k + 2 <= Kp; k += 2) {
+    const float4 x0 = *reinterpret_cast<const float4 *>(pbar_o + (size_t)k * stride + o);
+    const float4 x1 = *reinterpret_cast<const float4 *>(pbar_o + (size_t)(k + 1) * stride + o);
+    const float4 y0 = *reinterpret_cast<const float4 *>(u_o + (size_t)k * stride + o);
+    const float4 y1 = *reinterpret_cast<const float4 *>(u_o + (size_t)(k + 1) * stride + o);
+    a0.x += x0.x; a0.y += x0.y; a0.z += x0.z; a0.w += x0.w;
+    a1.x += x1.x; a1.y += x1.y; a1.z += x1.z; a1.w += x1.w;
+    b0.x += y0.x; b0.y += y0.y; b0.z += y0.z; b0.w += y0.w;
+    b1.x += y1.x; b1.y += y1.y; b1.z += y1.z; b1.w += y1.w;
+  }
+  if (k < Kp) {
+    const float4 x = *reinterpret_cast<const float4 *>(pbar_o + (size_t)k * stride + o);
+    const float4 y = *reinterpret_cast<const float4 *>(u_o + (size_t)k * stride + o);
+    a0.x += x.x; a0.y += x.y; a0.z += x.z; a0.w += x.w;
+    b0.x += y.x; b0.y += y.y; b0.z += y.z; b0.w += y.w;
+  }
+  sp = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+  sq = make_float4(b0.x + b1.x, b0.y + b1.y, b0.z + b1.z, b0.w + b1.w);
+}
+
+// X[t] = p_d[t] - avg_k(pbar + u) at the device's node n, t in [0, T), by
+// one warp (Section 3.2 step 2 input); the average was formed this iteration
+// by the node-average items into XS
+__device__ __forceinline__ void device_x(const Params &p, int n, const float *pd, float *X, int lane) {
+  const int T = p.T;
+  const float *xs = p.XS + (size_t)n * T;
+  for (int t = lane; t < T; t += 32) X[t] = pd[t] - __ldcg(xs + t);
+  __syncwarp();
+}
+
 // The warp's inner-ADMM state (lam, beta) lives in shared memory during the
 // inner iterations when it fits (lam_sh != nullptr), else in global memory.
 __device__ __forceinline__ void stage_in(float *&lam, float *&bet, float *lam_sh, int n, int lane) {
@@ -213,8 +250,7 @@ __device__ __forceinline__ void stage_out(float *lam_g, float *bet_g, const floa
 // Rows: p_t <= pmax_t, -p_t <= -pmin_t, p_{t+1} - p_t <= R, p_t - p_{t+1} <= R.
 // x-update matrix (2a + rho + 2 omega) I + 2 omega D'D is tridiagonal.
 // ---------------------------------------------------------------------------
-__device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf,
-                          const float *pbar_o, const float *u_o, float *sm, float *state_sh, int lane) {
+__device__ void ramp_prox(const Params &p, int r, float rho, float *sm, float *state_sh, int lane) {
   const int T = p.T;
   const int d = p.ramp_ids[r];
   const int n = p.dev_node[d];
@@ -241,12 +277,7 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf
     }
     __syncwarp();
   }
-  for (int t = lane; t < T; t += 32) {
-    float sp, sq;
-    ksum(pbar_o, u_o, (size_t)n * T + t, (size_t)p.N * T, p.Kp, sp, sq);
-    X[t] = pd[t] - (sp + su * sq) / kpf;   // p_d - avg_k(pbar + u)
-  }
-  __syncwarp();
+  device_x(p, n, pd, X, lane);   // p_d - avg_k(pbar + u)
   for (int itn = 0; itn < p.inner_iters; ++itn) {
     for (int t = lane; t < T - 1; t += 32)
       W[t] = (bet[RG_RU * T + t] - lam[RG_RU * T + t]) - (bet[RG_RD * T + t] - lam[RG_RD * T + t]);
@@ -300,8 +331,7 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float su, float kpf
 // (c_t, delta_t) per step (a 2x2 Schur complement), leaving a tridiagonal
 // system of size T + 1 in the state of charge s.
 // ---------------------------------------------------------------------------
-__device__ void stor_prox(const Params &p, int sidx, float rho, float su, float kpf,
-                          const float *pbar_o, const float *u_o, float *sm, float *state_sh, int lane) {
+__device__ void stor_prox(const Params &p, int sidx, float rho, float *sm, float *state_sh, int lane) {
   const int T = p.T, Tp = T + 1;
   const int d = p.stor_ids[sidx];
   const int n = p.dev_node[d];
@@ -336,12 +366,7 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float su, float 
     }
     __syncwarp();
   }
-  for (int t = lane; t < T; t += 32) {
-    float sp, sq;
-    ksum(pbar_o, u_o, (size_t)n * T + t, (size_t)p.N * T, p.Kp, sp, sq);
-    X[t] = pd[t] - (sp + su * sq) / kpf;   // p_d - avg_k(pbar + u)
-  }
-  __syncwarp();
+  device_x(p, n, pd, X, lane);   // p_d - avg_k(pbar + u)
 #define LAM(g, t) lam[(g) * Tp + (t)]
 #define BET(g, t) bet[(g) * Tp + (t)]
   for (int itn = 0; itn < p.inner_iters; ++itn) {
@@ -675,7 +700,6 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
 
   const int T = p.T, Kp = p.Kp, L = p.L, N = p.N, TV = T / VW;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gwarp = blockIdx.x * WARPS + wib, nwarp = gridDim.x * WARPS;
   const long long gthr = (long long)blockIdx.x * BLOCK + threadIdx.x;
   const long long nthr = (long long)gridDim.x * BLOCK;
   // per warp: 3 (T+1) work floats, then the inner-ADMM state if it fits
@@ -692,7 +716,6 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
   int v_fresh = sc0.v_fresh, converged = sc0.converged, status = 0;
   const float kpf = (float)Kp;
   const int n_inner = p.n_stor + p.n_ramp;
-  const long long n_cnode_items = (long long)p.n_cnode * T;
   const int line_per_k = L * TV;
 
   // a sticky device error (timeout, non-finite) leaves the state as it is
@@ -713,37 +736,88 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
     float acc[NSLOT] = {0.f, 0.f, 0.f, 0.f, 0.f};
 
     // ------- phase 1: steps 1 and 2, both from the previous iterate -------
-    // Device proxes first (the inner-ADMM warps are latency-bound), then the
-    // line proxes, taken in contingency-major order from a counter so that
-    // warps that had devices take fewer lines.
-    for (int w = gwarp; w < n_inner; w += nwarp) {
-      if (w < p.n_stor)
-        stor_prox(p, w, rho_dev, fsu, kpf, Bo, Uo, wsm, state_sh, lane);
-      else
-        ramp_prox(p, w - p.n_stor, rho_dev, fsu, kpf, Bo, Uo, wsm, state_sh, lane);
-    }
+    // (a) every warp: avg_k(pbar + u) at each node with devices, in chunks of
+    // 32 (node, VW time steps) items; the node's closed-form devices are
+    // updated on the spot (Section 4.2), and nodes with inner-ADMM devices
+    // keep the average in XS.
     {
       const float rkp = __frcp_rn(kpf);
-      Idx3 ix, dx;
-      ix.set((unsigned)gthr, 1 << 30, T);
-      dx.set((unsigned)nthr, 1 << 30, T);
-      for (unsigned item = (unsigned)gthr; item < (unsigned)n_cnode_items; item += (unsigned)nthr,
-                    ix.step(dx, 1 << 30, T)) {
-        const int ci = ix.b, t = ix.c;
-        const size_t on = (size_t)p.cnode_ids[ci] * T + t;
-        float sp, sq;
-        ksum(Bo, Uo, on, NT, Kp, sp, sq);          // sum_k pbar and sum_k u at the node
-        const float xs = div_rn(sp + fsu * sq, kpf, rkp);   // avg_k(pbar + u)
-        for (int j = p.cnode_ptr[ci]; j < p.cnode_ptr[ci + 1]; ++j) {
-          const int d = p.cnode_dev[j];
-          const size_t od = (size_t)d * T + t;
-          const float pd = p.PD[od];
-          const float x = pd - xs;                  // p_d - avg_k(pbar + u)
-          const float den = 2.f * p.dev_a[d] + rho_dev;
-          const float pn = fminf(fmaxf(div_rn(rho_dev * x - p.dev_b[d], den, __frcp_rn(den)), p.dev_lo[od]),
-                                 p.dev_hi[od]);
-          p.DPD[od] = pn - pd;
-          p.PD[od] = pn;
+      const unsigned n_xv = (unsigned)p.n_dnode * (unsigned)TV;
+      const unsigned n_xc = (n_xv + 31u) / 32u;
+      unsigned long long *xctr = p.work + 4 + (itn & 1), *xdone = p.work + 6 + (itn & 1);
+      for (;;) {
+        unsigned c = 0;
+        if (lane == 0) c = (unsigned)atomicAdd(xctr, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= n_xc) break;
+        const unsigned item = c * 32u + (unsigned)lane;
+        if (item < n_xv) {
+          const int ci = (int)(item / (unsigned)TV), t0 = (int)(item % (unsigned)TV) * VW;
+          const int nd = p.dnode_ids[ci];
+          const size_t on = (size_t)nd * T + t0;
+          FV<VW> xs;
+          if constexpr (VW == 4) {
+            float4 sp, sq;
+            ksum4(Bo, Uo, on, NT, Kp, sp, sq);                  // sum_k pbar, sum_k u at the node
+            xs.v[0] = div_rn(sp.x + fsu * sq.x, kpf, rkp);     // avg_k(pbar + u)
+            xs.v[1] = div_rn(sp.y + fsu * sq.y, kpf, rkp);
+            xs.v[2] = div_rn(sp.z + fsu * sq.z, kpf, rkp);
+            xs.v[3] = div_rn(sp.w + fsu * sq.w, kpf, rkp);
+          } else {
+            float sp, sq;
+            ksum(Bo, Uo, on, NT, Kp, sp, sq);
+            xs.v[0] = div_rn(sp + fsu * sq, kpf, rkp);
+          }
+          if (p.dnode_keep[ci]) stv<VW>(p.XS + on, xs);
+          for (int j = p.dnode_ptr[ci]; j < p.dnode_ptr[ci + 1]; ++j) {
+            const int d = p.dnode_dev[j];
+            const size_t od = (size_t)d * T + t0;
+            const float den = 2.f * p.dev_a[d] + rho_dev, rden = __frcp_rn(den), bd = p.dev_b[d];
+            const FV<VW> pd = ldv<VW>(p.PD + od), lo = ldv<VW>(p.dev_lo + od), hi = ldv<VW>(p.dev_hi + od);
+            FV<VW> pn, dp;
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+              const float x = pd.v[e] - xs.v[e];               // p_d - avg_k(pbar + u)
+              pn.v[e] = fminf(fmaxf(div_rn(rho_dev * x - bd, den, rden), lo.v[e]), hi.v[e]);
+              dp.v[e] = pn.v[e] - pd.v[e];
+            }
+            stv<VW>(p.DPD + od, dp);
+            stv<VW>(p.PD + od, pn);
+          }
+        }
+        // every lane's XS and device rows visible before the chunk counts as done
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(xdone, 1ull);
+      }
+      // (b) DEV_WARPS warps per CTA: inner-ADMM proxes (Appendix D) of
+      // batteries, then ramp generators, from a counter, once every average
+      // is in XS; the other warps go straight to the line stream.
+      if (wib < DEV_WARPS && n_inner > 0) {
+        int ok = 1;
+        if (lane == 0) {
+          const long long t0c = clock64();
+          while (*(volatile unsigned long long *)xdone < (unsigned long long)n_xc) {
+            if (*(volatile int *)p.err || clock64() - t0c > p.barrier_budget) {
+              atomicCAS(p.err, 0, ST_TIMEOUT);
+              ok = 0;
+              break;
+            }
+            __nanosleep(64);
+          }
+          __threadfence();
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        unsigned long long *dctr = p.work + 2 + (itn & 1);
+        for (; ok;) {
+          unsigned w = 0;
+          if (lane == 0) w = (unsigned)atomicAdd(dctr, 1ull);
+          w = __shfl_sync(0xffffffffu, w, 0);
+          if (w >= (unsigned)n_inner) break;
+          if (w < (unsigned)p.n_stor)
+            stor_prox(p, (int)w, rho_dev, wsm, state_sh, lane);
+          else
+            ramp_prox(p, (int)w - p.n_stor, rho_dev, wsm, state_sh, lane);
         }
       }
     }
@@ -836,7 +910,9 @@ __global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
         sd[4] = rp; sd[5] = rd; sd[6] = r_pp; sd[7] = r_pt; sd[8] = r_dp; sd[9] = r_dt;
         // this iteration's work counter is next used two iterations on,
         // after at least one more grid barrier
-        if (blockIdx.x == 0) p.work[itn & 1] = 0ull;
+        if (blockIdx.x == 0) {
+          for (int q = 0; q < 4; ++q) p.work[2 * q + (itn & 1)] = 0ull;
+        }
         sd[2] = rho_p / nrp;   // pending rescale of u and v (Section 3.5)
         sd[3] = rho_th / nrt;
         sd[0] = nrp;
