@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define OPF_ABI_VERSION 1
+#define OPF_ABI_VERSION 2
 
 typedef struct opf_ctx opf_ctx; /* opaque, created by opf_create, freed by opf_destroy */
 
@@ -44,11 +44,11 @@ typedef enum {
   OPF_EINVAL = 1,     /* bad argument or inconsistent network data */
   OPF_ENOMEM = 2,     /* a host or device allocation failed */
   OPF_ECUDA = 3,      /* a CUDA runtime call failed (message in opf_last_error) */
-  OPF_ETIMEOUT = 4,   /* a grid-wide barrier of the iteration kernel ran out of its
-                         spin budget; the iterate is incomplete (see OPF_ESTATE) */
+  OPF_ETIMEOUT = 4,   /* a synchronizing call gave up waiting for the context's
+                         queued GPU work after opf_options.sync_timeout_ms; the
+                         work continues and a later call can wait again */
   OPF_ENONFINITE = 5, /* a residual became NaN or infinite; iteration stopped */
-  OPF_ESTATE = 6      /* the state is unusable after an earlier OPF_ETIMEOUT;
-                         call opf_reset or opf_set_state before iterating again */
+  OPF_ESTATE = 6      /* the call does not apply to the context in its state */
 } opf_status;
 
 /*
@@ -105,8 +105,8 @@ typedef struct {
   int32_t inner_iters;      /* Appendix D iterations per iterative prox (>= 1) */
   int32_t check_every;      /* stopping test cadence; 0 disables stopping */
   int32_t reserved0;
-  int64_t barrier_timeout_cycles; /* spin budget of one grid barrier in SM clock
-                                     cycles; <= 0 selects the default (~2e9) */
+  int64_t sync_timeout_ms;  /* longest wait of a synchronizing call for the
+                               context's GPU work (OPF_ETIMEOUT after it); 0 = no limit */
   void *cuda_stream;        /* cudaStream_t to enqueue on; NULL = default stream */
 } opf_options;
 
@@ -153,11 +153,19 @@ opf_status opf_create(const opf_network *net, int32_t horizon_T,
                       const opf_contingencies *ctg, const opf_options *opt,
                       opf_ctx **out);
 
-/* Enqueue up to n_iters message-passing iterations (Section 3.2) as one
- * persistent cooperative kernel launch.  rho > 0 first sets rho_p = rho_theta
- * = rho, rescaling the scaled duals (Section 3.5); rho <= 0 keeps the current
- * (possibly adapted) penalties.  Stops early after a passed stopping test.
- * Asynchronous: device errors surface at the next synchronizing call. */
+/* Enqueue up to n_iters message-passing iterations (Section 3.2).  Each
+ * iteration is five kernels (device averages and closed-form devices, inner
+ * ADMM devices, line proxes on a second stream, node sums with the residual
+ * partials, decisions), replayed from CUDA graphs of 1 and 16 iterations.
+ * rho > 0 first sets rho_p = rho_theta = rho, rescaling the scaled duals
+ * (Section 3.5); rho <= 0 keeps the current (possibly adapted) penalties.
+ * After a passed stopping test (or a non-finite residual) the remaining
+ * iterations of the call do nothing.  Asynchronous with respect to the
+ * caller's stream when stopping is disabled (eps <= 0 or check_every = 0);
+ * with stopping enabled the call keeps at most 128 iterations queued ahead of
+ * the GPU so that it can stop launching, and it returns OPF_ETIMEOUT if that
+ * wait exceeds sync_timeout_ms.  Device errors surface at the next
+ * synchronizing call. */
 opf_status opf_iterate(opf_ctx *ctx, int32_t n_iters, double rho);
 
 /* Residuals of the last iteration run (Section 3.3), FP64:

@@ -53,7 +53,7 @@ class opf_options(C.Structure):
         ("mu", C.c_double), ("gamma", C.c_double),
         ("adapt_every", C.c_int32), ("inner_iters", C.c_int32), ("check_every", C.c_int32),
         ("reserved0", C.c_int32),
-        ("barrier_timeout_cycles", C.c_int64),
+        ("sync_timeout_ms", C.c_int64),
         ("cuda_stream", C.c_void_p),
     ]
 

@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -42,6 +44,7 @@ opf_status cuda_fail(cudaError_t e, const char *what) {
   } while (0)
 
 constexpr int kMaxT = 2048;
+constexpr int kGraphIters = 16;  // iterations in the larger of the two iteration graphs
 
 // bump allocator over one cudaMalloc
 struct Arena {
@@ -66,7 +69,14 @@ struct opf_ctx {
   int n_closed = 0, n_dnode = 0, n_ramp = 0, n_stor = 0;
   size_t n_tcode = 0;  // padded terminal-code list length
   float *price_scratch = nullptr;  // this device's fixed price staging array
-  int grid = 0;
+  opfk::IterPlan plan{};
+  // iteration streams (main: devices, node sums, decisions; aux: line proxes),
+  // the events that fork and join them, and the events that order them after
+  // and before the caller's stream
+  cudaStream_t s_main = nullptr, s_aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr, ev_out = nullptr, ev_sync = nullptr;
+  // CUDA graphs of 1 and kGraphIters iterations, built on first use
+  cudaGraphExec_t g_one = nullptr, g_many = nullptr;
   char *arena = nullptr;
   size_t arena_bytes = 0;
   Params P{};
@@ -91,7 +101,7 @@ void opf_default_options(opf_options *o) {
   o->adapt_every = 10;
   o->inner_iters = 10;
   o->check_every = 10;
-  o->barrier_timeout_cycles = 0;
+  o->sync_timeout_ms = 0;
   o->cuda_stream = nullptr;
 }
 
@@ -101,9 +111,9 @@ const char *opf_status_str(opf_status s) {
     case OPF_EINVAL: return "invalid argument";
     case OPF_ENOMEM: return "out of memory";
     case OPF_ECUDA: return "CUDA error";
-    case OPF_ETIMEOUT: return "grid barrier timeout";
+    case OPF_ETIMEOUT: return "GPU work still running at the synchronization timeout";
     case OPF_ENONFINITE: return "non-finite residual";
-    case OPF_ESTATE: return "state unusable after an earlier device error";
+    case OPF_ESTATE: return "call does not apply to the context in its state";
   }
   return "unknown status";
 }
@@ -302,13 +312,7 @@ void carve(opf_ctx *c, Arena &a) {
   p.line_perm = a.take<int>(c->L);
   // scratch
   p.XS = a.take<float>((size_t)c->N * T);
-  p.partials = a.take<double>((size_t)2 * c->grid * opfk::NSLOT);
-  // barrier count, generation, error word, pad, then four 64-bit work
-  // counters (line items and device items, by iteration parity)
-  p.bar_count = a.take<unsigned>(opfk::SYNC_WORDS);
-  p.bar_gen = p.bar_count ? p.bar_count + 1 : nullptr;
-  p.err = p.bar_count ? reinterpret_cast<int *>(p.bar_count + 2) : nullptr;
-  p.work = p.bar_count ? reinterpret_cast<unsigned long long *>(p.bar_count + 4) : nullptr;
+  p.partials = a.take<double>((size_t)c->plan.node_grid * opfk::NSLOT);
 }
 
 opf_status init_scalars(opf_ctx *c) {
@@ -323,11 +327,64 @@ opf_status init_scalars(opf_ctx *c) {
   return OPF_OK;
 }
 
+// Wait until the work queued on the caller's stream (which includes the
+// iterations, joined back into it) is done: without limit, or for at most
+// sync_timeout_ms, after which OPF_ETIMEOUT reports work still running.
+opf_status wait_stream(opf_ctx *c) {
+  if (c->opt.sync_timeout_ms <= 0) {
+    CK(cudaStreamSynchronize(c->stream));
+    return OPF_OK;
+  }
+  CK(cudaEventRecord(c->ev_sync, c->stream));
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(c->ev_sync);
+    if (e == cudaSuccess) return OPF_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery");
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+    if (ms.count() >= c->opt.sync_timeout_ms) return fail(OPF_ETIMEOUT, "GPU work still running at sync_timeout_ms");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
 opf_status read_scalars(opf_ctx *c, DevScalars *sc) {
-  CK(cudaStreamSynchronize(c->stream));
+  opf_status s = wait_stream(c);
+  if (s != OPF_OK) return s;
   CK(cudaMemcpy(sc, c->P.sc, sizeof(*sc), cudaMemcpyDeviceToHost));
   if (sc->status) c->host_status = sc->status;
   return OPF_OK;
+}
+
+// The iteration as a CUDA graph of `iters` iterations, captured from the two
+// iteration streams.
+opf_status build_graph(opf_ctx *c, int iters, cudaGraphExec_t *out) {
+  CK(cudaStreamBeginCapture(c->s_main, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < iters; ++i) {
+    if (opfk_iteration_enqueue(c->P, c->plan, c->s_main, c->s_aux, c->ev_fork, c->ev_join) != 0) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(c->s_main, &g);
+      if (g) cudaGraphDestroy(g);
+      return fail(OPF_ECUDA, "iteration enqueue failed during graph capture");
+    }
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamEndCapture(c->s_main, &g));
+  // keep the stream priorities of the captured kernels (device work ahead of
+  // the line CTAs it runs beside)
+  const cudaError_t e = cudaGraphInstantiateWithFlags(out, g, cudaGraphInstantiateFlagUseNodePriority);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return OPF_OK;
+}
+
+void release_cuda(opf_ctx *c) {
+  if (c->g_one) cudaGraphExecDestroy(c->g_one);
+  if (c->g_many) cudaGraphExecDestroy(c->g_many);
+  for (cudaEvent_t ev : {c->ev_fork, c->ev_join, c->ev_in, c->ev_out, c->ev_sync})
+    if (ev) cudaEventDestroy(ev);
+  if (c->s_main) cudaStreamDestroy(c->s_main);
+  if (c->s_aux) cudaStreamDestroy(c->s_aux);
+  if (c->arena) cudaFree(c->arena);
 }
 
 // device scratch for exports to host memory (not on the iteration path)
@@ -371,7 +428,7 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   opf_options opt;
   opf_default_options(&opt);
   if (opt_in) opt = *opt_in;
-  if (opt.barrier_timeout_cycles <= 0) opt.barrier_timeout_cycles = 2000000000LL;
+  if (opt.sync_timeout_ms < 0) opt.sync_timeout_ms = 0;
   opf_status st = validate(net, T, ctg, opt);
   if (st != OPF_OK) return st;
 
@@ -532,9 +589,20 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
       return ps;
     }
   }
-  if (opfk_max_grid(T, &c->grid) != 0) {
-    delete c;
-    return fail(OPF_ECUDA, "occupancy query for the iteration kernel failed");
+  {
+    // launch configuration (the node kernel's grid sizes the partial sums)
+    Params q{};
+    q.N = N;
+    q.L = L;
+    q.T = T;
+    q.Kp = c->Kp;
+    q.n_dnode = c->n_dnode;
+    q.n_ramp = c->n_ramp;
+    q.n_stor = c->n_stor;
+    if (opfk_plan(q, &c->plan) != 0) {
+      delete c;
+      return fail(OPF_ECUDA, "occupancy query for the iteration kernels failed");
+    }
   }
   // terminal codes per node, padded to a multiple of 4
   std::vector<int> tcode, tptr(N + 1, 0);
@@ -556,6 +624,22 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   a = Arena();
   a.base = c->arena;
   carve(c, a);
+  {
+    // iteration streams: devices and node sums at the higher priority so that
+    // their CTAs are scheduled ahead of the concurrent line CTAs
+    int lo = 0, hi = 0;
+    cudaError_t ce = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&c->s_main, cudaStreamNonBlocking, hi);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&c->s_aux, cudaStreamNonBlocking, lo);
+    for (cudaEvent_t *ev : {&c->ev_fork, &c->ev_join, &c->ev_in, &c->ev_out, &c->ev_sync})
+      if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+      opf_status es = cuda_fail(ce, "stream / event creation");
+      release_cuda(c);
+      delete c;
+      return es;
+    }
+  }
 
   Params &p = c->P;
   p.N = N;
@@ -572,7 +656,6 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   p.adapt_every = opt.adapt_every;
   p.check_every = opt.check_every;
   p.inner_iters = opt.inner_iters;
-  p.barrier_budget = opt.barrier_timeout_cycles;
   c->tol = opt.eps * std::sqrt(2.0 * (2.0 * L + S) * T * c->Kp);
   p.tol = c->tol;
 
@@ -638,7 +721,7 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   up(p.line_perm, line_perm);
   if (s == OPF_OK) s = init_scalars(c);
   if (s != OPF_OK) {
-    cudaFree(c->arena);
+    release_cuda(c);
     delete c;
     return s;
   }
@@ -648,28 +731,33 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
 
 void opf_destroy(opf_ctx *c) {
   if (!c) return;
-  if (c->arena) {
-    cudaStreamSynchronize(c->stream);
-    cudaFree(c->arena);
-  }
+  cudaStreamSynchronize(c->stream);
+  if (c->s_main) cudaStreamSynchronize(c->s_main);
+  release_cuda(c);
   delete c;
 }
 
 opf_status opf_iterate(opf_ctx *c, int32_t n_iters, double rho) {
   if (!c) return fail(OPF_EINVAL, "ctx is NULL");
-  if (c->host_status == OPF_ETIMEOUT || c->host_status == OPF_ESTATE)
-    return fail(OPF_ESTATE, "state unusable after a barrier timeout; call opf_reset or opf_set_state");
   if (n_iters < 0) return fail(OPF_EINVAL, "n_iters must be >= 0");
-  if (rho > 0) {
-    if (!std::isfinite(rho)) return fail(OPF_EINVAL, "rho must be finite");
-    if (opfk_set_rho_launch(c->P.sc, rho, c->stream) != 0) return fail(OPF_ECUDA, "set_rho launch failed");
+  if (rho > 0 && !std::isfinite(rho)) return fail(OPF_EINVAL, "rho must be finite");
+  if (n_iters > 0 && !c->g_one) {
+    opf_status gs = build_graph(c, 1, &c->g_one);
+    if (gs == OPF_OK) gs = build_graph(c, kGraphIters, &c->g_many);
+    if (gs != OPF_OK) return gs;
   }
-  if (n_iters == 0) return OPF_OK;
-  CK(cudaMemsetAsync(c->P.bar_count, 0, opfk::SYNC_WORDS * sizeof(unsigned), c->stream));
-  Params p = c->P;
-  p.n_iters = n_iters;
-  char msg[256];
-  if (opfk_iteration_launch(p, c->stream, c->grid, msg, sizeof(msg)) != 0) return fail(OPF_ECUDA, msg);
+  // after the caller's earlier work on its stream ...
+  CK(cudaEventRecord(c->ev_in, c->stream));
+  CK(cudaStreamWaitEvent(c->s_main, c->ev_in, 0));
+  if (rho > 0 && opfk_set_rho_launch(c->P.sc, rho, c->s_main) != 0) return fail(OPF_ECUDA, "set_rho launch failed");
+  if (n_iters > 0) {
+    CK(cudaMemsetAsync(&c->P.sc->stop, 0, sizeof(int), c->s_main));
+    for (int i = 0; i < n_iters / kGraphIters; ++i) CK(cudaGraphLaunch(c->g_many, c->s_main));
+    for (int i = 0; i < n_iters % kGraphIters; ++i) CK(cudaGraphLaunch(c->g_one, c->s_main));
+  }
+  // ... and before its later work
+  CK(cudaEventRecord(c->ev_out, c->s_main));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_out, 0));
   return OPF_OK;
 }
 

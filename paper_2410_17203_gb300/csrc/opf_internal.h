@@ -23,15 +23,13 @@
 #ifndef OPF_INTERNAL_H_
 #define OPF_INTERNAL_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 namespace opfk {
 
-// threads per CTA of the persistent iteration kernel
+// threads per CTA of the iteration kernels
 constexpr int BLOCK = 256;
-// 32-bit words of grid-synchronisation state (barrier count and generation,
-// error word, pad, eight 64-bit work counters), zeroed before each launch
-constexpr int SYNC_WORDS = 20;
 
 // residual partial-sum slots.  SL_NF counts non-finite node values: the prox
 // clamps (fminf/fmaxf) would otherwise turn a NaN input into a finite bound.
@@ -46,7 +44,8 @@ struct DevScalars {
   int converged;
   int status;            // sticky opf_status from the device (0 = ok)
   int v_fresh;           // 1: V1/V2 already hold the current v (after import / reset)
-  int pad;
+  int stop;              // set by the decision kernel (passed stopping test, error);
+                         // cleared at the start of every opf_iterate call
 };
 
 // Battery group offsets inside lam/beta rows of stride Tp = T + 1.
@@ -95,25 +94,30 @@ struct Params {
   // numbering maps (internal -> caller) for import / export
   const int *node_perm, *line_perm;
   // scratch
-  double *partials;  // [2][grid][NSLOT]
-  unsigned *bar_count, *bar_gen;
-  int *err;
-  unsigned long long *work;  // [8] counters by iteration parity: line items, inner devices,
-                             // node averages taken, node averages done
+  double *partials;  // [node_grid][NSLOT] per-CTA residual partial sums of the node kernel
   DevScalars *sc;
   // options
   double eps, mu, gamma, tol;
   int adapt_every, check_every, inner_iters;
-  long long barrier_budget;
-  int n_iters;
+};
+
+// Launch configuration of one iteration's kernels.
+struct IterPlan {
+  int line_grid, node_grid, xs_grid, inner_grid;  // 0: the kernel has no work
+  size_t inner_smem;
 };
 
 }  // namespace opfk
 
 // Launch wrappers implemented in opf_kernels.cu (host callable).
 extern "C++" {
-int opfk_iteration_launch(const opfk::Params &p, void *stream, int grid, char *msg, int msglen);
-int opfk_max_grid(int T, int *grid);
+// Grids of the iteration kernels for this problem on the current device.
+int opfk_plan(const opfk::Params &p, opfk::IterPlan *plan);
+// Enqueue one iteration: xs, inner and node / decide on main_stream, the line
+// kernel on aux_stream between the two events (fork after the previous
+// iteration, join before the node kernel).  Works under stream capture.
+int opfk_iteration_enqueue(const opfk::Params &p, const opfk::IterPlan &plan, void *main_stream,
+                           void *aux_stream, void *ev_fork, void *ev_join);
 // State import / export between internal and caller numbering; `cur` selects
 // the node buffer holding the current state.
 int opfk_import_launch(const opfk::Params &p, int cur, const float *p_line, const float *th1,

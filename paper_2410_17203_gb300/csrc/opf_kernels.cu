@@ -1,26 +1,31 @@
 // Proximal message passing for contingency-constrained DC OPF -- sm_103a kernels.
 //
-// One cooperative persistent launch runs many iterations of the message-passing
-// form of ADMM (Section 3.2).  Each iteration has three phases separated by
-// grid-wide barriers with a bounded spin:
+// One iteration of the message-passing form of ADMM (Section 3.2) is five
+// kernels, replayed from a CUDA graph; each reads the iteration's scalars
+// (penalties, pending rescales, buffer parity) from the device, so the same
+// graph serves every iteration:
 //
-//   D  step 2, the devices shared by all contingencies: one thread per
-//      (node with generators or loads, time chunk) sums pbar + u over k and
-//      applies the closed-form prox with weight (K+1) rho_p to
-//      p_d - avg_k(pbar + u) for every such device at the node; one warp per
-//      ramp-limited generator or battery runs the inner ADMM of Appendix D,
-//      lanes over time steps, each x-update a tridiagonal solve done by a
-//      warp-wide scan;
-//   N  one item per (contingency k, node n, chunk of time steps), taken in
-//      contingency-major order.  The item evaluates the closed-form prox of
-//      every incident line (step 1) from the previous line and node values at
-//      both ends -- both ends compute the same prox, the lower-numbered end
-//      stores it -- and forms pbar, theta_bar and u += pbar (step 3) as plain
-//      register sums over the node's terminals (no atomics), with the residual
-//      partial sums of Section 3.3 (one-pass Welford sums for theta~ and for
-//      the change of p~);
-//   C  every CTA reduces the per-CTA partial sums in the same order (FP64) and
-//      takes the same stopping / adaptive-penalty decision (Section 3.5).
+//   xs     step 2 input: avg_k(pbar + u) at every node with devices (128-bit
+//          loads over the K+1 contingency rows), and the closed-form prox
+//          with weight (K+1) rho_p of the node's generators and loads;
+//   inner  step 2, one warp per ramp-limited generator or battery: the inner
+//          ADMM of Appendix D, lanes over time steps, each x-update a
+//          tridiagonal solve by warp-wide scans;
+//   line   step 1, one thread per (contingency, line, 4 time steps), the
+//          closed-form line prox from the previous line and node values at
+//          both ends (runs concurrently with xs and inner: it reads only the
+//          previous iterate);
+//   node   step 3, one thread per (contingency, node, 2 time steps): pbar,
+//          theta_bar and u += pbar as register sums over the node's terminals
+//          in CSR order (no atomics), with the residual partial sums of
+//          Section 3.3 (one-pass Welford sums for theta~ and the change of p~);
+//   decide one CTA reduces the per-CTA partial sums in FP64 in a fixed order,
+//          forms the residuals, and takes the stopping and adaptive-penalty
+//          decisions (Section 3.5).
+//
+// Splitting the phases lets each kernel run at its own register budget (the
+// line and node kernels at 32 warps per SM).  There is no spin-wait on the
+// device: ordering comes from kernel boundaries and graph edges.
 //
 // Memory layout, numbering and the deferred v update: opf_internal.h.
 #include <cuda_runtime.h>
@@ -34,48 +39,9 @@
 namespace opfk {
 
 constexpr int WARPS = BLOCK / 32;
-constexpr int LGRAB = 8;
-constexpr int DEV_WARPS = 2;     // warps per CTA that take device proxes before lines         // 32-item groups of line items a warp takes per counter access
-constexpr int ST_TIMEOUT = 4;    // opf_status values used on the device
-constexpr int ST_NONFINITE = 5;
-
-// ---------------------------------------------------------------------------
-// grid barrier with a bounded spin.  On timeout the CTA records ST_TIMEOUT in
-// *err and returns false; every CTA that sees *err set returns false too, so
-// the whole grid leaves the iteration loop and the kernel ends.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_barrier(const Params &p, int *s_flag) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    volatile unsigned *vgen = p.bar_gen;
-    volatile int *verr = p.err;
-    unsigned g = *vgen;
-    __threadfence();
-    unsigned arrived = atomicAdd(p.bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
-      *p.bar_count = 0;
-      __threadfence();
-      atomicAdd(p.bar_gen, 1u);
-    } else {
-      long long t0 = clock64();
-      while (*vgen == g) {
-        if (*verr) { ok = 0; break; }
-        if (clock64() - t0 > p.barrier_budget) {
-          atomicCAS(p.err, 0, ST_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(40);
-      }
-    }
-    __threadfence();
-    if (*verr) ok = 0;
-    *s_flag = ok;
-  }
-  __syncthreads();
-  return *s_flag != 0;
-}
+constexpr int ST_NONFINITE = 5;  // opf_status value set on the device
+constexpr int NODE_MIN_CTAS = 4; // resident CTAs per SM the node kernel is compiled for
+constexpr int LINE_IPT = 4;      // line items per thread (CTA-sized blocks of items)
 
 // shared floats per warp: 3 (T+1) for the inner-ADMM work arrays, plus room
 // for one device's (lam, beta) while the horizon is short enough
@@ -446,13 +412,12 @@ struct FV {
 template <int VW>
 __device__ __forceinline__ FV<VW> ldv(const float *p) {
   FV<VW> r;
-  if constexpr (VW == 8) {
-    const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
-    r.v[0] = a.x; r.v[1] = a.y; r.v[2] = a.z; r.v[3] = a.w;
-    r.v[4] = b.x; r.v[5] = b.y; r.v[6] = b.z; r.v[7] = b.w;
-  } else if constexpr (VW == 4) {
+  if constexpr (VW == 4) {
     const float4 t = *reinterpret_cast<const float4 *>(p);
     r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else if constexpr (VW == 2) {
+    const float2 t = *reinterpret_cast<const float2 *>(p);
+    r.v[0] = t.x; r.v[1] = t.y;
   } else {
     r.v[0] = *p;
   }
@@ -466,6 +431,9 @@ __device__ __forceinline__ FV<VW> ldv_cs(const float *p) {
   if constexpr (VW == 4) {
     const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
     r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else if constexpr (VW == 2) {
+    const float2 t = __ldcs(reinterpret_cast<const float2 *>(p));
+    r.v[0] = t.x; r.v[1] = t.y;
   } else {
     r.v[0] = __ldcs(p);
   }
@@ -474,11 +442,10 @@ __device__ __forceinline__ FV<VW> ldv_cs(const float *p) {
 
 template <int VW>
 __device__ __forceinline__ void stv(float *p, const FV<VW> &r) {
-  if constexpr (VW == 8) {
+  if constexpr (VW == 4) {
     *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
-    *reinterpret_cast<float4 *>(p + 4) = make_float4(r.v[4], r.v[5], r.v[6], r.v[7]);
-  } else if constexpr (VW == 4) {
-    *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  } else if constexpr (VW == 2) {
+    *reinterpret_cast<float2 *>(p) = make_float2(r.v[0], r.v[1]);
   } else {
     *p = r.v[0];
   }
@@ -487,11 +454,10 @@ __device__ __forceinline__ void stv(float *p, const FV<VW> &r) {
 // streaming store (not read again in this iteration: evict first)
 template <int VW>
 __device__ __forceinline__ void stv_cs(float *p, const FV<VW> &r) {
-  if constexpr (VW == 8) {
+  if constexpr (VW == 4) {
     __stcs(reinterpret_cast<float4 *>(p), make_float4(r.v[0], r.v[1], r.v[2], r.v[3]));
-    __stcs(reinterpret_cast<float4 *>(p + 4), make_float4(r.v[4], r.v[5], r.v[6], r.v[7]));
-  } else if constexpr (VW == 4) {
-    __stcs(reinterpret_cast<float4 *>(p), make_float4(r.v[0], r.v[1], r.v[2], r.v[3]));
+  } else if constexpr (VW == 2) {
+    __stcs(reinterpret_cast<float2 *>(p), make_float2(r.v[0], r.v[1]));
   } else {
     __stcs(p, r.v[0]);
   }
@@ -689,260 +655,229 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
 // ---------------------------------------------------------------------------
 // the persistent iteration kernel
 // ---------------------------------------------------------------------------
-template <int VW>
-__global__ void __launch_bounds__(BLOCK, 2) iteration_kernel(Params p) {
-  extern __shared__ float smem[];
-  __shared__ double red[WARPS][NSLOT];
-  __shared__ double sd[10];   // thread 0: rho_p, rho_th, su, sv, res[6]
-  __shared__ float sf[5];     // broadcast: rho_p, rho_th, su, sv, (K+1) rho_p
-  __shared__ int s_code;
-  __shared__ int s_flag;
+// ---------------------------------------------------------------------------
+// the scalars of the current iteration, read once per CTA.  A context that
+// stopped in this call (passed stopping test) or holds a sticky error makes
+// every kernel return at once.
+// ---------------------------------------------------------------------------
+struct Iter {
+  float frp, frt, fsu, fsv, rho_dev;
+  int old, nw, v_fresh, skip;
+};
 
-  const int T = p.T, Kp = p.Kp, L = p.L, N = p.N, TV = T / VW;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long gthr = (long long)blockIdx.x * BLOCK + threadIdx.x;
-  const long long nthr = (long long)gridDim.x * BLOCK;
-  // per warp: 3 (T+1) work floats, then the inner-ADMM state if it fits
-  const int wfl = warp_smem_floats(T);
-  float *wsm = smem + (size_t)wib * wfl;
-  float *state_sh = (wfl > 3 * (T + 1)) ? wsm + 3 * (T + 1) : nullptr;
-
-  const DevScalars sc0 = *p.sc;
+__device__ __forceinline__ Iter iter_scalars(const Params &p) {
+  __shared__ Iter s;
   if (threadIdx.x == 0) {
-    sd[0] = sc0.rho_p; sd[1] = sc0.rho_th; sd[2] = sc0.su; sd[3] = sc0.sv;
-    for (int j = 0; j < 6; ++j) sd[4 + j] = sc0.res[j];
+    const DevScalars sc = *p.sc;
+    Iter r;
+    r.frp = (float)sc.rho_p;
+    r.frt = (float)sc.rho_th;
+    r.fsu = (float)sc.su;
+    r.fsv = (float)sc.sv;
+    r.rho_dev = (float)(p.Kp * sc.rho_p);   // rho' = (K+1) rho_p
+    r.old = (int)(sc.it & 1);
+    r.nw = r.old ^ 1;
+    r.v_fresh = sc.v_fresh;
+    r.skip = (sc.status != 0 || sc.stop != 0) ? 1 : 0;
+    s = r;
   }
-  long long it = sc0.it;
-  int v_fresh = sc0.v_fresh, converged = sc0.converged, status = 0;
-  const float kpf = (float)Kp;
+  __syncthreads();
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// xs: avg_k(pbar + u) at each node with devices, one (node, VW time steps)
+// item per thread; the node's closed-form devices are updated on the spot
+// (Section 4.2), nodes with inner-ADMM devices keep the average in XS
+// ---------------------------------------------------------------------------
+template <int VW>
+__global__ void __launch_bounds__(BLOCK) xs_kernel(Params p) {
+  const Iter q = iter_scalars(p);
+  if (q.skip) return;
+  const int T = p.T, TV = T / VW, Kp = p.Kp;
+  const float kpf = (float)Kp, rkp = __frcp_rn(kpf);
+  const size_t NT = (size_t)p.N * T;
+  const float *Uo = p.U[q.old], *Bo = p.PBAR[q.old];
+  const unsigned n_xv = (unsigned)p.n_dnode * (unsigned)TV;
+  for (unsigned item = blockIdx.x * BLOCK + threadIdx.x; item < n_xv; item += gridDim.x * BLOCK) {
+    const int ci = (int)(item / (unsigned)TV), t0 = (int)(item % (unsigned)TV) * VW;
+    const size_t on = (size_t)p.dnode_ids[ci] * T + t0;
+    FV<VW> xs;
+    if constexpr (VW == 4) {
+      float4 sp, sq;
+      ksum4(Bo, Uo, on, NT, Kp, sp, sq);                  // sum_k pbar, sum_k u at the node
+      xs.v[0] = div_rn(sp.x + q.fsu * sq.x, kpf, rkp);   // avg_k(pbar + u)
+      xs.v[1] = div_rn(sp.y + q.fsu * sq.y, kpf, rkp);
+      xs.v[2] = div_rn(sp.z + q.fsu * sq.z, kpf, rkp);
+      xs.v[3] = div_rn(sp.w + q.fsu * sq.w, kpf, rkp);
+    } else {
+      float sp, sq;
+      ksum(Bo, Uo, on, NT, Kp, sp, sq);
+      xs.v[0] = div_rn(sp + q.fsu * sq, kpf, rkp);
+    }
+    if (p.dnode_keep[ci]) stv<VW>(p.XS + on, xs);
+    for (int j = p.dnode_ptr[ci]; j < p.dnode_ptr[ci + 1]; ++j) {
+      const int d = p.dnode_dev[j];
+      const size_t od = (size_t)d * T + t0;
+      const float den = 2.f * p.dev_a[d] + q.rho_dev, rden = __frcp_rn(den), bd = p.dev_b[d];
+      const FV<VW> pd = ldv<VW>(p.PD + od), lo = ldv<VW>(p.dev_lo + od), hi = ldv<VW>(p.dev_hi + od);
+      FV<VW> pn, dp;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        const float x = pd.v[e] - xs.v[e];                 // p_d - avg_k(pbar + u)
+        pn.v[e] = fminf(fmaxf(div_rn(q.rho_dev * x - bd, den, rden), lo.v[e]), hi.v[e]);
+        dp.v[e] = pn.v[e] - pd.v[e];
+      }
+      stv<VW>(p.DPD + od, dp);
+      stv<VW>(p.PD + od, pn);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// inner: one warp per battery, then per ramp-limited generator (Appendix D)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(BLOCK) inner_kernel(Params p) {
+  extern __shared__ float smem[];
+  const Iter q = iter_scalars(p);
+  if (q.skip) return;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int wfl = warp_smem_floats(p.T);
+  float *wsm = smem + (size_t)wib * wfl;
+  float *state_sh = (wfl > 3 * (p.T + 1)) ? wsm + 3 * (p.T + 1) : nullptr;
   const int n_inner = p.n_stor + p.n_ramp;
-  const int line_per_k = L * TV;
+  for (int w = blockIdx.x * WARPS + wib; w < n_inner; w += gridDim.x * WARPS) {
+    if (w < p.n_stor)
+      stor_prox(p, w, q.rho_dev, wsm, state_sh, lane);
+    else
+      ramp_prox(p, w - p.n_stor, q.rho_dev, wsm, state_sh, lane);
+  }
+}
 
-  // a sticky device error (timeout, non-finite) leaves the state as it is
-  const int n_iters = sc0.status ? 0 : p.n_iters;
-  for (int i = 0; i < n_iters; ++i) {
-    const long long itn = it + 1;
-    const int old = (int)(it & 1), nw = old ^ 1;
-    const bool adapt_now = p.adapt_every > 0 && (itn % p.adapt_every) == 0;
-    const bool check_now = p.eps > 0 && p.check_every > 0 && (itn % p.check_every) == 0;
-    if (threadIdx.x == 0) {
-      sf[0] = (float)sd[0]; sf[1] = (float)sd[1]; sf[2] = (float)sd[2]; sf[3] = (float)sd[3];
-      sf[4] = (float)(Kp * sd[0]);
-    }
-    __syncthreads();
-    const float frp = sf[0], frt = sf[1], fsu = sf[2], fsv = sf[3], rho_dev = sf[4];
-    const float *Uo = p.U[old], *Bo = p.PBAR[old];
-    const size_t NT = (size_t)N * T;
-    float acc[NSLOT] = {0.f, 0.f, 0.f, 0.f, 0.f};
-
-    // ------- phase 1: steps 1 and 2, both from the previous iterate -------
-    // (a) every warp: avg_k(pbar + u) at each node with devices, in chunks of
-    // 32 (node, VW time steps) items; the node's closed-form devices are
-    // updated on the spot (Section 4.2), and nodes with inner-ADMM devices
-    // keep the average in XS.
-    {
-      const float rkp = __frcp_rn(kpf);
-      const unsigned n_xv = (unsigned)p.n_dnode * (unsigned)TV;
-      const unsigned n_xc = (n_xv + 31u) / 32u;
-      unsigned long long *xctr = p.work + 4 + (itn & 1), *xdone = p.work + 6 + (itn & 1);
-      for (;;) {
-        unsigned c = 0;
-        if (lane == 0) c = (unsigned)atomicAdd(xctr, 1ull);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= n_xc) break;
-        const unsigned item = c * 32u + (unsigned)lane;
-        if (item < n_xv) {
-          const int ci = (int)(item / (unsigned)TV), t0 = (int)(item % (unsigned)TV) * VW;
-          const int nd = p.dnode_ids[ci];
-          const size_t on = (size_t)nd * T + t0;
-          FV<VW> xs;
-          if constexpr (VW == 4) {
-            float4 sp, sq;
-            ksum4(Bo, Uo, on, NT, Kp, sp, sq);                  // sum_k pbar, sum_k u at the node
-            xs.v[0] = div_rn(sp.x + fsu * sq.x, kpf, rkp);     // avg_k(pbar + u)
-            xs.v[1] = div_rn(sp.y + fsu * sq.y, kpf, rkp);
-            xs.v[2] = div_rn(sp.z + fsu * sq.z, kpf, rkp);
-            xs.v[3] = div_rn(sp.w + fsu * sq.w, kpf, rkp);
-          } else {
-            float sp, sq;
-            ksum(Bo, Uo, on, NT, Kp, sp, sq);
-            xs.v[0] = div_rn(sp + fsu * sq, kpf, rkp);
-          }
-          if (p.dnode_keep[ci]) stv<VW>(p.XS + on, xs);
-          for (int j = p.dnode_ptr[ci]; j < p.dnode_ptr[ci + 1]; ++j) {
-            const int d = p.dnode_dev[j];
-            const size_t od = (size_t)d * T + t0;
-            const float den = 2.f * p.dev_a[d] + rho_dev, rden = __frcp_rn(den), bd = p.dev_b[d];
-            const FV<VW> pd = ldv<VW>(p.PD + od), lo = ldv<VW>(p.dev_lo + od), hi = ldv<VW>(p.dev_hi + od);
-            FV<VW> pn, dp;
-#pragma unroll
-            for (int e = 0; e < VW; ++e) {
-              const float x = pd.v[e] - xs.v[e];               // p_d - avg_k(pbar + u)
-              pn.v[e] = fminf(fmaxf(div_rn(rho_dev * x - bd, den, rden), lo.v[e]), hi.v[e]);
-              dp.v[e] = pn.v[e] - pd.v[e];
-            }
-            stv<VW>(p.DPD + od, dp);
-            stv<VW>(p.PD + od, pn);
-          }
-        }
-        // every lane's XS and device rows visible before the chunk counts as done
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) atomicAdd(xdone, 1ull);
-      }
-      // (b) DEV_WARPS warps per CTA: inner-ADMM proxes (Appendix D) of
-      // batteries, then ramp generators, from a counter, once every average
-      // is in XS; the other warps go straight to the line stream.
-      if (wib < DEV_WARPS && n_inner > 0) {
-        int ok = 1;
-        if (lane == 0) {
-          const long long t0c = clock64();
-          while (*(volatile unsigned long long *)xdone < (unsigned long long)n_xc) {
-            if (*(volatile int *)p.err || clock64() - t0c > p.barrier_budget) {
-              atomicCAS(p.err, 0, ST_TIMEOUT);
-              ok = 0;
-              break;
-            }
-            __nanosleep(64);
-          }
-          __threadfence();
-        }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        unsigned long long *dctr = p.work + 2 + (itn & 1);
-        for (; ok;) {
-          unsigned w = 0;
-          if (lane == 0) w = (unsigned)atomicAdd(dctr, 1ull);
-          w = __shfl_sync(0xffffffffu, w, 0);
-          if (w >= (unsigned)n_inner) break;
-          if (w < (unsigned)p.n_stor)
-            stor_prox(p, (int)w, rho_dev, wsm, state_sh, lane);
-          else
-            ramp_prox(p, (int)w - p.n_stor, rho_dev, wsm, state_sh, lane);
-        }
-      }
-    }
-    {
-      const unsigned na = (unsigned)Kp * (unsigned)line_per_k;
-      unsigned long long *wctr = p.work + (itn & 1);
-      for (;;) {
-        unsigned base = 0;
-        if (lane == 0) base = (unsigned)atomicAdd(wctr, (unsigned long long)(32 * LGRAB));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= na) break;
-        Idx3 ix, dx;
-        ix.set(base + lane, L, TV);
-        dx.set(32u, L, TV);
+// ---------------------------------------------------------------------------
+// line: step 1 for every (contingency, line, VW time steps)
+// ---------------------------------------------------------------------------
+template <int VW>
+__global__ void __launch_bounds__(BLOCK, 4) line_kernel(Params p) {
+  const Iter q = iter_scalars(p);
+  if (q.skip) return;
+  const int L = p.L, TV = p.T / VW;
+  const unsigned n = (unsigned)p.Kp * (unsigned)L * (unsigned)TV;
+  // each CTA takes LINE_IPT consecutive blocks of BLOCK items, so CTAs are
+  // short-lived and the device kernels' CTAs find room beside them
+  const unsigned base = blockIdx.x * (unsigned)(BLOCK * LINE_IPT) + threadIdx.x;
+  Idx3 ix, dx;
+  ix.set(base, L, TV);
+  dx.set(BLOCK, L, TV);
 #pragma unroll 1
-        for (int g = 0; g < LGRAB; ++g, ix.step(dx, L, TV)) {
-          if (base + g * 32 + lane < na) line_item<VW>(p, old, nw, ix.a, ix.b, ix.c * VW, frp, frt, fsu, fsv, v_fresh);
-        }
-      }
-    }
-    if (!grid_barrier(p, &s_flag)) { status = ST_TIMEOUT; break; }
-
-    // ------- phase 2: step 3, node sums of the new terminal values -------
-    {
-      const unsigned nn = (unsigned)Kp * (unsigned)(N * TV);
-      Idx3 ix, dx;
-      ix.set((unsigned)gthr, N, TV);
-      dx.set((unsigned)nthr, N, TV);
-      for (unsigned item = (unsigned)gthr; item < nn; item += (unsigned)nthr, ix.step(dx, N, TV))
-        node_item<VW>(p, old, nw, ix.a, ix.b, ix.c * VW, fsu, acc);
-    }
-
-    // block reduction of the partial sums: FP32 within a warp, FP64 across
-#pragma unroll
-    for (int s = 0; s < NSLOT; ++s) {
-      float v = acc[s];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) red[wib][s] = (double)v;
-    }
-    __syncthreads();
-    if (threadIdx.x < NSLOT) {
-      double v = 0.0;
-      for (int w = 0; w < WARPS; ++w) v += red[w][threadIdx.x];
-      p.partials[((size_t)(itn & 1) * gridDim.x + blockIdx.x) * NSLOT + threadIdx.x] = v;
-    }
-    if (!grid_barrier(p, &s_flag)) { status = ST_TIMEOUT; break; }
-
-    // ---------------- phase C: residuals and decisions (same in every CTA) ----------------
-    if (wib == 0) {
-      double tot[NSLOT];
-#pragma unroll
-      for (int s = 0; s < NSLOT; ++s) tot[s] = 0.0;
-      const double *base = p.partials + (size_t)(itn & 1) * gridDim.x * NSLOT;
-      for (int b = lane; b < (int)gridDim.x; b += 32) {
-        double v[NSLOT];
-#pragma unroll
-        for (int s = 0; s < NSLOT; ++s) v[s] = __ldcg(base + (size_t)b * NSLOT + s);
-#pragma unroll
-        for (int s = 0; s < NSLOT; ++s) tot[s] += v[s];
-      }
-#pragma unroll
-      for (int s = 0; s < NSLOT; ++s) {
-        double v = tot[s];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        tot[s] = v;
-      }
-      if (lane == 0) {
-        const double rho_p = sd[0], rho_th = sd[1];
-        const double r_pp = sqrt(fmax(tot[SL_PP], 0.0));
-        const double r_pt = sqrt(fmax(tot[SL_PT], 0.0));
-        const double r_dp = rho_p * sqrt(fmax(tot[SL_DP], 0.0));
-        const double r_dt = rho_th * sqrt(fmax(tot[SL_DT], 0.0));
-        const double rp = sqrt(r_pp * r_pp + r_pt * r_pt);
-        const double rd = sqrt(r_dp * r_dp + r_dt * r_dt);
-        int code = 0;
-        double nrp = rho_p, nrt = rho_th;
-        if (!isfinite(rp) || !isfinite(rd) || tot[SL_NF] != 0.0) {
-          code = 1 | (ST_NONFINITE << 2);
-        } else {
-          if (check_now && fmax(rp, rd) <= p.tol) code = 2;
-          if (adapt_now) {
-            if (r_pp > p.mu * r_dp) nrp = rho_p * p.gamma;
-            else if (r_dp > p.mu * r_pp) nrp = rho_p / p.gamma;
-            if (r_pt > p.mu * r_dt) nrt = rho_th * p.gamma;
-            else if (r_dt > p.mu * r_pt) nrt = rho_th / p.gamma;
-          }
-        }
-        sd[4] = rp; sd[5] = rd; sd[6] = r_pp; sd[7] = r_pt; sd[8] = r_dp; sd[9] = r_dt;
-        // this iteration's work counter is next used two iterations on,
-        // after at least one more grid barrier
-        if (blockIdx.x == 0) {
-          for (int q = 0; q < 4; ++q) p.work[2 * q + (itn & 1)] = 0ull;
-        }
-        sd[2] = rho_p / nrp;   // pending rescale of u and v (Section 3.5)
-        sd[3] = rho_th / nrt;
-        sd[0] = nrp;
-        sd[1] = nrt;
-        s_code = code;
-      }
-    }
-    __syncthreads();
-    const int code = s_code;
-    it = itn;
-    v_fresh = 0;
-    if ((code & 3) == 2) converged = 1;
-    if (code >= 4) status = code >> 2;
-    if (code != 0) break;
+  for (int j = 0; j < LINE_IPT; ++j, ix.step(dx, L, TV)) {
+    if (base + (unsigned)(j * BLOCK) < n)
+      line_item<VW>(p, q.old, q.nw, ix.a, ix.b, ix.c * VW, q.frp, q.frt, q.fsu, q.fsv, q.v_fresh);
   }
+}
 
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    DevScalars sc = sc0;
-    sc.rho_p = sd[0];
-    sc.rho_th = sd[1];
-    sc.su = sd[2];
-    sc.sv = sd[3];
-    for (int j = 0; j < 6; ++j) sc.res[j] = sd[4 + j];
-    sc.it = it;
-    sc.converged = converged;
-    const int e = *(volatile int *)p.err;
-    sc.status = status ? status : (e ? e : sc0.status);
-    sc.v_fresh = v_fresh;
-    *p.sc = sc;
+// ---------------------------------------------------------------------------
+// node: step 3 for every (contingency, node, VW time steps), and the CTA's
+// residual partial sums: FP32 per thread, FP64 across warps
+// ---------------------------------------------------------------------------
+template <int VW>
+__global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel(Params p) {
+  __shared__ double red[WARPS][NSLOT];
+  const Iter q = iter_scalars(p);
+  if (q.skip) return;
+  const int N = p.N, TV = p.T / VW;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned n = (unsigned)p.Kp * (unsigned)N * (unsigned)TV;
+  const unsigned stride = gridDim.x * BLOCK;
+  unsigned item = blockIdx.x * BLOCK + threadIdx.x;
+  float acc[NSLOT] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  Idx3 ix, dx;
+  ix.set(item, N, TV);
+  dx.set(stride, N, TV);
+  for (; item < n; item += stride, ix.step(dx, N, TV))
+    node_item<VW>(p, q.old, q.nw, ix.a, ix.b, ix.c * VW, q.fsu, acc);
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    float v = acc[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wib][s] = (double)v;
   }
+  __syncthreads();
+  if (threadIdx.x < NSLOT) {
+    double v = 0.0;
+    for (int w = 0; w < WARPS; ++w) v += red[w][threadIdx.x];
+    p.partials[(size_t)blockIdx.x * NSLOT + threadIdx.x] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// decide: residuals (Section 3.3) from the node kernel's n_part CTA partials
+// in FP64 and a fixed order, the stopping test of Eq. (converge) and the
+// adaptive penalty (Section 3.5); advances the iteration counter.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(BLOCK) decide_kernel(Params p, int n_part) {
+  __shared__ double red[WARPS][NSLOT];
+  const Iter q = iter_scalars(p);
+  if (q.skip) return;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double tot[NSLOT];
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) tot[s] = 0.0;
+  for (int b = threadIdx.x; b < n_part; b += BLOCK) {
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) tot[s] += p.partials[(size_t)b * NSLOT + s];
+  }
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    double v = tot[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wib][s] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    double v = 0.0;
+    for (int w = 0; w < WARPS; ++w) v += red[w][s];
+    tot[s] = v;
+  }
+  DevScalars sc = *p.sc;
+  const long long itn = sc.it + 1;
+  const bool adapt_now = p.adapt_every > 0 && (itn % p.adapt_every) == 0;
+  const bool check_now = p.eps > 0 && p.check_every > 0 && (itn % p.check_every) == 0;
+  const double rho_p = sc.rho_p, rho_th = sc.rho_th;
+  const double r_pp = sqrt(fmax(tot[SL_PP], 0.0));
+  const double r_pt = sqrt(fmax(tot[SL_PT], 0.0));
+  const double r_dp = rho_p * sqrt(fmax(tot[SL_DP], 0.0));
+  const double r_dt = rho_th * sqrt(fmax(tot[SL_DT], 0.0));
+  const double rp = sqrt(r_pp * r_pp + r_pt * r_pt);
+  const double rd = sqrt(r_dp * r_dp + r_dt * r_dt);
+  double nrp = rho_p, nrt = rho_th;
+  if (!isfinite(rp) || !isfinite(rd) || tot[SL_NF] != 0.0) {
+    sc.status = ST_NONFINITE;
+    sc.stop = 1;
+  } else {
+    if (check_now && fmax(rp, rd) <= p.tol) {
+      sc.converged = 1;
+      sc.stop = 1;
+    }
+    if (adapt_now) {
+      if (r_pp > p.mu * r_dp) nrp = rho_p * p.gamma;
+      else if (r_dp > p.mu * r_pp) nrp = rho_p / p.gamma;
+      if (r_pt > p.mu * r_dt) nrt = rho_th * p.gamma;
+      else if (r_dt > p.mu * r_pt) nrt = rho_th / p.gamma;
+    }
+  }
+  sc.res[0] = rp; sc.res[1] = rd; sc.res[2] = r_pp; sc.res[3] = r_pt; sc.res[4] = r_dp; sc.res[5] = r_dt;
+  sc.su = rho_p / nrp;   // pending rescale of u and v (Section 3.5), applied on their next read
+  sc.sv = rho_th / nrt;
+  sc.rho_p = nrp;
+  sc.rho_th = nrt;
+  sc.it = itn;
+  sc.v_fresh = 0;
+  *p.sc = sc;
 }
 
 // ---------------------------------------------------------------------------
@@ -1080,41 +1015,65 @@ __global__ void set_rho_kernel(DevScalars *sc, double rho) {
   *sc = s;
 }
 
-static size_t iteration_smem(int T) { return (size_t)WARPS * warp_smem_floats(T) * sizeof(float); }
+static size_t inner_smem(int T) { return (size_t)WARPS * warp_smem_floats(T) * sizeof(float); }
 
 }  // namespace opfk
 
 using namespace opfk;
 
-template <int VW>
-static cudaError_t occupancy(int *nb, size_t sm) {
-  if (sm > 48 * 1024) cudaFuncSetAttribute(iteration_kernel<VW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, iteration_kernel<VW>, BLOCK, sm);
-}
-
-int opfk_max_grid(int T, int *grid) {
+// blocks of a grid-stride kernel: resident CTAs per SM times the SM count
+template <class F>
+static int resident_grid(F fn, size_t smem) {
   int dev = 0, sms = 0, nb = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  const size_t sm = iteration_smem(T);
-  const cudaError_t e = (T % 4 == 0) ? occupancy<4>(&nb, sm) : occupancy<1>(&nb, sm);
-  if (e != cudaSuccess || nb < 1) return -1;
-  *grid = nb * sms;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, BLOCK, smem) != cudaSuccess || nb < 1) return -1;
+  return nb * sms;
+}
+
+int opfk_plan(const Params &p, IterPlan *plan) {
+  const bool v4 = (p.T % 4 == 0), v2 = (p.T % 2 == 0);
+  const size_t ism = inner_smem(p.T);
+  if (ism > 48 * 1024 &&
+      cudaFuncSetAttribute(inner_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism) != cudaSuccess)
+    return -1;
+  const int gn = v2 ? resident_grid(node_kernel<2>, 0) : resident_grid(node_kernel<1>, 0);
+  const int gx = v4 ? resident_grid(xs_kernel<4>, 0) : resident_grid(xs_kernel<1>, 0);
+  if (gn < 1 || gx < 1) return -1;
+  const long long nl = (long long)p.Kp * p.L * (p.T / (v4 ? 4 : 1));
+  const long long nn = (long long)p.Kp * p.N * (p.T / (v2 ? 2 : 1));
+  const long long nx = (long long)p.n_dnode * (p.T / (v4 ? 4 : 1));
+  const int n_inner = p.n_stor + p.n_ramp;
+  plan->line_grid = (int)((nl + (long long)BLOCK * LINE_IPT - 1) / ((long long)BLOCK * LINE_IPT));
+  plan->node_grid = (int)std::min<long long>(gn, (nn + BLOCK - 1) / BLOCK);
+  plan->xs_grid = (int)std::min<long long>(gx, (nx + BLOCK - 1) / BLOCK);
+  plan->inner_grid = (n_inner + WARPS - 1) / WARPS;
+  plan->inner_smem = ism;
   return 0;
 }
 
-int opfk_iteration_launch(const Params &p, void *stream, int grid, char *msg, int msglen) {
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t sm = iteration_smem(p.T);
-  Params pp = p;
-  void *args[] = {&pp};
-  void *fn = (p.T % 4 == 0) ? (void *)iteration_kernel<4> : (void *)iteration_kernel<1>;
-  const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(BLOCK), args, sm, s);
-  if (e != cudaSuccess) {
-    snprintf(msg, msglen, "cudaLaunchCooperativeKernel: %s", cudaGetErrorString(e));
-    return -1;
+int opfk_iteration_enqueue(const Params &p, const IterPlan &plan, void *main_stream, void *aux_stream,
+                           void *ev_fork, void *ev_join) {
+  cudaStream_t sm = (cudaStream_t)main_stream, sa = (cudaStream_t)aux_stream;
+  const bool v4 = (p.T % 4 == 0), v2 = (p.T % 2 == 0);
+  // step 1 reads only the previous iterate: it runs beside the device proxes
+  if (plan.line_grid > 0) {
+    if (cudaEventRecord((cudaEvent_t)ev_fork, sm) != cudaSuccess) return -1;
+    if (cudaStreamWaitEvent(sa, (cudaEvent_t)ev_fork, 0) != cudaSuccess) return -1;
+    if (v4) line_kernel<4><<<plan.line_grid, BLOCK, 0, sa>>>(p);
+    else line_kernel<1><<<plan.line_grid, BLOCK, 0, sa>>>(p);
+    if (cudaEventRecord((cudaEvent_t)ev_join, sa) != cudaSuccess) return -1;
   }
-  return 0;
+  if (plan.xs_grid > 0) {
+    if (v4) xs_kernel<4><<<plan.xs_grid, BLOCK, 0, sm>>>(p);
+    else xs_kernel<1><<<plan.xs_grid, BLOCK, 0, sm>>>(p);
+  }
+  if (plan.inner_grid > 0) inner_kernel<<<plan.inner_grid, BLOCK, plan.inner_smem, sm>>>(p);
+  if (plan.line_grid > 0 && cudaStreamWaitEvent(sm, (cudaEvent_t)ev_join, 0) != cudaSuccess) return -1;
+  if (v2) node_kernel<2><<<plan.node_grid, BLOCK, 0, sm>>>(p);
+  else node_kernel<1><<<plan.node_grid, BLOCK, 0, sm>>>(p);
+  decide_kernel<<<1, BLOCK, 0, sm>>>(p, plan.node_grid);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 static int aux_grid(long long work) {
