@@ -288,8 +288,7 @@ void carve(opf_ctx *c, Arena &a) {
   p.cnt_th = a.take<float>(c->N);
   p.rcnt_p = a.take<float>(c->N);
   p.rcnt_th = a.take<float>(c->N);
-  p.ndesc = a.take<int4>(c->N);
-  p.ncnt = a.take<float4>(c->N);
+  p.nrec = a.take<int4>(3 * (size_t)c->N);
   p.tcode = a.take<int>(c->n_tcode);
   p.dev_node = a.take<int>(c->S);
   p.dev_type = a.take<int>(c->S);
@@ -312,6 +311,9 @@ void carve(opf_ctx *c, Arena &a) {
   p.line_perm = a.take<int>(c->L);
   // scratch
   p.XS = a.take<float>((size_t)c->N * T);
+  p.DSP = a.take<float>((size_t)c->N * T);
+  p.DSM = a.take<float>((size_t)c->N * T);
+  p.DSQ = a.take<float>((size_t)c->N * T);
   p.partials = a.take<double>((size_t)c->plan.node_grid * opfk::NSLOT);
 }
 
@@ -599,19 +601,21 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
     q.n_dnode = c->n_dnode;
     q.n_ramp = c->n_ramp;
     q.n_stor = c->n_stor;
+    q.S = S;
     if (opfk_plan(q, &c->plan) != 0) {
       delete c;
       return fail(OPF_ECUDA, "occupancy query for the iteration kernels failed");
     }
   }
-  // terminal codes per node, padded to a multiple of 4
+  // line-terminal codes beyond the first four of each node, padded to a
+  // multiple of 4 (the first four sit in the node record)
   std::vector<int> tcode, tptr(N + 1, 0);
   for (int n = 0; n < N; ++n) {
-    for (int j = lptr[n]; j < lptr[n + 1]; ++j) tcode.push_back(lcsr[j].x);
+    for (int j = lptr[n] + 4; j < lptr[n + 1]; ++j) tcode.push_back(lcsr[j].x);
     while (tcode.size() % 4) tcode.push_back(-1);
     tptr[n + 1] = (int)tcode.size();
   }
-  c->n_tcode = tcode.size();
+  c->n_tcode = std::max<size_t>(tcode.size(), 4);
   Arena a;
   carve(c, a);
   c->arena_bytes = a.off + 256;
@@ -690,14 +694,20 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   up(p.rcnt_p, rcnt_p);
   up(p.rcnt_th, rcnt_th);
   {
-    std::vector<int4> nd(N);
-    std::vector<float4> nc(N);
+    std::vector<int4> rec(3 * (size_t)N);
+    auto fbits = [](float f) {
+      int i;
+      std::memcpy(&i, &f, sizeof(i));
+      return i;
+    };
     for (int n = 0; n < N; ++n) {
-      nd[n] = make_int4(tptr[n], tptr[n + 1], dptr[n], dptr[n + 1]);
-      nc[n] = make_float4(cnt_p[n], cnt_th[n], rcnt_p[n], rcnt_th[n]);
+      int code[4] = {-1, -1, -1, -1};
+      for (int j = lptr[n], q = 0; j < lptr[n + 1] && q < 4; ++j, ++q) code[q] = lcsr[j].x;
+      rec[3 * n] = make_int4(fbits(cnt_p[n]), fbits(cnt_th[n]), fbits(rcnt_p[n]), fbits(rcnt_th[n]));
+      rec[3 * n + 1] = make_int4(code[0], code[1], code[2], code[3]);
+      rec[3 * n + 2] = make_int4(tptr[n], tptr[n + 1], dptr[n + 1] - dptr[n], 0);
     }
-    up(p.ndesc, nd);
-    up(p.ncnt, nc);
+    up(p.nrec, rec);
   }
   up(p.tcode, tcode);
   up(p.dev_node, dev_node_int);

@@ -70,10 +70,16 @@ struct Params {
   const int *dcsr_ptr, *dcsr_idx;  // devices of each node
   const float *cnt_p, *cnt_th;     // terminals per node: all (power), line terminals (phase)
   const float *rcnt_p, *rcnt_th;   // their reciprocals (0 for a node without line terminals)
-  const int4 *ndesc;               // per node: tcode begin, end, dcsr begin, end
-  const float4 *ncnt;              // per node: cnt_p, cnt_th, rcnt_p, rcnt_th
-  const int *tcode;                // line terminals 2*l + end per node, each node's list
-                                   // padded to a multiple of 4 with -1 (int4 loads)
+  // per node, 3 int4: (cnt_p, cnt_th, rcnt_p, rcnt_th as float bits), the first
+  // four line-terminal codes 2*l + end (-1 = none), (tcode begin, end of the
+  // rest, device count, 0)
+  const int4 *nrec;
+  const int *tcode;                // line-terminal codes beyond the first four per node,
+                                   // each node's list padded to a multiple of 4 with -1
+  // per node and time step, over the node's devices (the same in every
+  // contingency): sum of p_d, and the Welford mean and sum of squared
+  // deviations of the change of p_d in this iteration
+  float *DSP, *DSM, *DSQ;          // [N][T]
   // devices: type 0 = closed-form prox clip((rho X - b)/(2a + rho), lo, hi), 1 = inner ADMM
   float *PD, *DPD;
   const int *dev_node, *dev_type;
@@ -103,7 +109,7 @@ struct Params {
 
 // Launch configuration of one iteration's kernels.
 struct IterPlan {
-  int line_grid, node_grid, xs_grid, inner_grid;  // 0: the kernel has no work
+  int line_grid, node_grid, xs_grid, inner_grid, dsum_grid;  // 0: the kernel has no work
   size_t inner_smem;
 };
 

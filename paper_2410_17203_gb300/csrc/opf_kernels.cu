@@ -585,27 +585,29 @@ template <int VW>
 __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int k, int n, int toff, float fsu,
                                           float *acc) {
   const int T = p.T, L = p.L, N = p.N;
-  const int4 nd = p.ndesc[n];
-  const float4 nc = p.ncnt[n];
-  const float cp = nc.x, ct = nc.y, rcp = nc.z, rct = nc.w;
-  const size_t on = ((size_t)k * N + n) * T + toff;
-  const FV<VW> uo = ldv<VW>(p.U[old] + on), go = ldv<VW>(p.THBAR[old] + on);
-  FV<VW> sp, st;
+  // level 1: the node record, the node's old rows and its device sums
+  const int4 r0 = p.nrec[3 * n], r1 = p.nrec[3 * n + 1], r2 = p.nrec[3 * n + 2];
+  const float cp = __int_as_float(r0.x), ct = __int_as_float(r0.y);
+  const float rcp = __int_as_float(r0.z), rct = __int_as_float(r0.w);
+  const size_t on = ((size_t)k * N + n) * T + toff, os = (size_t)n * T + toff;
+  const FV<VW> uo = ldv_cs<VW>(p.U[old] + on), go = ldv_cs<VW>(p.THBAR[old] + on);
+  // device terminals first: the sum and the Welford state after them, the
+  // same in every contingency
+  FV<VW> sp = ldv<VW>(p.DSP + os), st;
   Welf<VW> wdp, wth;
-  wdp.reset();
+  {
+    const FV<VW> m = ldv<VW>(p.DSM + os), q = ldv<VW>(p.DSQ + os);
+    wdp.n = (float)r2.z;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) { wdp.mean[e] = m.v[e]; wdp.m2[e] = q.v[e]; }
+  }
   wth.reset();
 #pragma unroll
-  for (int e = 0; e < VW; ++e) { sp.v[e] = 0.f; st.v[e] = 0.f; }
-  for (int j = nd.z; j < nd.w; ++j) {
-    const size_t od = (size_t)p.dcsr_idx[j] * T + toff;
-    const FV<VW> pd = ldv<VW>(p.PD + od), dpd = ldv<VW>(p.DPD + od);
-#pragma unroll
-    for (int e = 0; e < VW; ++e) sp.v[e] += pd.v[e];
-    wdp.add(dpd.v);
-  }
+  for (int e = 0; e < VW; ++e) st.v[e] = 0.f;
+  // level 2: the rows of the line terminals, four at a time
   const size_t kb = (size_t)k * L * T + toff;
-  for (int j = nd.x; j < nd.y; j += 4) {
-    const int4 c4 = *reinterpret_cast<const int4 *>(p.tcode + j);
+  int4 c4 = r1;
+  for (int j = r2.x - 4;;) {
     const int code[4] = {c4.x, c4.y, c4.z, c4.w};
     FV<VW> pn[4], po[4], th[4];
 #pragma unroll
@@ -613,7 +615,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
       if (code[q] >= 0) {
         const size_t ol = kb + (size_t)(code[q] >> 1) * T;
         pn[q] = ldv<VW>(p.P[nw] + ol);
-        po[q] = ldv<VW>(p.P[old] + ol);
+        po[q] = ldv_cs<VW>(p.P[old] + ol);
         th[q] = ldv<VW>(((code[q] & 1) ? p.TH2[nw] : p.TH1[nw]) + ol);
       }
     }
@@ -632,6 +634,9 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
         wth.add(th[q].v);
       }
     }
+    j += 4;
+    if (j >= r2.y) break;
+    c4 = *reinterpret_cast<const int4 *>(p.tcode + j);   // terminals beyond the first four
   }
   FV<VW> pb, tbar, un;
 #pragma unroll
@@ -751,6 +756,41 @@ __global__ void __launch_bounds__(BLOCK) inner_kernel(Params p) {
       stor_prox(p, w, q.rho_dev, wsm, state_sh, lane);
     else
       ramp_prox(p, w - p.n_stor, q.rho_dev, wsm, state_sh, lane);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dsum: per (node, VW time steps), the sum of the node's device powers and
+// the Welford state of their changes, in device order (the node sums of
+// every contingency start from it)
+// ---------------------------------------------------------------------------
+template <int VW>
+__global__ void __launch_bounds__(BLOCK) dsum_kernel(Params p) {
+  const Iter q = iter_scalars(p);
+  if (q.skip) return;
+  const int T = p.T, TV = T / VW;
+  const unsigned n_items = (unsigned)p.N * (unsigned)TV;
+  for (unsigned item = blockIdx.x * BLOCK + threadIdx.x; item < n_items; item += gridDim.x * BLOCK) {
+    const int n = (int)(item / (unsigned)TV), t0 = (int)(item % (unsigned)TV) * VW;
+    FV<VW> sp;
+    Welf<VW> w;
+    w.reset();
+#pragma unroll
+    for (int e = 0; e < VW; ++e) sp.v[e] = 0.f;
+    for (int j = p.dcsr_ptr[n]; j < p.dcsr_ptr[n + 1]; ++j) {
+      const size_t od = (size_t)p.dcsr_idx[j] * T + t0;
+      const FV<VW> pd = ldv<VW>(p.PD + od), dpd = ldv<VW>(p.DPD + od);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) sp.v[e] += pd.v[e];
+      w.add(dpd.v);
+    }
+    FV<VW> m, q2;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) { m.v[e] = w.mean[e]; q2.v[e] = w.m2[e]; }
+    const size_t os = (size_t)n * T + t0;
+    stv<VW>(p.DSP + os, sp);
+    stv<VW>(p.DSM + os, m);
+    stv<VW>(p.DSQ + os, q2);
   }
 }
 
@@ -1039,7 +1079,8 @@ int opfk_plan(const Params &p, IterPlan *plan) {
     return -1;
   const int gn = v2 ? resident_grid(node_kernel<2>, 0) : resident_grid(node_kernel<1>, 0);
   const int gx = v4 ? resident_grid(xs_kernel<4>, 0) : resident_grid(xs_kernel<1>, 0);
-  if (gn < 1 || gx < 1) return -1;
+  const int gd = v2 ? resident_grid(dsum_kernel<2>, 0) : resident_grid(dsum_kernel<1>, 0);
+  if (gn < 1 || gx < 1 || gd < 1) return -1;
   const long long nl = (long long)p.Kp * p.L * (p.T / (v4 ? 4 : 1));
   const long long nn = (long long)p.Kp * p.N * (p.T / (v2 ? 2 : 1));
   const long long nx = (long long)p.n_dnode * (p.T / (v4 ? 4 : 1));
@@ -1048,6 +1089,8 @@ int opfk_plan(const Params &p, IterPlan *plan) {
   plan->node_grid = (int)std::min<long long>(gn, (nn + BLOCK - 1) / BLOCK);
   plan->xs_grid = (int)std::min<long long>(gx, (nx + BLOCK - 1) / BLOCK);
   plan->inner_grid = (n_inner + WARPS - 1) / WARPS;
+  const long long nd = (long long)p.N * (p.T / (v2 ? 2 : 1));
+  plan->dsum_grid = (int)std::min<long long>(gd, (nd + BLOCK - 1) / BLOCK);
   plan->inner_smem = ism;
   return 0;
 }
@@ -1069,6 +1112,8 @@ int opfk_iteration_enqueue(const Params &p, const IterPlan &plan, void *main_str
     else xs_kernel<1><<<plan.xs_grid, BLOCK, 0, sm>>>(p);
   }
   if (plan.inner_grid > 0) inner_kernel<<<plan.inner_grid, BLOCK, plan.inner_smem, sm>>>(p);
+  if (v2) dsum_kernel<2><<<plan.dsum_grid, BLOCK, 0, sm>>>(p);
+  else dsum_kernel<1><<<plan.dsum_grid, BLOCK, 0, sm>>>(p);
   if (plan.line_grid > 0 && cudaStreamWaitEvent(sm, (cudaEvent_t)ev_join, 0) != cudaSuccess) return -1;
   if (v2) node_kernel<2><<<plan.node_grid, BLOCK, 0, sm>>>(p);
   else node_kernel<1><<<plan.node_grid, BLOCK, 0, sm>>>(p);
