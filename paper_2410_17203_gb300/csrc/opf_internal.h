@@ -110,6 +110,7 @@ struct Params {
 // Launch configuration of one iteration's kernels.
 struct IterPlan {
   int line_grid, node_grid, xs_grid, inner_grid, dsum_grid;  // 0: the kernel has no work
+  int n_slabs, slab_k;  // contingency slabs of the line / node kernels, slab_k contingencies each
   size_t inner_smem;
 };
 
@@ -119,9 +120,10 @@ struct IterPlan {
 extern "C++" {
 // Grids of the iteration kernels for this problem on the current device.
 int opfk_plan(const opfk::Params &p, opfk::IterPlan *plan);
-// Enqueue one iteration: xs, inner and node / decide on main_stream, the line
-// kernel on aux_stream between the two events (fork after the previous
-// iteration, join before the node kernel).  Works under stream capture.
+// Enqueue one iteration: xs, inner, dsum, the node kernels and decide on
+// main_stream, the line kernels on aux_stream (forked after the previous
+// iteration; each slab joined before its node kernel).  Works under stream
+// capture.
 int opfk_iteration_enqueue(const opfk::Params &p, const opfk::IterPlan &plan, void *main_stream,
                            void *aux_stream, void *ev_fork, void *ev_join);
 // State import / export between internal and caller numbering; `cur` selects

@@ -40,8 +40,10 @@ namespace opfk {
 
 constexpr int WARPS = BLOCK / 32;
 constexpr int ST_NONFINITE = 5;  // opf_status value set on the device
-constexpr int NODE_MIN_CTAS = 4; // resident CTAs per SM the node kernel is compiled for
+constexpr int NODE_VW = 4;       // time steps per node item
+constexpr int NODE_MIN_CTAS = 2; // resident CTAs per SM the node kernel is compiled for
 constexpr int LINE_IPT = 4;      // line items per thread (CTA-sized blocks of items)
+constexpr int N_SLABS = 1;       // contingency slabs per iteration (line / node overlap)
 
 // shared floats per warp: 3 (T+1) for the inner-ADMM work arrays, plus room
 // for one device's (lam, beta) while the horizon is short enough
@@ -798,11 +800,11 @@ __global__ void __launch_bounds__(BLOCK) dsum_kernel(Params p) {
 // line: step 1 for every (contingency, line, VW time steps)
 // ---------------------------------------------------------------------------
 template <int VW>
-__global__ void __launch_bounds__(BLOCK, 4) line_kernel(Params p) {
+__global__ void __launch_bounds__(BLOCK, 4) line_kernel(Params p, int k0, int k1) {
   const Iter q = iter_scalars(p);
   if (q.skip) return;
   const int L = p.L, TV = p.T / VW;
-  const unsigned n = (unsigned)p.Kp * (unsigned)L * (unsigned)TV;
+  const unsigned n = (unsigned)(k1 - k0) * (unsigned)L * (unsigned)TV;
   // each CTA takes LINE_IPT consecutive blocks of BLOCK items, so CTAs are
   // short-lived and the device kernels' CTAs find room beside them
   const unsigned base = blockIdx.x * (unsigned)(BLOCK * LINE_IPT) + threadIdx.x;
@@ -812,7 +814,7 @@ __global__ void __launch_bounds__(BLOCK, 4) line_kernel(Params p) {
 #pragma unroll 1
   for (int j = 0; j < LINE_IPT; ++j, ix.step(dx, L, TV)) {
     if (base + (unsigned)(j * BLOCK) < n)
-      line_item<VW>(p, q.old, q.nw, ix.a, ix.b, ix.c * VW, q.frp, q.frt, q.fsu, q.fsv, q.v_fresh);
+      line_item<VW>(p, q.old, q.nw, k0 + ix.a, ix.b, ix.c * VW, q.frp, q.frt, q.fsu, q.fsv, q.v_fresh);
   }
 }
 
@@ -821,13 +823,13 @@ __global__ void __launch_bounds__(BLOCK, 4) line_kernel(Params p) {
 // residual partial sums: FP32 per thread, FP64 across warps
 // ---------------------------------------------------------------------------
 template <int VW>
-__global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel(Params p) {
+__global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel(Params p, int k0, int k1, int first) {
   __shared__ double red[WARPS][NSLOT];
   const Iter q = iter_scalars(p);
   if (q.skip) return;
   const int N = p.N, TV = p.T / VW;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const unsigned n = (unsigned)p.Kp * (unsigned)N * (unsigned)TV;
+  const unsigned n = (unsigned)(k1 - k0) * (unsigned)N * (unsigned)TV;
   const unsigned stride = gridDim.x * BLOCK;
   unsigned item = blockIdx.x * BLOCK + threadIdx.x;
   float acc[NSLOT] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -835,7 +837,7 @@ __global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel(Params p) {
   ix.set(item, N, TV);
   dx.set(stride, N, TV);
   for (; item < n; item += stride, ix.step(dx, N, TV))
-    node_item<VW>(p, q.old, q.nw, ix.a, ix.b, ix.c * VW, q.fsu, acc);
+    node_item<VW>(p, q.old, q.nw, k0 + ix.a, ix.b, ix.c * VW, q.fsu, acc);
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     float v = acc[s];
@@ -844,8 +846,10 @@ __global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel(Params p) {
     if (lane == 0) red[wib][s] = (double)v;
   }
   __syncthreads();
+  // the slabs of one iteration run in order on one stream: the first one
+  // sets the CTA's partial sums, the others add to them
   if (threadIdx.x < NSLOT) {
-    double v = 0.0;
+    double v = first ? 0.0 : p.partials[(size_t)blockIdx.x * NSLOT + threadIdx.x];
     for (int w = 0; w < WARPS; ++w) v += red[w][threadIdx.x];
     p.partials[(size_t)blockIdx.x * NSLOT + threadIdx.x] = v;
   }
@@ -1077,12 +1081,21 @@ int opfk_plan(const Params &p, IterPlan *plan) {
   if (ism > 48 * 1024 &&
       cudaFuncSetAttribute(inner_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism) != cudaSuccess)
     return -1;
-  const int gn = v2 ? resident_grid(node_kernel<2>, 0) : resident_grid(node_kernel<1>, 0);
+  const bool vn = (p.T % NODE_VW == 0);
+  const int gn = vn ? resident_grid(node_kernel<NODE_VW>, 0) : resident_grid(node_kernel<1>, 0);
   const int gx = v4 ? resident_grid(xs_kernel<4>, 0) : resident_grid(xs_kernel<1>, 0);
   const int gd = v2 ? resident_grid(dsum_kernel<2>, 0) : resident_grid(dsum_kernel<1>, 0);
   if (gn < 1 || gx < 1 || gd < 1) return -1;
-  const long long nl = (long long)p.Kp * p.L * (p.T / (v4 ? 4 : 1));
-  const long long nn = (long long)p.Kp * p.N * (p.T / (v2 ? 2 : 1));
+  // contingency slabs: the node sums of slab s run beside the line proxes of
+  // slab s + 1, so the latency-bound node pass overlaps the bandwidth-bound
+  // line pass; a few slabs keep the launch count low
+  int ns = std::min(N_SLABS, p.Kp);
+  int G = (p.Kp + ns - 1) / ns;
+  ns = (p.Kp + G - 1) / G;
+  plan->n_slabs = ns;
+  plan->slab_k = G;
+  const long long tvl = p.T / (v4 ? 4 : 1), tvn = p.T / (vn ? NODE_VW : 1);
+  const long long nl = (long long)G * p.L * tvl, nn = (long long)G * p.N * tvn;
   const long long nx = (long long)p.n_dnode * (p.T / (v4 ? 4 : 1));
   const int n_inner = p.n_stor + p.n_ramp;
   plan->line_grid = (int)((nl + (long long)BLOCK * LINE_IPT - 1) / ((long long)BLOCK * LINE_IPT));
@@ -1099,14 +1112,11 @@ int opfk_iteration_enqueue(const Params &p, const IterPlan &plan, void *main_str
                            void *ev_fork, void *ev_join) {
   cudaStream_t sm = (cudaStream_t)main_stream, sa = (cudaStream_t)aux_stream;
   const bool v4 = (p.T % 4 == 0), v2 = (p.T % 2 == 0);
-  // step 1 reads only the previous iterate: it runs beside the device proxes
-  if (plan.line_grid > 0) {
-    if (cudaEventRecord((cudaEvent_t)ev_fork, sm) != cudaSuccess) return -1;
-    if (cudaStreamWaitEvent(sa, (cudaEvent_t)ev_fork, 0) != cudaSuccess) return -1;
-    if (v4) line_kernel<4><<<plan.line_grid, BLOCK, 0, sa>>>(p);
-    else line_kernel<1><<<plan.line_grid, BLOCK, 0, sa>>>(p);
-    if (cudaEventRecord((cudaEvent_t)ev_join, sa) != cudaSuccess) return -1;
-  }
+  // The line proxes of slab s (aux stream) read only the previous iterate;
+  // the node sums of slab s (main stream) follow them and the device
+  // kernels, and run beside the line proxes of slab s + 1.
+  if (cudaEventRecord((cudaEvent_t)ev_fork, sm) != cudaSuccess) return -1;
+  if (cudaStreamWaitEvent(sa, (cudaEvent_t)ev_fork, 0) != cudaSuccess) return -1;
   if (plan.xs_grid > 0) {
     if (v4) xs_kernel<4><<<plan.xs_grid, BLOCK, 0, sm>>>(p);
     else xs_kernel<1><<<plan.xs_grid, BLOCK, 0, sm>>>(p);
@@ -1114,9 +1124,19 @@ int opfk_iteration_enqueue(const Params &p, const IterPlan &plan, void *main_str
   if (plan.inner_grid > 0) inner_kernel<<<plan.inner_grid, BLOCK, plan.inner_smem, sm>>>(p);
   if (v2) dsum_kernel<2><<<plan.dsum_grid, BLOCK, 0, sm>>>(p);
   else dsum_kernel<1><<<plan.dsum_grid, BLOCK, 0, sm>>>(p);
-  if (plan.line_grid > 0 && cudaStreamWaitEvent(sm, (cudaEvent_t)ev_join, 0) != cudaSuccess) return -1;
-  if (v2) node_kernel<2><<<plan.node_grid, BLOCK, 0, sm>>>(p);
-  else node_kernel<1><<<plan.node_grid, BLOCK, 0, sm>>>(p);
+  for (int s = 0; s < plan.n_slabs; ++s) {
+    const int k0 = s * plan.slab_k, k1 = std::min(p.Kp, k0 + plan.slab_k);
+    if (plan.line_grid > 0 && p.L > 0) {
+      const int lg = (int)(((long long)(k1 - k0) * p.L * (p.T / (v4 ? 4 : 1)) + (long long)BLOCK * LINE_IPT - 1) /
+                           ((long long)BLOCK * LINE_IPT));
+      if (v4) line_kernel<4><<<lg, BLOCK, 0, sa>>>(p, k0, k1);
+      else line_kernel<1><<<lg, BLOCK, 0, sa>>>(p, k0, k1);
+      if (cudaEventRecord((cudaEvent_t)ev_join, sa) != cudaSuccess) return -1;
+      if (cudaStreamWaitEvent(sm, (cudaEvent_t)ev_join, 0) != cudaSuccess) return -1;
+    }
+    if (p.T % NODE_VW == 0) node_kernel<NODE_VW><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
+    else node_kernel<1><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
+  }
   decide_kernel<<<1, BLOCK, 0, sm>>>(p, plan.node_grid);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
