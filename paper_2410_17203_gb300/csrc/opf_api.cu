@@ -253,8 +253,7 @@ void carve(opf_ctx *c, Arena &a) {
   // state first (zeroed on reset)
   for (int b = 0; b < 2; ++b) {
     p.P[b] = a.take<float>(KLT);
-    p.TH1[b] = a.take<float>(KLT);
-    p.TH2[b] = a.take<float>(KLT);
+    p.MID[b] = a.take<float>(KLT);
     p.V1[b] = a.take<float>(KLT);
     p.V2[b] = a.take<float>(KLT);
     p.U[b] = a.take<float>(KNT);

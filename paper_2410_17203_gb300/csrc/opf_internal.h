@@ -9,7 +9,7 @@
 //
 // Device memory layout (structure of arrays, time innermost so that every row
 // of T floats is one contiguous, 16-byte aligned segment when T % 4 == 0):
-//   lines   P, TH1, TH2, V1, V2             2 x [Kp][L][T] float (double buffer)
+//   lines   P, MID, V1, V2                  2 x [Kp][L][T] float (double buffer)
 //   nodes   U, PBAR, THBAR                  2 x [Kp][N][T] float (double buffer)
 //   devices PD, DPD                         [S][T]         float
 //   inner ADMM state of ramp generators     lam, beta [n_ramp][4][T],  q [n_ramp][T]
@@ -61,7 +61,11 @@ struct Params {
   const int *line_n1, *line_n2;  // internal node of terminal 1 (from) and terminal 2 (to)
   const float *line_b, *line_u;
   const int *out_line;  // [Kp], internal index of the outaged line, -1 = none
-  float *P[2], *TH1[2], *TH2[2], *V1[2], *V2[2];  // double-buffered
+  // double-buffered line state: terminal-2 power p, the mean terminal angle
+  // mid (theta_{1,2} = mid +- p / (2b), the line prox keeps theta1 - theta2 =
+  // p / b; the outaged line of a contingency has p = 0 and stores its half
+  // angle difference in p's place), and the phase duals
+  float *P[2], *MID[2], *V1[2], *V2[2];
   // nodes (internal numbering), double-buffered
   float *U[2], *PBAR[2], *THBAR[2];
   // incident lines of each node: x = 2*l + end (end 1: the node is terminal 2), y = other node

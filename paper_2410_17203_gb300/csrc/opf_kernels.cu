@@ -529,8 +529,8 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
   const bool act = p.out_line[k] != l;
   const size_t ol = ((size_t)k * L + l) * T + toff;
   const size_t o1 = ((size_t)k * N + n1) * T + toff, o2 = ((size_t)k * N + n2) * T + toff;
-  // p stays cached: the node sums of the next stage read both its old and new value
-  FV<VW> P = ldv<VW>(p.P[old] + ol), A1 = ldv_cs<VW>(p.TH1[old] + ol), A2 = ldv_cs<VW>(p.TH2[old] + ol);
+  // p stays cached: the node sums read its old value again
+  FV<VW> P = ldv<VW>(p.P[old] + ol), M = ldv_cs<VW>(p.MID[old] + ol);
   FV<VW> V1 = ldv_cs<VW>(p.V1[old] + ol), V2 = ldv_cs<VW>(p.V2[old] + ol);
   const FV<VW> U1 = ldv<VW>(p.U[old] + o1), U2 = ldv<VW>(p.U[old] + o2);
   const FV<VW> B1 = ldv<VW>(p.PBAR[old] + o1), B2 = ldv<VW>(p.PBAR[old] + o2);
@@ -545,31 +545,28 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
   const float rden = __frcp_rn(den), rtb = __frcp_rn(tb);
 #pragma unroll
   for (int e = 0; e < VW; ++e) {
-    const float x1 = -P.v[e] - B1.v[e] - fsu * U1.v[e];     // p~ - u at terminal 1
-    const float x2 = P.v[e] - B2.v[e] - fsu * U2.v[e];      // p~ - u at terminal 2
-    const float v1 = v_fresh ? fsv * V1.v[e] : fsv * (V1.v[e] + (A1.v[e] - G1.v[e]));
-    const float v2 = v_fresh ? fsv * V2.v[e] : fsv * (V2.v[e] + (A2.v[e] - G2.v[e]));
+    // the previous prox's terminal values (stored as p and the mean angle)
+    const float po = act ? P.v[e] : 0.f;
+    const float ho = act ? div_rn(P.v[e], tb, rtb) : P.v[e];
+    const float a1 = M.v[e] + ho, a2 = M.v[e] - ho;
+    const float x1 = -po - B1.v[e] - fsu * U1.v[e];         // p~ - u at terminal 1
+    const float x2 = po - B2.v[e] - fsu * U2.v[e];          // p~ - u at terminal 2
+    const float v1 = v_fresh ? fsv * V1.v[e] : fsv * (V1.v[e] + (a1 - G1.v[e]));
+    const float v2 = v_fresh ? fsv * V2.v[e] : fsv * (V2.v[e] + (a2 - G2.v[e]));
     const float y1 = G1.v[e] - v1, y2 = G2.v[e] - v2;       // theta_bar - v
+    M.v[e] = 0.5f * (y1 + y2);
     if (act) {
       const float num = frp * (x2 - x1) + div_rn(frt * (y1 - y2), tb, rtb);
-      const float pn = fminf(fmaxf(div_rn(num, den, rden), -ulim), ulim);
-      const float mid = 0.5f * (y1 + y2);
-      const float h = div_rn(pn, tb, rtb);
-      P.v[e] = pn;
-      A1.v[e] = mid + h;
-      A2.v[e] = mid - h;
-    } else {  // outaged line: the terminals decouple
-      P.v[e] = 0.f;
-      A1.v[e] = y1;
-      A2.v[e] = y2;
+      P.v[e] = fminf(fmaxf(div_rn(num, den, rden), -ulim), ulim);   // theta_{1,2} = mid +- p / (2b)
+    } else {
+      P.v[e] = 0.5f * (y1 - y2);   // outaged line: p = 0, the terminals decouple, theta = y
     }
     V1.v[e] = v1;
     V2.v[e] = v2;
   }
-  // p and the angles are read back by the next stage's node sums; v is not
+  // p and the mean angle are read back by the node sums; v is not
   stv<VW>(p.P[nw] + ol, P);
-  stv<VW>(p.TH1[nw] + ol, A1);
-  stv<VW>(p.TH2[nw] + ol, A2);
+  stv<VW>(p.MID[nw] + ol, M);
   stv_cs<VW>(p.V1[nw] + ol, V1);
   stv_cs<VW>(p.V2[nw] + ol, V2);
 }
@@ -606,34 +603,43 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
   wth.reset();
 #pragma unroll
   for (int e = 0; e < VW; ++e) st.v[e] = 0.f;
-  // level 2: the rows of the line terminals, four at a time
+  // level 2: the rows of the line terminals, four at a time; a terminal's
+  // angle is mid +- p / (2b) (mid +- the stored value on the outaged line)
   const size_t kb = (size_t)k * L * T + toff;
+  const int lout = p.out_line[k];
   int4 c4 = r1;
   for (int j = r2.x - 4;;) {
     const int code[4] = {c4.x, c4.y, c4.z, c4.w};
-    FV<VW> pn[4], po[4], th[4];
+    FV<VW> pn[4], po[4], mq[4];
+    float bq[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (code[q] >= 0) {
-        const size_t ol = kb + (size_t)(code[q] >> 1) * T;
+        const int l = code[q] >> 1;
+        const size_t ol = kb + (size_t)l * T;
         pn[q] = ldv<VW>(p.P[nw] + ol);
         po[q] = ldv_cs<VW>(p.P[old] + ol);
-        th[q] = ldv<VW>(((code[q] & 1) ? p.TH2[nw] : p.TH1[nw]) + ol);
+        mq[q] = ldv<VW>(p.MID[nw] + ol);
+        bq[q] = p.line_b[l];
       }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (code[q] >= 0) {
-        const bool t2 = code[q] & 1;
-        float dpo[VW];
+        const bool t2 = code[q] & 1, act = (code[q] >> 1) != lout;
+        const float tb = 2.f * bq[q], rtb = __frcp_rn(tb);
+        float dpo[VW], th[VW];
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
-          sp.v[e] += t2 ? pn[q].v[e] : -pn[q].v[e];
-          st.v[e] += th[q].v[e];
-          dpo[e] = t2 ? pn[q].v[e] - po[q].v[e] : po[q].v[e] - pn[q].v[e];
+          const float pv = act ? pn[q].v[e] : 0.f, pov = act ? po[q].v[e] : 0.f;
+          const float h = act ? div_rn(pn[q].v[e], tb, rtb) : pn[q].v[e];
+          th[e] = t2 ? mq[q].v[e] - h : mq[q].v[e] + h;
+          sp.v[e] += t2 ? pv : -pv;
+          st.v[e] += th[e];
+          dpo[e] = t2 ? pv - pov : pov - pv;
         }
         wdp.add(dpo);
-        wth.add(th[q].v);
+        wth.add(th);
       }
     }
     j += 4;
@@ -924,6 +930,23 @@ __global__ void __launch_bounds__(BLOCK) decide_kernel(Params p, int n_part) {
   *p.sc = sc;
 }
 
+// A line's terminal values from its stored (p, mid) at contingency k:
+// p2 (0 on the outaged line) and theta_{1,2} = mid +- h, h = p / (2b) on an
+// active line and the stored value itself on the outaged line.
+__device__ __forceinline__ void line_terminals(const Params &p, int cur, int k, int l, size_t i, float &p2,
+                                               float &th1, float &th2) {
+  const float ps = p.P[cur][i], m = p.MID[cur][i];
+  float h = ps;
+  p2 = 0.f;
+  if (p.out_line[k] != l) {
+    const float tb = 2.f * p.line_b[l];
+    h = div_rn(ps, tb, __frcp_rn(tb));
+    p2 = ps;
+  }
+  th1 = m + h;
+  th2 = m - h;
+}
+
 // ---------------------------------------------------------------------------
 // import / export between internal and caller numbering
 // ---------------------------------------------------------------------------
@@ -938,9 +961,12 @@ __global__ void import_kernel(Params p, int cur, const float *pl, const float *a
       const long long rem = i - (long long)k * L * T;
       const int l = (int)(rem / T), t = (int)(rem % T);
       const size_t src = ((size_t)k * L + p.line_perm[l]) * T + t;
-      p.P[cur][i] = pl ? pl[src] : 0.f;
-      p.TH1[cur][i] = a1 ? a1[src] : 0.f;
-      p.TH2[cur][i] = a2 ? a2[src] : 0.f;
+      // stored as p and the mean angle; the outaged line keeps its half
+      // angle difference in p's place (its p is 0)
+      const float x1 = a1 ? a1[src] : 0.f, x2 = a2 ? a2[src] : 0.f;
+      const bool act = p.out_line[k] != l;
+      p.P[cur][i] = act ? (pl ? pl[src] : 0.f) : 0.5f * (x1 - x2);
+      p.MID[cur][i] = 0.5f * (x1 + x2);
       p.V1[cur][i] = v1 ? v1[src] : 0.f;
       p.V2[cur][i] = v2 ? v2[src] : 0.f;
     } else {
@@ -966,8 +992,10 @@ __global__ void node_average_kernel(Params p, int cur) {
       for (int j = p.lcsr_ptr[n]; j < p.lcsr_ptr[n + 1]; ++j) {
         const int code = p.lcsr[j].x;
         const size_t ol = ((size_t)k * L + (code >> 1)) * T + t;
-        sp += (code & 1) ? p.P[cur][ol] : -p.P[cur][ol];
-        st += (code & 1) ? p.TH2[cur][ol] : p.TH1[cur][ol];
+        float p2, th1, th2;
+        line_terminals(p, cur, k, code >> 1, ol, p2, th1, th2);
+        sp += (code & 1) ? p2 : -p2;
+        st += (code & 1) ? th2 : th1;
       }
       const size_t on = ((size_t)k * N + n) * T + t;
       const float pb = sp / p.cnt_p[n];
@@ -1014,14 +1042,16 @@ __global__ void export_lines_kernel(Params p, int cur, float *pl, float *a1, flo
     const long long rem = i - (long long)k * L * T;
     const int l = (int)(rem / T), t = (int)(rem % T);
     const size_t dst = ((size_t)k * L + p.line_perm[l]) * T + t;
-    if (pl) pl[dst] = p.P[cur][i];
-    if (a1) a1[dst] = p.TH1[cur][i];
-    if (a2) a2[dst] = p.TH2[cur][i];
+    float p2, th1, th2;
+    line_terminals(p, cur, k, l, (size_t)i, p2, th1, th2);
+    if (pl) pl[dst] = p2;
+    if (a1) a1[dst] = th1;
+    if (a2) a2[dst] = th2;
     if (v1 || v2) {
       float x = p.V1[cur][i], y = p.V2[cur][i];
       if (!sc.v_fresh) {
-        x += p.TH1[cur][i] - p.THBAR[cur][((size_t)k * N + p.line_n1[l]) * T + t];
-        y += p.TH2[cur][i] - p.THBAR[cur][((size_t)k * N + p.line_n2[l]) * T + t];
+        x += th1 - p.THBAR[cur][((size_t)k * N + p.line_n1[l]) * T + t];
+        y += th2 - p.THBAR[cur][((size_t)k * N + p.line_n2[l]) * T + t];
       }
       if (v1) v1[dst] = sv * x;
       if (v2) v2[dst] = sv * y;
