@@ -37,14 +37,17 @@ UNIT = "iter/s"
 WORKLOAD = "dcopf-10k-bus-T96-K50"
 KERNEL_SRC = [os.path.join(ROOT, "paper_2410_17203_gb300", "csrc", f)
               for f in ("opf_kernels.cu", "opf_internal.h")]
-PROFILE = os.path.join(ROOT, "profiles", "iteration_kernel_10k.txt")
+PROFILE = os.path.join(ROOT, "profiles", "iteration_10k.txt")
 FALLBACK_HBM_GBS = 6800.0
 
 
 def byte_model(d):
-    """Algorithmic bytes of one iteration: every carried FP32 state element read
-    once and written once -- lines p, theta1, theta2, v1, v2; nodes u, pbar,
-    theta_bar (each [K+1][.][T]); device power [S][T] (read and written)."""
+    """Algorithmic bytes of one iteration: every FP32 element of the method's
+    state (Section 4.4) read once and written once -- lines p, theta1, theta2,
+    v1, v2; nodes u, pbar, theta_bar (each [K+1][.][T]); device power [S][T].
+    The library stores theta1, theta2 as their mean plus p (theta1 - theta2 =
+    p / b after every line prox), so it moves less than this per iteration;
+    the measured DRAM traffic is reported beside it."""
     Kp, T = d["K"] + 1, d["T"]
     return 8 * Kp * T * (5 * d["L"] + 3 * d["N"]) + 8 * d["S"] * T
 
@@ -270,6 +273,7 @@ def ours_arm(args):
     ms = e0.elapsed_time(e1)
     res = opf_residuals(s.h)
     info = s.get_info()
+    kernels_per_iter = int(info["kernels_per_iteration"])
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -346,10 +350,12 @@ def ours_arm(args):
                          "frac": achieved / peak, "peak_source": src,
                          "traffic": (traffic * args.steps if traffic else None),
                          "algorithmic_bytes_per_iteration": B,
-                         "kernel": "opfk::iteration_kernel (one cooperative launch of K iterations)"},
+                         "kernel": "one iteration: xs, inner, dsum, line, node and decide kernels "
+                                   "replayed from CUDA graphs (unit = iteration; per-kernel shares in "
+                                   "profiles/iteration_10k.txt)"},
             "variable_updates_per_s": value * variables_per_iter(d),
             "e2e": e2e,
-            "gpu_launches": 1,
+            "gpu_launches": kernels_per_iter * args.steps,
             "clocks": ck,
             "residuals": [float(x) for x in res],
             "rho": [info["rho_p"], info["rho_theta"]],

@@ -141,6 +141,8 @@ typedef struct {
    * delta <= P (T), -delta <= 0 (T), s <= dur P (T+1), -s <= 0 (T+1)]. */
   int64_t inner_len;
   int64_t device_bytes;     /* device memory held by the context */
+  int32_t kernels_per_iteration; /* kernel launches one iteration makes */
+  int32_t reserved1;
 } opf_info;
 
 /* Fill `opt` with the defaults listed above. */

@@ -71,6 +71,7 @@ class opf_info(C.Structure):
         ("N", C.c_int32), ("L", C.c_int32), ("S", C.c_int32), ("T", C.c_int32),
         ("K", C.c_int32), ("J", C.c_int32), ("n_ramp", C.c_int32), ("n_stor", C.c_int32),
         ("inner_len", C.c_int64), ("device_bytes", C.c_int64),
+        ("kernels_per_iteration", C.c_int32), ("reserved1", C.c_int32),
     ]
 
 

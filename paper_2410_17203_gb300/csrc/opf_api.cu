@@ -791,6 +791,11 @@ opf_status opf_get_info(opf_ctx *c, opf_info *info) {
   info->rho_p = sc.rho_p;
   info->rho_theta = sc.rho_th;
   info->tolerance = c->tol;
+  {
+    const opfk::IterPlan &pl = c->plan;
+    info->kernels_per_iteration = (pl.xs_grid > 0) + (pl.inner_grid > 0) + 1 +
+                                  pl.n_slabs * ((pl.line_grid > 0 && c->L > 0) + 1) + 1;
+  }
   info->N = c->N;
   info->L = c->L;
   info->S = c->S;
