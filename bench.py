@@ -283,6 +283,74 @@ def time_to_tolerance(case, stream, args):
     return out
 
 
+def batch_instances(n, seed=3):
+    """The batched workload: n independent instances, buses log-uniform in
+    [100, 5000], T uniform in {1, 24, 48}, 0..20 outages, the device mix of the
+    other workloads (generators N/4, loads 3N/4, batteries N/20, lines 1.5 N)."""
+    import numpy as np
+    from gridgen import make_case, scale_case
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nb = int(round(float(np.exp(rng.uniform(np.log(100), np.log(5000))))))
+        T = int(rng.choice([1, 24, 48]))
+        K = int(rng.integers(0, 21))
+        out.append(make_case(scale_case(nb, T, K, seed=1000 + i, lines_per_node=1.5)))
+    return out
+
+
+def batched_vs_plain(stream, args):
+    """Solve every instance to eps = 1e-4: one after another through
+    opf_iterate (plain), and all at once through one batch graph."""
+    import torch
+    from paper_2410_17203_gb300 import (opf_batch_converged, opf_batch_create, opf_batch_destroy,
+                                        opf_batch_iterate, opf_create, opf_destroy, opf_get_info,
+                                        opf_iterate, opf_reset)
+    cases = batch_instances(args.batched)
+    opts = dict(adapt_every=10, eps=1e-4)
+    chunk = args.ttt_chunk
+    plain = [opf_create(c, opts, stream=stream.cuda_stream) for c in cases]
+    batch = [opf_create(c, opts, stream=stream.cuda_stream) for c in cases]
+    b = opf_batch_create(batch)
+    # build every graph once, then start from zero again
+    for h in plain:
+        opf_iterate(h, 17)
+    opf_batch_iterate(b, 17)
+    torch.cuda.synchronize()
+    for h in plain + batch:
+        opf_reset(h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its_plain = []
+    for h in plain:
+        done = 0
+        while done < args.ttt_max:
+            opf_iterate(h, chunk)
+            done += chunk
+            if opf_get_info(h)["converged"]:
+                break
+        its_plain.append(int(opf_get_info(h)["iterations"]))
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    done = 0
+    while done < args.ttt_max:
+        opf_batch_iterate(b, chunk)
+        done += chunk
+        if opf_batch_converged(b) == len(batch):
+            break
+    t_batch = time.perf_counter() - t0
+    its_batch = [int(opf_get_info(h)["iterations"]) for h in batch]
+    n_conv = opf_batch_converged(b)
+    opf_batch_destroy(b)
+    for h in plain + batch:
+        opf_destroy(h)
+    return {"instances": len(cases), "eps": 1e-4,
+            "plain_seconds": t_plain, "batched_seconds": t_batch, "speedup": t_plain / t_batch,
+            "converged_batched": n_conv, "iterations_total": int(sum(its_plain)),
+            "iterations_equal": its_plain == its_batch,
+            "workload": "buses log-uniform [100, 5000], T in {1, 24, 48}, K in 0..20, seed 3"}
+
+
 def ours_arm(args):
     import numpy as np
     import torch
@@ -369,6 +437,9 @@ def ours_arm(args):
     ttt = None
     if args.ttt and rank == 0:
         ttt = time_to_tolerance(case, stream, args)
+    batched = None
+    if args.batched > 0 and rank == 0:
+        batched = batched_vs_plain(stream, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -408,6 +479,8 @@ def ours_arm(args):
             line["cpu_baseline"] = cpu
         if ttt:
             line["time_to_tolerance"] = ttt
+        if batched:
+            line["batched_vs_plain"] = batched
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -427,6 +500,8 @@ def main():
                     help="skip the solves to eps = 1e-4 (cold, perturbed cold, perturbed warm)")
     ap.add_argument("--ttt-max", type=int, default=30000)
     ap.add_argument("--ttt-chunk", type=int, default=100)
+    ap.add_argument("--batched", type=int, default=0,
+                    help="also solve this many independent instances to eps = 1e-4, one by one and as one batch")
     ap.add_argument("--_oracle-child", dest="oracle_child", default=None)
     args = ap.parse_args()
     if args.oracle_child:

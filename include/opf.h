@@ -204,6 +204,25 @@ opf_status opf_solution(opf_ctx *ctx, int32_t on_device, double *objective, floa
 #define OPF_PRICE_SCRATCH_FLOATS (1 << 20)
 opf_status opf_price_noalloc(opf_ctx *ctx, float *price);
 
+/* Batched iteration of independent instances (the batch solver of the
+ * expansion-planning application, Section 5.6).  A batch groups existing
+ * contexts of the current device (the caller keeps owning them; each keeps
+ * its own state, options and stream) and captures every instance's
+ * iteration kernels as independent
+ * branches of one CUDA graph, so a batch step is one graph launch.
+ * opf_batch_iterate enqueues n_iters iterations of every instance after the
+ * work already queued on each instance's stream, and orders each stream
+ * after it.  Unlike opf_iterate it does not restart an instance that has
+ * stopped (passed stopping test or error): such an instance's kernels return
+ * at once, so a batch can be iterated until every instance has converged.
+ * opf_batch_converged counts the converged instances (synchronizes).  The
+ * contexts must outlive the batch. */
+typedef struct opf_batch opf_batch;
+opf_status opf_batch_create(opf_ctx *const *ctxs, int32_t n, opf_batch **out);
+opf_status opf_batch_iterate(opf_batch *batch, int32_t n_iters);
+opf_status opf_batch_converged(opf_batch *batch, int32_t *n_converged);
+void opf_batch_destroy(opf_batch *batch);
+
 /* Export / import the full state (warm start, checkpoint and resume,
  * Section 3.4).  Import recomputes the node averages from p and theta and
  * projects v onto v_bar = 0 per node (Appendix C); it clears a sticky

@@ -77,7 +77,8 @@ class opf_info(C.Structure):
 
 EXPORTS = ["opf_default_options", "opf_create", "opf_iterate", "opf_residuals", "opf_solution",
            "opf_price_noalloc", "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info",
-           "opf_destroy", "opf_status_str", "opf_last_error", "opf_abi_version"]
+           "opf_destroy", "opf_status_str", "opf_last_error", "opf_abi_version",
+           "opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_destroy"]
 
 _lib = None
 
@@ -112,6 +113,13 @@ def load_library(path=None):
     lib.opf_last_error.restype = C.c_char_p
     lib.opf_abi_version.argtypes = []
     lib.opf_abi_version.restype = C.c_int32
+    lib.opf_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]
+    lib.opf_batch_iterate.argtypes = [C.c_void_p, C.c_int32]
+    lib.opf_batch_converged.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+    lib.opf_batch_destroy.argtypes = [C.c_void_p]
+    lib.opf_batch_destroy.restype = None
+    for name in ("opf_batch_create", "opf_batch_iterate", "opf_batch_converged"):
+        getattr(lib, name).restype = C.c_int
     for name in ("opf_create", "opf_iterate", "opf_residuals", "opf_solution", "opf_price_noalloc",
                  "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info"):
         getattr(lib, name).restype = C.c_int
@@ -254,6 +262,29 @@ def opf_price_noalloc(h, out=None):
         raise ValueError("out must be a C-contiguous float32 NumPy array")
     _check(load_library().opf_price_noalloc(h, _addr(out)), "opf_price_noalloc")
     return out
+
+
+def opf_batch_create(handles):
+    """A batch over existing context handles (they must outlive it)."""
+    arr = (C.c_void_p * len(handles))(*handles)
+    out = C.c_void_p()
+    _check(load_library().opf_batch_create(arr, len(handles), C.byref(out)), "opf_batch_create")
+    return out
+
+
+def opf_batch_iterate(b, n_iters):
+    _check(load_library().opf_batch_iterate(b, int(n_iters)), "opf_batch_iterate")
+
+
+def opf_batch_converged(b):
+    n = C.c_int32(0)
+    _check(load_library().opf_batch_converged(b, C.byref(n)), "opf_batch_converged")
+    return n.value
+
+
+def opf_batch_destroy(b):
+    if b:
+        load_library().opf_batch_destroy(b)
 
 
 STATE_FIELDS = ("p_line", "th1", "th2", "v1", "v2", "p_dev", "u", "inner")

@@ -922,6 +922,131 @@ opf_status opf_solution(opf_ctx *c, int32_t on_device, double *objective, float 
   return (opf_status)sc.status;
 }
 
+}  // extern "C"
+
+struct opf_batch {
+  std::vector<opf_ctx *> ctx;
+  int device = 0;
+  cudaStream_t stream = nullptr;             // the batch graph runs here
+  cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
+  std::vector<cudaEvent_t> ev_join;          // one per instance
+  cudaGraphExec_t g_one = nullptr, g_many = nullptr;
+};
+
+namespace {
+
+void release_batch(opf_batch *b) {
+  if (b->g_one) cudaGraphExecDestroy(b->g_one);
+  if (b->g_many) cudaGraphExecDestroy(b->g_many);
+  for (cudaEvent_t e : b->ev_join)
+    if (e) cudaEventDestroy(e);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_done) cudaEventDestroy(b->ev_done);
+  if (b->stream) cudaStreamDestroy(b->stream);
+}
+
+// All instances' iterations as independent branches of one graph: the batch
+// stream forks into every instance's streams and joins them again.
+opf_status build_batch_graph(opf_batch *b, int iters, cudaGraphExec_t *out) {
+  CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  bool ok = cudaEventRecord(b->ev_fork, b->stream) == cudaSuccess;
+  for (size_t i = 0; ok && i < b->ctx.size(); ++i) {
+    opf_ctx *c = b->ctx[i];
+    ok = cudaStreamWaitEvent(c->s_main, b->ev_fork, 0) == cudaSuccess;
+    for (int it = 0; ok && it < iters; ++it)
+      ok = opfk_iteration_enqueue(c->P, c->plan, c->s_main, c->s_aux, c->ev_fork, c->ev_join) == 0;
+    ok = ok && cudaEventRecord(b->ev_join[i], c->s_main) == cudaSuccess &&
+         cudaStreamWaitEvent(b->stream, b->ev_join[i], 0) == cudaSuccess;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (!ok || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return ok ? cuda_fail(e, "cudaStreamEndCapture(batch)") : fail(OPF_ECUDA, "batch graph capture failed");
+  }
+  const cudaError_t ei = cudaGraphInstantiateWithFlags(out, g, cudaGraphInstantiateFlagUseNodePriority);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate(batch)");
+  return OPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+opf_status opf_batch_create(opf_ctx *const *ctxs, int32_t n, opf_batch **out) {
+  if (!out) return fail(OPF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctxs || n < 1) return fail(OPF_EINVAL, "a batch needs at least one context");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(OPF_EINVAL, "NULL context in batch");
+    if (ctxs[i]->device != dev) return fail(OPF_EINVAL, "batch contexts must be on the current device");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(OPF_EINVAL, "a context appears twice in the batch");
+  }
+  auto *b = new (std::nothrow) opf_batch();
+  if (!b) return fail(OPF_ENOMEM, "host allocation failed");
+  b->ctx.assign(ctxs, ctxs + n);
+  b->device = dev;
+  b->ev_join.assign(n, nullptr);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
+  for (int i = 0; e == cudaSuccess && i < n; ++i) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    const opf_status s = cuda_fail(e, "batch stream / event creation");
+    release_batch(b);
+    delete b;
+    return s;
+  }
+  *out = b;
+  return OPF_OK;
+}
+
+opf_status opf_batch_iterate(opf_batch *b, int32_t n_iters) {
+  if (!b) return fail(OPF_EINVAL, "batch is NULL");
+  if (n_iters < 0) return fail(OPF_EINVAL, "n_iters must be >= 0");
+  if (n_iters == 0) return OPF_OK;
+  if (!b->g_one) {
+    opf_status gs = build_batch_graph(b, 1, &b->g_one);
+    if (gs == OPF_OK) gs = build_batch_graph(b, kGraphIters, &b->g_many);
+    if (gs != OPF_OK) return gs;
+  }
+  // after each instance's queued work ...
+  for (opf_ctx *c : b->ctx) {
+    CK(cudaEventRecord(c->ev_in, c->stream));
+    CK(cudaStreamWaitEvent(b->stream, c->ev_in, 0));
+  }
+  for (int i = 0; i < n_iters / kGraphIters; ++i) CK(cudaGraphLaunch(b->g_many, b->stream));
+  for (int i = 0; i < n_iters % kGraphIters; ++i) CK(cudaGraphLaunch(b->g_one, b->stream));
+  // ... and before its later work
+  CK(cudaEventRecord(b->ev_done, b->stream));
+  for (opf_ctx *c : b->ctx) CK(cudaStreamWaitEvent(c->stream, b->ev_done, 0));
+  return OPF_OK;
+}
+
+opf_status opf_batch_converged(opf_batch *b, int32_t *n_converged) {
+  if (!b || !n_converged) return fail(OPF_EINVAL, "NULL argument");
+  int32_t n = 0;
+  for (opf_ctx *c : b->ctx) {
+    DevScalars sc;
+    const opf_status s = read_scalars(c, &sc);
+    if (s != OPF_OK) return s;
+    n += sc.converged ? 1 : 0;
+  }
+  *n_converged = n;
+  return OPF_OK;
+}
+
+void opf_batch_destroy(opf_batch *b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  release_batch(b);
+  delete b;
+}
+
 opf_status opf_price_noalloc(opf_ctx *c, float *price) {
   if (!c || !price) return fail(OPF_EINVAL, "NULL argument");
   const size_t NT = (size_t)c->N * c->T;
