@@ -653,6 +653,7 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   p.n_dnode = c->n_dnode;
   p.n_ramp = c->n_ramp;
   p.n_stor = c->n_stor;
+  p.node_grid = c->plan.node_grid;
   p.eps = opt.eps;
   p.mu = opt.mu;
   p.gamma = opt.gamma;
@@ -927,9 +928,14 @@ opf_status opf_solution(opf_ctx *c, int32_t on_device, double *objective, float 
 struct opf_batch {
   std::vector<opf_ctx *> ctx;
   int device = 0;
-  cudaStream_t stream = nullptr;             // the batch graph runs here
-  cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
-  std::vector<cudaEvent_t> ev_join;          // one per instance
+  // the batch kernels run on these two streams (main: devices, node sums,
+  // decisions; aux: line proxes); every instance's parameters and the CTA
+  // schedules of the batch kernels live in device memory
+  cudaStream_t stream = nullptr, s_aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr;
+  opfk::Params *d_params = nullptr;
+  int *d_sched = nullptr;
+  opfk::BatchPlan plan{};
   cudaGraphExec_t g_one = nullptr, g_many = nullptr;
 };
 
@@ -938,26 +944,21 @@ namespace {
 void release_batch(opf_batch *b) {
   if (b->g_one) cudaGraphExecDestroy(b->g_one);
   if (b->g_many) cudaGraphExecDestroy(b->g_many);
-  for (cudaEvent_t e : b->ev_join)
+  for (cudaEvent_t e : {b->ev_fork, b->ev_join, b->ev_done})
     if (e) cudaEventDestroy(e);
-  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-  if (b->ev_done) cudaEventDestroy(b->ev_done);
   if (b->stream) cudaStreamDestroy(b->stream);
+  if (b->s_aux) cudaStreamDestroy(b->s_aux);
+  if (b->d_params) cudaFree(b->d_params);
+  if (b->d_sched) cudaFree(b->d_sched);
 }
 
-// All instances' iterations as independent branches of one graph: the batch
-// stream forks into every instance's streams and joins them again.
+// `iters` iterations of every instance as one graph: per iteration one
+// launch per batch kernel (and width), whatever the number of instances.
 opf_status build_batch_graph(opf_batch *b, int iters, cudaGraphExec_t *out) {
   CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-  bool ok = cudaEventRecord(b->ev_fork, b->stream) == cudaSuccess;
-  for (size_t i = 0; ok && i < b->ctx.size(); ++i) {
-    opf_ctx *c = b->ctx[i];
-    ok = cudaStreamWaitEvent(c->s_main, b->ev_fork, 0) == cudaSuccess;
-    for (int it = 0; ok && it < iters; ++it)
-      ok = opfk_iteration_enqueue(c->P, c->plan, c->s_main, c->s_aux, c->ev_fork, c->ev_join) == 0;
-    ok = ok && cudaEventRecord(b->ev_join[i], c->s_main) == cudaSuccess &&
-         cudaStreamWaitEvent(b->stream, b->ev_join[i], 0) == cudaSuccess;
-  }
+  bool ok = true;
+  for (int it = 0; ok && it < iters; ++it)
+    ok = opfk_batch_enqueue(b->d_params, b->d_sched, b->plan, b->stream, b->s_aux, b->ev_fork, b->ev_join) == 0;
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
   if (!ok || e != cudaSuccess) {
@@ -990,16 +991,36 @@ opf_status opf_batch_create(opf_ctx *const *ctxs, int32_t n, opf_batch **out) {
   if (!b) return fail(OPF_ENOMEM, "host allocation failed");
   b->ctx.assign(ctxs, ctxs + n);
   b->device = dev;
-  b->ev_join.assign(n, nullptr);
-  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
-  for (int i = 0; e == cudaSuccess && i < n; ++i) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
-  if (e != cudaSuccess) {
-    const opf_status s = cuda_fail(e, "batch stream / event creation");
+  std::vector<Params> hp(n);
+  std::vector<opfk::IterPlan> plans(n);
+  for (int i = 0; i < n; ++i) {
+    hp[i] = ctxs[i]->P;
+    plans[i] = ctxs[i]->plan;
+  }
+  long long len = 0;
+  opf_status st = OPF_OK;
+  if (opfk_batch_plan(hp.data(), plans.data(), n, nullptr, 0, &len, &b->plan) != 0)
+    st = fail(OPF_ECUDA, "batch schedule");
+  std::vector<int> sched(4 * (size_t)std::max(len, 1LL));
+  if (st == OPF_OK && opfk_batch_plan(hp.data(), plans.data(), n, sched.data(), len, &len, &b->plan) != 0)
+    st = fail(OPF_ECUDA, "batch schedule");
+  int lo = 0, hi = 0;
+  cudaError_t e = st == OPF_OK ? cudaDeviceGetStreamPriorityRange(&lo, &hi) : cudaSuccess;
+  if (st == OPF_OK) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->stream, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->s_aux, cudaStreamNonBlocking, lo);
+    for (cudaEvent_t *ev : {&b->ev_fork, &b->ev_join, &b->ev_done})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_params, n * sizeof(Params));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sched, sched.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_params, hp.data(), n * sizeof(Params), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_sched, sched.data(), sched.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = cuda_fail(e, "batch set-up");
+  }
+  if (st != OPF_OK) {
     release_batch(b);
     delete b;
-    return s;
+    return st;
   }
   *out = b;
   return OPF_OK;

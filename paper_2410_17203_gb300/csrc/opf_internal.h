@@ -105,6 +105,7 @@ struct Params {
   const int *node_perm, *line_perm;
   // scratch
   double *partials;  // [node_grid][NSLOT] per-CTA residual partial sums of the node kernel
+  int node_grid;     // CTAs of the node kernel (partial-sum slots)
   DevScalars *sc;
   // options
   double eps, mu, gamma, tol;
@@ -115,6 +116,17 @@ struct Params {
 struct IterPlan {
   int line_grid, node_grid, xs_grid, inner_grid, dsum_grid;  // 0: the kernel has no work
   int n_slabs, slab_k;  // contingency slabs of the line / node kernels, slab_k contingencies each
+  size_t inner_smem;
+};
+
+// A batch of instances: the CTA schedules of each batch kernel, concatenated
+// in one array of (instance, block within the instance, blocks of the
+// instance, 0), in the order of BatchKernel.
+enum BatchKernel { BK_XS4, BK_XS1, BK_INNER, BK_DSUM2, BK_DSUM1, BK_LINE4, BK_LINE1, BK_NODE4, BK_NODE1,
+                   BK_DECIDE, BK_COUNT };
+struct BatchPlan {
+  int count[BK_COUNT];
+  int offset[BK_COUNT];
   size_t inner_smem;
 };
 
@@ -130,6 +142,14 @@ int opfk_plan(const opfk::Params &p, opfk::IterPlan *plan);
 // capture.
 int opfk_iteration_enqueue(const opfk::Params &p, const opfk::IterPlan &plan, void *main_stream,
                            void *aux_stream, void *ev_fork, void *ev_join);
+// Schedules of the batch kernels for n instances (host parameter copies and
+// their plans): fills sched (4 ints per CTA, BatchPlan order) and the plan.
+int opfk_batch_plan(const opfk::Params *hp, const opfk::IterPlan *plans, int n, int *sched_out,
+                    long long sched_cap, long long *sched_len, opfk::BatchPlan *bp);
+// Enqueue one iteration of every instance: d_params [n] and d_sched on the
+// device; the same stream and event roles as opfk_iteration_enqueue.
+int opfk_batch_enqueue(const opfk::Params *d_params, const int *d_sched, const opfk::BatchPlan &bp,
+                       void *main_stream, void *aux_stream, void *ev_fork, void *ev_join);
 // State import / export between internal and caller numbering; `cur` selects
 // the node buffer holding the current state.
 int opfk_import_launch(const opfk::Params &p, int cur, const float *p_line, const float *th1,

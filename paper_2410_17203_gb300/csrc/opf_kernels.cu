@@ -704,7 +704,7 @@ __device__ __forceinline__ Iter iter_scalars(const Params &p) {
 // (Section 4.2), nodes with inner-ADMM devices keep the average in XS
 // ---------------------------------------------------------------------------
 template <int VW>
-__global__ void __launch_bounds__(BLOCK) xs_kernel(Params p) {
+__device__ __forceinline__ void xs_body(const Params &p, unsigned bid, unsigned nblk) {
   const Iter q = iter_scalars(p);
   if (q.skip) return;
   const int T = p.T, TV = T / VW, Kp = p.Kp;
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(BLOCK) xs_kernel(Params p) {
   const size_t NT = (size_t)p.N * T;
   const float *Uo = p.U[q.old], *Bo = p.PBAR[q.old];
   const unsigned n_xv = (unsigned)p.n_dnode * (unsigned)TV;
-  for (unsigned item = blockIdx.x * BLOCK + threadIdx.x; item < n_xv; item += gridDim.x * BLOCK) {
+  for (unsigned item = bid * BLOCK + threadIdx.x; item < n_xv; item += nblk * BLOCK) {
     const int ci = (int)(item / (unsigned)TV), t0 = (int)(item % (unsigned)TV) * VW;
     const size_t on = (size_t)p.dnode_ids[ci] * T + t0;
     FV<VW> xs;
@@ -750,8 +750,7 @@ __global__ void __launch_bounds__(BLOCK) xs_kernel(Params p) {
 // ---------------------------------------------------------------------------
 // inner: one warp per battery, then per ramp-limited generator (Appendix D)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(BLOCK) inner_kernel(Params p) {
-  extern __shared__ float smem[];
+__device__ __forceinline__ void inner_body(const Params &p, unsigned bid, unsigned nblk, float *smem) {
   const Iter q = iter_scalars(p);
   if (q.skip) return;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -759,7 +758,7 @@ __global__ void __launch_bounds__(BLOCK) inner_kernel(Params p) {
   float *wsm = smem + (size_t)wib * wfl;
   float *state_sh = (wfl > 3 * (p.T + 1)) ? wsm + 3 * (p.T + 1) : nullptr;
   const int n_inner = p.n_stor + p.n_ramp;
-  for (int w = blockIdx.x * WARPS + wib; w < n_inner; w += gridDim.x * WARPS) {
+  for (int w = bid * WARPS + wib; w < n_inner; w += nblk * WARPS) {
     if (w < p.n_stor)
       stor_prox(p, w, q.rho_dev, wsm, state_sh, lane);
     else
@@ -773,12 +772,12 @@ __global__ void __launch_bounds__(BLOCK) inner_kernel(Params p) {
 // every contingency start from it)
 // ---------------------------------------------------------------------------
 template <int VW>
-__global__ void __launch_bounds__(BLOCK) dsum_kernel(Params p) {
+__device__ __forceinline__ void dsum_body(const Params &p, unsigned bid, unsigned nblk) {
   const Iter q = iter_scalars(p);
   if (q.skip) return;
   const int T = p.T, TV = T / VW;
   const unsigned n_items = (unsigned)p.N * (unsigned)TV;
-  for (unsigned item = blockIdx.x * BLOCK + threadIdx.x; item < n_items; item += gridDim.x * BLOCK) {
+  for (unsigned item = bid * BLOCK + threadIdx.x; item < n_items; item += nblk * BLOCK) {
     const int n = (int)(item / (unsigned)TV), t0 = (int)(item % (unsigned)TV) * VW;
     FV<VW> sp;
     Welf<VW> w;
@@ -806,14 +805,14 @@ __global__ void __launch_bounds__(BLOCK) dsum_kernel(Params p) {
 // line: step 1 for every (contingency, line, VW time steps)
 // ---------------------------------------------------------------------------
 template <int VW>
-__global__ void __launch_bounds__(BLOCK, 4) line_kernel(Params p, int k0, int k1) {
+__device__ __forceinline__ void line_body(const Params &p, int k0, int k1, unsigned bid) {
   const Iter q = iter_scalars(p);
   if (q.skip) return;
   const int L = p.L, TV = p.T / VW;
   const unsigned n = (unsigned)(k1 - k0) * (unsigned)L * (unsigned)TV;
   // each CTA takes LINE_IPT consecutive blocks of BLOCK items, so CTAs are
   // short-lived and the device kernels' CTAs find room beside them
-  const unsigned base = blockIdx.x * (unsigned)(BLOCK * LINE_IPT) + threadIdx.x;
+  const unsigned base = bid * (unsigned)(BLOCK * LINE_IPT) + threadIdx.x;
   Idx3 ix, dx;
   ix.set(base, L, TV);
   dx.set(BLOCK, L, TV);
@@ -829,15 +828,16 @@ __global__ void __launch_bounds__(BLOCK, 4) line_kernel(Params p, int k0, int k1
 // residual partial sums: FP32 per thread, FP64 across warps
 // ---------------------------------------------------------------------------
 template <int VW>
-__global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel(Params p, int k0, int k1, int first) {
+__device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int first, unsigned bid,
+                                          unsigned nblk) {
   __shared__ double red[WARPS][NSLOT];
   const Iter q = iter_scalars(p);
   if (q.skip) return;
   const int N = p.N, TV = p.T / VW;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned n = (unsigned)(k1 - k0) * (unsigned)N * (unsigned)TV;
-  const unsigned stride = gridDim.x * BLOCK;
-  unsigned item = blockIdx.x * BLOCK + threadIdx.x;
+  const unsigned stride = nblk * BLOCK;
+  unsigned item = bid * BLOCK + threadIdx.x;
   float acc[NSLOT] = {0.f, 0.f, 0.f, 0.f, 0.f};
   Idx3 ix, dx;
   ix.set(item, N, TV);
@@ -855,9 +855,9 @@ __global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel(Params p, in
   // the slabs of one iteration run in order on one stream: the first one
   // sets the CTA's partial sums, the others add to them
   if (threadIdx.x < NSLOT) {
-    double v = first ? 0.0 : p.partials[(size_t)blockIdx.x * NSLOT + threadIdx.x];
+    double v = first ? 0.0 : p.partials[(size_t)bid * NSLOT + threadIdx.x];
     for (int w = 0; w < WARPS; ++w) v += red[w][threadIdx.x];
-    p.partials[(size_t)blockIdx.x * NSLOT + threadIdx.x] = v;
+    p.partials[(size_t)bid * NSLOT + threadIdx.x] = v;
   }
 }
 
@@ -866,7 +866,7 @@ __global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel(Params p, in
 // in FP64 and a fixed order, the stopping test of Eq. (converge) and the
 // adaptive penalty (Section 3.5); advances the iteration counter.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(BLOCK) decide_kernel(Params p, int n_part) {
+__device__ __forceinline__ void decide_body(const Params &p, int n_part) {
   __shared__ double red[WARPS][NSLOT];
   const Iter q = iter_scalars(p);
   if (q.skip) return;
@@ -928,6 +928,97 @@ __global__ void __launch_bounds__(BLOCK) decide_kernel(Params p, int n_part) {
   sc.it = itn;
   sc.v_fresh = 0;
   *p.sc = sc;
+}
+
+// ---------------------------------------------------------------------------
+// kernel entry points: one instance (parameters in the constant bank), or a
+// batch of instances (each CTA looks up its instance, its block index within
+// the instance and the instance's block count in a schedule, and works on a
+// shared-memory copy of that instance's parameters)
+// ---------------------------------------------------------------------------
+template <int VW>
+__global__ void __launch_bounds__(BLOCK) xs_kernel(Params p) { xs_body<VW>(p, blockIdx.x, gridDim.x); }
+
+__global__ void __launch_bounds__(BLOCK) inner_kernel(Params p) {
+  extern __shared__ float smem[];
+  inner_body(p, blockIdx.x, gridDim.x, smem);
+}
+
+template <int VW>
+__global__ void __launch_bounds__(BLOCK) dsum_kernel(Params p) { dsum_body<VW>(p, blockIdx.x, gridDim.x); }
+
+template <int VW>
+__global__ void __launch_bounds__(BLOCK, 4) line_kernel(Params p, int k0, int k1) {
+  line_body<VW>(p, k0, k1, blockIdx.x);
+}
+
+template <int VW>
+__global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel(Params p, int k0, int k1, int first) {
+  node_body<VW>(p, k0, k1, first, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(BLOCK) decide_kernel(Params p, int n_part) { decide_body(p, n_part); }
+
+// the instance of this CTA: its parameters copied to shared memory, and
+// (block, blocks) within the instance
+__device__ __forceinline__ const Params &batch_params(const Params *ps, const int4 *sched, Params &sp,
+                                                      unsigned &bid, unsigned &nblk) {
+  const int4 e = sched[blockIdx.x];
+  static_assert(sizeof(Params) % 4 == 0, "Params is copied as 32-bit words");
+  const int *src = reinterpret_cast<const int *>(ps + e.x);
+  int *dst = reinterpret_cast<int *>(&sp);
+  for (int i = threadIdx.x; i < (int)(sizeof(Params) / 4); i += BLOCK) dst[i] = src[i];
+  __syncthreads();
+  bid = (unsigned)e.y;
+  nblk = (unsigned)e.z;
+  return sp;
+}
+
+template <int VW>
+__global__ void __launch_bounds__(BLOCK) xs_kernel_b(const Params *ps, const int4 *sched) {
+  __shared__ Params sp;
+  unsigned bid, nblk;
+  const Params &p = batch_params(ps, sched, sp, bid, nblk);
+  xs_body<VW>(p, bid, nblk);
+}
+
+__global__ void __launch_bounds__(BLOCK) inner_kernel_b(const Params *ps, const int4 *sched) {
+  extern __shared__ float smem[];
+  __shared__ Params sp;
+  unsigned bid, nblk;
+  const Params &p = batch_params(ps, sched, sp, bid, nblk);
+  inner_body(p, bid, nblk, smem);
+}
+
+template <int VW>
+__global__ void __launch_bounds__(BLOCK) dsum_kernel_b(const Params *ps, const int4 *sched) {
+  __shared__ Params sp;
+  unsigned bid, nblk;
+  const Params &p = batch_params(ps, sched, sp, bid, nblk);
+  dsum_body<VW>(p, bid, nblk);
+}
+
+template <int VW>
+__global__ void __launch_bounds__(BLOCK, 4) line_kernel_b(const Params *ps, const int4 *sched) {
+  __shared__ Params sp;
+  unsigned bid, nblk;
+  const Params &p = batch_params(ps, sched, sp, bid, nblk);
+  line_body<VW>(p, 0, p.Kp, bid);
+}
+
+template <int VW>
+__global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel_b(const Params *ps, const int4 *sched) {
+  __shared__ Params sp;
+  unsigned bid, nblk;
+  const Params &p = batch_params(ps, sched, sp, bid, nblk);
+  node_body<VW>(p, 0, p.Kp, 1, bid, nblk);
+}
+
+__global__ void __launch_bounds__(BLOCK) decide_kernel_b(const Params *ps, const int4 *sched) {
+  __shared__ Params sp;
+  unsigned bid, nblk;
+  const Params &p = batch_params(ps, sched, sp, bid, nblk);
+  decide_body(p, p.node_grid);
 }
 
 // A line's terminal values from its stored (p, mid) at contingency k:
@@ -1168,6 +1259,91 @@ int opfk_iteration_enqueue(const Params &p, const IterPlan &plan, void *main_str
     else node_kernel<1><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
   }
   decide_kernel<<<1, BLOCK, 0, sm>>>(p, plan.node_grid);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, int *sched_out, long long sched_cap,
+                    long long *sched_len, BatchPlan *bp) {
+  long long len = 0;
+  size_t ism = 0;
+  auto add = [&](int kind_unused, int inst, long long blocks) -> bool {
+    (void)kind_unused;
+    for (long long b = 0; b < blocks; ++b) {
+      if (sched_out) {
+        if (len >= sched_cap) return false;
+        int *e = sched_out + 4 * len;
+        e[0] = inst;
+        e[1] = (int)b;
+        e[2] = (int)blocks;
+        e[3] = 0;
+      }
+      ++len;
+    }
+    return true;
+  };
+  for (int kind = 0; kind < BK_COUNT; ++kind) {
+    bp->offset[kind] = (int)len;
+    for (int i = 0; i < n; ++i) {
+      const Params &p = hp[i];
+      const bool v4 = (p.T % 4 == 0), v2 = (p.T % 2 == 0), vn = (p.T % NODE_VW == 0);
+      const long long tv4 = p.T / (v4 ? 4 : 1), tvn = p.T / (vn ? NODE_VW : 1), tv2 = p.T / (v2 ? 2 : 1);
+      const int n_inner = p.n_stor + p.n_ramp;
+      long long blocks = 0;
+      switch (kind) {
+        case BK_XS4: case BK_XS1:
+          if ((kind == BK_XS4) == v4) blocks = ((long long)p.n_dnode * tv4 + BLOCK - 1) / BLOCK;
+          break;
+        case BK_INNER:
+          blocks = (n_inner + WARPS - 1) / WARPS;
+          if (blocks) ism = std::max(ism, inner_smem(p.T));
+          break;
+        case BK_DSUM2: case BK_DSUM1:
+          if ((kind == BK_DSUM2) == v2) blocks = ((long long)p.N * tv2 + BLOCK - 1) / BLOCK;
+          break;
+        case BK_LINE4: case BK_LINE1:
+          if ((kind == BK_LINE4) == v4 && p.L > 0)
+            blocks = ((long long)p.Kp * p.L * tv4 + (long long)BLOCK * LINE_IPT - 1) / ((long long)BLOCK * LINE_IPT);
+          break;
+        case BK_NODE4: case BK_NODE1:
+          if ((kind == BK_NODE4) == vn) blocks = plans[i].node_grid;
+          break;
+        case BK_DECIDE:
+          blocks = 1;
+          break;
+      }
+      if (!add(kind, i, blocks)) return -1;
+    }
+    bp->count[kind] = (int)(len - bp->offset[kind]);
+  }
+  static_assert(NODE_VW == 4, "the batch node kernels are instantiated for widths 4 and 1");
+  bp->inner_smem = ism;
+  if (ism > 48 * 1024 &&
+      cudaFuncSetAttribute(inner_kernel_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism) != cudaSuccess)
+    return -1;
+  *sched_len = len;
+  return 0;
+}
+
+int opfk_batch_enqueue(const Params *d_params, const int *d_sched, const BatchPlan &bp, void *main_stream,
+                       void *aux_stream, void *ev_fork, void *ev_join) {
+  cudaStream_t sm = (cudaStream_t)main_stream, sa = (cudaStream_t)aux_stream;
+  const int4 *sched = reinterpret_cast<const int4 *>(d_sched);
+  auto at = [&](int kind) { return sched + bp.offset[kind]; };
+  if (cudaEventRecord((cudaEvent_t)ev_fork, sm) != cudaSuccess) return -1;
+  if (cudaStreamWaitEvent(sa, (cudaEvent_t)ev_fork, 0) != cudaSuccess) return -1;
+  if (bp.count[BK_LINE4]) line_kernel_b<4><<<bp.count[BK_LINE4], BLOCK, 0, sa>>>(d_params, at(BK_LINE4));
+  if (bp.count[BK_LINE1]) line_kernel_b<1><<<bp.count[BK_LINE1], BLOCK, 0, sa>>>(d_params, at(BK_LINE1));
+  if (cudaEventRecord((cudaEvent_t)ev_join, sa) != cudaSuccess) return -1;
+  if (bp.count[BK_XS4]) xs_kernel_b<4><<<bp.count[BK_XS4], BLOCK, 0, sm>>>(d_params, at(BK_XS4));
+  if (bp.count[BK_XS1]) xs_kernel_b<1><<<bp.count[BK_XS1], BLOCK, 0, sm>>>(d_params, at(BK_XS1));
+  if (bp.count[BK_INNER])
+    inner_kernel_b<<<bp.count[BK_INNER], BLOCK, bp.inner_smem, sm>>>(d_params, at(BK_INNER));
+  if (bp.count[BK_DSUM2]) dsum_kernel_b<2><<<bp.count[BK_DSUM2], BLOCK, 0, sm>>>(d_params, at(BK_DSUM2));
+  if (bp.count[BK_DSUM1]) dsum_kernel_b<1><<<bp.count[BK_DSUM1], BLOCK, 0, sm>>>(d_params, at(BK_DSUM1));
+  if (cudaStreamWaitEvent(sm, (cudaEvent_t)ev_join, 0) != cudaSuccess) return -1;
+  if (bp.count[BK_NODE4]) node_kernel_b<4><<<bp.count[BK_NODE4], BLOCK, 0, sm>>>(d_params, at(BK_NODE4));
+  if (bp.count[BK_NODE1]) node_kernel_b<1><<<bp.count[BK_NODE1], BLOCK, 0, sm>>>(d_params, at(BK_NODE1));
+  decide_kernel_b<<<bp.count[BK_DECIDE], BLOCK, 0, sm>>>(d_params, at(BK_DECIDE));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
