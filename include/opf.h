@@ -207,16 +207,19 @@ opf_status opf_price_noalloc(opf_ctx *ctx, float *price);
 /* Batched iteration of independent instances (the batch solver of the
  * expansion-planning application, Section 5.6).  A batch groups existing
  * contexts of the current device (the caller keeps owning them; each keeps
- * its own state, options and stream) and captures every instance's
- * iteration kernels as independent
- * branches of one CUDA graph, so a batch step is one graph launch.
+ * its own state, options and stream).  One batch step launches each phase
+ * kernel once for all instances: every CTA finds its instance in a schedule
+ * built at opf_batch_create, so the launch count does not grow with the
+ * number of instances; steps are replayed from CUDA graphs of 1 and 16
+ * iterations.  Iterates equal those of opf_iterate on each context.
  * opf_batch_iterate enqueues n_iters iterations of every instance after the
  * work already queued on each instance's stream, and orders each stream
  * after it.  Unlike opf_iterate it does not restart an instance that has
- * stopped (passed stopping test or error): such an instance's kernels return
- * at once, so a batch can be iterated until every instance has converged.
+ * stopped (passed stopping test or error): such an instance's CTAs return at
+ * once, so a batch can be iterated until every instance has converged.
  * opf_batch_converged counts the converged instances (synchronizes).  The
- * contexts must outlive the batch. */
+ * contexts must outlive the batch; opf_batch_create allocates the device
+ * copies of the instances' parameters and the schedule. */
 typedef struct opf_batch opf_batch;
 opf_status opf_batch_create(opf_ctx *const *ctxs, int32_t n, opf_batch **out);
 opf_status opf_batch_iterate(opf_batch *batch, int32_t n_iters);

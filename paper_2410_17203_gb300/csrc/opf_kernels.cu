@@ -23,9 +23,11 @@
 //          forms the residuals, and takes the stopping and adaptive-penalty
 //          decisions (Section 3.5).
 //
-// Splitting the phases lets each kernel run at its own register budget (the
-// line and node kernels at 32 warps per SM).  There is no spin-wait on the
-// device: ordering comes from kernel boundaries and graph edges.
+// Splitting the phases lets each kernel run at its own register budget.
+// There is no spin-wait on the device: ordering comes from kernel boundaries
+// and graph edges.  Every kernel body also serves a batch of independent
+// instances: the batch entry points take the instances' parameters and a
+// CTA schedule, so one launch per phase covers all instances.
 //
 // Memory layout, numbering and the deferred v update: opf_internal.h.
 #include <cuda_runtime.h>
