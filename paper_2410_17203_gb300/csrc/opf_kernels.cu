@@ -620,7 +620,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
         const int l = code[q] >> 1;
         const size_t ol = kb + (size_t)l * T;
         pn[q] = ldv<VW>(p.P[nw] + ol);
-        po[q] = ldv_cs<VW>(p.P[old] + ol);
+        po[q] = ldv<VW>(p.P[old] + ol);   // kept in L2 for the line's other end
         mq[q] = ldv<VW>(p.MID[nw] + ol);
         bq[q] = p.line_b[l];
       }
