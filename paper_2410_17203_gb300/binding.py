@@ -78,7 +78,9 @@ class opf_info(C.Structure):
 EXPORTS = ["opf_default_options", "opf_create", "opf_iterate", "opf_residuals", "opf_solution",
            "opf_price_noalloc", "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info",
            "opf_destroy", "opf_status_str", "opf_last_error", "opf_abi_version",
-           "opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_destroy"]
+           "opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_destroy",
+           "opf_wsnet_param_count", "opf_wsnet_create", "opf_wsnet_get_params", "opf_wsnet_set_params",
+           "opf_wsnet_forward", "opf_wsnet_gradient", "opf_wsnet_train_step", "opf_wsnet_destroy"]
 
 _lib = None
 
@@ -119,6 +121,22 @@ def load_library(path=None):
     lib.opf_batch_destroy.argtypes = [C.c_void_p]
     lib.opf_batch_destroy.restype = None
     for name in ("opf_batch_create", "opf_batch_iterate", "opf_batch_converged"):
+        getattr(lib, name).restype = C.c_int
+    lib.opf_wsnet_param_count.argtypes = [C.c_int32]
+    lib.opf_wsnet_param_count.restype = C.c_int64
+    lib.opf_wsnet_create.argtypes = [C.c_int32, C.c_int32, I32P, I32P, F64P, C.c_int32, C.c_int32,
+                                     C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.opf_wsnet_get_params.argtypes = [C.c_void_p, C.c_void_p]
+    lib.opf_wsnet_set_params.argtypes = [C.c_void_p, C.c_void_p]
+    lib.opf_wsnet_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.opf_wsnet_gradient.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float),
+                                       C.POINTER(C.c_double), C.c_void_p]
+    lib.opf_wsnet_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float),
+                                         C.c_float, C.POINTER(C.c_double)]
+    lib.opf_wsnet_destroy.argtypes = [C.c_void_p]
+    lib.opf_wsnet_destroy.restype = None
+    for name in ("opf_wsnet_create", "opf_wsnet_get_params", "opf_wsnet_set_params", "opf_wsnet_forward",
+                 "opf_wsnet_gradient", "opf_wsnet_train_step"):
         getattr(lib, name).restype = C.c_int
     for name in ("opf_create", "opf_iterate", "opf_residuals", "opf_solution", "opf_price_noalloc",
                  "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info"):
@@ -285,6 +303,70 @@ def opf_batch_converged(b):
 def opf_batch_destroy(b):
     if b:
         load_library().opf_batch_destroy(b)
+
+
+def opf_wsnet_param_count(n_features):
+    return int(load_library().opf_wsnet_param_count(int(n_features)))
+
+
+class WarmStartNet:
+    """The learned warm-start network of include/opf_wsnet.h (device tensors
+    in, device tensors out; host NumPy for parameters and gradients)."""
+
+    def __init__(self, n_nodes, line_from, line_to, line_b, T, n_features, params=None, seed=0,
+                 stream=None):
+        lf = np.ascontiguousarray(line_from, np.int32)
+        lt = np.ascontiguousarray(line_to, np.int32)
+        lb = np.ascontiguousarray(line_b, np.float64)
+        self.R = int(n_nodes) * int(T)
+        self.F = int(n_features)
+        p = None if params is None else np.ascontiguousarray(params, np.float32)
+        self._keep = (lf, lt, lb, p)
+        out = C.c_void_p()
+        _check(load_library().opf_wsnet_create(
+            int(n_nodes), len(lf), lf.ctypes.data_as(I32P), lt.ctypes.data_as(I32P),
+            lb.ctypes.data_as(F64P), int(T), self.F, None if p is None else p.ctypes.data,
+            int(seed), stream, C.byref(out)), "opf_wsnet_create")
+        self.h = out
+
+    def params(self):
+        out = np.zeros(opf_wsnet_param_count(self.F), np.float32)
+        _check(load_library().opf_wsnet_get_params(self.h, out.ctypes.data), "opf_wsnet_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(load_library().opf_wsnet_set_params(self.h, p.ctypes.data), "opf_wsnet_set_params")
+
+    def forward(self, x, y):
+        _check(load_library().opf_wsnet_forward(self.h, _addr(x), _addr(y)), "opf_wsnet_forward")
+        return y
+
+    def gradient(self, x, y_target, scale):
+        sc = (C.c_float * 2)(*[float(v) for v in scale])
+        loss = C.c_double(0.0)
+        g = np.zeros(opf_wsnet_param_count(self.F), np.float32)
+        _check(load_library().opf_wsnet_gradient(self.h, _addr(x), _addr(y_target), sc, C.byref(loss),
+                                                 g.ctypes.data), "opf_wsnet_gradient")
+        return loss.value, g
+
+    def train_step(self, x, y_target, scale, lr):
+        sc = (C.c_float * 2)(*[float(v) for v in scale])
+        loss = C.c_double(0.0)
+        _check(load_library().opf_wsnet_train_step(self.h, _addr(x), _addr(y_target), sc, float(lr),
+                                                   C.byref(loss)), "opf_wsnet_train_step")
+        return loss.value
+
+    def close(self):
+        if self.h:
+            load_library().opf_wsnet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 STATE_FIELDS = ("p_line", "th1", "th2", "v1", "v2", "p_dev", "u", "inner")

@@ -1,6 +1,6 @@
 """Build the CUDA library ``lib/libopfmp.so`` in-tree with nvcc for sm_103a.
 
-The two translation units are compiled in parallel, then linked against the
+The translation units are compiled in parallel, then linked against the
 shared CUDA runtime so that a process that also loads PyTorch holds a single
 runtime instance.
 """
@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "lib", "libopfmp.so")
-SOURCES = ["opf_kernels.cu", "opf_api.cu"]
+SOURCES = ["opf_kernels.cu", "opf_api.cu", "opf_wsnet.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -32,6 +32,12 @@ opf_status fail(opf_status s, const char *msg) {
 
 opf_status fail(opf_status s, const std::string &msg) { return fail(s, msg.c_str()); }
 
+}  // namespace
+
+int opf_record_error(int s, const char *msg) { return (int)fail((opf_status)s, msg); }
+
+namespace {
+
 opf_status cuda_fail(cudaError_t e, const char *what) {
   snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? OPF_ENOMEM : OPF_ECUDA;

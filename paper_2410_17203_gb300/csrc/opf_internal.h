@@ -134,6 +134,8 @@ struct BatchPlan {
 
 // Launch wrappers implemented in opf_kernels.cu (host callable).
 extern "C++" {
+// Record the message returned by opf_last_error (opf_api.cu) and pass s on.
+int opf_record_error(int s, const char *msg);
 // Grids of the iteration kernels for this problem on the current device.
 int opfk_plan(const opfk::Params &p, opfk::IterPlan *plan);
 // Enqueue one iteration: xs, inner, dsum, the node kernels and decide on
