@@ -351,6 +351,101 @@ def batched_vs_plain(stream, args):
             "workload": "buses log-uniform [100, 5000], T in {1, 24, 48}, K in 0..20, seed 3"}
 
 
+def batch_solve(handles, args):
+    """Iterate a batch of contexts to eps = 1e-4; returns (iterations per
+    instance, seconds)."""
+    from paper_2410_17203_gb300 import (opf_batch_converged, opf_batch_create, opf_batch_destroy,
+                                        opf_batch_iterate, opf_get_info)
+    b = opf_batch_create(handles)
+    t0 = time.perf_counter()
+    done = 0
+    while done < args.ttt_max:
+        opf_batch_iterate(b, args.ttt_chunk)
+        done += args.ttt_chunk
+        if opf_batch_converged(b) == len(handles):
+            break
+    dt = time.perf_counter() - t0
+    its = [int(opf_get_info(h)["iterations"]) for h in handles]
+    conv = [bool(opf_get_info(h)["converged"]) for h in handles]
+    opf_batch_destroy(b)
+    return its, conv, dt
+
+
+def learned_warm_start(stream, args):
+    """Train the warm-start network on solutions of load-perturbed copies of
+    the 2k network and compare iterations to eps = 1e-4 on held-out copies:
+    cold start against the network's starting point."""
+    import numpy as np
+    import torch
+    from gridgen import make_case
+    from paper_2410_17203_gb300 import WarmStartNet, opf_create, opf_destroy, opf_set_state, opf_solution
+    from paper_2410_17203_gb300 import warmstart as ws
+
+    base = make_case("2k")
+    n_all = args.learned
+    n_test = max(1, n_all // 4)
+    rng = np.random.default_rng(4)
+    cases = []
+    for i in range(n_all):
+        c = dict(base)
+        c["load_p"] = base["load_p"] * rng.lognormal(0.0, 0.15, size=base["load_p"].shape)
+        cases.append(c)
+    opts = dict(adapt_every=10, eps=1e-4)
+    N, T = base["n_nodes"], base["T"]
+    Kp = len(base["outaged"]) + 1
+    # 1. every instance cold, batched: the training targets and the baseline
+    hs = [opf_create(c, opts, stream=stream.cuda_stream) for c in cases]
+    its_cold, conv_cold, t_gen = batch_solve(hs, args)
+    Y = []
+    for h in hs:
+        price = np.zeros((N, T), np.float32)
+        theta = np.zeros((Kp, N, T), np.float32)
+        opf_solution(h, False, False, theta_node=theta, price=price)
+        Y.append(ws.targets(price, theta[0]))
+        opf_destroy(h)
+    X = [ws.node_features(c) for c in cases]
+    train_idx = [i for i in range(n_all - n_test) if conv_cold[i]]
+    test_idx = list(range(n_all - n_test, n_all))
+    norm = ws.Normalizer(np.concatenate([X[i] for i in train_idx]))
+    ystd = np.concatenate([Y[i] for i in train_idx]).std(axis=0)
+    scale = tuple(float(1.0 / max(v * v, 1e-12)) for v in ystd)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xd = [torch.from_numpy(norm(x)).to(dev) for x in X]
+    yd = [torch.from_numpy(y.astype(np.float32)).to(dev) for y in Y]
+    # 2. train on the GPU with the library's kernels
+    net = WarmStartNet(N, base["line_from"], base["line_to"], base["line_b"], T, ws.N_FEATURES, seed=1,
+                       stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = ws.train(net, [xd[i] for i in train_idx], [yd[i] for i in train_idx], args.learned_epochs,
+                    args.learned_lr, scale=scale)
+    t_train = time.perf_counter() - t0
+    test_loss = float(np.mean([net.gradient(xd[i], yd[i], scale)[0] for i in test_idx]))
+    # 3. held-out instances from the network's starting point
+    hw = []
+    for i in test_idx:
+        y = torch.zeros((N * T, 2), dtype=torch.float32, device=dev)
+        net.forward(xd[i], y)
+        h = opf_create(cases[i], opts, stream=stream.cuda_stream)
+        opf_set_state(h, ws.warm_state(cases[i], y.cpu().numpy().astype(np.float64)))
+        hw.append(h)
+    its_warm, conv_warm, t_warm = batch_solve(hw, args)
+    for h in hw:
+        opf_destroy(h)
+    net.close()
+    cold = [its_cold[i] for i in test_idx]
+    return {"network": "2k buses, T=24, K=20; loads x lognormal(0, 0.15) per (load, step), seed 4",
+            "instances": n_all, "train": len(train_idx), "test": len(test_idx),
+            "epochs": args.learned_epochs, "lr": args.learned_lr,
+            "train_loss_first_last": [hist[0], hist[-1]], "test_loss": test_loss,
+            "train_seconds": t_train, "data_seconds": t_gen,
+            "test_iterations_cold": {"mean": float(np.mean(cold)), "median": float(np.median(cold))},
+            "test_iterations_learned": {"mean": float(np.mean(its_warm)), "median": float(np.median(its_warm))},
+            "test_converged_cold": int(sum(conv_cold[i] for i in test_idx)),
+            "test_converged_learned": int(sum(conv_warm)),
+            "test_seconds_learned_batched": t_warm}
+
+
 def ours_arm(args):
     import numpy as np
     import torch
@@ -440,6 +535,9 @@ def ours_arm(args):
     batched = None
     if args.batched > 0 and rank == 0:
         batched = batched_vs_plain(stream, args)
+    learned = None
+    if args.learned > 0 and rank == 0:
+        learned = learned_warm_start(stream, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -481,6 +579,8 @@ def ours_arm(args):
             line["time_to_tolerance"] = ttt
         if batched:
             line["batched_vs_plain"] = batched
+        if learned:
+            line["learned_warm_start"] = learned
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -500,6 +600,11 @@ def main():
                     help="skip the solves to eps = 1e-4 (cold, perturbed cold, perturbed warm)")
     ap.add_argument("--ttt-max", type=int, default=30000)
     ap.add_argument("--ttt-chunk", type=int, default=100)
+    ap.add_argument("--learned", type=int, default=0,
+                    help="also train the warm-start network on this many perturbed 2k instances "
+                         "(a quarter held out) and compare iterations to eps = 1e-4")
+    ap.add_argument("--learned-epochs", type=int, default=60)
+    ap.add_argument("--learned-lr", type=float, default=1e-3)
     ap.add_argument("--batched", type=int, default=0,
                     help="also solve this many independent instances to eps = 1e-4, one by one and as one batch")
     ap.add_argument("--_oracle-child", dest="oracle_child", default=None)

@@ -1,0 +1,87 @@
+"""The learned warm start end to end on the 30-bus grid: starting states built
+from prices and angles are valid (from the instance's own solution they cut
+the iterations to the tolerance), and the trained network's starting point
+reaches the same tolerance and objective as a cold start."""
+import numpy as np
+import pytest
+
+from gridgen import make_case
+
+pytestmark = pytest.mark.gpu
+
+OPTS = dict(adapt_every=0, rho_theta=10.0, eps=1e-4)   # every perturbed copy converges in 5,500-7,300 iterations
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2410_17203_gb300 import load_library
+    load_library()
+
+
+def _solve(cases, states=None):
+    from paper_2410_17203_gb300 import (opf_batch_converged, opf_batch_create, opf_batch_destroy,
+                                        opf_batch_iterate, opf_create, opf_get_info, opf_set_state)
+    hs = [opf_create(c, OPTS) for c in cases]
+    if states:
+        for h, st in zip(hs, states):
+            opf_set_state(h, st)
+    b = opf_batch_create(hs)
+    for _ in range(800):
+        opf_batch_iterate(b, 100)
+        if opf_batch_converged(b) == len(hs):
+            break
+    opf_batch_destroy(b)
+    return hs, [opf_get_info(h) for h in hs]
+
+
+def test_warm_state_from_the_solution_and_learned_start():
+    import torch
+    from paper_2410_17203_gb300 import WarmStartNet, opf_destroy, opf_solution
+    from paper_2410_17203_gb300 import warmstart as ws
+    base = make_case("tiny")
+    rng = np.random.default_rng(0)
+    cases = []
+    for _ in range(16):
+        c = dict(base)
+        c["load_p"] = base["load_p"] * rng.lognormal(0.0, 0.15, size=base["load_p"].shape)
+        cases.append(c)
+    N, T, Kp = base["n_nodes"], base["T"], len(base["outaged"]) + 1
+    hs, info = _solve(cases)
+    assert all(i["converged"] for i in info)
+    Y, obj = [], []
+    for h in hs:
+        price = np.zeros((N, T), np.float32)
+        theta = np.zeros((Kp, N, T), np.float32)
+        obj.append(opf_solution(h, False, True, theta_node=theta, price=price))
+        Y.append(ws.targets(price, theta[0]))
+        opf_destroy(h)
+    cold = [i["iterations"] for i in info]
+    # from each instance's own prices and angles: fewer iterations
+    hs2, info2 = _solve(cases[:4], [ws.warm_state(c, y) for c, y in zip(cases[:4], Y[:4])])
+    for h in hs2:
+        opf_destroy(h)
+    assert all(i["converged"] for i in info2)
+    assert np.mean([i["iterations"] for i in info2]) < np.mean(cold[:4])
+    # the trained network's starting point reaches the same tolerance and objective
+    X = [ws.node_features(c) for c in cases]
+    norm = ws.Normalizer(np.concatenate(X[:12]))
+    xd = [torch.from_numpy(norm(x)).cuda() for x in X]
+    yd = [torch.from_numpy(y.astype(np.float32)).cuda() for y in Y]
+    net = WarmStartNet(N, base["line_from"], base["line_to"], base["line_b"], T, ws.N_FEATURES, seed=2)
+    hist = ws.train(net, xd[:12], yd[:12], epochs=30, lr=1e-3)
+    assert hist[-1] < hist[0]
+    states = []
+    for i in range(12, 16):
+        y = torch.zeros((N * T, 2), dtype=torch.float32, device="cuda")
+        net.forward(xd[i], y)
+        states.append(ws.warm_state(cases[i], y.cpu().numpy().astype(np.float64)))
+    net.close()
+    hs3, info3 = _solve(cases[12:], states)
+    assert all(i["converged"] for i in info3)
+    # two points that both pass the eps = 1e-4 residual test from different
+    # starts agree on the objective to a few tenths of a percent
+    for h, o in zip(hs3, obj[12:]):
+        assert opf_solution(h, False, True) == pytest.approx(o, rel=1e-2)
+        opf_destroy(h)
