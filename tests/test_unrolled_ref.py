@@ -1,0 +1,68 @@
+"""Pins of the PyTorch unrolled reference (oracle/unrolled.py): it repeats the
+NumPy oracle's iterates; its autograd gradients match central finite
+differences; and with more iterations the gradient of the cost with respect
+to a fixed load moves toward the nodal price (Section 5.5: the derivative of
+the optimal cost with respect to the data is the dual variable)."""
+import numpy as np
+import pytest
+import torch
+
+from gridgen import make_case, scale_case
+from oracle import Oracle, OracleOptions
+from oracle.unrolled import Unrolled
+
+
+def _case():
+    return make_case(scale_case(40, 3, 2, seed=5, ramp=False, stor_per_node=0.0, fixed_frac=0.3))
+
+
+def test_repeats_the_oracle_iterates():
+    case = _case()
+    ur = Unrolled(case, rho_p=1.0, rho_theta=2.0)
+    f, pd = ur.run(ur.params(requires_grad=False), 17)
+    o = Oracle(case, OracleOptions(adapt_every=0, eps=0.0, rho_theta=2.0))
+    o.iterate(17, stop=False)
+    np.testing.assert_allclose(pd.numpy(), o.dev_p(), rtol=1e-12, atol=1e-12)
+    assert float(f) == pytest.approx(o.objective(), rel=1e-12)
+
+
+def test_gradients_match_finite_differences():
+    case = _case()
+    ur = Unrolled(case, rho_p=1.0, rho_theta=2.0)
+    prm = ur.params()
+    f, _ = ur.run(prm, 25)
+    f.backward()
+    rng = np.random.default_rng(0)
+    h = 1e-7
+    checked = 0
+    for name, p in prm.items():
+        g = p.grad.numpy().ravel()
+        flat = p.detach().numpy().ravel()
+        for j in rng.choice(flat.size, size=min(8, flat.size), replace=False):
+            vals = []
+            for s in (1, -1):
+                q = {k: v.detach().clone() for k, v in prm.items()}
+                q[name].view(-1)[j] += s * h
+                vals.append(float(ur.run(q, 25)[0]))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - g[j]) <= 1e-4 * (1 + abs(fd)), (name, j, fd, g[j])
+            checked += 1
+    assert checked >= 20
+
+
+@pytest.mark.slow
+def test_load_gradient_approaches_the_price_with_more_iterations():
+    """Section 5.5: unrolling more iterations gives derivatives closer to the
+    duality value; for a fixed load that value is the price at its node."""
+    case = make_case("tiny")                 # fixed loads, T = 1
+    ur = Unrolled(case, rho_p=1.0, rho_theta=10.0)
+    errs = []
+    for K in (2000, 6000):
+        prm = ur.params()
+        f, _ = ur.run(prm, K)
+        f.backward()
+        o = Oracle(case, OracleOptions(adapt_every=0, rho_theta=10.0, eps=0.0))
+        o.iterate(K, stop=False)
+        want = o.prices()[np.asarray(case["load_node"]), 0]
+        errs.append(np.linalg.norm(prm["load_p"].grad.numpy()[:, 0] - want) / np.linalg.norm(want))
+    assert errs[1] < 0.5 * errs[0]
