@@ -80,7 +80,8 @@ EXPORTS = ["opf_default_options", "opf_create", "opf_iterate", "opf_residuals", 
            "opf_destroy", "opf_status_str", "opf_last_error", "opf_abi_version",
            "opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_destroy",
            "opf_wsnet_param_count", "opf_wsnet_create", "opf_wsnet_get_params", "opf_wsnet_set_params",
-           "opf_wsnet_forward", "opf_wsnet_gradient", "opf_wsnet_train_step", "opf_wsnet_destroy"]
+           "opf_wsnet_forward", "opf_wsnet_gradient", "opf_wsnet_train_step", "opf_wsnet_destroy",
+           "opf_diff_create", "opf_diff_cost_grad", "opf_diff_destroy"]
 
 _lib = None
 
@@ -138,6 +139,15 @@ def load_library(path=None):
     for name in ("opf_wsnet_create", "opf_wsnet_get_params", "opf_wsnet_set_params", "opf_wsnet_forward",
                  "opf_wsnet_gradient", "opf_wsnet_train_step"):
         getattr(lib, name).restype = C.c_int
+    F32P = C.POINTER(C.c_float)
+    lib.opf_diff_create.argtypes = [C.POINTER(opf_network), C.c_int32, C.POINTER(opf_contingencies),
+                                    C.c_double, C.c_double, C.c_int32, C.c_void_p,
+                                    C.POINTER(C.c_void_p)]
+    lib.opf_diff_cost_grad.argtypes = [C.c_void_p, C.c_int32, F32P, F32P, F32P, F64P, F32P, F32P, F32P]
+    lib.opf_diff_destroy.argtypes = [C.c_void_p]
+    lib.opf_diff_destroy.restype = None
+    for name in ("opf_diff_create", "opf_diff_cost_grad"):
+        getattr(lib, name).restype = C.c_int
     for name in ("opf_create", "opf_iterate", "opf_residuals", "opf_solution", "opf_price_noalloc",
                  "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info"):
         getattr(lib, name).restype = C.c_int
@@ -182,10 +192,9 @@ def _ptr(a, ctype):
     return a.ctypes.data_as(C.POINTER(ctype)) if a is not None and a.size else C.POINTER(ctype)()
 
 
-def opf_create(case, options=None, stream=None):
-    """Create a solver context from a case dict (see ``gridgen``).  Returns the handle."""
-    lib = load_library()
-    T = int(case["T"])
+def _network(case):
+    """The opf_network and opf_contingencies of a case dict, plus the arrays
+    they point into (keep them alive while the structs are used)."""
     keep = {}
 
     def f64(name, shape=None):
@@ -211,7 +220,16 @@ def opf_create(case, options=None, stream=None):
         stor_dur=f64("stor_dur"), stor_eff=f64("stor_eff"), stor_cost=f64("stor_cost"),
     )
     out = np.ascontiguousarray(np.asarray(case["outaged"], dtype=np.int32))
+    keep["outaged"] = out
     ctg = opf_contingencies(K=len(out), outaged_line=_ptr(out, C.c_int32))
+    return net, ctg, keep
+
+
+def opf_create(case, options=None, stream=None):
+    """Create a solver context from a case dict (see ``gridgen``).  Returns the handle."""
+    lib = load_library()
+    T = int(case["T"])
+    net, ctg, keep = _network(case)
     if options is None:
         options = opf_default_options()
     elif isinstance(options, dict):
@@ -360,6 +378,56 @@ class WarmStartNet:
     def close(self):
         if self.h:
             load_library().opf_wsnet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class UnrolledCost:
+    """The cost after K unrolled iterations and its gradients (include/opf_diff.h).
+
+    ``cost_grad(K, load_p, gen_pmax, line_u)`` takes host arrays ([D][T],
+    [G][T], [L]; None = the case's own) and returns (f, dict of gradients
+    with the same keys and shapes)."""
+
+    def __init__(self, case, rho_p=1.0, rho_theta=1.0, checkpoint_every=16, stream=None):
+        net, ctg, keep = _network(case)
+        self.T = int(case["T"])
+        self.D, self.G, self.L = len(case["load_node"]), len(case["gen_node"]), len(case["line_from"])
+        out = C.c_void_p()
+        _check(load_library().opf_diff_create(C.byref(net), self.T, C.byref(ctg), float(rho_p),
+                                              float(rho_theta), int(checkpoint_every), stream,
+                                              C.byref(out)), "opf_diff_create")
+        del keep
+        self.h = out
+
+    def cost_grad(self, K, load_p=None, gen_pmax=None, line_u=None, grads=True):
+        F32P = C.POINTER(C.c_float)
+
+        def arr(x, shape):
+            if x is None:
+                return None, F32P()
+            a = np.ascontiguousarray(np.asarray(x, np.float32).reshape(shape))
+            return a, a.ctypes.data_as(F32P)
+
+        a1, p1 = arr(load_p, (self.D, self.T))
+        a2, p2 = arr(gen_pmax, (self.G, self.T))
+        a3, p3 = arr(line_u, (self.L,))
+        g = dict(load_p=np.zeros((self.D, self.T), np.float32), gen_pmax=np.zeros((self.G, self.T), np.float32),
+                 line_u=np.zeros(self.L, np.float32))
+        gp = [_ptr(g[k], C.c_float) if grads else F32P() for k in ("load_p", "gen_pmax", "line_u")]
+        f = C.c_double(0.0)
+        _check(load_library().opf_diff_cost_grad(self.h, int(K), p1, p2, p3, C.byref(f), *gp),
+               "opf_diff_cost_grad")
+        return f.value, (g if grads else None)
+
+    def close(self):
+        if self.h:
+            load_library().opf_diff_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "lib", "libopfmp.so")
-SOURCES = ["opf_kernels.cu", "opf_api.cu", "opf_wsnet.cu"]
+SOURCES = ["opf_kernels.cu", "opf_api.cu", "opf_wsnet.cu", "opf_diff.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

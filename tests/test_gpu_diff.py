@@ -1,0 +1,141 @@
+"""Parity of the unrolled-iteration gradients (include/opf_diff.h, Section 4.4
+and Section 5.5) against the PyTorch FP64 autograd reference oracle/unrolled.py.
+
+The device path runs in FP32.  Every step of the iteration is nonexpansive
+up to the penalty ratios, so the rounding of K steps grows roughly linearly
+with K (about 1e-6 relative per step); the gradients are compared normwise
+at 2e-3 for K <= 60 and the cost at 1e-4 relative.  Clipping decisions are
+taken on FP32 values on the device and FP64 values in the reference; the
+seeded cases here have no bound ties at that precision (a tie would show as a
+single large element, which the normwise test would report)."""
+import numpy as np
+import pytest
+import torch
+
+from gridgen import make_case, scale_case
+from oracle.unrolled import Unrolled
+
+pytestmark = pytest.mark.gpu
+
+GRAD_RTOL = 2e-3
+COST_RTOL = 1e-4
+
+
+def _lib():
+    from paper_2410_17203_gb300 import binding
+    return binding
+
+
+def _reference(case, K, rho_p, rho_theta):
+    ur = Unrolled(case, rho_p=rho_p, rho_theta=rho_theta)
+    prm = ur.params()
+    f, _ = ur.run(prm, K)
+    f.backward()
+    return float(f.detach()), {k: v.grad.numpy() for k, v in prm.items()}
+
+
+def _normwise(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / (nb if nb > 0 else 1.0)
+
+
+def _check(case, K, rho_p=10.0, rho_theta=20.0, ckpt=8):
+    b = _lib()
+    f_ref, g_ref = _reference(case, K, rho_p, rho_theta)
+    d = b.UnrolledCost(case, rho_p=rho_p, rho_theta=rho_theta, checkpoint_every=ckpt)
+    try:
+        f, g = d.cost_grad(K)
+    finally:
+        d.close()
+    assert f == pytest.approx(f_ref, rel=COST_RTOL)
+    for k in ("load_p", "gen_pmax", "line_u"):
+        assert g[k].shape == g_ref[k].shape
+        assert _normwise(g[k], g_ref[k]) <= GRAD_RTOL, (k, _normwise(g[k], g_ref[k]))
+    return g_ref
+
+
+def test_small_case_matches_autograd():
+    case = make_case(scale_case(40, 3, 2, seed=5, ramp=False, stor_per_node=0.0, fixed_frac=0.3))
+    g = _check(case, 40)
+    # at these penalties the case exercises every gradient path: fixed and
+    # curtailable loads, generators at their capacity, lines at their limit
+    assert np.count_nonzero(g["gen_pmax"]) > 0 and np.count_nonzero(g["line_u"]) > 0
+
+
+def test_several_tiles_and_contingencies():
+    case = make_case(scale_case(600, 5, 6, seed=11, ramp=False, stor_per_node=0.0, fixed_frac=0.2))
+    _check(case, 60, rho_p=1.0, rho_theta=5.0, ckpt=7)
+
+
+def test_base_case_only_and_single_step():
+    case = make_case(scale_case(50, 1, 0, seed=3, ramp=True, stor_per_node=0.0, fixed_frac=0.5))
+    _check(case, 1)
+    _check(case, 25, rho_p=50.0, rho_theta=100.0, ckpt=25)
+
+
+def test_checkpointing_is_exact():
+    """Recomputed segments repeat the forward pass bit for bit, so the
+    gradients do not depend on the checkpoint spacing."""
+    b = _lib()
+    case = make_case(scale_case(120, 4, 3, seed=8, ramp=False, stor_per_node=0.0, fixed_frac=0.3))
+    outs = []
+    for ckpt in (1, 5, 64):
+        d = b.UnrolledCost(case, rho_p=10.0, rho_theta=20.0, checkpoint_every=ckpt)
+        try:
+            outs.append(d.cost_grad(37))
+        finally:
+            d.close()
+    for f, g in outs[1:]:
+        assert f == outs[0][0]
+        for k in g:
+            np.testing.assert_array_equal(g[k], outs[0][1][k])
+
+
+def test_data_arguments_replace_the_case_data():
+    """Passing changed data equals differentiating the changed case."""
+    b = _lib()
+    case = make_case(scale_case(60, 2, 2, seed=4, ramp=False, stor_per_node=0.0, fixed_frac=0.3))
+    rng = np.random.default_rng(1)
+    lp = np.asarray(case["load_p"]) * (1 + 0.2 * rng.random(np.shape(case["load_p"])))
+    pm = np.asarray(case["gen_pmax"]) * 0.8
+    lu = np.asarray(case["line_u"]) * 0.7
+    changed = dict(case, load_p=lp, gen_pmax=pm, line_u=lu)
+    d = b.UnrolledCost(case, rho_p=10.0, rho_theta=20.0)
+    try:
+        f, g = d.cost_grad(30, load_p=lp, gen_pmax=pm, line_u=lu)
+        f0, g0 = d.cost_grad(30)
+        f_none, g_none = d.cost_grad(30, grads=False)
+    finally:
+        d.close()
+    f_ref, g_ref = _reference(changed, 30, 10.0, 20.0)
+    assert f == pytest.approx(f_ref, rel=COST_RTOL)
+    for k in g:
+        assert _normwise(g[k], g_ref[k]) <= GRAD_RTOL
+    assert f_none == f0 and g_none is None
+    assert f0 != f
+
+
+def test_rejects_devices_without_closed_form_prox():
+    b = _lib()
+    with_storage = make_case(scale_case(40, 3, 1, seed=2, ramp=False, stor_per_node=0.2))
+    with pytest.raises(b.OpfError):
+        b.UnrolledCost(with_storage)
+    ramped = make_case(scale_case(40, 3, 1, seed=2, ramp=True, stor_per_node=0.0))
+    if np.any(np.asarray(ramped["gen_ramp"]) >= 0):
+        with pytest.raises(b.OpfError):
+            b.UnrolledCost(ramped)
+    with pytest.raises(b.OpfError):
+        b.UnrolledCost(make_case(scale_case(40, 1, 1, seed=2, ramp=False, stor_per_node=0.0)), rho_p=0.0)
+
+
+def test_torch_tensors_are_accepted():
+    b = _lib()
+    case = make_case(scale_case(40, 2, 1, seed=6, ramp=False, stor_per_node=0.0, fixed_frac=0.3))
+    d = b.UnrolledCost(case, rho_p=10.0, rho_theta=20.0)
+    try:
+        f1, g1 = d.cost_grad(10, load_p=torch.tensor(np.asarray(case["load_p"])))
+        f2, g2 = d.cost_grad(10)
+    finally:
+        d.close()
+    assert f1 == f2
+    np.testing.assert_array_equal(g1["load_p"], g2["load_p"])

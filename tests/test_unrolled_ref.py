@@ -27,27 +27,38 @@ def test_repeats_the_oracle_iterates():
 
 
 def test_gradients_match_finite_differences():
+    """At these penalties 40 iterations reach a state where loads are served,
+    some generators sit at capacity and some lines at their limit, so every
+    gradient path is active; entries with a nonzero gradient are checked
+    first, then a few zero ones."""
     case = _case()
-    ur = Unrolled(case, rho_p=1.0, rho_theta=2.0)
+    K = 40
+    ur = Unrolled(case, rho_p=10.0, rho_theta=20.0)
     prm = ur.params()
-    f, _ = ur.run(prm, 25)
+    f, _ = ur.run(prm, K)
     f.backward()
     rng = np.random.default_rng(0)
     h = 1e-7
-    checked = 0
+    checked = nonzero = 0
     for name, p in prm.items():
         g = p.grad.numpy().ravel()
         flat = p.detach().numpy().ravel()
-        for j in rng.choice(flat.size, size=min(8, flat.size), replace=False):
+        nz = np.flatnonzero(g)
+        assert nz.size > 0, name
+        zero = np.flatnonzero(g == 0)
+        pick = list(rng.choice(nz, size=min(6, nz.size), replace=False))
+        pick += list(rng.choice(zero, size=min(2, zero.size), replace=False)) if zero.size else []
+        for j in pick:
             vals = []
             for s in (1, -1):
                 q = {k: v.detach().clone() for k, v in prm.items()}
                 q[name].view(-1)[j] += s * h
-                vals.append(float(ur.run(q, 25)[0]))
+                vals.append(float(ur.run(q, K)[0]))
             fd = (vals[0] - vals[1]) / (2 * h)
             assert abs(fd - g[j]) <= 1e-4 * (1 + abs(fd)), (name, j, fd, g[j])
             checked += 1
-    assert checked >= 20
+            nonzero += g[j] != 0
+    assert checked >= 15 and nonzero >= 10
 
 
 @pytest.mark.slow
