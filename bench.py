@@ -18,6 +18,9 @@ ABI: the instance cold, the instance with every load scaled by
 lognormal(0, 0.05) cold, and that perturbed instance warm-started from the
 first solution (Section 3.4).
 
+``--adjoint K``: wall time of the cost gradient after K unrolled iterations
+(include/opf_diff.h) on the 2k network with closed-form devices.
+
 ``--impl reference`` times the FP64 oracle on the host cores instead; each
 step is one oracle iteration on a bounded sample of the instance (the 10k
 network with fewer contingencies and time steps), converted to full-workload
@@ -446,6 +449,38 @@ def learned_warm_start(stream, args):
             "test_seconds_learned_batched": t_warm}
 
 
+def adjoint_leg(stream, args):
+    """Cost and gradient after K unrolled iterations (include/opf_diff.h) on
+    the 2k network with closed-form devices (no batteries, no ramp limits):
+    wall time of one forward + reverse pass against the forward alone."""
+    import numpy as np
+    import torch
+    from gridgen import make_case
+    from paper_2410_17203_gb300 import UnrolledCost
+
+    case = make_case("2k", n_stor=0, ramp=False)
+    K, ck = args.adjoint, 20
+    d = UnrolledCost(case, rho_p=1.0, rho_theta=1.0, checkpoint_every=ck, stream=stream.cuda_stream)
+    try:
+        d.cost_grad(K)                                   # warm-up (allocations, module load)
+        t_fg, t_f = [], []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            f, g = d.cost_grad(K)
+            t_fg.append(time.perf_counter() - t0)
+            t0 = time.perf_counter()
+            d.cost_grad(K, grads=False)
+            t_f.append(time.perf_counter() - t0)
+    finally:
+        d.close()
+    torch.cuda.synchronize()
+    return {"network": "2k buses, T=24, K=20, curtailable loads, generators without ramp limits, "
+                       "no batteries (closed-form proxes), seed 1",
+            "iterations": K, "checkpoint_every": ck, "seconds_cost_and_gradient": float(np.median(t_fg)),
+            "seconds_cost_only": float(np.median(t_f)), "cost": f,
+            "grad_norms": {k: float(np.linalg.norm(v)) for k, v in g.items()}}
+
+
 def ours_arm(args):
     import numpy as np
     import torch
@@ -538,6 +573,9 @@ def ours_arm(args):
     learned = None
     if args.learned > 0 and rank == 0:
         learned = learned_warm_start(stream, args)
+    adjoint = None
+    if args.adjoint > 0 and rank == 0:
+        adjoint = adjoint_leg(stream, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -581,6 +619,8 @@ def ours_arm(args):
             line["batched_vs_plain"] = batched
         if learned:
             line["learned_warm_start"] = learned
+        if adjoint:
+            line["adjoint"] = adjoint
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -607,6 +647,9 @@ def main():
     ap.add_argument("--learned-lr", type=float, default=1e-3)
     ap.add_argument("--batched", type=int, default=0,
                     help="also solve this many independent instances to eps = 1e-4, one by one and as one batch")
+    ap.add_argument("--adjoint", type=int, default=0,
+                    help="also time the cost gradient after this many unrolled iterations (2k network, "
+                         "closed-form devices)")
     ap.add_argument("--_oracle-child", dest="oracle_child", default=None)
     args = ap.parse_args()
     if args.oracle_child:

@@ -8,4 +8,5 @@ from .binding import (  # noqa: F401
     opf_batch_destroy, opf_batch_iterate, opf_create, opf_default_options,
     opf_destroy, opf_get_info, opf_get_state, opf_iterate, opf_last_error, opf_reset,
     opf_price_noalloc, opf_residuals, opf_set_state, opf_solution, opf_status_str, state_shapes,
+    unrolled_cost,
 )

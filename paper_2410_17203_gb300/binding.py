@@ -437,6 +437,41 @@ class UnrolledCost:
             pass
 
 
+_UNROLLED_FN = None
+
+
+def _unrolled_fn():
+    global _UNROLLED_FN
+    if _UNROLLED_FN is None:
+        import torch
+
+        class UnrolledCostFn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, diff, K, load_p, gen_pmax, line_u):
+                want = any(ctx.needs_input_grad[2:])
+                host = [x.detach().to("cpu", torch.float32).numpy() for x in (load_p, gen_pmax, line_u)]
+                f, g = diff.cost_grad(K, *host, grads=want)
+                if want:
+                    ctx.save_for_backward(*[torch.from_numpy(g[k]).to(x.device, x.dtype) for k, x in
+                                            zip(("load_p", "gen_pmax", "line_u"), (load_p, gen_pmax, line_u))])
+                return torch.tensor(f, dtype=load_p.dtype, device=load_p.device)
+
+            @staticmethod
+            def backward(ctx, go):
+                gl, gp, gu = ctx.saved_tensors
+                return None, None, go * gl, go * gp, go * gu
+
+        _UNROLLED_FN = UnrolledCostFn
+    return _UNROLLED_FN
+
+
+def unrolled_cost(diff, K, load_p, gen_pmax, line_u):
+    """f(p^K) of an :class:`UnrolledCost` as a torch scalar differentiable with
+    respect to the tensors load_p [D][T], gen_pmax [G][T] and line_u [L]; the
+    forward and the reverse pass both run in ``opf_diff_cost_grad``."""
+    return _unrolled_fn().apply(diff, int(K), load_p, gen_pmax, line_u)
+
+
 STATE_FIELDS = ("p_line", "th1", "th2", "v1", "v2", "p_dev", "u", "inner")
 
 

@@ -139,3 +139,61 @@ def test_torch_tensors_are_accepted():
         d.close()
     assert f1 == f2
     np.testing.assert_array_equal(g1["load_p"], g2["load_p"])
+
+
+def test_autograd_function():
+    """unrolled_cost plugs the device gradients into torch.autograd; a
+    gradient step on the capacities of the cheapest generators lowers the
+    cost (the use Section 5.6 makes of these derivatives)."""
+    b = _lib()
+    case = make_case(scale_case(60, 2, 2, seed=4, ramp=False, stor_per_node=0.0, fixed_frac=0.3))
+    d = b.UnrolledCost(case, rho_p=10.0, rho_theta=20.0)
+    try:
+        lp = torch.tensor(np.asarray(case["load_p"]), dtype=torch.float64, requires_grad=True)
+        pm = torch.tensor(np.asarray(case["gen_pmax"]), dtype=torch.float64, requires_grad=True)
+        lu = torch.tensor(np.asarray(case["line_u"]), dtype=torch.float64, requires_grad=True)
+        f = b.unrolled_cost(d, 30, lp, pm, lu)
+        (2.0 * f).backward()
+        f_ref, g_ref = d.cost_grad(30)
+        assert float(f) == f_ref
+        np.testing.assert_allclose(pm.grad.numpy(), 2.0 * g_ref["gen_pmax"], rtol=1e-6)
+        np.testing.assert_allclose(lp.grad.numpy(), 2.0 * g_ref["load_p"], rtol=1e-6)
+        np.testing.assert_allclose(lu.grad.numpy(), 2.0 * g_ref["line_u"], rtol=1e-6)
+        with torch.no_grad():
+            pm2 = pm - 1e-3 * pm.grad / max(1.0, float(pm.grad.abs().max()))
+        f2 = b.unrolled_cost(d, 30, lp.detach(), pm2, lu.detach())
+        assert float(f2) < float(f)
+    finally:
+        d.close()
+
+
+def test_gradients_approach_the_duals():
+    """Section 5.5: with more unrolled iterations the derivatives approach
+    the sensitivities of the optimal cost -- the nodal price for a fixed load
+    and (2 a pmax + b) - price for a generator at its capacity.  The
+    converged prices come from the FP64 oracle run to its fixed point."""
+    from oracle import Oracle, OracleOptions
+    b = _lib()
+    case = make_case("tiny")                       # fixed loads, T = 1
+    rp, rt = 10.0, 100.0
+    o = Oracle(case, OracleOptions(adapt_every=0, rho_p=rp, rho_theta=rt, eps=0.0))
+    o.iterate(30000, stop=False)
+    lam = o.prices()[:, 0]
+    want = lam[np.asarray(case["load_node"])]
+    gn = np.asarray(case["gen_node"])
+    pg = o.dev_p()[:len(gn), 0]
+    pmax = np.asarray(case["gen_pmax"])[:, 0]
+    mu = lam[gn] - (2 * np.asarray(case["gen_a"]) * pg + np.asarray(case["gen_b"]))
+    at_cap = np.flatnonzero((mu > 1.0) & (np.abs(pg - pmax) < 1e-6))
+    assert at_cap.size >= 1
+    d = b.UnrolledCost(case, rho_p=rp, rho_theta=rt, checkpoint_every=200)
+    try:
+        errs = []
+        for K in (3000, 24000):
+            _, g = d.cost_grad(K)
+            errs.append(np.linalg.norm(g["load_p"][:, 0] - want) / np.linalg.norm(want))
+        cap = g["gen_pmax"][at_cap, 0]
+    finally:
+        d.close()
+    assert errs[1] < 0.02 and errs[1] < 0.25 * errs[0], errs
+    np.testing.assert_allclose(cap, -mu[at_cap], rtol=0.1)
