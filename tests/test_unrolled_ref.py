@@ -16,8 +16,14 @@ def _case():
     return make_case(scale_case(40, 3, 2, seed=5, ramp=False, stor_per_node=0.0, fixed_frac=0.3))
 
 
-def test_repeats_the_oracle_iterates():
-    case = _case()
+def _case_inner():
+    """Ramp-limited generators and batteries: their prox is the inner ADMM."""
+    return make_case(scale_case(40, 6, 2, seed=7, ramp=True, stor_per_node=0.1, fixed_frac=0.3))
+
+
+@pytest.mark.parametrize("inner", [False, True])
+def test_repeats_the_oracle_iterates(inner):
+    case = _case_inner() if inner else _case()
     ur = Unrolled(case, rho_p=1.0, rho_theta=2.0)
     f, pd = ur.run(ur.params(requires_grad=False), 17)
     o = Oracle(case, OracleOptions(adapt_every=0, eps=0.0, rho_theta=2.0))
@@ -26,12 +32,14 @@ def test_repeats_the_oracle_iterates():
     assert float(f) == pytest.approx(o.objective(), rel=1e-12)
 
 
-def test_gradients_match_finite_differences():
+@pytest.mark.parametrize("inner", [False, True])
+def test_gradients_match_finite_differences(inner):
     """At these penalties 40 iterations reach a state where loads are served,
     some generators sit at capacity and some lines at their limit, so every
-    gradient path is active; entries with a nonzero gradient are checked
+    gradient path is active (with ``inner``, through the inner ADMM of ramp
+    generators and batteries); entries with a nonzero gradient are checked
     first, then a few zero ones."""
-    case = _case()
+    case = _case_inner() if inner else _case()
     K = 40
     ur = Unrolled(case, rho_p=10.0, rho_theta=20.0)
     prm = ur.params()
