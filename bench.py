@@ -19,7 +19,7 @@ lognormal(0, 0.05) cold, and that perturbed instance warm-started from the
 first solution (Section 3.4).
 
 ``--adjoint K``: wall time of the cost gradient after K unrolled iterations
-(include/opf_diff.h) on the 2k network with closed-form devices.
+(include/opf_diff.h) on the 2k instance, checkpoints every 20 iterations.
 
 ``--impl reference`` times the FP64 oracle on the host cores instead; each
 step is one oracle iteration on a bounded sample of the instance (the 10k
@@ -451,14 +451,14 @@ def learned_warm_start(stream, args):
 
 def adjoint_leg(stream, args):
     """Cost and gradient after K unrolled iterations (include/opf_diff.h) on
-    the 2k network with closed-form devices (no batteries, no ramp limits):
-    wall time of one forward + reverse pass against the forward alone."""
+    the 2k instance (ramp-limited generators and batteries through the inner
+    ADMM): wall time of one forward + reverse pass against the forward alone."""
     import numpy as np
     import torch
     from gridgen import make_case
     from paper_2410_17203_gb300 import UnrolledCost
 
-    case = make_case("2k", n_stor=0, ramp=False)
+    case = make_case("2k")
     K, ck = args.adjoint, 20
     d = UnrolledCost(case, rho_p=1.0, rho_theta=1.0, checkpoint_every=ck, stream=stream.cuda_stream)
     try:
@@ -474,8 +474,8 @@ def adjoint_leg(stream, args):
     finally:
         d.close()
     torch.cuda.synchronize()
-    return {"network": "2k buses, T=24, K=20, curtailable loads, generators without ramp limits, "
-                       "no batteries (closed-form proxes), seed 1",
+    return {"network": "2k instance: 2000 buses, T=24, K=20, 500 ramp-limited generators, 1500 curtailable "
+                       "loads, 100 batteries, seed 1; gradients w.r.t. loads, capacities and line limits",
             "iterations": K, "checkpoint_every": ck, "seconds_cost_and_gradient": float(np.median(t_fg)),
             "seconds_cost_only": float(np.median(t_f)), "cost": f,
             "grad_norms": {k: float(np.linalg.norm(v)) for k, v in g.items()}}
@@ -648,8 +648,7 @@ def main():
     ap.add_argument("--batched", type=int, default=0,
                     help="also solve this many independent instances to eps = 1e-4, one by one and as one batch")
     ap.add_argument("--adjoint", type=int, default=0,
-                    help="also time the cost gradient after this many unrolled iterations (2k network, "
-                         "closed-form devices)")
+                    help="also time the cost gradient after this many unrolled iterations on the 2k instance")
     ap.add_argument("--_oracle-child", dest="oracle_child", default=None)
     args = ap.parse_args()
     if args.oracle_child:

@@ -8,6 +8,7 @@
  * adaptation: the adaptive rule is a discrete decision) and returns
  *
  *     f(p^K) = sum_gen (a p^2 + b p) + sum_curtailable voll (p + P)
+ *              + sum_batteries cost . delta
  *
  * and its gradient with respect to the load power P [D][T], the generator
  * capacity pmax [G][T] and the line limits u [L], by a hand-written reverse
@@ -15,11 +16,16 @@
  * proxes, the node averages and the price updates).  The forward states are
  * kept every `checkpoint_every` iterations and recomputed in between.
  *
- * Scope: devices with a closed-form prox -- generators without ramp limits
- * (or T = 1), fixed and curtailable loads; networks with batteries or
- * ramp-limited generators are rejected with OPF_EINVAL.  Clipping follows
- * torch.clamp: the clipped value passes its gradient where lo <= x <= hi, a
- * bound receives it where x leaves the interval on its side.
+ * Every device type is covered.  Ramp-limited generators (T > 1) and
+ * batteries take their prox from 10 iterations of the Appendix D inner ADMM
+ * (omega = (K+1) rho_p, duals beta and lambda carried across outer
+ * iterations from zero), differentiated through those iterations; delta is
+ * a battery's discharge in the last inner iterate, and a ramp generator's
+ * capacity enters through the right-hand side of its p_t <= pmax_t rows.
+ * Clipping follows torch.clamp: the clipped value passes its gradient where
+ * lo <= x <= hi, a bound receives it where x leaves the interval on its
+ * side; the inner projection min(alpha + lambda, 0) is a clamp with upper
+ * bound 0.
  *
  * Arrays are in the caller's numbering and layout (opf.h); host pointers.
  * The computation runs in FP32 on the device; the cost is summed in FP64.
@@ -38,7 +44,9 @@ extern "C" {
 typedef struct opf_diff opf_diff; /* opaque */
 
 /* Copy the network (as opf_create) for differentiation with penalties
- * rho_p, rho_theta > 0; checkpoint_every >= 1. */
+ * rho_p, rho_theta > 0; checkpoint_every >= 1.  OPF_EINVAL for invalid data
+ * or a horizon whose inner-ADMM working set does not fit one CTA's shared
+ * memory (about T = 600). */
 opf_status opf_diff_create(const opf_network *net, int32_t horizon_T, const opf_contingencies *ctg,
                            double rho_p, double rho_theta, int32_t checkpoint_every,
                            void *cuda_stream, opf_diff **out);

@@ -2,17 +2,20 @@
 //
 // A self-contained differentiable path in the caller's numbering: the state
 // (p, theta1, theta2, v1, v2 per line and contingency; device power; u, and
-// the node averages pbar, theta_bar per node and contingency) is kept in
+// the node averages pbar, theta_bar per node and contingency; the inner-ADMM
+// duals beta, lambda of ramp-limited generators and batteries) is kept in
 // plain arrays, and every step of the iteration has a forward kernel and an
 // adjoint kernel.  Forward states are stored every `checkpoint_every`
 // iterations and recomputed segment by segment during the reverse pass.
 // Every adjoint item writes only its own entries (sums over a node's
-// terminals are CSR gathers), so the gradients are deterministic.
+// terminals are CSR gathers, an inner device is one CTA), so the gradients
+// are deterministic.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "opf_diff.h"
@@ -20,11 +23,24 @@
 
 namespace {
 
-constexpr int TB = 256;
+constexpr int TB = 256;       // threads per CTA of the element-wise kernels
+constexpr int TBI = 128;      // threads per CTA of the inner-ADMM kernels (one CTA per device)
+constexpr int N_INNER = 10;   // Appendix D iterations per prox evaluation (Section 4.5)
+
+// one inner-ADMM device: its index among all devices, its constraint shape,
+// and offsets of its inverse system matrix, right-hand side rows and linear cost
+struct IDev {
+  int dev, shape, minv, h, q, bat, pad0, pad1;  // bat: battery index, -1 for a generator
+};
+
+// constraint rows A z <= h (eq: = h) of one device kind, in CSR and CSC form
+struct Shape {
+  int n, m, rp, ci, tp, ti, eq, pad;
+};
 
 struct DP {
-  int N, L, T, Kp, G, D, S;
-  float rp, rt, rd;                    // rho_p, rho_theta, (K+1) rho_p
+  int N, L, T, Kp, G, D, B, S;
+  float rp, rt, rd;                    // rho_p, rho_theta, (K+1) rho_p (= omega of the inner ADMM)
   const int *n1, *n2;                  // line ends (terminal 1 at n1 carries -p)
   const float *b;                      // susceptance [L]
   const int *out;                      // [Kp] outaged line, -1 = none
@@ -32,17 +48,25 @@ struct DP {
   const int *dptr, *didx;              // node -> devices
   const float *cnt, *cth;              // terminals at a node: all, line (0: none)
   const int *dnode;                    // device node [S]
+  const int *kind;                     // [S] 0: closed-form prox, 1: inner ADMM
   const float *ga, *gb, *gpmin;        // generators: a, b [G]; pmin [G][T]
   const float *voll;                   // loads [D], < 0: fixed
   const float *load_p, *gpmax, *lu;    // data: [D][T], [G][T], [L]
+  // inner ADMM (Appendix D)
+  int n_inner, Mtot;                   // devices, rows over all devices
+  const IDev *idev;
+  const Shape *shape;
+  const int *arp, *aci, *atp, *ati;
+  const float *acv, *atv, *minv, *H, *Q, *scost;
+  const unsigned char *aeq;
 };
 
 struct St {
-  float *P, *TH1, *TH2, *V1, *V2, *PD, *U, *PB, *TBR;
+  float *P, *TH1, *TH2, *V1, *V2, *PD, *U, *PB, *TBR, *INS;  // INS: beta [Mtot] then lambda [Mtot]
 };
 
 struct Adj {
-  float *LP, *LT1, *LT2, *LV1, *LV2, *LPD, *LU;
+  float *LP, *LT1, *LT2, *LV1, *LV2, *LPD, *LU, *LINS;
 };
 
 __device__ __forceinline__ size_t li(const DP &p, int k, int l, int t) { return ((size_t)k * p.L + l) * p.T + t; }
@@ -115,11 +139,16 @@ __device__ __forceinline__ float dev_x(const DP &p, const St &s, int d, int t) {
   return s.PD[(size_t)d * p.T + t] - sum / (float)p.Kp;   // p_d - avg_k(pbar + u)
 }
 
-// step 2: devices shared by all contingencies, weight (K+1) rho_p
-__global__ void fwd_dev(DP p, St s, St nx) {
+// step 2: devices shared by all contingencies, weight (K+1) rho_p; the
+// inner-ADMM devices only record their input X here
+__global__ void fwd_dev(DP p, St s, St nx, float *XD) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
     const int t = (int)(i % p.T), d = (int)(i / p.T);
     const float X = dev_x(p, s, d, t);
+    if (p.kind[d]) {
+      XD[i] = X;
+      continue;
+    }
     float r;
     if (d < p.G) {
       const float z = (p.rd * X - p.gb[d]) / (2.f * p.ga[d] + p.rd);
@@ -131,6 +160,69 @@ __global__ void fwd_dev(DP p, St s, St nx) {
       else r = fminf(fmaxf((p.rd * X - p.voll[e]) / p.rd, -p.load_p[o]), 0.f);
     }
     nx.PD[i] = r;
+  }
+}
+
+// N_INNER iterations of the Appendix D ADMM for the device of this CTA:
+//   z = M^-1 (rho' E_p' x - q + omega A'(h + beta - lambda)),
+//   alpha = A z - h, beta = min(alpha + lambda, 0) (0 on equality rows),
+//   lambda = alpha + lambda - beta;
+// mask (optional) records the rows where beta took alpha + lambda
+__device__ void inner_forward(const DP &p, const Shape &sh, const IDev &di, const float *x, float *beta, float *lam,
+                              float *w, float *r, float *z, unsigned char *mask) {
+  const int n = sh.n, m = sh.m, T = p.T;
+  const float rho = p.rd, om = p.rd;
+  const float *Mi = p.minv + di.minv, *h = p.H + di.h, *q = p.Q + di.q;
+  for (int it = 0; it < N_INNER; ++it) {
+    for (int row = threadIdx.x; row < m; row += blockDim.x) w[row] = h[row] + beta[row] - lam[row];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      float acc = 0.f;
+      for (int e = p.atp[sh.tp + j]; e < p.atp[sh.tp + j + 1]; ++e) acc += p.atv[sh.ti + e] * w[p.ati[sh.ti + e]];
+      r[j] = -q[j] + om * acc + (j < T ? rho * x[j] : 0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {     // M^-1 is symmetric: read its columns coalesced
+      float acc = 0.f;
+      for (int j = 0; j < n; ++j) acc += Mi[(size_t)j * n + i] * r[j];
+      z[i] = acc;
+    }
+    __syncthreads();
+    for (int row = threadIdx.x; row < m; row += blockDim.x) {
+      float al = -h[row];
+      for (int e = p.arp[sh.rp + row]; e < p.arp[sh.rp + row + 1]; ++e) al += p.acv[sh.ci + e] * z[p.aci[sh.ci + e]];
+      const float s = al + lam[row];
+      const bool eq = p.aeq[sh.eq + row] != 0;
+      const float bt = eq ? 0.f : fminf(s, 0.f);
+      if (mask) mask[it * m + row] = (!eq && s <= 0.f);
+      beta[row] = bt;
+      lam[row] = s - bt;
+    }
+    __syncthreads();
+  }
+}
+
+// step 2 for the inner-ADMM devices: one CTA per device
+__global__ void __launch_bounds__(TBI) fwd_inner(DP p, St s, St nx, const float *XD, float *DEL) {
+  extern __shared__ float sm[];
+  const IDev di = p.idev[blockIdx.x];
+  const Shape sh = p.shape[di.shape];
+  const int n = sh.n, m = sh.m, T = p.T;
+  float *x = sm, *r = x + T, *z = r + n, *w = z + n, *beta = w + m, *lam = beta + m;
+  for (int t = threadIdx.x; t < T; t += blockDim.x) x[t] = XD[(size_t)di.dev * T + t];
+  for (int row = threadIdx.x; row < m; row += blockDim.x) {
+    beta[row] = s.INS[di.h + row];
+    lam[row] = s.INS[p.Mtot + di.h + row];
+  }
+  __syncthreads();
+  inner_forward(p, sh, di, x, beta, lam, w, r, z, nullptr);
+  for (int t = threadIdx.x; t < T; t += blockDim.x) {
+    nx.PD[(size_t)di.dev * T + t] = z[t];
+    if (di.bat >= 0) DEL[(size_t)di.bat * T + t] = z[2 * T + t];   // discharge, for the cost
+  }
+  for (int row = threadIdx.x; row < m; row += blockDim.x) {
+    nx.INS[di.h + row] = beta[row];
+    nx.INS[p.Mtot + di.h + row] = lam[row];
   }
 }
 
@@ -208,13 +300,20 @@ __global__ void bwd_line1(DP p, St s, Adj a, const float *A, const float *B, flo
   }
 }
 
-// the device proxes backwards; LX = d/dX per device
-__global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL, float *GP) {
+// the closed-form device proxes backwards; LX = d/dX per device.  For an
+// inner-ADMM device the kernel records X and the adjoint of its output for
+// bwd_inner.
+__global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL, float *GP, float *XD, float *LPDT) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
     const int t = (int)(i % p.T), d = (int)(i / p.T), n = p.dnode[d];
     float lpd = a.LPD[i];
     for (int k = 0; k < p.Kp; ++k) lpd += A[ni(p, k, n, t)] / p.cnt[n];
     const float X = dev_x(p, s, d, t);
+    if (p.kind[d]) {
+      XD[i] = X;
+      LPDT[i] = lpd;
+      continue;
+    }
     float lx = 0.f;
     if (d < p.G) {
       const float den = 2.f * p.ga[d] + p.rd;
@@ -233,6 +332,84 @@ __global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL,
       }
     }
     LX[i] = lx;
+  }
+}
+
+// the inner ADMM backwards, one CTA per device: recompute the N_INNER
+// iterations from state i-1 recording which rows clipped, then walk them in
+// reverse.  Per iteration, with s = alpha + lambda:
+//   d s = d lambda' + [clipped] (d beta' - d lambda'),
+//   d z = A' d s (+ the output's adjoint on the last iteration), d h -= d s,
+//   d r = M^-1 d z, d x += rho' (d r)_p, w = omega A d r:
+//   d h += w, d beta = w, d lambda = d s - w.
+// `last`: the iteration whose battery discharge enters the cost.
+__global__ void __launch_bounds__(TBI) bwd_inner(DP p, St s, Adj a, const float *XD, const float *LPDT, float *LX,
+                                                 float *HB, int last) {
+  extern __shared__ float sm[];
+  const IDev di = p.idev[blockIdx.x];
+  const Shape sh = p.shape[di.shape];
+  const int n = sh.n, m = sh.m, T = p.T;
+  const float rho = p.rd, om = p.rd;
+  float *x = sm, *r = x + T, *z = r + n, *w = z + n, *beta = w + m, *lam = beta + m;
+  float *zt = lam + m, *rb = zt + n, *sb = rb + n, *bb = sb + m, *lb = bb + m, *hb = lb + m, *xb = hb + m;
+  unsigned char *mask = reinterpret_cast<unsigned char *>(xb + T);
+  for (int t = threadIdx.x; t < T; t += blockDim.x) {
+    x[t] = XD[(size_t)di.dev * T + t];
+    xb[t] = 0.f;
+  }
+  for (int row = threadIdx.x; row < m; row += blockDim.x) {
+    beta[row] = s.INS[di.h + row];
+    lam[row] = s.INS[p.Mtot + di.h + row];
+  }
+  __syncthreads();
+  inner_forward(p, sh, di, x, beta, lam, w, r, z, mask);
+  for (int row = threadIdx.x; row < m; row += blockDim.x) {
+    bb[row] = a.LINS[di.h + row];
+    lb[row] = a.LINS[p.Mtot + di.h + row];
+    hb[row] = 0.f;
+  }
+  __syncthreads();
+  const float *Mi = p.minv + di.minv;
+  const float dcost = (last && di.bat >= 0) ? p.scost[di.bat] : 0.f;
+  for (int it = N_INNER - 1; it >= 0; --it) {
+    for (int row = threadIdx.x; row < m; row += blockDim.x) {
+      const float sv = lb[row] + (mask[it * m + row] ? bb[row] - lb[row] : 0.f);
+      sb[row] = sv;
+      hb[row] -= sv;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      float acc = 0.f;
+      for (int e = p.atp[sh.tp + j]; e < p.atp[sh.tp + j + 1]; ++e) acc += p.atv[sh.ti + e] * sb[p.ati[sh.ti + e]];
+      if (it == N_INNER - 1) {           // the output: p = z_p, and the discharge z_delta in the cost
+        if (j < T) acc += LPDT[(size_t)di.dev * T + j];
+        else if (j >= 2 * T && j < 3 * T) acc += dcost;
+      }
+      zt[j] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      float acc = 0.f;
+      for (int j = 0; j < n; ++j) acc += Mi[(size_t)j * n + i] * zt[j];
+      rb[i] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x) xb[t] += rho * rb[t];
+    for (int row = threadIdx.x; row < m; row += blockDim.x) {
+      float acc = 0.f;
+      for (int e = p.arp[sh.rp + row]; e < p.arp[sh.rp + row + 1]; ++e) acc += p.acv[sh.ci + e] * rb[p.aci[sh.ci + e]];
+      const float wv = om * acc;
+      hb[row] += wv;
+      bb[row] = wv;
+      lb[row] = sb[row] - wv;
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < T; t += blockDim.x) LX[(size_t)di.dev * T + t] = xb[t];
+  for (int row = threadIdx.x; row < m; row += blockDim.x) {
+    a.LINS[di.h + row] = bb[row];
+    a.LINS[p.Mtot + di.h + row] = lb[row];
+    HB[di.h + row] += hb[row];
   }
 }
 
@@ -277,29 +454,41 @@ __global__ void bwd_dev2(DP p, Adj a, const float *LX, const float *C) {
   }
 }
 
-// d f / d p_d at the last iterate, and f's direct dependence on P
+// d f / d p_d at the last iterate, and f's direct dependence on P (the
+// battery discharge term enters through bwd_inner's `last`)
 __global__ void bwd_init(DP p, St s, Adj a, float *GL) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
     const int t = (int)(i % p.T), d = (int)(i / p.T);
     if (d < p.G) {
       a.LPD[i] = 2.f * p.ga[d] * s.PD[i] + p.gb[d];
-    } else {
+    } else if (d < p.G + p.D) {
       const int e = d - p.G;
       a.LPD[i] = p.voll[e] < 0.f ? 0.f : p.voll[e];
       if (p.voll[e] >= 0.f) GL[(size_t)e * p.T + t] = p.voll[e];
+    } else {
+      a.LPD[i] = 0.f;
     }
   }
 }
 
 int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + TB - 1) / TB, 8192)); }
 
+size_t fwd_inner_smem(int T, int n, int m) { return (size_t)(T + 2 * n + 3 * m) * sizeof(float); }
+size_t bwd_inner_smem(int T, int n, int m) { return (size_t)(2 * T + 4 * n + 7 * m) * sizeof(float) + (size_t)N_INNER * m; }
+
 }  // namespace
 
 struct opf_diff {
-  int N = 0, L = 0, T = 0, Kp = 0, G = 0, D = 0, S = 0, ckpt = 1;
+  int N = 0, L = 0, T = 0, Kp = 0, G = 0, D = 0, B = 0, S = 0, ckpt = 1;
   cudaStream_t stream = nullptr;
   DP p{};
-  std::vector<float> ga, gb, voll, load_p, gpmax, lu;  // host copies (cost and defaults)
+  std::vector<float> ga, gb, voll, load_p, gpmax, lu, scost;  // host copies (cost and defaults)
+  std::vector<double> gpmin, ramp, sP, sdur;                 // right-hand sides of the inner rows
+  std::vector<int> ramp_gens;                                // generator of each ramp device
+  std::vector<IDev> idev;
+  int Mtot = 0;
+  size_t smem_fwd = 0, smem_bwd = 0;
+  float *H = nullptr;                                        // device copy of the right-hand sides
   std::vector<void *> allocs;
   size_t state_floats = 0;
 };
@@ -330,6 +519,108 @@ cudaError_t up(std::vector<void *> &list, const T **dst, const std::vector<T> &v
   return e;
 }
 
+// constraint rows of one device kind, as (row, column, value) lists
+struct Rows {
+  int n = 0, m = 0;
+  std::vector<std::vector<std::pair<int, double>>> row;
+  std::vector<unsigned char> eq;
+  void add(std::vector<std::pair<int, double>> r, bool is_eq) {
+    row.push_back(std::move(r));
+    eq.push_back(is_eq ? 1 : 0);
+    m = (int)row.size();
+  }
+};
+
+// generator with box and ramp limits (Section 2.1), variables p_0..p_{T-1}:
+// p_t <= pmax_t, -p_t <= -pmin_t, p_{t+1} - p_t <= R, p_t - p_{t+1} <= R
+Rows ramp_shape(int T) {
+  Rows r;
+  r.n = T;
+  for (int t = 0; t < T; ++t) r.add({{t, 1.0}}, false);
+  for (int t = 0; t < T; ++t) r.add({{t, -1.0}}, false);
+  for (int t = 0; t + 1 < T; ++t) r.add({{t + 1, 1.0}, {t, -1.0}}, false);
+  for (int t = 0; t + 1 < T; ++t) r.add({{t, 1.0}, {t + 1, -1.0}}, false);
+  return r;
+}
+
+void ramp_rhs(int T, const double *pmin, const double *pmax, double R, float *h) {
+  int o = 0;
+  for (int t = 0; t < T; ++t) h[o++] = (float)pmax[t];
+  for (int t = 0; t < T; ++t) h[o++] = (float)(-pmin[t]);
+  for (int i = 0; i < 2 * (T - 1); ++i) h[o++] = (float)R;
+}
+
+// battery (Section 2.1), variables (p, c, delta, s) with s of length T + 1:
+// p + c - delta = 0, s_{t+1} - s_t - eff c_t + delta_t = 0, s_0 = s_T = 0,
+// 0 <= c <= P, 0 <= delta <= P, 0 <= s <= dur P
+Rows storage_shape(int T, double eff) {
+  Rows r;
+  r.n = 4 * T + 1;
+  const int c0 = T, d0 = 2 * T, s0 = 3 * T;
+  for (int t = 0; t < T; ++t) r.add({{t, 1.0}, {c0 + t, 1.0}, {d0 + t, -1.0}}, true);
+  for (int t = 0; t < T; ++t) r.add({{s0 + t + 1, 1.0}, {s0 + t, -1.0}, {c0 + t, -eff}, {d0 + t, 1.0}}, true);
+  r.add({{s0, 1.0}}, true);
+  r.add({{s0 + T, 1.0}}, true);
+  for (int t = 0; t < T; ++t) r.add({{c0 + t, 1.0}}, false);
+  for (int t = 0; t < T; ++t) r.add({{c0 + t, -1.0}}, false);
+  for (int t = 0; t < T; ++t) r.add({{d0 + t, 1.0}}, false);
+  for (int t = 0; t < T; ++t) r.add({{d0 + t, -1.0}}, false);
+  for (int t = 0; t <= T; ++t) r.add({{s0 + t, 1.0}}, false);
+  for (int t = 0; t <= T; ++t) r.add({{s0 + t, -1.0}}, false);
+  return r;
+}
+
+void storage_rhs(int T, double P, double dur, float *h) {
+  int o = 0;
+  for (int i = 0; i < 2 * T + 2; ++i) h[o++] = 0.f;
+  for (int t = 0; t < T; ++t) h[o++] = (float)P;
+  for (int t = 0; t < T; ++t) h[o++] = 0.f;
+  for (int t = 0; t < T; ++t) h[o++] = (float)P;
+  for (int t = 0; t < T; ++t) h[o++] = 0.f;
+  for (int t = 0; t <= T; ++t) h[o++] = (float)(dur * P);
+  for (int t = 0; t <= T; ++t) h[o++] = 0.f;
+}
+
+// inverse of the symmetric positive definite M = diag(qd) + omega A'A (FP64
+// Cholesky, then one solve per unit vector), stored as FP32
+bool spd_inverse(const Rows &r, const std::vector<double> &qd, double omega, std::vector<float> &out) {
+  const int n = r.n;
+  std::vector<double> M((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) M[(size_t)i * n + i] = qd[i];
+  for (const auto &row : r.row)
+    for (const auto &a : row)
+      for (const auto &b : row) M[(size_t)a.first * n + b.first] += omega * a.second * b.second;
+  for (int j = 0; j < n; ++j) {                      // M = C C', C lower, in place
+    double d = M[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= M[(size_t)j * n + k] * M[(size_t)j * n + k];
+    if (!(d > 0)) return false;
+    d = std::sqrt(d);
+    M[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double v = M[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) v -= M[(size_t)i * n + k] * M[(size_t)j * n + k];
+      M[(size_t)i * n + j] = v / d;
+    }
+  }
+  const size_t base = out.size();
+  out.resize(base + (size_t)n * n);
+  std::vector<double> y(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {                    // C y = e_c
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) v -= M[(size_t)i * n + k] * y[k];
+      y[i] = v / M[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {               // C' x = y
+      double v = y[i];
+      for (int k = i + 1; k < n; ++k) v -= M[(size_t)k * n + i] * y[k];
+      y[i] = v / M[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) out[base + (size_t)c * n + i] = (float)y[i];
+  }
+  return true;
+}
+
 St carve_state(const opf_diff *d, float *base) {
   const size_t KLT = (size_t)d->Kp * d->L * d->T, KNT = (size_t)d->Kp * d->N * d->T, ST = (size_t)d->S * d->T;
   St s;
@@ -342,15 +633,17 @@ St carve_state(const opf_diff *d, float *base) {
   s.PD = c; c += ST;
   s.U = c; c += KNT;
   s.PB = c; c += KNT;
-  s.TBR = c;
+  s.TBR = c; c += KNT;
+  s.INS = c;
   return s;
 }
 
-void forward_step(const opf_diff *d, const St &s, const St &nx) {
+void forward_step(const opf_diff *d, const St &s, const St &nx, float *XD, float *DEL) {
   const DP &p = d->p;
   const long long nl = (long long)p.Kp * p.L * p.T, nn = (long long)p.Kp * p.N * p.T, ns = (long long)p.S * p.T;
   fwd_line<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx);
-  fwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, nx);
+  fwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, nx, XD);
+  if (p.n_inner) fwd_inner<<<p.n_inner, TBI, d->smem_fwd, d->stream>>>(p, s, nx, XD, DEL);
   fwd_avg<<<grid_for(nn), TB, 0, d->stream>>>(p, nx);
   fwd_upd_nodes<<<grid_for(nn), TB, 0, d->stream>>>(p, s, nx);
   fwd_upd_lines<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx);
@@ -367,12 +660,8 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   if (!net || T < 1) return dfail(OPF_EINVAL, "NULL network or horizon < 1");
   if (!(rho_p > 0) || !(rho_theta > 0) || checkpoint_every < 1)
     return dfail(OPF_EINVAL, "diff: penalties must be > 0 and checkpoint_every >= 1");
-  const int N = net->n_nodes, L = net->n_lines, G = net->n_gens, D = net->n_loads;
-  if (N < 1 || L < 0 || G < 0 || D < 0) return dfail(OPF_EINVAL, "diff: bad sizes");
-  if (net->n_stor > 0) return dfail(OPF_EINVAL, "diff: batteries are not covered (closed-form devices only)");
-  for (int g = 0; g < G; ++g)
-    if (net->gen_ramp && net->gen_ramp[g] >= 0 && T > 1)
-      return dfail(OPF_EINVAL, "diff: ramp-limited generators are not covered (closed-form devices only)");
+  const int N = net->n_nodes, L = net->n_lines, G = net->n_gens, D = net->n_loads, B = net->n_stor;
+  if (N < 1 || L < 0 || G < 0 || D < 0 || B < 0) return dfail(OPF_EINVAL, "diff: bad sizes");
   const int K = ctg ? ctg->K : 0;
   for (int l = 0; l < L; ++l) {
     const int a = net->line_from[l], c = net->line_to[l];
@@ -382,6 +671,9 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   for (int k = 0; k < K; ++k)
     if (ctg->outaged_line[k] < -1 || ctg->outaged_line[k] >= L)
       return dfail(OPF_EINVAL, "diff: outaged line id out of range");
+  for (int b = 0; b < B; ++b)
+    if (!(net->stor_P[b] >= 0) || !(net->stor_dur[b] >= 0) || !(net->stor_eff[b] > 0 && net->stor_eff[b] <= 1))
+      return dfail(OPF_EINVAL, "diff: bad battery data");
   auto *d = new (std::nothrow) opf_diff();
   if (!d) return dfail(OPF_ENOMEM, "host allocation failed");
   d->N = N;
@@ -390,11 +682,12 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   d->Kp = K + 1;
   d->G = G;
   d->D = D;
-  d->S = G + D;
+  d->B = B;
+  d->S = G + D + B;
   d->ckpt = checkpoint_every;
   d->stream = (cudaStream_t)cuda_stream;
   // incidence by node (caller's numbering)
-  std::vector<int> lptr(N + 1, 0), lcode(2 * (size_t)L), dptr(N + 1, 0), didx(d->S), dnode(d->S);
+  std::vector<int> lptr(N + 1, 0), lcode(2 * (size_t)L), dptr(N + 1, 0), didx(d->S), dnode(d->S), kind(d->S, 0);
   std::vector<float> cnt(N, 0.f), cth(N, 0.f);
   for (int l = 0; l < L; ++l) {
     ++lptr[net->line_from[l] + 1];
@@ -402,6 +695,7 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   }
   for (int g = 0; g < G; ++g) dnode[g] = net->gen_node[g];
   for (int e = 0; e < D; ++e) dnode[G + e] = net->load_node[e];
+  for (int b = 0; b < B; ++b) dnode[G + D + b] = net->stor_node[b];
   for (int s = 0; s < d->S; ++s) {
     if (dnode[s] < 0 || dnode[s] >= N) {
       delete d;
@@ -449,6 +743,120 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   for (size_t i = 0; i < (size_t)D * T; ++i) d->load_p[i] = (float)net->load_p[i];
   for (size_t i = 0; i < (size_t)G * T; ++i) d->gpmax[i] = (float)net->gen_pmax[i];
   for (int l = 0; l < L; ++l) d->lu[l] = (float)net->line_u[l];
+  d->gpmin.assign(net->gen_pmin, net->gen_pmin + (size_t)G * T);
+  // inner-ADMM devices (Appendix D): ramp-limited generators (T > 1), batteries
+  const double rd = (double)d->Kp * rho_p;
+  std::vector<Shape> shapes;
+  std::vector<int> arp, aci, atp, ati;
+  std::vector<float> acv, atv, minv, qv;
+  std::vector<unsigned char> aeq;
+  auto add_shape = [&](const Rows &r) {
+    Shape s{};
+    s.n = r.n;
+    s.m = r.m;
+    s.rp = (int)arp.size();
+    s.ci = (int)aci.size();
+    s.tp = (int)atp.size();
+    s.ti = (int)ati.size();
+    s.eq = (int)aeq.size();
+    arp.push_back(0);
+    std::vector<std::vector<std::pair<int, double>>> cols(r.n);
+    for (int i = 0; i < r.m; ++i) {
+      for (const auto &a : r.row[i]) {
+        aci.push_back(a.first);
+        acv.push_back((float)a.second);
+        cols[a.first].push_back({i, a.second});
+      }
+      arp.push_back((int)(aci.size() - s.ci));
+    }
+    atp.push_back(0);
+    for (int j = 0; j < r.n; ++j) {
+      for (const auto &a : cols[j]) {
+        ati.push_back(a.first);
+        atv.push_back((float)a.second);
+      }
+      atp.push_back((int)(ati.size() - s.ti));
+    }
+    aeq.insert(aeq.end(), r.eq.begin(), r.eq.end());
+    shapes.push_back(s);
+    return (int)shapes.size() - 1;
+  };
+  bool ok = true;
+  int hoff = 0;
+  if (T > 1 && net->gen_ramp) {
+    const Rows rr = ramp_shape(T);
+    int sh = -1;
+    for (int g = 0; g < G && ok; ++g) {
+      if (!(net->gen_ramp[g] >= 0)) continue;
+      if (sh < 0) sh = add_shape(rr);
+      IDev di{};
+      di.dev = g;
+      di.shape = sh;
+      di.minv = (int)minv.size();
+      di.h = hoff;
+      di.q = (int)qv.size();
+      di.bat = -1;
+      std::vector<double> qd(T, 2.0 * net->gen_a[g] + rd);   // 2 a + rho' on every step (all are power)
+      ok = spd_inverse(rr, qd, rd, minv);
+      for (int t = 0; t < T; ++t) qv.push_back((float)net->gen_b[g]);
+      hoff += rr.m;
+      kind[g] = 1;
+      d->ramp_gens.push_back(g);
+      d->ramp.push_back(net->gen_ramp[g]);
+      d->idev.push_back(di);
+    }
+  }
+  if (B > 0 && ok) {
+    std::map<double, std::pair<int, int>> by_eff;   // eff -> (shape, minv offset)
+    for (int bt = 0; bt < B && ok; ++bt) {
+      const double eff = net->stor_eff[bt];
+      auto it = by_eff.find(eff);
+      const Rows rs = storage_shape(T, eff);
+      if (it == by_eff.end()) {
+        const int sh = add_shape(rs);
+        const int mo = (int)minv.size();
+        std::vector<double> qd(rs.n, 0.0);
+        for (int t = 0; t < T; ++t) qd[t] = rd;       // rho' on the power entries
+        ok = spd_inverse(rs, qd, rd, minv);
+        it = by_eff.emplace(eff, std::make_pair(sh, mo)).first;
+      }
+      IDev di{};
+      di.dev = G + D + bt;
+      di.shape = it->second.first;
+      di.minv = it->second.second;
+      di.h = hoff;
+      di.q = (int)qv.size();
+      di.bat = bt;
+      for (int j = 0; j < rs.n; ++j) qv.push_back((j >= 2 * T && j < 3 * T) ? (float)net->stor_cost[bt] : 0.f);
+      hoff += rs.m;
+      kind[G + D + bt] = 1;
+      d->idev.push_back(di);
+    }
+  }
+  if (!ok) {
+    delete d;
+    return dfail(OPF_EINVAL, "diff: an inner-ADMM system matrix is not positive definite");
+  }
+  d->Mtot = hoff;
+  d->sP.assign(net->stor_P, net->stor_P + B);
+  d->sdur.assign(net->stor_dur, net->stor_dur + B);
+  d->scost.resize(B);
+  for (int bt = 0; bt < B; ++bt) d->scost[bt] = (float)net->stor_cost[bt];
+  for (const Shape &s : shapes) {
+    d->smem_fwd = std::max(d->smem_fwd, fwd_inner_smem(T, s.n, s.m));
+    d->smem_bwd = std::max(d->smem_bwd, bwd_inner_smem(T, s.n, s.m));
+  }
+  int dev = 0, smem_max = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess && (d->smem_bwd > (size_t)smem_max || d->smem_fwd > (size_t)smem_max)) {
+    delete d;
+    return dfail(OPF_EINVAL, "diff: the horizon is too long for one inner-ADMM device per CTA");
+  }
+  if (e == cudaSuccess && d->smem_fwd)
+    e = cudaFuncSetAttribute(fwd_inner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_fwd);
+  if (e == cudaSuccess && d->smem_bwd)
+    e = cudaFuncSetAttribute(bwd_inner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem_bwd);
   DP &p = d->p;
   p.N = N;
   p.L = L;
@@ -456,11 +864,13 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   p.Kp = d->Kp;
   p.G = G;
   p.D = D;
+  p.B = B;
   p.S = d->S;
   p.rp = (float)rho_p;
   p.rt = (float)rho_theta;
-  p.rd = (float)(d->Kp * rho_p);
-  cudaError_t e = cudaSuccess;
+  p.rd = (float)rd;
+  p.n_inner = (int)d->idev.size();
+  p.Mtot = d->Mtot;
   auto U = [&](auto **dst, const auto &v) {
     if (e == cudaSuccess) e = up(d->allocs, dst, v);
   };
@@ -475,20 +885,35 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   U(&p.cnt, cnt);
   U(&p.cth, cth);
   U(&p.dnode, dnode);
+  U(&p.kind, kind);
   U(&p.ga, d->ga);
   U(&p.gb, d->gb);
   U(&p.gpmin, gpmin);
   U(&p.voll, d->voll);
+  U(&p.idev, d->idev);
+  U(&p.shape, shapes);
+  U(&p.arp, arp);
+  U(&p.aci, aci);
+  U(&p.acv, acv);
+  U(&p.atp, atp);
+  U(&p.ati, ati);
+  U(&p.atv, atv);
+  U(&p.aeq, aeq);
+  U(&p.minv, minv);
+  U(&p.Q, qv);
+  U(&p.scost, d->scost);
   // data arrays, rewritten by every call
   U(&p.load_p, d->load_p);
   U(&p.gpmax, d->gpmax);
   U(&p.lu, d->lu);
+  if (e == cudaSuccess) e = dalloc(d->allocs, &d->H, (size_t)d->Mtot);
+  p.H = d->H;
   if (e != cudaSuccess) {
     for (void *q : d->allocs) cudaFree(q);
     delete d;
     return dfail(OPF_ECUDA, cudaGetErrorString(e));
   }
-  d->state_floats = 5 * (size_t)d->Kp * L * T + (size_t)d->S * T + 3 * (size_t)d->Kp * N * T;
+  d->state_floats = 5 * (size_t)d->Kp * L * T + (size_t)d->S * T + 3 * (size_t)d->Kp * N * T + 2 * (size_t)d->Mtot;
   *out = d;
   return OPF_OK;
 }
@@ -498,13 +923,24 @@ opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const
   if (!d) return dfail(OPF_EINVAL, "diff is NULL");
   if (K < 1) return dfail(OPF_EINVAL, "diff: K must be >= 1");
   const DP &p = d->p;
-  const size_t DT = (size_t)d->D * d->T, GT = (size_t)d->G * d->T, L = d->L;
-  std::vector<float> lp(load_p ? load_p : d->load_p.data(), (load_p ? load_p : d->load_p.data()) + DT);
-  DCK(cudaMemcpyAsync(const_cast<float *>(p.load_p), lp.data(), DT * 4, cudaMemcpyHostToDevice, d->stream));
-  DCK(cudaMemcpyAsync(const_cast<float *>(p.gpmax), gen_pmax ? gen_pmax : d->gpmax.data(), GT * 4,
-                      cudaMemcpyHostToDevice, d->stream));
+  const int T = d->T;
+  const size_t DT = (size_t)d->D * T, GT = (size_t)d->G * T, L = d->L, BT = (size_t)d->B * T;
+  const float *lp = load_p ? load_p : d->load_p.data();
+  const float *pm = gen_pmax ? gen_pmax : d->gpmax.data();
+  // right-hand sides of the inner rows (a ramp generator's first T rows are its capacity)
+  std::vector<float> H((size_t)d->Mtot);
+  for (size_t r = 0; r < d->ramp_gens.size(); ++r) {
+    const int g = d->ramp_gens[r];
+    std::vector<double> pmd(pm + (size_t)g * T, pm + (size_t)(g + 1) * T);
+    ramp_rhs(T, d->gpmin.data() + (size_t)g * T, pmd.data(), d->ramp[r], H.data() + d->idev[r].h);
+  }
+  for (int bt = 0; bt < d->B; ++bt)
+    storage_rhs(T, d->sP[bt], d->sdur[bt], H.data() + d->idev[d->ramp_gens.size() + bt].h);
+  DCK(cudaMemcpyAsync(const_cast<float *>(p.load_p), lp, DT * 4, cudaMemcpyHostToDevice, d->stream));
+  DCK(cudaMemcpyAsync(const_cast<float *>(p.gpmax), pm, GT * 4, cudaMemcpyHostToDevice, d->stream));
   DCK(cudaMemcpyAsync(const_cast<float *>(p.lu), line_u ? line_u : d->lu.data(), L * 4, cudaMemcpyHostToDevice,
                       d->stream));
+  if (d->Mtot) DCK(cudaMemcpyAsync(d->H, H.data(), H.size() * 4, cudaMemcpyHostToDevice, d->stream));
   // states: checkpoints 0, C, 2C, ... and one segment of C + 1 states
   const int C = std::min(d->ckpt, K);
   const int n_ck = K / C + 1;
@@ -514,15 +950,21 @@ opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const
     for (void *q : tmp) cudaFree(q);
   };
   float *ck = nullptr, *seg = nullptr, *adj = nullptr, *work = nullptr;
-  const size_t KLT = (size_t)d->Kp * d->L * d->T, KNT = (size_t)d->Kp * d->N * d->T, ST = (size_t)d->S * d->T;
+  const size_t KLT = (size_t)d->Kp * d->L * T, KNT = (size_t)d->Kp * d->N * T, ST = (size_t)d->S * T;
+  const size_t MT = (size_t)d->Mtot;
+  const size_t adj_floats = 5 * KLT + ST + KNT + 2 * MT;
+  const size_t work_floats = 5 * KLT + 4 * KNT + 3 * ST + DT + GT + MT + BT;
   cudaError_t e = dalloc(tmp, &ck, (size_t)n_ck * SF);
   if (e == cudaSuccess) e = dalloc(tmp, &seg, (size_t)(C + 1) * SF);
-  if (e == cudaSuccess) e = dalloc(tmp, &adj, 5 * KLT + ST + KNT);
-  if (e == cudaSuccess) e = dalloc(tmp, &work, 5 * KLT + 4 * KNT + ST + DT + GT);
+  if (e == cudaSuccess) e = dalloc(tmp, &adj, adj_floats);
+  if (e == cudaSuccess) e = dalloc(tmp, &work, work_floats);
   if (e != cudaSuccess) {
     release();
     return dfail(e == cudaErrorMemoryAllocation ? OPF_ENOMEM : OPF_ECUDA, "diff: device allocation failed");
   }
+  float *X1 = work, *X2 = X1 + KLT, *Y1 = X2 + KLT, *Y2 = Y1 + KLT, *GU = Y2 + KLT;
+  float *A = GU + KLT, *Bn = A + KNT, *Cn = Bn + KNT, *Dn = Cn + KNT, *LX = Dn + KNT, *XD = LX + ST;
+  float *LPDT = XD + ST, *GL = LPDT + ST, *GP = GL + DT, *HB = GP + GT, *DEL = HB + MT;
   auto ckst = [&](int j) { return carve_state(d, ck + (size_t)j * SF); };
   auto sgst = [&](int j) { return carve_state(d, seg + (size_t)j * SF); };
   // forward, keeping checkpoints
@@ -531,12 +973,13 @@ opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const
   float *scratch = seg;  // two alternating states in the segment buffer
   for (int i = 1; e == cudaSuccess && i <= K; ++i) {
     St nx = (i % C == 0) ? ckst(i / C) : carve_state(d, scratch + (size_t)(i & 1) * SF);
-    forward_step(d, cur, nx);
+    forward_step(d, cur, nx, XD, DEL);
     cur = nx;
   }
   if (e == cudaSuccess) e = cudaGetLastError();
-  std::vector<float> pd(ST);
+  std::vector<float> pd(ST), del(BT);
   if (e == cudaSuccess) e = cudaMemcpyAsync(pd.data(), cur.PD, ST * 4, cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess && BT) e = cudaMemcpyAsync(del.data(), DEL, BT * 4, cudaMemcpyDeviceToHost, d->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
   if (e != cudaSuccess) {
     release();
@@ -545,15 +988,17 @@ opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const
   if (cost) {
     double f = 0.0;
     for (int g = 0; g < d->G; ++g)
-      for (int t = 0; t < d->T; ++t) {
-        const double x = pd[(size_t)g * d->T + t];
+      for (int t = 0; t < T; ++t) {
+        const double x = pd[(size_t)g * T + t];
         f += d->ga[g] * x * x + d->gb[g] * x;
       }
     for (int k = 0; k < d->D; ++k) {
       if (d->voll[k] < 0) continue;
-      for (int t = 0; t < d->T; ++t)
-        f += (double)d->voll[k] * ((double)pd[(size_t)(d->G + k) * d->T + t] + lp[(size_t)k * d->T + t]);
+      for (int t = 0; t < T; ++t)
+        f += (double)d->voll[k] * ((double)pd[(size_t)(d->G + k) * T + t] + lp[(size_t)k * T + t]);
     }
+    for (int bt = 0; bt < d->B; ++bt)
+      for (int t = 0; t < T; ++t) f += (double)d->scost[bt] * del[(size_t)bt * T + t];
     *cost = f;
   }
   if (!g_load && !g_pmax && !g_u) {
@@ -569,23 +1014,24 @@ opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const
   a.LV2 = a.LV1 + KLT;
   a.LPD = a.LV2 + KLT;
   a.LU = a.LPD + ST;
-  float *X1 = work, *X2 = X1 + KLT, *Y1 = X2 + KLT, *Y2 = Y1 + KLT, *GU = Y2 + KLT;
-  float *A = GU + KLT, *B = A + KNT, *Cn = B + KNT, *Dn = Cn + KNT, *LX = Dn + KNT, *GL = LX + ST, *GP = GL + DT;
-  e = cudaMemsetAsync(adj, 0, (5 * KLT + ST + KNT) * 4, d->stream);
+  a.LINS = a.LU + KNT;
+  e = cudaMemsetAsync(adj, 0, adj_floats * 4, d->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(GU, 0, KLT * 4, d->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(GL, 0, (DT + GT) * 4, d->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(GL, 0, (DT + GT + MT) * 4, d->stream);
   if (e == cudaSuccess) bwd_init<<<grid_for((long long)ST), TB, 0, d->stream>>>(p, cur, a, GL);
   const long long nl = (long long)KLT, nn = (long long)KNT, ns = (long long)ST;
   for (int hi = K; e == cudaSuccess && hi > 0;) {
     // segment (lo, hi]: recompute states lo .. hi - 1 from checkpoint lo
     const int lo = ((hi - 1) / C) * C;
     e = cudaMemcpyAsync(seg, ck + (size_t)(lo / C) * SF, SF * 4, cudaMemcpyDeviceToDevice, d->stream);
-    for (int i = lo + 1; e == cudaSuccess && i < hi; ++i) forward_step(d, sgst(i - 1 - lo), sgst(i - lo));
+    for (int i = lo + 1; e == cudaSuccess && i < hi; ++i) forward_step(d, sgst(i - 1 - lo), sgst(i - lo), XD, DEL);
     for (int i = hi; e == cudaSuccess && i > lo; --i) {
       const St s = sgst(i - 1 - lo);   // state i - 1
-      bwd_node1<<<grid_for(nn), TB, 0, d->stream>>>(p, a, A, B);
-      bwd_line1<<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, B, X1, X2, Y1, Y2, GU);
-      bwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP);
+      bwd_node1<<<grid_for(nn), TB, 0, d->stream>>>(p, a, A, Bn);
+      bwd_line1<<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, Bn, X1, X2, Y1, Y2, GU);
+      bwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT);
+      if (p.n_inner)
+        bwd_inner<<<p.n_inner, TBI, d->smem_bwd, d->stream>>>(p, s, a, XD, LPDT, LX, HB, i == K ? 1 : 0);
       bwd_node2<<<grid_for(nn), TB, 0, d->stream>>>(p, a, X1, X2, Y1, Y2, LX, Cn, Dn);
       bwd_line2<<<grid_for(nl), TB, 0, d->stream>>>(p, a, Cn, Dn);
       bwd_dev2<<<grid_for(ns), TB, 0, d->stream>>>(p, a, LX, Cn);
@@ -593,19 +1039,26 @@ opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const
     hi = lo;
     if (e == cudaSuccess) e = cudaGetLastError();
   }
-  std::vector<float> gu(KLT);
+  std::vector<float> gu(KLT), hb(MT), gp(GT);
   if (e == cudaSuccess && g_load) e = cudaMemcpyAsync(g_load, GL, DT * 4, cudaMemcpyDeviceToHost, d->stream);
-  if (e == cudaSuccess && g_pmax) e = cudaMemcpyAsync(g_pmax, GP, GT * 4, cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess && g_pmax) e = cudaMemcpyAsync(gp.data(), GP, GT * 4, cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess && g_pmax && MT) e = cudaMemcpyAsync(hb.data(), HB, MT * 4, cudaMemcpyDeviceToHost, d->stream);
   if (e == cudaSuccess && g_u) e = cudaMemcpyAsync(gu.data(), GU, KLT * 4, cudaMemcpyDeviceToHost, d->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
   release();
   if (e != cudaSuccess) return dfail(OPF_ECUDA, cudaGetErrorString(e));
+  if (g_pmax) {
+    // a ramp generator's capacity is the right-hand side of its first T rows
+    for (size_t r = 0; r < d->ramp_gens.size(); ++r)
+      for (int t = 0; t < T; ++t) gp[(size_t)d->ramp_gens[r] * T + t] += hb[d->idev[r].h + t];
+    std::copy(gp.begin(), gp.end(), g_pmax);
+  }
   if (g_u) {
     // d f / d u_l: the limit is the same in every contingency and step
     for (int l = 0; l < d->L; ++l) {
       double s = 0.0;
       for (int k = 0; k < d->Kp; ++k)
-        for (int t = 0; t < d->T; ++t) s += gu[((size_t)k * d->L + l) * d->T + t];
+        for (int t = 0; t < T; ++t) s += gu[((size_t)k * d->L + l) * T + t];
       g_u[l] = (float)s;
     }
   }

@@ -77,7 +77,7 @@ def test_checkpointing_is_exact():
     """Recomputed segments repeat the forward pass bit for bit, so the
     gradients do not depend on the checkpoint spacing."""
     b = _lib()
-    case = make_case(scale_case(120, 4, 3, seed=8, ramp=False, stor_per_node=0.0, fixed_frac=0.3))
+    case = make_case(scale_case(120, 4, 3, seed=8, ramp=True, stor_per_node=0.05, fixed_frac=0.3))
     outs = []
     for ckpt in (1, 5, 64):
         d = b.UnrolledCost(case, rho_p=10.0, rho_theta=20.0, checkpoint_every=ckpt)
@@ -115,15 +115,26 @@ def test_data_arguments_replace_the_case_data():
     assert f0 != f
 
 
-def test_rejects_devices_without_closed_form_prox():
+def test_inner_admm_devices_match_autograd():
+    """Ramp-limited generators and batteries: the reverse pass runs through
+    the ten inner ADMM iterations of every outer iteration (Appendix D)."""
+    case = make_case(scale_case(40, 6, 2, seed=7, ramp=True, stor_per_node=0.1, fixed_frac=0.3))
+    _check(case, 40, ckpt=9)
+    case = make_case(scale_case(30, 1, 3, seed=9, ramp=True, stor_per_node=0.2, fixed_frac=0.3))
+    _check(case, 30, ckpt=4)                       # T = 1: batteries only
+
+
+def test_inner_admm_devices_several_tiles():
+    case = make_case(scale_case(300, 24, 4, seed=12, ramp=True, stor_per_node=0.05, fixed_frac=0.2))
+    _check(case, 40, rho_p=5.0, rho_theta=10.0, ckpt=6)
+
+
+def test_rejects_invalid_data():
     b = _lib()
-    with_storage = make_case(scale_case(40, 3, 1, seed=2, ramp=False, stor_per_node=0.2))
+    bad = make_case(scale_case(40, 3, 1, seed=2, ramp=False, stor_per_node=0.2))
+    bad["stor_eff"] = np.zeros(len(bad["stor_node"]))
     with pytest.raises(b.OpfError):
-        b.UnrolledCost(with_storage)
-    ramped = make_case(scale_case(40, 3, 1, seed=2, ramp=True, stor_per_node=0.0))
-    if np.any(np.asarray(ramped["gen_ramp"]) >= 0):
-        with pytest.raises(b.OpfError):
-            b.UnrolledCost(ramped)
+        b.UnrolledCost(bad)
     with pytest.raises(b.OpfError):
         b.UnrolledCost(make_case(scale_case(40, 1, 1, seed=2, ramp=False, stor_per_node=0.0)), rho_p=0.0)
 
@@ -155,14 +166,14 @@ def test_autograd_function():
         f = b.unrolled_cost(d, 30, lp, pm, lu)
         (2.0 * f).backward()
         f_ref, g_ref = d.cost_grad(30)
-        assert float(f) == f_ref
+        assert float(f.detach()) == f_ref
         np.testing.assert_allclose(pm.grad.numpy(), 2.0 * g_ref["gen_pmax"], rtol=1e-6)
         np.testing.assert_allclose(lp.grad.numpy(), 2.0 * g_ref["load_p"], rtol=1e-6)
         np.testing.assert_allclose(lu.grad.numpy(), 2.0 * g_ref["line_u"], rtol=1e-6)
         with torch.no_grad():
             pm2 = pm - 1e-3 * pm.grad / max(1.0, float(pm.grad.abs().max()))
         f2 = b.unrolled_cost(d, 30, lp.detach(), pm2, lu.detach())
-        assert float(f2) < float(f)
+        assert float(f2) < float(f.detach())
     finally:
         d.close()
 
