@@ -306,9 +306,9 @@ def batched_vs_plain(stream, args):
     """Solve every instance to eps = 1e-4: one after another through
     opf_iterate (plain), and all at once through one batch graph."""
     import torch
-    from paper_2410_17203_gb300 import (opf_batch_converged, opf_batch_create, opf_batch_destroy,
-                                        opf_batch_iterate, opf_create, opf_destroy, opf_get_info,
-                                        opf_iterate, opf_reset)
+    from paper_2410_17203_gb300 import (BATCH_LAYOUTS, opf_batch_autotune, opf_batch_converged, opf_batch_create,
+                                        opf_batch_destroy, opf_batch_iterate, opf_create, opf_destroy,
+                                        opf_get_info, opf_iterate, opf_reset)
     cases = batch_instances(args.batched)
     opts = dict(adapt_every=10, eps=1e-4)
     chunk = args.ttt_chunk
@@ -335,6 +335,8 @@ def batched_vs_plain(stream, args):
         its_plain.append(int(opf_get_info(h)["iterations"]))
     t_plain = time.perf_counter() - t0
     t0 = time.perf_counter()
+    choice, layout_ms = opf_batch_autotune(b, steps=20)    # from the zero state, which it restores
+    t_tune = time.perf_counter() - t0
     done = 0
     while done < args.ttt_max:
         opf_batch_iterate(b, chunk)
@@ -351,16 +353,19 @@ def batched_vs_plain(stream, args):
             "plain_seconds": t_plain, "batched_seconds": t_batch, "speedup": t_plain / t_batch,
             "converged_batched": n_conv, "iterations_total": int(sum(its_plain)),
             "iterations_equal": its_plain == its_batch,
+            "autotune": {"seconds": t_tune, "chosen": BATCH_LAYOUTS[choice],
+                         "ms_per_batch_iteration": dict(zip(BATCH_LAYOUTS, layout_ms))},
             "workload": "buses log-uniform [100, 5000], T in {1, 24, 48}, K in 0..20, seed 3"}
 
 
 def batch_solve(handles, args):
     """Iterate a batch of contexts to eps = 1e-4; returns (iterations per
     instance, seconds)."""
-    from paper_2410_17203_gb300 import (opf_batch_converged, opf_batch_create, opf_batch_destroy,
-                                        opf_batch_iterate, opf_get_info)
+    from paper_2410_17203_gb300 import (opf_batch_autotune, opf_batch_converged, opf_batch_create,
+                                        opf_batch_destroy, opf_batch_iterate, opf_get_info)
     b = opf_batch_create(handles)
     t0 = time.perf_counter()
+    opf_batch_autotune(b, steps=20)
     done = 0
     while done < args.ttt_max:
         opf_batch_iterate(b, args.ttt_chunk)

@@ -226,6 +226,26 @@ opf_status opf_batch_iterate(opf_batch *batch, int32_t n_iters);
 opf_status opf_batch_converged(opf_batch *batch, int32_t *n_converged);
 void opf_batch_destroy(opf_batch *batch);
 
+/* Pick the batch's CTA-to-instance schedule by timing.  Candidate layouts
+ * (index: instance order, CTAs per phase, CTAs of the grid-stride phases):
+ *   0 as given, contiguous, 1x   1 longest first, contiguous, 1x
+ *   2 longest first, round-robin, 1x   3 as given, contiguous, 1/4
+ *   4 longest first, contiguous, 1/4   5 longest first, round-robin, 1/4
+ * ("longest first" orders instances by (K+1) T (L + N); "round-robin" deals
+ * one CTA per instance in turn; "1/4" gives the device-sum, inner-ADMM and
+ * device-average phases a quarter of the CTAs, each doing four times the
+ * work).  Every candidate runs `steps` >= 1 batch iterations (after one
+ * warm-up) from the instances' current state, which is saved before and
+ * restored after, so the call leaves every iterate unchanged; the fastest
+ * layout is kept for later opf_batch_iterate calls.  The layout changes
+ * which CTA computes what, not the arithmetic: iterates are bit-identical
+ * under every layout.  choice and ms_each [OPF_BATCH_LAYOUTS] (each may be
+ * NULL) receive the chosen index and every layout's milliseconds per batch
+ * iteration.  Synchronizes; allocates a temporary copy of the instances'
+ * states. */
+#define OPF_BATCH_LAYOUTS 6
+opf_status opf_batch_autotune(opf_batch *batch, int32_t steps, int32_t *choice, double *ms_each);
+
 /* Export / import the full state (warm start, checkpoint and resume,
  * Section 3.4).  Import recomputes the node averages from p and theta and
  * projects v onto v_bar = 0 per node (Appendix C); it clears a sticky

@@ -79,6 +79,7 @@ EXPORTS = ["opf_default_options", "opf_create", "opf_iterate", "opf_residuals", 
            "opf_price_noalloc", "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info",
            "opf_destroy", "opf_status_str", "opf_last_error", "opf_abi_version",
            "opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_destroy",
+           "opf_batch_autotune",
            "opf_wsnet_param_count", "opf_wsnet_create", "opf_wsnet_get_params", "opf_wsnet_set_params",
            "opf_wsnet_forward", "opf_wsnet_gradient", "opf_wsnet_train_step", "opf_wsnet_destroy",
            "opf_diff_create", "opf_diff_cost_grad", "opf_diff_destroy"]
@@ -121,7 +122,8 @@ def load_library(path=None):
     lib.opf_batch_converged.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
     lib.opf_batch_destroy.argtypes = [C.c_void_p]
     lib.opf_batch_destroy.restype = None
-    for name in ("opf_batch_create", "opf_batch_iterate", "opf_batch_converged"):
+    lib.opf_batch_autotune.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), F64P]
+    for name in ("opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_autotune"):
         getattr(lib, name).restype = C.c_int
     lib.opf_wsnet_param_count.argtypes = [C.c_int32]
     lib.opf_wsnet_param_count.restype = C.c_int64
@@ -310,6 +312,20 @@ def opf_batch_create(handles):
 
 def opf_batch_iterate(b, n_iters):
     _check(load_library().opf_batch_iterate(b, int(n_iters)), "opf_batch_iterate")
+
+
+BATCH_LAYOUTS = ("as given, contiguous, 1x", "longest first, contiguous, 1x", "longest first, round-robin, 1x",
+                 "as given, contiguous, 1/4", "longest first, contiguous, 1/4", "longest first, round-robin, 1/4")
+
+
+def opf_batch_autotune(b, steps=20):
+    """Time the candidate schedules and keep the fastest; returns (index into
+    BATCH_LAYOUTS, ms per batch iteration of every layout).  Leaves the
+    iterates unchanged."""
+    choice = C.c_int32(-1)
+    ms = (C.c_double * len(BATCH_LAYOUTS))()
+    _check(load_library().opf_batch_autotune(b, int(steps), C.byref(choice), ms), "opf_batch_autotune")
+    return choice.value, list(ms)
 
 
 def opf_batch_converged(b):

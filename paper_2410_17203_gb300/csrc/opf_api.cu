@@ -942,6 +942,7 @@ struct opf_batch {
   opfk::Params *d_params = nullptr;
   int *d_sched = nullptr;
   opfk::BatchPlan plan{};
+  long long sched_cap = 0;    // schedule entries d_sched holds (the longest layout)
   cudaGraphExec_t g_one = nullptr, g_many = nullptr;
 };
 
@@ -977,6 +978,50 @@ opf_status build_batch_graph(opf_batch *b, int iters, cudaGraphExec_t *out) {
   return OPF_OK;
 }
 
+// Build the schedule of layout `lay` into d_sched and drop the graphs of the
+// previous one (rebuilt on the next iteration).  Waits for the batch stream.
+opf_status set_batch_layout(opf_batch *b, const opfk::BatchLayout &lay) {
+  const int n = (int)b->ctx.size();
+  std::vector<Params> hp(n);
+  std::vector<opfk::IterPlan> plans(n);
+  for (int i = 0; i < n; ++i) {
+    hp[i] = b->ctx[i]->P;
+    plans[i] = b->ctx[i]->plan;
+  }
+  long long len = 0;
+  opfk::BatchPlan bp{};
+  if (opfk_batch_plan(hp.data(), plans.data(), n, lay, nullptr, 0, &len, &bp) != 0 || len > b->sched_cap)
+    return fail(OPF_ECUDA, "batch schedule");
+  std::vector<int> sched(4 * (size_t)std::max(len, 1LL));
+  if (opfk_batch_plan(hp.data(), plans.data(), n, lay, sched.data(), len, &len, &bp) != 0)
+    return fail(OPF_ECUDA, "batch schedule");
+  CK(cudaStreamSynchronize(b->stream));
+  if (b->g_one) cudaGraphExecDestroy(b->g_one);
+  if (b->g_many) cudaGraphExecDestroy(b->g_many);
+  b->g_one = b->g_many = nullptr;
+  CK(cudaMemcpy(b->d_sched, sched.data(), sched.size() * sizeof(int), cudaMemcpyHostToDevice));
+  b->plan = bp;
+  return OPF_OK;
+}
+
+opf_status ensure_batch_graphs(opf_batch *b) {
+  if (b->g_one) return OPF_OK;
+  opf_status gs = build_batch_graph(b, 1, &b->g_one);
+  if (gs == OPF_OK) gs = build_batch_graph(b, kGraphIters, &b->g_many);
+  return gs;
+}
+
+void launch_batch_steps(opf_batch *b, int n_iters, cudaError_t *e) {
+  for (int i = 0; *e == cudaSuccess && i < n_iters / kGraphIters; ++i) *e = cudaGraphLaunch(b->g_many, b->stream);
+  for (int i = 0; *e == cudaSuccess && i < n_iters % kGraphIters; ++i) *e = cudaGraphLaunch(b->g_one, b->stream);
+}
+
+// bytes of an instance's mutable state: the iterate, the inner-ADMM state and
+// the device scalars lead its arena
+size_t mutable_bytes(const opf_ctx *c) {
+  return (size_t)(reinterpret_cast<const char *>(c->P.sc + 1) - c->arena);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1005,11 +1050,13 @@ opf_status opf_batch_create(opf_ctx *const *ctxs, int32_t n, opf_batch **out) {
   }
   long long len = 0;
   opf_status st = OPF_OK;
-  if (opfk_batch_plan(hp.data(), plans.data(), n, nullptr, 0, &len, &b->plan) != 0)
+  const opfk::BatchLayout lay{nullptr, 0, 1};   // as given, contiguous: the longest schedule
+  if (opfk_batch_plan(hp.data(), plans.data(), n, lay, nullptr, 0, &len, &b->plan) != 0)
     st = fail(OPF_ECUDA, "batch schedule");
   std::vector<int> sched(4 * (size_t)std::max(len, 1LL));
-  if (st == OPF_OK && opfk_batch_plan(hp.data(), plans.data(), n, sched.data(), len, &len, &b->plan) != 0)
+  if (st == OPF_OK && opfk_batch_plan(hp.data(), plans.data(), n, lay, sched.data(), len, &len, &b->plan) != 0)
     st = fail(OPF_ECUDA, "batch schedule");
+  b->sched_cap = len;
   int lo = 0, hi = 0;
   cudaError_t e = st == OPF_OK ? cudaDeviceGetStreamPriorityRange(&lo, &hi) : cudaSuccess;
   if (st == OPF_OK) {
@@ -1036,21 +1083,99 @@ opf_status opf_batch_iterate(opf_batch *b, int32_t n_iters) {
   if (!b) return fail(OPF_EINVAL, "batch is NULL");
   if (n_iters < 0) return fail(OPF_EINVAL, "n_iters must be >= 0");
   if (n_iters == 0) return OPF_OK;
-  if (!b->g_one) {
-    opf_status gs = build_batch_graph(b, 1, &b->g_one);
-    if (gs == OPF_OK) gs = build_batch_graph(b, kGraphIters, &b->g_many);
-    if (gs != OPF_OK) return gs;
-  }
+  const opf_status gs = ensure_batch_graphs(b);
+  if (gs != OPF_OK) return gs;
   // after each instance's queued work ...
   for (opf_ctx *c : b->ctx) {
     CK(cudaEventRecord(c->ev_in, c->stream));
     CK(cudaStreamWaitEvent(b->stream, c->ev_in, 0));
   }
-  for (int i = 0; i < n_iters / kGraphIters; ++i) CK(cudaGraphLaunch(b->g_many, b->stream));
-  for (int i = 0; i < n_iters % kGraphIters; ++i) CK(cudaGraphLaunch(b->g_one, b->stream));
+  cudaError_t le = cudaSuccess;
+  launch_batch_steps(b, n_iters, &le);
+  if (le != cudaSuccess) return cuda_fail(le, "cudaGraphLaunch(batch)");
   // ... and before its later work
   CK(cudaEventRecord(b->ev_done, b->stream));
   for (opf_ctx *c : b->ctx) CK(cudaStreamWaitEvent(c->stream, b->ev_done, 0));
+  return OPF_OK;
+}
+
+opf_status opf_batch_autotune(opf_batch *b, int32_t steps, int32_t *choice, double *ms_each) {
+  if (!b) return fail(OPF_EINVAL, "batch is NULL");
+  if (steps < 1) return fail(OPF_EINVAL, "steps must be >= 1");
+  const int n = (int)b->ctx.size();
+  // instances by decreasing work (line and node items), for longest-first layouts
+  std::vector<int> lpt(n);
+  for (int i = 0; i < n; ++i) lpt[i] = i;
+  auto work = [&](int i) {
+    const opf_ctx *c = b->ctx[i];
+    return (double)c->Kp * c->T * ((double)c->L + c->N);
+  };
+  std::stable_sort(lpt.begin(), lpt.end(), [&](int x, int y) { return work(x) > work(y); });
+  const opfk::BatchLayout cands[OPF_BATCH_LAYOUTS] = {
+      {nullptr, 0, 1}, {lpt.data(), 0, 1}, {lpt.data(), 1, 1},
+      {nullptr, 0, 4}, {lpt.data(), 0, 4}, {lpt.data(), 1, 4}};
+  // save every instance's mutable state after its queued work
+  std::vector<size_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) off[i + 1] = off[i] + mutable_bytes(b->ctx[i]);
+  char *snap = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaMalloc(&snap, std::max<size_t>(off[n], 1));
+  if (e != cudaSuccess) return cuda_fail(e, "autotune snapshot");
+  auto copy_all = [&](bool save) {
+    for (int i = 0; e == cudaSuccess && i < n; ++i) {
+      char *a = b->ctx[i]->arena, *s = snap + off[i];
+      e = cudaMemcpyAsync(save ? s : a, save ? a : s, off[i + 1] - off[i], cudaMemcpyDeviceToDevice, b->stream);
+    }
+  };
+  for (opf_ctx *c : b->ctx) {
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_in, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, c->ev_in, 0);
+  }
+  copy_all(true);
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  opf_status st = e == cudaSuccess ? OPF_OK : cuda_fail(e, "autotune set-up");
+  int best = -1;
+  float best_ms = 0.f;
+  double times[OPF_BATCH_LAYOUTS] = {0};
+  for (int ci = 0; st == OPF_OK && ci < OPF_BATCH_LAYOUTS; ++ci) {
+    st = set_batch_layout(b, cands[ci]);
+    if (st == OPF_OK) st = ensure_batch_graphs(b);
+    if (st != OPF_OK) break;
+    copy_all(false);
+    launch_batch_steps(b, 1, &e);                    // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
+    launch_batch_steps(b, steps, &e);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "autotune timing");
+      break;
+    }
+    times[ci] = (double)ms / steps;
+    if (best < 0 || ms < best_ms) {
+      best = ci;
+      best_ms = ms;
+    }
+  }
+  if (st == OPF_OK) st = set_batch_layout(b, cands[best]);
+  if (st == OPF_OK) {
+    copy_all(false);                                 // the instances as they were
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_done, b->stream);
+    for (opf_ctx *c : b->ctx)
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, b->ev_done, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "autotune restore");
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaStreamSynchronize(b->stream);
+  cudaFree(snap);
+  if (st != OPF_OK) return st;
+  if (choice) *choice = best;
+  if (ms_each) std::copy(times, times + OPF_BATCH_LAYOUTS, ms_each);
   return OPF_OK;
 }
 

@@ -129,6 +129,15 @@ struct BatchPlan {
   int offset[BK_COUNT];
   size_t inner_smem;
 };
+// How a batch schedule lays out CTAs: instances in `order` (NULL: as given),
+// each instance's CTAs of a phase contiguous or dealt round-robin across
+// instances, and `div` times fewer CTAs for the grid-stride phases (xs,
+// inner, dsum), each doing proportionally more work.
+struct BatchLayout {
+  const int *order;
+  int interleave;
+  int div;
+};
 
 }  // namespace opfk
 
@@ -146,8 +155,8 @@ int opfk_iteration_enqueue(const opfk::Params &p, const opfk::IterPlan &plan, vo
                            void *aux_stream, void *ev_fork, void *ev_join);
 // Schedules of the batch kernels for n instances (host parameter copies and
 // their plans): fills sched (4 ints per CTA, BatchPlan order) and the plan.
-int opfk_batch_plan(const opfk::Params *hp, const opfk::IterPlan *plans, int n, int *sched_out,
-                    long long sched_cap, long long *sched_len, opfk::BatchPlan *bp);
+int opfk_batch_plan(const opfk::Params *hp, const opfk::IterPlan *plans, int n, const opfk::BatchLayout &lay,
+                    int *sched_out, long long sched_cap, long long *sched_len, opfk::BatchPlan *bp);
 // Enqueue one iteration of every instance: d_params [n] and d_sched on the
 // device; the same stream and event roles as opfk_iteration_enqueue.
 int opfk_batch_enqueue(const opfk::Params *d_params, const int *d_sched, const opfk::BatchPlan &bp,

@@ -35,6 +35,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "opf_internal.h"
 
@@ -1264,28 +1265,29 @@ int opfk_iteration_enqueue(const Params &p, const IterPlan &plan, void *main_str
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, int *sched_out, long long sched_cap,
-                    long long *sched_len, BatchPlan *bp) {
+int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, const BatchLayout &lay, int *sched_out,
+                    long long sched_cap, long long *sched_len, BatchPlan *bp) {
   long long len = 0;
   size_t ism = 0;
-  auto add = [&](int kind_unused, int inst, long long blocks) -> bool {
-    (void)kind_unused;
-    for (long long b = 0; b < blocks; ++b) {
-      if (sched_out) {
-        if (len >= sched_cap) return false;
-        int *e = sched_out + 4 * len;
-        e[0] = inst;
-        e[1] = (int)b;
-        e[2] = (int)blocks;
-        e[3] = 0;
-      }
-      ++len;
+  auto put = [&](int inst, long long b, long long blocks) -> bool {
+    if (sched_out) {
+      if (len >= sched_cap) return false;
+      int *e = sched_out + 4 * len;
+      e[0] = inst;
+      e[1] = (int)b;
+      e[2] = (int)blocks;
+      e[3] = 0;
     }
+    ++len;
     return true;
   };
+  const int div = std::max(1, lay.div);
+  std::vector<long long> nb(n);
   for (int kind = 0; kind < BK_COUNT; ++kind) {
     bp->offset[kind] = (int)len;
-    for (int i = 0; i < n; ++i) {
+    long long most = 0;
+    for (int j = 0; j < n; ++j) {
+      const int i = lay.order ? lay.order[j] : j;
       const Params &p = hp[i];
       const bool v4 = (p.T % 4 == 0), v2 = (p.T % 2 == 0), vn = (p.T % NODE_VW == 0);
       const long long tv4 = p.T / (v4 ? 4 : 1), tvn = p.T / (vn ? NODE_VW : 1), tv2 = p.T / (v2 ? 2 : 1);
@@ -1313,7 +1315,22 @@ int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, int *sched_o
           blocks = 1;
           break;
       }
-      if (!add(kind, i, blocks)) return -1;
+      // the grid-stride phases take any block count: `div` puts more work in each CTA
+      if (blocks > 0 && (kind == BK_XS4 || kind == BK_XS1 || kind == BK_INNER || kind == BK_DSUM2 ||
+                         kind == BK_DSUM1))
+        blocks = (blocks + div - 1) / div;
+      nb[j] = blocks;
+      most = std::max(most, blocks);
+    }
+    // instances in `order`, each instance's CTAs together or dealt round-robin
+    if (lay.interleave) {
+      for (long long r = 0; r < most; ++r)
+        for (int j = 0; j < n; ++j)
+          if (r < nb[j] && !put(lay.order ? lay.order[j] : j, r, nb[j])) return -1;
+    } else {
+      for (int j = 0; j < n; ++j)
+        for (long long r = 0; r < nb[j]; ++r)
+          if (!put(lay.order ? lay.order[j] : j, r, nb[j])) return -1;
     }
     bp->count[kind] = (int)(len - bp->offset[kind]);
   }

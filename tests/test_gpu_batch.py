@@ -83,3 +83,36 @@ def test_batch_rejects_bad_arguments():
             opf_batch_create([s.h, s.h])
     finally:
         s.close()
+
+
+def test_autotune_keeps_iterates_and_the_chosen_layout_is_exact():
+    """The autotuner restores the instances' states, and whichever layout it
+    keeps, later batch iterates equal single-instance iterates bit for bit."""
+    from paper_2410_17203_gb300 import (BATCH_LAYOUTS, Solver, opf_batch_autotune, opf_batch_create,
+                                        opf_batch_destroy, opf_batch_iterate)
+    opts = dict(adapt_every=10, eps=0.0)
+    batch_solvers = [Solver(c, opts) for c in _cases()]
+    single = [Solver(c, opts) for c in _cases()]
+    b = opf_batch_create([s.h for s in batch_solvers])
+    try:
+        opf_batch_iterate(b, 5)
+        before = [s.state() for s in batch_solvers]
+        choice, ms = opf_batch_autotune(b, steps=8)
+        assert 0 <= choice < len(BATCH_LAYOUTS) and len(ms) == len(BATCH_LAYOUTS)
+        assert all(m > 0 for m in ms) and ms[choice] == min(ms)
+        for s, st in zip(batch_solvers, before):
+            a = s.state()
+            for k in a:
+                np.testing.assert_array_equal(a[k], st[k], err_msg=k)
+            assert s.get_info()["iterations"] == 5
+        opf_batch_iterate(b, 20)
+        for s in single:
+            s.iterate(25)
+        for sb, ss in zip(batch_solvers, single):
+            a, c = sb.state(), ss.state()
+            for k in a:
+                np.testing.assert_array_equal(a[k], c[k], err_msg=k)
+    finally:
+        opf_batch_destroy(b)
+        for s in batch_solvers + single:
+            s.close()
