@@ -75,22 +75,24 @@ CONFIGS = {
 
 def scale_case(n_nodes, T, K, seed, *, lines_per_node=1.6, fixed_frac=0.0, ramp=True,
                stor_per_node=0.05, gens_per_node=0.25, loads_per_node=0.75,
-               topology="geometric"):
+               topology="geometric", n_hvdc=0):
     """Config dict for an arbitrary size with the 2k/10k device mix."""
     n_lines = max(n_nodes - 1, int(round(lines_per_node * n_nodes)))
     return dict(n_nodes=int(n_nodes), n_lines=int(n_lines),
                 n_gens=max(1, int(round(gens_per_node * n_nodes))),
                 n_loads=max(1, int(round(loads_per_node * n_nodes))),
                 n_stor=int(round(stor_per_node * n_nodes)), T=int(T), K=int(K), seed=int(seed),
-                topology=topology, fixed_frac=float(fixed_frac), ramp=bool(ramp))
+                topology=topology, fixed_frac=float(fixed_frac), ramp=bool(ramp), n_hvdc=int(n_hvdc))
 
 
 def case_dims(case):
-    """Sizes of an instance: N, L, gens, loads, storage, T, K, terminals J."""
+    """Sizes of an instance: N, L, gens, loads, storage, HVDC links, T, K,
+    single-schedule terminals S (two per HVDC link) and terminals J."""
     L = len(case["line_from"])
-    S = len(case["gen_node"]) + len(case["load_node"]) + len(case["stor_node"])
+    H = len(case.get("hvdc_from", ()))
+    S = len(case["gen_node"]) + len(case["load_node"]) + len(case["stor_node"]) + 2 * H
     return dict(N=int(case["n_nodes"]), L=L, G=len(case["gen_node"]), D=len(case["load_node"]),
-                B=len(case["stor_node"]), T=int(case["T"]), K=len(case["outaged"]),
+                B=len(case["stor_node"]), H=H, T=int(case["T"]), K=len(case["outaged"]),
                 J=2 * L + S, S=S)
 
 
@@ -263,6 +265,19 @@ def make_case(cfg="tiny", seed=None, **overrides):
         fmax = np.maximum(fmax, _dc_flows(n, frm, to, bsus, inj, drop=l))
     line_u = np.maximum(u_draw, 1.2 * fmax)
 
+    # HVDC links (Section 2.1, other devices): distinct node pairs (no two
+    # links join the same two nodes), limit U[1, 3]; drawn last so that cases
+    # without them are unchanged
+    H = int(cfg.get("n_hvdc", 0))
+    pairs = []
+    while len(pairs) < H:
+        a, c = (int(v) for v in rng.choice(n, 2, replace=False))
+        if (a, c) not in pairs and (c, a) not in pairs:
+            pairs.append((a, c))
+    hvdc_from = np.array([a for a, _ in pairs], np.int64)
+    hvdc_to = np.array([c for _, c in pairs], np.int64)
+    hvdc_u = rng.uniform(1.0, 3.0, H)
+
     return dict(
         name=name, seed=int(cfg["seed"]), T=int(T), n_nodes=int(n),
         line_from=frm.astype(np.int32), line_to=to.astype(np.int32),
@@ -273,4 +288,5 @@ def make_case(cfg="tiny", seed=None, **overrides):
         stor_node=stor_node.astype(np.int32), stor_P=stor_P, stor_dur=stor_dur,
         stor_eff=stor_eff, stor_cost=stor_cost,
         outaged=np.asarray(outaged, np.int32),
+        hvdc_from=hvdc_from.astype(np.int32), hvdc_to=hvdc_to.astype(np.int32), hvdc_u=hvdc_u,
     )

@@ -11,7 +11,7 @@ analytic small grids or identities that the paper states.
 """
 from .mp import (  # noqa: F401
     Oracle, OracleOptions, Network, Shard,
-    prox_gen, prox_line, prox_fixed_load,
+    prox_gen, prox_line, prox_fixed_load, prox_hvdc,
     ramp_rows, storage_rows, inner_admm, inner_matrix,
     node_mean, average, residual,
 )

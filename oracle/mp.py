@@ -121,6 +121,17 @@ def prox_line(x1, x2, y1, y2, u, b, rho_p, rho_theta, active):
 # iterative proxes: Appendix D inner ADMM on f = min_s s'Qs + q's + I{A z <= h}
 # ---------------------------------------------------------------------------
 
+def prox_hvdc(x1, x2, u):
+    """Prox of an HVDC link (Section 2.1, other devices): two terminals with
+    ``p1 + p2 = 0`` and ``|p2| <= u`` and no angle relation (the link is
+    converter-controlled).  Minimising ``(rho/2)((p1 - x1)^2 + (p2 - x2)^2)``
+    over ``p1 = -p2`` is ``(rho/2)((p2 + x1)^2 + (p2 - x2)^2)``, a parabola
+    with vertex ``(x2 - x1)/2``; the limit clips it.  Independent of rho.
+    Returns ``(p1, p2)``."""
+    p2 = np.clip((x2 - x1) / 2.0, -u, u)
+    return -p2, p2
+
+
 def ramp_rows(pmin, pmax, R):
     """Constraint rows ``A p <= h`` of a generator with box and ramp limits.
 
@@ -248,8 +259,12 @@ def inner_admm(x, A, h, eq, q, rho, omega, Minv, beta, lam, n_iter):
 class Network:
     """Device-node model of an instance (Section 2, Section 2.2 type sets).
 
-    Power terminals: every terminal (``J = 2L + G + D + B``).  Phase
-    terminals: the ``2L`` line terminals (the first ``2L`` power terminals).
+    Power terminals: every terminal (``J = 2L + G + D + B + 2H``, two per
+    HVDC link, terminal 1 then 2 of each link).  Phase terminals: the ``2L``
+    AC-line terminals (the first ``2L`` power terminals).  HVDC links are
+    not of the contingency type (Section 2.3: only the first type, AC lines,
+    changes per contingency), so like the other devices they keep one
+    schedule for every contingency.
     """
 
     def __init__(self, case, k_ids=None):
@@ -272,10 +287,16 @@ class Network:
         L, G, D, B = self.L, self.G, self.D, self.B
         self.sl_t1 = slice(0, L)
         self.sl_t2 = slice(L, 2 * L)
-        self.sl_dev = slice(2 * L, 2 * L + G + D + B)
-        self.term_node = np.concatenate([lf, lt, self.gen_node, self.load_node, self.stor_node])
+        self.sl_dev = slice(2 * L, 2 * L + G + D + B + 2 * len(case.get("hvdc_from", ())))
+        hf = np.asarray(case.get("hvdc_from", ()), np.int64)
+        ht = np.asarray(case.get("hvdc_to", ()), np.int64)
+        self.H = len(hf)
+        self.hvdc_u = np.asarray(case.get("hvdc_u", ()), float)
+        hv = np.empty(2 * self.H, np.int64)
+        hv[0::2], hv[1::2] = hf, ht
+        self.term_node = np.concatenate([lf, lt, self.gen_node, self.load_node, self.stor_node, hv])
         self.J = len(self.term_node)
-        self.S = G + D + B
+        self.S = G + D + B + 2 * self.H
         # node-terminal incidence (Appendix B: A = L' diag(|n|)^-1 L), for
         # power (all terminals) and for phase (line terminals)
         self.Linc = csr_matrix((np.ones(self.J), (self.term_node, np.arange(self.J))),
@@ -554,7 +575,7 @@ class Oracle:
         # batteries: iterative prox
         if B:
             _, _, sdl, _ = storage_layout(T)
-            Xb = X[G + D:]
+            Xb = X[G + D:G + D + B]
             pb = np.empty_like(Xb)
             for eff, members in self.stor_groups.items():
                 mb = np.asarray(members)
@@ -566,7 +587,11 @@ class Oracle:
                     o.inner_iters)
                 self.stor_beta[mb], self.stor_lam[mb], self.stor_z[mb] = bet, lam, z
                 pb[mb] = z[:, :T]
-            pd[G + D:] = pb
+            pd[G + D:G + D + B] = pb
+        # HVDC links: closed form, one schedule for every contingency
+        if net.H:
+            h0, h1 = G + D + B, G + D + B + 2 * net.H
+            pd[h0:h1:2], pd[h0 + 1:h1:2] = prox_hvdc(X[h0:h1:2], X[h0 + 1:h1:2], net.hvdc_u[:, None])
         p_new[:, sd] = pd[None]
 
         # step 3: scaled price updates u += pbar, v += theta~

@@ -56,6 +56,7 @@ class Unrolled:
         self.gen_pmin = t(net.gen_pmin)
         self.load_voll = t(net.load_voll)
         self.is_fixed = t(net.is_fixed, torch.bool)
+        self.hvdc_u = t(net.hvdc_u)
         # inner-ADMM devices (Appendix D), factored once: the penalties are fixed
         T = net.T
         rho_d = net.Kp * self.rho_p
@@ -176,7 +177,7 @@ class Unrolled:
                 pg = pg.index_put((ri,), z[:, :T])
             parts = [pg, pl]
             if self.stor:
-                Xb = X[G + D:]
+                Xb = X[G + D:G + D + n.B]
                 pb = torch.zeros_like(Xb)
                 for i, g in enumerate(self.stor):
                     z, bt, lm = self._inner(Xb[g["members"]], g["A"], g["h"], g["eq"], g["q"], rho_d, g["Minv"],
@@ -185,6 +186,13 @@ class Unrolled:
                     s_z[i] = z
                     pb = pb.index_put((g["members"],), z[:, :T])
                 parts.append(pb)
+            if n.H:
+                # HVDC links: p2 = clip((x2 - x1) / 2, -u, u), p1 = -p2 (oracle.mp.prox_hvdc)
+                h0 = G + D + n.B
+                xh = X[h0:h0 + 2 * n.H].reshape(n.H, 2, T)
+                hu = self.hvdc_u[:, None]
+                p2h = torch.clamp((xh[:, 1] - xh[:, 0]) / 2, min=-hu, max=hu)
+                parts.append(torch.stack([-p2h, p2h], dim=1).reshape(2 * n.H, T))
             pd = torch.cat(parts, dim=0)
             p = torch.cat([-p2, p2, pd[None].expand(Kp, -1, -1)], dim=1)
             th = torch.cat([th1, th2], dim=1)

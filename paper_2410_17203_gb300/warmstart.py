@@ -75,7 +75,8 @@ def warm_state(case, y, rho_p=1.0):
     for k, l in enumerate(out, start=1):
         if l >= 0:
             p_line[k, l] = 0.0
-    S = len(case["gen_node"]) + len(case["load_node"]) + len(case["stor_node"])
+    S = (len(case["gen_node"]) + len(case["load_node"]) + len(case["stor_node"])
+         + 2 * len(case.get("hvdc_from", ())))
     u = np.repeat((-lam / (rho_p * Kp))[None], Kp, axis=0)
     f32 = np.float32
     return dict(p_line=p_line.astype(f32), th1=np.repeat(t1[None], Kp, 0).astype(f32),

@@ -11,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import (inner_admm, inner_matrix, prox_fixed_load, prox_gen, prox_line,
+from oracle import (inner_admm, inner_matrix, prox_fixed_load, prox_gen, prox_hvdc, prox_line,
                     ramp_rows, storage_rows)
 from oracle.mp import storage_layout
 
@@ -114,6 +114,18 @@ def test_prox_line_outage_decouples():
     # contingency parameters u = b = 0 (Section 2.3): no flow, angles follow their targets
     p1, p2, t1, t2 = prox_line(0.7, -0.2, 0.3, -0.4, 0.0, 0.0, 1.0, 1.0, False)
     assert (p1, p2, t1, t2) == (0.0, 0.0, 0.3, -0.4)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_prox_hvdc_matches_brute_force(seed):
+    # HVDC link (Section 2.1, other devices): p1 + p2 = 0, |p2| <= u, no angle
+    r = np.random.default_rng(100 + seed)
+    x1, x2 = r.normal(0, 2, 2)
+    u = r.uniform(0.05, 3)
+    rho = r.uniform(0.1, 50)
+    p2 = golden(lambda q: rho / 2 * ((-q - x1) ** 2 + (q - x2) ** 2), -u, u)
+    got = prox_hvdc(x1, x2, u)
+    np.testing.assert_allclose(got, (-p2, p2), rtol=1e-6, atol=1e-7)
 
 
 # --------------------------------------------------------------------------

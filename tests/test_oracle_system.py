@@ -11,7 +11,7 @@ import os
 
 import numpy as np
 import pytest
-from scipy.optimize import minimize
+from scipy.optimize import Bounds, LinearConstraint, minimize
 
 from gridgen import make_case
 from oracle import Oracle, OracleOptions
@@ -87,13 +87,18 @@ def _dcopf_slsqp(case):
     N, T = case["n_nodes"], case["T"]
     assert T == 1 and len(case["stor_node"]) == 0
     G = len(case["gen_node"])
+    # HVDC links: flow f_h from hvdc_from to hvdc_to, |f_h| <= u_h
+    hf, ht = case.get("hvdc_from", np.zeros(0, int)), case.get("hvdc_to", np.zeros(0, int))
+    H = len(hf)
     fr, to, bs, us = case["line_from"], case["line_to"], case["line_b"], case["line_u"]
     L = len(fr)
     out = case["outaged"]
     load = np.zeros(N)
     np.add.at(load, case["load_node"], case["load_p"][:, 0])
-    C = np.zeros((N, G))
+    C = np.zeros((N, G + H))                    # injections of the variables (g, f)
     C[case["gen_node"], np.arange(G)] = 1.0
+    C[hf, G + np.arange(H)] -= 1.0
+    C[ht, G + np.arange(H)] += 1.0
     Ain, bin_ = [], []
     for k in range(len(out) + 1):
         act = np.ones(L, bool)
@@ -112,16 +117,31 @@ def _dcopf_slsqp(case):
         bin_ += [-us[act] - F @ load, -us[act] + F @ load]
     Ain = np.vstack(Ain)
     bin_ = np.concatenate(bin_)
-    a, b = case["gen_a"], case["gen_b"]
-    cons = [dict(type="eq", fun=lambda g: np.array([g.sum() - load.sum()]),
-                 jac=lambda g: np.ones((1, G))),
+    a = np.concatenate([case["gen_a"], np.zeros(H)])
+    b = np.concatenate([case["gen_b"], np.zeros(H)])
+    bal = np.concatenate([np.ones(G), np.zeros(H)])
+    cons = [dict(type="eq", fun=lambda g: np.array([bal @ g - load.sum()]),
+                 jac=lambda g: bal[None, :]),
             dict(type="ineq", fun=lambda g: Ain @ g - bin_, jac=lambda g: Ain)]
     bounds = [(case["gen_pmin"][g, 0], case["gen_pmax"][g, 0]) for g in range(G)]
-    res = minimize(lambda g: np.sum(a * g * g + b * g), np.full(G, load.sum() / G),
+    bounds += [(-case["hvdc_u"][h], case["hvdc_u"][h]) for h in range(H)]
+    x0 = np.concatenate([np.full(G, load.sum() / G), np.zeros(H)])
+    if H:
+        # the zero-cost link flows make SLSQP's line search stall; an
+        # interior-point solve handles them
+        lb, ub = np.array([v[0] for v in bounds]), np.array([v[1] for v in bounds])
+        res = minimize(lambda g: np.sum(a * g * g + b * g), x0, jac=lambda g: 2 * a * g + b,
+                       hess=lambda g: np.diag(2 * a), method="trust-constr", bounds=Bounds(lb, ub),
+                       constraints=[LinearConstraint(bal, load.sum(), load.sum()),
+                                    LinearConstraint(Ain, bin_, np.inf)],
+                       options=dict(gtol=1e-12, xtol=1e-14, maxiter=20000))
+        assert res.status in (1, 2), res.message
+        return res.x[:G], res.fun
+    res = minimize(lambda g: np.sum(a * g * g + b * g), x0,
                    jac=lambda g: 2 * a * g + b, bounds=bounds, constraints=cons,
                    method="SLSQP", options=dict(maxiter=1000, ftol=1e-14))
     assert res.success, res.message
-    return res.x, res.fun
+    return res.x[:G], res.fun
 
 
 @pytest.fixture(scope="module")
@@ -293,3 +313,38 @@ def test_ramp_and_storage_iteration_converges_to_qp_optimum(rng):
     assert o.rho_history                    # adaptation ran (rescaling the inner duals)
     assert o.objective() == pytest.approx(f_ref, rel=1e-5)
     np.testing.assert_allclose(o.dev_p()[:3], g_ref, atol=2e-4)
+
+
+def test_two_areas_joined_by_hvdc_match_merit_order():
+    """Two single-bus areas joined only by an HVDC link (Section 2.1, other
+    devices): the cheap area exports up to the link limit, and each area's
+    price is its own marginal generator's cost."""
+    u = 0.7
+    case = dict(
+        n_nodes=2, T=1, line_from=np.zeros(0, np.int32), line_to=np.zeros(0, np.int32),
+        line_b=np.zeros(0), line_u=np.zeros(0),
+        gen_node=np.array([0, 1], np.int32), gen_a=np.array([0.5, 1.0]), gen_b=np.array([10.0, 30.0]),
+        gen_pmin=np.zeros((2, 1)), gen_pmax=np.full((2, 1), 5.0), gen_ramp=-np.ones(2),
+        load_node=np.array([0, 1], np.int32), load_p=np.array([[0.5], [2.0]]), load_voll=-np.ones(2),
+        stor_node=np.zeros(0, np.int32), stor_P=np.zeros(0), stor_dur=np.zeros(0),
+        stor_eff=np.zeros(0), stor_cost=np.zeros(0), outaged=np.zeros(0, np.int32),
+        hvdc_from=np.array([0], np.int32), hvdc_to=np.array([1], np.int32), hvdc_u=np.array([u]))
+    o = Oracle(case, OracleOptions(adapt_every=10, eps=1e-10))
+    o.iterate(200000)
+    assert o.converged
+    # area 0 serves its load and the export u: g0 = 0.5 + 0.7 = 1.2 at price
+    # 2 * 0.5 * 1.2 + 10 = 11.2; area 1 serves 2.0 - 0.7 = 1.3 at 2 * 1.0 * 1.3 + 30 = 32.6
+    pd = o.dev_p()[:, 0]
+    np.testing.assert_allclose(pd[:2], [1.2, 1.3], atol=1e-6)
+    np.testing.assert_allclose(pd[4:], [-u, u], atol=1e-6)
+    np.testing.assert_allclose(o.prices()[:, 0], [11.2, 32.6], atol=1e-4)
+
+
+def test_tiny_with_hvdc_converges_to_independent_qp_optimum():
+    case = make_case("tiny", n_hvdc=3)
+    o = Oracle(case, OracleOptions(adapt_every=0, rho_theta=10.0, eps=1e-8))
+    o.iterate(200000)
+    assert o.converged
+    g, fopt = _dcopf_slsqp(case)
+    assert o.objective() == pytest.approx(fopt, rel=1e-6)
+    np.testing.assert_allclose(o.dev_p()[:len(g), 0], g, atol=2e-4)

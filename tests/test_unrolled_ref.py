@@ -17,8 +17,9 @@ def _case():
 
 
 def _case_inner():
-    """Ramp-limited generators and batteries: their prox is the inner ADMM."""
-    return make_case(scale_case(40, 6, 2, seed=7, ramp=True, stor_per_node=0.1, fixed_frac=0.3))
+    """Ramp-limited generators and batteries, whose prox is the inner ADMM,
+    and two HVDC links."""
+    return make_case(scale_case(40, 6, 2, seed=7, ramp=True, stor_per_node=0.1, fixed_frac=0.3, n_hvdc=2))
 
 
 @pytest.mark.parametrize("inner", [False, True])
