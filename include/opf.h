@@ -18,8 +18,10 @@
  *     the current CUDA device.
  *   - Arrays are row-major; the time step t is always the innermost index.
  *     K is the number of contingencies, Kp = K + 1 (contingency 0 is the base
- *     case), L lines, N nodes, S = n_gens + n_loads + n_stor single-terminal
- *     devices ordered generators, then loads, then batteries.
+ *     case), L lines, N nodes, S = n_gens + n_loads + n_stor + 2 n_hvdc
+ *     device terminals with one schedule for all contingencies, ordered
+ *     generators, loads, batteries, then terminal 1 and terminal 2 of each
+ *     HVDC link.
  *   - Power p > 0 flows from a device into its node (Section 2).  A line's
  *     power is reported at its second terminal (the `to` node); its first
  *     terminal carries -p.
@@ -35,7 +37,7 @@
 extern "C" {
 #endif
 
-#define OPF_ABI_VERSION 2
+#define OPF_ABI_VERSION 3
 
 typedef struct opf_ctx opf_ctx; /* opaque, created by opf_create, freed by opf_destroy */
 
@@ -85,6 +87,15 @@ typedef struct {
   int32_t n_stor;
   const int32_t *stor_node;
   const double *stor_P, *stor_dur, *stor_eff, *stor_cost;
+
+  /* HVDC links (Section 2.1, other devices): I{p1 + p2 = 0} + I{|p2| <= u},
+   * no angle relation.  Terminal 1 sits at hvdc_from, terminal 2 at hvdc_to
+   * (distinct nodes), hvdc_u >= 0.  Only AC lines change per contingency
+   * (Section 2.3), so a link keeps one schedule for every contingency; its
+   * prox is p2 = clip((x2 - x1) / 2, -u, u). */
+  int32_t n_hvdc;
+  const int32_t *hvdc_from, *hvdc_to;
+  const double *hvdc_u;
 } opf_network;
 
 /* Contingencies k = 1..K: in contingency k the line outaged_line[k-1] has
@@ -114,7 +125,7 @@ typedef struct {
  * inner ADMM duals.  Each pointer may be NULL to skip that array.
  *   p_line, th1, th2, v1, v2: [Kp][L][T]  line terminal-2 power, terminal
  *                                          angles and phase duals
- *   p_dev:  [S][T]                         single-terminal device power
+ *   p_dev:  [S][T]                         device terminal power (one schedule)
  *   u:      [Kp][N][T]                     scaled power-balance duals (per node)
  *   inner:  [inner_len]                    inner ADMM (lambda, beta) of the
  *           iterative proxes, layout documented at opf_get_info. */

@@ -40,6 +40,7 @@ class opf_network(C.Structure):
         ("n_loads", C.c_int32), ("load_node", I32P), ("load_p", F64P), ("load_voll", F64P),
         ("n_stor", C.c_int32), ("stor_node", I32P), ("stor_P", F64P), ("stor_dur", F64P),
         ("stor_eff", F64P), ("stor_cost", F64P),
+        ("n_hvdc", C.c_int32), ("hvdc_from", I32P), ("hvdc_to", I32P), ("hvdc_u", F64P),
     ]
 
 
@@ -75,6 +76,8 @@ class opf_info(C.Structure):
     ]
 
 
+ABI_VERSION = 3     # OPF_ABI_VERSION of include/opf.h
+
 EXPORTS = ["opf_default_options", "opf_create", "opf_iterate", "opf_residuals", "opf_solution",
            "opf_price_noalloc", "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info",
            "opf_destroy", "opf_status_str", "opf_last_error", "opf_abi_version",
@@ -96,6 +99,10 @@ def load_library(path=None):
     if not os.path.exists(p):
         raise OSError(f"CUDA library not built: {p} (run __graft_entry__.build())")
     lib = C.CDLL(p)
+    lib.opf_abi_version.restype = C.c_int32
+    if lib.opf_abi_version() != ABI_VERSION:
+        raise OSError(f"{p} has ABI version {lib.opf_abi_version()}, this binding expects {ABI_VERSION} "
+                      "(rebuild the library)")
     lib.opf_default_options.argtypes = [C.POINTER(opf_options)]
     lib.opf_default_options.restype = None
     lib.opf_create.argtypes = [C.POINTER(opf_network), C.c_int32, C.POINTER(opf_contingencies),
@@ -200,12 +207,12 @@ def _network(case):
     keep = {}
 
     def f64(name, shape=None):
-        a = np.ascontiguousarray(np.asarray(case[name], dtype=np.float64))
+        a = np.ascontiguousarray(np.asarray(case.get(name, ()), dtype=np.float64))
         keep[name] = a
         return _ptr(a, C.c_double)
 
     def i32(name):
-        a = np.ascontiguousarray(np.asarray(case[name], dtype=np.int32))
+        a = np.ascontiguousarray(np.asarray(case.get(name, ()), dtype=np.int32))
         keep[name] = a
         return _ptr(a, C.c_int32)
 
@@ -220,6 +227,8 @@ def _network(case):
         load_voll=f64("load_voll"),
         n_stor=len(case["stor_node"]), stor_node=i32("stor_node"), stor_P=f64("stor_P"),
         stor_dur=f64("stor_dur"), stor_eff=f64("stor_eff"), stor_cost=f64("stor_cost"),
+        n_hvdc=len(case.get("hvdc_from", ())), hvdc_from=i32("hvdc_from"), hvdc_to=i32("hvdc_to"),
+        hvdc_u=f64("hvdc_u"),
     )
     out = np.ascontiguousarray(np.asarray(case["outaged"], dtype=np.int32))
     keep["outaged"] = out

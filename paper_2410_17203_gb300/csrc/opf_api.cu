@@ -71,7 +71,7 @@ struct opf_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   opf_options opt{};
-  int N = 0, L = 0, T = 0, K = 0, Kp = 0, S = 0, G = 0, D = 0, B = 0;
+  int N = 0, L = 0, T = 0, K = 0, Kp = 0, S = 0, G = 0, D = 0, B = 0, H = 0;
   int n_closed = 0, n_dnode = 0, n_ramp = 0, n_stor = 0;
   size_t n_tcode = 0;  // padded terminal-code list length
   float *price_scratch = nullptr;  // this device's fixed price staging array
@@ -143,7 +143,7 @@ opf_status validate(const opf_network *net, int T, const opf_contingencies *ctg,
   if (!net) return fail(OPF_EINVAL, "network is NULL");
   if (T < 1 || T > kMaxT) return fail(OPF_EINVAL, "horizon T must be in [1, 2048]");
   if (net->n_nodes < 1) return fail(OPF_EINVAL, "n_nodes must be >= 1");
-  if (net->n_lines < 0 || net->n_gens < 0 || net->n_loads < 0 || net->n_stor < 0)
+  if (net->n_lines < 0 || net->n_gens < 0 || net->n_loads < 0 || net->n_stor < 0 || net->n_hvdc < 0)
     return fail(OPF_EINVAL, "negative device count");
   const int N = net->n_nodes;
   auto bad_nodes = [N](const int32_t *a, int n) {
@@ -195,6 +195,16 @@ opf_status validate(const opf_network *net, int T, const opf_contingencies *ctg,
           !(net->stor_eff[b] <= 1) || !(net->stor_cost[b] >= 0) || !std::isfinite(net->stor_P[b]) ||
           !std::isfinite(net->stor_dur[b]) || !std::isfinite(net->stor_cost[b]))
         return fail(OPF_EINVAL, "battery data out of range");
+    }
+  }
+  if (net->n_hvdc) {
+    if (!net->hvdc_from || !net->hvdc_to || !net->hvdc_u) return fail(OPF_EINVAL, "HVDC arrays missing");
+    if (bad_nodes(net->hvdc_from, net->n_hvdc) || bad_nodes(net->hvdc_to, net->n_hvdc))
+      return fail(OPF_EINVAL, "HVDC node id out of range");
+    for (int h = 0; h < net->n_hvdc; ++h) {
+      if (net->hvdc_from[h] == net->hvdc_to[h]) return fail(OPF_EINVAL, "HVDC link connects a node to itself");
+      if (!(net->hvdc_u[h] >= 0.0) || !std::isfinite(net->hvdc_u[h]))
+        return fail(OPF_EINVAL, "HVDC limit must be finite and >= 0");
     }
   }
   if (ctg && ctg->K < 0) return fail(OPF_EINVAL, "K must be >= 0");
@@ -312,6 +322,7 @@ void carve(opf_ctx *c, Arena &a) {
   p.stor_P = a.take<float>(c->n_stor);
   p.stor_dur = a.take<float>(c->n_stor);
   p.stor_cost = a.take<float>(c->n_stor);
+  p.hvdc_u = a.take<float>(c->H);
   p.node_perm = a.take<int>(c->N);
   p.line_perm = a.take<int>(c->L);
   // scratch
@@ -451,7 +462,8 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   c->G = net->n_gens;
   c->D = net->n_loads;
   c->B = net->n_stor;
-  c->S = c->G + c->D + c->B;
+  c->H = net->n_hvdc;
+  c->S = c->G + c->D + c->B + 2 * c->H;
   const int N = c->N, L = c->L, S = c->S, G = c->G, D = c->D;
   const size_t nT = (size_t)T;
 
@@ -460,6 +472,10 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   for (int g = 0; g < G; ++g) dev_node[g] = net->gen_node[g];
   for (int d = 0; d < D; ++d) dev_node[G + d] = net->load_node[d];
   for (int b = 0; b < c->B; ++b) dev_node[G + D + b] = net->stor_node[b];
+  for (int h = 0; h < c->H; ++h) {
+    dev_node[G + D + c->B + 2 * h] = net->hvdc_from[h];
+    dev_node[G + D + c->B + 2 * h + 1] = net->hvdc_to[h];
+  }
   std::vector<int> lcnt(N, 0), dcnt(N, 0);
   for (int l = 0; l < L; ++l) {
     lcnt[net->line_from[l]]++;
@@ -558,6 +574,12 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
     sdur.push_back((float)net->stor_dur[b]);
     scost.push_back((float)net->stor_cost[b]);
   }
+  // HVDC terminals: evaluated by the inner kernel, which needs both ends' averages
+  std::vector<float> hvdc_u(c->H);
+  for (int h = 0; h < c->H; ++h) {
+    dev_type[G + D + c->B + 2 * h] = dev_type[G + D + c->B + 2 * h + 1] = 2;
+    hvdc_u[h] = (float)net->hvdc_u[h];
+  }
   // nodes with devices (avg_k(pbar + u) is formed once per node), their
   // closed-form devices, and whether inner-ADMM devices need the average
   std::vector<int> dnode_ids, dnode_ptr(1, 0), dnode_dev, dnode_keep;
@@ -606,6 +628,7 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
     q.n_dnode = c->n_dnode;
     q.n_ramp = c->n_ramp;
     q.n_stor = c->n_stor;
+    q.n_hvdc = c->H;
     q.S = S;
     if (opfk_plan(q, &c->plan) != 0) {
       delete c;
@@ -659,6 +682,8 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   p.n_dnode = c->n_dnode;
   p.n_ramp = c->n_ramp;
   p.n_stor = c->n_stor;
+  p.n_hvdc = c->H;
+  p.hvdc0 = G + D + c->B;
   p.node_grid = c->plan.node_grid;
   p.eps = opt.eps;
   p.mu = opt.mu;
@@ -733,6 +758,7 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   up(p.stor_P, sP);
   up(p.stor_dur, sdur);
   up(p.stor_cost, scost);
+  up(p.hvdc_u, hvdc_u);
   up(p.node_perm, node_perm);
   up(p.line_perm, line_perm);
   if (s == OPF_OK) s = init_scalars(c);

@@ -39,7 +39,7 @@ struct Shape {
 };
 
 struct DP {
-  int N, L, T, Kp, G, D, B, S;
+  int N, L, T, Kp, G, D, B, H, S;       // H HVDC links, terminals H0 + 2h and H0 + 2h + 1 (H0 = G + D + B)
   float rp, rt, rd;                    // rho_p, rho_theta, (K+1) rho_p (= omega of the inner ADMM)
   const int *n1, *n2;                  // line ends (terminal 1 at n1 carries -p)
   const float *b;                      // susceptance [L]
@@ -48,7 +48,8 @@ struct DP {
   const int *dptr, *didx;              // node -> devices
   const float *cnt, *cth;              // terminals at a node: all, line (0: none)
   const int *dnode;                    // device node [S]
-  const int *kind;                     // [S] 0: closed-form prox, 1: inner ADMM
+  const int *kind;                     // [S] 0: closed-form prox, 1: inner ADMM, 2: HVDC terminal
+  const float *hvdc_u;                 // [H]
   const float *ga, *gb, *gpmin;        // generators: a, b [G]; pmin [G][T]
   const float *voll;                   // loads [D], < 0: fixed
   const float *load_p, *gpmax, *lu;    // data: [D][T], [G][T], [L]
@@ -57,7 +58,7 @@ struct DP {
   const IDev *idev;
   const Shape *shape;
   const int *arp, *aci, *atp, *ati;
-  const float *acv, *atv, *minv, *H, *Q, *scost;
+  const float *acv, *atv, *minv, *RH, *Q, *scost;   // RH: right-hand sides of the inner rows
   const unsigned char *aeq;
 };
 
@@ -140,13 +141,21 @@ __device__ __forceinline__ float dev_x(const DP &p, const St &s, int d, int t) {
 }
 
 // step 2: devices shared by all contingencies, weight (K+1) rho_p; the
-// inner-ADMM devices only record their input X here
+// inner-ADMM devices only record their input X here.  An HVDC terminal
+// evaluates its link's prox p2 = clip((x2 - x1)/2, -u, u), p1 = -p2.
 __global__ void fwd_dev(DP p, St s, St nx, float *XD) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
     const int t = (int)(i % p.T), d = (int)(i / p.T);
     const float X = dev_x(p, s, d, t);
-    if (p.kind[d]) {
+    if (p.kind[d] == 1) {
       XD[i] = X;
+      continue;
+    }
+    if (p.kind[d] == 2) {
+      const int e = d - (p.G + p.D + p.B), d1 = d - (e & 1), h = e >> 1;
+      const float x1 = (e & 1) ? dev_x(p, s, d1, t) : X, x2 = (e & 1) ? X : dev_x(p, s, d1 + 1, t);
+      const float f = fminf(fmaxf(0.5f * (x2 - x1), -p.hvdc_u[h]), p.hvdc_u[h]);
+      nx.PD[i] = (e & 1) ? f : -f;
       continue;
     }
     float r;
@@ -172,7 +181,7 @@ __device__ void inner_forward(const DP &p, const Shape &sh, const IDev &di, cons
                               float *w, float *r, float *z, unsigned char *mask) {
   const int n = sh.n, m = sh.m, T = p.T;
   const float rho = p.rd, om = p.rd;
-  const float *Mi = p.minv + di.minv, *h = p.H + di.h, *q = p.Q + di.q;
+  const float *Mi = p.minv + di.minv, *h = p.RH + di.h, *q = p.Q + di.q;
   for (int it = 0; it < N_INNER; ++it) {
     for (int row = threadIdx.x; row < m; row += blockDim.x) w[row] = h[row] + beta[row] - lam[row];
     __syncthreads();
@@ -303,15 +312,30 @@ __global__ void bwd_line1(DP p, St s, Adj a, const float *A, const float *B, flo
 // the closed-form device proxes backwards; LX = d/dX per device.  For an
 // inner-ADMM device the kernel records X and the adjoint of its output for
 // bwd_inner.
+__device__ __forceinline__ float dev_lpd(const DP &p, const Adj &a, const float *A, int d, int t) {
+  const int n = p.dnode[d];
+  float lpd = a.LPD[(size_t)d * p.T + t];
+  for (int k = 0; k < p.Kp; ++k) lpd += A[ni(p, k, n, t)] / p.cnt[n];
+  return lpd;
+}
+
 __global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL, float *GP, float *XD, float *LPDT) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
-    const int t = (int)(i % p.T), d = (int)(i / p.T), n = p.dnode[d];
-    float lpd = a.LPD[i];
-    for (int k = 0; k < p.Kp; ++k) lpd += A[ni(p, k, n, t)] / p.cnt[n];
+    const int t = (int)(i % p.T), d = (int)(i / p.T);
+    const float lpd = dev_lpd(p, a, A, d, t);
     const float X = dev_x(p, s, d, t);
-    if (p.kind[d]) {
+    if (p.kind[d] == 1) {
       XD[i] = X;
       LPDT[i] = lpd;
+      continue;
+    }
+    if (p.kind[d] == 2) {                // HVDC: both terminals' adjoints meet in d/d p2
+      const int e = d - (p.G + p.D + p.B), d1 = d - (e & 1), h = e >> 1;
+      const float x1 = (e & 1) ? dev_x(p, s, d1, t) : X, x2 = (e & 1) ? X : dev_x(p, s, d1 + 1, t);
+      const float l1 = (e & 1) ? dev_lpd(p, a, A, d1, t) : lpd, l2 = (e & 1) ? lpd : dev_lpd(p, a, A, d1 + 1, t);
+      const float z = 0.5f * (x2 - x1), u = p.hvdc_u[h];
+      const float lz = (z >= -u && z <= u) ? 0.5f * (l2 - l1) : 0.f;
+      LX[i] = (e & 1) ? lz : -lz;
       continue;
     }
     float lx = 0.f;
@@ -479,7 +503,7 @@ size_t bwd_inner_smem(int T, int n, int m) { return (size_t)(2 * T + 4 * n + 7 *
 }  // namespace
 
 struct opf_diff {
-  int N = 0, L = 0, T = 0, Kp = 0, G = 0, D = 0, B = 0, S = 0, ckpt = 1;
+  int N = 0, L = 0, T = 0, Kp = 0, G = 0, D = 0, B = 0, H = 0, S = 0, ckpt = 1;
   cudaStream_t stream = nullptr;
   DP p{};
   std::vector<float> ga, gb, voll, load_p, gpmax, lu, scost;  // host copies (cost and defaults)
@@ -488,7 +512,7 @@ struct opf_diff {
   std::vector<IDev> idev;
   int Mtot = 0;
   size_t smem_fwd = 0, smem_bwd = 0;
-  float *H = nullptr;                                        // device copy of the right-hand sides
+  float *RH = nullptr;                                       // device copy of the right-hand sides
   std::vector<void *> allocs;
   size_t state_floats = 0;
 };
@@ -661,7 +685,11 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   if (!(rho_p > 0) || !(rho_theta > 0) || checkpoint_every < 1)
     return dfail(OPF_EINVAL, "diff: penalties must be > 0 and checkpoint_every >= 1");
   const int N = net->n_nodes, L = net->n_lines, G = net->n_gens, D = net->n_loads, B = net->n_stor;
-  if (N < 1 || L < 0 || G < 0 || D < 0 || B < 0) return dfail(OPF_EINVAL, "diff: bad sizes");
+  const int H = net->n_hvdc;
+  if (N < 1 || L < 0 || G < 0 || D < 0 || B < 0 || H < 0) return dfail(OPF_EINVAL, "diff: bad sizes");
+  for (int h = 0; h < H; ++h)
+    if (net->hvdc_from[h] == net->hvdc_to[h] || !(net->hvdc_u[h] >= 0))
+      return dfail(OPF_EINVAL, "diff: bad HVDC link");
   const int K = ctg ? ctg->K : 0;
   for (int l = 0; l < L; ++l) {
     const int a = net->line_from[l], c = net->line_to[l];
@@ -683,7 +711,8 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   d->G = G;
   d->D = D;
   d->B = B;
-  d->S = G + D + B;
+  d->H = H;
+  d->S = G + D + B + 2 * H;
   d->ckpt = checkpoint_every;
   d->stream = (cudaStream_t)cuda_stream;
   // incidence by node (caller's numbering)
@@ -696,6 +725,11 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   for (int g = 0; g < G; ++g) dnode[g] = net->gen_node[g];
   for (int e = 0; e < D; ++e) dnode[G + e] = net->load_node[e];
   for (int b = 0; b < B; ++b) dnode[G + D + b] = net->stor_node[b];
+  for (int h = 0; h < H; ++h) {
+    dnode[G + D + B + 2 * h] = net->hvdc_from[h];
+    dnode[G + D + B + 2 * h + 1] = net->hvdc_to[h];
+    kind[G + D + B + 2 * h] = kind[G + D + B + 2 * h + 1] = 2;
+  }
   for (int s = 0; s < d->S; ++s) {
     if (dnode[s] < 0 || dnode[s] >= N) {
       delete d;
@@ -865,6 +899,7 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   p.G = G;
   p.D = D;
   p.B = B;
+  p.H = H;
   p.S = d->S;
   p.rp = (float)rho_p;
   p.rt = (float)rho_theta;
@@ -902,12 +937,15 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   U(&p.minv, minv);
   U(&p.Q, qv);
   U(&p.scost, d->scost);
+  std::vector<float> hu(H);
+  for (int h = 0; h < H; ++h) hu[h] = (float)net->hvdc_u[h];
+  U(&p.hvdc_u, hu);
   // data arrays, rewritten by every call
   U(&p.load_p, d->load_p);
   U(&p.gpmax, d->gpmax);
   U(&p.lu, d->lu);
-  if (e == cudaSuccess) e = dalloc(d->allocs, &d->H, (size_t)d->Mtot);
-  p.H = d->H;
+  if (e == cudaSuccess) e = dalloc(d->allocs, &d->RH, (size_t)d->Mtot);
+  p.RH = d->RH;
   if (e != cudaSuccess) {
     for (void *q : d->allocs) cudaFree(q);
     delete d;
@@ -940,7 +978,7 @@ opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const
   DCK(cudaMemcpyAsync(const_cast<float *>(p.gpmax), pm, GT * 4, cudaMemcpyHostToDevice, d->stream));
   DCK(cudaMemcpyAsync(const_cast<float *>(p.lu), line_u ? line_u : d->lu.data(), L * 4, cudaMemcpyHostToDevice,
                       d->stream));
-  if (d->Mtot) DCK(cudaMemcpyAsync(d->H, H.data(), H.size() * 4, cudaMemcpyHostToDevice, d->stream));
+  if (d->Mtot) DCK(cudaMemcpyAsync(d->RH, H.data(), H.size() * 4, cudaMemcpyHostToDevice, d->stream));
   // states: checkpoints 0, C, 2C, ... and one segment of C + 1 states
   const int C = std::min(d->ckpt, K);
   const int n_ck = K / C + 1;

@@ -57,6 +57,7 @@ enum { RG_UP = 0, RG_LO = 1, RG_RU = 2, RG_RD = 3, RG_N = 4 };
 struct Params {
   int N, L, T, Kp, S;
   int n_dnode, n_ramp, n_stor;
+  int n_hvdc, hvdc0;                     // HVDC links; device id of the first link's terminal 1
   // lines (internal numbering)
   const int *line_n1, *line_n2;  // internal node of terminal 1 (from) and terminal 2 (to)
   const float *line_b, *line_u;
@@ -100,6 +101,7 @@ struct Params {
   // batteries
   const int *stor_ids;
   const float *stor_eff, *stor_P, *stor_dur, *stor_cost;
+  const float *hvdc_u;                   // [n_hvdc]; link h has terminals hvdc0 + 2h, hvdc0 + 2h + 1
   float *stor_lam, *stor_beta, *stor_q, *stor_rho, *stor_delta;  // delta [n_stor][T]
   // numbering maps (internal -> caller) for import / export
   const int *node_perm, *line_perm;

@@ -297,6 +297,28 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float *sm, float *s
 }
 
 // ---------------------------------------------------------------------------
+// HVDC link (one warp, lanes over t): with x_i = p_i - avg_k(pbar + u) at
+// terminal i, p2 = clip((x2 - x1) / 2, -u, u) and p1 = -p2 (the minimiser
+// of the two squared distances over p1 + p2 = 0, clipped to the limit)
+// ---------------------------------------------------------------------------
+__device__ void hvdc_prox(const Params &p, int h, int lane) {
+  const int T = p.T;
+  const int d1 = p.hvdc0 + 2 * h, d2 = d1 + 1;
+  const float u = p.hvdc_u[h];
+  const float *xs1 = p.XS + (size_t)p.dev_node[d1] * T, *xs2 = p.XS + (size_t)p.dev_node[d2] * T;
+  float *pd1 = p.PD + (size_t)d1 * T, *pd2 = p.PD + (size_t)d2 * T;
+  for (int t = lane; t < T; t += 32) {
+    const float q1 = pd1[t], q2 = pd2[t];
+    const float x1 = q1 - __ldcg(xs1 + t), x2 = q2 - __ldcg(xs2 + t);
+    const float f = fminf(fmaxf(0.5f * (x2 - x1), -u), u);
+    p.DPD[(size_t)d1 * T + t] = -f - q1;
+    p.DPD[(size_t)d2 * T + t] = f - q2;
+    pd1[t] = -f;
+    pd2[t] = f;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Appendix D inner ADMM, battery (one warp, lanes over t).  Variables
 // (p, c, delta, s), rows as in opf.h.  The x-update eliminates p_t, then
 // (c_t, delta_t) per step (a 2x2 Schur complement), leaving a tridiagonal
@@ -760,12 +782,14 @@ __device__ __forceinline__ void inner_body(const Params &p, unsigned bid, unsign
   const int wfl = warp_smem_floats(p.T);
   float *wsm = smem + (size_t)wib * wfl;
   float *state_sh = (wfl > 3 * (p.T + 1)) ? wsm + 3 * (p.T + 1) : nullptr;
-  const int n_inner = p.n_stor + p.n_ramp;
+  const int n_inner = p.n_stor + p.n_ramp + p.n_hvdc;
   for (int w = bid * WARPS + wib; w < n_inner; w += nblk * WARPS) {
     if (w < p.n_stor)
       stor_prox(p, w, q.rho_dev, wsm, state_sh, lane);
-    else
+    else if (w < p.n_stor + p.n_ramp)
       ramp_prox(p, w - p.n_stor, q.rho_dev, wsm, state_sh, lane);
+    else
+      hvdc_prox(p, w - p.n_stor - p.n_ramp, lane);
   }
 }
 
@@ -1221,7 +1245,7 @@ int opfk_plan(const Params &p, IterPlan *plan) {
   const long long tvl = p.T / (v4 ? 4 : 1), tvn = p.T / (vn ? NODE_VW : 1);
   const long long nl = (long long)G * p.L * tvl, nn = (long long)G * p.N * tvn;
   const long long nx = (long long)p.n_dnode * (p.T / (v4 ? 4 : 1));
-  const int n_inner = p.n_stor + p.n_ramp;
+  const int n_inner = p.n_stor + p.n_ramp + p.n_hvdc;
   plan->line_grid = (int)((nl + (long long)BLOCK * LINE_IPT - 1) / ((long long)BLOCK * LINE_IPT));
   plan->node_grid = (int)std::min<long long>(gn, (nn + BLOCK - 1) / BLOCK);
   plan->xs_grid = (int)std::min<long long>(gx, (nx + BLOCK - 1) / BLOCK);
@@ -1291,7 +1315,7 @@ int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, const BatchL
       const Params &p = hp[i];
       const bool v4 = (p.T % 4 == 0), v2 = (p.T % 2 == 0), vn = (p.T % NODE_VW == 0);
       const long long tv4 = p.T / (v4 ? 4 : 1), tvn = p.T / (vn ? NODE_VW : 1), tv2 = p.T / (v2 ? 2 : 1);
-      const int n_inner = p.n_stor + p.n_ramp;
+      const int n_inner = p.n_stor + p.n_ramp + p.n_hvdc;
       long long blocks = 0;
       switch (kind) {
         case BK_XS4: case BK_XS1:

@@ -48,7 +48,7 @@ def test_price_scratch_capacity_matches_header():
 
 def test_abi_version_and_status_strings(lib):
     from paper_2410_17203_gb300 import binding as b
-    assert b.opf_abi_version() == 2
+    assert b.opf_abi_version() == 3
     for s in range(7):
         assert b.opf_status_str(s) not in ("", "unknown status")
     assert b.opf_status_str(99) == "unknown status"
@@ -105,6 +105,12 @@ def _bad(case, **changes):
     (lambda c: c.__setitem__("outaged", np.array([40], np.int32)), "outaged line"),
     (lambda c: c.__setitem__("T", 0), "horizon"),
     (lambda c: c.__setitem__("T", 4096), "horizon"),
+    (lambda c: c.update(hvdc_from=np.array([3], np.int32), hvdc_to=np.array([3], np.int32),
+                        hvdc_u=np.array([1.0])), "HVDC link connects a node to itself"),
+    (lambda c: c.update(hvdc_from=np.array([3], np.int32), hvdc_to=np.array([30], np.int32),
+                        hvdc_u=np.array([1.0])), "HVDC node id"),
+    (lambda c: c.update(hvdc_from=np.array([3], np.int32), hvdc_to=np.array([4], np.int32),
+                        hvdc_u=np.array([-1.0])), "HVDC limit"),
 ])
 def test_invalid_networks_are_rejected_on_the_host(lib, mutate, what):
     from gridgen import make_case

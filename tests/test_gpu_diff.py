@@ -124,6 +124,11 @@ def test_inner_admm_devices_match_autograd():
     _check(case, 30, ckpt=4)                       # T = 1: batteries only
 
 
+def test_hvdc_links_match_autograd():
+    case = make_case(scale_case(40, 6, 2, seed=7, ramp=True, stor_per_node=0.1, fixed_frac=0.3, n_hvdc=2))
+    _check(case, 40, ckpt=9)
+
+
 def test_inner_admm_devices_several_tiles():
     case = make_case(scale_case(300, 24, 4, seed=12, ramp=True, stor_per_node=0.05, fixed_frac=0.2))
     _check(case, 40, rho_p=5.0, rho_theta=10.0, ckpt=6)

@@ -45,6 +45,8 @@ CASES = {
     "T1_outages": lambda: make_case(scale_case(120, 1, 9, seed=24, fixed_frac=0.2)),
     "dup_noout": lambda: dict(make_case(scale_case(60, 12, 0, seed=25)),
                               outaged=np.array([-1, -1], np.int32)),
+    "hvdc_T24": lambda: make_case(scale_case(160, 24, 5, seed=26, n_hvdc=4)),
+    "hvdc_tiny": lambda: make_case("tiny", n_hvdc=3),
 }
 
 
@@ -59,7 +61,7 @@ def test_iterates_match_oracle_no_adaptation(name, n):
     assert info["iterations"] == n
 
 
-@pytest.mark.parametrize("name", ["tiny", "mixed_T24", "scalar_T7"])
+@pytest.mark.parametrize("name", ["tiny", "mixed_T24", "scalar_T7", "hvdc_T24"])
 def test_iterates_and_penalties_match_with_adaptation(name):
     case = CASES[name]()
     n = 100
