@@ -65,6 +65,7 @@ class OracleOptions:
     adapt_every: int = 10     # i_adapt (0 disables adaptation)
     inner_iters: int = 10     # inner ADMM iterations per iterative prox (Appendix D)
     check_every: int = 10     # stopping test cadence (0 = never)
+    alpha: float = 1.0        # over-relaxation parameter in [1, 2) (Section 3.6); 1 = plain ADMM
 
 
 # ---------------------------------------------------------------------------
@@ -393,6 +394,9 @@ class Oracle:
         self.th = np.zeros((Kp, 2 * L, T))
         self.v = np.zeros((Kp, 2 * L, T))
         self.u = np.zeros((Kp, N, T))
+        # duplicate variables of the over-relaxed form (Section 3.6)
+        self.z = np.zeros((Kp, J, T))
+        self.xi = np.zeros((Kp, 2 * L, T))
         self.rho_p = float(self.opts.rho_p)
         self.rho_th = float(self.opts.rho_theta)
         self.it = 0
@@ -461,6 +465,10 @@ class Oracle:
         self.v[:, :L] = f(st["v1"])
         self.v[:, L:] = f(st["v2"])
         self.u[:] = f(st["u"])
+        # the over-relaxed form restarts its duplicates where plain ADMM has
+        # them: z = p~, xi = theta_bar
+        self.z = self.p - average(net, self.p)
+        self.xi = average(net, self.th, phase=True)
         if rho_p is not None:
             self.rho_p = float(rho_p)
         if rho_theta is not None:
@@ -523,8 +531,9 @@ class Oracle:
 
     # -- one iteration
     def step(self):
-        net, o = self.net, self.opts
-        Kp, T, L = net.Kp, net.T, net.L
+        if self.opts.alpha != 1.0:
+            return self._step_relaxed()
+        net = self.net
         rp, rt = self.rho_p, self.rho_th
         p, th, u, v = self.p, self.th, self.u, self.v
         tn = net.term_node
@@ -535,11 +544,79 @@ class Oracle:
         ptil_old = p - pbar
         thbar_old = thbar
 
-        p_new = np.empty_like(p)
+        # step 1 at prox(p~ - u, theta_bar - v); step 2 at p_d - avg_k(pbar_kd + u_kd)
+        sd = net.sl_dev
+        p_new, th_new = self._proxes(ptil_old - uj, thbar - v,
+                                     p[0, sd] - self._kmean(pbar[:, sd] + uj[:, sd]))
 
-        # step 1: contingency devices (lines), every k -- prox(p~ - u, theta_bar - v)
-        x = ptil_old - uj
-        y = thbar - v
+        # step 3: scaled price updates u += pbar, v += theta~
+        pbar_new_n = node_mean(net, p_new)
+        pbar_new = pbar_new_n[:, tn, :]
+        thbar_new = average(net, th_new, phase=True)
+        u_new = u + pbar_new_n
+        v_new = v + (th_new - thbar_new)
+
+        # residuals (Section 3.3), with the penalties used in this iteration
+        r_pp = self._norm(pbar_new)
+        r_pt = self._norm(th_new - thbar_new)
+        r_dp = rp * self._norm((p_new - pbar_new) - ptil_old)
+        r_dt = rt * self._norm(thbar_new - thbar_old)
+        self._finish(p_new, th_new, u_new, v_new, r_pp, r_pt, r_dp, r_dt)
+
+    def _finish(self, p_new, th_new, u_new, v_new, r_pp, r_pt, r_dp, r_dt):
+        self.res = np.array([np.hypot(r_pp, r_pt), np.hypot(r_dp, r_dt), r_pp, r_pt, r_dp, r_dt])
+        self.p, self.th, self.u, self.v = p_new, th_new, u_new, v_new
+        self.it += 1
+        # adaptive penalty (Section 3.5), every adapt_every iterations
+        o = self.opts
+        if o.adapt_every and self.it % o.adapt_every == 0:
+            self._adapt(r_pp, r_pt, r_dp, r_dt)
+
+    def _step_relaxed(self):
+        """One over-relaxed ADMM iteration (Section 3.6) in the original form
+        of Section 3.1 with explicit duplicate variables z (every terminal)
+        and xi (phase terminals):
+
+        1-2. the proxes at (z - u, xi - v), and for the devices shared by all
+             contingencies at avg_k(z_kd - u_kd) with weight (K+1) rho_p;
+        3.   p^half = alpha p + (1 - alpha) z, theta^half likewise with xi;
+             z = projection of p^half + u onto {zbar = 0} (the residual
+             operator), xi = projection of theta^half + v onto {xi~ = 0}
+             (the average operator);
+        4.   u += p^half - z, v += theta^half - xi.
+        Residuals: r = (p - z, theta - xi), s = (rho_p (z - z_prev),
+        rho_theta (xi - xi_prev)).  With alpha = 1 this is the message
+        passing step above."""
+        net = self.net
+        tn = net.term_node
+        a, rp, rt = self.opts.alpha, self.rho_p, self.rho_th
+        z, xi = self.z, self.xi
+        uj = self.u[:, tn, :]
+        sd = net.sl_dev
+        p_new, th_new = self._proxes(z - uj, xi - self.v, self._kmean(z[:, sd] - uj[:, sd]))
+        p_half = a * p_new + (1.0 - a) * z
+        th_half = a * th_new + (1.0 - a) * xi
+        w = p_half + uj
+        u_node = node_mean(net, w)                      # average of p^half + u at each node
+        z_new = w - u_node[:, tn, :]                    # residual operator: zbar = 0
+        xi_new = average(net, th_half + self.v, phase=True)
+        u_new = u_node                                  # u + p^half - z (node-constant)
+        v_new = self.v + th_half - xi_new
+        r_pp = self._norm(p_new - z_new)
+        r_pt = self._norm(th_new - xi_new)
+        r_dp = rp * self._norm(z_new - z)
+        r_dt = rt * self._norm(xi_new - xi)
+        self.z, self.xi = z_new, xi_new
+        self._finish(p_new, th_new, u_new, v_new, r_pp, r_pt, r_dp, r_dt)
+
+    def _proxes(self, x, y, X):
+        """Steps 1 and 2: the line proxes of every contingency at (x, y)
+        (terminal-level) and the shared devices at X [S][T]; returns the new
+        terminal powers [Kp][J][T] and line angles [Kp][2L][T]."""
+        net, o = self.net, self.opts
+        Kp, T, L = net.Kp, net.T, net.L
+        rp, rt = self.rho_p, self.rho_th
+        p_new = np.empty((Kp, net.J, T))
         act = np.broadcast_to(net.active[:, :, None], (Kp, L, T))
         u_k = net.line_u[None, :, None] * act
         b_k = net.line_b[None, :, None] * act
@@ -548,10 +625,9 @@ class Oracle:
         p_new[:, net.sl_t1], p_new[:, net.sl_t2] = p1, p2
         th_new = np.concatenate([th1, th2], axis=1)
 
-        # step 2: non-contingency devices, one schedule shared by all k:
-        # prox with weight (K+1) rho_p at p_d - avg_k(pbar_kd + u_kd)
+        # step 2: non-contingency devices, one schedule shared by all k, prox
+        # with weight (K+1) rho_p
         sd = net.sl_dev
-        X = p[0, sd] - self._kmean(pbar[:, sd] + uj[:, sd])
         rho_d = self.Kp_total * rp
         self._factor()
         pd = np.empty_like(X)
@@ -593,27 +669,7 @@ class Oracle:
             h0, h1 = G + D + B, G + D + B + 2 * net.H
             pd[h0:h1:2], pd[h0 + 1:h1:2] = prox_hvdc(X[h0:h1:2], X[h0 + 1:h1:2], net.hvdc_u[:, None])
         p_new[:, sd] = pd[None]
-
-        # step 3: scaled price updates u += pbar, v += theta~
-        pbar_new_n = node_mean(net, p_new)
-        pbar_new = pbar_new_n[:, tn, :]
-        thbar_new = average(net, th_new, phase=True)
-        u_new = u + pbar_new_n
-        v_new = v + (th_new - thbar_new)
-
-        # residuals (Section 3.3), with the penalties used in this iteration
-        r_pp = self._norm(pbar_new)
-        r_pt = self._norm(th_new - thbar_new)
-        r_dp = rp * self._norm((p_new - pbar_new) - ptil_old)
-        r_dt = rt * self._norm(thbar_new - thbar_old)
-        self.res = np.array([np.hypot(r_pp, r_pt), np.hypot(r_dp, r_dt), r_pp, r_pt, r_dp, r_dt])
-
-        self.p, self.th, self.u, self.v = p_new, th_new, u_new, v_new
-        self.it += 1
-
-        # adaptive penalty (Section 3.5), every adapt_every iterations
-        if o.adapt_every and self.it % o.adapt_every == 0:
-            self._adapt(r_pp, r_pt, r_dp, r_dt)
+        return p_new, th_new
 
     # -- the two couplings across contingencies (reduced over a shard's peers)
     def _kmean(self, a):

@@ -8,7 +8,9 @@
   non-contingency prox input;
 * the residuals of Section 3.3 recomputed with the dense average matrix
   ``A = L' diag(|n|)^-1 L`` of Appendix B;
-* the invariant ``v_bar = 0`` (Section 3.2, Appendix C).
+* the invariant ``v_bar = 0`` (Section 3.2, Appendix C);
+* the over-relaxed iteration (Section 3.6) against the same dense full ADMM
+  with ``alpha p + (1 - alpha) z`` in the copy and price updates.
 """
 import numpy as np
 import pytest
@@ -68,7 +70,8 @@ class FullADMM:
 
     Closed-form devices only (lines, generators without ramps, loads)."""
 
-    def __init__(self, case, rho_p, rho_t):
+    def __init__(self, case, rho_p, rho_t, alpha=1.0):
+        self.alpha = alpha
         self.net = net = Network(case)
         assert not net.is_ramp.any() and net.B == 0
         Kp, J, L, T = net.Kp, net.J, net.L, net.T
@@ -104,13 +107,20 @@ class FullADMM:
         pl[net.is_fixed] = prox_fixed_load(pl[net.is_fixed], net.load_p[net.is_fixed])
         pd[G:G + D] = pl
         p[:, sd] = pd[None]
+        # over-relaxation (Section 3.6): the copies and prices see
+        # alpha p + (1 - alpha) z in place of p (alpha = 1: plain ADMM)
+        a = self.alpha
+        ph = a * p + (1 - a) * self.z
+        thh = a * th + (1 - a) * self.xi
         # 3. copies: projections onto {z_bar = 0} and {xi~ = 0}
-        w = p + self.u
+        w = ph + self.u
         z = w - np.einsum("ij,kjt->kit", self.Ap, w)
-        xi = np.einsum("ij,kjt->kit", self.At, th + self.v)
+        xi = np.einsum("ij,kjt->kit", self.At, thh + self.v)
         # 4. scaled prices
-        self.u = self.u + p - z
-        self.v = self.v + th - xi
+        self.u = self.u + ph - z
+        self.v = self.v + thh - xi
+        self.res = np.array([np.linalg.norm(p - z), np.linalg.norm(th - xi),
+                             self.rp * np.linalg.norm(z - self.z), self.rt * np.linalg.norm(xi - self.xi)])
         self.p, self.th, self.z, self.xi = p, th, z, xi
 
 
@@ -127,6 +137,30 @@ def test_message_passing_equals_full_admm(K):
         np.testing.assert_allclose(ora.th, ref.th, atol=1e-11)
         np.testing.assert_allclose(ora.u[:, net.term_node], ref.u, atol=1e-11)   # u~ = 0 kept
         np.testing.assert_allclose(ora.v, ref.v, atol=1e-11)
+
+
+@pytest.mark.parametrize("K", [0, 3])
+def test_over_relaxed_oracle_equals_full_admm(K):
+    """Section 3.6 with alpha = 1.5: the oracle's explicit-copy step (node
+    averages by CSR) against the dense full ADMM above, iterates, copies and
+    the four residual parts."""
+    case = small_case(K=K)
+    ora = Oracle(case, OracleOptions(adapt_every=0, rho_p=1.3, rho_theta=7.0, alpha=1.5))
+    ref = FullADMM(case, 1.3, 7.0, alpha=1.5)
+    net = ora.net
+    for _ in range(25):
+        ora.step()
+        ref.step()
+        np.testing.assert_allclose(ora.p, ref.p, atol=1e-11)
+        np.testing.assert_allclose(ora.th, ref.th, atol=1e-11)
+        np.testing.assert_allclose(ora.z, ref.z, atol=1e-11)
+        np.testing.assert_allclose(ora.xi, ref.xi, atol=1e-11)
+        np.testing.assert_allclose(ora.u[:, net.term_node], ref.u, atol=1e-11)   # u stays node-constant
+        np.testing.assert_allclose(ora.v, ref.v, atol=1e-11)
+        np.testing.assert_allclose(ora.res[2:], ref.res, rtol=1e-10, atol=1e-12)
+        # the invariants the simplification of Section 3.2 rests on also hold here
+        np.testing.assert_allclose(node_mean(net, ora.z), 0.0, atol=1e-11)
+        np.testing.assert_allclose(average(net, ora.v, phase=True), 0.0, atol=1e-11)
 
 
 def test_sign_of_u_in_device_prox_matters():

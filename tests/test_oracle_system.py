@@ -348,3 +348,15 @@ def test_tiny_with_hvdc_converges_to_independent_qp_optimum():
     g, fopt = _dcopf_slsqp(case)
     assert o.objective() == pytest.approx(fopt, rel=1e-6)
     np.testing.assert_allclose(o.dev_p()[:len(g), 0], g, atol=2e-4)
+
+
+def test_over_relaxed_iteration_reaches_the_same_optimum(tiny_converged):
+    """Section 3.6: alpha = 1.5 changes the path, not the fixed point."""
+    case, o1 = tiny_converged
+    o = Oracle(case, OracleOptions(adapt_every=0, rho_theta=10.0, eps=1e-8, alpha=1.5))
+    o.iterate(200000)
+    assert o.converged
+    g, fopt = _dcopf_slsqp(case)
+    assert o.objective() == pytest.approx(fopt, rel=1e-6)
+    np.testing.assert_allclose(o.dev_p()[:len(g), 0], g, atol=2e-4)
+    np.testing.assert_allclose(o.prices(), o1.prices(), rtol=1e-3)
