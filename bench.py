@@ -16,7 +16,8 @@ iterations and the solution download are inside the timed region.
 the eps = 1e-4 test of Eq. (converge) with the adaptive penalty, through the C
 ABI: the instance cold, the instance with every load scaled by
 lognormal(0, 0.05) cold, and that perturbed instance warm-started from the
-first solution (Section 3.4).
+first solution (Section 3.4); and the instance cold with over-relaxation
+alpha = 1.5 (Section 3.6; ``--ttt-alpha``).
 
 ``--adjoint K``: wall time of the cost gradient after K unrolled iterations
 (include/opf_diff.h) on the 2k instance, checkpoints every 20 iterations.
@@ -283,6 +284,11 @@ def time_to_tolerance(case, stream, args):
     out["perturbed_warm"] = entry(info, dt, h)
     opf_destroy(h)
     out["perturbation"] = "load_p x lognormal(0, 0.05) per (load, step), seed 12345"
+    if args.ttt_alpha != 1.0:
+        # the instance cold with over-relaxation (Section 3.6)
+        info, dt, h = solve_to_tolerance(case, stream, args, opts=dict(alpha=args.ttt_alpha))
+        out[f"cold_alpha_{args.ttt_alpha:g}"] = entry(info, dt, h)
+        opf_destroy(h)
     return out
 
 
@@ -391,7 +397,7 @@ def learned_warm_start(stream, args):
 
     base = make_case("2k")
     n_all = args.learned
-    n_test = max(1, n_all // 4)
+    n_test = min(256, max(1, n_all // 4))
     rng = np.random.default_rng(4)
     cases = []
     for i in range(n_all):
@@ -401,16 +407,21 @@ def learned_warm_start(stream, args):
     opts = dict(adapt_every=10, eps=1e-4)
     N, T = base["n_nodes"], base["T"]
     Kp = len(base["outaged"]) + 1
-    # 1. every instance cold, batched: the training targets and the baseline
-    hs = [opf_create(c, opts, stream=stream.cuda_stream) for c in cases]
-    its_cold, conv_cold, t_gen = batch_solve(hs, args)
-    Y = []
-    for h in hs:
-        price = np.zeros((N, T), np.float32)
-        theta = np.zeros((Kp, N, T), np.float32)
-        opf_solution(h, False, False, theta_node=theta, price=price)
-        Y.append(ws.targets(price, theta[0]))
-        opf_destroy(h)
+    # 1. every instance cold, in batches of at most 256 contexts (device
+    #    memory): the training targets and the baseline
+    its_cold, conv_cold, t_gen, Y = [], [], 0.0, []
+    for c0 in range(0, n_all, 256):
+        hs = [opf_create(c, opts, stream=stream.cuda_stream) for c in cases[c0:c0 + 256]]
+        its, conv, dt = batch_solve(hs, args)
+        its_cold += its
+        conv_cold += conv
+        t_gen += dt
+        for h in hs:
+            price = np.zeros((N, T), np.float32)
+            theta = np.zeros((Kp, N, T), np.float32)
+            opf_solution(h, False, False, theta_node=theta, price=price)
+            Y.append(ws.targets(price, theta[0]))
+            opf_destroy(h)
     X = [ws.node_features(c) for c in cases]
     train_idx = [i for i in range(n_all - n_test) if conv_cold[i]]
     test_idx = list(range(n_all - n_test, n_all))
@@ -442,7 +453,8 @@ def learned_warm_start(stream, args):
         opf_destroy(h)
     net.close()
     cold = [its_cold[i] for i in test_idx]
-    return {"network": "2k buses, T=24, K=20; loads x lognormal(0, 0.15) per (load, step), seed 4",
+    return {"network": "2k buses, T=24, K=20; loads x lognormal(0, 0.15) per (load, step), seed 4; "
+                       "test = the last min(256, n/4) instances",
             "instances": n_all, "train": len(train_idx), "test": len(test_idx),
             "epochs": args.learned_epochs, "lr": args.learned_lr,
             "train_loss_first_last": [hist[0], hist[-1]], "test_loss": test_loss,
@@ -645,6 +657,8 @@ def main():
                     help="skip the solves to eps = 1e-4 (cold, perturbed cold, perturbed warm)")
     ap.add_argument("--ttt-max", type=int, default=30000)
     ap.add_argument("--ttt-chunk", type=int, default=100)
+    ap.add_argument("--ttt-alpha", type=float, default=1.5,
+                    help="also solve the instance cold with this over-relaxation (1 = skip)")
     ap.add_argument("--learned", type=int, default=0,
                     help="also train the warm-start network on this many perturbed 2k instances "
                          "(a quarter held out) and compare iterations to eps = 1e-4")

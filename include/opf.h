@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define OPF_ABI_VERSION 3
+#define OPF_ABI_VERSION 4
 
 typedef struct opf_ctx opf_ctx; /* opaque, created by opf_create, freed by opf_destroy */
 
@@ -106,12 +106,17 @@ typedef struct {
 } opf_contingencies;
 
 /* Algorithm options.  opf_default_options fills the paper's defaults
- * (Section 5.2): rho_p = rho_theta = 1, mu = 2, gamma = 1.1, adapt every 10
+ * (Section 5.2): rho_p = rho_theta = 1, mu = 2, gamma = 1.1, alpha = 1, adapt every 10
  * iterations, 10 inner iterations (Section 4.5), eps = 1e-4 tested every 10. */
 typedef struct {
   double rho_p, rho_theta;  /* initial penalties (> 0) */
   double eps;               /* Eq. (converge) tolerance; <= 0 disables stopping */
   double mu, gamma;         /* adaptive penalty: threshold and factor (Section 3.5) */
+  double alpha;             /* over-relaxation in [1, 2) (Section 3.6); 1 = message passing.
+                               With alpha != 1 the copies and prices take
+                               alpha p + (1 - alpha) z; exported schedules are the
+                               actual iterate, and a state import restarts the
+                               copies at z = p~, xi = theta_bar */
   int32_t adapt_every;      /* penalty update cadence; 0 disables adaptation */
   int32_t inner_iters;      /* Appendix D iterations per iterative prox (>= 1) */
   int32_t check_every;      /* stopping test cadence; 0 disables stopping */
@@ -230,7 +235,8 @@ opf_status opf_price_noalloc(opf_ctx *ctx, float *price);
  * once, so a batch can be iterated until every instance has converged.
  * opf_batch_converged counts the converged instances (synchronizes).  The
  * contexts must outlive the batch; opf_batch_create allocates the device
- * copies of the instances' parameters and the schedule. */
+ * copies of the instances' parameters and the schedule.  The instances of a
+ * batch all run plain (alpha = 1) or all over-relaxed (OPF_EINVAL otherwise). */
 typedef struct opf_batch opf_batch;
 opf_status opf_batch_create(opf_ctx *const *ctxs, int32_t n, opf_batch **out);
 opf_status opf_batch_iterate(opf_batch *batch, int32_t n_iters);

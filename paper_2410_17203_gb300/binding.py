@@ -51,7 +51,7 @@ class opf_contingencies(C.Structure):
 class opf_options(C.Structure):
     _fields_ = [
         ("rho_p", C.c_double), ("rho_theta", C.c_double), ("eps", C.c_double),
-        ("mu", C.c_double), ("gamma", C.c_double),
+        ("mu", C.c_double), ("gamma", C.c_double), ("alpha", C.c_double),
         ("adapt_every", C.c_int32), ("inner_iters", C.c_int32), ("check_every", C.c_int32),
         ("reserved0", C.c_int32),
         ("sync_timeout_ms", C.c_int64),
@@ -76,7 +76,7 @@ class opf_info(C.Structure):
     ]
 
 
-ABI_VERSION = 3     # OPF_ABI_VERSION of include/opf.h
+ABI_VERSION = 4     # OPF_ABI_VERSION of include/opf.h
 
 EXPORTS = ["opf_default_options", "opf_create", "opf_iterate", "opf_residuals", "opf_solution",
            "opf_price_noalloc", "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info",

@@ -104,6 +104,7 @@ void opf_default_options(opf_options *o) {
   o->eps = 1e-4;
   o->mu = 2.0;
   o->gamma = 1.1;
+  o->alpha = 1.0;
   o->adapt_every = 10;
   o->inner_iters = 10;
   o->check_every = 10;
@@ -222,6 +223,7 @@ opf_status validate(const opf_network *net, int T, const opf_contingencies *ctg,
   }
   if (!(o.rho_p > 0) || !(o.rho_theta > 0) || !std::isfinite(o.rho_p) || !std::isfinite(o.rho_theta))
     return fail(OPF_EINVAL, "penalties must be finite and > 0");
+  if (!(o.alpha >= 1.0 && o.alpha < 2.0)) return fail(OPF_EINVAL, "over-relaxation alpha must be in [1, 2)");
   if (!(o.mu > 0) || !(o.gamma >= 1) || o.inner_iters < 1 || o.adapt_every < 0 || o.check_every < 0 ||
       !std::isfinite(o.eps))
     return fail(OPF_EINVAL, "invalid options");
@@ -688,6 +690,7 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   p.eps = opt.eps;
   p.mu = opt.mu;
   p.gamma = opt.gamma;
+  p.alpha = (float)opt.alpha;
   p.adapt_every = opt.adapt_every;
   p.check_every = opt.check_every;
   p.inner_iters = opt.inner_iters;
@@ -907,16 +910,25 @@ opf_status opf_solution(opf_ctx *c, int32_t on_device, double *objective, float 
   if ((s = read_scalars(c, &sc)) != OPF_OK) return s;
   const int cur = (int)(sc.it & 1);
   const size_t T = c->T, KLT = (size_t)c->Kp * c->L * T, KNT = (size_t)c->Kp * c->N * T, NT = (size_t)c->N * T;
-  if (p_dev)
-    CK(cudaMemcpyAsync(p_dev, c->P.PD, (size_t)c->S * T * sizeof(float),
-                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  const size_t ST = (size_t)c->S * T;
+  const bool relax = c->opt.alpha != 1.0;
   DevTmp tmp;
-  if (!on_device && (p_line || theta_node || price)) {
-    if ((s = alloc_tmp(tmp, (p_line ? KLT : 0) + (theta_node ? KNT : 0) + (price ? NT : 0))) != OPF_OK)
+  if ((!on_device && (p_line || theta_node || price)) || (relax && (p_dev || objective))) {
+    if ((s = alloc_tmp(tmp, (p_line ? KLT : 0) + (theta_node ? KNT : 0) + (price ? NT : 0) + ST)) != OPF_OK)
       return s;
   }
   float *tl = tmp.p, *tt = tmp.p ? tmp.p + (p_line ? KLT : 0) : nullptr;
   float *tp = tt ? tt + (theta_node ? KNT : 0) : nullptr;
+  // device powers: PD itself, or the actual iterate rebuilt from the relaxed state
+  const float *pd_src = c->P.PD;
+  if (relax && (p_dev || objective)) {
+    float *td = tmp.p + (p_line ? KLT : 0) + (theta_node ? KNT : 0) + (price ? NT : 0);
+    if (opfk_export_pdev_launch(c->P, td, c->stream) != 0) return fail(OPF_ECUDA, "export launch failed");
+    pd_src = td;
+  }
+  if (p_dev)
+    CK(cudaMemcpyAsync(p_dev, pd_src, ST * sizeof(float),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   if (p_line && opfk_export_lines_launch(c->P, cur, stage(p_line, on_device, tl), nullptr, nullptr,
                                          nullptr, nullptr, c->stream) != 0)
     return fail(OPF_ECUDA, "export launch failed");
@@ -931,7 +943,7 @@ opf_status opf_solution(opf_ctx *c, int32_t on_device, double *objective, float 
   }
   if (objective) {
     std::vector<float> pd((size_t)c->S * T), dl((size_t)c->n_stor * T);
-    CK(cudaMemcpyAsync(pd.data(), c->P.PD, pd.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(pd.data(), pd_src, pd.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     if (!dl.empty())
       CK(cudaMemcpyAsync(dl.data(), c->P.stor_delta, dl.size() * sizeof(float), cudaMemcpyDeviceToHost,
                          c->stream));
@@ -1077,8 +1089,9 @@ opf_status opf_batch_create(opf_ctx *const *ctxs, int32_t n, opf_batch **out) {
   long long len = 0;
   opf_status st = OPF_OK;
   const opfk::BatchLayout lay{nullptr, 0, 1};   // as given, contiguous: the longest schedule
-  if (opfk_batch_plan(hp.data(), plans.data(), n, lay, nullptr, 0, &len, &b->plan) != 0)
-    st = fail(OPF_ECUDA, "batch schedule");
+  const int pr = opfk_batch_plan(hp.data(), plans.data(), n, lay, nullptr, 0, &len, &b->plan);
+  if (pr == -2) st = fail(OPF_EINVAL, "a batch cannot mix over-relaxed (alpha != 1) and plain instances");
+  else if (pr != 0) st = fail(OPF_ECUDA, "batch schedule");
   std::vector<int> sched(4 * (size_t)std::max(len, 1LL));
   if (st == OPF_OK && opfk_batch_plan(hp.data(), plans.data(), n, lay, sched.data(), len, &len, &b->plan) != 0)
     st = fail(OPF_ECUDA, "batch schedule");
@@ -1249,18 +1262,27 @@ opf_status opf_get_state(opf_ctx *c, int32_t on_device, const opf_state *dst) {
   if ((s = read_scalars(c, &sc)) != OPF_OK) return s;
   const int cur = (int)(sc.it & 1);
   const size_t KLT = (size_t)c->Kp * c->L * c->T, KNT = (size_t)c->Kp * c->N * c->T;
-  if (dst->p_dev)
-    CK(cudaMemcpyAsync(dst->p_dev, c->P.PD, (size_t)c->S * c->T * sizeof(float),
-                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  const size_t ST = (size_t)c->S * c->T;
+  const bool relax = c->opt.alpha != 1.0;
   float *lines[5] = {dst->p_line, dst->th1, dst->th2, dst->v1, dst->v2};
   DevTmp tmp;
-  if (!on_device) {
-    size_t n = dst->u ? KNT : 0;
+  if (!on_device || (relax && dst->p_dev)) {
+    size_t n = (dst->u ? KNT : 0) + ST;
     for (float *x : lines) n += x ? KLT : 0;
     if ((s = alloc_tmp(tmp, n)) != OPF_OK) return s;
   }
+  if (dst->p_dev) {
+    const float *pd_src = c->P.PD;
+    if (relax) {
+      float *td = tmp.p;   // the first ST floats of the staging area
+      if (opfk_export_pdev_launch(c->P, td, c->stream) != 0) return fail(OPF_ECUDA, "export launch failed");
+      pd_src = td;
+    }
+    CK(cudaMemcpyAsync(dst->p_dev, pd_src, ST * sizeof(float),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  }
   float *stg[5];
-  float *cursor = tmp.p;
+  float *cursor = tmp.p ? tmp.p + ST : nullptr;
   for (int j = 0; j < 5; ++j) {
     stg[j] = lines[j] ? (on_device ? lines[j] : cursor) : nullptr;
     if (lines[j] && !on_device) cursor += KLT;

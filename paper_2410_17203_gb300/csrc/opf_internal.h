@@ -102,6 +102,7 @@ struct Params {
   const int *stor_ids;
   const float *stor_eff, *stor_P, *stor_dur, *stor_cost;
   const float *hvdc_u;                   // [n_hvdc]; link h has terminals hvdc0 + 2h, hvdc0 + 2h + 1
+  float alpha;                           // over-relaxation (Section 3.6); 1 = plain message passing
   float *stor_lam, *stor_beta, *stor_q, *stor_rho, *stor_delta;  // delta [n_stor][T]
   // numbering maps (internal -> caller) for import / export
   const int *node_perm, *line_perm;
@@ -130,6 +131,7 @@ struct BatchPlan {
   int count[BK_COUNT];
   int offset[BK_COUNT];
   size_t inner_smem;
+  int relax;   // the instances run over-relaxed (alpha != 1): the node kernels that carry it
 };
 // How a batch schedule lays out CTAs: instances in `order` (NULL: as given),
 // each instance's CTAs of a phase contiguous or dealt round-robin across
@@ -172,6 +174,8 @@ int opfk_node_average_launch(const opfk::Params &p, int cur, void *stream);
 int opfk_project_v_launch(const opfk::Params &p, int cur, void *stream);
 int opfk_export_lines_launch(const opfk::Params &p, int cur, float *p_line, float *th1, float *th2,
                              float *v1, float *v2, void *stream);
+// Device powers [S][T] (caller order = internal order) of the actual iterate.
+int opfk_export_pdev_launch(const opfk::Params &p, float *out, void *stream);
 int opfk_export_nodes_launch(const opfk::Params &p, int cur, float *u, float *theta_node,
                              float *price, void *stream);
 int opfk_set_rho_launch(opfk::DevScalars *sc, double rho, void *stream);

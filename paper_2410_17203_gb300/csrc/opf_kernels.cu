@@ -186,6 +186,14 @@ __device__ __forceinline__ void ksum4(const float *pbar_o, const float *u_o, siz
 // X[t] = p_d[t] - avg_k(pbar + u) at the device's node n, t in [0, T), by
 // one warp (Section 3.2 step 2 input); the average was formed this iteration
 // by the node-average items into XS
+// Over-relaxation (Section 3.6) in the form kept on the device: the stored
+// schedules are the relaxed P = alpha p + (1 - alpha) P_prev, whose node
+// averages are the copies' complements (z = P - avg_n P, xi = avg_n Theta);
+// alpha = 1 returns p exactly.
+__device__ __forceinline__ float relaxed(float alpha, float pnew, float pold) {
+  return fmaf(alpha, pnew, (1.f - alpha) * pold);
+}
+
 __device__ __forceinline__ void device_x(const Params &p, int n, const float *pd, float *X, int lane) {
   const int T = p.T;
   const float *xs = p.XS + (size_t)n * T;
@@ -289,7 +297,7 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float *sm, float *s
   }
   stage_out(lam_g, bet_g, state_sh, RG_N * T, lane);
   for (int t = lane; t < T; t += 32) {
-    const float pn = Z[t];
+    const float pn = relaxed(p.alpha, Z[t], pd[t]);
     p.DPD[(size_t)d * T + t] = pn - pd[t];
     pd[t] = pn;
   }
@@ -311,10 +319,11 @@ __device__ void hvdc_prox(const Params &p, int h, int lane) {
     const float q1 = pd1[t], q2 = pd2[t];
     const float x1 = q1 - __ldcg(xs1 + t), x2 = q2 - __ldcg(xs2 + t);
     const float f = fminf(fmaxf(0.5f * (x2 - x1), -u), u);
-    p.DPD[(size_t)d1 * T + t] = -f - q1;
-    p.DPD[(size_t)d2 * T + t] = f - q2;
-    pd1[t] = -f;
-    pd2[t] = f;
+    const float r1 = relaxed(p.alpha, -f, q1), r2 = relaxed(p.alpha, f, q2);
+    p.DPD[(size_t)d1 * T + t] = r1 - q1;
+    p.DPD[(size_t)d2 * T + t] = r2 - q2;
+    pd1[t] = r1;
+    pd2[t] = r2;
   }
 }
 
@@ -421,7 +430,7 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float *sm, float
 #undef BET
   stage_out(lam_g, bet_g, state_sh, SG_N * Tp, lane);
   for (int t = lane; t < T; t += 32) {
-    const float pn = TAU[t];
+    const float pn = relaxed(p.alpha, TAU[t], pd[t]);
     p.DPD[(size_t)d * T + t] = pn - pd[t];
     pd[t] = pn;
   }
@@ -512,6 +521,32 @@ struct Welf {
   }
 };
 
+// one-pass sums of two series over a node's terminals (Welford with the
+// co-moment): means, centred second moments and sum (x - mean_x)(y - mean_y)
+template <int VW>
+struct Welf2 {
+  float n;
+  float mx[VW], my[VW], m2x[VW], m2y[VW], cxy[VW];
+  __device__ __forceinline__ void reset() {
+    n = 0.f;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) { mx[e] = my[e] = m2x[e] = m2y[e] = cxy[e] = 0.f; }
+  }
+  __device__ __forceinline__ void add(const float *x, const float *y) {
+    n += 1.f;
+    const float r = __frcp_rn(n);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const float dx = x[e] - mx[e], dy = y[e] - my[e];
+      mx[e] = fmaf(dx, r, mx[e]);
+      my[e] = fmaf(dy, r, my[e]);
+      m2x[e] = fmaf(dx, x[e] - mx[e], m2x[e]);
+      m2y[e] = fmaf(dy, y[e] - my[e], m2y[e]);
+      cxy[e] = fmaf(dx, y[e] - my[e], cxy[e]);
+    }
+  }
+};
+
 // x / c given r = 1/c rounded to nearest: one FMA correction step gives the
 // correctly rounded quotient for these well-scaled operands (a plain x * r
 // would carry the rounding bias of r into every node average, iteration
@@ -568,26 +603,33 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
     den = 2.f * frp + frt / (tb * bb);   // denominator as derived in the oracle
   }
   const float rden = __frcp_rn(den), rtb = __frcp_rn(tb);
+  const float al = p.alpha, oma = 1.f - p.alpha;
 #pragma unroll
   for (int e = 0; e < VW; ++e) {
-    // the previous prox's terminal values (stored as p and the mean angle)
+    // the previous prox's terminal values (stored as p and the mean angle;
+    // relaxed values when alpha != 1, Section 3.6)
     const float po = act ? P.v[e] : 0.f;
     const float ho = act ? div_rn(P.v[e], tb, rtb) : P.v[e];
     const float a1 = M.v[e] + ho, a2 = M.v[e] - ho;
-    const float x1 = -po - B1.v[e] - fsu * U1.v[e];         // p~ - u at terminal 1
+    const float x1 = -po - B1.v[e] - fsu * U1.v[e];         // p~ - u at terminal 1 (z - u relaxed)
     const float x2 = po - B2.v[e] - fsu * U2.v[e];          // p~ - u at terminal 2
-    const float v1 = v_fresh ? fsv * V1.v[e] : fsv * (V1.v[e] + (a1 - G1.v[e]));
-    const float v2 = v_fresh ? fsv * V2.v[e] : fsv * (V2.v[e] + (a2 - G2.v[e]));
+    const float r1 = a1 - G1.v[e], r2 = a2 - G2.v[e];       // theta - theta_bar (Theta - xi relaxed)
+    const float v1 = v_fresh ? fsv * V1.v[e] : fsv * (V1.v[e] + r1);
+    const float v2 = v_fresh ? fsv * V2.v[e] : fsv * (V2.v[e] + r2);
     const float y1 = G1.v[e] - v1, y2 = G2.v[e] - v2;       // theta_bar - v
-    M.v[e] = 0.5f * (y1 + y2);
+    const float mo = M.v[e], sto = P.v[e];
+    M.v[e] = fmaf(al, 0.5f * (y1 + y2), oma * mo);
     if (act) {
       const float num = frp * (x2 - x1) + div_rn(frt * (y1 - y2), tb, rtb);
       P.v[e] = fminf(fmaxf(div_rn(num, den, rden), -ulim), ulim);   // theta_{1,2} = mid +- p / (2b)
     } else {
       P.v[e] = 0.5f * (y1 - y2);   // outaged line: p = 0, the terminals decouple, theta = y
     }
-    V1.v[e] = v1;
-    V2.v[e] = v2;
+    P.v[e] = fmaf(al, P.v[e], oma * sto);
+    // v' = v - (Theta - xi) is what the next pass completes:
+    // v'_new = v + alpha theta~_new - (Theta_new - xi_new) = v - (1 - alpha) (Theta - xi)
+    V1.v[e] = fmaf(-oma, r1, v1);
+    V2.v[e] = fmaf(-oma, r2, v2);
   }
   // p and the mean angle are read back by the node sums; v is not
   stv<VW>(p.P[nw] + ol, P);
@@ -605,7 +647,7 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
 // terminal codes come four at a time so that a node's row loads issue
 // together.
 // ---------------------------------------------------------------------------
-template <int VW>
+template <int VW, bool RELAX>
 __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int k, int n, int toff, float fsu,
                                           float *acc) {
   const int T = p.T, L = p.L, N = p.N;
@@ -619,6 +661,8 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
   // same in every contingency
   FV<VW> sp = ldv<VW>(p.DSP + os), st;
   Welf<VW> wdp, wth;
+  Welf2<VW> wrx;   // RELAX: (Theta_new, Theta_new - Theta_old) over the line terminals
+  if constexpr (RELAX) wrx.reset();
   {
     const FV<VW> m = ldv<VW>(p.DSM + os), q = ldv<VW>(p.DSQ + os);
     wdp.n = (float)r2.z;
@@ -635,7 +679,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
   int4 c4 = r1;
   for (int j = r2.x - 4;;) {
     const int code[4] = {c4.x, c4.y, c4.z, c4.w};
-    FV<VW> pn[4], po[4], mq[4];
+    FV<VW> pn[4], po[4], mq[4], mo[RELAX ? 4 : 1];
     float bq[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -645,6 +689,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
         pn[q] = ldv<VW>(p.P[nw] + ol);
         po[q] = ldv<VW>(p.P[old] + ol);   // kept in L2 for the line's other end
         mq[q] = ldv<VW>(p.MID[nw] + ol);
+        if constexpr (RELAX) mo[q] = ldv<VW>(p.MID[old] + ol);
         bq[q] = p.line_b[l];
       }
     }
@@ -653,7 +698,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
       if (code[q] >= 0) {
         const bool t2 = code[q] & 1, act = (code[q] >> 1) != lout;
         const float tb = 2.f * bq[q], rtb = __frcp_rn(tb);
-        float dpo[VW], th[VW];
+        float dpo[VW], th[VW], dth[VW];
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
           const float pv = act ? pn[q].v[e] : 0.f, pov = act ? po[q].v[e] : 0.f;
@@ -662,9 +707,14 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
           sp.v[e] += t2 ? pv : -pv;
           st.v[e] += th[e];
           dpo[e] = t2 ? pv - pov : pov - pv;
+          if constexpr (RELAX) {
+            const float ho = act ? div_rn(po[q].v[e], tb, rtb) : po[q].v[e];
+            dth[e] = th[e] - (t2 ? mo[q].v[e] - ho : mo[q].v[e] + ho);
+          }
         }
         wdp.add(dpo);
-        wth.add(th);
+        if constexpr (RELAX) wrx.add(th, dth);
+        else wth.add(th);
       }
     }
     j += 4;
@@ -676,10 +726,23 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
   for (int e = 0; e < VW; ++e) {
     pb.v[e] = div_rn(sp.v[e], cp, rcp);                      // Eq. (average-op)
     tbar.v[e] = ct > 0.f ? div_rn(st.v[e], ct, rct) : 0.f;
-    un.v[e] = fsu * uo.v[e] + pb.v[e];                       // u += pbar
     const float dt = tbar.v[e] - go.v[e];
-    acc[SL_PP] += cp * pb.v[e] * pb.v[e];
-    acc[SL_PT] += wth.m2[e];
+    if constexpr (RELAX) {
+      // stored values are relaxed: pb = Q = avg_n P, tbar = xi.  The actual
+      // iterate is P + c dP with c = (1 - alpha) / alpha, so
+      //   u += alpha pbar_actual = alpha Q + (1 - alpha) dQ,
+      //   ||p - z||^2 = c^2 sum (dP - dQ)^2 + |n| (Q + c dQ)^2,
+      //   ||theta - xi||^2 = sum (Theta - xi + c dTheta)^2 by the co-moment
+      const float a = p.alpha, c = (1.f - a) / a, dq = wdp.mean[e];
+      un.v[e] = fsu * uo.v[e] + fmaf(a, pb.v[e], (1.f - a) * dq);
+      const float qc = fmaf(c, dq, pb.v[e]);
+      acc[SL_PP] += fmaf(c * c, wdp.m2[e], cp * qc * qc);
+      acc[SL_PT] += wrx.m2x[e] + c * (2.f * wrx.cxy[e] + c * fmaf(wrx.n * wrx.my[e], wrx.my[e], wrx.m2y[e]));
+    } else {
+      un.v[e] = fsu * uo.v[e] + pb.v[e];                     // u += pbar
+      acc[SL_PP] += cp * pb.v[e] * pb.v[e];
+      acc[SL_PT] += wth.m2[e];
+    }
     acc[SL_DP] += wdp.m2[e];
     acc[SL_DT] += ct * dt * dt;
     if (!isfinite(un.v[e]) || !isfinite(tbar.v[e])) acc[SL_NF] += 1.f;
@@ -763,7 +826,8 @@ __device__ __forceinline__ void xs_body(const Params &p, unsigned bid, unsigned 
 #pragma unroll
       for (int e = 0; e < VW; ++e) {
         const float x = pd.v[e] - xs.v[e];                 // p_d - avg_k(pbar + u)
-        pn.v[e] = fminf(fmaxf(div_rn(q.rho_dev * x - bd, den, rden), lo.v[e]), hi.v[e]);
+        pn.v[e] = relaxed(p.alpha, fminf(fmaxf(div_rn(q.rho_dev * x - bd, den, rden), lo.v[e]), hi.v[e]),
+                          pd.v[e]);
         dp.v[e] = pn.v[e] - pd.v[e];
       }
       stv<VW>(p.DPD + od, dp);
@@ -854,7 +918,7 @@ __device__ __forceinline__ void line_body(const Params &p, int k0, int k1, unsig
 // node: step 3 for every (contingency, node, VW time steps), and the CTA's
 // residual partial sums: FP32 per thread, FP64 across warps
 // ---------------------------------------------------------------------------
-template <int VW>
+template <int VW, bool RELAX>
 __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int first, unsigned bid,
                                           unsigned nblk) {
   __shared__ double red[WARPS][NSLOT];
@@ -870,7 +934,7 @@ __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int f
   ix.set(item, N, TV);
   dx.set(stride, N, TV);
   for (; item < n; item += stride, ix.step(dx, N, TV))
-    node_item<VW>(p, q.old, q.nw, k0 + ix.a, ix.b, ix.c * VW, q.fsu, acc);
+    node_item<VW, RELAX>(p, q.old, q.nw, k0 + ix.a, ix.b, ix.c * VW, q.fsu, acc);
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     float v = acc[s];
@@ -979,9 +1043,11 @@ __global__ void __launch_bounds__(BLOCK, 4) line_kernel(Params p, int k0, int k1
   line_body<VW>(p, k0, k1, blockIdx.x);
 }
 
-template <int VW>
-__global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel(Params p, int k0, int k1, int first) {
-  node_body<VW>(p, k0, k1, first, blockIdx.x, gridDim.x);
+// the over-relaxed variant carries more per-terminal state: it takes the
+// registers of one CTA per SM rather than spill
+template <int VW, bool RELAX>
+__global__ void __launch_bounds__(BLOCK, RELAX ? 1 : NODE_MIN_CTAS) node_kernel(Params p, int k0, int k1, int first) {
+  node_body<VW, RELAX>(p, k0, k1, first, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(BLOCK) decide_kernel(Params p, int n_part) { decide_body(p, n_part); }
@@ -1033,12 +1099,12 @@ __global__ void __launch_bounds__(BLOCK, 4) line_kernel_b(const Params *ps, cons
   line_body<VW>(p, 0, p.Kp, bid);
 }
 
-template <int VW>
-__global__ void __launch_bounds__(BLOCK, NODE_MIN_CTAS) node_kernel_b(const Params *ps, const int4 *sched) {
+template <int VW, bool RELAX>
+__global__ void __launch_bounds__(BLOCK, RELAX ? 1 : NODE_MIN_CTAS) node_kernel_b(const Params *ps, const int4 *sched) {
   __shared__ Params sp;
   unsigned bid, nblk;
   const Params &p = batch_params(ps, sched, sp, bid, nblk);
-  node_body<VW>(p, 0, p.Kp, 1, bid, nblk);
+  node_body<VW, RELAX>(p, 0, p.Kp, 1, bid, nblk);
 }
 
 __global__ void __launch_bounds__(BLOCK) decide_kernel_b(const Params *ps, const int4 *sched) {
@@ -1051,6 +1117,11 @@ __global__ void __launch_bounds__(BLOCK) decide_kernel_b(const Params *ps, const
 // A line's terminal values from its stored (p, mid) at contingency k:
 // p2 (0 on the outaged line) and theta_{1,2} = mid +- h, h = p / (2b) on an
 // active line and the stored value itself on the outaged line.
+// the actual iterate from two relaxed ones: (P - (1 - alpha) P_prev) / alpha
+__device__ __forceinline__ float actual(float alpha, float cur, float prev) {
+  return (cur - (1.f - alpha) * prev) / alpha;
+}
+
 __device__ __forceinline__ void line_terminals(const Params &p, int cur, int k, int l, size_t i, float &p2,
                                                float &th1, float &th2) {
   const float ps = p.P[cur][i], m = p.MID[cur][i];
@@ -1162,9 +1233,6 @@ __global__ void export_lines_kernel(Params p, int cur, float *pl, float *a1, flo
     const size_t dst = ((size_t)k * L + p.line_perm[l]) * T + t;
     float p2, th1, th2;
     line_terminals(p, cur, k, l, (size_t)i, p2, th1, th2);
-    if (pl) pl[dst] = p2;
-    if (a1) a1[dst] = th1;
-    if (a2) a2[dst] = th2;
     if (v1 || v2) {
       float x = p.V1[cur][i], y = p.V2[cur][i];
       if (!sc.v_fresh) {
@@ -1174,6 +1242,17 @@ __global__ void export_lines_kernel(Params p, int cur, float *pl, float *a1, flo
       if (v1) v1[dst] = sv * x;
       if (v2) v2[dst] = sv * y;
     }
+    if (p.alpha != 1.f && !sc.v_fresh) {
+      // over-relaxed: the buffers hold P = alpha p + (1 - alpha) P_prev
+      float q2, q1a, q2a;
+      line_terminals(p, cur ^ 1, k, l, (size_t)i, q2, q1a, q2a);
+      p2 = actual(p.alpha, p2, q2);
+      th1 = actual(p.alpha, th1, q1a);
+      th2 = actual(p.alpha, th2, q2a);
+    }
+    if (pl) pl[dst] = p2;
+    if (a1) a1[dst] = th1;
+    if (a2) a2[dst] = th2;
   }
 }
 
@@ -1191,11 +1270,24 @@ __global__ void export_nodes_kernel(Params p, int cur, float *u, float *theta, f
       const size_t o = (size_t)k * N * T + i;
       const float uu = p.U[cur][o];
       if (u) u[(size_t)k * N * T + ext] = (float)(sc.su * uu);
-      if (theta) theta[(size_t)k * N * T + ext] = p.THBAR[cur][o];
+      if (theta)
+        theta[(size_t)k * N * T + ext] = (p.alpha != 1.f && !sc.v_fresh)
+                                             ? actual(p.alpha, p.THBAR[cur][o], p.THBAR[cur ^ 1][o])
+                                             : p.THBAR[cur][o];
       s += uu;
     }
     if (price) price[ext] = (float)(-sc.rho_p * sc.su * s);
   }
+}
+
+// device powers in caller order: the actual iterate (relaxed state undone)
+__global__ void export_pdev_kernel(Params p, float *out) {
+  const DevScalars sc = *p.sc;
+  const bool rx = p.alpha != 1.f && !sc.v_fresh;
+  const float c = (1.f - p.alpha) / p.alpha;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)p.S * p.T;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = rx ? fmaf(c, p.DPD[i], p.PD[i]) : p.PD[i];
 }
 
 __global__ void set_rho_kernel(DevScalars *sc, double rho) {
@@ -1230,7 +1322,7 @@ int opfk_plan(const Params &p, IterPlan *plan) {
       cudaFuncSetAttribute(inner_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism) != cudaSuccess)
     return -1;
   const bool vn = (p.T % NODE_VW == 0);
-  const int gn = vn ? resident_grid(node_kernel<NODE_VW>, 0) : resident_grid(node_kernel<1>, 0);
+  const int gn = vn ? resident_grid(node_kernel<NODE_VW, false>, 0) : resident_grid(node_kernel<1, false>, 0);
   const int gx = v4 ? resident_grid(xs_kernel<4>, 0) : resident_grid(xs_kernel<1>, 0);
   const int gd = v2 ? resident_grid(dsum_kernel<2>, 0) : resident_grid(dsum_kernel<1>, 0);
   if (gn < 1 || gx < 1 || gd < 1) return -1;
@@ -1282,8 +1374,11 @@ int opfk_iteration_enqueue(const Params &p, const IterPlan &plan, void *main_str
       if (cudaEventRecord((cudaEvent_t)ev_join, sa) != cudaSuccess) return -1;
       if (cudaStreamWaitEvent(sm, (cudaEvent_t)ev_join, 0) != cudaSuccess) return -1;
     }
-    if (p.T % NODE_VW == 0) node_kernel<NODE_VW><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
-    else node_kernel<1><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
+    const bool vn = p.T % NODE_VW == 0, rx = p.alpha != 1.f;
+    if (vn && !rx) node_kernel<NODE_VW, false><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
+    else if (!rx) node_kernel<1, false><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
+    else if (vn) node_kernel<NODE_VW, true><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
+    else node_kernel<1, true><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
   }
   decide_kernel<<<1, BLOCK, 0, sm>>>(p, plan.node_grid);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -1360,6 +1455,9 @@ int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, const BatchL
   }
   static_assert(NODE_VW == 4, "the batch node kernels are instantiated for widths 4 and 1");
   bp->inner_smem = ism;
+  bp->relax = (n > 0 && hp[0].alpha != 1.f) ? 1 : 0;
+  for (int i = 0; i < n; ++i)
+    if ((hp[i].alpha != 1.f) != (bp->relax != 0)) return -2;   // one node kernel for every instance
   if (ism > 48 * 1024 &&
       cudaFuncSetAttribute(inner_kernel_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism) != cudaSuccess)
     return -1;
@@ -1384,8 +1482,13 @@ int opfk_batch_enqueue(const Params *d_params, const int *d_sched, const BatchPl
   if (bp.count[BK_DSUM2]) dsum_kernel_b<2><<<bp.count[BK_DSUM2], BLOCK, 0, sm>>>(d_params, at(BK_DSUM2));
   if (bp.count[BK_DSUM1]) dsum_kernel_b<1><<<bp.count[BK_DSUM1], BLOCK, 0, sm>>>(d_params, at(BK_DSUM1));
   if (cudaStreamWaitEvent(sm, (cudaEvent_t)ev_join, 0) != cudaSuccess) return -1;
-  if (bp.count[BK_NODE4]) node_kernel_b<4><<<bp.count[BK_NODE4], BLOCK, 0, sm>>>(d_params, at(BK_NODE4));
-  if (bp.count[BK_NODE1]) node_kernel_b<1><<<bp.count[BK_NODE1], BLOCK, 0, sm>>>(d_params, at(BK_NODE1));
+  if (!bp.relax) {
+    if (bp.count[BK_NODE4]) node_kernel_b<4, false><<<bp.count[BK_NODE4], BLOCK, 0, sm>>>(d_params, at(BK_NODE4));
+    if (bp.count[BK_NODE1]) node_kernel_b<1, false><<<bp.count[BK_NODE1], BLOCK, 0, sm>>>(d_params, at(BK_NODE1));
+  } else {
+    if (bp.count[BK_NODE4]) node_kernel_b<4, true><<<bp.count[BK_NODE4], BLOCK, 0, sm>>>(d_params, at(BK_NODE4));
+    if (bp.count[BK_NODE1]) node_kernel_b<1, true><<<bp.count[BK_NODE1], BLOCK, 0, sm>>>(d_params, at(BK_NODE1));
+  }
   decide_kernel_b<<<bp.count[BK_DECIDE], BLOCK, 0, sm>>>(d_params, at(BK_DECIDE));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -1418,6 +1521,11 @@ int opfk_export_lines_launch(const Params &p, int cur, float *pl, float *a1, flo
                              float *v2, void *stream) {
   export_lines_kernel<<<aux_grid((long long)p.Kp * p.L * p.T), 256, 0, (cudaStream_t)stream>>>(
       p, cur, pl, a1, a2, v1, v2);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int opfk_export_pdev_launch(const Params &p, float *out, void *stream) {
+  export_pdev_kernel<<<aux_grid((long long)p.S * p.T), 256, 0, (cudaStream_t)stream>>>(p, out);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

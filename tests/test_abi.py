@@ -48,7 +48,7 @@ def test_price_scratch_capacity_matches_header():
 
 def test_abi_version_and_status_strings(lib):
     from paper_2410_17203_gb300 import binding as b
-    assert b.opf_abi_version() == 3
+    assert b.opf_abi_version() == 4
     for s in range(7):
         assert b.opf_status_str(s) not in ("", "unknown status")
     assert b.opf_status_str(99) == "unknown status"

@@ -117,3 +117,30 @@ def test_autotune_keeps_iterates_and_the_chosen_layout_is_exact():
         opf_batch_destroy(b)
         for s in batch_solvers + single:
             s.close()
+
+
+def test_over_relaxed_batch_equals_single_and_mixing_is_rejected():
+    from paper_2410_17203_gb300 import (OpfError, Solver, opf_batch_create, opf_batch_destroy,
+                                        opf_batch_iterate)
+    opts = dict(adapt_every=10, eps=0.0, alpha=1.5)
+    batch_solvers = [Solver(c, opts) for c in _cases()]
+    single = [Solver(c, opts) for c in _cases()]
+    b = opf_batch_create([s.h for s in batch_solvers])
+    try:
+        opf_batch_iterate(b, 21)
+        for s in single:
+            s.iterate(21)
+        for sb, ss in zip(batch_solvers, single):
+            a, c = sb.state(), ss.state()
+            for k in a:
+                np.testing.assert_array_equal(a[k], c[k], err_msg=k)
+        plain = Solver(make_case("tiny"), dict(adapt_every=10, eps=0.0))
+        try:
+            with pytest.raises(OpfError):
+                opf_batch_create([batch_solvers[0].h, plain.h])
+        finally:
+            plain.close()
+    finally:
+        opf_batch_destroy(b)
+        for s in batch_solvers + single:
+            s.close()

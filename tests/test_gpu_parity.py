@@ -219,3 +219,78 @@ def test_empty_and_degenerate_shapes():
                 outaged=np.zeros(0, np.int32))
     st, res, info, o = run_both(case, 30, adapt_every=10, eps=0.0)
     compare_states(st, o, keys=["p_dev", "u"])
+
+
+# --------------------------------------------------------------------------
+# over-relaxation (Section 3.6)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["tiny", "mixed_T24", "scalar_T7", "T1_outages", "hvdc_T24"])
+@pytest.mark.parametrize("n", [1, 10, 100])
+def test_over_relaxed_iterates_match_oracle(name, n):
+    """alpha = 1.5: the device keeps relaxed schedules and rebuilds the
+    actual iterate on export; the oracle runs the explicit-copy ADMM."""
+    case = CASES[name]()
+    st, res, info, o = run_both(case, n, adapt_every=0, eps=0.0, rho_theta=5.0, alpha=1.5)
+    compare_states(st, o)
+    scale = max(np.linalg.norm(a) for a in oracle_arrays(o).values())
+    compare_residuals(res, o.res, scale)
+
+
+@pytest.mark.parametrize("name", ["tiny", "mixed_T24"])
+def test_over_relaxed_penalties_match_with_adaptation(name):
+    case = CASES[name]()
+    st, res, info, o = run_both(case, 100, adapt_every=10, eps=0.0, alpha=1.5)
+    assert info["rho_p"] == pytest.approx(o.rho_p, rel=1e-12)
+    assert info["rho_theta"] == pytest.approx(o.rho_th, rel=1e-12)
+    compare_states(st, o)
+
+
+def test_over_relaxed_split_launches_and_solution():
+    """Relaxed state carried across launches; opf_solution's schedules and
+    objective are those of the actual iterate."""
+    from paper_2410_17203_gb300 import Solver
+    case = CASES["mixed_T24"]()
+    opts = dict(adapt_every=10, eps=0.0, alpha=1.5)
+    a, b = Solver(case, opts), Solver(case, opts)
+    try:
+        a.iterate(37)
+        for n in (5, 16, 1, 15):
+            b.iterate(n)
+        sa, sb = a.state(), b.state()
+        for k in sa:
+            np.testing.assert_array_equal(sa[k], sb[k], err_msg=k)
+        o = Oracle(case, OracleOptions(**opts))
+        o.iterate(37, stop=False)
+        sol = a.solution()
+        assert sol["objective"] == pytest.approx(o.objective(), rel=1e-5)
+        assert rel_err(sol["p_dev"], o.dev_p()) <= 1e-5
+    finally:
+        a.close()
+        b.close()
+
+
+def test_over_relaxed_converges_to_the_plain_optimum():
+    from paper_2410_17203_gb300 import Solver
+    case = CASES["tiny"]()
+    base = dict(adapt_every=0, rho_theta=10.0, eps=1e-4)
+    obj = []
+    for alpha in (1.0, 1.5):
+        s = Solver(case, dict(base, alpha=alpha))
+        try:
+            for _ in range(400):
+                s.iterate(100)
+                if s.get_info()["converged"]:
+                    break
+            assert s.get_info()["converged"]
+            obj.append(s.solution()["objective"])
+        finally:
+            s.close()
+    assert obj[1] == pytest.approx(obj[0], rel=1e-3)
+
+
+def test_alpha_out_of_range_is_rejected():
+    from paper_2410_17203_gb300 import OpfError, Solver
+    for alpha in (0.9, 2.0):
+        with pytest.raises(OpfError):
+            Solver(CASES["tiny"](), dict(alpha=alpha))

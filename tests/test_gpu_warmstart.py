@@ -85,3 +85,36 @@ def test_warm_state_from_the_solution_and_learned_start():
     for h, o in zip(hs3, obj[12:]):
         assert opf_solution(h, False, True) == pytest.approx(o, rel=1e-2)
         opf_destroy(h)
+
+
+def test_gpu_solutions_pass_the_oracle_certificate():
+    """The training targets are solutions the GPU path produces; each one is
+    checked here the way the oracle would judge it: the GPU's converged
+    state (with its penalties and inner-ADMM duals) is loaded into the FP64
+    oracle, whose next iteration must still meet the stopping test and keep
+    the objective (a state that only looked converged in FP32 would not)."""
+    from oracle import Oracle, OracleOptions
+    from gridgen import scale_case
+    from paper_2410_17203_gb300 import Solver
+    base = make_case(scale_case(200, 24, 4, seed=31))
+    rng = np.random.default_rng(2)
+    for _ in range(2):
+        case = dict(base)
+        case["load_p"] = base["load_p"] * rng.lognormal(0.0, 0.15, size=base["load_p"].shape)
+        s = Solver(case, dict(adapt_every=10, eps=1e-4))
+        try:
+            for _ in range(300):
+                s.iterate(100)
+                if s.get_info()["converged"]:
+                    break
+            info = s.get_info()
+            assert info["converged"]
+            st = s.state()
+            obj = s.solution()["objective"]
+        finally:
+            s.close()
+        o = Oracle(case, OracleOptions(adapt_every=0, eps=1e-4))
+        o.load_state(st, rho_p=info["rho_p"], rho_theta=info["rho_theta"])
+        o.step()
+        assert o.res[0] <= o.tolerance() and o.res[1] <= o.tolerance(), (o.res[:2], o.tolerance())
+        assert o.objective() == pytest.approx(obj, rel=1e-3)
