@@ -9,8 +9,10 @@
 //
 // Device memory layout (structure of arrays, time innermost so that every row
 // of T floats is one contiguous, 16-byte aligned segment when T % 4 == 0):
-//   lines   P, MID, V1, V2                  2 x [Kp][L][T] float (double buffer)
-//   nodes   U, PBAR, THBAR                  2 x [Kp][N][T] float (double buffer)
+//   lines   P, MID, V1, V2                  2 x [L][Kp][T] float (double buffer)
+//   nodes   U, PBAR, THBAR                  2 x [N][Kp][T] float (double buffer)
+// (line- and node-major: the K+1 contingency rows of one line or node are
+// one contiguous run, so the node sums gather long runs per terminal)
 //   devices PD, DPD                         [S][T]         float
 //   inner ADMM state of ramp generators     lam, beta [n_ramp][4][T],  q [n_ramp][T]
 //   inner ADMM state of batteries           lam, beta [n_stor][9][T+1], q [n_stor][T+1]
@@ -114,6 +116,14 @@ struct Params {
   double eps, mu, gamma, tol;
   int adapt_every, check_every, inner_iters;
 };
+
+// offsets of element (contingency k, line l / node n, step t)
+__host__ __device__ __forceinline__ size_t lidx(const Params &p, int k, int l, int t) {
+  return ((size_t)l * p.Kp + k) * p.T + t;
+}
+__host__ __device__ __forceinline__ size_t nidx(const Params &p, int k, int n, int t) {
+  return ((size_t)n * p.Kp + k) * p.T + t;
+}
 
 // Launch configuration of one iteration's kernels.
 struct IterPlan {

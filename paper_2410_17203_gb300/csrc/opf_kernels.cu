@@ -587,8 +587,8 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
   const int T = p.T, L = p.L, N = p.N;
   const int n1 = p.line_n1[l], n2 = p.line_n2[l];
   const bool act = p.out_line[k] != l;
-  const size_t ol = ((size_t)k * L + l) * T + toff;
-  const size_t o1 = ((size_t)k * N + n1) * T + toff, o2 = ((size_t)k * N + n2) * T + toff;
+  const size_t ol = lidx(p, k, l, toff);
+  const size_t o1 = nidx(p, k, n1, toff), o2 = nidx(p, k, n2, toff);
   // p stays cached: the node sums read its old value again
   FV<VW> P = ldv<VW>(p.P[old] + ol), M = ldv_cs<VW>(p.MID[old] + ol);
   FV<VW> V1 = ldv_cs<VW>(p.V1[old] + ol), V2 = ldv_cs<VW>(p.V2[old] + ol);
@@ -655,7 +655,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
   const int4 r0 = p.nrec[3 * n], r1 = p.nrec[3 * n + 1], r2 = p.nrec[3 * n + 2];
   const float cp = __int_as_float(r0.x), ct = __int_as_float(r0.y);
   const float rcp = __int_as_float(r0.z), rct = __int_as_float(r0.w);
-  const size_t on = ((size_t)k * N + n) * T + toff, os = (size_t)n * T + toff;
+  const size_t on = nidx(p, k, n, toff), os = (size_t)n * T + toff;
   const FV<VW> uo = ldv_cs<VW>(p.U[old] + on), go = ldv_cs<VW>(p.THBAR[old] + on);
   // device terminals first: the sum and the Welford state after them, the
   // same in every contingency
@@ -674,7 +674,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
   for (int e = 0; e < VW; ++e) st.v[e] = 0.f;
   // level 2: the rows of the line terminals, four at a time; a terminal's
   // angle is mid +- p / (2b) (mid +- the stored value on the outaged line)
-  const size_t kb = (size_t)k * L * T + toff;
+  const size_t kb = (size_t)k * T + toff, lrow = (size_t)p.Kp * T;   // line l's row of k: l * lrow + kb
   const int lout = p.out_line[k];
   int4 c4 = r1;
   for (int j = r2.x - 4;;) {
@@ -685,7 +685,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
     for (int q = 0; q < 4; ++q) {
       if (code[q] >= 0) {
         const int l = code[q] >> 1;
-        const size_t ol = kb + (size_t)l * T;
+        const size_t ol = (size_t)l * lrow + kb;
         pn[q] = ldv<VW>(p.P[nw] + ol);
         po[q] = ldv<VW>(p.P[old] + ol);   // kept in L2 for the line's other end
         mq[q] = ldv<VW>(p.MID[nw] + ol);
@@ -797,7 +797,7 @@ __device__ __forceinline__ void xs_body(const Params &p, unsigned bid, unsigned 
   if (q.skip) return;
   const int T = p.T, TV = T / VW, Kp = p.Kp;
   const float kpf = (float)Kp, rkp = __frcp_rn(kpf);
-  const size_t NT = (size_t)p.N * T;
+  const size_t KT = (size_t)Kp * T;    // a node's K+1 rows are contiguous
   const float *Uo = p.U[q.old], *Bo = p.PBAR[q.old];
   const unsigned n_xv = (unsigned)p.n_dnode * (unsigned)TV;
   for (unsigned item = bid * BLOCK + threadIdx.x; item < n_xv; item += nblk * BLOCK) {
@@ -806,14 +806,14 @@ __device__ __forceinline__ void xs_body(const Params &p, unsigned bid, unsigned 
     FV<VW> xs;
     if constexpr (VW == 4) {
       float4 sp, sq;
-      ksum4(Bo, Uo, on, NT, Kp, sp, sq);                  // sum_k pbar, sum_k u at the node
+      ksum4(Bo, Uo, (size_t)p.dnode_ids[ci] * KT + t0, T, Kp, sp, sq);   // sum_k pbar, sum_k u
       xs.v[0] = div_rn(sp.x + q.fsu * sq.x, kpf, rkp);   // avg_k(pbar + u)
       xs.v[1] = div_rn(sp.y + q.fsu * sq.y, kpf, rkp);
       xs.v[2] = div_rn(sp.z + q.fsu * sq.z, kpf, rkp);
       xs.v[3] = div_rn(sp.w + q.fsu * sq.w, kpf, rkp);
     } else {
       float sp, sq;
-      ksum(Bo, Uo, on, NT, Kp, sp, sq);
+      ksum(Bo, Uo, (size_t)p.dnode_ids[ci] * KT + t0, T, Kp, sp, sq);
       xs.v[0] = div_rn(sp + q.fsu * sq, kpf, rkp);
     }
     if (p.dnode_keep[ci]) stv<VW>(p.XS + on, xs);
@@ -904,13 +904,15 @@ __device__ __forceinline__ void line_body(const Params &p, int k0, int k1, unsig
   // each CTA takes LINE_IPT consecutive blocks of BLOCK items, so CTAs are
   // short-lived and the device kernels' CTAs find room beside them
   const unsigned base = bid * (unsigned)(BLOCK * LINE_IPT) + threadIdx.x;
+  // items (line, contingency, step block): a line's K+1 rows are contiguous
+  const int KK = k1 - k0;
   Idx3 ix, dx;
-  ix.set(base, L, TV);
-  dx.set(BLOCK, L, TV);
+  ix.set(base, KK, TV);
+  dx.set(BLOCK, KK, TV);
 #pragma unroll 1
-  for (int j = 0; j < LINE_IPT; ++j, ix.step(dx, L, TV)) {
+  for (int j = 0; j < LINE_IPT; ++j, ix.step(dx, KK, TV)) {
     if (base + (unsigned)(j * BLOCK) < n)
-      line_item<VW>(p, q.old, q.nw, k0 + ix.a, ix.b, ix.c * VW, q.frp, q.frt, q.fsu, q.fsv, q.v_fresh);
+      line_item<VW>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.frp, q.frt, q.fsu, q.fsv, q.v_fresh);
   }
 }
 
@@ -930,11 +932,14 @@ __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int f
   const unsigned stride = nblk * BLOCK;
   unsigned item = bid * BLOCK + threadIdx.x;
   float acc[NSLOT] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  // items (node, contingency, step block): a node's K+1 rows are contiguous,
+  // and so are the K+1 rows of each line it gathers
+  const int KK = k1 - k0;
   Idx3 ix, dx;
-  ix.set(item, N, TV);
-  dx.set(stride, N, TV);
-  for (; item < n; item += stride, ix.step(dx, N, TV))
-    node_item<VW, RELAX>(p, q.old, q.nw, k0 + ix.a, ix.b, ix.c * VW, q.fsu, acc);
+  ix.set(item, KK, TV);
+  dx.set(stride, KK, TV);
+  for (; item < n; item += stride, ix.step(dx, KK, TV))
+    node_item<VW, RELAX>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.fsu, acc);
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     float v = acc[s];
@@ -1149,21 +1154,21 @@ __global__ void import_kernel(Params p, int cur, const float *pl, const float *a
       const int k = (int)(i / ((long long)L * T));
       const long long rem = i - (long long)k * L * T;
       const int l = (int)(rem / T), t = (int)(rem % T);
-      const size_t src = ((size_t)k * L + p.line_perm[l]) * T + t;
+      const size_t src = ((size_t)k * L + p.line_perm[l]) * T + t, dst = lidx(p, k, l, t);
       // stored as p and the mean angle; the outaged line keeps its half
       // angle difference in p's place (its p is 0)
       const float x1 = a1 ? a1[src] : 0.f, x2 = a2 ? a2[src] : 0.f;
       const bool act = p.out_line[k] != l;
-      p.P[cur][i] = act ? (pl ? pl[src] : 0.f) : 0.5f * (x1 - x2);
-      p.MID[cur][i] = 0.5f * (x1 + x2);
-      p.V1[cur][i] = v1 ? v1[src] : 0.f;
-      p.V2[cur][i] = v2 ? v2[src] : 0.f;
+      p.P[cur][dst] = act ? (pl ? pl[src] : 0.f) : 0.5f * (x1 - x2);
+      p.MID[cur][dst] = 0.5f * (x1 + x2);
+      p.V1[cur][dst] = v1 ? v1[src] : 0.f;
+      p.V2[cur][dst] = v2 ? v2[src] : 0.f;
     } else {
       const long long j = i - nl;
       const int k = (int)(j / ((long long)N * T));
       const long long rem = j - (long long)k * N * T;
       const int n = (int)(rem / T), t = (int)(rem % T);
-      p.U[cur][j] = u ? u[((size_t)k * N + p.node_perm[n]) * T + t] : 0.f;
+      p.U[cur][nidx(p, k, n, t)] = u ? u[((size_t)k * N + p.node_perm[n]) * T + t] : 0.f;
     }
   }
 }
@@ -1180,13 +1185,13 @@ __global__ void node_average_kernel(Params p, int cur) {
       float sp = devsum, st = 0.f;
       for (int j = p.lcsr_ptr[n]; j < p.lcsr_ptr[n + 1]; ++j) {
         const int code = p.lcsr[j].x;
-        const size_t ol = ((size_t)k * L + (code >> 1)) * T + t;
+        const size_t ol = lidx(p, k, code >> 1, t);
         float p2, th1, th2;
         line_terminals(p, cur, k, code >> 1, ol, p2, th1, th2);
         sp += (code & 1) ? p2 : -p2;
         st += (code & 1) ? th2 : th1;
       }
-      const size_t on = ((size_t)k * N + n) * T + t;
+      const size_t on = nidx(p, k, n, t);
       const float pb = sp / p.cnt_p[n];
       p.PBAR[cur][on] = pb;
       p.THBAR[cur][on] = p.cnt_th[n] > 0.f ? st / p.cnt_th[n] : 0.f;
@@ -1207,13 +1212,13 @@ __global__ void project_v_kernel(Params p, int cur) {
     float s = 0.f;
     for (int j = l0; j < l1; ++j) {
       const int code = p.lcsr[j].x;
-      const size_t ol = ((size_t)k * L + (code >> 1)) * T + t;
+      const size_t ol = lidx(p, k, code >> 1, t);
       s += (code & 1) ? p.V2[cur][ol] : p.V1[cur][ol];
     }
     const float m = s / p.cnt_th[n];
     for (int j = l0; j < l1; ++j) {
       const int code = p.lcsr[j].x;
-      const size_t ol = ((size_t)k * L + (code >> 1)) * T + t;
+      const size_t ol = lidx(p, k, code >> 1, t);
       if (code & 1) p.V2[cur][ol] -= m; else p.V1[cur][ol] -= m;
     }
   }
@@ -1230,14 +1235,14 @@ __global__ void export_lines_kernel(Params p, int cur, float *pl, float *a1, flo
     const int k = (int)(i / ((long long)L * T));
     const long long rem = i - (long long)k * L * T;
     const int l = (int)(rem / T), t = (int)(rem % T);
-    const size_t dst = ((size_t)k * L + p.line_perm[l]) * T + t;
+    const size_t dst = ((size_t)k * L + p.line_perm[l]) * T + t, li = lidx(p, k, l, t);
     float p2, th1, th2;
-    line_terminals(p, cur, k, l, (size_t)i, p2, th1, th2);
+    line_terminals(p, cur, k, l, li, p2, th1, th2);
     if (v1 || v2) {
-      float x = p.V1[cur][i], y = p.V2[cur][i];
+      float x = p.V1[cur][li], y = p.V2[cur][li];
       if (!sc.v_fresh) {
-        x += th1 - p.THBAR[cur][((size_t)k * N + p.line_n1[l]) * T + t];
-        y += th2 - p.THBAR[cur][((size_t)k * N + p.line_n2[l]) * T + t];
+        x += th1 - p.THBAR[cur][nidx(p, k, p.line_n1[l], t)];
+        y += th2 - p.THBAR[cur][nidx(p, k, p.line_n2[l], t)];
       }
       if (v1) v1[dst] = sv * x;
       if (v2) v2[dst] = sv * y;
@@ -1245,7 +1250,7 @@ __global__ void export_lines_kernel(Params p, int cur, float *pl, float *a1, flo
     if (p.alpha != 1.f && !sc.v_fresh) {
       // over-relaxed: the buffers hold P = alpha p + (1 - alpha) P_prev
       float q2, q1a, q2a;
-      line_terminals(p, cur ^ 1, k, l, (size_t)i, q2, q1a, q2a);
+      line_terminals(p, cur ^ 1, k, l, li, q2, q1a, q2a);
       p2 = actual(p.alpha, p2, q2);
       th1 = actual(p.alpha, th1, q1a);
       th2 = actual(p.alpha, th2, q2a);
@@ -1267,7 +1272,7 @@ __global__ void export_nodes_kernel(Params p, int cur, float *u, float *theta, f
     const size_t ext = (size_t)p.node_perm[n] * T + t;
     double s = 0.0;
     for (int k = 0; k < p.Kp; ++k) {
-      const size_t o = (size_t)k * N * T + i;
+      const size_t o = nidx(p, k, n, t);
       const float uu = p.U[cur][o];
       if (u) u[(size_t)k * N * T + ext] = (float)(sc.su * uu);
       if (theta)
