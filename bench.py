@@ -623,7 +623,7 @@ def ours_arm(args):
                                    "profiles/iteration_10k.txt)"},
             "variable_updates_per_s": value * variables_per_iter(d),
             "e2e": e2e,
-            "gpu_launches": kernels_per_iter * args.steps,
+            "gpu_launches": kernels_per_iter * args.steps + 1,   # + the call's begin kernel
             "clocks": ck,
             "residuals": [float(x) for x in res],
             "rho": [info["rho_p"], info["rho_theta"]],

@@ -796,7 +796,7 @@ opf_status opf_iterate(opf_ctx *c, int32_t n_iters, double rho) {
   CK(cudaStreamWaitEvent(c->s_main, c->ev_in, 0));
   if (rho > 0 && opfk_set_rho_launch(c->P.sc, rho, c->s_main) != 0) return fail(OPF_ECUDA, "set_rho launch failed");
   if (n_iters > 0) {
-    CK(cudaMemsetAsync(&c->P.sc->stop, 0, sizeof(int), c->s_main));
+    if (opfk_begin_launch(c->P.sc, n_iters, 1, c->s_main) != 0) return fail(OPF_ECUDA, "begin launch failed");
     for (int i = 0; i < n_iters / kGraphIters; ++i) CK(cudaGraphLaunch(c->g_many, c->s_main));
     for (int i = 0; i < n_iters % kGraphIters; ++i) CK(cudaGraphLaunch(c->g_one, c->s_main));
   }
@@ -1129,6 +1129,8 @@ opf_status opf_batch_iterate(opf_batch *b, int32_t n_iters) {
     CK(cudaEventRecord(c->ev_in, c->stream));
     CK(cudaStreamWaitEvent(b->stream, c->ev_in, 0));
   }
+  if (opfk_begin_batch_launch(b->d_params, (int)b->ctx.size(), n_iters, b->stream) != 0)
+    return fail(OPF_ECUDA, "begin launch failed");
   cudaError_t le = cudaSuccess;
   launch_batch_steps(b, n_iters, &le);
   if (le != cudaSuccess) return cuda_fail(le, "cudaGraphLaunch(batch)");

@@ -48,6 +48,8 @@ struct DevScalars {
   int v_fresh;           // 1: V1/V2 already hold the current v (after import / reset)
   int stop;              // set by the decision kernel (passed stopping test, error);
                          // cleared at the start of every opf_iterate call
+  long long it_last;     // the last iteration of the current call: residuals are formed
+                         // there and at stopping-test and adaptation iterations only
 };
 
 // Battery group offsets inside lam/beta rows of stride Tp = T + 1.
@@ -161,6 +163,10 @@ extern "C++" {
 int opf_record_error(int s, const char *msg);
 // Grids of the iteration kernels for this problem on the current device.
 int opfk_plan(const opfk::Params &p, opfk::IterPlan *plan);
+// Start a call of n iterations: the residuals are formed at its last one;
+// clear_stop restarts a context that stopped (opf_iterate, not batches).
+int opfk_begin_launch(opfk::DevScalars *sc, long long n, int clear_stop, void *stream);
+int opfk_begin_batch_launch(const opfk::Params *d_params, int n_inst, long long n, void *stream);
 // Enqueue one iteration: xs, inner, dsum, the node kernels and decide on
 // main_stream, the line kernels on aux_stream (forked after the previous
 // iteration; each slab joined before its node kernel).  Works under stream

@@ -647,23 +647,29 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
 // terminal codes come four at a time so that a node's row loads issue
 // together.
 // ---------------------------------------------------------------------------
+// res = 0: the iteration's residuals are not read, so the node sums skip the
+// inputs only they need (old p and theta_bar rows, the device Welford state)
+// and their accumulation; the relaxed variant always needs the mean change.
 template <int VW, bool RELAX>
 __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int k, int n, int toff, float fsu,
-                                          float *acc) {
-  const int T = p.T, L = p.L, N = p.N;
+                                          float *acc, bool res) {
+  const int T = p.T;
+  if constexpr (RELAX) res = true;
   // level 1: the node record, the node's old rows and its device sums
   const int4 r0 = p.nrec[3 * n], r1 = p.nrec[3 * n + 1], r2 = p.nrec[3 * n + 2];
   const float cp = __int_as_float(r0.x), ct = __int_as_float(r0.y);
   const float rcp = __int_as_float(r0.z), rct = __int_as_float(r0.w);
   const size_t on = nidx(p, k, n, toff), os = (size_t)n * T + toff;
-  const FV<VW> uo = ldv_cs<VW>(p.U[old] + on), go = ldv_cs<VW>(p.THBAR[old] + on);
+  const FV<VW> uo = ldv_cs<VW>(p.U[old] + on);
+  FV<VW> go;
+  if (res) go = ldv_cs<VW>(p.THBAR[old] + on);
   // device terminals first: the sum and the Welford state after them, the
   // same in every contingency
   FV<VW> sp = ldv<VW>(p.DSP + os), st;
   Welf<VW> wdp, wth;
   Welf2<VW> wrx;   // RELAX: (Theta_new, Theta_new - Theta_old) over the line terminals
   if constexpr (RELAX) wrx.reset();
-  {
+  if (res) {
     const FV<VW> m = ldv<VW>(p.DSM + os), q = ldv<VW>(p.DSQ + os);
     wdp.n = (float)r2.z;
 #pragma unroll
@@ -687,7 +693,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
         const int l = code[q] >> 1;
         const size_t ol = (size_t)l * lrow + kb;
         pn[q] = ldv<VW>(p.P[nw] + ol);
-        po[q] = ldv<VW>(p.P[old] + ol);   // kept in L2 for the line's other end
+        if (res) po[q] = ldv<VW>(p.P[old] + ol);   // kept in L2 for the line's other end
         mq[q] = ldv<VW>(p.MID[nw] + ol);
         if constexpr (RELAX) mo[q] = ldv<VW>(p.MID[old] + ol);
         bq[q] = p.line_b[l];
@@ -701,7 +707,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
         float dpo[VW], th[VW], dth[VW];
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
-          const float pv = act ? pn[q].v[e] : 0.f, pov = act ? po[q].v[e] : 0.f;
+          const float pv = act ? pn[q].v[e] : 0.f, pov = (act && res) ? po[q].v[e] : 0.f;
           const float h = act ? div_rn(pn[q].v[e], tb, rtb) : pn[q].v[e];
           th[e] = t2 ? mq[q].v[e] - h : mq[q].v[e] + h;
           sp.v[e] += t2 ? pv : -pv;
@@ -712,9 +718,11 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
             dth[e] = th[e] - (t2 ? mo[q].v[e] - ho : mo[q].v[e] + ho);
           }
         }
-        wdp.add(dpo);
-        if constexpr (RELAX) wrx.add(th, dth);
-        else wth.add(th);
+        if (res) {
+          wdp.add(dpo);
+          if constexpr (RELAX) wrx.add(th, dth);
+          else wth.add(th);
+        }
       }
     }
     j += 4;
@@ -726,6 +734,11 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
   for (int e = 0; e < VW; ++e) {
     pb.v[e] = div_rn(sp.v[e], cp, rcp);                      // Eq. (average-op)
     tbar.v[e] = ct > 0.f ? div_rn(st.v[e], ct, rct) : 0.f;
+    if (!res) {
+      un.v[e] = fsu * uo.v[e] + pb.v[e];                     // u += pbar
+      if (!isfinite(un.v[e]) || !isfinite(tbar.v[e])) acc[SL_NF] += 1.f;
+      continue;
+    }
     const float dt = tbar.v[e] - go.v[e];
     if constexpr (RELAX) {
       // stored values are relaxed: pb = Q = avg_n P, tbar = xi.  The actual
@@ -764,6 +777,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
 struct Iter {
   float frp, frt, fsu, fsv, rho_dev;
   int old, nw, v_fresh, skip;
+  int res;   // this iteration's residuals are read (stopping test, adaptation, end of the call)
 };
 
 __device__ __forceinline__ Iter iter_scalars(const Params &p) {
@@ -780,6 +794,9 @@ __device__ __forceinline__ Iter iter_scalars(const Params &p) {
     r.nw = r.old ^ 1;
     r.v_fresh = sc.v_fresh;
     r.skip = (sc.status != 0 || sc.stop != 0) ? 1 : 0;
+    const long long itn = sc.it + 1;
+    r.res = (p.adapt_every > 0 && itn % p.adapt_every == 0) ||
+            (p.eps > 0 && p.check_every > 0 && itn % p.check_every == 0) || itn >= sc.it_last;
     s = r;
   }
   __syncthreads();
@@ -939,7 +956,7 @@ __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int f
   ix.set(item, KK, TV);
   dx.set(stride, KK, TV);
   for (; item < n; item += stride, ix.step(dx, KK, TV))
-    node_item<VW, RELAX>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.fsu, acc);
+    node_item<VW, RELAX>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.fsu, acc, q.res != 0);
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     float v = acc[s];
@@ -991,6 +1008,19 @@ __device__ __forceinline__ void decide_body(const Params &p, int n_part) {
   }
   DevScalars sc = *p.sc;
   const long long itn = sc.it + 1;
+  if (!q.res) {
+    // no residuals this iteration (only the non-finite count is formed)
+    if (tot[SL_NF] != 0.0) {
+      sc.status = ST_NONFINITE;
+      sc.stop = 1;
+    }
+    sc.su = 1.0;
+    sc.sv = 1.0;
+    sc.it = itn;
+    sc.v_fresh = 0;
+    *p.sc = sc;
+    return;
+  }
   const bool adapt_now = p.adapt_every > 0 && (itn % p.adapt_every) == 0;
   const bool check_now = p.eps > 0 && p.check_every > 0 && (itn % p.check_every) == 0;
   const double rho_p = sc.rho_p, rho_th = sc.rho_th;
@@ -1295,6 +1325,16 @@ __global__ void export_pdev_kernel(Params p, float *out) {
     out[i] = rx ? fmaf(c, p.DPD[i], p.PD[i]) : p.PD[i];
 }
 
+__global__ void begin_kernel(DevScalars *sc, long long n, int clear_stop) {
+  if (clear_stop) sc->stop = 0;
+  sc->it_last = sc->it + n;
+}
+
+__global__ void begin_batch_kernel(const Params *ps, int n_inst, long long n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_inst) ps[i].sc->it_last = ps[i].sc->it + n;
+}
+
 __global__ void set_rho_kernel(DevScalars *sc, double rho) {
   DevScalars s = *sc;
   s.su *= s.rho_p / rho;
@@ -1526,6 +1566,16 @@ int opfk_export_lines_launch(const Params &p, int cur, float *pl, float *a1, flo
                              float *v2, void *stream) {
   export_lines_kernel<<<aux_grid((long long)p.Kp * p.L * p.T), 256, 0, (cudaStream_t)stream>>>(
       p, cur, pl, a1, a2, v1, v2);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int opfk_begin_launch(DevScalars *sc, long long n, int clear_stop, void *stream) {
+  begin_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(sc, n, clear_stop);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int opfk_begin_batch_launch(const Params *d_params, int n_inst, long long n, void *stream) {
+  begin_batch_kernel<<<(n_inst + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_params, n_inst, n);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
