@@ -275,7 +275,7 @@ void carve(opf_ctx *c, Arena &a) {
     p.V1[b] = a.take<float>(KLT);
     p.V2[b] = a.take<float>(KLT);
     p.U[b] = a.take<float>(KNT);
-    p.PBAR[b] = a.take<float>(KNT);
+    p.PU[b] = a.take<float>(KNT);
     p.THBAR[b] = a.take<float>(KNT);
   }
   p.PD = a.take<float>(ST);

@@ -10,7 +10,7 @@
 // Device memory layout (structure of arrays, time innermost so that every row
 // of T floats is one contiguous, 16-byte aligned segment when T % 4 == 0):
 //   lines   P, MID, V1, V2                  2 x [L][Kp][T] float (double buffer)
-//   nodes   U, PBAR, THBAR                  2 x [N][Kp][T] float (double buffer)
+//   nodes   U, PU = pbar + u, THBAR         2 x [N][Kp][T] float (double buffer)
 // (line- and node-major: the K+1 contingency rows of one line or node are
 // one contiguous run, so the node sums gather long runs per terminal)
 //   devices PD, DPD                         [S][T]         float
@@ -72,7 +72,7 @@ struct Params {
   // angle difference in p's place), and the phase duals
   float *P[2], *MID[2], *V1[2], *V2[2];
   // nodes (internal numbering), double-buffered
-  float *U[2], *PBAR[2], *THBAR[2];
+  float *U[2], *PU[2], *THBAR[2];   // PU = pbar + u (unscaled): what the proxes read
   // incident lines of each node: x = 2*l + end (end 1: the node is terminal 2), y = other node
   const int *lcsr_ptr;
   const int2 *lcsr;

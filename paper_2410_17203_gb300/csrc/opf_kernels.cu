@@ -134,8 +134,9 @@ __device__ void warp_tri_solve(const float *__restrict__ q, float off, float *bu
   __syncwarp();
 }
 
-// sum over contingencies k of pbar and u at one (node, t) offset o, with 8
-// independent loads in flight per step
+// sums over contingencies k of two node arrays (pbar + u and u; u_o may be
+// NULL, giving 0) at one (node, t) offset o, with 8 independent loads in
+// flight per step
 __device__ __forceinline__ void ksum(const float *pbar_o, const float *u_o, size_t o, size_t stride, int Kp,
                                      float &sp, float &sq) {
   float a[8], b[8];
@@ -146,12 +147,12 @@ __device__ __forceinline__ void ksum(const float *pbar_o, const float *u_o, size
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       a[j] += pbar_o[(size_t)(k + j) * stride + o];
-      b[j] += u_o[(size_t)(k + j) * stride + o];
+      b[j] += u_o ? u_o[(size_t)(k + j) * stride + o] : 0.f;
     }
   }
   for (; k < Kp; ++k) {
     a[0] += pbar_o[(size_t)k * stride + o];
-    b[0] += u_o[(size_t)k * stride + o];
+    b[0] += u_o ? u_o[(size_t)k * stride + o] : 0.f;
   }
   sp = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   sq = ((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + (b[6] + b[7]));
@@ -163,11 +164,12 @@ __device__ __forceinline__ void ksum4(const float *pbar_o, const float *u_o, siz
                                       float4 &sp, float4 &sq) {
   float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
   int k = 0;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
   for (; k + 2 <= Kp; k += 2) {
     const float4 x0 = *reinterpret_cast<const float4 *>(pbar_o + (size_t)k * stride + o);
     const float4 x1 = *reinterpret_cast<const float4 *>(pbar_o + (size_t)(k + 1) * stride + o);
-    const float4 y0 = *reinterpret_cast<const float4 *>(u_o + (size_t)k * stride + o);
-    const float4 y1 = *reinterpret_cast<const float4 *>(u_o + (size_t)(k + 1) * stride + o);
+    const float4 y0 = u_o ? *reinterpret_cast<const float4 *>(u_o + (size_t)k * stride + o) : z;
+    const float4 y1 = u_o ? *reinterpret_cast<const float4 *>(u_o + (size_t)(k + 1) * stride + o) : z;
     a0.x += x0.x; a0.y += x0.y; a0.z += x0.z; a0.w += x0.w;
     a1.x += x1.x; a1.y += x1.y; a1.z += x1.z; a1.w += x1.w;
     b0.x += y0.x; b0.y += y0.y; b0.z += y0.z; b0.w += y0.w;
@@ -175,7 +177,7 @@ __device__ __forceinline__ void ksum4(const float *pbar_o, const float *u_o, siz
   }
   if (k < Kp) {
     const float4 x = *reinterpret_cast<const float4 *>(pbar_o + (size_t)k * stride + o);
-    const float4 y = *reinterpret_cast<const float4 *>(u_o + (size_t)k * stride + o);
+    const float4 y = u_o ? *reinterpret_cast<const float4 *>(u_o + (size_t)k * stride + o) : z;
     a0.x += x.x; a0.y += x.y; a0.z += x.z; a0.w += x.w;
     b0.x += y.x; b0.y += y.y; b0.z += y.z; b0.w += y.w;
   }
@@ -592,8 +594,15 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
   // p stays cached: the node sums read its old value again
   FV<VW> P = ldv<VW>(p.P[old] + ol), M = ldv_cs<VW>(p.MID[old] + ol);
   FV<VW> V1 = ldv_cs<VW>(p.V1[old] + ol), V2 = ldv_cs<VW>(p.V2[old] + ol);
-  const FV<VW> U1 = ldv<VW>(p.U[old] + o1), U2 = ldv<VW>(p.U[old] + o2);
-  const FV<VW> B1 = ldv<VW>(p.PBAR[old] + o1), B2 = ldv<VW>(p.PBAR[old] + o2);
+  // pbar + s u at both ends from PU = pbar + u; u itself only while a
+  // penalty rescale s != 1 is pending (an adaptation iteration)
+  const FV<VW> B1 = ldv<VW>(p.PU[old] + o1), B2 = ldv<VW>(p.PU[old] + o2);
+  FV<VW> U1, U2;
+  const bool rescale = fsu != 1.f;
+  if (rescale) {
+    U1 = ldv<VW>(p.U[old] + o1);
+    U2 = ldv<VW>(p.U[old] + o2);
+  }
   const FV<VW> G1 = ldv<VW>(p.THBAR[old] + o1), G2 = ldv<VW>(p.THBAR[old] + o2);
   float tb = 1.f, den = 1.f, ulim = 0.f;
   if (act) {
@@ -611,8 +620,10 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
     const float po = act ? P.v[e] : 0.f;
     const float ho = act ? div_rn(P.v[e], tb, rtb) : P.v[e];
     const float a1 = M.v[e] + ho, a2 = M.v[e] - ho;
-    const float x1 = -po - B1.v[e] - fsu * U1.v[e];         // p~ - u at terminal 1 (z - u relaxed)
-    const float x2 = po - B2.v[e] - fsu * U2.v[e];          // p~ - u at terminal 2
+    const float w1 = rescale ? fmaf(fsu - 1.f, U1.v[e], B1.v[e]) : B1.v[e];   // pbar + s u
+    const float w2 = rescale ? fmaf(fsu - 1.f, U2.v[e], B2.v[e]) : B2.v[e];
+    const float x1 = -po - w1;                              // p~ - u at terminal 1 (z - u relaxed)
+    const float x2 = po - w2;                               // p~ - u at terminal 2
     const float r1 = a1 - G1.v[e], r2 = a2 - G2.v[e];       // theta - theta_bar (Theta - xi relaxed)
     const float v1 = v_fresh ? fsv * V1.v[e] : fsv * (V1.v[e] + r1);
     const float v2 = v_fresh ? fsv * V2.v[e] : fsv * (V2.v[e] + r2);
@@ -762,7 +773,10 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
   }
   // the new node rows are read in the next iteration only
   stv_cs<VW>(p.U[nw] + on, un);
-  stv_cs<VW>(p.PBAR[nw] + on, pb);
+  FV<VW> pu;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) pu.v[e] = pb.v[e] + un.v[e];
+  stv_cs<VW>(p.PU[nw] + on, pu);
   stv_cs<VW>(p.THBAR[nw] + on, tbar);
 }
 
@@ -815,23 +829,27 @@ __device__ __forceinline__ void xs_body(const Params &p, unsigned bid, unsigned 
   const int T = p.T, TV = T / VW, Kp = p.Kp;
   const float kpf = (float)Kp, rkp = __frcp_rn(kpf);
   const size_t KT = (size_t)Kp * T;    // a node's K+1 rows are contiguous
-  const float *Uo = p.U[q.old], *Bo = p.PBAR[q.old];
+  // avg_k(pbar + s u) = (sum_k PU + (s - 1) sum_k u) / (K+1); u is read only
+  // while a penalty rescale s != 1 is pending
+  const float *Uo = p.U[q.old], *Wo = p.PU[q.old];
+  const bool rescale = q.fsu != 1.f;
+  const float sm1 = q.fsu - 1.f;
   const unsigned n_xv = (unsigned)p.n_dnode * (unsigned)TV;
   for (unsigned item = bid * BLOCK + threadIdx.x; item < n_xv; item += nblk * BLOCK) {
     const int ci = (int)(item / (unsigned)TV), t0 = (int)(item % (unsigned)TV) * VW;
-    const size_t on = (size_t)p.dnode_ids[ci] * T + t0;
+    const size_t on = (size_t)p.dnode_ids[ci] * T + t0, ok = (size_t)p.dnode_ids[ci] * KT + t0;
     FV<VW> xs;
     if constexpr (VW == 4) {
       float4 sp, sq;
-      ksum4(Bo, Uo, (size_t)p.dnode_ids[ci] * KT + t0, T, Kp, sp, sq);   // sum_k pbar, sum_k u
-      xs.v[0] = div_rn(sp.x + q.fsu * sq.x, kpf, rkp);   // avg_k(pbar + u)
-      xs.v[1] = div_rn(sp.y + q.fsu * sq.y, kpf, rkp);
-      xs.v[2] = div_rn(sp.z + q.fsu * sq.z, kpf, rkp);
-      xs.v[3] = div_rn(sp.w + q.fsu * sq.w, kpf, rkp);
+      ksum4(Wo, rescale ? Uo : nullptr, ok, T, Kp, sp, sq);   // sum_k PU, sum_k u
+      xs.v[0] = div_rn(fmaf(sm1, sq.x, sp.x), kpf, rkp);
+      xs.v[1] = div_rn(fmaf(sm1, sq.y, sp.y), kpf, rkp);
+      xs.v[2] = div_rn(fmaf(sm1, sq.z, sp.z), kpf, rkp);
+      xs.v[3] = div_rn(fmaf(sm1, sq.w, sp.w), kpf, rkp);
     } else {
       float sp, sq;
-      ksum(Bo, Uo, (size_t)p.dnode_ids[ci] * KT + t0, T, Kp, sp, sq);
-      xs.v[0] = div_rn(sp + q.fsu * sq, kpf, rkp);
+      ksum(Wo, rescale ? Uo : nullptr, ok, T, Kp, sp, sq);
+      xs.v[0] = div_rn(fmaf(sm1, sq, sp), kpf, rkp);
     }
     if (p.dnode_keep[ci]) stv<VW>(p.XS + on, xs);
     for (int j = p.dnode_ptr[ci]; j < p.dnode_ptr[ci + 1]; ++j) {
@@ -1223,7 +1241,7 @@ __global__ void node_average_kernel(Params p, int cur) {
       }
       const size_t on = nidx(p, k, n, t);
       const float pb = sp / p.cnt_p[n];
-      p.PBAR[cur][on] = pb;
+      p.PU[cur][on] = pb + p.U[cur][on];   // u was imported before
       p.THBAR[cur][on] = p.cnt_th[n] > 0.f ? st / p.cnt_th[n] : 0.f;
     }
   }
