@@ -747,7 +747,6 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
     tbar.v[e] = ct > 0.f ? div_rn(st.v[e], ct, rct) : 0.f;
     if (!res) {
       un.v[e] = fsu * uo.v[e] + pb.v[e];                     // u += pbar
-      if (!isfinite(un.v[e]) || !isfinite(tbar.v[e])) acc[SL_NF] += 1.f;
       continue;
     }
     const float dt = tbar.v[e] - go.v[e];
@@ -975,6 +974,7 @@ __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int f
   dx.set(stride, KK, TV);
   for (; item < n; item += stride, ix.step(dx, KK, TV))
     node_item<VW, RELAX>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.fsu, acc, q.res != 0);
+  if (!q.res) return;   // nothing reads this iteration's partial sums
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     float v = acc[s];
@@ -1001,6 +1001,19 @@ __device__ __forceinline__ void decide_body(const Params &p, int n_part) {
   __shared__ double red[WARPS][NSLOT];
   const Iter q = iter_scalars(p);
   if (q.skip) return;
+  if (!q.res) {
+    // nothing reads this iteration's residuals (a non-finite value is caught
+    // at the next iteration that forms them): advance
+    if (threadIdx.x == 0) {
+      DevScalars sc = *p.sc;
+      sc.su = 1.0;
+      sc.sv = 1.0;
+      sc.it = sc.it + 1;
+      sc.v_fresh = 0;
+      *p.sc = sc;
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double tot[NSLOT];
 #pragma unroll
@@ -1026,19 +1039,6 @@ __device__ __forceinline__ void decide_body(const Params &p, int n_part) {
   }
   DevScalars sc = *p.sc;
   const long long itn = sc.it + 1;
-  if (!q.res) {
-    // no residuals this iteration (only the non-finite count is formed)
-    if (tot[SL_NF] != 0.0) {
-      sc.status = ST_NONFINITE;
-      sc.stop = 1;
-    }
-    sc.su = 1.0;
-    sc.sv = 1.0;
-    sc.it = itn;
-    sc.v_fresh = 0;
-    *p.sc = sc;
-    return;
-  }
   const bool adapt_now = p.adapt_every > 0 && (itn % p.adapt_every) == 0;
   const bool check_now = p.eps > 0 && p.check_every > 0 && (itn % p.check_every) == 0;
   const double rho_p = sc.rho_p, rho_th = sc.rho_th;

@@ -201,7 +201,10 @@ def test_nonfinite_state_is_reported():
     s.iterate(5)
     _, status = opf_residuals(s.h, raise_on_status=False)
     assert status == 5                               # OPF_ENONFINITE
-    assert s.get_info()["iterations"] == 1
+    # found at the first iteration that forms residuals: here the call's last
+    assert s.get_info()["iterations"] == 5
+    s.iterate(5)                                     # a stopped context stays stopped
+    assert s.get_info()["iterations"] == 5
 
 
 def test_empty_and_degenerate_shapes():
