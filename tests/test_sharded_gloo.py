@@ -17,8 +17,8 @@ import pytest
 from gridgen import make_case, scale_case
 
 
-def _case():
-    return make_case(scale_case(60, 6, 5, seed=31))
+def _case(hvdc=False):
+    return make_case(scale_case(60, 6, 5, seed=31, n_hvdc=3 if hvdc else 0))
 
 
 def _free_port():
@@ -27,7 +27,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, out_dir, n_iter):
+def _rank_main(rank, world, port, out_dir, n_iter, alpha=1.0, hvdc=False):
     import torch
     import torch.distributed as dist
     from oracle import Oracle, OracleOptions, Shard
@@ -35,7 +35,7 @@ def _rank_main(rank, world, port, out_dir, n_iter):
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
                             world_size=world)
     try:
-        case = _case()
+        case = _case(hvdc)
         K = len(case["outaged"])
         k_ids = np.array_split(np.arange(K + 1), world)[rank]
 
@@ -44,7 +44,7 @@ def _rank_main(rank, world, port, out_dir, n_iter):
             dist.all_reduce(t)
             return t.numpy()
 
-        o = Oracle(case, OracleOptions(adapt_every=10, eps=0.0), shard=Shard(k_ids, K, allreduce))
+        o = Oracle(case, OracleOptions(adapt_every=10, eps=0.0, alpha=alpha), shard=Shard(k_ids, K, allreduce))
         res = []
         for _ in range(n_iter):
             o.step()
@@ -56,17 +56,20 @@ def _rank_main(rank, world, port, out_dir, n_iter):
         dist.destroy_process_group()
 
 
-def test_two_rank_contingency_shards_reproduce_the_iteration(tmp_path):
+@pytest.mark.parametrize("alpha, hvdc", [(1.0, False), (1.5, True)])
+def test_two_rank_contingency_shards_reproduce_the_iteration(tmp_path, alpha, hvdc):
+    """Plain message passing, and the over-relaxed iteration (Section 3.6) on
+    a grid with HVDC links (two-terminal devices shared by all contingencies)."""
     import torch.multiprocessing as mp
     from oracle import Oracle, OracleOptions
 
     n_iter = 30
     port = _free_port()
-    mp.start_processes(_rank_main, args=(2, port, str(tmp_path), n_iter), nprocs=2, join=True,
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path), n_iter, alpha, hvdc), nprocs=2, join=True,
                        start_method="spawn")
     parts = [np.load(tmp_path / f"rank{r}.npz") for r in range(2)]
 
-    ref = Oracle(_case(), OracleOptions(adapt_every=10, eps=0.0))
+    ref = Oracle(_case(hvdc), OracleOptions(adapt_every=10, eps=0.0, alpha=alpha))
     res = []
     for _ in range(n_iter):
         ref.step()
