@@ -830,7 +830,8 @@ opf_status opf_get_info(opf_ctx *c, opf_info *info) {
   {
     const opfk::IterPlan &pl = c->plan;
     info->kernels_per_iteration = (pl.xs_grid > 0) + (pl.inner_grid > 0) + 1 +
-                                  pl.n_slabs * ((pl.line_grid > 0 && c->L > 0) + 1) + 1;
+                                  pl.n_slabs * ((pl.line_grid > 0 && c->L > 0) + 1 +
+                                                (pl.lean_grid > 0 && c->opt.alpha == 1.0)) + 1;
   }
   info->N = c->N;
   info->L = c->L;

@@ -130,6 +130,7 @@ __host__ __device__ __forceinline__ size_t nidx(const Params &p, int k, int n, i
 // Launch configuration of one iteration's kernels.
 struct IterPlan {
   int line_grid, node_grid, xs_grid, inner_grid, dsum_grid;  // 0: the kernel has no work
+  int lean_grid;   // residual-free node pass (T % 4 == 0 and plain ADMM only)
   int n_slabs, slab_k;  // contingency slabs of the line / node kernels, slab_k contingencies each
   size_t inner_smem;
 };

@@ -46,7 +46,8 @@ constexpr int ST_NONFINITE = 5;  // opf_status value set on the device
 constexpr int NODE_VW = 4;       // time steps per node item
 constexpr int NODE_MIN_CTAS = 2; // resident CTAs per SM the node kernel is compiled for
 constexpr int LINE_IPT = 4;      // line items per thread (CTA-sized blocks of items)
-constexpr int N_SLABS = 1;       // contingency slabs per iteration (line / node overlap)
+constexpr int N_SLABS = 1;
+constexpr int NODE_LEAN_CTAS = 3;   // resident CTAs per SM of the residual-free node pass       // contingency slabs per iteration (line / node overlap)
 
 // shared floats per warp: 3 (T+1) for the inner-ADMM work arrays, plus room
 // for one device's (lam, beta) while the horizon is short enough
@@ -954,12 +955,20 @@ __device__ __forceinline__ void line_body(const Params &p, int k0, int k1, unsig
 // node: step 3 for every (contingency, node, VW time steps), and the CTA's
 // residual partial sums: FP32 per thread, FP64 across warps
 // ---------------------------------------------------------------------------
-template <int VW, bool RELAX>
+// LEAN: the variant for iterations that form no residuals (it returns at
+// once on the others); the general variant returns at once on those when a
+// lean launch covers them.
+template <int VW, bool RELAX, bool LEAN = false>
 __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int first, unsigned bid,
-                                          unsigned nblk) {
+                                          unsigned nblk, bool lean_split = false) {
   __shared__ double red[WARPS][NSLOT];
   const Iter q = iter_scalars(p);
   if (q.skip) return;
+  if constexpr (LEAN) {
+    if (q.res) return;
+  } else {
+    if (lean_split && !q.res) return;
+  }
   const int N = p.N, TV = p.T / VW;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned n = (unsigned)(k1 - k0) * (unsigned)N * (unsigned)TV;
@@ -973,8 +982,8 @@ __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int f
   ix.set(item, KK, TV);
   dx.set(stride, KK, TV);
   for (; item < n; item += stride, ix.step(dx, KK, TV))
-    node_item<VW, RELAX>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.fsu, acc, q.res != 0);
-  if (!q.res) return;   // nothing reads this iteration's partial sums
+    node_item<VW, RELAX>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.fsu, acc, LEAN ? false : q.res != 0);
+  if (LEAN || !q.res) return;   // nothing reads this iteration's partial sums
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     float v = acc[s];
@@ -1100,7 +1109,12 @@ __global__ void __launch_bounds__(BLOCK, 4) line_kernel(Params p, int k0, int k1
 // registers of one CTA per SM rather than spill
 template <int VW, bool RELAX>
 __global__ void __launch_bounds__(BLOCK, RELAX ? 1 : NODE_MIN_CTAS) node_kernel(Params p, int k0, int k1, int first) {
-  node_body<VW, RELAX>(p, k0, k1, first, blockIdx.x, gridDim.x);
+  node_body<VW, RELAX>(p, k0, k1, first, blockIdx.x, gridDim.x, !RELAX && VW == NODE_VW);
+}
+
+// the residual-free node pass: fewer live values, more CTAs per SM
+__global__ void __launch_bounds__(BLOCK, NODE_LEAN_CTAS) node_kernel_lean(Params p, int k0, int k1, int first) {
+  node_body<NODE_VW, false, true>(p, k0, k1, first, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(BLOCK) decide_kernel(Params p, int n_part) { decide_body(p, n_part); }
@@ -1386,6 +1400,7 @@ int opfk_plan(const Params &p, IterPlan *plan) {
     return -1;
   const bool vn = (p.T % NODE_VW == 0);
   const int gn = vn ? resident_grid(node_kernel<NODE_VW, false>, 0) : resident_grid(node_kernel<1, false>, 0);
+  const int gl = vn ? resident_grid(node_kernel_lean, 0) : 0;
   const int gx = v4 ? resident_grid(xs_kernel<4>, 0) : resident_grid(xs_kernel<1>, 0);
   const int gd = v2 ? resident_grid(dsum_kernel<2>, 0) : resident_grid(dsum_kernel<1>, 0);
   if (gn < 1 || gx < 1 || gd < 1) return -1;
@@ -1403,6 +1418,7 @@ int opfk_plan(const Params &p, IterPlan *plan) {
   const int n_inner = p.n_stor + p.n_ramp + p.n_hvdc;
   plan->line_grid = (int)((nl + (long long)BLOCK * LINE_IPT - 1) / ((long long)BLOCK * LINE_IPT));
   plan->node_grid = (int)std::min<long long>(gn, (nn + BLOCK - 1) / BLOCK);
+  plan->lean_grid = vn ? (int)std::min<long long>(gl, (nn + BLOCK - 1) / BLOCK) : 0;
   plan->xs_grid = (int)std::min<long long>(gx, (nx + BLOCK - 1) / BLOCK);
   plan->inner_grid = (n_inner + WARPS - 1) / WARPS;
   const long long nd = (long long)p.N * (p.T / (v2 ? 2 : 1));
@@ -1438,7 +1454,12 @@ int opfk_iteration_enqueue(const Params &p, const IterPlan &plan, void *main_str
       if (cudaStreamWaitEvent(sm, (cudaEvent_t)ev_join, 0) != cudaSuccess) return -1;
     }
     const bool vn = p.T % NODE_VW == 0, rx = p.alpha != 1.f;
-    if (vn && !rx) node_kernel<NODE_VW, false><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
+    if (vn && !rx) {
+      // one of the two returns at once: the general pass forms residuals,
+      // the lean one runs the iterations that need none
+      node_kernel<NODE_VW, false><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
+      node_kernel_lean<<<plan.lean_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
+    }
     else if (!rx) node_kernel<1, false><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
     else if (vn) node_kernel<NODE_VW, true><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
     else node_kernel<1, true><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
