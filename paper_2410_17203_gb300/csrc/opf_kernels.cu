@@ -46,8 +46,8 @@ constexpr int ST_NONFINITE = 5;  // opf_status value set on the device
 constexpr int NODE_VW = 4;       // time steps per node item
 constexpr int NODE_MIN_CTAS = 2; // resident CTAs per SM the node kernel is compiled for
 constexpr int LINE_IPT = 4;      // line items per thread (CTA-sized blocks of items)
-constexpr int N_SLABS = 1;
-constexpr int NODE_LEAN_CTAS = 3;   // resident CTAs per SM of the residual-free node pass       // contingency slabs per iteration (line / node overlap)
+constexpr int N_SLABS = 1;       // contingency slabs per iteration (line / node overlap)
+constexpr int NODE_LEAN_CTAS = 3;  // resident CTAs per SM of the residual-free node pass
 
 // shared floats per warp: 3 (T+1) for the inner-ADMM work arrays, plus room
 // for one device's (lam, beta) while the horizon is short enough
