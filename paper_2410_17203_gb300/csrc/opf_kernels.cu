@@ -47,7 +47,8 @@ constexpr int NODE_VW = 4;       // time steps per node item
 constexpr int NODE_MIN_CTAS = 2; // resident CTAs per SM the node kernel is compiled for
 constexpr int LINE_IPT = 4;      // line items per thread (CTA-sized blocks of items)
 constexpr int N_SLABS = 1;       // contingency slabs per iteration (line / node overlap)
-constexpr int NODE_LEAN_CTAS = 3;  // resident CTAs per SM of the residual-free node pass
+constexpr int NODE_LEAN_CTAS = 4;  // resident CTAs per SM of the residual-free node pass
+constexpr int NODE_LEAN_NB = 2;    // line terminals it gathers together
 
 // shared floats per warp: 3 (T+1) for the inner-ADMM work arrays, plus room
 // for one device's (lam, beta) while the horizon is short enough
@@ -662,7 +663,7 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
 // res = 0: the iteration's residuals are not read, so the node sums skip the
 // inputs only they need (old p and theta_bar rows, the device Welford state)
 // and their accumulation; the relaxed variant always needs the mean change.
-template <int VW, bool RELAX>
+template <int VW, bool RELAX, int NB = 4>
 __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int k, int n, int toff, float fsu,
                                           float *acc, bool res) {
   const int T = p.T;
@@ -696,11 +697,16 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
   const int lout = p.out_line[k];
   int4 c4 = r1;
   for (int j = r2.x - 4;;) {
-    const int code[4] = {c4.x, c4.y, c4.z, c4.w};
-    FV<VW> pn[4], po[4], mq[4], mo[RELAX ? 4 : 1];
-    float bq[4];
+    const int code4[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll 1
+    for (int half = 0; half < 4; half += NB) {
+    int code[NB];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < NB; ++q) code[q] = code4[half + q];
+    FV<VW> pn[NB], po[NB], mq[NB], mo[RELAX ? NB : 1];
+    float bq[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
       if (code[q] >= 0) {
         const int l = code[q] >> 1;
         const size_t ol = (size_t)l * lrow + kb;
@@ -712,7 +718,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < NB; ++q) {
       if (code[q] >= 0) {
         const bool t2 = code[q] & 1, act = (code[q] >> 1) != lout;
         const float tb = 2.f * bq[q], rtb = __frcp_rn(tb);
@@ -736,6 +742,7 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
           else wth.add(th);
         }
       }
+    }
     }
     j += 4;
     if (j >= r2.y) break;
@@ -982,7 +989,8 @@ __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int f
   ix.set(item, KK, TV);
   dx.set(stride, KK, TV);
   for (; item < n; item += stride, ix.step(dx, KK, TV))
-    node_item<VW, RELAX>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.fsu, acc, LEAN ? false : q.res != 0);
+    node_item<VW, RELAX, LEAN ? NODE_LEAN_NB : 4>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.fsu, acc,
+                                                  LEAN ? false : q.res != 0);
   if (LEAN || !q.res) return;   // nothing reads this iteration's partial sums
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
