@@ -1150,9 +1150,9 @@ __global__ void __launch_bounds__(BLOCK) xs_kernel_b(const Params *ps, const int
   xs_body<VW>(p, bid, nblk);
 }
 
-// batches keep the GPU full of inner-ADMM warps: 80 registers, 3 CTAs per SM
+// batches keep the GPU full of inner-ADMM warps: 64 registers, 4 CTAs per SM
 // (the single-instance kernel runs beside the line kernel and keeps 2)
-__global__ void __launch_bounds__(BLOCK, 3) inner_kernel_b(const Params *ps, const int4 *sched) {
+__global__ void __launch_bounds__(BLOCK, 4) inner_kernel_b(const Params *ps, const int4 *sched) {
   extern __shared__ float smem[];
   __shared__ Params sp;
   unsigned bid, nblk;
