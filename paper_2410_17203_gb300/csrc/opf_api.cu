@@ -1039,6 +1039,9 @@ opf_status set_batch_layout(opf_batch *b, const opfk::BatchLayout &lay) {
   if (b->g_many) cudaGraphExecDestroy(b->g_many);
   b->g_one = b->g_many = nullptr;
   CK(cudaMemcpy(b->d_sched, sched.data(), sched.size() * sizeof(int), cudaMemcpyHostToDevice));
+  // the node phase's CTA count sizes each instance's partial sums
+  for (int i = 0; i < n; ++i) hp[i].node_grid = opfk_batch_node_blocks(plans[i], lay.div);
+  CK(cudaMemcpy(b->d_params, hp.data(), n * sizeof(Params), cudaMemcpyHostToDevice));
   b->plan = bp;
   return OPF_OK;
 }

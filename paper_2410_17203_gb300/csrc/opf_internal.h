@@ -178,6 +178,9 @@ int opfk_iteration_enqueue(const opfk::Params &p, const opfk::IterPlan &plan, vo
 // their plans): fills sched (4 ints per CTA, BatchPlan order) and the plan.
 int opfk_batch_plan(const opfk::Params *hp, const opfk::IterPlan *plans, int n, const opfk::BatchLayout &lay,
                     int *sched_out, long long sched_cap, long long *sched_len, opfk::BatchPlan *bp);
+// Node CTAs (and partial sums) of an instance under a layout's `div`: the
+// batch's copy of the instance's Params must carry it as node_grid.
+int opfk_batch_node_blocks(const opfk::IterPlan &plan, int div);
 // Enqueue one iteration of every instance: d_params [n] and d_sched on the
 // device; the same stream and event roles as opfk_iteration_enqueue.
 int opfk_batch_enqueue(const opfk::Params *d_params, const int *d_sched, const opfk::BatchPlan &bp,

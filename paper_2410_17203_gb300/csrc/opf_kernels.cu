@@ -1528,9 +1528,11 @@ int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, const BatchL
           blocks = 1;
           break;
       }
-      // the grid-stride phases take any block count: `div` puts more work in each CTA
+      // the grid-stride phases take any block count: `div` puts more work in
+      // each CTA (for the node phase the caller sets the instance's partial-sum
+      // count to the same number, batch_node_blocks)
       if (blocks > 0 && (kind == BK_XS4 || kind == BK_XS1 || kind == BK_INNER || kind == BK_DSUM2 ||
-                         kind == BK_DSUM1))
+                         kind == BK_DSUM1 || kind == BK_NODE4 || kind == BK_NODE1))
         blocks = (blocks + div - 1) / div;
       nb[j] = blocks;
       most = std::max(most, blocks);
@@ -1557,6 +1559,11 @@ int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, const BatchL
     return -1;
   *sched_len = len;
   return 0;
+}
+
+int opfk_batch_node_blocks(const IterPlan &plan, int div) {
+  const int d = div > 1 ? div : 1;
+  return (plan.node_grid + d - 1) / d;
 }
 
 int opfk_batch_enqueue(const Params *d_params, const int *d_sched, const BatchPlan &bp, void *main_stream,
