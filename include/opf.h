@@ -171,18 +171,22 @@ opf_status opf_create(const opf_network *net, int32_t horizon_T,
                       const opf_contingencies *ctg, const opf_options *opt,
                       opf_ctx **out);
 
-/* Enqueue up to n_iters message-passing iterations (Section 3.2).  Each
- * iteration is five kernels (device averages and closed-form devices, inner
- * ADMM devices, line proxes on a second stream, node sums with the residual
- * partials, decisions), replayed from CUDA graphs of 1 and 16 iterations.
- * rho > 0 first sets rho_p = rho_theta = rho, rescaling the scaled duals
- * (Section 3.5); rho <= 0 keeps the current (possibly adapted) penalties.
- * After a passed stopping test (or a non-finite residual) the remaining
- * iterations of the call do nothing.  Asynchronous with respect to the
- * caller's stream when stopping is disabled (eps <= 0 or check_every = 0);
- * with stopping enabled the call keeps at most 128 iterations queued ahead of
- * the GPU so that it can stop launching, and it returns OPF_ETIMEOUT if that
- * wait exceeds sync_timeout_ms.  Device errors surface at the next
+/* Enqueue n_iters message-passing iterations (Section 3.2).  Each iteration
+ * is seven kernels (device averages and closed-form devices, inner-ADMM
+ * devices, device sums, line proxes on a second stream, the node sums -- a
+ * general pass on iterations that form residuals and a lean pass on the
+ * others, each returning at once on the other's iterations -- and the
+ * decisions), replayed from CUDA graphs of 1 and 16 iterations after a
+ * one-thread kernel that records the call's last iteration.  Residuals
+ * (Section 3.3) are formed on stopping-test iterations (every check_every),
+ * adaptation iterations (every adapt_every) and the call's last iteration;
+ * a non-finite value is reported (OPF_ENONFINITE) at the first of these
+ * after it appears.  rho > 0 first sets rho_p = rho_theta = rho, rescaling
+ * the scaled duals (Section 3.5); rho <= 0 keeps the current (possibly
+ * adapted) penalties.  After a passed stopping test or an error the
+ * remaining iterations of the call return at once.  Asynchronous: the call
+ * only enqueues on the context's streams, ordered after the caller's stream
+ * and before its later work; device errors surface at the next
  * synchronizing call. */
 opf_status opf_iterate(opf_ctx *ctx, int32_t n_iters, double rho);
 
