@@ -249,6 +249,32 @@ def run_oracle(cfg, k_s, T_s, steps, warmup, world=1):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def host_cpu():
+    """The host CPU's model as the OS reports it (x86: model name; Arm: the
+    implementer / part codes and the lscpu model name when present)."""
+    import platform
+    info = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    info.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if "model name" in info:
+        return info["model name"]
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    parts = [f"{k} {info[k]}" for k in ("CPU implementer", "CPU part") if k in info]
+    return ", ".join(parts) or platform.machine()
+
+
 def oracle_value(res, full_vars):
     """Full-workload iterations/s from the sample's variable-update rate."""
     upd = res["vars_per_iter"] * res["steps"] / res["seconds"]
@@ -289,7 +315,8 @@ def reference_arm(args):
             "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "N": d["N"], "L": d["L"], "T": d["T"], "K": d["K"],
                        "S": d["S"]},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu": host_cpu(), "host_cores": os.cpu_count()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -658,6 +685,7 @@ def ours_arm(args):
         k_s = 10
         r = run_oracle(args.config, k_s, d["T"], 2, 1)
         cpu = {"value": oracle_value(r, variables_per_iter(d)), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "cpu": host_cpu(), "host_cores": os.cpu_count(),
                "sample": f"{args.config} network with contingencies 0..{k_s} (of {d['K']}), 2 timed "
                          f"iterations after 1 warm-up; value scaled by 4JT(K+1) variables per iteration"}
         # all host cores: the oracle sharded by contingency over single-threaded processes
