@@ -297,3 +297,26 @@ def test_alpha_out_of_range_is_rejected():
     for alpha in (0.9, 2.0):
         with pytest.raises(OpfError):
             Solver(CASES["tiny"](), dict(alpha=alpha))
+
+
+def test_over_relaxed_state_import_restarts_the_copies():
+    """With alpha != 1 an imported state restarts the duplicate variables at
+    z = p~, xi = theta_bar on both sides (the device's relaxed schedules
+    become the imported ones); the continuation then matches the oracle."""
+    from paper_2410_17203_gb300 import Solver
+    case = CASES["mixed_T24"]()
+    opts = dict(adapt_every=0, eps=0.0, rho_theta=5.0, alpha=1.5)
+    a = Solver(case, opts)
+    b = Solver(case, opts)
+    try:
+        a.iterate(20)
+        st = a.state()
+        b.set_state(st)
+        b.iterate(10)
+        o = Oracle(case, OracleOptions(**opts))
+        o.load_state({k: v.astype(np.float64) for k, v in st.items()})
+        o.iterate(10, stop=False)
+        compare_states(b.state(), o)
+    finally:
+        a.close()
+        b.close()
