@@ -1,27 +1,26 @@
 // Proximal message passing for contingency-constrained DC OPF -- sm_103a kernels.
 //
-// One iteration of the message-passing form of ADMM (Section 3.2) is five
-// kernels, replayed from a CUDA graph; each reads the iteration's scalars
-// (penalties, pending rescales, buffer parity) from the device, so the same
-// graph serves every iteration:
-//
-//   xs     step 2 input: avg_k(pbar + u) at every node with devices (128-bit
-//          loads over the K+1 contingency rows), and the closed-form prox
-//          with weight (K+1) rho_p of the node's generators and loads;
-//   inner  step 2, one warp per ramp-limited generator or battery: the inner
-//          ADMM of Appendix D, lanes over time steps, each x-update a
-//          tridiagonal solve by warp-wide scans;
-//   line   step 1, one thread per (contingency, line, 4 time steps), the
-//          closed-form line prox from the previous line and node values at
-//          both ends (runs concurrently with xs and inner: it reads only the
-//          previous iterate);
-//   node   step 3, one thread per (contingency, node, 2 time steps): pbar,
-//          theta_bar and u += pbar as register sums over the node's terminals
-//          in CSR order (no atomics), with the residual partial sums of
-//          Section 3.3 (one-pass Welford sums for theta~ and the change of p~);
-//   decide one CTA reduces the per-CTA partial sums in FP64 in a fixed order,
-//          forms the residuals, and takes the stopping and adaptive-penalty
-//          decisions (Section 3.5).
+// One iteration of the message-passing form of ADMM (Section 3.2) is seven
+// kernels replayed from CUDA graphs; each reads the iteration's scalars
+// (penalties, pending rescales, buffer parity, whether residuals are read)
+// from the device, so the same graph serves every iteration:
+//   xs     step 2 input: avg_k(pbar + u) from the stored pbar + u at every
+//          node with devices (a node's K+1 rows are one run), and the
+//          closed-form prox with weight (K+1) rho_p of its generators/loads;
+//   inner  step 2, one warp per ramp-limited generator, battery or HVDC link:
+//          the inner ADMM of Appendix D (lanes over time steps, tridiagonal
+//          x-updates by warp-wide scans) or the link's closed form;
+//   dsum   the node sums of device powers and their Welford change state;
+//   line   step 1, one thread per (line, contingency, 4 time steps): the line
+//          prox from the previous iterate at both ends (second stream, beside
+//          xs, inner and dsum), the deferred v update, over-relaxed blends;
+//   node   step 3 where the residuals are read (stopping test, adaptation,
+//          end of a call): pbar, theta_bar, u += pbar as register sums over
+//          the node's terminals in CSR order (no atomics), the residual
+//          partial sums (one-pass Welford sums); node_lean does step 3 alone
+//          on the other iterations (each returns at once on the other's);
+//   decide FP64 reduction of the partial sums in a fixed order, stopping
+//          test and adaptive penalty (Section 3.5); advances the counter.
 //
 // Splitting the phases lets each kernel run at its own register budget.
 // There is no spin-wait on the device: ordering comes from kernel boundaries
@@ -29,7 +28,8 @@
 // instances: the batch entry points take the instances' parameters and a
 // CTA schedule, so one launch per phase covers all instances.
 //
-// Memory layout, numbering and the deferred v update: opf_internal.h.
+// Memory layout (line- and node-major), numbering and the deferred v
+// update: opf_internal.h.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -588,7 +588,7 @@ struct Idx3 {
 template <int VW>
 __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int k, int l, int toff, float frp,
                                           float frt, float fsu, float fsv, bool v_fresh) {
-  const int T = p.T, L = p.L, N = p.N;
+  // offsets of the line and its end nodes' rows: lidx / nidx
   const int n1 = p.line_n1[l], n2 = p.line_n2[l];
   const bool act = p.out_line[k] != l;
   const size_t ol = lidx(p, k, l, toff);
@@ -1247,7 +1247,7 @@ __global__ void import_kernel(Params p, int cur, const float *pl, const float *a
 
 // node averages from the stored terminal values (after import)
 __global__ void node_average_kernel(Params p, int cur) {
-  const int T = p.T, N = p.N, L = p.L;
+  const int T = p.T, N = p.N;
   for (long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x; item < (long long)N * T;
        item += (long long)gridDim.x * blockDim.x) {
     const int n = (int)(item / T), t = (int)(item % T);
@@ -1273,7 +1273,7 @@ __global__ void node_average_kernel(Params p, int cur) {
 
 // v projected onto v_bar = 0 per node and contingency (Appendix C)
 __global__ void project_v_kernel(Params p, int cur) {
-  const int T = p.T, N = p.N, L = p.L;
+  const int T = p.T, N = p.N;
   for (long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
        item < (long long)p.Kp * N * T; item += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(item / ((long long)N * T));
@@ -1301,7 +1301,7 @@ __global__ void export_lines_kernel(Params p, int cur, float *pl, float *a1, flo
                                     float *v2) {
   const DevScalars sc = *p.sc;
   const float sv = (float)sc.sv;
-  const int T = p.T, N = p.N, L = p.L;
+  const int T = p.T, L = p.L;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)p.Kp * L * T;
        i += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(i / ((long long)L * T));
@@ -1503,7 +1503,7 @@ int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, const BatchL
       const int i = lay.order ? lay.order[j] : j;
       const Params &p = hp[i];
       const bool v4 = (p.T % 4 == 0), v2 = (p.T % 2 == 0), vn = (p.T % NODE_VW == 0);
-      const long long tv4 = p.T / (v4 ? 4 : 1), tvn = p.T / (vn ? NODE_VW : 1), tv2 = p.T / (v2 ? 2 : 1);
+      const long long tv4 = p.T / (v4 ? 4 : 1), tv2 = p.T / (v2 ? 2 : 1);
       const int n_inner = p.n_stor + p.n_ramp + p.n_hvdc;
       long long blocks = 0;
       switch (kind) {
