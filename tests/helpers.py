@@ -9,6 +9,21 @@ STATE_RTOL = 1e-5
 RES_RTOL = 1e-3
 
 
+def hang_triangle(case, node=0):
+    """The case with two device-free nodes X, Y joined to ``node`` and to each
+    other (lines node-X, X-Y, Y-node, appended last): no power flows in the
+    triangle at any fixed point, and outaging X-Y (line index L - 2) leaves a
+    node whose only active terminal is one line."""
+    n0 = case["n_nodes"]
+    ext = dict(case)
+    ext["n_nodes"] = n0 + 2
+    ext["line_from"] = np.concatenate([case["line_from"], np.array([node, n0, n0 + 1], np.int32)])
+    ext["line_to"] = np.concatenate([case["line_to"], np.array([n0, n0 + 1, node], np.int32)])
+    ext["line_b"] = np.concatenate([case["line_b"], [8.0, 12.0, 10.0]])
+    ext["line_u"] = np.concatenate([case["line_u"], [0.7, 0.9, 1.1]])
+    return ext
+
+
 def oracle_arrays(o):
     L = o.net.L
     return dict(p_line=o.line_p(), th1=o.th[:, :L], th2=o.th[:, L:], v1=o.v[:, :L],

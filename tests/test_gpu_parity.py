@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from gridgen import make_case, scale_case
-from helpers import compare_residuals, compare_states, oracle_arrays, rel_err
+from helpers import compare_residuals, compare_states, hang_triangle, oracle_arrays, rel_err
 from oracle import Oracle, OracleOptions
 
 pytestmark = pytest.mark.gpu
@@ -37,6 +37,13 @@ def run_both(case, n, **opts):
     return st, res, info, o
 
 
+def _line_only_nodes():
+    base = make_case(scale_case(80, 12, 2, seed=27))
+    ext = hang_triangle(base, node=5)
+    xy = len(ext["line_b"]) - 2
+    return dict(ext, outaged=np.array([xy, base["outaged"][0], xy, base["outaged"][1]], np.int32))
+
+
 CASES = {
     "tiny": lambda: make_case("tiny"),
     "mixed_T24": lambda: make_case(scale_case(150, 24, 6, seed=21)),
@@ -47,6 +54,8 @@ CASES = {
                               outaged=np.array([-1, -1], np.int32)),
     "hvdc_T24": lambda: make_case(scale_case(160, 24, 5, seed=26, n_hvdc=4)),
     "hvdc_tiny": lambda: make_case("tiny", n_hvdc=3),
+    # nodes with line terminals only; one of them keeps a single active line
+    "line_only_nodes": lambda: _line_only_nodes(),
 }
 
 

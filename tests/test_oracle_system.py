@@ -14,6 +14,7 @@ import pytest
 from scipy.optimize import Bounds, LinearConstraint, minimize
 
 from gridgen import make_case
+from helpers import hang_triangle
 from oracle import Oracle, OracleOptions
 
 HERE = os.path.dirname(__file__)
@@ -188,6 +189,33 @@ def test_duplicate_no_outage_contingencies_keep_the_solution():
     np.testing.assert_allclose(o3.dev_p(), o0.dev_p(), atol=1e-5)
     assert o3.objective() == pytest.approx(o0.objective(), rel=2e-6)
     np.testing.assert_allclose(o3.prices(), o0.prices(), atol=1e-4)
+
+
+def test_outage_of_a_zero_flow_line_keeps_the_solution():
+    """Outaging a line that carries no power at the optimum changes no
+    constraint that binds, so K such contingencies leave the dispatch, cost
+    and prices of the base case (Eq. contingency-dispatch).  The line is the
+    side X-Y of a triangle 0-X-Y hung on node 0 whose nodes X, Y have no
+    devices: every flow in the triangle is zero, with or without the outage,
+    and the outaged line is not a bridge."""
+    base = make_case("tiny", K=0)
+    n0 = base["n_nodes"]
+    ext = hang_triangle(base)
+    L = len(ext["line_b"])
+    opts = OracleOptions(adapt_every=0, rho_theta=10.0, eps=1e-8)
+    o0 = Oracle(base, opts)
+    oe = Oracle(dict(ext, outaged=np.zeros(0, np.int32)), opts)
+    ok = Oracle(dict(ext, outaged=np.array([L - 2] * 3, np.int32)), opts)
+    for o in (o0, oe, ok):
+        o.iterate(200000)
+        assert o.converged
+    for o in (oe, ok):
+        np.testing.assert_allclose(o.dev_p(), o0.dev_p(), atol=1e-5)
+        assert o.objective() == pytest.approx(o0.objective(), rel=2e-6)
+        np.testing.assert_allclose(o.prices()[:n0], o0.prices(), atol=1e-4)
+        np.testing.assert_allclose(o.line_p()[:, L - 3:], 0.0, atol=1e-6)
+    # the outaged copies carry nothing on X-Y; the base row is the base case
+    np.testing.assert_allclose(ok.line_p()[1:, L - 2], 0.0, atol=0)
 
 
 def test_adaptive_penalty_keeps_the_fixed_point():
