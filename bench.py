@@ -44,7 +44,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ADMM iterations/s"
 UNIT = "iter/s"
-WORKLOAD = "dcopf-10k-bus-T96-K50"
+def workload_name(config, d):
+    """Name of the timed workload: the network size, horizon and contingencies."""
+    return f"dcopf-{config}-bus-T{d['T']}-K{d['K']}"
 KERNEL_SRC = [os.path.join(ROOT, "paper_2410_17203_gb300", "csrc", f)
               for f in ("opf_kernels.cu", "opf_internal.h")]
 PROFILE = os.path.join(ROOT, "profiles", "iteration_10k.txt")
@@ -313,7 +315,7 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds"] / res["steps"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "N": d["N"], "L": d["L"], "T": d["T"], "K": d["K"],
+            "config": {"workload": workload_name(args.config, d), "N": d["N"], "L": d["L"], "T": d["T"], "K": d["K"],
                        "S": d["S"]},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                              "cpu": host_cpu(), "host_cores": os.cpu_count()},
@@ -709,7 +711,7 @@ def ours_arm(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": d["N"], "L": d["L"], "T": d["T"], "K": d["K"],
+            "config": {"workload": workload_name(args.config, d), "N": d["N"], "L": d["L"], "T": d["T"], "K": d["K"],
                        "S": d["S"], "J": d["J"], "parallelism": f"independent instance per GPU x{ws}",
                        "l2": "inputs larger than L2 (state %.2f GB)" % (info["device_bytes"] / 1e9),
                        "adapt_every": 10},
