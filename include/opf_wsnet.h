@@ -4,8 +4,8 @@
  * The paper has no counterpart: its warm start (Section 3.4) reuses a
  * previous solution.  This network proposes initial nodal prices and node
  * angles for the message-passing iteration from node features; the
- * iteration then runs unchanged to the same tolerance, so it stays the
- * judge of the answer.
+ * iteration then runs unchanged to the same tolerance, so its own stopping
+ * test still certifies the answer.
  *
  * Model (rows r = t * N + n, the same weights at every time step t):
  *   H0 = relu(X W0 + b0)                       X  [R][F],  W0 [F][64]

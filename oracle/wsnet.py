@@ -5,7 +5,7 @@ the product library.  The paper has no learned component: its warm start
 (Section 3.4) reuses a previous solution.  This network is the project's
 addition, which proposes initial prices and node angles for the message
 passing iteration; the iteration itself is unchanged and runs to the same
-tolerance, so it stays the judge of the result.
+tolerance, so its own stopping test still certifies the result.
 
 The network maps node features to node outputs independently at every time
 step t, with the same weights at every step.  Rows are ``r = t * N + n``.

@@ -89,7 +89,7 @@ def test_warm_state_from_the_solution_and_learned_start():
 
 def test_gpu_solutions_pass_the_oracle_certificate():
     """The training targets are solutions the GPU path produces; each one is
-    checked here the way the oracle would judge it: the GPU's converged
+    checked here by the oracle's own stopping test: the GPU's converged
     state (with its penalties and inner-ADMM duals) is loaded into the FP64
     oracle, whose next iteration must still meet the stopping test and keep
     the objective (a state that only looked converged in FP32 would not)."""
