@@ -56,6 +56,9 @@ CASES = {
     "hvdc_tiny": lambda: make_case("tiny", n_hvdc=3),
     # nodes with line terminals only; one of them keeps a single active line
     "line_only_nodes": lambda: _line_only_nodes(),
+    # horizons above 128 steps: the inner-ADMM state stays in global memory
+    "long_T200": lambda: make_case(scale_case(40, 200, 2, seed=29)),
+    "long_T150": lambda: make_case(scale_case(30, 150, 1, seed=30, stor_per_node=0.1, fixed_frac=0.3)),
 }
 
 
@@ -214,6 +217,16 @@ def test_nonfinite_state_is_reported():
     assert s.get_info()["iterations"] == 5
     s.iterate(5)                                     # a stopped context stays stopped
     assert s.get_info()["iterations"] == 5
+
+
+def test_longest_horizon_matches_oracle():
+    """T = 2048, the largest horizon the library takes: ramp-limited
+    generators' inner ADMM over 2048 steps (work arrays of 192 KB of shared
+    memory per CTA, state in global memory), with an outage."""
+    case = make_case(scale_case(12, 2048, 1, seed=31, stor_per_node=0.0))
+    st, res, info, o = run_both(case, 20, adapt_every=10, eps=0.0)
+    compare_states(st, o)
+    assert info["iterations"] == 20
 
 
 def test_empty_and_degenerate_shapes():
