@@ -24,7 +24,9 @@ def _cases():
             make_case(scale_case(90, 7, 3, seed=22, fixed_frac=0.3)),
             make_case(scale_case(70, 8, 0, seed=23, fixed_frac=0.5, stor_per_node=0.0)),
             make_case(scale_case(80, 12, 2, seed=27, n_hvdc=3)),
-            hang_triangle(make_case(scale_case(40, 5, 1, seed=28)), node=3)]
+            hang_triangle(make_case(scale_case(40, 5, 1, seed=28)), node=3),
+            # a horizon above 128 steps: inner-ADMM state in global memory
+            make_case(scale_case(30, 150, 1, seed=30, stor_per_node=0.1, fixed_frac=0.3))]
 
 
 def test_batch_iterates_equal_single_instance_iterates():
