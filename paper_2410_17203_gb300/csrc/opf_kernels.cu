@@ -991,21 +991,23 @@ __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int f
   for (; item < n; item += stride, ix.step(dx, KK, TV))
     node_item<VW, RELAX, LEAN ? NODE_LEAN_NB : 4>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.fsu, acc,
                                                   LEAN ? false : q.res != 0);
-  if (LEAN || !q.res) return;   // nothing reads this iteration's partial sums
+  if constexpr (!LEAN) {
+    if (!q.res) return;   // nothing reads this iteration's partial sums
 #pragma unroll
-  for (int s = 0; s < NSLOT; ++s) {
-    float v = acc[s];
+    for (int s = 0; s < NSLOT; ++s) {
+      float v = acc[s];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wib][s] = (double)v;
-  }
-  __syncthreads();
-  // the slabs of one iteration run in order on one stream: the first one
-  // sets the CTA's partial sums, the others add to them
-  if (threadIdx.x < NSLOT) {
-    double v = first ? 0.0 : p.partials[(size_t)bid * NSLOT + threadIdx.x];
-    for (int w = 0; w < WARPS; ++w) v += red[w][threadIdx.x];
-    p.partials[(size_t)bid * NSLOT + threadIdx.x] = v;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wib][s] = (double)v;
+    }
+    __syncthreads();
+    // the slabs of one iteration run in order on one stream: the first one
+    // sets the CTA's partial sums, the others add to them
+    if (threadIdx.x < NSLOT) {
+      double v = first ? 0.0 : p.partials[(size_t)bid * NSLOT + threadIdx.x];
+      for (int w = 0; w < WARPS; ++w) v += red[w][threadIdx.x];
+      p.partials[(size_t)bid * NSLOT + threadIdx.x] = v;
+    }
   }
 }
 
