@@ -256,15 +256,16 @@ void opf_batch_destroy(opf_batch *batch);
  * one CTA per instance in turn; "1/4" gives the device-sum, inner-ADMM,
  * device-average and node-sum phases a quarter of the CTAs, each doing four
  * times the work; deeper divisors tuned on the first iterations lose on the
- * tail, when the largest instances run alone).  Every candidate runs `steps` >= 1 batch iterations (after one
- * warm-up) from the instances' current state, which is saved before and
- * restored after, so the call leaves every iterate unchanged; the fastest
- * layout is kept for later opf_batch_iterate calls.  The layout changes
- * which CTA computes what, not the arithmetic of an iterate; only the split
- * of the residual norms' partial sums over CTAs moves (their last bits).  choice and ms_each [OPF_BATCH_LAYOUTS] (each may be
- * NULL) receive the chosen index and every layout's milliseconds per batch
- * iteration.  Synchronizes; allocates a temporary copy of the instances'
- * states. */
+ * tail, when the largest instances run alone).  Every candidate runs
+ * `steps` >= 1 batch iterations (after one warm-up) from the instances'
+ * current state, which is saved before and restored after, so the call
+ * leaves every iterate unchanged; the fastest layout is kept for later
+ * opf_batch_iterate calls.  The layout changes which CTA computes what, not
+ * the arithmetic of an iterate; only the split of the residual norms'
+ * partial sums over CTAs moves (their last bits).  choice and
+ * ms_each [OPF_BATCH_LAYOUTS] (each may be NULL) receive the chosen index
+ * and every layout's milliseconds per batch iteration.  Synchronizes;
+ * allocates a temporary copy of the instances' states. */
 #define OPF_BATCH_LAYOUTS 6
 opf_status opf_batch_autotune(opf_batch *batch, int32_t steps, int32_t *choice, double *ms_each);
 
