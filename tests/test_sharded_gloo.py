@@ -1,8 +1,9 @@
-"""Contingency sharding over two processes (gloo, CPU).
+"""Contingency sharding over several processes (gloo, CPU).
 
 The iteration couples contingencies only through the sums over k that feed
 the non-contingency proxes (Section 3.2) and through the residual norms
-(Section 3.3).  Two ranks each hold half of the contingencies, all-reduce
+(Section 3.3).  Ranks each hold a contiguous block of the contingencies
+(uneven blocks when K + 1 does not divide evenly), all-reduce
 exactly those quantities, and must reproduce the single-process iteration:
 the same states (to FP64 rounding of the split sums), residuals and
 penalty decisions.  This is the exchange a contingency-sharded multi-GPU
@@ -56,18 +57,19 @@ def _rank_main(rank, world, port, out_dir, n_iter, alpha=1.0, hvdc=False):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("alpha, hvdc", [(1.0, False), (1.5, True)])
-def test_two_rank_contingency_shards_reproduce_the_iteration(tmp_path, alpha, hvdc):
+@pytest.mark.parametrize("world, alpha, hvdc", [(2, 1.0, False), (2, 1.5, True), (4, 1.0, True)])
+def test_contingency_shards_reproduce_the_iteration(tmp_path, world, alpha, hvdc):
     """Plain message passing, and the over-relaxed iteration (Section 3.6) on
-    a grid with HVDC links (two-terminal devices shared by all contingencies)."""
+    a grid with HVDC links (two-terminal devices shared by all contingencies);
+    four ranks split the six contingency rows 2, 2, 1, 1."""
     import torch.multiprocessing as mp
     from oracle import Oracle, OracleOptions
 
     n_iter = 30
     port = _free_port()
-    mp.start_processes(_rank_main, args=(2, port, str(tmp_path), n_iter, alpha, hvdc), nprocs=2, join=True,
-                       start_method="spawn")
-    parts = [np.load(tmp_path / f"rank{r}.npz") for r in range(2)]
+    mp.start_processes(_rank_main, args=(world, port, str(tmp_path), n_iter, alpha, hvdc), nprocs=world,
+                       join=True, start_method="spawn")
+    parts = [np.load(tmp_path / f"rank{r}.npz") for r in range(world)]
 
     ref = Oracle(_case(hvdc), OracleOptions(adapt_every=10, eps=0.0, alpha=alpha))
     res = []
@@ -87,3 +89,4 @@ def test_two_rank_contingency_shards_reproduce_the_iteration(tmp_path, alpha, hv
         assert q["hist"].tolist() == [list(h) for h in ref.rho_history]
         np.testing.assert_allclose(q["prices"], ref.prices(), rtol=1e-10, atol=1e-12)
     assert np.concatenate([q["k_ids"] for q in parts]).tolist() == list(range(ref.net.Kp))
+    assert [len(q["k_ids"]) for q in parts] == [len(b) for b in np.array_split(np.arange(ref.net.Kp), world)]
