@@ -48,3 +48,17 @@ def test_oracle_arm_on_other_ranks_does_no_work():
                         "--config", "tiny", "--steps", "3", "--warmup", "3"], cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_oracle_arm_under_torchrun_prints_one_line():
+    """Launched like the multi-GPU bench (one process per rank): rank 0 alone
+    times the oracle and prints; the other rank exits 0 without work."""
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", "0", os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--config", "tiny", "--steps", "3", "--warmup", "3",
+                        "--gpus", "2"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    assert j["impl"] == "reference" and j["n_gpus"] == 2 and j["value"] > 0
