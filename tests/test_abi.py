@@ -155,3 +155,16 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     from paper_2410_17203_gb300 import binding
     with pytest.raises(OSError):
         binding.load_library(str(tmp_path / "missing.so"))
+
+
+def test_valid_network_without_a_gpu_fails_loudly(lib):
+    """With no CUDA device the library reports the failed CUDA call; it has
+    no host fallback that would iterate on the CPU."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the context is created there")
+    from gridgen import make_case
+    from paper_2410_17203_gb300 import OpfError, opf_create
+    with pytest.raises(OpfError) as e:
+        opf_create(make_case("tiny"))
+    assert e.value.status in (2, 3)            # OPF_ENOMEM / OPF_ECUDA, never OPF_OK
