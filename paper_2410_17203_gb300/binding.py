@@ -201,9 +201,37 @@ def _ptr(a, ctype):
     return a.ctypes.data_as(C.POINTER(ctype)) if a is not None and a.size else C.POINTER(ctype)()
 
 
-def _network(case):
+# array lengths of a case: (count key, per time step) for every array field
+_SIZES = {
+    "line_to": ("line_from", False), "line_b": ("line_from", False), "line_u": ("line_from", False),
+    "gen_a": ("gen_node", False), "gen_b": ("gen_node", False), "gen_ramp": ("gen_node", False),
+    "gen_pmin": ("gen_node", True), "gen_pmax": ("gen_node", True),
+    "load_p": ("load_node", True), "load_voll": ("load_node", False),
+    "stor_P": ("stor_node", False), "stor_dur": ("stor_node", False), "stor_eff": ("stor_node", False),
+    "stor_cost": ("stor_node", False),
+    "hvdc_to": ("hvdc_from", False), "hvdc_u": ("hvdc_from", False),
+}
+
+
+def _check_sizes(case, where):
+    """The C entry points take plain pointers and read n (or n x T) values
+    behind each; an array of another length would be read past its end, so
+    the lengths are checked here, against the declared horizon T."""
+    T = int(case["T"])
+    for name, (count_key, per_t) in _SIZES.items():
+        n = len(case.get(count_key, ()))
+        a = np.asarray(case.get(name, ()))
+        if per_t:
+            if a.size != n * T or (a.ndim == 2 and a.shape != (n, T)):
+                raise OpfError(OPF_EINVAL, where, f"{name} has shape {a.shape}; expected ({n}, horizon T = {T})")
+        elif a.size != n:
+            raise OpfError(OPF_EINVAL, where, f"{name} has {a.size} values; expected {n}")
+
+
+def _network(case, where="opf_create"):
     """The opf_network and opf_contingencies of a case dict, plus the arrays
     they point into (keep them alive while the structs are used)."""
+    _check_sizes(case, where)
     keep = {}
 
     def f64(name, shape=None):
@@ -420,7 +448,7 @@ class UnrolledCost:
     with the same keys and shapes)."""
 
     def __init__(self, case, rho_p=1.0, rho_theta=1.0, checkpoint_every=16, stream=None):
-        net, ctg, keep = _network(case)
+        net, ctg, keep = _network(case, "opf_diff_create")
         self.T = int(case["T"])
         self.D, self.G, self.L = len(case["load_node"]), len(case["gen_node"]), len(case["line_from"])
         out = C.c_void_p()

@@ -132,6 +132,40 @@ def test_invalid_networks_are_rejected_on_the_host(lib, mutate, what):
     assert what.split()[0].lower() in str(e.value).lower()
 
 
+@pytest.mark.parametrize("T", [0, -3, 2049])
+def test_horizon_is_checked_by_the_library(lib, T):
+    """The C entry point itself rejects a horizon outside [1, 2048] before
+    reading any array (called here without the binding's size checks)."""
+    import ctypes as C
+    from gridgen import make_case
+    from paper_2410_17203_gb300 import binding as b
+    net, ctg, keep = b._network(make_case("tiny"))
+    h = C.c_void_p()
+    assert lib.opf_create(C.byref(net), T, C.byref(ctg), None, C.byref(h)) == b.OPF_EINVAL
+    assert "horizon" in b.opf_last_error().lower() and not h
+
+
+@pytest.mark.parametrize("mutate, what", [
+    (lambda c: c.__setitem__("line_u", c["line_u"][:-1]), "line_u has 39 values; expected 40"),
+    (lambda c: c.__setitem__("gen_pmax", c["gen_pmax"][:, [0, 0]]), "gen_pmax has shape (6, 2)"),
+    (lambda c: c.__setitem__("load_p", np.zeros((1, 20))), "load_p has shape (1, 20)"),
+    (lambda c: c.__setitem__("stor_eff", np.ones(2)), "stor_eff has 2 values; expected 0"),
+    (lambda c: c.update(hvdc_from=np.array([1], np.int32), hvdc_to=np.array([2, 3], np.int32),
+                        hvdc_u=np.ones(1)), "hvdc_to has 2 values; expected 1"),
+])
+def test_array_lengths_are_checked_by_the_binding(lib, mutate, what):
+    """Plain pointers carry no length: the binding checks every array against
+    the counts and the horizon before the library reads them."""
+    from gridgen import make_case
+    from paper_2410_17203_gb300 import OpfError, UnrolledCost, opf_create
+    bad = _bad(make_case("tiny"))
+    mutate(bad)
+    for make in (opf_create, UnrolledCost):
+        with pytest.raises(OpfError) as e:
+            make(bad)
+        assert e.value.status == 1 and what in str(e.value)
+
+
 def test_isolated_node_is_rejected(lib):
     from gridgen import make_case
     from paper_2410_17203_gb300 import OpfError, opf_create
