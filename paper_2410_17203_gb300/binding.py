@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libopfmp.so")
 OPF_OK, OPF_EINVAL, OPF_ENOMEM, OPF_ECUDA, OPF_ETIMEOUT, OPF_ENONFINITE, OPF_ESTATE = range(7)
 # capacity of the fixed device array behind opf_price_noalloc (N * T floats)
 OPF_PRICE_SCRATCH_FLOATS = 1 << 20
+OPF_WSNET_OUT = 2      # outputs per row of the warm-start network (price, angle)
 
 F32P = C.POINTER(C.c_float)
 F64P = C.POINTER(C.c_double)
@@ -278,11 +279,13 @@ def opf_create(case, options=None, stream=None):
     h = C.c_void_p()
     _check(lib.opf_create(C.byref(net), T, C.byref(ctg), C.byref(options), C.byref(h)),
            "opf_create")
+    _CTX_INFO[h.value] = opf_get_info(h)
     return h
 
 
 def opf_destroy(h):
     if h:
+        _CTX_INFO.pop(getattr(h, "value", h), None)
         load_library().opf_destroy(h)
 
 
@@ -314,15 +317,47 @@ def _addr(x):
     return x.ctypes.data
 
 
+def _buf(x, n, on_device, name, where):
+    """Address of a float32 buffer of exactly n elements: a contiguous CUDA
+    tensor when on_device, else a C-contiguous NumPy array.  The library
+    reads or writes n elements behind the pointer, so anything else is
+    refused here rather than touched out of bounds there."""
+    if x is None:
+        return None
+    if on_device:
+        ok = (hasattr(x, "data_ptr") and getattr(x, "is_cuda", False) and str(x.dtype) == "torch.float32"
+              and x.is_contiguous() and x.numel() == n)
+        if not ok:
+            raise OpfError(OPF_EINVAL, where, f"{name} must be a contiguous float32 CUDA tensor of {n} elements")
+        return x.data_ptr()
+    ok = (isinstance(x, np.ndarray) and x.dtype == np.float32 and x.flags.c_contiguous and x.size == n)
+    if not ok:
+        raise OpfError(OPF_EINVAL, where, f"{name} must be a C-contiguous float32 NumPy array of {n} elements")
+    return x.ctypes.data
+
+
+# sizes of each context (fixed for its lifetime), filled by opf_create
+_CTX_INFO = {}
+
+
+def _ctx_info(h):
+    info = _CTX_INFO.get(getattr(h, "value", h))
+    return info if info is not None else opf_get_info(h)
+
+
 def opf_solution(h, on_device=False, objective=True, p_dev=None, p_line=None, theta_node=None,
                  price=None):
     """Fill the given output buffers (NumPy float32 on host, tensors on device).
 
     Returns the objective (float) or None."""
+    i = _ctx_info(h)
+    Kp, L, N, S, T = i["K"] + 1, i["L"], i["N"], i["S"], i["T"]
+    dv = bool(on_device)
+    ptrs = [_buf(p_dev, S * T, dv, "p_dev", "opf_solution"), _buf(p_line, Kp * L * T, dv, "p_line", "opf_solution"),
+            _buf(theta_node, Kp * N * T, dv, "theta_node", "opf_solution"),
+            _buf(price, N * T, dv, "price", "opf_solution")]
     obj = C.c_double(0.0)
-    st = load_library().opf_solution(
-        h, int(bool(on_device)), C.byref(obj) if objective else F64P(),
-        _addr(p_dev), _addr(p_line), _addr(theta_node), _addr(price))
+    st = load_library().opf_solution(h, int(dv), C.byref(obj) if objective else F64P(), *ptrs)
     _check(st, "opf_solution")
     return obj.value if objective else None
 
@@ -330,12 +365,11 @@ def opf_solution(h, on_device=False, objective=True, p_dev=None, p_line=None, th
 def opf_price_noalloc(h, out=None):
     """Nodal prices [N][T] into the host float32 array ``out`` (or a new one),
     staged through the library's fixed device array (no allocation)."""
+    info = _ctx_info(h)
     if out is None:
-        info = opf_get_info(h)
         out = np.zeros((info["N"], info["T"]), np.float32)
-    if not (isinstance(out, np.ndarray) and out.dtype == np.float32 and out.flags.c_contiguous):
-        raise ValueError("out must be a C-contiguous float32 NumPy array")
-    _check(load_library().opf_price_noalloc(h, _addr(out)), "opf_price_noalloc")
+    ptr = _buf(out, info["N"] * info["T"], False, "out", "opf_price_noalloc")
+    _check(load_library().opf_price_noalloc(h, ptr), "opf_price_noalloc")
     return out
 
 
@@ -389,9 +423,14 @@ class WarmStartNet:
         lf = np.ascontiguousarray(line_from, np.int32)
         lt = np.ascontiguousarray(line_to, np.int32)
         lb = np.ascontiguousarray(line_b, np.float64)
+        if not (lt.size == lf.size and lb.size == lf.size):
+            raise OpfError(OPF_EINVAL, "opf_wsnet_create", "line_from, line_to and line_b differ in length")
         self.R = int(n_nodes) * int(T)
         self.F = int(n_features)
         p = None if params is None else np.ascontiguousarray(params, np.float32)
+        if p is not None and p.size != opf_wsnet_param_count(self.F):
+            raise OpfError(OPF_EINVAL, "opf_wsnet_create",
+                           f"params has {p.size} values; expected {opf_wsnet_param_count(self.F)}")
         self._keep = (lf, lt, lb, p)
         out = C.c_void_p()
         _check(load_library().opf_wsnet_create(
@@ -407,25 +446,31 @@ class WarmStartNet:
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, np.float32)
-        _check(load_library().opf_wsnet_set_params(self.h, p.ctypes.data), "opf_wsnet_set_params")
+        ptr = _buf(p, opf_wsnet_param_count(self.F), False, "params", "opf_wsnet_set_params")
+        _check(load_library().opf_wsnet_set_params(self.h, ptr), "opf_wsnet_set_params")
+
+    def _xy(self, x, y, where):
+        return (_buf(x, self.R * self.F, True, "x", where),
+                _buf(y, self.R * OPF_WSNET_OUT, True, "y", where))
 
     def forward(self, x, y):
-        _check(load_library().opf_wsnet_forward(self.h, _addr(x), _addr(y)), "opf_wsnet_forward")
+        _check(load_library().opf_wsnet_forward(self.h, *self._xy(x, y, "opf_wsnet_forward")),
+               "opf_wsnet_forward")
         return y
 
     def gradient(self, x, y_target, scale):
         sc = (C.c_float * 2)(*[float(v) for v in scale])
         loss = C.c_double(0.0)
         g = np.zeros(opf_wsnet_param_count(self.F), np.float32)
-        _check(load_library().opf_wsnet_gradient(self.h, _addr(x), _addr(y_target), sc, C.byref(loss),
-                                                 g.ctypes.data), "opf_wsnet_gradient")
+        _check(load_library().opf_wsnet_gradient(self.h, *self._xy(x, y_target, "opf_wsnet_gradient"), sc,
+                                                 C.byref(loss), g.ctypes.data), "opf_wsnet_gradient")
         return loss.value, g
 
     def train_step(self, x, y_target, scale, lr):
         sc = (C.c_float * 2)(*[float(v) for v in scale])
         loss = C.c_double(0.0)
-        _check(load_library().opf_wsnet_train_step(self.h, _addr(x), _addr(y_target), sc, float(lr),
-                                                   C.byref(loss)), "opf_wsnet_train_step")
+        _check(load_library().opf_wsnet_train_step(self.h, *self._xy(x, y_target, "opf_wsnet_train_step"), sc,
+                                                   float(lr), C.byref(loss)), "opf_wsnet_train_step")
         return loss.value
 
     def close(self):
@@ -536,18 +581,20 @@ def state_shapes(info):
 
 def opf_get_state(h, on_device=False, out=None):
     """Export the state into ``out`` (dict of buffers) or new host arrays."""
-    info = opf_get_info(h)
+    info = _ctx_info(h)
     if out is None:
         if on_device:
             raise ValueError("pass device buffers in `out` for on_device=True")
         out = {k: np.zeros(s, np.float32) for k, s in state_shapes(info).items()}
-    st = opf_state(**{k: _addr(out.get(k)) for k in STATE_FIELDS})
+    n = {k: int(np.prod(s)) for k, s in state_shapes(info).items()}
+    st = opf_state(**{k: _buf(out.get(k), n[k], bool(on_device), k, "opf_get_state") for k in STATE_FIELDS})
     _check(load_library().opf_get_state(h, int(bool(on_device)), C.byref(st)), "opf_get_state")
     return out
 
 
 def opf_set_state(h, state, on_device=False):
     """Import a state dict (missing keys are zeroed on the device)."""
+    n = {k: int(np.prod(s)) for k, s in state_shapes(_ctx_info(h)).items()}
     keep = {}
     ptrs = {}
     for k in STATE_FIELDS:
@@ -558,7 +605,7 @@ def opf_set_state(h, state, on_device=False):
         if not on_device:
             x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
             keep[k] = x
-        ptrs[k] = _addr(x)
+        ptrs[k] = _buf(x, n[k], bool(on_device), k, "opf_set_state")
     st = opf_state(**ptrs)
     _check(load_library().opf_set_state(h, int(bool(on_device)), C.byref(st)), "opf_set_state")
 

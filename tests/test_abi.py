@@ -202,3 +202,31 @@ def test_valid_network_without_a_gpu_fails_loudly(lib):
     with pytest.raises(OpfError) as e:
         opf_create(make_case("tiny"))
     assert e.value.status in (2, 3)            # OPF_ENOMEM / OPF_ECUDA, never OPF_OK
+
+
+def test_buffers_are_checked_before_the_library_touches_them(lib):
+    """Output and input buffers travel as plain pointers: the binding accepts
+    only float32 buffers of the exact element count (C-contiguous NumPy on the
+    host, contiguous CUDA tensors on the device)."""
+    import torch
+    from paper_2410_17203_gb300 import OpfError, binding as b
+    ok = np.zeros((3, 4), np.float32)
+    assert b._buf(ok, 12, False, "x", "f") == ok.ctypes.data
+    assert b._buf(None, 12, False, "x", "f") is None
+    for bad in (np.zeros((3, 5), np.float32), np.zeros((3, 4)), np.zeros((4, 3), np.float32).T,
+                torch.zeros(12)):
+        with pytest.raises(OpfError) as e:
+            b._buf(bad, 12, False, "x", "f")
+        assert e.value.status == 1 and "12 elements" in str(e.value)
+    # a host tensor is not a device buffer
+    with pytest.raises(OpfError, match="CUDA tensor"):
+        b._buf(torch.zeros(12), 12, True, "x", "f")
+
+
+def test_warm_start_network_arguments_are_checked(lib):
+    from paper_2410_17203_gb300 import OpfError, WarmStartNet, binding as b
+    with pytest.raises(OpfError, match="differ in length"):
+        WarmStartNet(4, [0, 1, 2], [1, 2], [1.0, 1.0, 1.0], 2, 3)
+    with pytest.raises(OpfError, match="params has 5 values"):
+        WarmStartNet(4, [0, 1, 2], [1, 2, 3], [1.0, 1.0, 1.0], 2, 3, params=np.zeros(5, np.float32))
+    assert b.opf_wsnet_param_count(3) == 64 * 3 + 64 + 3 * (2 * 64 * 64 + 64) + 64 * 2 + 2
