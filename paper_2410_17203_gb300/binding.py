@@ -279,7 +279,11 @@ def opf_create(case, options=None, stream=None):
     h = C.c_void_p()
     _check(lib.opf_create(C.byref(net), T, C.byref(ctg), C.byref(options), C.byref(h)),
            "opf_create")
-    _CTX_INFO[h.value] = opf_get_info(h)
+    try:
+        _CTX_INFO[h.value] = opf_get_info(h)
+    except OpfError:
+        lib.opf_destroy(h)
+        raise
     return h
 
 
