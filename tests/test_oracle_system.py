@@ -45,6 +45,46 @@ def test_three_bus_congested_matches_analytic():
     assert o.objective() == pytest.approx(exp["objective"], rel=1e-6)
 
 
+def test_three_bus_golden_is_the_lp_optimum():
+    """The hand-derived 3-bus values, re-derived by a linear program (HiGHS)
+    over the generator outputs with shift-factor flow limits; the nodal
+    prices are the LP cost's sensitivities to the load at each node."""
+    from scipy.optimize import linprog
+    case, exp = load_golden("three_bus_congested.json")
+    N, fr, to, b, u = 3, case["line_from"], case["line_to"], case["line_b"], case["line_u"]
+    inc = np.zeros((3, N))
+    inc[np.arange(3), fr] = 1.0
+    inc[np.arange(3), to] = -1.0
+    Bbus = inc.T @ np.diag(b) @ inc
+    X = np.zeros((N, N))
+    X[1:, 1:] = np.linalg.inv(Bbus[1:, 1:])
+    F = np.diag(b) @ inc @ X                            # flows = F @ injections
+    C = np.zeros((N, 2))
+    C[case["gen_node"], [0, 1]] = 1.0
+
+    def solve(load):
+        A = F @ C
+        res = linprog(case["gen_b"], A_ub=np.vstack([A, -A]),
+                      b_ub=np.concatenate([u + F @ load, u - F @ load]),
+                      A_eq=np.ones((1, 2)), b_eq=[load.sum()], bounds=[(0, 5), (0, 5)], method="highs")
+        assert res.status == 0
+        return res.x, res.fun
+
+    load = np.zeros(N)
+    np.add.at(load, case["load_node"], case["load_p"][:, 0])
+    g, f = solve(load)
+    np.testing.assert_allclose(g, exp["gen_p"], atol=1e-9)
+    assert f == pytest.approx(exp["objective"], abs=1e-9)
+    flow = F @ (C @ g - load)
+    np.testing.assert_allclose(flow, exp["line_flow"], atol=1e-9)
+    assert flow[0] / b[0] == pytest.approx(exp["angle_diff_n1_n3"], abs=1e-12)
+    assert flow[1] / b[1] == pytest.approx(exp["angle_diff_n1_n2"], abs=1e-12)
+    assert flow[2] / b[2] == pytest.approx(exp["angle_diff_n2_n3"], abs=1e-12)
+    h = 1e-4
+    prices = [(solve(load + h * np.eye(N)[n])[1] - f) / h for n in range(N)]
+    np.testing.assert_allclose(prices, exp["price"], atol=1e-6)
+
+
 def _single_bus_case(rng, T=3):
     G, D = 5, 4
     pmax = rng.uniform(1, 3, G)
