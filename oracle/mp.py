@@ -134,7 +134,9 @@ def prox_hvdc(x1, x2, u):
 
 
 def ramp_rows(pmin, pmax, R):
-    """Constraint rows ``A p <= h`` of a generator with box and ramp limits.
+    """Constraint rows ``A p <= h`` of a generator with box and ramp limits
+(the ramp-limited generator of Section 2.1, in the ``A x <= h`` form of
+Appendix D).
 
     Variables ``z = p`` (length T).  Rows: ``p_t <= pmax_t``,
     ``-p_t <= -pmin_t``, ``p_{t+1} - p_t <= R`` and ``p_t - p_{t+1} <= R``
@@ -151,7 +153,9 @@ def ramp_rows(pmin, pmax, R):
 
 
 def storage_layout(T):
-    """Index slices of ``z = (p, c, delta, s)`` for a battery with horizon T."""
+    """Index slices of ``z = (p, c, delta, s)`` for a battery with horizon T
+    (the storage device of Section 2.1: power, charge, discharge, state of
+    charge)."""
     return (slice(0, T), slice(T, 2 * T), slice(2 * T, 3 * T), slice(3 * T, 4 * T + 1))
 
 
@@ -432,6 +436,8 @@ class Oracle:
 
     # -- cached inner factorizations (Appendix D: reused while rho, omega fixed)
     def _factor(self):
+        """Inverse x-update matrices of the inner ADMM (Appendix D) at the
+        current device weight (K+1) rho_p, recomputed when it changes."""
         rho = self.Kp_total * self.rho_p
         if self._factored_rho == rho:
             return
@@ -453,7 +459,8 @@ class Oracle:
         """Set the iterate from a state dict with keys p_line, th1, th2, v1, v2
         ``[K+1, L, T]``, p_dev ``[S, T]``, u ``[K+1, N, T]`` and optionally
         ``inner`` (ramp generators then batteries, each lambda then beta over
-        the rows of ``ramp_rows`` / ``storage_rows``)."""
+        the rows of ``ramp_rows`` / ``storage_rows``): the warm start of
+        Section 3.4, which restarts the iteration from a given state."""
         net = self.net
         L = net.L
         f = lambda x: np.asarray(x, dtype=np.float64)
@@ -503,9 +510,11 @@ class Oracle:
         return self.p[0, self.net.sl_dev]
 
     def pbar(self):
+        """Node means of terminal power, ``[K+1, N, T]`` (Eq. average-op)."""
         return node_mean(self.net, self.p)
 
     def thbar(self):
+        """Node means of line-terminal angles, ``[K+1, N, T]`` (Eq. average-op)."""
         return node_mean(self.net, self.th, phase=True)
 
     def prices(self):
@@ -516,7 +525,8 @@ class Oracle:
         return -self.rho_p * s
 
     def objective(self):
-        """Sum of device costs at the current iterate (line costs are indicators)."""
+        """Sum of device costs at the current iterate, the objective of Eq.
+        contingency-dispatch (line costs are indicators)."""
         net = self.net
         pd = self.dev_p()
         pg = pd[:net.G]
@@ -531,6 +541,10 @@ class Oracle:
 
     # -- one iteration
     def step(self):
+        """One message-passing iteration (Section 3.2): step 1 the line proxes
+        of every contingency, step 2 the shared devices' proxes, step 3 the
+        node averages and scaled price updates, then the residuals of Section
+        3.3 and the adaptive penalty of Section 3.5."""
         if self.opts.alpha != 1.0:
             return self._step_relaxed()
         net = self.net
@@ -564,6 +578,8 @@ class Oracle:
         self._finish(p_new, th_new, u_new, v_new, r_pp, r_pt, r_dp, r_dt)
 
     def _finish(self, p_new, th_new, u_new, v_new, r_pp, r_pt, r_dp, r_dt):
+        """Store the new iterate and its residual parts (Section 3.3); adapt
+        the penalties on adaptation iterations (Section 3.5)."""
         self.res = np.array([np.hypot(r_pp, r_pt), np.hypot(r_dp, r_dt), r_pp, r_pt, r_dp, r_dt])
         self.p, self.th, self.u, self.v = p_new, th_new, u_new, v_new
         self.it += 1
@@ -673,18 +689,24 @@ class Oracle:
 
     # -- the two couplings across contingencies (reduced over a shard's peers)
     def _kmean(self, a):
-        """``(1/(K+1)) sum_k a_k`` over all contingencies."""
+        """``(1/(K+1)) sum_k a_k`` over all contingencies (the average over k
+        that step 2 of Section 3.2 takes for the shared devices)."""
         if self.shard is None:
             return np.mean(a, axis=0)
         return self.shard.allreduce(np.sum(a, axis=0)) / self.Kp_total
 
     def _norm(self, x):
-        """Euclidean norm over all contingencies."""
+        """Euclidean norm over all contingencies (the residual norms of
+        Section 3.3)."""
         if self.shard is None:
             return np.linalg.norm(x)
         return float(np.sqrt(self.shard.allreduce(np.array([np.sum(x * x)]))[0]))
 
     def _adapt(self, r_pp, r_pt, r_dp, r_dt):
+        """Residual balancing (Section 3.5): each penalty grows by gamma when
+        its primal part exceeds mu times its dual part, shrinks by gamma in
+        the opposite case; the scaled duals are rescaled by rho_old /
+        rho_new so that the unscaled duals stay fixed."""
         o = self.opts
 
         def rule(rho, rprim, rdual):
