@@ -89,7 +89,8 @@ class Unrolled:
 
     @staticmethod
     def _inner(x, A, h, eq, q, rho, Minv, beta, lam, n_iter):
-        """The inner ADMM of ``oracle.mp.inner_admm`` (omega = rho) on tensors."""
+        """The inner ADMM of ``oracle.mp.inner_admm`` (Appendix D, omega =
+        rho) on tensors, so that autograd differentiates through it."""
         n_p = x.shape[1]
         z = None
         for _ in range(n_iter):
@@ -103,7 +104,9 @@ class Unrolled:
         return z, beta, lam
 
     def params(self, requires_grad=True):
-        """The data the cost is differentiated with respect to, as leaf tensors."""
+        """The data the cost is differentiated with respect to (loads,
+        generator capacities, line limits: the sensitivities of Section 5.5),
+        as leaf tensors."""
         n = self.net
         out = dict(load_p=torch.tensor(n.load_p, dtype=torch.float64),
                    gen_pmax=torch.tensor(n.gen_pmax, dtype=torch.float64),
@@ -122,7 +125,9 @@ class Unrolled:
         return s / self.cnt[None, :, None]
 
     def run(self, prm, K, inner_iters=10):
-        """Iterate K times from zero; returns (cost f(p^K), final p_dev [S][T])."""
+        """Iterate K times from zero at fixed penalties (the unrolled map of
+        Section 4.4, each step the message-passing iteration of Section 3.2);
+        returns (cost f(p^K), final p_dev [S][T])."""
         n = self.net
         Kp, J, L, T = n.Kp, n.J, n.L, n.T
         G, D = n.G, n.D
