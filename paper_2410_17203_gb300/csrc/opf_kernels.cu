@@ -611,7 +611,7 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
     const float bb = p.line_b[l];
     ulim = p.line_u[l];
     tb = 2.f * bb;
-    den = 2.f * frp + frt / (tb * bb);   // denominator as derived in the oracle
+    den = 2.f * frp + frt / (tb * bb);   // 2 rho_p + rho_theta / (2 b^2), Section 4.2 (reading of the garbled print)
   }
   const float rden = __frcp_rn(den), rtb = __frcp_rn(tb);
   const float al = p.alpha, oma = 1.f - p.alpha;
