@@ -1,20 +1,26 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
-times (six kernels per iteration from CUDA graphs, adaptive penalty on).
+times (seven kernels per iteration from CUDA graphs, the adaptive penalty
+every 10 iterations, residuals formed on adaptation iterations and at the
+end of a call, the lean node pass on the others).
 
-* 2k buses, T = 24, K = 20: every state array after 10 iterations against
-  the oracle.
-* 10k buses, T = 96, K = 50: every state array after one iteration against
-  the oracle (one FP64 oracle iteration at this size takes tens of seconds),
-  and properties that hold at any iteration after 200 GPU iterations: line
+* 2k buses, T = 24, K = 20: every state array after 100 iterations (ten
+  adaptations) against the oracle sharded by contingency over the host's
+  cores, with the residuals and the penalties.
+* 10k buses, T = 96, K = 50: every state array after 10 iterations against
+  the sharded oracle -- nine lean node passes and one general pass with an
+  adaptation -- then 10 more iterations in a second call: the rescale of
+  the scaled duals pending from the adaptation is applied by the first
+  iteration of the next call.
+* 10k after 200 GPU iterations: properties that hold at any iteration (line
   flows within their limits, outaged lines carrying nothing, curtailable
-  loads within their boxes, and v_bar = 0 at every node and contingency.
+  loads within their boxes, v_bar = 0 at every node and contingency).
 """
 import numpy as np
 import pytest
 
 from gridgen import make_case
-from helpers import compare_states, oracle_arrays, compare_residuals
-from oracle import Oracle, OracleOptions
+from helpers import STATE_RTOL, compare_residuals
+from sharded_oracle import compare_with_sharded_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -29,40 +35,53 @@ def _lib():
     load_library()
 
 
-def _gpu_state(case, n):
+def _gpu_state(case, calls):
     from paper_2410_17203_gb300 import Solver
     s = Solver(case, dict(BENCH_OPTS))
-    s.iterate(n)
+    for n in calls:
+        s.iterate(n)
     st, res, info = s.state(), s.residuals(), s.get_info()
     s.close()
     return st, res, info
 
 
-def test_2k_ten_iterations_match_oracle():
+def _check(out, res, info, n):
+    bad = {k: e for k, e in out["rel_err"].items() if not e <= STATE_RTOL}
+    assert not bad, f"normwise relative error above {STATE_RTOL}: {bad} (all: {out['rel_err']})"
+    compare_residuals(res, out["res"], out["state_scale"])
+    assert info["iterations"] == n == out["it"]
+    # the same penalty decisions (Section 3.5), evaluated in FP64 on both sides
+    assert info["rho_p"] == pytest.approx(out["rho"][0], rel=1e-12)
+    assert info["rho_theta"] == pytest.approx(out["rho"][1], rel=1e-12)
+
+
+def test_2k_hundred_iterations_match_oracle(tmp_path):
     case = make_case("2k")
-    st, res, info = _gpu_state(case, 10)
-    o = Oracle(case, OracleOptions(**BENCH_OPTS))
-    o.iterate(10, stop=False)
-    compare_states(st, o)
-    scale = max(np.linalg.norm(a) for a in oracle_arrays(o).values())
-    compare_residuals(res, o.res, scale)
-    assert info["iterations"] == 10
+    st, res, info = _gpu_state(case, [100])
+    out = compare_with_sharded_oracle("2k", BENCH_OPTS, 100, st, str(tmp_path))
+    _check(out, res, info, 100)
+    assert len(out["rho_history"]) == 10
 
 
 @pytest.mark.slow
-def test_10k_one_iteration_matches_oracle():
+def test_10k_ten_iterations_match_oracle(tmp_path):
     case = make_case("10k")
-    st, res, info = _gpu_state(case, 1)
-    o = Oracle(case, OracleOptions(**BENCH_OPTS))
-    o.iterate(1, stop=False)
-    compare_states(st, o)
-    scale = max(np.linalg.norm(a) for a in oracle_arrays(o).values())
-    compare_residuals(res, o.res, scale)
+    st, res, info = _gpu_state(case, [10])
+    out = compare_with_sharded_oracle("10k", BENCH_OPTS, 10, st, str(tmp_path))
+    _check(out, res, info, 10)
+
+
+@pytest.mark.slow
+def test_10k_twenty_iterations_in_two_calls_match_oracle(tmp_path):
+    case = make_case("10k")
+    st, res, info = _gpu_state(case, [10, 10])
+    out = compare_with_sharded_oracle("10k", BENCH_OPTS, 20, st, str(tmp_path))
+    _check(out, res, info, 20)
 
 
 def test_10k_properties_after_200_iterations():
     case = make_case("10k")
-    st, res, info = _gpu_state(case, 200)
+    st, res, info = _gpu_state(case, [200])
     assert info["iterations"] == 200 and info["status"] == 0
     assert np.isfinite(res).all()
     pl = st["p_line"].astype(np.float64)

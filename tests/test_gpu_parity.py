@@ -179,6 +179,39 @@ def test_converged_objective_matches_oracle():
     assert sol["objective"] == pytest.approx(o.objective(), rel=1e-4)
 
 
+@pytest.mark.parametrize("spec", [dict(n_nodes=30, T=24, K=4, seed=24, stor_per_node=0.1),
+                                  dict(n_nodes=40, T=6, K=4, seed=21, stor_per_node=0.1)])
+def test_converged_objective_matches_oracle_multiperiod(spec):
+    """The setting the benchmark solves in: T > 1 with ramp-limited
+    generators and batteries (Appendix D inner ADMM, whose discharge
+    variable carries the storage cost), curtailable loads, four outages, the
+    adaptive penalty every 10 iterations.  Both sides run to eps = 1e-4
+    (Eq. converge); the objectives agree to 1e-4 relative and the GPU's
+    primal residual is within the tolerance, i.e. at most 1e-4 per terminal
+    in the RMS sense of Eq. (converge)."""
+    from paper_2410_17203_gb300 import Solver
+    case = make_case(scale_case(**spec))
+    assert len(case["stor_node"]) > 0 and (case["gen_ramp"] >= 0).all() and case["T"] > 1
+    opts = dict(adapt_every=10, eps=1e-4)
+    s = Solver(case, opts)
+    try:
+        s.iterate(30000)
+        info, res, sol = s.get_info(), s.residuals(), s.solution()
+    finally:
+        s.close()
+    o = Oracle(case, OracleOptions(**opts))
+    o.iterate(30000)
+    assert o.converged and info["converged"] == 1
+    assert max(res[0], res[1]) <= info["tolerance"]
+    assert info["tolerance"] == pytest.approx(o.tolerance(), rel=1e-12)
+    # primal residual per terminal (RMS over the 2 J T (K+1) entries) <= 1e-4
+    d = info
+    assert res[0] / np.sqrt(2.0 * d["J"] * d["T"] * (d["K"] + 1)) <= 1e-4
+    assert sol["objective"] == pytest.approx(o.objective(), rel=1e-4)
+    # the two sides stop within a few tests of each other
+    assert abs(info["iterations"] - o.it) <= 0.1 * o.it
+
+
 # ---------------------------------------------------------------------------
 # failure detection without a GPU fault
 # ---------------------------------------------------------------------------

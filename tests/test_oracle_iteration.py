@@ -232,3 +232,37 @@ def test_adaptation_rescales_scaled_duals():
     np.testing.assert_allclose(ora.rho_p * ora.u, shadow.rho_p * shadow.u, atol=1e-12)
     np.testing.assert_allclose(ora.rho_th * ora.v, shadow.rho_th * shadow.v, atol=1e-12)
     assert (ora.rho_p, ora.rho_th) != (1.0, 1.0)
+
+
+@pytest.mark.parametrize("part", ["p", "theta"])
+def test_adaptive_rule_direction_per_part(part):
+    """Section 3.5's case rule, pinned directly on residual pairs built on
+    each side of mu: a primal part above mu times its dual part multiplies
+    that part's penalty by gamma, a dual part above mu times the primal part
+    divides it by gamma, anything in between (including equality at mu,
+    the comparisons being strict) keeps it.  The other part's penalty is left
+    alone, and the scaled duals of the changed part are multiplied by
+    rho_old / rho_new (u for power, v for phase)."""
+    mu, gamma = 2.0, 1.1
+    case = make_case(scale_case(14, 4, 2, seed=11))
+    cases = [((3.0, 1.0), gamma), ((2.0 + 1e-9, 1.0), gamma), ((2.0, 1.0), 1.0), ((1.5, 1.0), 1.0),
+             ((1.0, 1.0), 1.0), ((1.0, 2.0), 1.0), ((1.0, 2.0 + 1e-9), 1 / gamma), ((1.0, 5.0), 1 / gamma),
+             ((0.0, 0.0), 1.0)]
+    for (rprim, rdual), factor in cases:
+        ora = Oracle(case, OracleOptions(adapt_every=10, mu=mu, gamma=gamma, rho_p=0.7, rho_theta=3.0))
+        for _ in range(3):
+            ora.step()
+        u0, v0 = ora.u.copy(), ora.v.copy()
+        # the other part sits exactly at balance (both zero): never changes
+        if part == "p":
+            ora._adapt(rprim, 0.0, rdual, 0.0)
+            assert ora.rho_p == pytest.approx(0.7 * factor, rel=1e-15), (rprim, rdual)
+            assert ora.rho_th == 3.0
+            np.testing.assert_allclose(ora.u, u0 / factor, rtol=1e-14, atol=0)
+            np.testing.assert_array_equal(ora.v, v0)
+        else:
+            ora._adapt(0.0, rprim, 0.0, rdual)
+            assert ora.rho_th == pytest.approx(3.0 * factor, rel=1e-15), (rprim, rdual)
+            assert ora.rho_p == 0.7
+            np.testing.assert_allclose(ora.v, v0 / factor, rtol=1e-14, atol=0)
+            np.testing.assert_array_equal(ora.u, u0)

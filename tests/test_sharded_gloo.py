@@ -90,3 +90,28 @@ def test_contingency_shards_reproduce_the_iteration(tmp_path, world, alpha, hvdc
         np.testing.assert_allclose(q["prices"], ref.prices(), rtol=1e-10, atol=1e-12)
     assert np.concatenate([q["k_ids"] for q in parts]).tolist() == list(range(ref.net.Kp))
     assert [len(q["k_ids"]) for q in parts] == [len(b) for b in np.array_split(np.arange(ref.net.Kp), world)]
+
+
+def test_sharded_comparison_helper_finds_agreement_and_a_planted_error(tmp_path):
+    """The helper the full-size GPU parity tests use: a state taken from the
+    unsharded oracle compares at FP64 rounding, and the same state with one
+    entry of one contingency changed is reported for that array only."""
+    from helpers import oracle_arrays
+    from oracle import Oracle, OracleOptions
+    from sharded_oracle import compare_with_sharded_oracle
+    spec = dict(n_nodes=40, T=4, K=5, seed=33)
+    opts = dict(adapt_every=10, eps=0.0)
+    ref = Oracle(make_case(scale_case(**spec)), OracleOptions(**opts))
+    ref.iterate(25, stop=False)
+    st = {k: np.array(v) for k, v in oracle_arrays(ref).items()}
+    (tmp_path / "a").mkdir()
+    out = compare_with_sharded_oracle(spec, opts, 25, st, str(tmp_path / "a"), world=3)
+    assert out["world"] == 3 and out["it"] == 25
+    assert max(out["rel_err"].values()) < 1e-12
+    np.testing.assert_allclose(out["res"], ref.res, rtol=1e-10)
+    assert out["rho"] == [ref.rho_p, ref.rho_th]
+    st["v2"][4, 7, 2] += 0.5 * np.abs(st["v2"]).max()
+    (tmp_path / "b").mkdir()
+    out = compare_with_sharded_oracle(spec, opts, 25, st, str(tmp_path / "b"), world=2)
+    assert out["rel_err"]["v2"] > 1e-3
+    assert max(v for k, v in out["rel_err"].items() if k != "v2") < 1e-12
