@@ -66,6 +66,12 @@ class OracleOptions:
     inner_iters: int = 10     # inner ADMM iterations per iterative prox (Appendix D)
     check_every: int = 10     # stopping test cadence (0 = never)
     alpha: float = 1.0        # over-relaxation parameter in [1, 2) (Section 3.6); 1 = plain ADMM
+    # Not in the paper (Section 3.5 adapts for the whole run): the residual
+    # balancing rule it takes from Boyd et al. (2011, Section 3.4.1) keeps
+    # ADMM's convergence guarantee only if the penalty stops changing after
+    # finitely many iterations.
+    adapt_until: int = 0      # last iteration that may adapt (0 = no limit)
+    stall_window: int = 0     # progress window of the stopping test (0 = off); see Oracle._stall
 
 
 # ---------------------------------------------------------------------------
@@ -407,6 +413,12 @@ class Oracle:
         self.res = np.zeros(6)
         self.converged = False
         self.rho_history = []
+        # the stall rule's state (Oracle._stall)
+        self.frozen_at = 0        # iteration at which the rule fixed the penalties (0 = never)
+        self.stalled = False
+        self.stall_ref = np.inf   # best max(||r_primal||, ||r_dual||) at a stopping test ...
+        self.stall_it = 0         # ... and the iteration where it was reached
+        self._conv_now = False    # the last iteration passed a stopping test
         # inner ADMM state of the iterative proxes
         self.ramp_idx = np.nonzero(net.is_ramp)[0]
         if len(self.ramp_idx):
@@ -482,6 +494,9 @@ class Oracle:
             self.rho_th = float(rho_theta)
         if it is not None:
             self.it = int(it)
+        # a warm start restarts the stall rule with adapting penalties
+        self.frozen_at, self.stalled = 0, False
+        self.stall_ref, self.stall_it = np.inf, self.it
         inner = st.get("inner")
         if inner is not None:
             x = f(inner)
@@ -578,15 +593,50 @@ class Oracle:
         self._finish(p_new, th_new, u_new, v_new, r_pp, r_pt, r_dp, r_dt)
 
     def _finish(self, p_new, th_new, u_new, v_new, r_pp, r_pt, r_dp, r_dt):
-        """Store the new iterate and its residual parts (Section 3.3); adapt
-        the penalties on adaptation iterations (Section 3.5)."""
+        """Store the new iterate and its residual parts (Section 3.3); on
+        stopping-test iterations the test of Eq. (converge) and the stall
+        rule; adapt the penalties on adaptation iterations (Section 3.5)."""
         self.res = np.array([np.hypot(r_pp, r_pt), np.hypot(r_dp, r_dt), r_pp, r_pt, r_dp, r_dt])
         self.p, self.th, self.u, self.v = p_new, th_new, u_new, v_new
         self.it += 1
-        # adaptive penalty (Section 3.5), every adapt_every iterations
         o = self.opts
-        if o.adapt_every and self.it % o.adapt_every == 0:
+        self._conv_now = False
+        if o.eps > 0 and o.check_every and self.it % o.check_every == 0:
+            self._conv_now = max(self.res[0], self.res[1]) <= self.tolerance()
+            if not self._conv_now and o.stall_window > 0:
+                self._stall()
+        # adaptive penalty (Section 3.5), every adapt_every iterations
+        if self._adapting() and self.it % o.adapt_every == 0:
             self._adapt(r_pp, r_pt, r_dp, r_dt)
+
+    def _adapting(self):
+        """Whether the penalties may still adapt at the current iteration."""
+        o = self.opts
+        return bool(o.adapt_every) and (o.adapt_until <= 0 or self.it <= o.adapt_until) and not self.frozen_at
+
+    def _stall(self):
+        """Stall rule at a stopping test that failed (not in the paper).  Let
+        m = max(||r_primal||, ||r_dual||).  When m falls below 0.99 times the
+        best value so far, that value and its iteration are recorded.  When
+        no such fall has happened for stall_window iterations:
+
+        * while the penalties still adapt, they are fixed from this iteration
+          on (ADMM with a penalty that stops changing converges for a
+          feasible convex problem; Boyd et al. 2011, Section 3.4.1) and the
+          window restarts;
+        * with fixed penalties the run is stalled: iteration stops (an
+          infeasible problem keeps a primal residual bounded away from zero).
+        """
+        o = self.opts
+        m = max(self.res[0], self.res[1])
+        if m < 0.99 * self.stall_ref:
+            self.stall_ref, self.stall_it = m, self.it
+        elif self.it - self.stall_it >= o.stall_window:
+            if self._adapting():
+                self.frozen_at = self.it
+                self.stall_ref, self.stall_it = m, self.it
+            else:
+                self.stalled = True
 
     def _step_relaxed(self):
         """One over-relaxed ADMM iteration (Section 3.6) in the original form
@@ -738,16 +788,20 @@ class Oracle:
         return self.opts.eps * np.sqrt(2.0 * n.J * n.T * self.Kp_total)
 
     def iterate(self, n_iters, stop=True):
-        """Run up to ``n_iters`` iterations; with ``stop`` the Eq. (converge) test
-        runs every ``check_every`` iterations.  Returns iterations run."""
-        o = self.opts
+        """Run up to ``n_iters`` iterations; with ``stop`` the run ends at the
+        first stopping test (every ``check_every`` iterations) that passes
+        Eq. (converge), or at a stall (``_stall``).  A stalled run restarts
+        its stall window here.  Returns iterations run."""
+        if self.stalled:
+            self.stalled = False
+            self.stall_ref, self.stall_it = np.inf, self.it
         done = 0
         for _ in range(n_iters):
             self.step()
             done += 1
-            if (stop and o.eps > 0 and o.check_every
-                    and self.it % o.check_every == 0
-                    and max(self.res[0], self.res[1]) <= self.tolerance()):
+            if stop and self._conv_now:
                 self.converged = True
+                break
+            if stop and self.stalled:
                 break
         return done
