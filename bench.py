@@ -398,13 +398,16 @@ def batch_instances(n, seed=3):
 
 def batched_vs_plain(stream, args):
     """Solve every instance to eps = 1e-4: one after another through
-    opf_iterate (plain), and all at once through one batch graph."""
+    opf_iterate (plain), and all at once through one batch graph.  With the
+    stall rule (--stall-window) an instance on which the adaptive penalty
+    cycles has its penalties fixed and goes on; one that stops falling at
+    fixed penalties stops with OPF_ESTALLED."""
     import torch
-    from paper_2410_17203_gb300 import (BATCH_LAYOUTS, opf_batch_autotune, opf_batch_converged, opf_batch_create,
-                                        opf_batch_destroy, opf_batch_iterate, opf_create, opf_destroy,
+    from paper_2410_17203_gb300 import (BATCH_LAYOUTS, opf_batch_autotune, opf_batch_create, opf_batch_destroy,
+                                        opf_batch_iterate, opf_batch_stopped, opf_create, opf_destroy,
                                         opf_get_info, opf_iterate, opf_reset)
     cases = batch_instances(args.batched)
-    opts = dict(adapt_every=10, eps=1e-4)
+    opts = dict(adapt_every=10, eps=1e-4, stall_window=args.stall_window)
     chunk = args.ttt_chunk
     plain = [opf_create(c, opts, stream=stream.cuda_stream) for c in cases]
     batch = [opf_create(c, opts, stream=stream.cuda_stream) for c in cases]
@@ -424,7 +427,8 @@ def batched_vs_plain(stream, args):
         while done < args.ttt_max:
             opf_iterate(h, chunk)
             done += chunk
-            if opf_get_info(h)["converged"]:
+            i = opf_get_info(h)
+            if i["converged"] or i["stalled"]:
                 break
         its_plain.append(int(opf_get_info(h)["iterations"]))
     t_plain = time.perf_counter() - t0
@@ -435,17 +439,22 @@ def batched_vs_plain(stream, args):
     while done < args.ttt_max:
         opf_batch_iterate(b, chunk)
         done += chunk
-        if opf_batch_converged(b) == len(batch):
+        if sum(opf_batch_stopped(b)) == len(batch):
             break
     t_batch = time.perf_counter() - t0
-    its_batch = [int(opf_get_info(h)["iterations"]) for h in batch]
-    n_conv = opf_batch_converged(b)
+    infos = [opf_get_info(h) for h in batch]
+    its_batch = [int(i["iterations"]) for i in infos]
+    n_conv, n_stall, n_err = opf_batch_stopped(b)
+    n_frozen_conv = sum(1 for i in infos if i["converged"] and i["frozen_at"] > 0)
     opf_batch_destroy(b)
     for h in plain + batch:
         opf_destroy(h)
-    return {"instances": len(cases), "eps": 1e-4,
+    return {"instances": len(cases), "eps": 1e-4, "stall_window": args.stall_window,
             "plain_seconds": t_plain, "batched_seconds": t_batch, "speedup": t_plain / t_batch,
-            "converged_batched": n_conv, "iterations_total": int(sum(its_plain)),
+            "converged_batched": n_conv, "stalled_batched": n_stall, "error_batched": n_err,
+            "at_cap_batched": len(batch) - n_conv - n_stall - n_err,
+            "converged_after_fixing_penalties": n_frozen_conv,
+            "iterations_total": int(sum(its_plain)),
             "iterations_equal": its_plain == its_batch,
             "autotune": {"seconds": t_tune, "chosen": BATCH_LAYOUTS[choice],
                          "ms_per_batch_iteration": dict(zip(BATCH_LAYOUTS, layout_ms))},
@@ -717,7 +726,7 @@ def ours_arm(args):
                        "adapt_every": 10},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": src,
-                         "traffic": (traffic * args.steps if traffic else None),
+                         "traffic": traffic,
                          "algorithmic_bytes_per_iteration": B,
                          "kernel": "one iteration: xs, inner, dsum, line, node and decide kernels "
                                    "replayed from CUDA graphs (unit = iteration; per-kernel shares in "
@@ -765,8 +774,11 @@ def main():
                          "(a quarter held out) and compare iterations to eps = 1e-4")
     ap.add_argument("--learned-epochs", type=int, default=60)
     ap.add_argument("--learned-lr", type=float, default=1e-3)
-    ap.add_argument("--batched", type=int, default=0,
-                    help="also solve this many independent instances to eps = 1e-4, one by one and as one batch")
+    ap.add_argument("--batched", type=int, default=64,
+                    help="also solve this many independent instances to eps = 1e-4, one by one and as one batch "
+                         "(0 = skip)")
+    ap.add_argument("--stall-window", type=int, default=3000,
+                    help="stall rule of the batched solves (include/opf.h opf_options.stall_window; 0 = off)")
     ap.add_argument("--adjoint", type=int, default=0,
                     help="also time the cost gradient after this many unrolled iterations on the 2k instance")
     ap.add_argument("--_oracle-child", dest="oracle_child", default=None)

@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define OPF_ABI_VERSION 4
+#define OPF_ABI_VERSION 5
 
 typedef struct opf_ctx opf_ctx; /* opaque, created by opf_create, freed by opf_destroy */
 
@@ -50,7 +50,10 @@ typedef enum {
                          queued GPU work after opf_options.sync_timeout_ms; the
                          work continues and a later call can wait again */
   OPF_ENONFINITE = 5, /* a residual became NaN or infinite; iteration stopped */
-  OPF_ESTATE = 6      /* the call does not apply to the context in its state */
+  OPF_ESTATE = 6,     /* the call does not apply to the context in its state */
+  OPF_ESTALLED = 7    /* the residuals stopped falling at fixed penalties
+                         (opf_options.stall_window); iteration stopped, and the
+                         next opf_iterate call continues */
 } opf_status;
 
 /*
@@ -107,7 +110,27 @@ typedef struct {
 
 /* Algorithm options.  opf_default_options fills the paper's defaults
  * (Section 5.2): rho_p = rho_theta = 1, mu = 2, gamma = 1.1, alpha = 1, adapt every 10
- * iterations, 10 inner iterations (Section 4.5), eps = 1e-4 tested every 10. */
+ * iterations, 10 inner iterations (Section 4.5), eps = 1e-4 tested every 10;
+ * no limit on the adaptation and no stall rule; a residual history of 4096
+ * rows.
+ *
+ * The penalty limit and the stall rule are not in the paper, which adapts the
+ * penalties for the whole run (Section 3.5).  The residual balancing rule it
+ * takes from Boyd et al. (2011, Section 3.4.1) keeps ADMM's convergence
+ * guarantee only when the penalties stop changing after finitely many
+ * iterations; applied for ever it can cycle (the residuals approach the
+ * tolerance, then grow again).
+ *   adapt_until   the last iteration that may adapt the penalties (0 = no limit).
+ *   stall_window  at every stopping test that fails, let m = max(||r_primal||,
+ *                 ||r_dual||).  When m falls below 0.99 times its best value
+ *                 so far, that value and its iteration are kept.  When it has
+ *                 not done so for stall_window iterations: while the penalties
+ *                 still adapt, they are fixed from that iteration on and the
+ *                 window restarts; with fixed penalties the call stops and
+ *                 reports OPF_ESTALLED.  An infeasible problem stalls (its
+ *                 primal residual stays bounded away from zero); so can a
+ *                 feasible one that converges very slowly, and the window
+ *                 sets how long to wait for a 1 % gain.  0 = off. */
 typedef struct {
   double rho_p, rho_theta;  /* initial penalties (> 0) */
   double eps;               /* Eq. (converge) tolerance; <= 0 disables stopping */
@@ -120,10 +143,13 @@ typedef struct {
   int32_t adapt_every;      /* penalty update cadence; 0 disables adaptation */
   int32_t inner_iters;      /* Appendix D iterations per iterative prox (>= 1) */
   int32_t check_every;      /* stopping test cadence; 0 disables stopping */
-  int32_t reserved0;
+  int32_t stall_window;     /* stall rule window in iterations (above); 0 = off */
   int64_t sync_timeout_ms;  /* longest wait of a synchronizing call for the
                                context's GPU work (OPF_ETIMEOUT after it); 0 = no limit */
   void *cuda_stream;        /* cudaStream_t to enqueue on; NULL = default stream */
+  int64_t adapt_until;      /* last iteration that may adapt the penalties; 0 = no limit */
+  int32_t history_len;      /* rows of residual history kept on the device (opf_history); 0 = none */
+  int32_t reserved0;
 } opf_options;
 
 /* Solver state, the iterate s = (p, theta, u, v) of Section 4.4 plus the
@@ -158,7 +184,9 @@ typedef struct {
   int64_t inner_len;
   int64_t device_bytes;     /* device memory held by the context */
   int32_t kernels_per_iteration; /* kernel launches one iteration makes */
-  int32_t reserved1;
+  int32_t stalled;          /* 1 when the last call stopped at a stall (OPF_ESTALLED) */
+  int64_t frozen_at;        /* iteration at which the stall rule fixed the penalties; 0 = never */
+  int64_t history_rows;     /* residual-history rows written since create / reset */
 } opf_info;
 
 /* Fill `opt` with the defaults listed above. */
@@ -183,8 +211,10 @@ opf_status opf_create(const opf_network *net, int32_t horizon_T,
  * a non-finite value is reported (OPF_ENONFINITE) at the first of these
  * after it appears.  rho > 0 first sets rho_p = rho_theta = rho, rescaling
  * the scaled duals (Section 3.5); rho <= 0 keeps the current (possibly
- * adapted) penalties.  After a passed stopping test or an error the
- * remaining iterations of the call return at once.  Asynchronous: the call
+ * adapted) penalties.  After a passed stopping test, a stall
+ * (opf_options.stall_window) or an error the remaining iterations of the
+ * call return at once; a call after a stall restarts the stall window, a
+ * call after an error does nothing.  Asynchronous: the call
  * only enqueues on the context's streams, ordered after the caller's stream
  * and before its later work; device errors surface at the next
  * synchronizing call. */
@@ -193,7 +223,8 @@ opf_status opf_iterate(opf_ctx *ctx, int32_t n_iters, double rho);
 /* Residuals of the last iteration run (Section 3.3), FP64:
  * out[0] = ||r_primal||, out[1] = ||r_dual||, out[2] = primal power part,
  * out[3] = primal phase part, out[4] = dual power part, out[5] = dual phase part.
- * Synchronizes; returns the sticky device status. */
+ * Synchronizes; returns the sticky device status, else OPF_ESTALLED when the
+ * last call stopped at a stall, else OPF_OK. */
 opf_status opf_residuals(opf_ctx *ctx, double out[6]);
 
 /* Solution at the current iterate.  Any pointer may be NULL.
@@ -206,6 +237,23 @@ opf_status opf_residuals(opf_ctx *ctx, double out[6]);
 opf_status opf_solution(opf_ctx *ctx, int32_t on_device, double *objective, float *p_dev,
                         float *p_line, float *theta_node, float *price);
 
+/* Residual history (Section 3.3), one row per iteration that formed its
+ * residuals: the stopping-test iterations (every check_every), the adaptation
+ * iterations (every adapt_every) and the last iteration of every call.  The
+ * decision kernel writes each row into a ring of opf_options.history_len rows
+ * on the device, so a convergence trace needs no host round trip.  Row layout
+ * (OPF_HISTORY_COLS doubles):
+ *   [0] iteration (1-based count after it)  [1] ||r_primal||  [2] ||r_dual||
+ *   [3..6] primal power, primal phase, dual power, dual phase parts
+ *   [7] rho_p, [8] rho_theta in force during the iteration
+ *   [9] flags: 1 converged, 2 penalties changed after it, 4 the stall rule fixed
+ *       the penalties, 8 stalled (OPF_ESTALLED), 16 non-finite
+ * rows [max_rows][OPF_HISTORY_COLS] host, caller-owned, receives the most
+ * recent min(max_rows, history_len, rows written) rows, oldest first;
+ * *n_rows their count.  Synchronizes. */
+#define OPF_HISTORY_COLS 10
+opf_status opf_history(opf_ctx *ctx, int32_t max_rows, double *rows, int32_t *n_rows);
+
 /* Nodal prices without any allocation: the same export as opf_solution's
  * `price`, staged through a fixed device array instead of a per-call device
  * buffer.  The paper has no counterpart; this is a serving convenience for
@@ -213,14 +261,16 @@ opf_status opf_solution(opf_ctx *ctx, int32_t on_device, double *objective, floa
  *   price   host float [N][T] (caller's node numbering), -rho_p * sum_k u_k
  * Scratch: one file-scope device array of OPF_PRICE_SCRATCH_FLOATS floats
  * (4 MiB) per device.  N * T above that returns OPF_EINVAL before any device
- * work.  Its address is resolved once per device by opf_create (so the first
- * price call never resolves it, e.g. during stream capture); the call itself
- * makes no cudaMalloc / cudaFree or allocating library call, on the device
- * or the host.  Every staged element is written before it is read, so nothing
- * needs clearing between calls.  The array is shared by all contexts of a
- * device: calls that overlap in time (from several threads, or on different
- * streams) race on it and must be serialized by the caller.
- * Synchronizes the context's stream. */
+ * work.  opf_create looks up the array's device address (with the context's
+ * device current) and keeps it in the context, so the call makes no symbol
+ * lookup; the call itself makes no cudaMalloc / cudaFree or allocating
+ * library call, on the device or the host.  Every staged element is written
+ * before it is read, so nothing needs clearing between calls.  The array is
+ * shared by all contexts of a device: calls that overlap in time (from
+ * several threads, or on different streams) race on it and must be
+ * serialized by the caller.  The call waits for the context's queued work
+ * and synchronizes its stream, so it must not be made while that stream is
+ * being captured into a CUDA graph. */
 #define OPF_PRICE_SCRATCH_FLOATS (1 << 20)
 opf_status opf_price_noalloc(opf_ctx *ctx, float *price);
 
@@ -235,8 +285,9 @@ opf_status opf_price_noalloc(opf_ctx *ctx, float *price);
  * opf_batch_iterate enqueues n_iters iterations of every instance after the
  * work already queued on each instance's stream, and orders each stream
  * after it.  Unlike opf_iterate it does not restart an instance that has
- * stopped (passed stopping test or error): such an instance's CTAs return at
- * once, so a batch can be iterated until every instance has converged.
+ * stopped (passed stopping test, stall or error): such an instance's CTAs
+ * return at once, so a batch can be iterated until every instance has
+ * stopped (opf_batch_stopped).
  * opf_batch_converged counts the converged instances (synchronizes).  The
  * contexts must outlive the batch; opf_batch_create allocates the device
  * copies of the instances' parameters and the schedule.  The instances of a
@@ -245,6 +296,9 @@ typedef struct opf_batch opf_batch;
 opf_status opf_batch_create(opf_ctx *const *ctxs, int32_t n, opf_batch **out);
 opf_status opf_batch_iterate(opf_batch *batch, int32_t n_iters);
 opf_status opf_batch_converged(opf_batch *batch, int32_t *n_converged);
+/* Stopped instances of a batch: converged, stalled (OPF_ESTALLED) and holding
+ * an error status; each pointer may be NULL.  Synchronizes. */
+opf_status opf_batch_stopped(opf_batch *batch, int32_t *n_converged, int32_t *n_stalled, int32_t *n_error);
 void opf_batch_destroy(opf_batch *batch);
 
 /* Pick the batch's CTA-to-instance schedule by timing.  Candidate layouts
@@ -272,11 +326,13 @@ opf_status opf_batch_autotune(opf_batch *batch, int32_t steps, int32_t *choice, 
 /* Export / import the full state (warm start, checkpoint and resume,
  * Section 3.4).  Import recomputes the node averages from p and theta and
  * projects v onto v_bar = 0 per node (Appendix C); it clears a sticky
- * OPF_ETIMEOUT / OPF_ESTATE.  Arrays left NULL on import are zeroed. */
+ * OPF_ETIMEOUT / OPF_ESTATE and restarts the stall rule with adapting
+ * penalties.  Arrays left NULL on import are zeroed. */
 opf_status opf_get_state(opf_ctx *ctx, int32_t on_device, const opf_state *dst);
 opf_status opf_set_state(opf_ctx *ctx, int32_t on_device, const opf_state *src);
 
-/* Zero the state (cold start), restore the initial penalties and counters. */
+/* Zero the state (cold start); restore the initial penalties, the counters,
+ * the stall rule and the residual history. */
 opf_status opf_reset(opf_ctx *ctx);
 
 opf_status opf_get_info(opf_ctx *ctx, opf_info *info);

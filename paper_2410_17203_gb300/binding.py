@@ -15,7 +15,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libopfmp.so")
 
-OPF_OK, OPF_EINVAL, OPF_ENOMEM, OPF_ECUDA, OPF_ETIMEOUT, OPF_ENONFINITE, OPF_ESTATE = range(7)
+OPF_OK, OPF_EINVAL, OPF_ENOMEM, OPF_ECUDA, OPF_ETIMEOUT, OPF_ENONFINITE, OPF_ESTATE, OPF_ESTALLED = range(8)
+OPF_HISTORY_COLS = 10  # doubles per residual-history row (opf_history)
 # capacity of the fixed device array behind opf_price_noalloc (N * T floats)
 OPF_PRICE_SCRATCH_FLOATS = 1 << 20
 OPF_WSNET_OUT = 2      # outputs per row of the warm-start network (price, angle)
@@ -54,9 +55,10 @@ class opf_options(C.Structure):
         ("rho_p", C.c_double), ("rho_theta", C.c_double), ("eps", C.c_double),
         ("mu", C.c_double), ("gamma", C.c_double), ("alpha", C.c_double),
         ("adapt_every", C.c_int32), ("inner_iters", C.c_int32), ("check_every", C.c_int32),
-        ("reserved0", C.c_int32),
+        ("stall_window", C.c_int32),
         ("sync_timeout_ms", C.c_int64),
         ("cuda_stream", C.c_void_p),
+        ("adapt_until", C.c_int64), ("history_len", C.c_int32), ("reserved0", C.c_int32),
     ]
 
 
@@ -73,16 +75,18 @@ class opf_info(C.Structure):
         ("N", C.c_int32), ("L", C.c_int32), ("S", C.c_int32), ("T", C.c_int32),
         ("K", C.c_int32), ("J", C.c_int32), ("n_ramp", C.c_int32), ("n_stor", C.c_int32),
         ("inner_len", C.c_int64), ("device_bytes", C.c_int64),
-        ("kernels_per_iteration", C.c_int32), ("reserved1", C.c_int32),
+        ("kernels_per_iteration", C.c_int32), ("stalled", C.c_int32),
+        ("frozen_at", C.c_int64), ("history_rows", C.c_int64),
     ]
 
 
-ABI_VERSION = 4     # OPF_ABI_VERSION of include/opf.h
+ABI_VERSION = 5     # OPF_ABI_VERSION of include/opf.h
 
 EXPORTS = ["opf_default_options", "opf_create", "opf_iterate", "opf_residuals", "opf_solution",
-           "opf_price_noalloc", "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info",
+           "opf_price_noalloc", "opf_history", "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info",
            "opf_destroy", "opf_status_str", "opf_last_error", "opf_abi_version",
-           "opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_destroy",
+           "opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_stopped",
+           "opf_batch_destroy",
            "opf_batch_autotune",
            "opf_wsnet_param_count", "opf_wsnet_create", "opf_wsnet_get_params", "opf_wsnet_set_params",
            "opf_wsnet_forward", "opf_wsnet_gradient", "opf_wsnet_train_step", "opf_wsnet_destroy",
@@ -113,6 +117,7 @@ def load_library(path=None):
     lib.opf_solution.argtypes = [C.c_void_p, C.c_int32, F64P, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]
     lib.opf_price_noalloc.argtypes = [C.c_void_p, C.c_void_p]
+    lib.opf_history.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]
     lib.opf_get_state.argtypes = [C.c_void_p, C.c_int32, C.POINTER(opf_state)]
     lib.opf_set_state.argtypes = [C.c_void_p, C.c_int32, C.POINTER(opf_state)]
     lib.opf_reset.argtypes = [C.c_void_p]
@@ -128,10 +133,13 @@ def load_library(path=None):
     lib.opf_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]
     lib.opf_batch_iterate.argtypes = [C.c_void_p, C.c_int32]
     lib.opf_batch_converged.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+    lib.opf_batch_stopped.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_int32)]
     lib.opf_batch_destroy.argtypes = [C.c_void_p]
     lib.opf_batch_destroy.restype = None
     lib.opf_batch_autotune.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), F64P]
-    for name in ("opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_autotune"):
+    for name in ("opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_stopped",
+                 "opf_batch_autotune"):
         getattr(lib, name).restype = C.c_int
     lib.opf_wsnet_param_count.argtypes = [C.c_int32]
     lib.opf_wsnet_param_count.restype = C.c_int64
@@ -158,7 +166,7 @@ def load_library(path=None):
     lib.opf_diff_destroy.restype = None
     for name in ("opf_diff_create", "opf_diff_cost_grad"):
         getattr(lib, name).restype = C.c_int
-    for name in ("opf_create", "opf_iterate", "opf_residuals", "opf_solution", "opf_price_noalloc",
+    for name in ("opf_create", "opf_iterate", "opf_residuals", "opf_solution", "opf_price_noalloc", "opf_history",
                  "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info"):
         getattr(lib, name).restype = C.c_int
     if path is None:
@@ -377,6 +385,20 @@ def opf_price_noalloc(h, out=None):
     return out
 
 
+def opf_history(h, max_rows=None):
+    """The residual history kept on the device (include/opf.h, opf_history):
+    an array [rows, OPF_HISTORY_COLS], oldest row first, of the most recent
+    ``max_rows`` rows (default: all that are kept)."""
+    if max_rows is None:
+        max_rows = int(opf_get_info(h)["history_rows"])
+    max_rows = max(0, int(max_rows))
+    out = np.zeros((max_rows, OPF_HISTORY_COLS), np.float64)
+    n = C.c_int32(0)
+    _check(load_library().opf_history(h, max_rows, out.ctypes.data if max_rows else None, C.byref(n)),
+           "opf_history")
+    return out[:n.value]
+
+
 def opf_batch_create(handles):
     """A batch over existing context handles (they must outlive it)."""
     arr = (C.c_void_p * len(handles))(*handles)
@@ -407,6 +429,13 @@ def opf_batch_converged(b):
     n = C.c_int32(0)
     _check(load_library().opf_batch_converged(b, C.byref(n)), "opf_batch_converged")
     return n.value
+
+
+def opf_batch_stopped(b):
+    """(converged, stalled, with an error status) instance counts of a batch."""
+    n = [C.c_int32(0) for _ in range(3)]
+    _check(load_library().opf_batch_stopped(b, *(C.byref(x) for x in n)), "opf_batch_stopped")
+    return tuple(x.value for x in n)
 
 
 def opf_batch_destroy(b):
@@ -630,6 +659,9 @@ class Solver:
 
     def residuals(self):
         return opf_residuals(self.h)
+
+    def history(self, max_rows=None):
+        return opf_history(self.h, max_rows)
 
     def get_info(self):
         return opf_get_info(self.h)

@@ -8,7 +8,6 @@
 #include <cstdio>
 #include <cstring>
 #include <chrono>
-#include <mutex>
 #include <thread>
 #include <string>
 #include <vector>
@@ -50,6 +49,7 @@ opf_status cuda_fail(cudaError_t e, const char *what) {
   } while (0)
 
 constexpr int kMaxT = 2048;
+constexpr int kMaxHistory = 1 << 20;  // rows of residual history a context may keep
 constexpr int kGraphIters = 16;  // iterations in the larger of the two iteration graphs
 
 // bump allocator over one cudaMalloc
@@ -108,8 +108,11 @@ void opf_default_options(opf_options *o) {
   o->adapt_every = 10;
   o->inner_iters = 10;
   o->check_every = 10;
+  o->stall_window = 0;
   o->sync_timeout_ms = 0;
   o->cuda_stream = nullptr;
+  o->adapt_until = 0;
+  o->history_len = 4096;
 }
 
 const char *opf_status_str(opf_status s) {
@@ -121,6 +124,7 @@ const char *opf_status_str(opf_status s) {
     case OPF_ETIMEOUT: return "GPU work still running at the synchronization timeout";
     case OPF_ENONFINITE: return "non-finite residual";
     case OPF_ESTATE: return "call does not apply to the context in its state";
+    case OPF_ESTALLED: return "residuals stopped falling at fixed penalties";
   }
   return "unknown status";
 }
@@ -227,6 +231,8 @@ opf_status validate(const opf_network *net, int T, const opf_contingencies *ctg,
   if (!(o.mu > 0) || !(o.gamma >= 1) || o.inner_iters < 1 || o.adapt_every < 0 || o.check_every < 0 ||
       !std::isfinite(o.eps))
     return fail(OPF_EINVAL, "invalid options");
+  if (o.stall_window < 0 || o.adapt_until < 0 || o.history_len < 0 || o.history_len > kMaxHistory)
+    return fail(OPF_EINVAL, "stall_window, adapt_until must be >= 0 and history_len in [0, 2^20]");
   return OPF_OK;
 }
 
@@ -289,6 +295,9 @@ void carve(opf_ctx *c, Arena &a) {
   p.stor_q = a.take<float>((size_t)c->n_stor * Tp);
   p.stor_rho = a.take<float>(c->n_stor);
   p.stor_delta = a.take<float>((size_t)c->n_stor * T);
+  // residual history: part of the mutable state that a batch autotune saves
+  // and restores
+  p.hist = a.take<double>((size_t)c->opt.history_len * opfk::HIST_COLS);
   c->state_bytes = a.off;
   p.sc = a.take<DevScalars>(1);
   // parameters
@@ -342,6 +351,7 @@ opf_status init_scalars(opf_ctx *c) {
   sc.su = 1.0;
   sc.sv = 1.0;
   sc.v_fresh = 1;
+  sc.stall_ref = HUGE_VAL;
   CK(cudaMemcpyAsync(c->P.sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return OPF_OK;
@@ -419,21 +429,16 @@ struct DevTmp {
 // so it exists once per device the library runs on and is never allocated.
 static __device__ __align__(256) float g_price_scratch[OPF_PRICE_SCRATCH_FLOATS];
 
-// Its address on each device, resolved once (cudaGetSymbolAddress) at
-// context creation, before any call can run inside a stream capture.
-constexpr int kMaxDevices = 64;
-float *g_price_scratch_addr[kMaxDevices] = {};
-std::mutex g_price_scratch_mu;
-
-opf_status resolve_price_scratch(int device, float **out) {
-  if (device < 0 || device >= kMaxDevices) return fail(OPF_EINVAL, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_price_scratch_mu);
-  if (!g_price_scratch_addr[device]) {
-    void *a = nullptr;
-    CK(cudaGetSymbolAddress(&a, g_price_scratch));
-    g_price_scratch_addr[device] = static_cast<float *>(a);
-  }
-  *out = g_price_scratch_addr[device];
+// Its address on the current device.  In host code the variable's name is a
+// host-side stand-in, never a device address, so the address is looked up
+// with cudaGetSymbolAddress -- by every opf_create, with the context's device
+// current, and kept in the context: a price call then makes no symbol lookup,
+// and no address outlives the CUDA context it was resolved in (a cache keyed
+// by device alone would go stale after cudaDeviceReset).
+opf_status resolve_price_scratch(float **out) {
+  void *a = nullptr;
+  CK(cudaGetSymbolAddress(&a, g_price_scratch));
+  *out = static_cast<float *>(a);
   return OPF_OK;
 }
 
@@ -614,7 +619,7 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
     return cuda_fail(e, "cudaGetDevice");
   }
   {
-    const opf_status ps = resolve_price_scratch(c->device, &c->price_scratch);
+    const opf_status ps = resolve_price_scratch(&c->price_scratch);
     if (ps != OPF_OK) {
       delete c;
       return ps;
@@ -694,6 +699,9 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   p.adapt_every = opt.adapt_every;
   p.check_every = opt.check_every;
   p.inner_iters = opt.inner_iters;
+  p.stall_window = opt.stall_window;
+  p.adapt_until = opt.adapt_until;
+  p.hist_cap = opt.history_len;
   c->tol = opt.eps * std::sqrt(2.0 * (2.0 * L + S) * T * c->Kp);
   p.tol = c->tol;
 
@@ -812,7 +820,8 @@ opf_status opf_residuals(opf_ctx *c, double out[6]) {
   opf_status s = read_scalars(c, &sc);
   if (s != OPF_OK) return s;
   for (int j = 0; j < 6; ++j) out[j] = sc.res[j];
-  return (opf_status)sc.status;
+  if (sc.status) return (opf_status)sc.status;
+  return sc.stalled ? OPF_ESTALLED : OPF_OK;
 }
 
 opf_status opf_get_info(opf_ctx *c, opf_info *info) {
@@ -844,6 +853,32 @@ opf_status opf_get_info(opf_ctx *c, opf_info *info) {
   info->inner_len = (int64_t)c->n_ramp * 2 * (4 * (int64_t)c->T - 2) +
                     (int64_t)c->n_stor * 2 * (8 * (int64_t)c->T + 4);
   info->device_bytes = (int64_t)c->arena_bytes;
+  info->stalled = sc.stalled;
+  info->frozen_at = sc.frozen_at;
+  info->history_rows = sc.hist_n;
+  return OPF_OK;
+}
+
+opf_status opf_history(opf_ctx *c, int32_t max_rows, double *rows, int32_t *n_rows) {
+  if (!c || !n_rows || (max_rows > 0 && !rows)) return fail(OPF_EINVAL, "NULL argument");
+  if (max_rows < 0) return fail(OPF_EINVAL, "max_rows must be >= 0");
+  DevScalars sc;
+  opf_status s = read_scalars(c, &sc);
+  if (s != OPF_OK) return s;
+  const long long cap = c->opt.history_len;
+  const long long n = std::min<long long>(std::min<long long>(sc.hist_n, cap), max_rows);
+  *n_rows = (int32_t)n;
+  if (n == 0) return OPF_OK;
+  // rows hist_n - n .. hist_n - 1, oldest first, in at most two pieces of the ring
+  const size_t row_bytes = opfk::HIST_COLS * sizeof(double);
+  const long long first = (sc.hist_n - n) % cap;
+  const long long n1 = std::min(n, cap - first);
+  CK(cudaMemcpyAsync(rows, c->P.hist + first * opfk::HIST_COLS, n1 * row_bytes, cudaMemcpyDeviceToHost,
+                     c->stream));
+  if (n > n1)
+    CK(cudaMemcpyAsync(rows + n1 * opfk::HIST_COLS, c->P.hist, (n - n1) * row_bytes, cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return OPF_OK;
 }
 
@@ -1237,6 +1272,23 @@ opf_status opf_batch_converged(opf_batch *b, int32_t *n_converged) {
   return OPF_OK;
 }
 
+opf_status opf_batch_stopped(opf_batch *b, int32_t *n_converged, int32_t *n_stalled, int32_t *n_error) {
+  if (!b) return fail(OPF_EINVAL, "NULL argument");
+  int32_t nc = 0, ns = 0, ne = 0;
+  for (opf_ctx *c : b->ctx) {
+    DevScalars sc;
+    const opf_status s = read_scalars(c, &sc);
+    if (s != OPF_OK) return s;
+    nc += sc.converged ? 1 : 0;
+    ns += sc.stalled ? 1 : 0;
+    ne += sc.status ? 1 : 0;
+  }
+  if (n_converged) *n_converged = nc;
+  if (n_stalled) *n_stalled = ns;
+  if (n_error) *n_error = ne;
+  return OPF_OK;
+}
+
 void opf_batch_destroy(opf_batch *b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
@@ -1410,6 +1462,11 @@ opf_status opf_set_state(opf_ctx *c, int32_t on_device, const opf_state *src) {
   sc.v_fresh = 1;
   sc.status = 0;
   sc.converged = 0;
+  // a warm start restarts the stall rule with adapting penalties
+  sc.stalled = 0;
+  sc.frozen_at = 0;
+  sc.stall_ref = HUGE_VAL;
+  sc.stall_it = sc.it;
   CK(cudaMemcpyAsync(c->P.sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   c->host_status = 0;

@@ -50,6 +50,16 @@ struct DevScalars {
                          // cleared at the start of every opf_iterate call
   long long it_last;     // the last iteration of the current call: residuals are formed
                          // there and at stopping-test and adaptation iterations only
+  // stall rule (opf_options.stall_window): best max(||r_primal||, ||r_dual||)
+  // at a stopping test and its iteration; the iteration at which the rule
+  // fixed the penalties (0 = they still adapt); 1 after a stall at fixed
+  // penalties (stops the call; the next opf_iterate restarts the window)
+  double stall_ref;
+  long long stall_it;
+  long long frozen_at;
+  int stalled;
+  int pad0;
+  long long hist_n;      // residual-history rows written (ring of Params::hist_cap rows)
 };
 
 // Battery group offsets inside lam/beta rows of stride Tp = T + 1.
@@ -117,7 +127,15 @@ struct Params {
   // options
   double eps, mu, gamma, tol;
   int adapt_every, check_every, inner_iters;
+  int stall_window;     // 0 = no stall rule
+  long long adapt_until;  // last iteration that may adapt (0 = no limit)
+  double *hist;         // residual history ring [hist_cap][HIST_COLS]
+  int hist_cap;
 };
+
+// columns of a residual-history row (include/opf.h, opf_history)
+constexpr int HIST_COLS = 10;
+enum { HF_CONVERGED = 1, HF_ADAPTED = 2, HF_FROZEN = 4, HF_STALLED = 8, HF_NONFINITE = 16 };
 
 // offsets of element (contingency k, line l / node n, step t)
 __host__ __device__ __forceinline__ size_t lidx(const Params &p, int k, int l, int t) {

@@ -801,6 +801,16 @@ struct Iter {
   int res;   // this iteration's residuals are read (stopping test, adaptation, end of the call)
 };
 
+// whether the penalties may still change after iteration itn (1-based):
+// adaptation on, within opf_options.adapt_until, not fixed by the stall rule
+__device__ __forceinline__ bool adapting(const Params &p, const DevScalars &sc, long long itn) {
+  return p.adapt_every > 0 && (p.adapt_until <= 0 || itn <= p.adapt_until) && sc.frozen_at == 0;
+}
+// iteration itn adapts the penalties (Section 3.5, every adapt_every iterations)
+__device__ __forceinline__ bool adapt_at(const Params &p, const DevScalars &sc, long long itn) {
+  return adapting(p, sc, itn) && itn % p.adapt_every == 0;
+}
+
 __device__ __forceinline__ Iter iter_scalars(const Params &p) {
   __shared__ Iter s;
   if (threadIdx.x == 0) {
@@ -816,8 +826,8 @@ __device__ __forceinline__ Iter iter_scalars(const Params &p) {
     r.v_fresh = sc.v_fresh;
     r.skip = (sc.status != 0 || sc.stop != 0) ? 1 : 0;
     const long long itn = sc.it + 1;
-    r.res = (p.adapt_every > 0 && itn % p.adapt_every == 0) ||
-            (p.eps > 0 && p.check_every > 0 && itn % p.check_every == 0) || itn >= sc.it_last;
+    r.res = adapt_at(p, sc, itn) || (p.eps > 0 && p.check_every > 0 && itn % p.check_every == 0) ||
+            itn >= sc.it_last;
     s = r;
   }
   __syncthreads();
@@ -1058,9 +1068,9 @@ __device__ __forceinline__ void decide_body(const Params &p, int n_part) {
   }
   DevScalars sc = *p.sc;
   const long long itn = sc.it + 1;
-  const bool adapt_now = p.adapt_every > 0 && (itn % p.adapt_every) == 0;
   const bool check_now = p.eps > 0 && p.check_every > 0 && (itn % p.check_every) == 0;
   const double rho_p = sc.rho_p, rho_th = sc.rho_th;
+  int flags = 0;
   const double r_pp = sqrt(fmax(tot[SL_PP], 0.0));
   const double r_pt = sqrt(fmax(tot[SL_PT], 0.0));
   const double r_dp = rho_p * sqrt(fmax(tot[SL_DP], 0.0));
@@ -1071,17 +1081,54 @@ __device__ __forceinline__ void decide_body(const Params &p, int n_part) {
   if (!isfinite(rp) || !isfinite(rd) || tot[SL_NF] != 0.0) {
     sc.status = ST_NONFINITE;
     sc.stop = 1;
+    flags |= HF_NONFINITE;
   } else {
-    if (check_now && fmax(rp, rd) <= p.tol) {
+    const double m = fmax(rp, rd);
+    if (check_now && m <= p.tol) {
       sc.converged = 1;
       sc.stop = 1;
+      flags |= HF_CONVERGED;
+    } else if (check_now && p.stall_window > 0) {
+      // stall rule (include/opf.h, opf_options): progress is a fall of the
+      // best m by 1 %; without it for stall_window iterations, fix adapting
+      // penalties, else stop with a stall
+      if (m < 0.99 * sc.stall_ref) {
+        sc.stall_ref = m;
+        sc.stall_it = itn;
+      } else if (itn - sc.stall_it >= p.stall_window) {
+        if (adapting(p, sc, itn)) {
+          sc.frozen_at = itn;
+          sc.stall_ref = m;
+          sc.stall_it = itn;
+          flags |= HF_FROZEN;
+        } else {
+          sc.stalled = 1;
+          sc.stop = 1;
+          flags |= HF_STALLED;
+        }
+      }
     }
-    if (adapt_now) {
+    if (adapt_at(p, sc, itn)) {   // Section 3.5 (strict comparisons, FP64)
       if (r_pp > p.mu * r_dp) nrp = rho_p * p.gamma;
       else if (r_dp > p.mu * r_pp) nrp = rho_p / p.gamma;
       if (r_pt > p.mu * r_dt) nrt = rho_th * p.gamma;
       else if (r_dt > p.mu * r_pt) nrt = rho_th / p.gamma;
+      if (nrp != rho_p || nrt != rho_th) flags |= HF_ADAPTED;
     }
+  }
+  if (p.hist_cap > 0) {   // residual history ring (opf_history)
+    double *row = p.hist + (size_t)(sc.hist_n % p.hist_cap) * HIST_COLS;
+    row[0] = (double)itn;
+    row[1] = rp;
+    row[2] = rd;
+    row[3] = r_pp;
+    row[4] = r_pt;
+    row[5] = r_dp;
+    row[6] = r_dt;
+    row[7] = rho_p;
+    row[8] = rho_th;
+    row[9] = (double)flags;
+    sc.hist_n += 1;
   }
   sc.res[0] = rp; sc.res[1] = rd; sc.res[2] = r_pp; sc.res[3] = r_pt; sc.res[4] = r_dp; sc.res[5] = r_dt;
   sc.su = rho_p / nrp;   // pending rescale of u and v (Section 3.5), applied on their next read
@@ -1370,7 +1417,14 @@ __global__ void export_pdev_kernel(Params p, float *out) {
 }
 
 __global__ void begin_kernel(DevScalars *sc, long long n, int clear_stop) {
-  if (clear_stop) sc->stop = 0;
+  if (clear_stop) {
+    sc->stop = 0;
+    if (sc->stalled) {   // a new call after a stall restarts the stall window
+      sc->stalled = 0;
+      sc->stall_ref = HUGE_VAL;
+      sc->stall_it = sc->it;
+    }
+  }
   sc->it_last = sc->it + n;
 }
 

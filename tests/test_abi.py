@@ -40,6 +40,16 @@ def test_every_declared_function_is_exported(lib):
     assert set(names) == set(binding.EXPORTS)
 
 
+def test_history_columns_and_status_codes_match_header():
+    from paper_2410_17203_gb300 import binding
+    h = open(HEADER).read()
+    m = re.search(r"#define OPF_HISTORY_COLS (\d+)", h)
+    assert m and binding.OPF_HISTORY_COLS == int(m.group(1))
+    for name in ("OPF_ESTATE", "OPF_ESTALLED", "OPF_ENONFINITE"):
+        m = re.search(name + r" = (\d+)", h)
+        assert m and getattr(binding, name) == int(m.group(1)), name
+
+
 def test_price_scratch_capacity_matches_header():
     from paper_2410_17203_gb300 import binding
     m = re.search(r"#define OPF_PRICE_SCRATCH_FLOATS \(1 << (\d+)\)", open(HEADER).read())
@@ -48,8 +58,8 @@ def test_price_scratch_capacity_matches_header():
 
 def test_abi_version_and_status_strings(lib):
     from paper_2410_17203_gb300 import binding as b
-    assert b.opf_abi_version() == 4
-    for s in range(7):
+    assert b.opf_abi_version() == 5
+    for s in range(8):
         assert b.opf_status_str(s) not in ("", "unknown status")
     assert b.opf_status_str(99) == "unknown status"
 
@@ -59,6 +69,8 @@ def test_default_options_are_the_papers(lib):
     o = opf_default_options()
     assert (o.rho_p, o.rho_theta, o.mu, o.gamma) == (1.0, 1.0, 2.0, 1.1)
     assert (o.adapt_every, o.inner_iters, o.check_every, o.eps) == (10, 10, 10, 1e-4)
+    # no limit on the adaptation and no stall rule (Section 3.5 adapts for the whole run)
+    assert (o.adapt_until, o.stall_window, o.history_len) == (0, 0, 4096)
 
 
 def test_ctypes_layout_matches_c(lib, tmp_path):

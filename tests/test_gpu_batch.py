@@ -148,3 +148,67 @@ def test_over_relaxed_batch_equals_single_and_mixing_is_rejected():
         opf_batch_destroy(b)
         for s in batch_solvers + single:
             s.close()
+
+
+@pytest.mark.parametrize("alpha", [1.0, 1.5])
+def test_batch_iterates_match_the_oracle(alpha):
+    """Every instance of a batch (uneven sizes, T from 1 to 150, outages,
+    HVDC links, device-free nodes), after 37 batch iterations in three calls
+    (graphs of 1 and 16 iterations) with the adaptive penalty, against the
+    FP64 oracle run on that instance alone: normwise 1e-5 per state array,
+    the same penalties."""
+    from helpers import compare_states
+    from oracle import Oracle, OracleOptions
+    from paper_2410_17203_gb300 import Solver, opf_batch_create, opf_batch_destroy, opf_batch_iterate
+    opts = dict(adapt_every=10, eps=0.0, alpha=alpha)
+    cases = _cases()
+    solvers = [Solver(c, opts) for c in cases]
+    b = opf_batch_create([s.h for s in solvers])
+    try:
+        for n in (3, 16, 18):
+            opf_batch_iterate(b, n)
+        for s, c in zip(solvers, cases):
+            o = Oracle(c, OracleOptions(**opts))
+            o.iterate(37, stop=False)
+            compare_states(s.state(), o)
+            info = s.get_info()
+            assert (info["rho_p"], info["rho_theta"]) == pytest.approx((o.rho_p, o.rho_th), rel=1e-12)
+    finally:
+        opf_batch_destroy(b)
+        for s in solvers:
+            s.close()
+
+
+def test_batched_workload_instances_match_the_oracle():
+    """Instances drawn by the batched workload's recipe (buses log-uniform in
+    [100, 5000], T in {1, 24, 48}, 0..20 outages; the smaller ones, so that
+    the oracle finishes in seconds), batched after autotuning, against the
+    oracle after 30 iterations."""
+    from helpers import compare_states
+    from oracle import Oracle, OracleOptions
+    from paper_2410_17203_gb300 import (Solver, opf_batch_autotune, opf_batch_create, opf_batch_destroy,
+                                        opf_batch_iterate)
+    rng = np.random.default_rng(3)
+    specs = []
+    for i in range(40):
+        nb = int(round(float(np.exp(rng.uniform(np.log(100), np.log(5000))))))
+        T = int(rng.choice([1, 24, 48]))
+        K = int(rng.integers(0, 21))
+        if nb * T * (K + 1) <= 200000:
+            specs.append(scale_case(nb, T, K, seed=1000 + i, lines_per_node=1.5))
+    assert len(specs) >= 4
+    cases = [make_case(sp) for sp in specs]
+    opts = dict(adapt_every=10, eps=0.0)
+    solvers = [Solver(c, opts) for c in cases]
+    b = opf_batch_create([s.h for s in solvers])
+    try:
+        opf_batch_autotune(b, steps=4)
+        opf_batch_iterate(b, 30)
+        for s, c in zip(solvers, cases):
+            o = Oracle(c, OracleOptions(**opts))
+            o.iterate(30, stop=False)
+            compare_states(s.state(), o)
+    finally:
+        opf_batch_destroy(b)
+        for s in solvers:
+            s.close()

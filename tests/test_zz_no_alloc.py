@@ -67,16 +67,50 @@ def test_two_contexts_use_the_same_array_one_after_the_other():
         s2.close()
 
 
-def test_too_large_network_is_rejected_before_device_work():
-    from paper_2410_17203_gb300 import OpfError, Solver, opf_price_noalloc
+def test_largest_network_is_exported_in_full():
+    """N * T exactly OPF_PRICE_SCRATCH_FLOATS (1024 buses, T = 1024): every
+    element of the array is staged and copied out."""
+    from paper_2410_17203_gb300 import Solver, opf_price_noalloc
     from paper_2410_17203_gb300.binding import OPF_PRICE_SCRATCH_FLOATS
-    case = make_case(scale_case(1200, 900, 0, seed=5, stor_per_node=0.0))
-    assert case["n_nodes"] * case["T"] > OPF_PRICE_SCRATCH_FLOATS
+    case = make_case(scale_case(1024, 1024, 0, seed=6, stor_per_node=0.0))
+    assert case["n_nodes"] * case["T"] == OPF_PRICE_SCRATCH_FLOATS
     s = Solver(case, dict(eps=0.0))
     try:
+        s.iterate(7)
+        out = np.full((case["n_nodes"], case["T"]), np.nan, np.float32)
+        opf_price_noalloc(s.h, out)
+        ref = _price_via_solution(s)
+        np.testing.assert_array_equal(out, ref)
+        assert np.isfinite(out).all() and np.abs(out).max() > 0
+    finally:
+        s.close()
+
+
+def test_network_above_the_limit_is_rejected_and_the_context_still_works():
+    """N * T one row of T above the capacity (1025 buses, T = 1024): the call
+    fails with OPF_EINVAL, leaves the output untouched, and the context's
+    iterate and later calls are unaffected."""
+    from paper_2410_17203_gb300 import OpfError, Solver, opf_price_noalloc
+    from paper_2410_17203_gb300.binding import OPF_PRICE_SCRATCH_FLOATS
+    case = make_case(scale_case(1025, 1024, 0, seed=5, stor_per_node=0.0))
+    assert case["n_nodes"] * case["T"] == OPF_PRICE_SCRATCH_FLOATS + 1024
+    s = Solver(case, dict(eps=0.0))
+    try:
+        s.iterate(3)
+        before = s.state()
+        out = np.full((case["n_nodes"], case["T"]), 7.0, np.float32)
         with pytest.raises(OpfError) as e:
-            opf_price_noalloc(s.h, np.zeros((case["n_nodes"], case["T"]), np.float32))
+            opf_price_noalloc(s.h, out)
         assert e.value.status == 1
         assert "OPF_PRICE_SCRATCH_FLOATS" in str(e.value)
+        assert np.all(out == 7.0)
+        assert s.get_info()["iterations"] == 3
+        after = s.state()
+        for k in before:
+            np.testing.assert_array_equal(before[k], after[k], err_msg=k)
+        price = _price_via_solution(s)
+        assert np.isfinite(price).all()
+        s.iterate(2)
+        assert s.get_info()["iterations"] == 5
     finally:
         s.close()
