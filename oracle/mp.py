@@ -14,8 +14,8 @@ stores node-constant quantities per node; ``u`` is node-constant because
 Terminal order: terminal 1 of every line, terminal 2 of every line, then
 generators, loads and batteries (one terminal each).
 
-Readings of passages where the paper is garbled or silent (each is listed
-with its reason in the design notes of the repository):
+Readings of passages where the paper is garbled or silent, each with the
+reason it is taken:
 
 * generator prox: ``clip((rho x - b) / (2 a + rho), pmin, pmax)`` -- Section
   4.2 prints the fraction upside down;
