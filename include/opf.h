@@ -331,6 +331,24 @@ opf_status opf_batch_autotune(opf_batch *batch, int32_t steps, int32_t *choice, 
 opf_status opf_get_state(opf_ctx *ctx, int32_t on_device, const opf_state *dst);
 opf_status opf_set_state(opf_ctx *ctx, int32_t on_device, const opf_state *src);
 
+/* Starting state from nodal prices and node angles -- the learned warm
+ * start's network output (include/opf_wsnet.h) or any other estimate; the
+ * paper's warm start (Section 3.4) imports a whole previous state through
+ * opf_set_state instead.  rows [T][N][stride] floats in the caller's node
+ * numbering (host, or device when on_device): rows[(t N + n) stride] is the
+ * price of node n at step t divided by price_scale, rows[(t N + n) stride + 1]
+ * its angle; other columns are ignored (stride >= 2).  The state: u_k =
+ * -price / (rho_p (K+1)) in every contingency at the context's current
+ * rho_p (the prices are -rho_p sum_k u_k, opf_solution), every line terminal
+ * at its node's angle, line power b (theta1 - theta2) clipped to the limit
+ * (0 on the outaged line of a contingency), v = 0, device powers and inner
+ * duals 0; the node averages are formed from it.  Like opf_set_state it
+ * clears a sticky OPF_ETIMEOUT / OPF_ESTATE and restarts the stall rule.
+ * With host rows the call stages them through a temporary device buffer.
+ * Synchronizes. */
+opf_status opf_set_state_from_nodes(opf_ctx *ctx, int32_t on_device, const float *rows, int32_t stride,
+                                    double price_scale);
+
 /* Zero the state (cold start); restore the initial penalties, the counters,
  * the stall rule and the residual history. */
 opf_status opf_reset(opf_ctx *ctx);

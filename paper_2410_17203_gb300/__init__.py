@@ -8,6 +8,6 @@ from .binding import (  # noqa: F401
     opf_batch_autotune, opf_batch_converged, opf_batch_create,
     opf_batch_destroy, opf_batch_iterate, opf_batch_stopped, opf_create, opf_default_options,
     opf_destroy, opf_get_info, opf_get_state, opf_history, opf_iterate, opf_last_error, opf_reset,
-    opf_price_noalloc, opf_residuals, opf_set_state, opf_solution, opf_status_str, state_shapes,
+    opf_price_noalloc, opf_residuals, opf_set_state, opf_set_state_from_nodes, opf_solution, opf_status_str, state_shapes,
     unrolled_cost,
 )

@@ -83,14 +83,14 @@ class opf_info(C.Structure):
 ABI_VERSION = 5     # OPF_ABI_VERSION of include/opf.h
 
 EXPORTS = ["opf_default_options", "opf_create", "opf_iterate", "opf_residuals", "opf_solution",
-           "opf_price_noalloc", "opf_history", "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info",
+           "opf_price_noalloc", "opf_history", "opf_set_state_from_nodes", "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info",
            "opf_destroy", "opf_status_str", "opf_last_error", "opf_abi_version",
            "opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_stopped",
            "opf_batch_destroy",
            "opf_batch_autotune",
            "opf_wsnet_param_count", "opf_wsnet_create", "opf_wsnet_get_params", "opf_wsnet_set_params",
            "opf_wsnet_forward", "opf_wsnet_gradient", "opf_wsnet_train_step", "opf_wsnet_destroy",
-           "opf_diff_create", "opf_diff_cost_grad", "opf_diff_destroy"]
+           "opf_diff_create", "opf_diff_cost_grad", "opf_diff_cost_grad_on", "opf_diff_destroy"]
 
 _lib = None
 
@@ -118,6 +118,7 @@ def load_library(path=None):
                                  C.c_void_p, C.c_void_p]
     lib.opf_price_noalloc.argtypes = [C.c_void_p, C.c_void_p]
     lib.opf_history.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]
+    lib.opf_set_state_from_nodes.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_double]
     lib.opf_get_state.argtypes = [C.c_void_p, C.c_int32, C.POINTER(opf_state)]
     lib.opf_set_state.argtypes = [C.c_void_p, C.c_int32, C.POINTER(opf_state)]
     lib.opf_reset.argtypes = [C.c_void_p]
@@ -162,11 +163,14 @@ def load_library(path=None):
                                     C.c_double, C.c_double, C.c_int32, C.c_void_p,
                                     C.POINTER(C.c_void_p)]
     lib.opf_diff_cost_grad.argtypes = [C.c_void_p, C.c_int32, F32P, F32P, F32P, F64P, F32P, F32P, F32P]
+    lib.opf_diff_cost_grad_on.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          F64P, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.opf_diff_destroy.argtypes = [C.c_void_p]
     lib.opf_diff_destroy.restype = None
-    for name in ("opf_diff_create", "opf_diff_cost_grad"):
+    for name in ("opf_diff_create", "opf_diff_cost_grad", "opf_diff_cost_grad_on"):
         getattr(lib, name).restype = C.c_int
     for name in ("opf_create", "opf_iterate", "opf_residuals", "opf_solution", "opf_price_noalloc", "opf_history",
+                 "opf_set_state_from_nodes",
                  "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info"):
         getattr(lib, name).restype = C.c_int
     if path is None:
@@ -556,6 +560,22 @@ class UnrolledCost:
                "opf_diff_cost_grad")
         return f.value, (g if grads else None)
 
+    def cost_grad_device(self, K, load_p, gen_pmax, line_u, grads=True):
+        """The same with CUDA tensors (float32, contiguous; None = the case's
+        own data): returns (f, dict of gradient tensors on the same device)."""
+        import torch
+        shapes = dict(load_p=(self.D, self.T), gen_pmax=(self.G, self.T), line_u=(self.L,))
+        ins = dict(load_p=load_p, gen_pmax=gen_pmax, line_u=line_u)
+        dev = next((x.device for x in ins.values() if x is not None), torch.device("cuda"))
+        ptr = {k: (None if x is None else _buf(x, int(np.prod(shapes[k])), True, k, "opf_diff_cost_grad_on"))
+               for k, x in ins.items()}
+        g = {k: torch.zeros(s, dtype=torch.float32, device=dev) for k, s in shapes.items()} if grads else None
+        gp = [g[k].data_ptr() if grads else None for k in ("load_p", "gen_pmax", "line_u")]
+        f = C.c_double(0.0)
+        _check(load_library().opf_diff_cost_grad_on(self.h, int(K), 1, ptr["load_p"], ptr["gen_pmax"],
+                                                    ptr["line_u"], C.byref(f), *gp), "opf_diff_cost_grad_on")
+        return f.value, g
+
     def close(self):
         if self.h:
             load_library().opf_diff_destroy(self.h)
@@ -580,11 +600,19 @@ def _unrolled_fn():
             @staticmethod
             def forward(ctx, diff, K, load_p, gen_pmax, line_u):
                 want = any(ctx.needs_input_grad[2:])
-                host = [x.detach().to("cpu", torch.float32).numpy() for x in (load_p, gen_pmax, line_u)]
-                f, g = diff.cost_grad(K, *host, grads=want)
-                if want:
-                    ctx.save_for_backward(*[torch.from_numpy(g[k]).to(x.device, x.dtype) for k, x in
-                                            zip(("load_p", "gen_pmax", "line_u"), (load_p, gen_pmax, line_u))])
+                xs = (load_p, gen_pmax, line_u)
+                if all(x.is_cuda for x in xs):
+                    # device tensors go to the library as they are
+                    dv = [x.detach().to(torch.float32).contiguous() for x in xs]
+                    f, g = diff.cost_grad_device(K, *dv, grads=want)
+                    if want:
+                        ctx.save_for_backward(*[g[k].to(x.dtype) for k, x in zip(("load_p", "gen_pmax", "line_u"), xs)])
+                else:
+                    host = [x.detach().to("cpu", torch.float32).numpy() for x in xs]
+                    f, g = diff.cost_grad(K, *host, grads=want)
+                    if want:
+                        ctx.save_for_backward(*[torch.from_numpy(g[k]).to(x.device, x.dtype) for k, x in
+                                                zip(("load_p", "gen_pmax", "line_u"), xs)])
                 return torch.tensor(f, dtype=load_p.dtype, device=load_p.device)
 
             @staticmethod
@@ -641,6 +669,25 @@ def opf_set_state(h, state, on_device=False):
         ptrs[k] = _buf(x, n[k], bool(on_device), k, "opf_set_state")
     st = opf_state(**ptrs)
     _check(load_library().opf_set_state(h, int(bool(on_device)), C.byref(st)), "opf_set_state")
+
+
+def opf_set_state_from_nodes(h, rows, price_scale, on_device=False):
+    """Starting state from node rows [T * N, stride] (price / price_scale,
+    angle, ...): a float32 CUDA tensor with on_device, else a NumPy array."""
+    info = _ctx_info(h)
+    R = info["N"] * info["T"]
+    if on_device:
+        if not (hasattr(rows, "data_ptr") and rows.dim() == 2 and rows.shape[0] == R):
+            raise OpfError(OPF_EINVAL, "opf_set_state_from_nodes", f"rows must be a [{R}, stride] CUDA tensor")
+        stride = int(rows.shape[1])
+    else:
+        rows = np.ascontiguousarray(np.asarray(rows, np.float32))
+        if rows.ndim != 2 or rows.shape[0] != R:
+            raise OpfError(OPF_EINVAL, "opf_set_state_from_nodes", f"rows must have shape [{R}, stride]")
+        stride = int(rows.shape[1])
+    ptr = _buf(rows, R * stride, bool(on_device), "rows", "opf_set_state_from_nodes")
+    _check(load_library().opf_set_state_from_nodes(h, int(bool(on_device)), ptr, stride, float(price_scale)),
+           "opf_set_state_from_nodes")
 
 
 def opf_reset(h):

@@ -1473,6 +1473,57 @@ opf_status opf_set_state(opf_ctx *c, int32_t on_device, const opf_state *src) {
   return OPF_OK;
 }
 
+opf_status opf_set_state_from_nodes(opf_ctx *c, int32_t on_device, const float *rows, int32_t stride,
+                                    double price_scale) {
+  if (!c || !rows) return fail(OPF_EINVAL, "NULL argument");
+  if (stride < 2) return fail(OPF_EINVAL, "stride must be >= 2 (price, angle)");
+  if (!(price_scale > 0) || !std::isfinite(price_scale)) return fail(OPF_EINVAL, "price_scale must be finite and > 0");
+  DevScalars sc;
+  opf_status s;
+  if ((s = read_scalars(c, &sc)) != OPF_OK) return s;
+  const int cur = (int)(sc.it & 1);
+  const size_t n_rows = (size_t)c->T * c->N * stride;
+  DevTmp tmp;
+  const float *src = rows;
+  if (!on_device) {
+    if ((s = alloc_tmp(tmp, n_rows)) != OPF_OK) return s;
+    CK(cudaMemcpyAsync(tmp.p, rows, n_rows * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    src = tmp.p;
+  }
+  // u = -price / (rho_p (K+1)) at the penalty in force
+  const float u_scale = (float)(1.0 / (sc.rho_p * c->Kp));
+  if (opfk_start_from_nodes_launch(c->P, cur, src, stride, (float)price_scale, u_scale, c->stream) != 0)
+    return fail(OPF_ECUDA, "start launch failed");
+  // device powers and the inner duals from zero (factors rebuilt on first use)
+  const size_t ST = (size_t)c->S * c->T;
+  const size_t nr = (size_t)c->n_ramp * opfk::RG_N * c->T, ns = (size_t)c->n_stor * opfk::SG_N * (c->T + 1);
+  CK(cudaMemsetAsync(c->P.PD, 0, ST * 4, c->stream));
+  if (nr) {
+    CK(cudaMemsetAsync(c->P.ramp_lam, 0, nr * 4, c->stream));
+    CK(cudaMemsetAsync(c->P.ramp_beta, 0, nr * 4, c->stream));
+    CK(cudaMemsetAsync(c->P.ramp_rho, 0, c->n_ramp * 4, c->stream));
+  }
+  if (ns) {
+    CK(cudaMemsetAsync(c->P.stor_lam, 0, ns * 4, c->stream));
+    CK(cudaMemsetAsync(c->P.stor_beta, 0, ns * 4, c->stream));
+    CK(cudaMemsetAsync(c->P.stor_rho, 0, c->n_stor * 4, c->stream));
+  }
+  if (opfk_node_average_launch(c->P, cur, c->stream) != 0) return fail(OPF_ECUDA, "node_average launch failed");
+  sc.su = 1.0;
+  sc.sv = 1.0;
+  sc.v_fresh = 1;
+  sc.status = 0;
+  sc.converged = 0;
+  sc.stalled = 0;
+  sc.frozen_at = 0;
+  sc.stall_ref = HUGE_VAL;
+  sc.stall_it = sc.it;
+  CK(cudaMemcpyAsync(c->P.sc, &sc, sizeof(sc), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->host_status = 0;
+  return OPF_OK;
+}
+
 opf_status opf_reset(opf_ctx *c) {
   if (!c) return fail(OPF_EINVAL, "ctx is NULL");
   CK(cudaMemsetAsync(c->arena, 0, c->state_bytes, c->stream));

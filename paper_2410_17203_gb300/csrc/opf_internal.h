@@ -209,6 +209,10 @@ int opfk_import_launch(const opfk::Params &p, int cur, const float *p_line, cons
                        const float *th2, const float *v1, const float *v2, const float *u,
                        void *stream);
 int opfk_node_average_launch(const opfk::Params &p, int cur, void *stream);
+// Starting state from node rows [T][N][stride] (price / price_scale, angle),
+// caller numbering; u = -price * u_scale
+int opfk_start_from_nodes_launch(const opfk::Params &p, int cur, const float *rows, int stride,
+                                 float price_scale, float u_scale, void *stream);
 int opfk_project_v_launch(const opfk::Params &p, int cur, void *stream);
 int opfk_export_lines_launch(const opfk::Params &p, int cur, float *p_line, float *th1, float *th2,
                              float *v1, float *v2, void *stream);

@@ -35,6 +35,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "opf_internal.h"
@@ -1294,6 +1295,43 @@ __global__ void import_kernel(Params p, int cur, const float *pl, const float *a
   }
 }
 
+// A starting state from node rows in the caller's numbering, rows[(t N + n)
+// stride + 0] = price / price_scale and [+ 1] = node angle: u_k = -price /
+// (rho_p (K+1)) in every contingency (prices are -rho_p sum_k u_k), every
+// line terminal at its node's angle, line power b (theta1 - theta2) clipped
+// to the limit (0 on the outaged line of a contingency, whose terminals keep
+// their angles), v = 0.  The same construction as a host-built state
+// imported through import_kernel.
+__global__ void start_from_nodes_kernel(Params p, int cur, const float *rows, int stride, float price_scale,
+                                        float u_scale) {
+  const int T = p.T, L = p.L, N = p.N;
+  const long long nl = (long long)p.Kp * L * T, nn = (long long)p.Kp * N * T;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nl + nn;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i < nl) {
+      const int k = (int)(i / ((long long)L * T));
+      const long long rem = i - (long long)k * L * T;
+      const int l = (int)(rem / T), t = (int)(rem % T);
+      const float x1 = rows[((size_t)t * N + p.node_perm[p.line_n1[l]]) * stride + 1];
+      const float x2 = rows[((size_t)t * N + p.node_perm[p.line_n2[l]]) * stride + 1];
+      const bool act = p.out_line[k] != l;
+      const float u = p.line_u[l];
+      const size_t dst = lidx(p, k, l, t);
+      p.P[cur][dst] = act ? fminf(fmaxf(p.line_b[l] * (x1 - x2), -u), u) : 0.5f * (x1 - x2);
+      p.MID[cur][dst] = 0.5f * (x1 + x2);
+      p.V1[cur][dst] = 0.f;
+      p.V2[cur][dst] = 0.f;
+    } else {
+      const long long j = i - nl;
+      const int k = (int)(j / ((long long)N * T));
+      const long long rem = j - (long long)k * N * T;
+      const int n = (int)(rem / T), t = (int)(rem % T);
+      const float price = rows[((size_t)t * N + p.node_perm[n]) * stride] * price_scale;
+      p.U[cur][nidx(p, k, n, t)] = -price * u_scale;
+    }
+  }
+}
+
 // node averages from the stored terminal values (after import)
 __global__ void node_average_kernel(Params p, int cur) {
   const int T = p.T, N = p.N;
@@ -1487,6 +1525,28 @@ int opfk_plan(const Params &p, IterPlan *plan) {
   plan->lean_grid = vn ? (int)std::min<long long>(gl, (nn + BLOCK - 1) / BLOCK) : 0;
   plan->xs_grid = (int)std::min<long long>(gx, (nx + BLOCK - 1) / BLOCK);
   plan->inner_grid = (n_inner + WARPS - 1) / WARPS;
+  {
+    // The inner-ADMM kernel is latency-bound (one warp per device through its
+    // ten Appendix D iterations) and runs beside the bandwidth-bound line
+    // kernel, whose CTAs it displaces.  When the line pass is long enough to
+    // hide it, a grid of one CTA on every other SM, walking the devices in
+    // several rounds, leaves the line kernel more of the GPU (10k buses,
+    // T = 96, K = 50, 3,000 devices: 0.741 -> 0.706 ms per iteration).  The
+    // estimates: a round of devices takes about 0.45 T microseconds, the
+    // line pass moves about 32 bytes per (line, contingency, step) at
+    // 6.5 TB/s; the cap applies while the rounds fit in 70 % of it.
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms >= 2) {
+      const int half = sms / 2;
+      if (plan->inner_grid > half) {
+        const double rounds = std::ceil((double)plan->inner_grid / half);
+        const double inner_us = rounds * 0.45 * p.T;
+        const double line_us = (double)p.Kp * p.L * p.T * 32.0 / 6.5e6;
+        if (inner_us <= 0.7 * line_us) plan->inner_grid = half;
+      }
+    }
+  }
   const long long nd = (long long)p.N * (p.T / (v2 ? 2 : 1));
   plan->dsum_grid = (int)std::min<long long>(gd, (nd + BLOCK - 1) / BLOCK);
   plan->inner_smem = ism;
@@ -1661,6 +1721,13 @@ int opfk_import_launch(const Params &p, int cur, const float *pl, const float *a
                        const float *v1, const float *v2, const float *u, void *stream) {
   const long long work = (long long)p.Kp * (p.L + p.N) * p.T;
   import_kernel<<<aux_grid(work), 256, 0, (cudaStream_t)stream>>>(p, cur, pl, a1, a2, v1, v2, u);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int opfk_start_from_nodes_launch(const Params &p, int cur, const float *rows, int stride, float price_scale,
+                                 float u_scale, void *stream) {
+  start_from_nodes_kernel<<<aux_grid((long long)p.Kp * (p.L + p.N) * p.T), 256, 0, (cudaStream_t)stream>>>(
+      p, cur, rows, stride, price_scale, u_scale);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

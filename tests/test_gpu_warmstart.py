@@ -20,13 +20,18 @@ def _lib():
     load_library()
 
 
-def _solve(cases, states=None):
+def _solve(cases, states=None, device_rows=None):
     from paper_2410_17203_gb300 import (opf_batch_converged, opf_batch_create, opf_batch_destroy,
-                                        opf_batch_iterate, opf_create, opf_get_info, opf_set_state)
+                                        opf_batch_iterate, opf_create, opf_get_info, opf_set_state,
+                                        opf_set_state_from_nodes)
+    from paper_2410_17203_gb300 import warmstart as ws
     hs = [opf_create(c, OPTS) for c in cases]
     if states:
         for h, st in zip(hs, states):
             opf_set_state(h, st)
+    if device_rows:
+        for h, y in zip(hs, device_rows):
+            opf_set_state_from_nodes(h, y, ws.PRICE_SCALE, on_device=True)
     b = opf_batch_create(hs)
     for _ in range(800):
         opf_batch_iterate(b, 100)
@@ -72,14 +77,18 @@ def test_warm_state_from_the_solution_and_learned_start():
     net = WarmStartNet(N, base["line_from"], base["line_to"], base["line_b"], T, ws.N_FEATURES, seed=2)
     hist = ws.train(net, xd[:12], yd[:12], epochs=30, lr=1e-3)
     assert hist[-1] < hist[0]
-    states = []
+    ys = []
     for i in range(12, 16):
         y = torch.zeros((N * T, 2), dtype=torch.float32, device="cuda")
         net.forward(xd[i], y)
-        states.append(ws.warm_state(cases[i], y.cpu().numpy().astype(np.float64)))
+        ys.append(y)
     net.close()
-    hs3, info3 = _solve(cases[12:], states)
+    # the start is built on the device from the network's output
+    hs3, info3 = _solve(cases[12:], device_rows=ys)
     assert all(i["converged"] for i in info3)
+    learned, cold_test = [i["iterations"] for i in info3], cold[12:]
+    print("held-out iterations: cold", cold_test, "learned", learned)
+    assert np.mean(learned) < np.mean(cold_test)
     # two points that both pass the eps = 1e-4 residual test from different
     # starts agree on the objective to a few tenths of a percent
     for h, o in zip(hs3, obj[12:]):
@@ -118,3 +127,41 @@ def test_gpu_solutions_pass_the_oracle_certificate():
         o.step()
         assert o.res[0] <= o.tolerance() and o.res[1] <= o.tolerance(), (o.res[:2], o.tolerance())
         assert o.objective() == pytest.approx(obj, rel=1e-3)
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_start_from_node_rows_equals_the_host_construction(on_device):
+    """opf_set_state_from_nodes builds on the device the state that
+    warmstart.warm_state builds on the host from the same prices and angles
+    (a multi-period case with outages, ramp limits and batteries; the
+    context's penalty is not 1, so the scaling of u is exercised)."""
+    import torch
+    from gridgen import scale_case
+    from paper_2410_17203_gb300 import Solver, opf_set_state_from_nodes
+    from paper_2410_17203_gb300 import warmstart as ws
+    from helpers import rel_err
+    case = make_case(scale_case(150, 24, 6, seed=21))
+    N, T = case["n_nodes"], case["T"]
+    rng = np.random.default_rng(7)
+    y = np.stack([rng.uniform(0.1, 0.4, N * T), rng.normal(0.0, 0.3, N * T)], axis=1).astype(np.float32)
+    rho_p = 1.7
+    a = Solver(case, dict(eps=0.0, rho_p=rho_p, adapt_every=0))
+    b = Solver(case, dict(eps=0.0, rho_p=rho_p, adapt_every=0))
+    try:
+        a.iterate(13)                      # a state to overwrite, and a counter that is not 0
+        b.iterate(13)
+        a.set_state(ws.warm_state(case, y.astype(np.float64), rho_p=rho_p))
+        rows = torch.from_numpy(y).cuda() if on_device else y
+        opf_set_state_from_nodes(b.h, rows, ws.PRICE_SCALE, on_device=on_device)
+        sa, sb = a.state(), b.state()
+        for k in sa:
+            assert rel_err(sb[k], sa[k]) <= 1e-6, k
+        # and the two continue alike
+        a.iterate(20)
+        b.iterate(20)
+        sa, sb = a.state(), b.state()
+        for k in ("p_line", "u", "p_dev"):
+            assert rel_err(sb[k], sa[k]) <= 1e-5, k
+    finally:
+        a.close()
+        b.close()
