@@ -618,6 +618,57 @@ def adjoint_leg(stream, args):
             "grad_norms": {k: float(np.linalg.norm(v)) for k, v in g.items()}}
 
 
+class PlainRunner:
+    """One context over the whole instance, iterated by opf_iterate."""
+
+    def __init__(self, case, opts, stream):
+        from paper_2410_17203_gb300 import opf_create
+        self.h = opf_create(case, opts, stream=stream.cuda_stream)
+
+    def run(self, n):
+        from paper_2410_17203_gb300 import opf_iterate
+        opf_iterate(self.h, n)
+
+    def close(self):
+        from paper_2410_17203_gb300 import opf_destroy
+        opf_destroy(self.h)
+
+
+class SliceRunner:
+    """This rank's block of the contingencies (include/opf.h, contingency
+    slices): per iteration the local half, an all-reduce of the exchange
+    buffer on the context's stream, and the decisions."""
+
+    def __init__(self, case, opts, stream, dist, ws, rank):
+        import numpy as np
+        import torch
+        from paper_2410_17203_gb300 import opf_create_slice, opf_slice_exchange, opf_slice_prime
+        blocks = np.array_split(np.arange(len(case["outaged"]) + 1), ws)
+        self.k0, self.k1 = int(blocks[rank][0]), int(blocks[rank][-1]) + 1
+        self.h = opf_create_slice(case, self.k0, self.k1, opts, stream=stream.cuda_stream)
+        self.x = opf_slice_exchange(self.h)
+        self.dist, self.stream = dist, stream
+        with torch.cuda.stream(stream):
+            opf_slice_prime(self.h)
+            self.exchange()
+
+    def exchange(self):
+        if self.dist is not None:
+            self.dist.all_reduce(self.x)
+
+    def run(self, n):
+        from paper_2410_17203_gb300 import opf_slice_begin, opf_slice_finish, opf_slice_local
+        opf_slice_begin(self.h, n)
+        for _ in range(n):
+            opf_slice_local(self.h)
+            self.exchange()
+            opf_slice_finish(self.h)
+
+    def close(self):
+        from paper_2410_17203_gb300 import opf_destroy
+        opf_destroy(self.h)
+
+
 def ours_arm(args):
     import numpy as np
     import torch
@@ -634,20 +685,29 @@ def ours_arm(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    case = make_case(args.config, seed=None if ws == 1 else 1000 + rank)
+    # N > 1: the contingencies of one instance split over the GPUs (each rank a
+    # slice, one all-reduce of the exchange buffer per iteration), unless
+    # --replicas asks for an independent instance per GPU
+    shard = (ws > 1 and not args.replicas) or args.shard
+    case = make_case(args.config, seed=None if (ws == 1 or shard) else 1000 + rank)
     d = case_dims(case)
     B = byte_model(d)
     stream = torch.cuda.Stream(device=dev)
     opts = dict(adapt_every=10, eps=0.0)
-    s = Solver(case, opts, stream=stream.cuda_stream)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
+    if shard:
+        runner = SliceRunner(case, opts, stream, dist, ws, rank)
+    else:
+        runner = PlainRunner(case, opts, stream)
+    s = runner
+
     # warm-up
     with torch.cuda.stream(stream):
-        opf_iterate(s.h, args.warmup)
+        runner.run(args.warmup)
     torch.cuda.synchronize()
     barrier()
     clocks = Clocks(local) if rank == 0 else None
@@ -657,20 +717,22 @@ def ours_arm(args):
     torch.cuda.synchronize()
     barrier()
     e0.record(stream)
-    opf_iterate(s.h, args.steps)
+    with torch.cuda.stream(stream):
+        runner.run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     ck = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1)
     res = opf_residuals(s.h)
-    info = s.get_info()
-    kernels_per_iter = int(info["kernels_per_iteration"])
+    info = opf_get_info(s.h)
+    kernels_per_iter = int(info["kernels_per_iteration"]) + (1 if shard else 0)   # + the exchange sums
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    value = ws * args.steps / (ms_max / 1e3)
+    # a slice run solves one instance on all GPUs; replicas solve one each
+    value = (1 if shard else ws) * args.steps / (ms_max / 1e3)
     s.close()
 
     # end to end through the C ABI with host buffers
@@ -684,16 +746,17 @@ def ours_arm(args):
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        h = opf_create(case, opts, stream=stream.cuda_stream)
-        opf_iterate(h, args.steps)
-        r = opf_residuals(h)
-        opf_solution(h, False, True, p_dev=p_dev, price=price)
-        opf_destroy(h)
+        r2 = SliceRunner(case, opts, stream, dist, ws, rank) if shard else PlainRunner(case, opts, stream)
+        with torch.cuda.stream(stream):
+            r2.run(args.steps)
+        r = opf_residuals(r2.h)
+        opf_solution(r2.h, False, True, p_dev=p_dev, price=price)
+        r2.close()
         dt = time.perf_counter() - t0
         tt = torch.tensor([dt], dtype=torch.float64, device=dev)
         if dist is not None:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": ws * args.steps / float(tt.item()), "unit": UNIT,
+        e2e = {"value": (1 if shard else ws) * args.steps / float(tt.item()), "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "includes": "opf_create (host network upload, device arena), K iterations, "
                            "residuals + solution download, opf_destroy"}
@@ -702,16 +765,16 @@ def ours_arm(args):
     # solve, then a load-perturbed instance solved cold and warm-started from
     # the first solution (Section 3.4)
     ttt = None
-    if args.ttt and rank == 0:
+    if args.ttt and rank == 0 and ws == 1:
         ttt = time_to_tolerance(case, stream, args)
     batched = None
-    if args.batched > 0 and rank == 0:
+    if args.batched > 0 and rank == 0 and ws == 1:
         batched = batched_vs_plain(stream, args)
     learned = None
-    if args.learned > 0 and rank == 0:
+    if args.learned > 0 and rank == 0 and ws == 1:
         learned = learned_warm_start(stream, args)
     adjoint = None
-    if args.adjoint > 0 and rank == 0:
+    if args.adjoint > 0 and rank == 0 and ws == 1:
         adjoint = adjoint_leg(stream, args)
 
     cpu = None
@@ -737,14 +800,17 @@ def ours_arm(args):
 
     if rank == 0:
         peak, src = peak_hbm()
-        achieved = B * args.steps / (ms / 1e3) / 1e9
+        # bytes moved per GPU: a slice holds 1/ws of the contingency-replicated state
+        achieved = B * args.steps / (ms / 1e3) / 1e9 / (ws if shard else 1)
         traffic = profiled_traffic()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(args.config, d), "N": d["N"], "L": d["L"], "T": d["T"], "K": d["K"],
-                       "S": d["S"], "J": d["J"], "parallelism": f"independent instance per GPU x{ws}",
+                       "S": d["S"], "J": d["J"],
+                       "parallelism": (f"contingency slices x{ws} (one all-reduce of the exchange buffer per iteration)"
+                                       if shard else f"independent instance per GPU x{ws}"),
                        "l2": "inputs larger than L2 (state %.2f GB)" % (info["device_bytes"] / 1e9),
                        "adapt_every": 10},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -785,6 +851,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="10k")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="run the timed iterations as contingency slices even on one GPU (the default for N > 1)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="N > 1: an independent instance per GPU instead of contingency slices")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", dest="ttt", action="store_false",
                     help="skip the solves to eps = 1e-4 (cold, perturbed cold, perturbed warm)")

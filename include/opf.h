@@ -187,6 +187,8 @@ typedef struct {
   int32_t stalled;          /* 1 when the last call stopped at a stall (OPF_ESTALLED) */
   int64_t frozen_at;        /* iteration at which the stall rule fixed the penalties; 0 = never */
   int64_t history_rows;     /* residual-history rows written since create / reset */
+  int32_t k_begin, k_count; /* contingencies held: k_begin .. k_begin + k_count - 1 (all
+                               K + 1 of them unless the context is a slice) */
 } opf_info;
 
 /* Fill `opt` with the defaults listed above. */
@@ -219,6 +221,47 @@ opf_status opf_create(const opf_network *net, int32_t horizon_T,
  * and before its later work; device errors surface at the next
  * synchronizing call. */
 opf_status opf_iterate(opf_ctx *ctx, int32_t n_iters, double rho);
+
+/* Contingency slices: the iteration on several GPUs (one process each),
+ * each holding a block of the contingencies.  The contingencies are coupled
+ * only by the sums over k that feed the devices shared by all of them
+ * (Section 3.2 step 2) and by the residual norms (Section 3.3), so a slice
+ * keeps the lines, node arrays and phase duals of its own contingencies and
+ * a replica of the shared devices, and the slices exchange one buffer per
+ * iteration, which the caller sums over all slices (an all-reduce).
+ *
+ * opf_create_slice is opf_create for contingencies k_begin .. k_end - 1 of
+ * 0 .. K (0 is the base case; the blocks of the slices must partition
+ * 0 .. K).  Every slice gets the whole network and contingency list, the
+ * same options (plain message passing, alpha = 1) and its own device.
+ * Per iteration, on every slice, in this order:
+ *   opf_slice_local   the devices (from the exchanged sums), this slice's
+ *                     line proxes and node sums, then its share of the sums
+ *                     written into the exchange buffer;
+ *   (the caller)      sums the exchange buffers of all slices, in place, on
+ *                     the stream of opf_options.cuda_stream;
+ *   opf_slice_finish  the residuals, stopping test and adaptive penalty from
+ *                     the summed buffer (the same decisions on every slice).
+ * Before the first iteration after create, reset or a state import, call
+ * opf_slice_prime and exchange once: it writes this slice's share of the
+ * sums of its current state.  opf_slice_begin(n, rho) starts a call of n
+ * iterations as opf_iterate does (the residuals are formed at its last
+ * iteration; rho > 0 sets the penalties) and must precede them.  After a
+ * stop (converged, stalled, error) the local half contributes the sums of
+ * the unchanged state, so the exchange stays consistent.
+ * opf_slice_exchange returns the library-owned device buffer (n doubles:
+ * sum_k (pbar + u) and sum_k u at the nodes with devices, then the residual
+ * partial sums) for the caller's all-reduce.  Exports of a slice hold its own
+ * contingencies (K + 1 replaced by k_end - k_begin); opf_solution's price is
+ * this slice's part of -rho_p sum_k u_k (sum it over the slices).  A slice
+ * cannot be iterated by opf_iterate (OPF_ESTATE) or join a batch. */
+opf_status opf_create_slice(const opf_network *net, int32_t horizon_T, const opf_contingencies *ctg,
+                            int32_t k_begin, int32_t k_end, const opf_options *opt, opf_ctx **out);
+opf_status opf_slice_exchange(opf_ctx *ctx, double **buffer, int64_t *n_doubles);
+opf_status opf_slice_prime(opf_ctx *ctx);
+opf_status opf_slice_begin(opf_ctx *ctx, int32_t n_iters, double rho);
+opf_status opf_slice_local(opf_ctx *ctx);
+opf_status opf_slice_finish(opf_ctx *ctx);
 
 /* Residuals of the last iteration run (Section 3.3), FP64:
  * out[0] = ||r_primal||, out[1] = ||r_dual||, out[2] = primal power part,

@@ -27,8 +27,10 @@
  * side; the inner projection min(alpha + lambda, 0) is a clamp with upper
  * bound 0.
  *
- * Arrays are in the caller's numbering and layout (opf.h); host pointers.
- * The computation runs in FP32 on the device; the cost is summed in FP64.
+ * Arrays are in the caller's numbering and layout (opf.h); host pointers
+ * (opf_diff_cost_grad_on also takes device pointers).  The computation runs
+ * in FP32 on the device; the cost is summed in FP64, and so is the line-limit
+ * gradient over contingencies and steps.
  */
 #ifndef OPF_DIFF_H_
 #define OPF_DIFF_H_
@@ -57,6 +59,14 @@ opf_status opf_diff_create(const opf_network *net, int32_t horizon_T, const opf_
 opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const float *gen_pmax,
                               const float *line_u, double *cost, float *grad_load_p,
                               float *grad_gen_pmax, float *grad_line_u);
+
+/* The same with every array on the device when on_device != 0 (device
+ * pointers of the context's device; the cost stays a host double), or on the
+ * host when 0.  The buffers a call needs (checkpoints, one segment of states,
+ * adjoints) are kept by the context and reused by later calls. */
+opf_status opf_diff_cost_grad_on(opf_diff *d, int32_t K, int32_t on_device, const float *load_p,
+                                 const float *gen_pmax, const float *line_u, double *cost, float *grad_load_p,
+                                 float *grad_gen_pmax, float *grad_line_u);
 
 void opf_diff_destroy(opf_diff *d);
 

@@ -77,12 +77,14 @@ class opf_info(C.Structure):
         ("inner_len", C.c_int64), ("device_bytes", C.c_int64),
         ("kernels_per_iteration", C.c_int32), ("stalled", C.c_int32),
         ("frozen_at", C.c_int64), ("history_rows", C.c_int64),
+        ("k_begin", C.c_int32), ("k_count", C.c_int32),
     ]
 
 
 ABI_VERSION = 5     # OPF_ABI_VERSION of include/opf.h
 
-EXPORTS = ["opf_default_options", "opf_create", "opf_iterate", "opf_residuals", "opf_solution",
+EXPORTS = ["opf_default_options", "opf_create", "opf_create_slice", "opf_slice_exchange", "opf_slice_prime",
+           "opf_slice_begin", "opf_slice_local", "opf_slice_finish", "opf_iterate", "opf_residuals", "opf_solution",
            "opf_price_noalloc", "opf_history", "opf_set_state_from_nodes", "opf_get_state", "opf_set_state", "opf_reset", "opf_get_info",
            "opf_destroy", "opf_status_str", "opf_last_error", "opf_abi_version",
            "opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_stopped",
@@ -113,6 +115,13 @@ def load_library(path=None):
     lib.opf_create.argtypes = [C.POINTER(opf_network), C.c_int32, C.POINTER(opf_contingencies),
                                C.POINTER(opf_options), C.POINTER(C.c_void_p)]
     lib.opf_iterate.argtypes = [C.c_void_p, C.c_int32, C.c_double]
+    lib.opf_create_slice.argtypes = [C.POINTER(opf_network), C.c_int32, C.POINTER(opf_contingencies), C.c_int32,
+                                     C.c_int32, C.POINTER(opf_options), C.POINTER(C.c_void_p)]
+    lib.opf_slice_exchange.argtypes = [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]
+    lib.opf_slice_prime.argtypes = [C.c_void_p]
+    lib.opf_slice_begin.argtypes = [C.c_void_p, C.c_int32, C.c_double]
+    lib.opf_slice_local.argtypes = [C.c_void_p]
+    lib.opf_slice_finish.argtypes = [C.c_void_p]
     lib.opf_residuals.argtypes = [C.c_void_p, F64P]
     lib.opf_solution.argtypes = [C.c_void_p, C.c_int32, F64P, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]
@@ -168,6 +177,9 @@ def load_library(path=None):
     lib.opf_diff_destroy.argtypes = [C.c_void_p]
     lib.opf_diff_destroy.restype = None
     for name in ("opf_diff_create", "opf_diff_cost_grad", "opf_diff_cost_grad_on"):
+        getattr(lib, name).restype = C.c_int
+    for name in ("opf_create_slice", "opf_slice_exchange", "opf_slice_prime", "opf_slice_begin", "opf_slice_local",
+                 "opf_slice_finish"):
         getattr(lib, name).restype = C.c_int
     for name in ("opf_create", "opf_iterate", "opf_residuals", "opf_solution", "opf_price_noalloc", "opf_history",
                  "opf_set_state_from_nodes",
@@ -299,6 +311,63 @@ def opf_create(case, options=None, stream=None):
     return h
 
 
+def opf_create_slice(case, k_begin, k_end, options=None, stream=None):
+    """A context for contingencies k_begin .. k_end - 1 of the case (0 is the
+    base case); see include/opf.h for the iteration protocol."""
+    lib = load_library()
+    T = int(case["T"])
+    net, ctg, keep = _network(case, "opf_create_slice")
+    if options is None:
+        options = opf_default_options()
+    elif isinstance(options, dict):
+        options = opf_default_options(**options)
+    if stream is not None:
+        options.cuda_stream = C.c_void_p(int(stream))
+    h = C.c_void_p()
+    _check(lib.opf_create_slice(C.byref(net), T, C.byref(ctg), int(k_begin), int(k_end), C.byref(options),
+                                C.byref(h)), "opf_create_slice")
+    try:
+        _CTX_INFO[h.value] = opf_get_info(h)
+    except OpfError:
+        lib.opf_destroy(h)
+        raise
+    return h
+
+
+class _DeviceBuffer:
+    """A device array the library owns, exposed to torch without a copy."""
+
+    def __init__(self, ptr, n, device):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+        self.device = device
+
+
+def opf_slice_exchange(h):
+    """The slice's exchange buffer as a float64 CUDA tensor sharing the
+    library's memory (sum it over the slices between local and finish)."""
+    import torch
+    ptr, n = C.c_void_p(), C.c_int64()
+    _check(load_library().opf_slice_exchange(h, C.byref(ptr), C.byref(n)), "opf_slice_exchange")
+    return torch.as_tensor(_DeviceBuffer(ptr.value, n.value, None), device="cuda")
+
+
+def opf_slice_prime(h):
+    _check(load_library().opf_slice_prime(h), "opf_slice_prime")
+
+
+def opf_slice_begin(h, n_iters, rho=0.0):
+    _check(load_library().opf_slice_begin(h, int(n_iters), float(rho)), "opf_slice_begin")
+
+
+def opf_slice_local(h):
+    _check(load_library().opf_slice_local(h), "opf_slice_local")
+
+
+def opf_slice_finish(h):
+    _check(load_library().opf_slice_finish(h), "opf_slice_finish")
+
+
 def opf_destroy(h):
     if h:
         _CTX_INFO.pop(getattr(h, "value", h), None)
@@ -367,7 +436,7 @@ def opf_solution(h, on_device=False, objective=True, p_dev=None, p_line=None, th
 
     Returns the objective (float) or None."""
     i = _ctx_info(h)
-    Kp, L, N, S, T = i["K"] + 1, i["L"], i["N"], i["S"], i["T"]
+    Kp, L, N, S, T = i["k_count"], i["L"], i["N"], i["S"], i["T"]
     dv = bool(on_device)
     ptrs = [_buf(p_dev, S * T, dv, "p_dev", "opf_solution"), _buf(p_line, Kp * L * T, dv, "p_line", "opf_solution"),
             _buf(theta_node, Kp * N * T, dv, "theta_node", "opf_solution"),
@@ -635,7 +704,7 @@ STATE_FIELDS = ("p_line", "th1", "th2", "v1", "v2", "p_dev", "u", "inner")
 
 
 def state_shapes(info):
-    Kp, L, N, S, T = info["K"] + 1, info["L"], info["N"], info["S"], info["T"]
+    Kp, L, N, S, T = info["k_count"], info["L"], info["N"], info["S"], info["T"]
     return dict(p_line=(Kp, L, T), th1=(Kp, L, T), th2=(Kp, L, T), v1=(Kp, L, T),
                 v2=(Kp, L, T), p_dev=(S, T), u=(Kp, N, T), inner=(info["inner_len"],))
 
@@ -721,7 +790,7 @@ class Solver:
 
     def solution(self):
         i = self.info
-        Kp, L, N, S, T = i["K"] + 1, i["L"], i["N"], i["S"], i["T"]
+        Kp, L, N, S, T = i["k_count"], i["L"], i["N"], i["S"], i["T"]
         out = dict(p_dev=np.zeros((S, T), np.float32), p_line=np.zeros((Kp, L, T), np.float32),
                    theta_node=np.zeros((Kp, N, T), np.float32), price=np.zeros((N, T), np.float32))
         out["objective"] = opf_solution(self.h, False, True, **out)

@@ -72,6 +72,11 @@ struct opf_ctx {
   cudaStream_t stream = nullptr;
   opf_options opt{};
   int N = 0, L = 0, T = 0, K = 0, Kp = 0, S = 0, G = 0, D = 0, B = 0, H = 0;
+  // contingency slice: Kp local contingencies k_base .. k_base + Kp - 1 of
+  // Kp_glob (= Kp for a whole context)
+  int k_base = 0, Kp_glob = 0;
+  bool slice = false;
+  cudaGraphExec_t g_local = nullptr;   // a slice's local half of one iteration
   int n_closed = 0, n_dnode = 0, n_ramp = 0, n_stor = 0;
   size_t n_tcode = 0;  // padded terminal-code list length
   float *price_scratch = nullptr;  // this device's fixed price staging array
@@ -268,6 +273,10 @@ std::vector<int> rcm_order(int N, const std::vector<int> &ptr, const std::vector
   return order;
 }
 
+// doubles in a slice's exchange buffer: sum_k (pbar + u) and sum_k u at the
+// nodes with devices, then the residual partial sums
+size_t slice_exchange_len(const opf_ctx *c) { return (size_t)2 * c->n_dnode * c->T + opfk::NSLOT; }
+
 // The arena layout; called once with a null base to size it.
 void carve(opf_ctx *c, Arena &a) {
   Params &p = c->P;
@@ -342,6 +351,7 @@ void carve(opf_ctx *c, Arena &a) {
   p.DSM = a.take<float>((size_t)c->N * T);
   p.DSQ = a.take<float>((size_t)c->N * T);
   p.partials = a.take<double>((size_t)c->plan.node_grid * opfk::NSLOT);
+  p.xsum = c->slice ? a.take<double>(slice_exchange_len(c)) : nullptr;
 }
 
 opf_status init_scalars(opf_ctx *c) {
@@ -387,10 +397,12 @@ opf_status read_scalars(opf_ctx *c, DevScalars *sc) {
 
 // The iteration as a CUDA graph of `iters` iterations, captured from the two
 // iteration streams.
-opf_status build_graph(opf_ctx *c, int iters, cudaGraphExec_t *out) {
+opf_status build_graph(opf_ctx *c, int iters, cudaGraphExec_t *out, bool slice_local = false) {
   CK(cudaStreamBeginCapture(c->s_main, cudaStreamCaptureModeThreadLocal));
   for (int i = 0; i < iters; ++i) {
-    if (opfk_iteration_enqueue(c->P, c->plan, c->s_main, c->s_aux, c->ev_fork, c->ev_join) != 0) {
+    const int r = slice_local ? opfk_slice_local_enqueue(c->P, c->plan, c->s_main, c->s_aux, c->ev_fork, c->ev_join)
+                              : opfk_iteration_enqueue(c->P, c->plan, c->s_main, c->s_aux, c->ev_fork, c->ev_join);
+    if (r != 0) {
       cudaGraph_t g = nullptr;
       cudaStreamEndCapture(c->s_main, &g);
       if (g) cudaGraphDestroy(g);
@@ -408,6 +420,7 @@ opf_status build_graph(opf_ctx *c, int iters, cudaGraphExec_t *out) {
 }
 
 void release_cuda(opf_ctx *c) {
+  if (c->g_local) cudaGraphExecDestroy(c->g_local);
   if (c->g_one) cudaGraphExecDestroy(c->g_one);
   if (c->g_many) cudaGraphExecDestroy(c->g_many);
   for (cudaEvent_t ev : {c->ev_fork, c->ev_join, c->ev_in, c->ev_out, c->ev_sync})
@@ -446,8 +459,13 @@ opf_status resolve_price_scratch(float **out) {
 
 extern "C" {
 
-opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies *ctg,
-                      const opf_options *opt_in, opf_ctx **out) {
+}  // extern "C"
+
+namespace {
+
+// a context over contingencies k_begin .. k_end - 1 (all of them: 0 .. K + 1)
+opf_status create_impl(const opf_network *net, int32_t T, const opf_contingencies *ctg, int k_begin, int k_end,
+                       bool slice, const opf_options *opt_in, opf_ctx **out) {
   if (!out) return fail(OPF_EINVAL, "out is NULL");
   *out = nullptr;
   opf_options opt;
@@ -465,7 +483,14 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   c->L = net->n_lines;
   c->T = T;
   c->K = ctg ? ctg->K : 0;
-  c->Kp = c->K + 1;
+  c->Kp_glob = c->K + 1;
+  if (k_begin < 0 || k_end > c->Kp_glob || k_begin >= k_end) {
+    delete c;
+    return fail(OPF_EINVAL, "contingency range [k_begin, k_end) must lie in [0, K + 1) and be non-empty");
+  }
+  c->k_base = k_begin;
+  c->Kp = k_end - k_begin;
+  c->slice = slice;
   c->G = net->n_gens;
   c->D = net->n_loads;
   c->B = net->n_stor;
@@ -699,10 +724,13 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   p.adapt_every = opt.adapt_every;
   p.check_every = opt.check_every;
   p.inner_iters = opt.inner_iters;
+  p.Kp_glob = c->Kp_glob;
+  p.k_base = c->k_base;
+  p.slice = c->slice ? 1 : 0;
   p.stall_window = opt.stall_window;
   p.adapt_until = opt.adapt_until;
   p.hist_cap = opt.history_len;
-  c->tol = opt.eps * std::sqrt(2.0 * (2.0 * L + S) * T * c->Kp);
+  c->tol = opt.eps * std::sqrt(2.0 * (2.0 * L + S) * T * c->Kp_glob);
   p.tol = c->tol;
 
   std::vector<int> outl(c->Kp, -1);
@@ -711,7 +739,10 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
     lb[li] = (float)net->line_b[line_perm[li]];
     lu[li] = (float)net->line_u[line_perm[li]];
   }
-  for (int k = 0; k < c->K; ++k) outl[k + 1] = ctg->outaged_line[k] >= 0 ? line_inv[ctg->outaged_line[k]] : -1;
+  for (int j = 0; j < c->Kp; ++j) {
+    const int k = c->k_base + j;   // global contingency; 0 is the base case
+    if (k >= 1) outl[j] = ctg->outaged_line[k - 1] >= 0 ? line_inv[ctg->outaged_line[k - 1]] : -1;
+  }
 
   opf_status s = OPF_OK;
   auto up = [&](const void *dst, const auto &v) {
@@ -782,6 +813,24 @@ opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies
   return OPF_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+opf_status opf_create(const opf_network *net, int32_t T, const opf_contingencies *ctg,
+                      const opf_options *opt, opf_ctx **out) {
+  return create_impl(net, T, ctg, 0, 1 + (ctg ? std::max<int>(ctg->K, 0) : 0), false, opt, out);
+}
+
+opf_status opf_create_slice(const opf_network *net, int32_t T, const opf_contingencies *ctg, int32_t k_begin,
+                            int32_t k_end, const opf_options *opt, opf_ctx **out) {
+  if (opt && opt->alpha != 1.0) {
+    if (out) *out = nullptr;
+    return fail(OPF_EINVAL, "contingency slices run plain message passing (alpha = 1)");
+  }
+  return create_impl(net, T, ctg, k_begin, k_end, true, opt, out);
+}
+
 void opf_destroy(opf_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
@@ -792,6 +841,7 @@ void opf_destroy(opf_ctx *c) {
 
 opf_status opf_iterate(opf_ctx *c, int32_t n_iters, double rho) {
   if (!c) return fail(OPF_EINVAL, "ctx is NULL");
+  if (c->slice) return fail(OPF_ESTATE, "a contingency slice iterates through opf_slice_local / opf_slice_finish");
   if (n_iters < 0) return fail(OPF_EINVAL, "n_iters must be >= 0");
   if (rho > 0 && !std::isfinite(rho)) return fail(OPF_EINVAL, "rho must be finite");
   if (n_iters > 0 && !c->g_one) {
@@ -812,6 +862,70 @@ opf_status opf_iterate(opf_ctx *c, int32_t n_iters, double rho) {
   CK(cudaEventRecord(c->ev_out, c->s_main));
   CK(cudaStreamWaitEvent(c->stream, c->ev_out, 0));
   return OPF_OK;
+}
+
+opf_status opf_slice_exchange(opf_ctx *c, double **buf, int64_t *n) {
+  if (!c || !buf || !n) return fail(OPF_EINVAL, "NULL argument");
+  if (!c->slice) return fail(OPF_ESTATE, "not a contingency slice (opf_create_slice)");
+  *buf = c->P.xsum;
+  *n = (int64_t)slice_exchange_len(c);
+  return OPF_OK;
+}
+
+// order the context's streams after the caller's stream, and back
+static opf_status slice_in(opf_ctx *c) {
+  CK(cudaEventRecord(c->ev_in, c->stream));
+  CK(cudaStreamWaitEvent(c->s_main, c->ev_in, 0));
+  return OPF_OK;
+}
+
+static opf_status slice_out(opf_ctx *c) {
+  CK(cudaEventRecord(c->ev_out, c->s_main));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_out, 0));
+  return OPF_OK;
+}
+
+opf_status opf_slice_prime(opf_ctx *c) {
+  if (!c) return fail(OPF_EINVAL, "ctx is NULL");
+  if (!c->slice) return fail(OPF_ESTATE, "not a contingency slice (opf_create_slice)");
+  opf_status s = slice_in(c);
+  if (s != OPF_OK) return s;
+  if (opfk_slice_prime_launch(c->P, c->s_main) != 0) return fail(OPF_ECUDA, "slice prime launch failed");
+  return slice_out(c);
+}
+
+opf_status opf_slice_begin(opf_ctx *c, int32_t n_iters, double rho) {
+  if (!c) return fail(OPF_EINVAL, "ctx is NULL");
+  if (!c->slice) return fail(OPF_ESTATE, "not a contingency slice (opf_create_slice)");
+  if (n_iters < 0) return fail(OPF_EINVAL, "n_iters must be >= 0");
+  if (rho > 0 && !std::isfinite(rho)) return fail(OPF_EINVAL, "rho must be finite");
+  opf_status s = slice_in(c);
+  if (s != OPF_OK) return s;
+  if (rho > 0 && opfk_set_rho_launch(c->P.sc, rho, c->s_main) != 0) return fail(OPF_ECUDA, "set_rho launch failed");
+  if (opfk_begin_launch(c->P.sc, n_iters, 1, c->s_main) != 0) return fail(OPF_ECUDA, "begin launch failed");
+  return slice_out(c);
+}
+
+opf_status opf_slice_local(opf_ctx *c) {
+  if (!c) return fail(OPF_EINVAL, "ctx is NULL");
+  if (!c->slice) return fail(OPF_ESTATE, "not a contingency slice (opf_create_slice)");
+  if (!c->g_local) {
+    opf_status gs = build_graph(c, 1, &c->g_local, true);
+    if (gs != OPF_OK) return gs;
+  }
+  opf_status s = slice_in(c);
+  if (s != OPF_OK) return s;
+  CK(cudaGraphLaunch(c->g_local, c->s_main));
+  return slice_out(c);
+}
+
+opf_status opf_slice_finish(opf_ctx *c) {
+  if (!c) return fail(OPF_EINVAL, "ctx is NULL");
+  if (!c->slice) return fail(OPF_ESTATE, "not a contingency slice (opf_create_slice)");
+  opf_status s = slice_in(c);
+  if (s != OPF_OK) return s;
+  if (opfk_slice_finish_enqueue(c->P, c->s_main) != 0) return fail(OPF_ECUDA, "slice decision launch failed");
+  return slice_out(c);
 }
 
 opf_status opf_residuals(opf_ctx *c, double out[6]) {
@@ -856,6 +970,8 @@ opf_status opf_get_info(opf_ctx *c, opf_info *info) {
   info->stalled = sc.stalled;
   info->frozen_at = sc.frozen_at;
   info->history_rows = sc.hist_n;
+  info->k_begin = c->k_base;
+  info->k_count = c->Kp;
   return OPF_OK;
 }
 
@@ -1112,6 +1228,7 @@ opf_status opf_batch_create(opf_ctx *const *ctxs, int32_t n, opf_batch **out) {
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return fail(OPF_EINVAL, "NULL context in batch");
     if (ctxs[i]->device != dev) return fail(OPF_EINVAL, "batch contexts must be on the current device");
+    if (ctxs[i]->slice) return fail(OPF_EINVAL, "a contingency slice cannot join a batch");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return fail(OPF_EINVAL, "a context appears twice in the batch");
   }
@@ -1425,7 +1542,7 @@ opf_status opf_set_state(opf_ctx *c, int32_t on_device, const opf_state *src) {
   else
     CK(cudaMemsetAsync(c->P.PD, 0, ST * 4, c->stream));
   // inner duals: scaled for the current penalty; factors rebuilt on first use
-  const float rho_dev = (float)(c->Kp * sc.rho_p);
+  const float rho_dev = (float)(c->Kp_glob * sc.rho_p);
   const size_t nr = (size_t)c->n_ramp * opfk::RG_N * c->T, ns = (size_t)c->n_stor * opfk::SG_N * (c->T + 1);
   std::vector<float> rl(nr, 0.f), rb(nr, 0.f), sl(ns, 0.f), sb(ns, 0.f);
   if (src->inner) {
@@ -1491,7 +1608,7 @@ opf_status opf_set_state_from_nodes(opf_ctx *c, int32_t on_device, const float *
     src = tmp.p;
   }
   // u = -price / (rho_p (K+1)) at the penalty in force
-  const float u_scale = (float)(1.0 / (sc.rho_p * c->Kp));
+  const float u_scale = (float)(1.0 / (sc.rho_p * c->Kp_glob));
   if (opfk_start_from_nodes_launch(c->P, cur, src, stride, (float)price_scale, u_scale, c->stream) != 0)
     return fail(OPF_ECUDA, "start launch failed");
   // device powers and the inner duals from zero (factors rebuilt on first use)

@@ -34,8 +34,9 @@ struct IDev {
 };
 
 // constraint rows A z <= h (eq: = h) of one device kind, in CSR and CSC form
+// (nnz nonzeros)
 struct Shape {
-  int n, m, rp, ci, tp, ti, eq, pad;
+  int n, m, rp, ci, tp, ti, eq, nnz;
 };
 
 struct DP {
@@ -73,7 +74,10 @@ struct Adj {
 __device__ __forceinline__ size_t li(const DP &p, int k, int l, int t) { return ((size_t)k * p.L + l) * p.T + t; }
 __device__ __forceinline__ size_t ni(const DP &p, int k, int n, int t) { return ((size_t)k * p.N + n) * p.T + t; }
 
-#define GRID_STRIDE(i, n) for (long long i = (long long)blockIdx.x * TB + threadIdx.x; i < (n); i += (long long)gridDim.x * TB)
+// item loops with 32-bit indices: opf_diff_create checks that every item
+// count stays below 2^31 (64-bit divisions per item cost more than the work)
+#define GRID_STRIDE(i, n) \
+  for (unsigned i = blockIdx.x * TB + threadIdx.x, n_##i = (unsigned)(n); i < n_##i; i += gridDim.x * TB)
 
 // ---------------------------------------------------------------------------
 // forward (Section 3.2)
@@ -82,7 +86,8 @@ __device__ __forceinline__ size_t ni(const DP &p, int k, int n, int t) { return 
 // node averages (Eq. average-op) of the terminal values of a state
 __global__ void fwd_avg(DP p, St s) {
   GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
-    const int t = (int)(i % p.T), n = (int)((i / p.T) % p.N), k = (int)(i / ((long long)p.T * p.N));
+    const unsigned q = i / (unsigned)p.T;
+    const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
     float sp = 0.f, st = 0.f;
     for (int j = p.dptr[n]; j < p.dptr[n + 1]; ++j) sp += s.PD[(size_t)p.didx[j] * p.T + t];
     for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
@@ -114,7 +119,8 @@ __device__ __forceinline__ LineIn line_inputs(const DP &p, const St &s, int k, i
 // step 1: line prox (Section 4.2); outaged lines decouple
 __global__ void fwd_line(DP p, St s, St nx) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
-    const int t = (int)(i % p.T), l = (int)((i / p.T) % p.L), k = (int)(i / ((long long)p.T * p.L));
+    const unsigned q = i / (unsigned)p.T;
+    const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
     const LineIn in = line_inputs(p, s, k, l, t);
     if (p.out[k] != l) {
       const float b = p.b[l], tb = 2.f * b, u = p.lu[l];
@@ -145,7 +151,7 @@ __device__ __forceinline__ float dev_x(const DP &p, const St &s, int d, int t) {
 // evaluates its link's prox p2 = clip((x2 - x1)/2, -u, u), p1 = -p2.
 __global__ void fwd_dev(DP p, St s, St nx, float *XD) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
-    const int t = (int)(i % p.T), d = (int)(i / p.T);
+    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T);
     const float X = dev_x(p, s, d, t);
     if (p.kind[d] == 1) {
       XD[i] = X;
@@ -172,36 +178,114 @@ __global__ void fwd_dev(DP p, St s, St nx, float *XD) {
   }
 }
 
+// One device's inner problem as the kernels read it: constraint rows in CSR
+// (row pointers relative to the shape's nonzeros) and CSC form, the inverse
+// system matrix, right-hand sides and linear cost.  stage_view copies them
+// into shared memory, where the ten inner iterations re-read them, instead of
+// chasing the same global pointers every iteration.
+struct View {
+  int n, m;
+  const int *arp, *aci, *atp, *ati;
+  const float *acv, *atv, *Mi, *h, *q;
+  const unsigned char *eq;
+};
+
+// What the kernels copy into shared memory: 0 nothing (long horizons), 1 the
+// constraint structure, right-hand sides and cost, 2 also the inverse.
+// view_words: the 4-byte words that takes.
+__host__ __device__ inline size_t view_words(int n, int m, int nnz, int level) {
+  if (level <= 0) return 0;
+  return (size_t)(m + 1) + (n + 1) + 2 * (size_t)nnz     // arp, atp, aci, ati
+         + 2 * (size_t)nnz + m + n                         // acv, atv, h, q
+         + ((size_t)m + 3) / 4                             // eq bytes
+         + (level >= 2 ? (size_t)n * n : 0);
+}
+
+__device__ View stage_view(const DP &p, const Shape &sh, const IDev &di, float *sm, int level) {
+  const int n = sh.n, m = sh.m, nnz = sh.nnz, tid = threadIdx.x, nt = blockDim.x;
+  if (level <= 0) {
+    View g;
+    g.n = n;
+    g.m = m;
+    g.arp = p.arp + sh.rp;
+    g.atp = p.atp + sh.tp;
+    g.aci = p.aci + sh.ci;
+    g.acv = p.acv + sh.ci;
+    g.ati = p.ati + sh.ti;
+    g.atv = p.atv + sh.ti;
+    g.h = p.RH + di.h;
+    g.q = p.Q + di.q;
+    g.eq = p.aeq + sh.eq;
+    g.Mi = p.minv + di.minv;
+    return g;
+  }
+  const bool with_minv = level >= 2;
+  int *arp = reinterpret_cast<int *>(sm), *atp = arp + m + 1, *aci = atp + n + 1, *ati = aci + nnz;
+  float *acv = reinterpret_cast<float *>(ati + nnz), *atv = acv + nnz, *h = atv + nnz, *q = h + m;
+  unsigned char *eq = reinterpret_cast<unsigned char *>(q + n);
+  float *Mi = q + n + (m + 3) / 4;
+  for (int i = tid; i <= m; i += nt) arp[i] = p.arp[sh.rp + i];
+  for (int i = tid; i <= n; i += nt) atp[i] = p.atp[sh.tp + i];
+  for (int i = tid; i < nnz; i += nt) {
+    aci[i] = p.aci[sh.ci + i];
+    acv[i] = p.acv[sh.ci + i];
+    ati[i] = p.ati[sh.ti + i];
+    atv[i] = p.atv[sh.ti + i];
+  }
+  for (int i = tid; i < m; i += nt) {
+    h[i] = p.RH[di.h + i];
+    eq[i] = p.aeq[sh.eq + i];
+  }
+  for (int i = tid; i < n; i += nt) q[i] = p.Q[di.q + i];
+  const float *mg = p.minv + di.minv;
+  if (with_minv)
+    for (int i = tid; i < n * n; i += nt) Mi[i] = mg[i];
+  __syncthreads();
+  View v;
+  v.n = n;
+  v.m = m;
+  v.arp = arp;
+  v.atp = atp;
+  v.aci = aci;
+  v.ati = ati;
+  v.acv = acv;
+  v.atv = atv;
+  v.h = h;
+  v.q = q;
+  v.eq = eq;
+  v.Mi = with_minv ? Mi : mg;
+  return v;
+}
+
 // N_INNER iterations of the Appendix D ADMM for the device of this CTA:
 //   z = M^-1 (rho' E_p' x - q + omega A'(h + beta - lambda)),
 //   alpha = A z - h, beta = min(alpha + lambda, 0) (0 on equality rows),
 //   lambda = alpha + lambda - beta;
 // mask (optional) records the rows where beta took alpha + lambda
-__device__ void inner_forward(const DP &p, const Shape &sh, const IDev &di, const float *x, float *beta, float *lam,
+__device__ void inner_forward(const DP &p, const View &v, const float *x, float *beta, float *lam,
                               float *w, float *r, float *z, unsigned char *mask) {
-  const int n = sh.n, m = sh.m, T = p.T;
+  const int n = v.n, m = v.m, T = p.T;
   const float rho = p.rd, om = p.rd;
-  const float *Mi = p.minv + di.minv, *h = p.RH + di.h, *q = p.Q + di.q;
   for (int it = 0; it < N_INNER; ++it) {
-    for (int row = threadIdx.x; row < m; row += blockDim.x) w[row] = h[row] + beta[row] - lam[row];
+    for (int row = threadIdx.x; row < m; row += blockDim.x) w[row] = v.h[row] + beta[row] - lam[row];
     __syncthreads();
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       float acc = 0.f;
-      for (int e = p.atp[sh.tp + j]; e < p.atp[sh.tp + j + 1]; ++e) acc += p.atv[sh.ti + e] * w[p.ati[sh.ti + e]];
-      r[j] = -q[j] + om * acc + (j < T ? rho * x[j] : 0.f);
+      for (int e = v.atp[j]; e < v.atp[j + 1]; ++e) acc += v.atv[e] * w[v.ati[e]];
+      r[j] = -v.q[j] + om * acc + (j < T ? rho * x[j] : 0.f);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {     // M^-1 is symmetric: read its columns coalesced
       float acc = 0.f;
-      for (int j = 0; j < n; ++j) acc += Mi[(size_t)j * n + i] * r[j];
+      for (int j = 0; j < n; ++j) acc += v.Mi[(size_t)j * n + i] * r[j];
       z[i] = acc;
     }
     __syncthreads();
     for (int row = threadIdx.x; row < m; row += blockDim.x) {
-      float al = -h[row];
-      for (int e = p.arp[sh.rp + row]; e < p.arp[sh.rp + row + 1]; ++e) al += p.acv[sh.ci + e] * z[p.aci[sh.ci + e]];
+      float al = -v.h[row];
+      for (int e = v.arp[row]; e < v.arp[row + 1]; ++e) al += v.acv[e] * z[v.aci[e]];
       const float s = al + lam[row];
-      const bool eq = p.aeq[sh.eq + row] != 0;
+      const bool eq = v.eq[row] != 0;
       const float bt = eq ? 0.f : fminf(s, 0.f);
       if (mask) mask[it * m + row] = (!eq && s <= 0.f);
       beta[row] = bt;
@@ -212,19 +296,20 @@ __device__ void inner_forward(const DP &p, const Shape &sh, const IDev &di, cons
 }
 
 // step 2 for the inner-ADMM devices: one CTA per device
-__global__ void __launch_bounds__(TBI) fwd_inner(DP p, St s, St nx, const float *XD, float *DEL) {
+__global__ void __launch_bounds__(TBI) fwd_inner(DP p, St s, St nx, const float *XD, float *DEL, int level) {
   extern __shared__ float sm[];
   const IDev di = p.idev[blockIdx.x];
   const Shape sh = p.shape[di.shape];
   const int n = sh.n, m = sh.m, T = p.T;
   float *x = sm, *r = x + T, *z = r + n, *w = z + n, *beta = w + m, *lam = beta + m;
+  const View v = stage_view(p, sh, di, lam + m, level);
   for (int t = threadIdx.x; t < T; t += blockDim.x) x[t] = XD[(size_t)di.dev * T + t];
   for (int row = threadIdx.x; row < m; row += blockDim.x) {
     beta[row] = s.INS[di.h + row];
     lam[row] = s.INS[p.Mtot + di.h + row];
   }
   __syncthreads();
-  inner_forward(p, sh, di, x, beta, lam, w, r, z, nullptr);
+  inner_forward(p, v, x, beta, lam, w, r, z, nullptr);
   for (int t = threadIdx.x; t < T; t += blockDim.x) {
     nx.PD[(size_t)di.dev * T + t] = z[t];
     if (di.bat >= 0) DEL[(size_t)di.bat * T + t] = z[2 * T + t];   // discharge, for the cost
@@ -242,7 +327,8 @@ __global__ void fwd_upd_nodes(DP p, St s, St nx) {
 
 __global__ void fwd_upd_lines(DP p, St s, St nx) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
-    const int t = (int)(i % p.T), l = (int)((i / p.T) % p.L), k = (int)(i / ((long long)p.T * p.L));
+    const unsigned q = i / (unsigned)p.T;
+    const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
     nx.V1[i] = s.V1[i] + nx.TH1[i] - nx.TBR[ni(p, k, p.n1[l], t)];
     nx.V2[i] = s.V2[i] + nx.TH2[i] - nx.TBR[ni(p, k, p.n2[l], t)];
   }
@@ -257,7 +343,8 @@ __global__ void fwd_upd_lines(DP p, St s, St nx) {
 // v' = v + theta' - theta_bar': A = d/d pbar', B = d/d theta_bar'
 __global__ void bwd_node1(DP p, Adj a, float *A, float *B) {
   GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
-    const int t = (int)(i % p.T), n = (int)((i / p.T) % p.N), k = (int)(i / ((long long)p.T * p.N));
+    const unsigned q = i / (unsigned)p.T;
+    const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
     float s = 0.f;
     for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
       const int c = p.lcode[j];
@@ -272,7 +359,8 @@ __global__ void bwd_node1(DP p, Adj a, float *A, float *B) {
 __global__ void bwd_line1(DP p, St s, Adj a, const float *A, const float *B, float *X1, float *X2, float *Y1,
                           float *Y2, float *GU) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
-    const int t = (int)(i % p.T), l = (int)((i / p.T) % p.L), k = (int)(i / ((long long)p.T * p.L));
+    const unsigned q = i / (unsigned)p.T;
+    const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
     const int n1 = p.n1[l], n2 = p.n2[l];
     const size_t o1 = ni(p, k, n1, t), o2 = ni(p, k, n2, t);
     const float lp = a.LP[i] - A[o1] / p.cnt[n1] + A[o2] / p.cnt[n2];
@@ -321,7 +409,7 @@ __device__ __forceinline__ float dev_lpd(const DP &p, const Adj &a, const float 
 
 __global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL, float *GP, float *XD, float *LPDT) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
-    const int t = (int)(i % p.T), d = (int)(i / p.T);
+    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T);
     const float lpd = dev_lpd(p, a, A, d, t);
     const float X = dev_x(p, s, d, t);
     if (p.kind[d] == 1) {
@@ -368,7 +456,7 @@ __global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL,
 //   d h += w, d beta = w, d lambda = d s - w.
 // `last`: the iteration whose battery discharge enters the cost.
 __global__ void __launch_bounds__(TBI) bwd_inner(DP p, St s, Adj a, const float *XD, const float *LPDT, float *LX,
-                                                 float *HB, int last) {
+                                                 float *HB, int last, int level) {
   extern __shared__ float sm[];
   const IDev di = p.idev[blockIdx.x];
   const Shape sh = p.shape[di.shape];
@@ -376,7 +464,8 @@ __global__ void __launch_bounds__(TBI) bwd_inner(DP p, St s, Adj a, const float 
   const float rho = p.rd, om = p.rd;
   float *x = sm, *r = x + T, *z = r + n, *w = z + n, *beta = w + m, *lam = beta + m;
   float *zt = lam + m, *rb = zt + n, *sb = rb + n, *bb = sb + m, *lb = bb + m, *hb = lb + m, *xb = hb + m;
-  unsigned char *mask = reinterpret_cast<unsigned char *>(xb + T);
+  const View v = stage_view(p, sh, di, xb + T, level);
+  unsigned char *mask = reinterpret_cast<unsigned char *>(xb + T + view_words(n, m, sh.nnz, level));
   for (int t = threadIdx.x; t < T; t += blockDim.x) {
     x[t] = XD[(size_t)di.dev * T + t];
     xb[t] = 0.f;
@@ -386,14 +475,14 @@ __global__ void __launch_bounds__(TBI) bwd_inner(DP p, St s, Adj a, const float 
     lam[row] = s.INS[p.Mtot + di.h + row];
   }
   __syncthreads();
-  inner_forward(p, sh, di, x, beta, lam, w, r, z, mask);
+  inner_forward(p, v, x, beta, lam, w, r, z, mask);
   for (int row = threadIdx.x; row < m; row += blockDim.x) {
     bb[row] = a.LINS[di.h + row];
     lb[row] = a.LINS[p.Mtot + di.h + row];
     hb[row] = 0.f;
   }
   __syncthreads();
-  const float *Mi = p.minv + di.minv;
+  const float *Mi = v.Mi;
   const float dcost = (last && di.bat >= 0) ? p.scost[di.bat] : 0.f;
   for (int it = N_INNER - 1; it >= 0; --it) {
     for (int row = threadIdx.x; row < m; row += blockDim.x) {
@@ -404,7 +493,7 @@ __global__ void __launch_bounds__(TBI) bwd_inner(DP p, St s, Adj a, const float 
     __syncthreads();
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       float acc = 0.f;
-      for (int e = p.atp[sh.tp + j]; e < p.atp[sh.tp + j + 1]; ++e) acc += p.atv[sh.ti + e] * sb[p.ati[sh.ti + e]];
+      for (int e = v.atp[j]; e < v.atp[j + 1]; ++e) acc += v.atv[e] * sb[v.ati[e]];
       if (it == N_INNER - 1) {           // the output: p = z_p, and the discharge z_delta in the cost
         if (j < T) acc += LPDT[(size_t)di.dev * T + j];
         else if (j >= 2 * T && j < 3 * T) acc += dcost;
@@ -421,7 +510,7 @@ __global__ void __launch_bounds__(TBI) bwd_inner(DP p, St s, Adj a, const float 
     for (int t = threadIdx.x; t < T; t += blockDim.x) xb[t] += rho * rb[t];
     for (int row = threadIdx.x; row < m; row += blockDim.x) {
       float acc = 0.f;
-      for (int e = p.arp[sh.rp + row]; e < p.arp[sh.rp + row + 1]; ++e) acc += p.acv[sh.ci + e] * rb[p.aci[sh.ci + e]];
+      for (int e = v.arp[row]; e < v.arp[row + 1]; ++e) acc += v.acv[e] * rb[v.aci[e]];
       const float wv = om * acc;
       hb[row] += wv;
       bb[row] = wv;
@@ -441,7 +530,8 @@ __global__ void __launch_bounds__(TBI) bwd_inner(DP p, St s, Adj a, const float 
 __global__ void bwd_node2(DP p, Adj a, const float *X1, const float *X2, const float *Y1, const float *Y2,
                           const float *LX, float *C, float *Dt) {
   GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
-    const int t = (int)(i % p.T), n = (int)((i / p.T) % p.N), k = (int)(i / ((long long)p.T * p.N));
+    const unsigned q = i / (unsigned)p.T;
+    const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
     float sx = 0.f, sy = 0.f, sd = 0.f;
     for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
       const int c = p.lcode[j];
@@ -460,7 +550,8 @@ __global__ void bwd_node2(DP p, Adj a, const float *X1, const float *X2, const f
 // the old node averages back onto the old line values and device powers
 __global__ void bwd_line2(DP p, Adj a, const float *C, const float *Dt) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
-    const int t = (int)(i % p.T), l = (int)((i / p.T) % p.L), k = (int)(i / ((long long)p.T * p.L));
+    const unsigned q = i / (unsigned)p.T;
+    const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
     const int n1 = p.n1[l], n2 = p.n2[l];
     const size_t o1 = ni(p, k, n1, t), o2 = ni(p, k, n2, t);
     a.LP[i] += -C[o1] / p.cnt[n1] + C[o2] / p.cnt[n2];
@@ -471,7 +562,7 @@ __global__ void bwd_line2(DP p, Adj a, const float *C, const float *Dt) {
 
 __global__ void bwd_dev2(DP p, Adj a, const float *LX, const float *C) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
-    const int t = (int)(i % p.T), d = (int)(i / p.T), n = p.dnode[d];
+    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T), n = p.dnode[d];
     float s = LX[i];
     for (int k = 0; k < p.Kp; ++k) s += C[ni(p, k, n, t)] / p.cnt[n];
     a.LPD[i] = s;
@@ -482,7 +573,7 @@ __global__ void bwd_dev2(DP p, Adj a, const float *LX, const float *C) {
 // battery discharge term enters through bwd_inner's `last`)
 __global__ void bwd_init(DP p, St s, Adj a, float *GL) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
-    const int t = (int)(i % p.T), d = (int)(i / p.T);
+    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T);
     if (d < p.G) {
       a.LPD[i] = 2.f * p.ga[d] * s.PD[i] + p.gb[d];
     } else if (d < p.G + p.D) {
@@ -495,10 +586,44 @@ __global__ void bwd_init(DP p, St s, Adj a, float *GL) {
   }
 }
 
+// the capacity rows of every ramp-limited generator (its first T inner rows,
+// p_t <= pmax_t) from the capacity data of this call
+__global__ void set_ramp_rhs(DP p, float *RH) {
+  GRID_STRIDE(i, (long long)p.n_inner * p.T) {
+    const int r = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)r * (unsigned)p.T);
+    const IDev di = p.idev[r];
+    if (di.bat < 0) RH[di.h + t] = p.gpmax[(size_t)di.dev * p.T + t];
+  }
+}
+
+// d f / d u_l: the limit is the same in every contingency and step, so the
+// per-(k, l, t) adjoints are summed (FP64, fixed order); and a ramp
+// generator's capacity gradient gains the adjoint of its capacity rows
+__global__ void finish_line_grad(DP p, const float *GU, float *out) {
+  GRID_STRIDE(l, (long long)p.L) {
+    double s = 0.0;
+    for (int k = 0; k < p.Kp; ++k)
+      for (int t = 0; t < p.T; ++t) s += GU[((size_t)k * p.L + l) * p.T + t];
+    out[l] = (float)s;
+  }
+}
+
+__global__ void finish_cap_grad(DP p, const float *HB, float *GP) {
+  GRID_STRIDE(i, (long long)p.n_inner * p.T) {
+    const int r = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)r * (unsigned)p.T);
+    const IDev di = p.idev[r];
+    if (di.bat < 0) GP[(size_t)di.dev * p.T + t] += HB[di.h + t];
+  }
+}
+
 int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + TB - 1) / TB, 8192)); }
 
-size_t fwd_inner_smem(int T, int n, int m) { return (size_t)(T + 2 * n + 3 * m) * sizeof(float); }
-size_t bwd_inner_smem(int T, int n, int m) { return (size_t)(2 * T + 4 * n + 7 * m) * sizeof(float) + (size_t)N_INNER * m; }
+size_t fwd_inner_smem(int T, int n, int m, int nnz, int level) {
+  return (size_t)(T + 2 * n + 3 * m + view_words(n, m, nnz, level)) * sizeof(float);
+}
+size_t bwd_inner_smem(int T, int n, int m, int nnz, int level) {
+  return (size_t)(2 * T + 4 * n + 7 * m + view_words(n, m, nnz, level)) * sizeof(float) + (size_t)N_INNER * m;
+}
 
 }  // namespace
 
@@ -512,9 +637,15 @@ struct opf_diff {
   std::vector<IDev> idev;
   int Mtot = 0;
   size_t smem_fwd = 0, smem_bwd = 0;
+  int stage = 0;         // what the inner kernels copy into shared memory (view_words)
   float *RH = nullptr;                                       // device copy of the right-hand sides
   std::vector<void *> allocs;
   size_t state_floats = 0;
+  // per-call buffers, kept between calls and grown when a call needs more:
+  // checkpoints, one segment of states, the adjoint, work arrays, the
+  // per-line limit gradient and the host staging of the cost's inputs
+  float *ck = nullptr, *seg = nullptr, *adj = nullptr, *work = nullptr, *gline = nullptr;
+  size_t ck_cap = 0, seg_cap = 0;
 };
 
 namespace {
@@ -667,7 +798,7 @@ void forward_step(const opf_diff *d, const St &s, const St &nx, float *XD, float
   const long long nl = (long long)p.Kp * p.L * p.T, nn = (long long)p.Kp * p.N * p.T, ns = (long long)p.S * p.T;
   fwd_line<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx);
   fwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, nx, XD);
-  if (p.n_inner) fwd_inner<<<p.n_inner, TBI, d->smem_fwd, d->stream>>>(p, s, nx, XD, DEL);
+  if (p.n_inner) fwd_inner<<<p.n_inner, TBI, d->smem_fwd, d->stream>>>(p, s, nx, XD, DEL, d->stage);
   fwd_avg<<<grid_for(nn), TB, 0, d->stream>>>(p, nx);
   fwd_upd_nodes<<<grid_for(nn), TB, 0, d->stream>>>(p, s, nx);
   fwd_upd_lines<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx);
@@ -691,6 +822,9 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
     if (net->hvdc_from[h] == net->hvdc_to[h] || !(net->hvdc_u[h] >= 0))
       return dfail(OPF_EINVAL, "diff: bad HVDC link");
   const int K = ctg ? ctg->K : 0;
+  if (K < 0) return dfail(OPF_EINVAL, "diff: K must be >= 0");
+  if ((double)(K + 1) * std::max(L, N) * T >= 2147483647.0 || (double)(G + D + B + 2 * H) * T >= 2147483647.0)
+    return dfail(OPF_EINVAL, "diff: (K+1) * max(lines, nodes) * T and devices * T must stay below 2^31");
   for (int l = 0; l < L; ++l) {
     const int a = net->line_from[l], c = net->line_to[l];
     if (a < 0 || a >= N || c < 0 || c >= N || a == c || !(net->line_b[l] > 0))
@@ -812,6 +946,7 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
       atp.push_back((int)(ati.size() - s.ti));
     }
     aeq.insert(aeq.end(), r.eq.begin(), r.eq.end());
+    s.nnz = (int)(aci.size() - s.ci);
     shapes.push_back(s);
     return (int)shapes.size() - 1;
   };
@@ -876,13 +1011,24 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   d->sdur.assign(net->stor_dur, net->stor_dur + B);
   d->scost.resize(B);
   for (int bt = 0; bt < B; ++bt) d->scost[bt] = (float)net->stor_cost[bt];
-  for (const Shape &s : shapes) {
-    d->smem_fwd = std::max(d->smem_fwd, fwd_inner_smem(T, s.n, s.m));
-    d->smem_bwd = std::max(d->smem_bwd, bwd_inner_smem(T, s.n, s.m));
-  }
   int dev = 0, smem_max = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // the inverse joins the staged structure while the reverse kernel's shared
+  // memory stays within 100 KB (two CTAs per SM); the structure alone while
+  // it fits; longer horizons read both from global memory
+  {
+    size_t with2 = 0, with1 = 0;
+    for (const Shape &s : shapes) {
+      with2 = std::max(with2, bwd_inner_smem(T, s.n, s.m, s.nnz, 2));
+      with1 = std::max(with1, std::max(bwd_inner_smem(T, s.n, s.m, s.nnz, 1), fwd_inner_smem(T, s.n, s.m, s.nnz, 1)));
+    }
+    d->stage = with2 <= 100 * 1024 ? 2 : (e == cudaSuccess && with1 <= (size_t)smem_max ? 1 : 0);
+  }
+  for (const Shape &s : shapes) {
+    d->smem_fwd = std::max(d->smem_fwd, fwd_inner_smem(T, s.n, s.m, s.nnz, d->stage));
+    d->smem_bwd = std::max(d->smem_bwd, bwd_inner_smem(T, s.n, s.m, s.nnz, d->stage));
+  }
   if (e == cudaSuccess && (d->smem_bwd > (size_t)smem_max || d->smem_fwd > (size_t)smem_max)) {
     delete d;
     return dfail(OPF_EINVAL, "diff: the horizon is too long for one inner-ADMM device per CTA");
@@ -946,6 +1092,19 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   U(&p.lu, d->lu);
   if (e == cudaSuccess) e = dalloc(d->allocs, &d->RH, (size_t)d->Mtot);
   p.RH = d->RH;
+  if (e == cudaSuccess && d->Mtot) {
+    // right-hand sides of the inner rows; a call rewrites the capacity rows
+    // of the ramp-limited generators from its capacity data (set_ramp_rhs)
+    std::vector<float> Hh((size_t)d->Mtot);
+    for (size_t r = 0; r < d->ramp_gens.size(); ++r) {
+      const int g = d->ramp_gens[r];
+      std::vector<double> pmd(net->gen_pmax + (size_t)g * T, net->gen_pmax + (size_t)(g + 1) * T);
+      ramp_rhs(T, d->gpmin.data() + (size_t)g * T, pmd.data(), d->ramp[r], Hh.data() + d->idev[r].h);
+    }
+    for (int bt = 0; bt < B; ++bt)
+      storage_rhs(T, d->sP[bt], d->sdur[bt], Hh.data() + d->idev[d->ramp_gens.size() + bt].h);
+    e = cudaMemcpy(d->RH, Hh.data(), Hh.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     for (void *q : d->allocs) cudaFree(q);
     delete d;
@@ -956,50 +1115,57 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   return OPF_OK;
 }
 
-opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const float *gen_pmax,
-                              const float *line_u, double *cost, float *g_load, float *g_pmax, float *g_u) {
+}  // extern "C"
+
+namespace {
+
+// grow one of the kept buffers to n floats (contents not kept)
+cudaError_t ensure(float **buf, size_t *cap, size_t n) {
+  if (*buf && *cap >= n) return cudaSuccess;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void **>(buf), std::max<size_t>(n, 1) * sizeof(float));
+  if (e == cudaSuccess) *cap = n;
+  return e;
+}
+
+opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p, const float *gen_pmax,
+                     const float *line_u, double *cost, float *g_load, float *g_pmax, float *g_u) {
   if (!d) return dfail(OPF_EINVAL, "diff is NULL");
   if (K < 1) return dfail(OPF_EINVAL, "diff: K must be >= 1");
   const DP &p = d->p;
   const int T = d->T;
   const size_t DT = (size_t)d->D * T, GT = (size_t)d->G * T, L = d->L, BT = (size_t)d->B * T;
-  const float *lp = load_p ? load_p : d->load_p.data();
-  const float *pm = gen_pmax ? gen_pmax : d->gpmax.data();
-  // right-hand sides of the inner rows (a ramp generator's first T rows are its capacity)
-  std::vector<float> H((size_t)d->Mtot);
-  for (size_t r = 0; r < d->ramp_gens.size(); ++r) {
-    const int g = d->ramp_gens[r];
-    std::vector<double> pmd(pm + (size_t)g * T, pm + (size_t)(g + 1) * T);
-    ramp_rhs(T, d->gpmin.data() + (size_t)g * T, pmd.data(), d->ramp[r], H.data() + d->idev[r].h);
-  }
-  for (int bt = 0; bt < d->B; ++bt)
-    storage_rhs(T, d->sP[bt], d->sdur[bt], H.data() + d->idev[d->ramp_gens.size() + bt].h);
-  DCK(cudaMemcpyAsync(const_cast<float *>(p.load_p), lp, DT * 4, cudaMemcpyHostToDevice, d->stream));
-  DCK(cudaMemcpyAsync(const_cast<float *>(p.gpmax), pm, GT * 4, cudaMemcpyHostToDevice, d->stream));
-  DCK(cudaMemcpyAsync(const_cast<float *>(p.lu), line_u ? line_u : d->lu.data(), L * 4, cudaMemcpyHostToDevice,
-                      d->stream));
-  if (d->Mtot) DCK(cudaMemcpyAsync(d->RH, H.data(), H.size() * 4, cudaMemcpyHostToDevice, d->stream));
+  const cudaMemcpyKind in_kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind out_kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  // this call's data (NULL: the network's own, kept on the host)
+  if (load_p) DCK(cudaMemcpyAsync(const_cast<float *>(p.load_p), load_p, DT * 4, in_kind, d->stream));
+  else DCK(cudaMemcpyAsync(const_cast<float *>(p.load_p), d->load_p.data(), DT * 4, cudaMemcpyHostToDevice, d->stream));
+  if (gen_pmax) DCK(cudaMemcpyAsync(const_cast<float *>(p.gpmax), gen_pmax, GT * 4, in_kind, d->stream));
+  else DCK(cudaMemcpyAsync(const_cast<float *>(p.gpmax), d->gpmax.data(), GT * 4, cudaMemcpyHostToDevice, d->stream));
+  if (line_u) DCK(cudaMemcpyAsync(const_cast<float *>(p.lu), line_u, L * 4, in_kind, d->stream));
+  else DCK(cudaMemcpyAsync(const_cast<float *>(p.lu), d->lu.data(), L * 4, cudaMemcpyHostToDevice, d->stream));
+  // the capacity rows of the ramp-limited generators' inner problems
+  if (p.n_inner) set_ramp_rhs<<<grid_for((long long)p.n_inner * T), TB, 0, d->stream>>>(p, d->RH);
   // states: checkpoints 0, C, 2C, ... and one segment of C + 1 states
   const int C = std::min(d->ckpt, K);
   const int n_ck = K / C + 1;
   const size_t SF = d->state_floats;
-  std::vector<void *> tmp;
-  auto release = [&]() {
-    for (void *q : tmp) cudaFree(q);
-  };
-  float *ck = nullptr, *seg = nullptr, *adj = nullptr, *work = nullptr;
   const size_t KLT = (size_t)d->Kp * d->L * T, KNT = (size_t)d->Kp * d->N * T, ST = (size_t)d->S * T;
   const size_t MT = (size_t)d->Mtot;
   const size_t adj_floats = 5 * KLT + ST + KNT + 2 * MT;
   const size_t work_floats = 5 * KLT + 4 * KNT + 3 * ST + DT + GT + MT + BT;
-  cudaError_t e = dalloc(tmp, &ck, (size_t)n_ck * SF);
-  if (e == cudaSuccess) e = dalloc(tmp, &seg, (size_t)(C + 1) * SF);
-  if (e == cudaSuccess) e = dalloc(tmp, &adj, adj_floats);
-  if (e == cudaSuccess) e = dalloc(tmp, &work, work_floats);
-  if (e != cudaSuccess) {
-    release();
+  const bool grads = g_load || g_pmax || g_u;
+  size_t adj_cap = d->adj ? adj_floats : 0, work_cap = d->work ? work_floats : 0, gl_cap = d->gline ? L : 0;
+  cudaError_t e = ensure(&d->ck, &d->ck_cap, (size_t)n_ck * SF);
+  if (e == cudaSuccess) e = ensure(&d->seg, &d->seg_cap, (size_t)(grads ? C + 1 : 2) * SF);
+  if (e == cudaSuccess) e = ensure(&d->adj, &adj_cap, adj_floats);
+  if (e == cudaSuccess) e = ensure(&d->work, &work_cap, work_floats);
+  if (e == cudaSuccess) e = ensure(&d->gline, &gl_cap, L);
+  if (e != cudaSuccess)
     return dfail(e == cudaErrorMemoryAllocation ? OPF_ENOMEM : OPF_ECUDA, "diff: device allocation failed");
-  }
+  float *ck = d->ck, *seg = d->seg, *adj = d->adj, *work = d->work;
   float *X1 = work, *X2 = X1 + KLT, *Y1 = X2 + KLT, *Y2 = Y1 + KLT, *GU = Y2 + KLT;
   float *A = GU + KLT, *Bn = A + KNT, *Cn = Bn + KNT, *Dn = Cn + KNT, *LX = Dn + KNT, *XD = LX + ST;
   float *LPDT = XD + ST, *GL = LPDT + ST, *GP = GL + DT, *HB = GP + GT, *DEL = HB + MT;
@@ -1015,14 +1181,12 @@ opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const
     cur = nx;
   }
   if (e == cudaSuccess) e = cudaGetLastError();
-  std::vector<float> pd(ST), del(BT);
+  std::vector<float> pd(ST), del(BT), lp(DT);
   if (e == cudaSuccess) e = cudaMemcpyAsync(pd.data(), cur.PD, ST * 4, cudaMemcpyDeviceToHost, d->stream);
   if (e == cudaSuccess && BT) e = cudaMemcpyAsync(del.data(), DEL, BT * 4, cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess && DT) e = cudaMemcpyAsync(lp.data(), p.load_p, DT * 4, cudaMemcpyDeviceToHost, d->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
-  if (e != cudaSuccess) {
-    release();
-    return dfail(OPF_ECUDA, cudaGetErrorString(e));
-  }
+  if (e != cudaSuccess) return dfail(OPF_ECUDA, cudaGetErrorString(e));
   if (cost) {
     double f = 0.0;
     for (int g = 0; g < d->G; ++g)
@@ -1039,10 +1203,7 @@ opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const
       for (int t = 0; t < T; ++t) f += (double)d->scost[bt] * del[(size_t)bt * T + t];
     *cost = f;
   }
-  if (!g_load && !g_pmax && !g_u) {
-    release();
-    return OPF_OK;
-  }
+  if (!grads) return OPF_OK;
   // reverse pass
   Adj a;
   a.LP = adj;
@@ -1069,7 +1230,8 @@ opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const
       bwd_line1<<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, Bn, X1, X2, Y1, Y2, GU);
       bwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT);
       if (p.n_inner)
-        bwd_inner<<<p.n_inner, TBI, d->smem_bwd, d->stream>>>(p, s, a, XD, LPDT, LX, HB, i == K ? 1 : 0);
+        bwd_inner<<<p.n_inner, TBI, d->smem_bwd, d->stream>>>(p, s, a, XD, LPDT, LX, HB, i == K ? 1 : 0,
+                                                             d->stage);
       bwd_node2<<<grid_for(nn), TB, 0, d->stream>>>(p, a, X1, X2, Y1, Y2, LX, Cn, Dn);
       bwd_line2<<<grid_for(nl), TB, 0, d->stream>>>(p, a, Cn, Dn);
       bwd_dev2<<<grid_for(ns), TB, 0, d->stream>>>(p, a, LX, Cn);
@@ -1077,36 +1239,39 @@ opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const
     hi = lo;
     if (e == cudaSuccess) e = cudaGetLastError();
   }
-  std::vector<float> gu(KLT), hb(MT), gp(GT);
-  if (e == cudaSuccess && g_load) e = cudaMemcpyAsync(g_load, GL, DT * 4, cudaMemcpyDeviceToHost, d->stream);
-  if (e == cudaSuccess && g_pmax) e = cudaMemcpyAsync(gp.data(), GP, GT * 4, cudaMemcpyDeviceToHost, d->stream);
-  if (e == cudaSuccess && g_pmax && MT) e = cudaMemcpyAsync(hb.data(), HB, MT * 4, cudaMemcpyDeviceToHost, d->stream);
-  if (e == cudaSuccess && g_u) e = cudaMemcpyAsync(gu.data(), GU, KLT * 4, cudaMemcpyDeviceToHost, d->stream);
+  if (e == cudaSuccess && g_pmax && p.n_inner)
+    finish_cap_grad<<<grid_for((long long)p.n_inner * T), TB, 0, d->stream>>>(p, HB, GP);
+  if (e == cudaSuccess && g_u) finish_line_grad<<<grid_for((long long)L), TB, 0, d->stream>>>(p, GU, d->gline);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess && g_load) e = cudaMemcpyAsync(g_load, GL, DT * 4, out_kind, d->stream);
+  if (e == cudaSuccess && g_pmax) e = cudaMemcpyAsync(g_pmax, GP, GT * 4, out_kind, d->stream);
+  if (e == cudaSuccess && g_u) e = cudaMemcpyAsync(g_u, d->gline, L * 4, out_kind, d->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
-  release();
   if (e != cudaSuccess) return dfail(OPF_ECUDA, cudaGetErrorString(e));
-  if (g_pmax) {
-    // a ramp generator's capacity is the right-hand side of its first T rows
-    for (size_t r = 0; r < d->ramp_gens.size(); ++r)
-      for (int t = 0; t < T; ++t) gp[(size_t)d->ramp_gens[r] * T + t] += hb[d->idev[r].h + t];
-    std::copy(gp.begin(), gp.end(), g_pmax);
-  }
-  if (g_u) {
-    // d f / d u_l: the limit is the same in every contingency and step
-    for (int l = 0; l < d->L; ++l) {
-      double s = 0.0;
-      for (int k = 0; k < d->Kp; ++k)
-        for (int t = 0; t < T; ++t) s += gu[((size_t)k * d->L + l) * T + t];
-      g_u[l] = (float)s;
-    }
-  }
   return OPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+opf_status opf_diff_cost_grad(opf_diff *d, int32_t K, const float *load_p, const float *gen_pmax,
+                              const float *line_u, double *cost, float *g_load, float *g_pmax, float *g_u) {
+  return cost_grad(d, K, 0, load_p, gen_pmax, line_u, cost, g_load, g_pmax, g_u);
+}
+
+opf_status opf_diff_cost_grad_on(opf_diff *d, int32_t K, int32_t on_device, const float *load_p,
+                                 const float *gen_pmax, const float *line_u, double *cost, float *g_load,
+                                 float *g_pmax, float *g_u) {
+  return cost_grad(d, K, on_device ? 1 : 0, load_p, gen_pmax, line_u, cost, g_load, g_pmax, g_u);
 }
 
 void opf_diff_destroy(opf_diff *d) {
   if (!d) return;
   cudaStreamSynchronize(d->stream);
   for (void *q : d->allocs) cudaFree(q);
+  for (float *q : {d->ck, d->seg, d->adj, d->work, d->gline})
+    if (q) cudaFree(q);
   delete d;
 }
 

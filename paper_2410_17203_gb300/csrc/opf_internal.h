@@ -131,6 +131,17 @@ struct Params {
   long long adapt_until;  // last iteration that may adapt (0 = no limit)
   double *hist;         // residual history ring [hist_cap][HIST_COLS]
   int hist_cap;
+  // contingency slice (opf_create_slice): this context holds contingencies
+  // k_base .. k_base + Kp - 1 of Kp_glob; the sums over k that couple them
+  // (Section 3.2 step 2) and the residual sums (Section 3.3) go through the
+  // exchange buffer xsum, which the caller sums over the slices:
+  //   [n_dnode][T] sum_k (pbar + u) at the nodes with devices,
+  //   [n_dnode][T] sum_k u there (on adaptation iterations; else 0),
+  //   [NSLOT] residual partial sums
+  int Kp_glob;          // K + 1 of the whole problem (= Kp without slices)
+  int k_base;
+  int slice;            // 1: a slice context
+  double *xsum;
 };
 
 // columns of a residual-history row (include/opf.h, opf_history)
@@ -221,6 +232,14 @@ int opfk_export_pdev_launch(const opfk::Params &p, float *out, void *stream);
 int opfk_export_nodes_launch(const opfk::Params &p, int cur, float *u, float *theta_node,
                              float *price, void *stream);
 int opfk_set_rho_launch(opfk::DevScalars *sc, double rho, void *stream);
+// Contingency slices: the local half of one iteration (devices from the
+// exchanged sums, line proxes, node sums, then this slice's sums into the
+// exchange buffer) and the decisions from the exchanged sums; `prime`
+// writes the sums of the current state (before the first iteration).
+int opfk_slice_local_enqueue(const opfk::Params &p, const opfk::IterPlan &plan, void *main_stream,
+                             void *aux_stream, void *ev_fork, void *ev_join);
+int opfk_slice_finish_enqueue(const opfk::Params &p, void *stream);
+int opfk_slice_prime_launch(const opfk::Params &p, void *stream);
 }
 
 #endif  // OPF_INTERNAL_H_

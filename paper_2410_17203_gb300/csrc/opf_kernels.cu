@@ -821,7 +821,7 @@ __device__ __forceinline__ Iter iter_scalars(const Params &p) {
     r.frt = (float)sc.rho_th;
     r.fsu = (float)sc.su;
     r.fsv = (float)sc.sv;
-    r.rho_dev = (float)(p.Kp * sc.rho_p);   // rho' = (K+1) rho_p
+    r.rho_dev = (float)(p.Kp_glob * sc.rho_p);   // rho' = (K+1) rho_p
     r.old = (int)(sc.it & 1);
     r.nw = r.old ^ 1;
     r.v_fresh = sc.v_fresh;
@@ -845,7 +845,7 @@ __device__ __forceinline__ void xs_body(const Params &p, unsigned bid, unsigned 
   const Iter q = iter_scalars(p);
   if (q.skip) return;
   const int T = p.T, TV = T / VW, Kp = p.Kp;
-  const float kpf = (float)Kp, rkp = __frcp_rn(kpf);
+  const float kpf = (float)p.Kp_glob, rkp = __frcp_rn(kpf);
   const size_t KT = (size_t)Kp * T;    // a node's K+1 rows are contiguous
   // avg_k(pbar + s u) = (sum_k PU + (s - 1) sum_k u) / (K+1); u is read only
   // while a penalty rescale s != 1 is pending
@@ -857,7 +857,12 @@ __device__ __forceinline__ void xs_body(const Params &p, unsigned bid, unsigned 
     const int ci = (int)(item / (unsigned)TV), t0 = (int)(item % (unsigned)TV) * VW;
     const size_t on = (size_t)p.dnode_ids[ci] * T + t0, ok = (size_t)p.dnode_ids[ci] * KT + t0;
     FV<VW> xs;
-    if constexpr (VW == 4) {
+    if (p.slice) {
+      // a contingency slice: the sums over every slice's k, exchanged
+      const double *esp = p.xsum + (size_t)ci * T + t0, *esq = p.xsum + (size_t)(p.n_dnode + ci) * T + t0;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) xs.v[e] = div_rn(fmaf(sm1, (float)esq[e], (float)esp[e]), kpf, rkp);
+    } else if constexpr (VW == 4) {
       float4 sp, sq;
       ksum4(Wo, rescale ? Uo : nullptr, ok, T, Kp, sp, sq);   // sum_k PU, sum_k u
       xs.v[0] = div_rn(fmaf(sm1, sq.x, sp.x), kpf, rkp);
@@ -1027,6 +1032,35 @@ __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int f
 // in FP64 and a fixed order, the stopping test of Eq. (converge) and the
 // adaptive penalty (Section 3.5); advances the iteration counter.
 // ---------------------------------------------------------------------------
+// the node kernel's n_part CTA partial sums reduced in FP64 and a fixed
+// order; thread 0 returns true with the totals
+__device__ __forceinline__ bool reduce_partials(const Params &p, int n_part, double tot[NSLOT],
+                                                double (*red)[NSLOT]) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) tot[s] = 0.0;
+  for (int b = threadIdx.x; b < n_part; b += BLOCK) {
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) tot[s] += p.partials[(size_t)b * NSLOT + s];
+  }
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    double v = tot[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wib][s] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return false;
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    double v = 0.0;
+    for (int w = 0; w < WARPS; ++w) v += red[w][s];
+    tot[s] = v;
+  }
+  return true;
+}
+
 __device__ __forceinline__ void decide_body(const Params &p, int n_part) {
   __shared__ double red[WARPS][NSLOT];
   const Iter q = iter_scalars(p);
@@ -1044,28 +1078,14 @@ __device__ __forceinline__ void decide_body(const Params &p, int n_part) {
     }
     return;
   }
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double tot[NSLOT];
+  if (p.slice) {
+    // a contingency slice: the residual sums of every slice, exchanged
+    if (threadIdx.x != 0) return;
 #pragma unroll
-  for (int s = 0; s < NSLOT; ++s) tot[s] = 0.0;
-  for (int b = threadIdx.x; b < n_part; b += BLOCK) {
-#pragma unroll
-    for (int s = 0; s < NSLOT; ++s) tot[s] += p.partials[(size_t)b * NSLOT + s];
-  }
-#pragma unroll
-  for (int s = 0; s < NSLOT; ++s) {
-    double v = tot[s];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wib][s] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-#pragma unroll
-  for (int s = 0; s < NSLOT; ++s) {
-    double v = 0.0;
-    for (int w = 0; w < WARPS; ++w) v += red[w][s];
-    tot[s] = v;
+    for (int s = 0; s < NSLOT; ++s) tot[s] = p.xsum[(size_t)2 * p.n_dnode * p.T + s];
+  } else {
+    if (!reduce_partials(p, n_part, tot, red)) return;
   }
   DevScalars sc = *p.sc;
   const long long itn = sc.it + 1;
@@ -1176,6 +1196,53 @@ __global__ void __launch_bounds__(BLOCK, NODE_LEAN_CTAS) node_kernel_lean(Params
 }
 
 __global__ void __launch_bounds__(BLOCK) decide_kernel(Params p, int n_part) { decide_body(p, n_part); }
+
+// A contingency slice's contributions to the exchange (after its node
+// sums): sum over its k of pbar + u at every node with devices, the same of
+// u on adaptation iterations (whose decision may rescale u before the next
+// device prox reads it), and its residual partial sums on iterations that
+// form residuals.  A stopped context (and `prime`, before the first
+// iteration) contributes the sums of its current state, so that the
+// caller's exchange always sums fresh contributions of every slice.
+__global__ void __launch_bounds__(BLOCK) slice_sums_kernel(Params p, int prime) {
+  __shared__ double red[WARPS][NSLOT];
+  __shared__ int s_buf, s_with_u, s_res;
+  if (threadIdx.x == 0) {
+    const DevScalars sc = *p.sc;
+    const long long itn = sc.it + 1;
+    const bool stopped = sc.status != 0 || sc.stop != 0;
+    const bool current = prime || stopped;
+    const int old = (int)(sc.it & 1);
+    s_buf = current ? old : old ^ 1;
+    s_with_u = current || adapt_at(p, sc, itn);
+    s_res = !current && ((p.adapt_every > 0 && adapt_at(p, sc, itn)) ||
+                         (p.eps > 0 && p.check_every > 0 && itn % p.check_every == 0) || itn >= sc.it_last);
+  }
+  __syncthreads();
+  const int T = p.T, Kp = p.Kp;
+  const size_t KT = (size_t)Kp * T;
+  const float *W = p.PU[s_buf], *U = p.U[s_buf];
+  const bool with_u = s_with_u != 0;
+  double *esp = p.xsum, *esq = p.xsum + (size_t)p.n_dnode * T;
+  for (long long i = (long long)blockIdx.x * BLOCK + threadIdx.x; i < (long long)p.n_dnode * T;
+       i += (long long)gridDim.x * BLOCK) {
+    const int ci = (int)(i / T), t = (int)(i % T);
+    float sp, sq;
+    ksum(W, with_u ? U : nullptr, (size_t)p.dnode_ids[ci] * KT + t, T, Kp, sp, sq);
+    esp[i] = (double)sp;
+    esq[i] = (double)sq;
+  }
+  if (blockIdx.x == 0) {
+    double tot[NSLOT];
+    double *tail = p.xsum + (size_t)2 * p.n_dnode * T;
+    if (s_res) {
+      if (reduce_partials(p, p.node_grid, tot, red))
+        for (int s = 0; s < NSLOT; ++s) tail[s] = tot[s];
+    } else if (threadIdx.x < NSLOT) {
+      tail[threadIdx.x] = 0.0;
+    }
+  }
+}
 
 // the instance of this CTA: its parameters copied to shared memory, and
 // (block, blocks) within the instance
@@ -1553,8 +1620,10 @@ int opfk_plan(const Params &p, IterPlan *plan) {
   return 0;
 }
 
-int opfk_iteration_enqueue(const Params &p, const IterPlan &plan, void *main_stream, void *aux_stream,
-                           void *ev_fork, void *ev_join) {
+static int aux_grid(long long work);
+
+static int iteration_enqueue(const Params &p, const IterPlan &plan, void *main_stream, void *aux_stream,
+                             void *ev_fork, void *ev_join, bool slice) {
   cudaStream_t sm = (cudaStream_t)main_stream, sa = (cudaStream_t)aux_stream;
   const bool v4 = (p.T % 4 == 0), v2 = (p.T % 2 == 0);
   // The line proxes of slab s (aux stream) read only the previous iterate;
@@ -1590,7 +1659,28 @@ int opfk_iteration_enqueue(const Params &p, const IterPlan &plan, void *main_str
     else if (vn) node_kernel<NODE_VW, true><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
     else node_kernel<1, true><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
   }
-  decide_kernel<<<1, BLOCK, 0, sm>>>(p, plan.node_grid);
+  if (slice) slice_sums_kernel<<<aux_grid((long long)p.n_dnode * p.T), BLOCK, 0, sm>>>(p, 0);
+  else decide_kernel<<<1, BLOCK, 0, sm>>>(p, plan.node_grid);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int opfk_iteration_enqueue(const Params &p, const IterPlan &plan, void *main_stream, void *aux_stream,
+                           void *ev_fork, void *ev_join) {
+  return iteration_enqueue(p, plan, main_stream, aux_stream, ev_fork, ev_join, false);
+}
+
+int opfk_slice_local_enqueue(const Params &p, const IterPlan &plan, void *main_stream, void *aux_stream,
+                             void *ev_fork, void *ev_join) {
+  return iteration_enqueue(p, plan, main_stream, aux_stream, ev_fork, ev_join, true);
+}
+
+int opfk_slice_finish_enqueue(const Params &p, void *stream) {
+  decide_kernel<<<1, BLOCK, 0, (cudaStream_t)stream>>>(p, p.node_grid);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int opfk_slice_prime_launch(const Params &p, void *stream) {
+  slice_sums_kernel<<<aux_grid((long long)p.n_dnode * p.T), BLOCK, 0, (cudaStream_t)stream>>>(p, 1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -242,3 +242,18 @@ def test_warm_start_network_arguments_are_checked(lib):
     with pytest.raises(OpfError, match="params has 5 values"):
         WarmStartNet(4, [0, 1, 2], [1, 2, 3], [1.0, 1.0, 1.0], 2, 3, params=np.zeros(5, np.float32))
     assert b.opf_wsnet_param_count(3) == 64 * 3 + 64 + 3 * (2 * 64 * 64 + 64) + 64 * 2 + 2
+
+
+def test_slice_range_is_checked_on_the_host(lib):
+    """opf_create_slice refuses an empty or out-of-range block of
+    contingencies, and over-relaxation, before touching the device."""
+    from gridgen import make_case
+    from paper_2410_17203_gb300 import OpfError, opf_create_slice
+    case = make_case("tiny")                     # K = 5: contingencies 0 .. 5
+    for a, b in [(0, 0), (3, 2), (-1, 2), (0, 7), (6, 7)]:
+        with pytest.raises(OpfError) as e:
+            opf_create_slice(case, a, b)
+        assert e.value.status == 1, (a, b)
+    with pytest.raises(OpfError) as e:
+        opf_create_slice(case, 0, 3, dict(alpha=1.5))
+    assert e.value.status == 1

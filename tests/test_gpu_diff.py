@@ -183,6 +183,41 @@ def test_autograd_function():
         d.close()
 
 
+def test_device_tensors_match_host_arrays_and_calls_repeat():
+    """opf_diff_cost_grad_on with device pointers returns what the host-array
+    entry returns, bit for bit (the same kernels on the same data); calls of
+    different lengths reuse the context's buffers and repeat exactly; the
+    autograd function keeps CUDA tensors on the device."""
+    b = _lib()
+    case = make_case(scale_case(80, 6, 3, seed=12, stor_per_node=0.1))
+    d = b.UnrolledCost(case, rho_p=2.0, rho_theta=5.0, checkpoint_every=7)
+    try:
+        rng = np.random.default_rng(3)
+        lp = np.asarray(case["load_p"]) * rng.uniform(0.9, 1.1, size=np.shape(case["load_p"]))
+        pm = np.asarray(case["gen_pmax"]) * rng.uniform(0.9, 1.1, size=np.shape(case["gen_pmax"]))
+        lu = np.asarray(case["line_u"]) * rng.uniform(0.9, 1.1, size=np.shape(case["line_u"]))
+        f_h, g_h = d.cost_grad(40, lp, pm, lu)
+        dv = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in (lp, pm, lu)]
+        f_d, g_d = d.cost_grad_device(40, *dv)
+        assert f_d == f_h
+        for k in g_h:
+            np.testing.assert_array_equal(g_d[k].cpu().numpy(), g_h[k], err_msg=k)
+        f_short, _ = d.cost_grad(13, lp, pm, lu)         # a shorter call in between
+        f_again, g_again = d.cost_grad(40, lp, pm, lu)
+        assert f_again == f_h and f_short != f_h
+        for k in g_h:
+            np.testing.assert_array_equal(g_again[k], g_h[k], err_msg=k)
+        xs = [x.clone().requires_grad_(True) for x in dv]
+        f = b.unrolled_cost(d, 40, *xs)
+        assert f.is_cuda and float(f.detach()) == float(np.float32(f_h))   # a float32 tensor
+        f.backward()
+        for x, k in zip(xs, ("load_p", "gen_pmax", "line_u")):
+            assert x.grad.is_cuda
+            np.testing.assert_array_equal(x.grad.cpu().numpy(), g_h[k], err_msg=k)
+    finally:
+        d.close()
+
+
 def test_gradients_approach_the_duals():
     """Section 5.5: with more unrolled iterations the derivatives approach
     the sensitivities of the optimal cost -- the nodal price for a fixed load
