@@ -189,3 +189,32 @@ def test_slices_continue_from_an_imported_state():
     finally:
         sl.close()
         whole.close()
+
+
+@pytest.mark.slow
+def test_benchmark_instance_as_four_slices():
+    """The 10k workload (K = 50) split into four slices of 13, 13, 13 and 12
+    contingencies, the launch configuration of a four-GPU benchmark run:
+    after 20 iterations (two adaptations) every state array within the
+    split-sum bound of the whole context, the same penalties and
+    residuals."""
+    from paper_2410_17203_gb300 import Solver, opf_get_info, opf_residuals
+    case = make_case("10k")
+    opts = dict(adapt_every=10, eps=0.0)
+    blocks = np.array_split(np.arange(51), 4)
+    sl = Slices(case, [(int(b[0]), int(b[-1]) + 1) for b in blocks], opts)
+    whole = Solver(case, opts)
+    try:
+        sl.iterate(20)
+        whole.iterate(20)
+        st, ref = sl.state(), whole.state()
+        for k in ref:
+            assert rel_err(st[k], ref[k]) <= SPLIT_RTOL * 20, (k, rel_err(st[k], ref[k]))
+        iw = whole.get_info()
+        for h in sl.hs:
+            i = opf_get_info(h)
+            assert (i["rho_p"], i["rho_theta"], i["iterations"]) == (iw["rho_p"], iw["rho_theta"], 20)
+            np.testing.assert_allclose(opf_residuals(h), whole.residuals(), rtol=1e-4)
+    finally:
+        sl.close()
+        whole.close()
