@@ -74,6 +74,83 @@ __global__ void __launch_bounds__(TB) linear_kernel(const float *__restrict__ a,
   }
 }
 
+// The same for J = 64 outputs, register-tiled: a CTA computes TROWS rows x
+// 64 columns, each thread 8 rows x 4 columns in registers (32 products per
+// 12 shared-memory reads), with the layer's weights staged once per TROWS
+// rows (the kernel above re-stages them for every 32 rows and runs one
+// dependent chain of K products per output).  Shared memory: the weights
+// [K][64] (twice with a2) and the row tiles [TROWS][K + 1] (the padding
+// spreads a column's rows over the banks).
+constexpr int TROWS = 128;
+
+__host__ __device__ inline size_t linear64_smem(int K, bool two) {
+  return ((size_t)(two ? 2 : 1) * (K * HID + TROWS * (K + 1))) * sizeof(float);
+}
+
+template <bool TRANS>
+__global__ void __launch_bounds__(TB) linear64_kernel(const float *__restrict__ a, const __nv_bfloat16 *__restrict__ W,
+                                                      const float *__restrict__ a2,
+                                                      const __nv_bfloat16 *__restrict__ W2,
+                                                      const float *__restrict__ bias, float *out, float *pre, int R,
+                                                      int K, int relu, int accum) {
+  extern __shared__ float sm64[];
+  const int KP = K + 1;
+  float *ws = sm64, *at = ws + K * HID;
+  float *ws2 = at + TROWS * KP, *at2 = ws2 + K * HID;
+  const int r0 = blockIdx.x * TROWS;
+  for (int i = threadIdx.x; i < K * HID; i += TB) {
+    const int k = i / HID, j = i - k * HID;
+    const int src = TRANS ? j * K + k : k * HID + j;
+    ws[i] = __bfloat162float(W[src]);
+    if (a2) ws2[i] = __bfloat162float(W2[src]);
+  }
+  for (int i = threadIdx.x; i < TROWS * K; i += TB) {
+    const int rr = i / K, k = i - rr * K;
+    const int r = r0 + rr;
+    at[rr * KP + k] = r < R ? a[(size_t)r * K + k] : 0.f;
+    if (a2) at2[rr * KP + k] = r < R ? a2[(size_t)r * K + k] : 0.f;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // columns 4 tx .. 4 tx + 3, rows 8 ty .. 8 ty + 7
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
+  for (int pass = 0; pass < (a2 ? 2 : 1); ++pass) {
+    const float *A = pass ? at2 : at, *Ws = pass ? ws2 : ws;
+    for (int k = 0; k < K; ++k) {
+      const float4 w4 = *reinterpret_cast<const float4 *>(Ws + k * HID + 4 * tx);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float av = A[(8 * ty + i) * KP + k];
+        acc[i][0] = fmaf(av, w4.x, acc[i][0]);
+        acc[i][1] = fmaf(av, w4.y, acc[i][1]);
+        acc[i][2] = fmaf(av, w4.z, acc[i][2]);
+        acc[i][3] = fmaf(av, w4.w, acc[i][3]);
+      }
+    }
+  }
+  float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (bias) b4 = *reinterpret_cast<const float4 *>(bias + 4 * tx);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = r0 + 8 * ty + i;
+    if (r >= R) break;
+    const size_t oi = (size_t)r * HID + 4 * tx;
+    float4 v = make_float4(acc[i][0] + b4.x, acc[i][1] + b4.y, acc[i][2] + b4.z, acc[i][3] + b4.w);
+    if (accum) {
+      const float4 o = *reinterpret_cast<const float4 *>(out + oi);
+      v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+    }
+    if (pre) *reinterpret_cast<float4 *>(pre + oi) = v;
+    if (relu) {
+      v.x = fmaxf(v.x, 0.f); v.y = fmaxf(v.y, 0.f); v.z = fmaxf(v.z, 0.f); v.w = fmaxf(v.w, 0.f);
+    }
+    *reinterpret_cast<float4 *>(out + oi) = v;
+  }
+}
+
 // out[t, n][c] = sum_{j in ptr[n]..ptr[n+1]} w[j] in[t, nbr[j]][c]
 __global__ void __launch_bounds__(TB) agg_kernel(const float *__restrict__ in, float *__restrict__ out,
                                                  const int *__restrict__ ptr, const int *__restrict__ nbr,
@@ -130,6 +207,48 @@ __global__ void __launch_bounds__(TB) wgrad_part_kernel(const float *__restrict_
   for (int q = 0; q < 16; ++q) {
     const int o = threadIdx.x + q * TB;
     if (o < K * J) part[(size_t)blockIdx.x * K * J + o] = acc[q];
+  }
+}
+
+// The same for J = 64 and K <= 64, register-tiled: thread (ty, tx) keeps the
+// 4 x 4 block k = 4 ty .., j = 4 tx .. of the partial sums (16 products per 8
+// shared-memory reads); every output still sums the CTA's rows in order, so
+// the partial sums equal the kernel above's.
+__global__ void __launch_bounds__(TB) wgrad64_part_kernel(const float *__restrict__ a, const float *__restrict__ g,
+                                                          float *__restrict__ part, int R, int K) {
+  __shared__ __align__(16) float at[ROWS * HID], gt[ROWS * HID];
+  const int r0 = blockIdx.x * GRAD_ROWS, r1 = min(R, r0 + GRAD_ROWS);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
+  for (int rb = r0; rb < r1; rb += ROWS) {
+    const int nr = min(ROWS, r1 - rb);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ROWS * HID; i += TB) {
+      const int rr = i / HID, k = i - rr * HID;
+      at[i] = (rr < nr && k < K) ? a[(size_t)(rb + rr) * K + k] : 0.f;
+      gt[i] = rr < nr ? g[(size_t)(rb + rr) * HID + k] : 0.f;
+    }
+    __syncthreads();
+    for (int rr = 0; rr < nr; ++rr) {
+      const float4 a4 = *reinterpret_cast<const float4 *>(at + rr * HID + 4 * ty);
+      const float4 g4 = *reinterpret_cast<const float4 *>(gt + rr * HID + 4 * tx);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(av[i], gv[c], acc[i][c]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int k = 4 * ty + i;
+    if (k < K)
+      *reinterpret_cast<float4 *>(part + (size_t)blockIdx.x * K * HID + (size_t)k * HID + 4 * tx) =
+          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
   }
 }
 
@@ -255,8 +374,17 @@ void he_init(std::vector<float> &p, const opf_wsnet *w, uint64_t seed) {
 
 void launch_linear(const opf_wsnet *w, bool trans, const float *a, long long oW, const float *a2, long long oW2,
                    const float *bias, float *out, float *pre, int K, int J, bool relu, bool accum) {
-  const int grid = (w->R + ROWS - 1) / ROWS;
   const __nv_bfloat16 *W = w->Pb + oW, *W2 = a2 ? w->Pb + oW2 : nullptr;
+  if (J == HID) {
+    const int g = (w->R + TROWS - 1) / TROWS;
+    const size_t sm = linear64_smem(K, a2 != nullptr);
+    if (trans)
+      linear64_kernel<true><<<g, TB, sm, w->stream>>>(a, W, a2, W2, bias, out, pre, w->R, K, relu, accum);
+    else
+      linear64_kernel<false><<<g, TB, sm, w->stream>>>(a, W, a2, W2, bias, out, pre, w->R, K, relu, accum);
+    return;
+  }
+  const int grid = (w->R + ROWS - 1) / ROWS;
   if (trans)
     linear_kernel<true><<<grid, TB, 0, w->stream>>>(a, W, a2, W2, bias, out, pre, w->R, K, J, relu, accum);
   else
@@ -264,7 +392,10 @@ void launch_linear(const opf_wsnet *w, bool trans, const float *a, long long oW,
 }
 
 void launch_wgrad(opf_wsnet *w, const float *a, const float *g, int K, int J, long long off) {
-  wgrad_part_kernel<<<w->n_gpart, TB, 0, w->stream>>>(a, g, w->part, w->R, K, J);
+  if (a && J == HID)
+    wgrad64_part_kernel<<<w->n_gpart, TB, 0, w->stream>>>(a, g, w->part, w->R, K);
+  else
+    wgrad_part_kernel<<<w->n_gpart, TB, 0, w->stream>>>(a, g, w->part, w->R, K, J);
   wgrad_sum_kernel<<<(K * J + TB - 1) / TB, TB, 0, w->stream>>>(w->part, w->G + off, w->n_gpart, K * J);
 }
 
@@ -412,6 +543,13 @@ opf_status opf_wsnet_create(int32_t n_nodes, int32_t n_lines, const int32_t *lin
   A(&w->dC, RH);
   A(&w->part, (size_t)w->n_gpart * HID * HID);
   A(&w->lpart, w->n_lpart);
+  // the register-tiled layers use up to 97 KB of shared memory per CTA
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(linear64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)linear64_smem(HID, true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(linear64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)linear64_smem(HID, true));
   std::vector<float> p0(w->C);
   if (params) std::memcpy(p0.data(), params, w->C * sizeof(float));
   else he_init(p0, w, seed);

@@ -20,9 +20,9 @@ def _lib():
     load_library()
 
 
-def _setup(T=5, F=6, seed=0):
+def _setup(T=5, F=6, seed=0, case=None):
     import torch
-    case = make_case("tiny")
+    case = case or make_case("tiny")
     N = case["n_nodes"]
     rng = np.random.default_rng(seed)
     X = rng.normal(size=(T * N, F)).astype(np.float32)
@@ -88,4 +88,35 @@ def test_adam_step_matches_reference_and_training_lowers_the_loss():
     np.testing.assert_allclose(got[big], want[big], rtol=0, atol=2e-6)
     losses = [l0] + [net.train_step(xd, yd, scale, lr) for _ in range(60)]
     assert losses[-1] < 0.5 * losses[0]
+    net.close()
+
+
+@pytest.mark.parametrize("F", [9, 64])
+def test_forward_and_gradient_over_many_row_tiles(F):
+    """A 300-bus grid over 24 steps (7,200 rows: 56 full tiles of the
+    register-tiled layers and a ragged one), with the bench's nine features
+    and with the largest feature count the network takes (forward only: with
+    64 unit-variance inputs many first-layer pre-activations sit within FP32
+    rounding of the ReLU kink, where the FP32 and FP64 gradients take
+    different branches)."""
+    import torch
+    from gridgen import scale_case
+    from paper_2410_17203_gb300 import WarmStartNet
+    case, N, T, F, X, Yt, params, flat, ref, xd, yd = _setup(T=24, F=F, seed=7,
+                                                             case=make_case(scale_case(300, 24, 0, seed=8)))
+    assert (T * N) % 128 != 0
+    net = WarmStartNet(N, case["line_from"], case["line_to"], case["line_b"], T, F, params=flat)
+    y = torch.zeros((T * N, 2), dtype=torch.float32, device="cuda")
+    net.forward(xd, y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.float64)
+    want = ref.forward(params, X)
+    assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want)
+    if F <= 9:
+        scale = (1.0, 4.0)
+        loss, g = net.gradient(xd, yd, scale)
+        rl, rg = ref.loss_and_grads(params, X, Yt, np.array(scale))
+        assert loss == pytest.approx(rl, rel=1e-5)
+        for i, (a, b) in enumerate(zip(_unflatten(g, F), rg)):
+            assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(b) + 1e-9, i
     net.close()
