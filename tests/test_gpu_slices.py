@@ -218,3 +218,37 @@ def test_benchmark_instance_as_four_slices():
     finally:
         sl.close()
         whole.close()
+
+
+@pytest.mark.parametrize("K, bounds", [(0, [(0, 1)]), (2, [(0, 1), (1, 2), (2, 3)])])
+def test_single_contingency_slices(K, bounds):
+    """Degenerate blocks: the base case alone as one slice (K = 0), and one
+    contingency per slice."""
+    from paper_2410_17203_gb300 import Solver
+    case = make_case(scale_case(60, 8, K, seed=41))
+    opts = dict(adapt_every=10, eps=0.0)
+    sl = Slices(case, bounds, opts)
+    whole = Solver(case, opts)
+    try:
+        sl.iterate(30)
+        whole.iterate(30)
+        st, ref = sl.state(), whole.state()
+        for k in ref:
+            assert rel_err(st[k], ref[k]) <= SPLIT_RTOL * 30, k
+    finally:
+        sl.close()
+        whole.close()
+
+
+def test_slice_refuses_whole_context_calls():
+    from paper_2410_17203_gb300 import OpfError, opf_batch_create, opf_create_slice, opf_destroy, opf_iterate
+    case = make_case("tiny")
+    h = opf_create_slice(case, 0, 3)
+    try:
+        with pytest.raises(OpfError) as e:
+            opf_iterate(h, 5)
+        assert e.value.status == 6                     # OPF_ESTATE
+        with pytest.raises(OpfError):
+            opf_batch_create([h])
+    finally:
+        opf_destroy(h)

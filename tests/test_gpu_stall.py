@@ -165,3 +165,27 @@ def test_batch_counts_converged_and_stalled_instances():
         opf_batch_destroy(b)
         for h in hs:
             opf_destroy(h)
+
+
+def test_history_edge_cases():
+    """No ring (history_len = 0): nothing is kept; no stopping test and no
+    adaptation: one row per call, at its last iteration; no stopping test
+    (eps = 0): the stall rule has nothing to look at and never acts."""
+    from paper_2410_17203_gb300 import Solver
+    case = make_case("tiny")
+    s = Solver(case, dict(eps=1e-4, history_len=0))
+    try:
+        s.iterate(30)
+        assert s.get_info()["history_rows"] == 0 and len(s.history()) == 0
+    finally:
+        s.close()
+    s = Solver(case, dict(eps=0.0, adapt_every=0, check_every=0, stall_window=10))
+    try:
+        for n in (7, 5, 9):
+            s.iterate(n)
+        h = s.history()
+        assert [int(r[0]) for r in h] == [7, 12, 21]
+        info = s.get_info()
+        assert info["stalled"] == 0 and info["frozen_at"] == 0
+    finally:
+        s.close()
