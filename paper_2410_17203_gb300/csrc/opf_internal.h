@@ -162,6 +162,7 @@ struct IterPlan {
   int lean_grid;   // residual-free node pass (T % 4 == 0 and plain ADMM only)
   int n_slabs, slab_k;  // contingency slabs of the line / node kernels, slab_k contingencies each
   size_t inner_smem;
+  int inner_c;     // register chunk of the inner-ADMM kernel (0: shared-memory path)
 };
 
 // A batch of instances: the CTA schedules of each batch kernel, concatenated
@@ -173,6 +174,7 @@ struct BatchPlan {
   int count[BK_COUNT];
   int offset[BK_COUNT];
   size_t inner_smem;
+  int inner_c;  // register chunk of the batch's inner-ADMM kernel (0: shared-memory path)
   int relax;   // the instances run over-relaxed (alpha != 1): the node kernels that carry it
 };
 // How a batch schedule lays out CTAs: instances in `order` (NULL: as given),

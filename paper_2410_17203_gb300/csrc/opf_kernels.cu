@@ -50,12 +50,40 @@ constexpr int LINE_IPT = 4;      // line items per thread (CTA-sized blocks of i
 constexpr int N_SLABS = 1;       // contingency slabs per iteration (line / node overlap)
 constexpr int NODE_LEAN_CTAS = 4;  // resident CTAs per SM of the residual-free node pass
 constexpr int NODE_LEAN_NB = 2;    // line terminals it gathers together
+constexpr int REG_T = 127;         // longest horizon of the register-resident inner ADMM (T + 1 <= 4 x 32)
 
-// shared floats per warp: 3 (T+1) for the inner-ADMM work arrays, plus room
-// for one device's (lam, beta) while the horizon is short enough
+// shared floats per warp of the shared-memory inner ADMM: 3 (T+1) for the
+// work arrays, plus room for one device's (lam, beta) while the horizon is
+// short enough
 __host__ __device__ inline int warp_smem_floats(int T) {
   const int work = 3 * (T + 1), state = 2 * SG_N * (T + 1);
   return T <= 128 ? work + state : work;
+}
+
+// register chunk of the inner ADMM at horizon T: a battery's T + 1 elements
+// over 32 lanes (1 .. 4); 0 beyond REG_T (the shared-memory path)
+__host__ __device__ inline int inner_chunk(int T) { return T <= REG_T ? (T + 32) >> 5 : 0; }
+
+// ---------------------------------------------------------------------------
+// The inner ADMM (Appendix D) writes every product, sum and quotient with its
+// rounding (__fmul_rn, __fadd_rn, __fmaf_rn, ...), which the compiler may not
+// contract or reorder: its shared-memory and register forms, and each kernel
+// that inlines them (one instance, a batch), compute the same bits.
+// ---------------------------------------------------------------------------
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// one projected dual step of an inequality row (Appendix D): lam += al - nb,
+// beta = nb = min(al + lam, 0)
+__device__ __forceinline__ void ineq_step(float al, float &lam, float &bet) {
+  const float nb = fminf(radd(al, lam), 0.f);
+  lam = radd(lam, rsub(al, nb));
+  bet = nb;
 }
 
 // ---------------------------------------------------------------------------
@@ -69,7 +97,7 @@ __device__ void tri_factor(float *q, int n, float d_end, float d_mid, float off)
   float prev = 0.f;
   for (int i = 0; i < n; ++i) {
     const float d = (i == 0 || i == n - 1) ? d_end : d_mid;
-    const float qi = (i == 0) ? d : d - off * (off / prev);
+    const float qi = (i == 0) ? d : rsub(d, rmul(off, rdiv(off, prev)));
     q[i] = qi;
     prev = qi;
   }
@@ -84,29 +112,30 @@ __device__ void warp_tri_solve(const float *__restrict__ q, float off, float *bu
                                int lane) {
   const int cs = (n + 31) >> 5;
   const int i0 = min(lane * cs, n), i1 = min(i0 + cs, n);
-  // forward
+  const float noff = -off;
+  // forward (r_i = buf_i / q_i is kept in buf for the second pass)
   float Ac = 1.f, Bc = 0.f;
   for (int i = i0; i < i1; ++i) {
-    const float qi = q[i];
-    const float Ai = (i == 0) ? 0.f : -off / qi;
-    Bc = fmaf(Ai, Bc, buf[i] / qi);
-    Ac = Ai * Ac;
+    const float ri = rdiv(buf[i], q[i]);
+    const float Ai = (i == 0) ? 0.f : rdiv(noff, q[i]);
+    buf[i] = ri;
+    Bc = rfma(Ai, Bc, ri);
+    Ac = rmul(Ai, Ac);
   }
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const float Ap = __shfl_up_sync(0xffffffffu, Ac, d);
-    const float Bp = __shfl_up_sync(0xffffffffu, Bc, d);
+    const float Ap = __shfl_up_sync(FULL, Ac, d);
+    const float Bp = __shfl_up_sync(FULL, Bc, d);
     if (lane >= d) {
-      Bc = fmaf(Ac, Bp, Bc);
-      Ac = Ac * Ap;
+      Bc = rfma(Ac, Bp, Bc);
+      Ac = rmul(Ac, Ap);
     }
   }
-  float prev = __shfl_up_sync(0xffffffffu, Bc, 1);
+  float prev = __shfl_up_sync(FULL, Bc, 1);
   if (lane == 0) prev = 0.f;
   for (int i = i0; i < i1; ++i) {
-    const float qi = q[i];
-    const float Ai = (i == 0) ? 0.f : -off / qi;
-    prev = fmaf(Ai, prev, buf[i] / qi);
+    const float Ai = (i == 0) ? 0.f : rdiv(noff, q[i]);
+    prev = rfma(Ai, prev, buf[i]);
     buf[i] = prev;
   }
   __syncwarp();
@@ -114,24 +143,24 @@ __device__ void warp_tri_solve(const float *__restrict__ q, float off, float *bu
   Ac = 1.f;
   Bc = 0.f;
   for (int i = i1 - 1; i >= i0; --i) {
-    const float Ci = (i == n - 1) ? 0.f : -off / q[i];
-    Bc = fmaf(Ci, Bc, buf[i]);
-    Ac = Ci * Ac;
+    const float Ci = (i == n - 1) ? 0.f : rdiv(noff, q[i]);
+    Bc = rfma(Ci, Bc, buf[i]);
+    Ac = rmul(Ci, Ac);
   }
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const float Ap = __shfl_down_sync(0xffffffffu, Ac, d);
-    const float Bp = __shfl_down_sync(0xffffffffu, Bc, d);
+    const float Ap = __shfl_down_sync(FULL, Ac, d);
+    const float Bp = __shfl_down_sync(FULL, Bc, d);
     if (lane + d < 32) {
-      Bc = fmaf(Ac, Bp, Bc);
-      Ac = Ac * Ap;
+      Bc = rfma(Ac, Bp, Bc);
+      Ac = rmul(Ac, Ap);
     }
   }
-  float nxt = __shfl_down_sync(0xffffffffu, Bc, 1);
+  float nxt = __shfl_down_sync(FULL, Bc, 1);
   if (lane == 31) nxt = 0.f;
   for (int i = i1 - 1; i >= i0; --i) {
-    const float Ci = (i == n - 1) ? 0.f : -off / q[i];
-    nxt = fmaf(Ci, nxt, buf[i]);
+    const float Ci = (i == n - 1) ? 0.f : rdiv(noff, q[i]);
+    nxt = rfma(Ci, nxt, buf[i]);
     buf[i] = nxt;
   }
   __syncwarp();
@@ -196,13 +225,13 @@ __device__ __forceinline__ void ksum4(const float *pbar_o, const float *u_o, siz
 // averages are the copies' complements (z = P - avg_n P, xi = avg_n Theta);
 // alpha = 1 returns p exactly.
 __device__ __forceinline__ float relaxed(float alpha, float pnew, float pold) {
-  return fmaf(alpha, pnew, (1.f - alpha) * pold);
+  return rfma(alpha, pnew, rmul(rsub(1.f, alpha), pold));
 }
 
 __device__ __forceinline__ void device_x(const Params &p, int n, const float *pd, float *X, int lane) {
   const int T = p.T;
   const float *xs = p.XS + (size_t)n * T;
-  for (int t = lane; t < T; t += 32) X[t] = pd[t] - __ldcg(xs + t);
+  for (int t = lane; t < T; t += 32) X[t] = rsub(pd[t], __ldcg(xs + t));
   __syncwarp();
 }
 
@@ -239,7 +268,7 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float *sm, float *s
   const int d = p.ramp_ids[r];
   const int n = p.dev_node[d];
   const float a = p.dev_a[d], b = p.dev_b[d], R = p.ramp_R[r];
-  const float om = rho;
+  const float om = rho, om2 = rmul(2.f, om);
   float *const lam_g = p.ramp_lam + (size_t)r * RG_N * T;
   float *const bet_g = p.ramp_beta + (size_t)r * RG_N * T;
   float *lam = lam_g, *bet = bet_g;
@@ -251,12 +280,14 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float *sm, float *s
   float *X = sm, *W = sm + (T + 1), *Z = sm + 2 * (T + 1);
 
   // keep the unscaled inner duals omega * lam when omega changes; refactor
+  // (2a + rho + 2 omega) I + 2 omega D'D
   const float rho_old = p.ramp_rho[r];
   if (rho_old != rho) {
-    const float ls = (rho_old == 0.f) ? 1.f : fabsf(rho_old) / rho;
-    for (int t = lane; t < RG_N * T; t += 32) lam[t] *= ls;
+    const float ls = (rho_old == 0.f) ? 1.f : rdiv(fabsf(rho_old), rho);
+    for (int t = lane; t < RG_N * T; t += 32) lam[t] = rmul(lam[t], ls);
     if (lane == 0) {
-      tri_factor(mf, T, 2.f * a + rho + 4.f * om, 2.f * a + rho + 6.f * om, -2.f * om);
+      const float base = radd(rmul(2.f, a), rho);
+      tri_factor(mf, T, radd(base, rmul(4.f, om)), radd(base, rmul(6.f, om)), -om2);
       p.ramp_rho[r] = rho;
     }
     __syncwarp();
@@ -264,38 +295,25 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float *sm, float *s
   device_x(p, n, pd, X, lane);   // p_d - avg_k(pbar + u)
   for (int itn = 0; itn < p.inner_iters; ++itn) {
     for (int t = lane; t < T - 1; t += 32)
-      W[t] = (bet[RG_RU * T + t] - lam[RG_RU * T + t]) - (bet[RG_RD * T + t] - lam[RG_RD * T + t]);
+      W[t] = rsub(rsub(bet[RG_RU * T + t], lam[RG_RU * T + t]), rsub(bet[RG_RD * T + t], lam[RG_RD * T + t]));
     __syncwarp();
     for (int t = lane; t < T; t += 32) {
-      float atr = (hi[t] + bet[RG_UP * T + t] - lam[RG_UP * T + t]) -
-                  (-lo[t] + bet[RG_LO * T + t] - lam[RG_LO * T + t]);
-      if (t >= 1) atr += W[t - 1];
-      if (t <= T - 2) atr -= W[t];
-      Z[t] = rho * X[t] - b + om * atr;
+      float atr = rsub(rsub(radd(hi[t], bet[RG_UP * T + t]), lam[RG_UP * T + t]),
+                       rsub(radd(-lo[t], bet[RG_LO * T + t]), lam[RG_LO * T + t]));
+      if (t >= 1) atr = radd(atr, W[t - 1]);
+      if (t <= T - 2) atr = rsub(atr, W[t]);
+      Z[t] = rfma(om, atr, rfma(rho, X[t], -b));
     }
     __syncwarp();
-    warp_tri_solve(mf, -2.f * om, Z, T, lane);
+    warp_tri_solve(mf, -om2, Z, T, lane);
     for (int t = lane; t < T; t += 32) {
       const float pt = Z[t];
-      float al, nb;
-      al = pt - hi[t];
-      nb = fminf(al + lam[RG_UP * T + t], 0.f);
-      lam[RG_UP * T + t] += al - nb;
-      bet[RG_UP * T + t] = nb;
-      al = lo[t] - pt;
-      nb = fminf(al + lam[RG_LO * T + t], 0.f);
-      lam[RG_LO * T + t] += al - nb;
-      bet[RG_LO * T + t] = nb;
+      ineq_step(rsub(pt, hi[t]), lam[RG_UP * T + t], bet[RG_UP * T + t]);
+      ineq_step(rsub(lo[t], pt), lam[RG_LO * T + t], bet[RG_LO * T + t]);
       if (t < T - 1) {
         const float pn = Z[t + 1];
-        al = pn - pt - R;
-        nb = fminf(al + lam[RG_RU * T + t], 0.f);
-        lam[RG_RU * T + t] += al - nb;
-        bet[RG_RU * T + t] = nb;
-        al = pt - pn - R;
-        nb = fminf(al + lam[RG_RD * T + t], 0.f);
-        lam[RG_RD * T + t] += al - nb;
-        bet[RG_RD * T + t] = nb;
+        ineq_step(rsub(rsub(pn, pt), R), lam[RG_RU * T + t], bet[RG_RU * T + t]);
+        ineq_step(rsub(rsub(pt, pn), R), lam[RG_RD * T + t], bet[RG_RD * T + t]);
       }
     }
     __syncwarp();
@@ -303,7 +321,7 @@ __device__ void ramp_prox(const Params &p, int r, float rho, float *sm, float *s
   stage_out(lam_g, bet_g, state_sh, RG_N * T, lane);
   for (int t = lane; t < T; t += 32) {
     const float pn = relaxed(p.alpha, Z[t], pd[t]);
-    p.DPD[(size_t)d * T + t] = pn - pd[t];
+    p.DPD[(size_t)d * T + t] = rsub(pn, pd[t]);
     pd[t] = pn;
   }
   __syncwarp();
@@ -342,9 +360,9 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float *sm, float
   const int T = p.T, Tp = T + 1;
   const int d = p.stor_ids[sidx];
   const int n = p.dev_node[d];
-  const float eta = p.stor_eff[sidx], Pm = p.stor_P[sidx], Em = p.stor_dur[sidx] * Pm;
+  const float eta = p.stor_eff[sidx], Pm = p.stor_P[sidx], Em = rmul(p.stor_dur[sidx], Pm);
   const float q = p.stor_cost[sidx];
-  const float om = rho;
+  const float om = rho, om2 = rmul(2.f, om);
   float *const lam_g = p.stor_lam + (size_t)sidx * SG_N * Tp;
   float *const bet_g = p.stor_beta + (size_t)sidx * SG_N * Tp;
   float *lam = lam_g, *bet = bet_g;
@@ -355,20 +373,22 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float *sm, float
   float *X = sm, *TAU = sm + Tp, *S = sm + 2 * Tp;
 
   // 2x2 block of (c, delta) after eliminating p; constants of the reduction
-  const float kap = rho * om / (rho + om);
-  const float h00 = kap + 2.f * om + om * eta * eta, h01 = -kap - om * eta, h11 = kap + 3.f * om;
-  const float det = h00 * h11 - h01 * h01;
-  const float i00 = h11 / det, i01 = -h01 / det, i11 = h00 / det;
-  const float f1c = om * eta, f1d = -om;
-  const float w0 = i00 * f1c + i01 * f1d, w1 = i01 * f1c + i11 * f1d;
-  const float gam = om - (f1c * w0 + f1d * w1);
+  const float kap = rdiv(rmul(rho, om), radd(rho, om));
+  const float h00 = radd(radd(kap, om2), rmul(rmul(om, eta), eta));
+  const float h01 = rsub(-kap, rmul(om, eta)), h11 = radd(kap, rmul(3.f, om));
+  const float det = rsub(rmul(h00, h11), rmul(h01, h01));
+  const float i00 = rdiv(h11, det), i01 = rdiv(-h01, det), i11 = rdiv(h00, det);
+  const float f1c = rmul(om, eta), f1d = -om;
+  const float w0 = radd(rmul(i00, f1c), rmul(i01, f1d)), w1 = radd(rmul(i01, f1c), rmul(i11, f1d));
+  const float gam = rsub(om, radd(rmul(f1c, w0), rmul(f1d, w1)));
+  const float rpo = radd(rho, om);
 
   const float rho_old = p.stor_rho[sidx];
   if (rho_old != rho) {
-    const float ls = (rho_old == 0.f) ? 1.f : fabsf(rho_old) / rho;
-    for (int t = lane; t < SG_N * Tp; t += 32) lam[t] *= ls;
+    const float ls = (rho_old == 0.f) ? 1.f : rdiv(fabsf(rho_old), rho);
+    for (int t = lane; t < SG_N * Tp; t += 32) lam[t] = rmul(lam[t], ls);
     if (lane == 0) {
-      tri_factor(mf, Tp, gam + 3.f * om, 2.f * gam + 2.f * om, -gam);
+      tri_factor(mf, Tp, radd(gam, rmul(3.f, om)), radd(rmul(2.f, gam), om2), -gam);
       p.stor_rho[sidx] = rho;
     }
     __syncwarp();
@@ -379,55 +399,54 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float *sm, float
   for (int itn = 0; itn < p.inner_iters; ++itn) {
     for (int t = lane; t < T; t += 32) {
       const float r1 = -LAM(SG_E1, t), r2 = -LAM(SG_E2, t);
-      const float mc = 0.5f * ((Pm + BET(SG_CU, t) - LAM(SG_CU, t)) - (BET(SG_CL, t) - LAM(SG_CL, t)));
-      const float md = 0.5f * ((Pm + BET(SG_DU, t) - LAM(SG_DU, t)) - (BET(SG_DL, t) - LAM(SG_DL, t)));
-      const float e1 = r1 - X[t];
-      const float f0c = kap * e1 + 2.f * om * mc;
-      const float f0d = -kap * e1 - q + 2.f * om * md;
-      TAU[t] = r2 + (w0 * f0c + w1 * f0d) / gam;
+      const float mc = rmul(0.5f, rsub(rsub(radd(Pm, BET(SG_CU, t)), LAM(SG_CU, t)), rsub(BET(SG_CL, t), LAM(SG_CL, t))));
+      const float md = rmul(0.5f, rsub(rsub(radd(Pm, BET(SG_DU, t)), LAM(SG_DU, t)), rsub(BET(SG_DL, t), LAM(SG_DL, t))));
+      const float e1 = rsub(r1, X[t]);
+      const float f0c = rfma(kap, e1, rmul(om2, mc));
+      const float f0d = rfma(om2, md, rsub(rmul(-kap, e1), q));
+      TAU[t] = radd(r2, rdiv(rfma(w0, f0c, rmul(w1, f0d)), gam));
     }
     __syncwarp();
     for (int j = lane; j < Tp; j += 32) {
-      const float ms = 0.5f * ((Em + BET(SG_SU, j) - LAM(SG_SU, j)) - (BET(SG_SL, j) - LAM(SG_SL, j)));
-      float rhs = 2.f * om * ms;
-      if (j >= 1) rhs += gam * TAU[j - 1];
-      if (j <= T - 1) rhs -= gam * TAU[j];
-      if (j == 0) rhs -= om * LAM(SG_E3, 0);
-      if (j == T) rhs -= om * LAM(SG_E3, 1);
+      const float ms = rmul(0.5f, rsub(rsub(radd(Em, BET(SG_SU, j)), LAM(SG_SU, j)), rsub(BET(SG_SL, j), LAM(SG_SL, j))));
+      float rhs = rmul(om2, ms);
+      if (j >= 1) rhs = rfma(gam, TAU[j - 1], rhs);
+      if (j <= T - 1) rhs = rfma(-gam, TAU[j], rhs);
+      if (j == 0) rhs = rfma(-om, LAM(SG_E3, 0), rhs);
+      if (j == T) rhs = rfma(-om, LAM(SG_E3, 1), rhs);
       S[j] = rhs;
     }
     __syncwarp();
     warp_tri_solve(mf, -gam, S, Tp, lane);
     for (int t = lane; t < T; t += 32) {
       const float r1 = -LAM(SG_E1, t), r2 = -LAM(SG_E2, t);
-      const float mc = 0.5f * ((Pm + BET(SG_CU, t) - LAM(SG_CU, t)) - (BET(SG_CL, t) - LAM(SG_CL, t)));
-      const float md = 0.5f * ((Pm + BET(SG_DU, t) - LAM(SG_DU, t)) - (BET(SG_DL, t) - LAM(SG_DL, t)));
-      const float e1 = r1 - X[t];
-      const float f0c = kap * e1 + 2.f * om * mc;
-      const float f0d = -kap * e1 - q + 2.f * om * md;
+      const float mc = rmul(0.5f, rsub(rsub(radd(Pm, BET(SG_CU, t)), LAM(SG_CU, t)), rsub(BET(SG_CL, t), LAM(SG_CL, t))));
+      const float md = rmul(0.5f, rsub(rsub(radd(Pm, BET(SG_DU, t)), LAM(SG_DU, t)), rsub(BET(SG_DL, t), LAM(SG_DL, t))));
+      const float e1 = rsub(r1, X[t]);
+      const float f0c = rfma(kap, e1, rmul(om2, mc));
+      const float f0d = rfma(om2, md, rsub(rmul(-kap, e1), q));
       const float s0 = S[t], s1 = S[t + 1];
-      const float g = s1 - s0 - r2;
-      const float fc = f0c + g * f1c, fd = f0d + g * f1d;
-      const float c = i00 * fc + i01 * fd;
-      const float dl = i01 * fc + i11 * fd;
-      const float pt = (rho * X[t] + om * (r1 - c + dl)) / (rho + om);
+      const float ds = rsub(s1, s0);
+      const float g = rsub(ds, r2);
+      const float fc = rfma(g, f1c, f0c), fd = rfma(g, f1d, f0d);
+      const float c = rfma(i00, fc, rmul(i01, fd));
+      const float dl = rfma(i01, fc, rmul(i11, fd));
+      const float pt = rdiv(rfma(om, radd(rsub(r1, c), dl), rmul(rho, X[t])), rpo);
       TAU[t] = pt;  // TAU is consumed; keep p_t for the end
       dl_out[t] = dl;
-      float al, nb;
-      LAM(SG_E1, t) += pt + c - dl;                  // equality rows: beta = 0
-      LAM(SG_E2, t) += s1 - s0 - eta * c + dl;
-      al = c - Pm;  nb = fminf(al + LAM(SG_CU, t), 0.f); LAM(SG_CU, t) += al - nb; BET(SG_CU, t) = nb;
-      al = -c;      nb = fminf(al + LAM(SG_CL, t), 0.f); LAM(SG_CL, t) += al - nb; BET(SG_CL, t) = nb;
-      al = dl - Pm; nb = fminf(al + LAM(SG_DU, t), 0.f); LAM(SG_DU, t) += al - nb; BET(SG_DU, t) = nb;
-      al = -dl;     nb = fminf(al + LAM(SG_DL, t), 0.f); LAM(SG_DL, t) += al - nb; BET(SG_DL, t) = nb;
+      LAM(SG_E1, t) = radd(LAM(SG_E1, t), rsub(radd(pt, c), dl));   // equality rows: beta = 0
+      LAM(SG_E2, t) = radd(LAM(SG_E2, t), radd(rfma(-eta, c, ds), dl));
+      ineq_step(rsub(c, Pm), LAM(SG_CU, t), BET(SG_CU, t));
+      ineq_step(-c, LAM(SG_CL, t), BET(SG_CL, t));
+      ineq_step(rsub(dl, Pm), LAM(SG_DU, t), BET(SG_DU, t));
+      ineq_step(-dl, LAM(SG_DL, t), BET(SG_DL, t));
     }
     for (int j = lane; j < Tp; j += 32) {
       const float sj = S[j];
-      float al, nb;
-      if (j == 0) LAM(SG_E3, 0) += sj;
-      if (j == T) LAM(SG_E3, 1) += sj;
-      al = sj - Em; nb = fminf(al + LAM(SG_SU, j), 0.f); LAM(SG_SU, j) += al - nb; BET(SG_SU, j) = nb;
-      al = -sj;     nb = fminf(al + LAM(SG_SL, j), 0.f); LAM(SG_SL, j) += al - nb; BET(SG_SL, j) = nb;
+      if (j == 0) LAM(SG_E3, 0) = radd(LAM(SG_E3, 0), sj);
+      if (j == T) LAM(SG_E3, 1) = radd(LAM(SG_E3, 1), sj);
+      ineq_step(rsub(sj, Em), LAM(SG_SU, j), BET(SG_SU, j));
+      ineq_step(-sj, LAM(SG_SL, j), BET(SG_SL, j));
     }
     __syncwarp();
   }
@@ -436,10 +455,338 @@ __device__ void stor_prox(const Params &p, int sidx, float rho, float *sm, float
   stage_out(lam_g, bet_g, state_sh, SG_N * Tp, lane);
   for (int t = lane; t < T; t += 32) {
     const float pn = relaxed(p.alpha, TAU[t], pd[t]);
-    p.DPD[(size_t)d * T + t] = pn - pd[t];
+    p.DPD[(size_t)d * T + t] = rsub(pn, pd[t]);
     pd[t] = pn;
   }
   __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// The same inner ADMM with the device's state in registers, for horizons of
+// at most REG_T steps: lane l holds the C = ceil(n / 32) consecutive
+// elements l C .. l C + C - 1 of each vector (the solve's chunks), so the
+// inner iterations touch no memory; neighbours across a chunk boundary come
+// by one shuffle.  Every product, sum and quotient is written with its
+// rounding (__fmul_rn, __fadd_rn, __fmaf_rn, ...), which the compiler may
+// not contract or reorder, so each kernel that inlines this path (one
+// instance, a batch) computes the same bits.
+// ---------------------------------------------------------------------------
+
+// warp_tri_solve on a chunk held in registers (element i = lane C + j, valid
+// while i < n), a[j] = -off / q[j]
+template <int C>
+__device__ __forceinline__ void warp_tri_solve_r(const float (&q)[C], const float (&a)[C], float (&x)[C], int n,
+                                                 int lane) {
+  const int i0 = lane * C;
+  float r[C];
+  float Ac = 1.f, Bc = 0.f;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int i = i0 + j;
+    if (i < n) {
+      r[j] = rdiv(x[j], q[j]);
+      const float Ai = (i == 0) ? 0.f : a[j];
+      Bc = rfma(Ai, Bc, r[j]);
+      Ac = rmul(Ai, Ac);
+    }
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float Ap = __shfl_up_sync(FULL, Ac, d);
+    const float Bp = __shfl_up_sync(FULL, Bc, d);
+    if (lane >= d) {
+      Bc = rfma(Ac, Bp, Bc);
+      Ac = rmul(Ac, Ap);
+    }
+  }
+  float prev = __shfl_up_sync(FULL, Bc, 1);
+  if (lane == 0) prev = 0.f;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int i = i0 + j;
+    if (i < n) {
+      const float Ai = (i == 0) ? 0.f : a[j];
+      prev = rfma(Ai, prev, r[j]);
+      x[j] = prev;
+    }
+  }
+  Ac = 1.f;
+  Bc = 0.f;
+#pragma unroll
+  for (int j = C - 1; j >= 0; --j) {
+    const int i = i0 + j;
+    if (i < n) {
+      const float Ci = (i == n - 1) ? 0.f : a[j];
+      Bc = rfma(Ci, Bc, x[j]);
+      Ac = rmul(Ci, Ac);
+    }
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float Ap = __shfl_down_sync(FULL, Ac, d);
+    const float Bp = __shfl_down_sync(FULL, Bc, d);
+    if (lane + d < 32) {
+      Bc = rfma(Ac, Bp, Bc);
+      Ac = rmul(Ac, Ap);
+    }
+  }
+  float nxt = __shfl_down_sync(FULL, Bc, 1);
+  if (lane == 31) nxt = 0.f;
+#pragma unroll
+  for (int j = C - 1; j >= 0; --j) {
+    const int i = i0 + j;
+    if (i < n) {
+      const float Ci = (i == n - 1) ? 0.f : a[j];
+      nxt = rfma(Ci, nxt, x[j]);
+      x[j] = nxt;
+    }
+  }
+}
+
+
+template <int C>
+__device__ void ramp_prox_r(const Params &p, int r, float rho, int lane) {
+  const int T = p.T, t0 = lane * C;
+  const int d = p.ramp_ids[r];
+  const int n = p.dev_node[d];
+  const float a = p.dev_a[d], b = p.dev_b[d], R = p.ramp_R[r];
+  const float om = rho, om2 = rmul(2.f, om);
+  float *const lam_g = p.ramp_lam + (size_t)r * RG_N * T;
+  float *const bet_g = p.ramp_beta + (size_t)r * RG_N * T;
+  float *mf = p.ramp_q + (size_t)r * T;
+  // keep the unscaled inner duals omega * lam when omega changes; refactor
+  // (2a + rho + 2 omega) I + 2 omega D'D
+  const float rho_old = p.ramp_rho[r];
+  const bool rescale = rho_old != rho;
+  const float ls = (rho_old == 0.f) ? 1.f : rdiv(fabsf(rho_old), rho);
+  if (rescale) {
+    if (lane == 0) {
+      const float base = radd(rmul(2.f, a), rho);
+      tri_factor(mf, T, radd(base, rmul(4.f, om)), radd(base, rmul(6.f, om)), -om2);
+      p.ramp_rho[r] = rho;
+    }
+    __syncwarp();
+  }
+  float lam[RG_N][C], bet[RG_N][C], hi[C], lo[C], X[C], pd[C], qv[C], av[C], Z[C];
+  const float *xs = p.XS + (size_t)n * T;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int t = t0 + j;
+    const bool in = t < T;
+#pragma unroll
+    for (int g = 0; g < RG_N; ++g) {
+      lam[g][j] = in ? lam_g[g * T + t] : 0.f;
+      bet[g][j] = in ? bet_g[g * T + t] : 0.f;
+      if (rescale) lam[g][j] = rmul(lam[g][j], ls);
+    }
+    hi[j] = in ? p.dev_hi[(size_t)d * T + t] : 0.f;
+    lo[j] = in ? p.dev_lo[(size_t)d * T + t] : 0.f;
+    pd[j] = in ? p.PD[(size_t)d * T + t] : 0.f;
+    X[j] = in ? rsub(pd[j], __ldcg(xs + t)) : 0.f;   // p_d - avg_k(pbar + u)
+    qv[j] = in ? mf[t] : 1.f;
+    av[j] = rdiv(om2, qv[j]);                         // -off / q with off = -2 omega
+    Z[j] = 0.f;
+  }
+  for (int itn = 0; itn < p.inner_iters; ++itn) {
+    float W[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+      W[j] = rsub(rsub(bet[RG_RU][j], lam[RG_RU][j]), rsub(bet[RG_RD][j], lam[RG_RD][j]));
+    const float wprev = __shfl_up_sync(FULL, W[C - 1], 1);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int t = t0 + j;
+      if (t < T) {
+        float atr = rsub(rsub(radd(hi[j], bet[RG_UP][j]), lam[RG_UP][j]),
+                         rsub(radd(-lo[j], bet[RG_LO][j]), lam[RG_LO][j]));
+        if (t >= 1) atr = radd(atr, (j == 0) ? wprev : W[j - 1]);
+        if (t <= T - 2) atr = rsub(atr, W[j]);
+        Z[j] = rfma(om, atr, rfma(rho, X[j], -b));
+      }
+    }
+    warp_tri_solve_r<C>(qv, av, Z, T, lane);
+    const float znext = __shfl_down_sync(FULL, Z[0], 1);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int t = t0 + j;
+      if (t < T) {
+        const float pt = Z[j];
+        ineq_step(rsub(pt, hi[j]), lam[RG_UP][j], bet[RG_UP][j]);
+        ineq_step(rsub(lo[j], pt), lam[RG_LO][j], bet[RG_LO][j]);
+        if (t < T - 1) {
+          const float pn = (j == C - 1) ? znext : Z[j + 1];
+          ineq_step(rsub(rsub(pn, pt), R), lam[RG_RU][j], bet[RG_RU][j]);
+          ineq_step(rsub(rsub(pt, pn), R), lam[RG_RD][j], bet[RG_RD][j]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int t = t0 + j;
+    if (t < T) {
+#pragma unroll
+      for (int g = 0; g < RG_N; ++g) {
+        lam_g[g * T + t] = lam[g][j];
+        bet_g[g * T + t] = bet[g][j];
+      }
+      const float pn = relaxed(p.alpha, Z[j], pd[j]);
+      p.DPD[(size_t)d * T + t] = rsub(pn, pd[j]);
+      p.PD[(size_t)d * T + t] = pn;
+    }
+  }
+}
+
+template <int C>
+__device__ void stor_prox_r(const Params &p, int sidx, float rho, int lane) {
+  const int T = p.T, Tp = T + 1, t0 = lane * C;
+  const int d = p.stor_ids[sidx];
+  const int n = p.dev_node[d];
+  const float eta = p.stor_eff[sidx], Pm = p.stor_P[sidx], Em = rmul(p.stor_dur[sidx], Pm);
+  const float q = p.stor_cost[sidx];
+  const float om = rho, om2 = rmul(2.f, om);
+  float *const lam_g = p.stor_lam + (size_t)sidx * SG_N * Tp;
+  float *const bet_g = p.stor_beta + (size_t)sidx * SG_N * Tp;
+  float *mf = p.stor_q + (size_t)sidx * Tp;
+
+  // 2x2 block of (c, delta) after eliminating p; constants of the reduction
+  const float kap = rdiv(rmul(rho, om), radd(rho, om));
+  const float h00 = radd(radd(kap, om2), rmul(rmul(om, eta), eta));
+  const float h01 = rsub(-kap, rmul(om, eta)), h11 = radd(kap, rmul(3.f, om));
+  const float det = rsub(rmul(h00, h11), rmul(h01, h01));
+  const float i00 = rdiv(h11, det), i01 = rdiv(-h01, det), i11 = rdiv(h00, det);
+  const float f1c = rmul(om, eta), f1d = -om;
+  const float w0 = radd(rmul(i00, f1c), rmul(i01, f1d)), w1 = radd(rmul(i01, f1c), rmul(i11, f1d));
+  const float gam = rsub(om, radd(rmul(f1c, w0), rmul(f1d, w1)));
+  const float rpo = radd(rho, om);
+
+  const float rho_old = p.stor_rho[sidx];
+  const bool rescale = rho_old != rho;
+  const float ls = (rho_old == 0.f) ? 1.f : rdiv(fabsf(rho_old), rho);
+  if (rescale) {
+    if (lane == 0) {
+      tri_factor(mf, Tp, radd(gam, rmul(3.f, om)), radd(rmul(2.f, gam), om2), -gam);
+      p.stor_rho[sidx] = rho;
+    }
+    __syncwarp();
+  }
+  // element e = t0 + j: step t = e of (p, c, delta) while e < T, state of
+  // charge s_e while e < T + 1
+  float lE1[C], lE2[C], lCU[C], lCL[C], lDU[C], lDL[C], lSU[C], lSL[C];
+  float bCU[C], bCL[C], bDU[C], bDL[C], bSU[C], bSL[C];
+  float X[C], pd[C], qv[C], av[C], S[C], TAU[C], DL[C];
+  float e3a = lam_g[SG_E3 * Tp], e3b = lam_g[SG_E3 * Tp + 1];   // s_0 and s_T rows
+  if (rescale) {
+    e3a = rmul(e3a, ls);
+    e3b = rmul(e3b, ls);
+  }
+  const float *xs = p.XS + (size_t)n * T;
+#define LD_L(arr, g) arr[j] = in ? (rescale ? rmul(lam_g[(g) * Tp + e], ls) : lam_g[(g) * Tp + e]) : 0.f
+#define LD_B(arr, g) arr[j] = in ? bet_g[(g) * Tp + e] : 0.f
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int e = t0 + j;
+    const bool in = e < Tp;
+    LD_L(lE1, SG_E1); LD_L(lE2, SG_E2); LD_L(lCU, SG_CU); LD_L(lCL, SG_CL);
+    LD_L(lDU, SG_DU); LD_L(lDL, SG_DL); LD_L(lSU, SG_SU); LD_L(lSL, SG_SL);
+    LD_B(bCU, SG_CU); LD_B(bCL, SG_CL); LD_B(bDU, SG_DU); LD_B(bDL, SG_DL);
+    LD_B(bSU, SG_SU); LD_B(bSL, SG_SL);
+    const bool st = e < T;
+    pd[j] = st ? p.PD[(size_t)d * T + e] : 0.f;
+    X[j] = st ? rsub(pd[j], __ldcg(xs + e)) : 0.f;   // p_d - avg_k(pbar + u)
+    qv[j] = in ? mf[e] : 1.f;
+    av[j] = rdiv(gam, qv[j]);                         // -off / q with off = -gam
+    S[j] = TAU[j] = DL[j] = 0.f;
+  }
+#undef LD_L
+#undef LD_B
+  for (int itn = 0; itn < p.inner_iters; ++itn) {
+    float f0c[C], f0d[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      f0c[j] = f0d[j] = 0.f;
+      if (t0 + j < T) {
+        const float r1 = -lE1[j], r2 = -lE2[j];
+        const float mc = rmul(0.5f, rsub(rsub(radd(Pm, bCU[j]), lCU[j]), rsub(bCL[j], lCL[j])));
+        const float md = rmul(0.5f, rsub(rsub(radd(Pm, bDU[j]), lDU[j]), rsub(bDL[j], lDL[j])));
+        const float e1 = rsub(r1, X[j]);
+        f0c[j] = rfma(kap, e1, rmul(om2, mc));
+        f0d[j] = rfma(om2, md, rsub(rmul(-kap, e1), q));
+        TAU[j] = radd(r2, rdiv(rfma(w0, f0c[j], rmul(w1, f0d[j])), gam));
+      }
+    }
+    const float tprev = __shfl_up_sync(FULL, TAU[C - 1], 1);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int e = t0 + j;
+      if (e < Tp) {
+        const float ms = rmul(0.5f, rsub(rsub(radd(Em, bSU[j]), lSU[j]), rsub(bSL[j], lSL[j])));
+        float rhs = rmul(om2, ms);
+        if (e >= 1) rhs = rfma(gam, (j == 0) ? tprev : TAU[j - 1], rhs);
+        if (e <= T - 1) rhs = rfma(-gam, TAU[j], rhs);
+        if (e == 0) rhs = rfma(-om, e3a, rhs);
+        if (e == T) rhs = rfma(-om, e3b, rhs);
+        S[j] = rhs;
+      }
+    }
+    warp_tri_solve_r<C>(qv, av, S, Tp, lane);
+    const float snext = __shfl_down_sync(FULL, S[0], 1);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      if (t0 + j < T) {
+        const float r1 = -lE1[j], r2 = -lE2[j];
+        const float s0 = S[j], s1 = (j == C - 1) ? snext : S[j + 1];
+        const float ds = rsub(s1, s0);
+        const float g = rsub(ds, r2);
+        const float fc = rfma(g, f1c, f0c[j]), fd = rfma(g, f1d, f0d[j]);
+        const float c = rfma(i00, fc, rmul(i01, fd));
+        const float dl = rfma(i01, fc, rmul(i11, fd));
+        const float pt = rdiv(rfma(om, radd(rsub(r1, c), dl), rmul(rho, X[j])), rpo);
+        TAU[j] = pt;   // TAU is consumed; keep p_t for the end
+        DL[j] = dl;
+        lE1[j] = radd(lE1[j], rsub(radd(pt, c), dl));   // equality rows: beta = 0
+        lE2[j] = radd(lE2[j], radd(rfma(-eta, c, ds), dl));
+        ineq_step(rsub(c, Pm), lCU[j], bCU[j]);
+        ineq_step(-c, lCL[j], bCL[j]);
+        ineq_step(rsub(dl, Pm), lDU[j], bDU[j]);
+        ineq_step(-dl, lDL[j], bDL[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int e = t0 + j;
+      if (e < Tp) {
+        const float sj = S[j];
+        if (e == 0) e3a = radd(e3a, sj);
+        if (e == T) e3b = radd(e3b, sj);
+        ineq_step(rsub(sj, Em), lSU[j], bSU[j]);
+        ineq_step(-sj, lSL[j], bSL[j]);
+      }
+    }
+  }
+#define ST_L(arr, g) lam_g[(g) * Tp + e] = arr[j]
+#define ST_B(arr, g) bet_g[(g) * Tp + e] = arr[j]
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int e = t0 + j;
+    if (e < T) {
+      ST_L(lE1, SG_E1); ST_L(lE2, SG_E2); ST_L(lCU, SG_CU); ST_L(lCL, SG_CL);
+      ST_L(lDU, SG_DU); ST_L(lDL, SG_DL);
+      ST_B(bCU, SG_CU); ST_B(bCL, SG_CL); ST_B(bDU, SG_DU); ST_B(bDL, SG_DL);
+      const float pn = relaxed(p.alpha, TAU[j], pd[j]);
+      p.DPD[(size_t)d * T + e] = rsub(pn, pd[j]);
+      p.PD[(size_t)d * T + e] = pn;
+      p.stor_delta[(size_t)sidx * T + e] = DL[j];
+    }
+    if (e < Tp) {
+      ST_L(lSU, SG_SU); ST_L(lSL, SG_SL);
+      ST_B(bSU, SG_SU); ST_B(bSL, SG_SL);
+      if (e == 0) lam_g[SG_E3 * Tp] = e3a;
+      if (e == T) lam_g[SG_E3 * Tp + 1] = e3b;
+    }
+  }
+#undef ST_L
+#undef ST_B
 }
 
 // ---------------------------------------------------------------------------
@@ -894,24 +1241,71 @@ __device__ __forceinline__ void xs_body(const Params &p, unsigned bid, unsigned 
   }
 }
 
+// the register path at the device's own chunk (cs, cr <= C)
+template <int C>
+__device__ __forceinline__ void stor_r(const Params &p, int sidx, float rho, int lane, int cs) {
+  if constexpr (C > 1) {
+    if (cs < C) {
+      stor_r<C - 1>(p, sidx, rho, lane, cs);
+      return;
+    }
+  }
+  stor_prox_r<C>(p, sidx, rho, lane);
+}
+
+template <int C>
+__device__ __forceinline__ void ramp_r(const Params &p, int r, float rho, int lane, int cr) {
+  if constexpr (C > 1) {
+    if (cr < C) {
+      ramp_r<C - 1>(p, r, rho, lane, cr);
+      return;
+    }
+  }
+  ramp_prox_r<C>(p, r, rho, lane);
+}
+
 // ---------------------------------------------------------------------------
-// inner: one warp per battery, then per ramp-limited generator (Appendix D)
+// inner: one warp per battery, then per ramp-limited generator (Appendix D).
+// C > 0: the register path, for horizons of at most REG_T steps (chunks of
+// at most C); C = 0: the shared-memory path.  MIXED (batches): the
+// instance's horizon chooses, beyond REG_T the shared-memory path.
 // ---------------------------------------------------------------------------
+template <int C, bool MIXED>
 __device__ __forceinline__ void inner_body(const Params &p, unsigned bid, unsigned nblk, float *smem) {
   const Iter q = iter_scalars(p);
   if (q.skip) return;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int wfl = warp_smem_floats(p.T);
-  float *wsm = smem + (size_t)wib * wfl;
-  float *state_sh = (wfl > 3 * (p.T + 1)) ? wsm + 3 * (p.T + 1) : nullptr;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int T = p.T;
   const int n_inner = p.n_stor + p.n_ramp + p.n_hvdc;
-  for (int w = bid * WARPS + wib; w < n_inner; w += nblk * WARPS) {
-    if (w < p.n_stor)
-      stor_prox(p, w, q.rho_dev, wsm, state_sh, lane);
-    else if (w < p.n_stor + p.n_ramp)
-      ramp_prox(p, w - p.n_stor, q.rho_dev, wsm, state_sh, lane);
-    else
+  constexpr bool HAS_SMEM = C == 0 || MIXED, HAS_REG = C > 0;
+  const bool reg = HAS_REG && (!HAS_SMEM || T <= REG_T);
+  float *wsm = nullptr, *state_sh = nullptr;
+  if (HAS_SMEM && !reg) {
+    const int wfl = warp_smem_floats(T);
+    wsm = smem + (size_t)wib * wfl;
+    state_sh = (wfl > 3 * (T + 1)) ? wsm + 3 * (T + 1) : nullptr;
+  }
+  const int cs = (T + 32) >> 5, cr = (T + 31) >> 5;   // chunks of T + 1 and T elements
+  for (int w = bid * nw + wib; w < n_inner; w += nblk * nw) {
+    if (w < p.n_stor) {
+      if constexpr (HAS_REG) {
+        if (reg) {
+          stor_r<C>(p, w, q.rho_dev, lane, cs);
+          continue;
+        }
+      }
+      if constexpr (HAS_SMEM) stor_prox(p, w, q.rho_dev, wsm, state_sh, lane);
+    } else if (w < p.n_stor + p.n_ramp) {
+      if constexpr (HAS_REG) {
+        if (reg) {
+          ramp_r<C>(p, w - p.n_stor, q.rho_dev, lane, cr);
+          continue;
+        }
+      }
+      if constexpr (HAS_SMEM) ramp_prox(p, w - p.n_stor, q.rho_dev, wsm, state_sh, lane);
+    } else {
       hvdc_prox(p, w - p.n_stor - p.n_ramp, lane);
+    }
   }
 }
 
@@ -1170,9 +1564,10 @@ __device__ __forceinline__ void decide_body(const Params &p, int n_part) {
 template <int VW>
 __global__ void __launch_bounds__(BLOCK) xs_kernel(Params p) { xs_body<VW>(p, blockIdx.x, gridDim.x); }
 
+template <int C>
 __global__ void __launch_bounds__(BLOCK) inner_kernel(Params p) {
   extern __shared__ float smem[];
-  inner_body(p, blockIdx.x, gridDim.x, smem);
+  inner_body<C, false>(p, blockIdx.x, gridDim.x, smem);
 }
 
 template <int VW>
@@ -1267,14 +1662,17 @@ __global__ void __launch_bounds__(BLOCK) xs_kernel_b(const Params *ps, const int
   xs_body<VW>(p, bid, nblk);
 }
 
-// batches keep the GPU full of inner-ADMM warps: 64 registers, 4 CTAs per SM
-// (the single-instance kernel runs beside the line kernel and keeps 2)
-__global__ void __launch_bounds__(BLOCK, 4) inner_kernel_b(const Params *ps, const int4 *sched) {
+// batches keep the GPU full of inner-ADMM warps: on the shared-memory path
+// alone 64 registers, 4 CTAs per SM; C: the largest register chunk of the
+// batch's instances (0: every horizon beyond REG_T), any longer horizon on
+// the shared-memory path
+template <int C>
+__global__ void __launch_bounds__(BLOCK, C == 0 ? 4 : 1) inner_kernel_b(const Params *ps, const int4 *sched) {
   extern __shared__ float smem[];
   __shared__ Params sp;
   unsigned bid, nblk;
   const Params &p = batch_params(ps, sched, sp, bid, nblk);
-  inner_body(p, bid, nblk, smem);
+  inner_body<C, true>(p, bid, nblk, smem);
 }
 
 template <int VW>
@@ -1565,9 +1963,11 @@ static int resident_grid(F fn, size_t smem) {
 
 int opfk_plan(const Params &p, IterPlan *plan) {
   const bool v4 = (p.T % 4 == 0), v2 = (p.T % 2 == 0);
-  const size_t ism = inner_smem(p.T);
+  // the inner ADMM in registers up to REG_T steps, else in shared memory
+  const int ic = inner_chunk(p.T);
+  const size_t ism = ic ? 0 : inner_smem(p.T);
   if (ism > 48 * 1024 &&
-      cudaFuncSetAttribute(inner_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism) != cudaSuccess)
+      cudaFuncSetAttribute(inner_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism) != cudaSuccess)
     return -1;
   const bool vn = (p.T % NODE_VW == 0);
   const int gn = vn ? resident_grid(node_kernel<NODE_VW, false>, 0) : resident_grid(node_kernel<1, false>, 0);
@@ -1617,6 +2017,7 @@ int opfk_plan(const Params &p, IterPlan *plan) {
   const long long nd = (long long)p.N * (p.T / (v2 ? 2 : 1));
   plan->dsum_grid = (int)std::min<long long>(gd, (nd + BLOCK - 1) / BLOCK);
   plan->inner_smem = ism;
+  plan->inner_c = ic;
   return 0;
 }
 
@@ -1635,7 +2036,15 @@ static int iteration_enqueue(const Params &p, const IterPlan &plan, void *main_s
     if (v4) xs_kernel<4><<<plan.xs_grid, BLOCK, 0, sm>>>(p);
     else xs_kernel<1><<<plan.xs_grid, BLOCK, 0, sm>>>(p);
   }
-  if (plan.inner_grid > 0) inner_kernel<<<plan.inner_grid, BLOCK, plan.inner_smem, sm>>>(p);
+  if (plan.inner_grid > 0) {
+    switch (plan.inner_c) {
+      case 1: inner_kernel<1><<<plan.inner_grid, BLOCK, 0, sm>>>(p); break;
+      case 2: inner_kernel<2><<<plan.inner_grid, BLOCK, 0, sm>>>(p); break;
+      case 3: inner_kernel<3><<<plan.inner_grid, BLOCK, 0, sm>>>(p); break;
+      case 4: inner_kernel<4><<<plan.inner_grid, BLOCK, 0, sm>>>(p); break;
+      default: inner_kernel<0><<<plan.inner_grid, BLOCK, plan.inner_smem, sm>>>(p); break;
+    }
+  }
   if (v2) dsum_kernel<2><<<plan.dsum_grid, BLOCK, 0, sm>>>(p);
   else dsum_kernel<1><<<plan.dsum_grid, BLOCK, 0, sm>>>(p);
   for (int s = 0; s < plan.n_slabs; ++s) {
@@ -1688,6 +2097,7 @@ int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, const BatchL
                     long long sched_cap, long long *sched_len, BatchPlan *bp) {
   long long len = 0;
   size_t ism = 0;
+  int ic_max = 0;
   auto put = [&](int inst, long long b, long long blocks) -> bool {
     if (sched_out) {
       if (len >= sched_cap) return false;
@@ -1718,7 +2128,11 @@ int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, const BatchL
           break;
         case BK_INNER:
           blocks = (n_inner + WARPS - 1) / WARPS;
-          if (blocks) ism = std::max(ism, inner_smem(p.T));
+          if (blocks) {
+            const int ic = inner_chunk(p.T);
+            if (ic) ic_max = std::max(ic_max, ic);
+            else ism = std::max(ism, inner_smem(p.T));   // the shared-memory path
+          }
           break;
         case BK_DSUM2: case BK_DSUM1:
           if ((kind == BK_DSUM2) == v2) blocks = ((long long)p.N * tv2 + BLOCK - 1) / BLOCK;
@@ -1756,13 +2170,21 @@ int opfk_batch_plan(const Params *hp, const IterPlan *plans, int n, const BatchL
     bp->count[kind] = (int)(len - bp->offset[kind]);
   }
   static_assert(NODE_VW == 4, "the batch node kernels are instantiated for widths 4 and 1");
+  bp->inner_c = ic_max;
   bp->inner_smem = ism;
   bp->relax = (n > 0 && hp[0].alpha != 1.f) ? 1 : 0;
   for (int i = 0; i < n; ++i)
     if ((hp[i].alpha != 1.f) != (bp->relax != 0)) return -2;   // one node kernel for every instance
-  if (ism > 48 * 1024 &&
-      cudaFuncSetAttribute(inner_kernel_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism) != cudaSuccess)
-    return -1;
+  if (ism > 48 * 1024) {
+    const int a = (int)ism;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (cudaFuncSetAttribute(inner_kernel_b<0>, at, a) != cudaSuccess ||
+        cudaFuncSetAttribute(inner_kernel_b<1>, at, a) != cudaSuccess ||
+        cudaFuncSetAttribute(inner_kernel_b<2>, at, a) != cudaSuccess ||
+        cudaFuncSetAttribute(inner_kernel_b<3>, at, a) != cudaSuccess ||
+        cudaFuncSetAttribute(inner_kernel_b<4>, at, a) != cudaSuccess)
+      return -1;
+  }
   *sched_len = len;
   return 0;
 }
@@ -1784,8 +2206,17 @@ int opfk_batch_enqueue(const Params *d_params, const int *d_sched, const BatchPl
   if (cudaEventRecord((cudaEvent_t)ev_join, sa) != cudaSuccess) return -1;
   if (bp.count[BK_XS4]) xs_kernel_b<4><<<bp.count[BK_XS4], BLOCK, 0, sm>>>(d_params, at(BK_XS4));
   if (bp.count[BK_XS1]) xs_kernel_b<1><<<bp.count[BK_XS1], BLOCK, 0, sm>>>(d_params, at(BK_XS1));
-  if (bp.count[BK_INNER])
-    inner_kernel_b<<<bp.count[BK_INNER], BLOCK, bp.inner_smem, sm>>>(d_params, at(BK_INNER));
+  if (bp.count[BK_INNER]) {
+    const int4 *si = at(BK_INNER);
+    const int nb = bp.count[BK_INNER];
+    switch (bp.inner_c) {
+      case 1: inner_kernel_b<1><<<nb, BLOCK, bp.inner_smem, sm>>>(d_params, si); break;
+      case 2: inner_kernel_b<2><<<nb, BLOCK, bp.inner_smem, sm>>>(d_params, si); break;
+      case 3: inner_kernel_b<3><<<nb, BLOCK, bp.inner_smem, sm>>>(d_params, si); break;
+      case 4: inner_kernel_b<4><<<nb, BLOCK, bp.inner_smem, sm>>>(d_params, si); break;
+      default: inner_kernel_b<0><<<nb, BLOCK, bp.inner_smem, sm>>>(d_params, si); break;
+    }
+  }
   if (bp.count[BK_DSUM2]) dsum_kernel_b<2><<<bp.count[BK_DSUM2], BLOCK, 0, sm>>>(d_params, at(BK_DSUM2));
   if (bp.count[BK_DSUM1]) dsum_kernel_b<1><<<bp.count[BK_DSUM1], BLOCK, 0, sm>>>(d_params, at(BK_DSUM1));
   if (cudaStreamWaitEvent(sm, (cudaEvent_t)ev_join, 0) != cudaSuccess) return -1;

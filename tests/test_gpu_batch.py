@@ -52,6 +52,35 @@ def test_batch_iterates_equal_single_instance_iterates():
             s.close()
 
 
+def test_mixed_horizons_equal_single_instance_iterates():
+    """Horizons of 1, 24, 48, 96 and 150 steps in one batch: the inner ADMM
+    runs from registers at every horizon up to 127 steps, each with its own
+    chunk of steps per lane, in a kernel sized for the longest (and in
+    shared memory at 150 steps), and still repeats the single-instance
+    iterates bit for bit."""
+    from paper_2410_17203_gb300 import (Solver, opf_batch_create, opf_batch_destroy,
+                                        opf_batch_iterate)
+    specs = [scale_case(100, 1, 3, seed=23), scale_case(150, 24, 6, seed=21), scale_case(120, 48, 4, seed=22),
+             scale_case(120, 96, 4, seed=24), scale_case(30, 150, 1, seed=30, stor_per_node=0.1)]
+    cases = [make_case(sp) for sp in specs]
+    opts = dict(adapt_every=10, eps=0.0)
+    batch_solvers = [Solver(c, opts) for c in cases]
+    single = [Solver(c, opts) for c in cases]
+    b = opf_batch_create([s.h for s in batch_solvers])
+    try:
+        opf_batch_iterate(b, 23)
+        for s in single:
+            s.iterate(23)
+        for sb, ss, sp in zip(batch_solvers, single, specs):
+            a, c = sb.state(), ss.state()
+            for k in a:
+                np.testing.assert_array_equal(a[k], c[k], err_msg=f"T={sp['T']} {k}")
+    finally:
+        opf_batch_destroy(b)
+        for s in batch_solvers + single:
+            s.close()
+
+
 def test_converged_instances_stay_stopped():
     from paper_2410_17203_gb300 import (Solver, opf_batch_converged, opf_batch_create,
                                         opf_batch_destroy, opf_batch_iterate)
