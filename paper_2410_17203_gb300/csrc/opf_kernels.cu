@@ -1996,21 +1996,28 @@ int opfk_plan(const Params &p, IterPlan *plan) {
     // The inner-ADMM kernel is latency-bound (one warp per device through its
     // ten Appendix D iterations) and runs beside the bandwidth-bound line
     // kernel, whose CTAs it displaces.  When the line pass is long enough to
-    // hide it, a grid of one CTA on every other SM, walking the devices in
-    // several rounds, leaves the line kernel more of the GPU (10k buses,
-    // T = 96, K = 50, 3,000 devices: 0.741 -> 0.706 ms per iteration).  The
-    // estimates: a round of devices takes about 0.45 T microseconds, the
-    // line pass moves about 32 bytes per (line, contingency, step) at
-    // 6.5 TB/s; the cap applies while the rounds fit in 70 % of it.
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms >= 2) {
-      const int half = sms / 2;
-      if (plan->inner_grid > half) {
-        const double rounds = std::ceil((double)plan->inner_grid / half);
-        const double inner_us = rounds * 0.45 * p.T;
-        const double line_us = (double)p.Kp * p.L * p.T * 32.0 / 6.5e6;
-        if (inner_us <= 0.7 * line_us) plan->inner_grid = half;
+    // hide it, fewer CTAs walking the devices in several rounds leave the
+    // line kernel more of the GPU.  The estimates: the line pass moves about
+    // 32 bytes per (line, contingency, step) at 6.5 TB/s; a round of devices
+    // takes about 0.13 T microseconds from registers, 0.45 T in shared memory.
+    // Registers: the fewest CTAs whose rounds fit in half the line pass (10k
+    // buses, T = 96, K = 50, 3,000 devices, in ms per iteration: 375 CTAs
+    // 0.706, 76 CTAs 0.706, 38 0.698, 25 0.696, 19 0.704, 12 0.851).  Shared
+    // memory: one CTA on every other SM while its rounds fit in 70 % of it
+    // (0.741 -> 0.706 at the same size).
+    const double line_us = (double)p.Kp * p.L * p.T * 32.0 / 6.5e6;
+    if (ic) {
+      const int max_rounds = (int)std::floor(0.5 * line_us / (0.13 * p.T));
+      if (max_rounds >= 2) plan->inner_grid = (plan->inner_grid + max_rounds - 1) / max_rounds;
+    } else {
+      int dev = 0, sms = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms >= 2) {
+        const int half = sms / 2;
+        if (plan->inner_grid > half) {
+          const double rounds = std::ceil((double)plan->inner_grid / half);
+          if (rounds * 0.45 * p.T <= 0.7 * line_us) plan->inner_grid = half;
+        }
       }
     }
   }
