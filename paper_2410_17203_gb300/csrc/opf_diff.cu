@@ -296,7 +296,10 @@ __device__ void inner_forward(const DP &p, const View &v, const float *x, float 
 }
 
 // step 2 for the inner-ADMM devices: one CTA per device
-__global__ void __launch_bounds__(TBI) fwd_inner(DP p, St s, St nx, const float *XD, float *DEL, int level) {
+// gmask: when not NULL, the iteration's record of which rows clipped
+// (device blocks of N_INNER x m bytes at N_INNER x its first row)
+__global__ void __launch_bounds__(TBI) fwd_inner(DP p, St s, St nx, const float *XD, float *DEL, int level,
+                                                 unsigned char *gmask) {
   extern __shared__ float sm[];
   const IDev di = p.idev[blockIdx.x];
   const Shape sh = p.shape[di.shape];
@@ -309,7 +312,7 @@ __global__ void __launch_bounds__(TBI) fwd_inner(DP p, St s, St nx, const float 
     lam[row] = s.INS[p.Mtot + di.h + row];
   }
   __syncthreads();
-  inner_forward(p, v, x, beta, lam, w, r, z, nullptr);
+  inner_forward(p, v, x, beta, lam, w, r, z, gmask ? gmask + (size_t)N_INNER * di.h : nullptr);
   for (int t = threadIdx.x; t < T; t += blockDim.x) {
     nx.PD[(size_t)di.dev * T + t] = z[t];
     if (di.bat >= 0) DEL[(size_t)di.bat * T + t] = z[2 * T + t];   // discharge, for the cost
@@ -447,16 +450,17 @@ __global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL,
   }
 }
 
-// the inner ADMM backwards, one CTA per device: recompute the N_INNER
-// iterations from state i-1 recording which rows clipped, then walk them in
-// reverse.  Per iteration, with s = alpha + lambda:
+// the inner ADMM backwards, one CTA per device: which rows clipped in each
+// of the N_INNER iterations comes from the forward pass's record (gmask) or,
+// without one, from recomputing the iterations from state i-1; then walk
+// them in reverse.  Per iteration, with s = alpha + lambda:
 //   d s = d lambda' + [clipped] (d beta' - d lambda'),
 //   d z = A' d s (+ the output's adjoint on the last iteration), d h -= d s,
 //   d r = M^-1 d z, d x += rho' (d r)_p, w = omega A d r:
 //   d h += w, d beta = w, d lambda = d s - w.
 // `last`: the iteration whose battery discharge enters the cost.
 __global__ void __launch_bounds__(TBI) bwd_inner(DP p, St s, Adj a, const float *XD, const float *LPDT, float *LX,
-                                                 float *HB, int last, int level) {
+                                                 float *HB, int last, int level, const unsigned char *gmask) {
   extern __shared__ float sm[];
   const IDev di = p.idev[blockIdx.x];
   const Shape sh = p.shape[di.shape];
@@ -465,17 +469,21 @@ __global__ void __launch_bounds__(TBI) bwd_inner(DP p, St s, Adj a, const float 
   float *x = sm, *r = x + T, *z = r + n, *w = z + n, *beta = w + m, *lam = beta + m;
   float *zt = lam + m, *rb = zt + n, *sb = rb + n, *bb = sb + m, *lb = bb + m, *hb = lb + m, *xb = hb + m;
   const View v = stage_view(p, sh, di, xb + T, level);
-  unsigned char *mask = reinterpret_cast<unsigned char *>(xb + T + view_words(n, m, sh.nnz, level));
-  for (int t = threadIdx.x; t < T; t += blockDim.x) {
-    x[t] = XD[(size_t)di.dev * T + t];
-    xb[t] = 0.f;
+  const unsigned char *mask = reinterpret_cast<unsigned char *>(xb + T + view_words(n, m, sh.nnz, level));
+  for (int t = threadIdx.x; t < T; t += blockDim.x) xb[t] = 0.f;
+  if (gmask) {
+    // recorded by the forward pass
+    mask = gmask + (size_t)N_INNER * di.h;
+  } else {
+    unsigned char *msh = reinterpret_cast<unsigned char *>(xb + T + view_words(n, m, sh.nnz, level));
+    for (int t = threadIdx.x; t < T; t += blockDim.x) x[t] = XD[(size_t)di.dev * T + t];
+    for (int row = threadIdx.x; row < m; row += blockDim.x) {
+      beta[row] = s.INS[di.h + row];
+      lam[row] = s.INS[p.Mtot + di.h + row];
+    }
+    __syncthreads();
+    inner_forward(p, v, x, beta, lam, w, r, z, msh);
   }
-  for (int row = threadIdx.x; row < m; row += blockDim.x) {
-    beta[row] = s.INS[di.h + row];
-    lam[row] = s.INS[p.Mtot + di.h + row];
-  }
-  __syncthreads();
-  inner_forward(p, v, x, beta, lam, w, r, z, mask);
   for (int row = threadIdx.x; row < m; row += blockDim.x) {
     bb[row] = a.LINS[di.h + row];
     lb[row] = a.LINS[p.Mtot + di.h + row];
@@ -646,6 +654,10 @@ struct opf_diff {
   // per-line limit gradient and the host staging of the cost's inputs
   float *ck = nullptr, *seg = nullptr, *adj = nullptr, *work = nullptr, *gline = nullptr;
   size_t ck_cap = 0, seg_cap = 0;
+  // which inner-ADMM rows clipped, per iteration of the forward pass
+  // ([K][N_INNER rows of every device], one byte each), for the reverse pass
+  float *masks = nullptr;
+  size_t masks_cap = 0;
 };
 
 namespace {
@@ -793,12 +805,13 @@ St carve_state(const opf_diff *d, float *base) {
   return s;
 }
 
-void forward_step(const opf_diff *d, const St &s, const St &nx, float *XD, float *DEL) {
+void forward_step(const opf_diff *d, const St &s, const St &nx, float *XD, float *DEL,
+                  unsigned char *mask = nullptr) {
   const DP &p = d->p;
   const long long nl = (long long)p.Kp * p.L * p.T, nn = (long long)p.Kp * p.N * p.T, ns = (long long)p.S * p.T;
   fwd_line<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx);
   fwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, nx, XD);
-  if (p.n_inner) fwd_inner<<<p.n_inner, TBI, d->smem_fwd, d->stream>>>(p, s, nx, XD, DEL, d->stage);
+  if (p.n_inner) fwd_inner<<<p.n_inner, TBI, d->smem_fwd, d->stream>>>(p, s, nx, XD, DEL, d->stage, mask);
   fwd_avg<<<grid_for(nn), TB, 0, d->stream>>>(p, nx);
   fwd_upd_nodes<<<grid_for(nn), TB, 0, d->stream>>>(p, s, nx);
   fwd_upd_lines<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx);
@@ -1120,6 +1133,9 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
 namespace {
 
 // grow one of the kept buffers to n floats (contents not kept)
+// the largest record of clipped inner rows a call keeps (bytes)
+constexpr size_t kMaskBytes = size_t(4) << 30;
+
 cudaError_t ensure(float **buf, size_t *cap, size_t n) {
   if (*buf && *cap >= n) return cudaSuccess;
   if (*buf) cudaFree(*buf);
@@ -1163,8 +1179,16 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   if (e == cudaSuccess) e = ensure(&d->adj, &adj_cap, adj_floats);
   if (e == cudaSuccess) e = ensure(&d->work, &work_cap, work_floats);
   if (e == cudaSuccess) e = ensure(&d->gline, &gl_cap, L);
+  // the forward pass records which inner rows clipped, so that the reverse
+  // pass need not run each iteration's inner ADMM again (while the record
+  // stays within kMaskBytes)
+  const size_t mask_iter = (size_t)N_INNER * MT;
+  const bool rec = grads && p.n_inner > 0 && (size_t)K * mask_iter <= kMaskBytes;
+  if (e == cudaSuccess && rec) e = ensure(&d->masks, &d->masks_cap, ((size_t)K * mask_iter + 3) / 4);
   if (e != cudaSuccess)
     return dfail(e == cudaErrorMemoryAllocation ? OPF_ENOMEM : OPF_ECUDA, "diff: device allocation failed");
+  unsigned char *masks = rec ? reinterpret_cast<unsigned char *>(d->masks) : nullptr;
+  auto mask_of = [&](int i) { return masks ? masks + (size_t)(i - 1) * mask_iter : nullptr; };   // iteration i
   float *ck = d->ck, *seg = d->seg, *adj = d->adj, *work = d->work;
   float *X1 = work, *X2 = X1 + KLT, *Y1 = X2 + KLT, *Y2 = Y1 + KLT, *GU = Y2 + KLT;
   float *A = GU + KLT, *Bn = A + KNT, *Cn = Bn + KNT, *Dn = Cn + KNT, *LX = Dn + KNT, *XD = LX + ST;
@@ -1177,7 +1201,7 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   float *scratch = seg;  // two alternating states in the segment buffer
   for (int i = 1; e == cudaSuccess && i <= K; ++i) {
     St nx = (i % C == 0) ? ckst(i / C) : carve_state(d, scratch + (size_t)(i & 1) * SF);
-    forward_step(d, cur, nx, XD, DEL);
+    forward_step(d, cur, nx, XD, DEL, mask_of(i));
     cur = nx;
   }
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -1231,7 +1255,7 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
       bwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT);
       if (p.n_inner)
         bwd_inner<<<p.n_inner, TBI, d->smem_bwd, d->stream>>>(p, s, a, XD, LPDT, LX, HB, i == K ? 1 : 0,
-                                                             d->stage);
+                                                             d->stage, mask_of(i));
       bwd_node2<<<grid_for(nn), TB, 0, d->stream>>>(p, a, X1, X2, Y1, Y2, LX, Cn, Dn);
       bwd_line2<<<grid_for(nl), TB, 0, d->stream>>>(p, a, Cn, Dn);
       bwd_dev2<<<grid_for(ns), TB, 0, d->stream>>>(p, a, LX, Cn);
@@ -1270,7 +1294,7 @@ void opf_diff_destroy(opf_diff *d) {
   if (!d) return;
   cudaStreamSynchronize(d->stream);
   for (void *q : d->allocs) cudaFree(q);
-  for (float *q : {d->ck, d->seg, d->adj, d->work, d->gline})
+  for (float *q : {d->ck, d->seg, d->adj, d->work, d->gline, d->masks})
     if (q) cudaFree(q);
   delete d;
 }
