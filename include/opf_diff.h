@@ -68,6 +68,16 @@ opf_status opf_diff_cost_grad_on(opf_diff *d, int32_t K, int32_t on_device, cons
                                  const float *gen_pmax, const float *line_u, double *cost, float *grad_load_p,
                                  float *grad_gen_pmax, float *grad_line_u);
 
+/* The most device memory (bytes) a gradient call may keep for its record of
+ * the forward pass: per iteration, which inner-ADMM rows clipped (one byte
+ * per row and inner iteration) and where each line's and closed-form
+ * device's unclipped value lay (one byte per line item and device step).
+ * With the record the reverse pass runs no inner iteration and recomputes no
+ * prox input; a call whose record would exceed the limit (and every call
+ * after a limit of 0) recomputes them from the states instead, with the same
+ * result bit for bit.  Default 4 GiB.  OPF_EINVAL for d NULL or bytes < 0. */
+opf_status opf_diff_set_record_limit(opf_diff *d, int64_t bytes);
+
 void opf_diff_destroy(opf_diff *d);
 
 #ifdef __cplusplus

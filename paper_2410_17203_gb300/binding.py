@@ -92,7 +92,8 @@ EXPORTS = ["opf_default_options", "opf_create", "opf_create_slice", "opf_slice_e
            "opf_batch_autotune",
            "opf_wsnet_param_count", "opf_wsnet_create", "opf_wsnet_get_params", "opf_wsnet_set_params",
            "opf_wsnet_forward", "opf_wsnet_gradient", "opf_wsnet_train_step", "opf_wsnet_destroy",
-           "opf_diff_create", "opf_diff_cost_grad", "opf_diff_cost_grad_on", "opf_diff_destroy"]
+           "opf_diff_create", "opf_diff_cost_grad", "opf_diff_cost_grad_on", "opf_diff_set_record_limit",
+           "opf_diff_destroy"]
 
 _lib = None
 
@@ -174,9 +175,10 @@ def load_library(path=None):
     lib.opf_diff_cost_grad.argtypes = [C.c_void_p, C.c_int32, F32P, F32P, F32P, F64P, F32P, F32P, F32P]
     lib.opf_diff_cost_grad_on.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                           F64P, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.opf_diff_set_record_limit.argtypes = [C.c_void_p, C.c_int64]
     lib.opf_diff_destroy.argtypes = [C.c_void_p]
     lib.opf_diff_destroy.restype = None
-    for name in ("opf_diff_create", "opf_diff_cost_grad", "opf_diff_cost_grad_on"):
+    for name in ("opf_diff_create", "opf_diff_cost_grad", "opf_diff_cost_grad_on", "opf_diff_set_record_limit"):
         getattr(lib, name).restype = C.c_int
     for name in ("opf_create_slice", "opf_slice_exchange", "opf_slice_prime", "opf_slice_begin", "opf_slice_local",
                  "opf_slice_finish"):
@@ -608,6 +610,11 @@ class UnrolledCost:
                                               C.byref(out)), "opf_diff_create")
         del keep
         self.h = out
+
+    def set_record_limit(self, nbytes):
+        """Device memory a gradient call may keep for its record of the
+        forward pass (opf_diff_set_record_limit); 0 recomputes instead."""
+        _check(load_library().opf_diff_set_record_limit(self.h, int(nbytes)), "opf_diff_set_record_limit")
 
     def cost_grad(self, K, load_p=None, gen_pmax=None, line_u=None, grads=True):
         F32P = C.POINTER(C.c_float)

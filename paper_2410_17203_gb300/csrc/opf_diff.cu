@@ -116,8 +116,17 @@ __device__ __forceinline__ LineIn line_inputs(const DP &p, const St &s, int k, i
   return r;
 }
 
-// step 1: line prox (Section 4.2); outaged lines decouple
-__global__ void fwd_line(DP p, St s, St nx) {
+// where an unclipped value z lies against [lo, hi]: 0 inside, 1 above, 2
+// below, 3 unordered (not a number); the reverse pass reads it from the
+// forward's record
+enum { CLIP_IN = 0, CLIP_HI = 1, CLIP_LO = 2, CLIP_NAN = 3 };
+__device__ __forceinline__ unsigned char clip_code(float z, float lo, float hi) {
+  return (z >= lo && z <= hi) ? CLIP_IN : z > hi ? CLIP_HI : z < lo ? CLIP_LO : CLIP_NAN;
+}
+
+// step 1: line prox (Section 4.2); outaged lines decouple.  lmask (optional):
+// the iteration's record of where each line's unclipped flow lay
+__global__ void fwd_line(DP p, St s, St nx, unsigned char *lmask) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
@@ -126,6 +135,7 @@ __global__ void fwd_line(DP p, St s, St nx) {
       const float b = p.b[l], tb = 2.f * b, u = p.lu[l];
       const float den = 2.f * p.rp + p.rt / (tb * b);
       const float z = (p.rp * (in.x2 - in.x1) + p.rt * (in.y1 - in.y2) / tb) / den;
+      if (lmask) lmask[i] = clip_code(z, -u, u);
       const float p2 = fminf(fmaxf(z, -u), u);
       const float mid = 0.5f * (in.y1 + in.y2);
       nx.P[i] = p2;
@@ -149,7 +159,9 @@ __device__ __forceinline__ float dev_x(const DP &p, const St &s, int d, int t) {
 // step 2: devices shared by all contingencies, weight (K+1) rho_p; the
 // inner-ADMM devices only record their input X here.  An HVDC terminal
 // evaluates its link's prox p2 = clip((x2 - x1)/2, -u, u), p1 = -p2.
-__global__ void fwd_dev(DP p, St s, St nx, float *XD) {
+// dmask (optional): the iteration's record of where each closed-form
+// device's unclipped power lay
+__global__ void fwd_dev(DP p, St s, St nx, float *XD, unsigned char *dmask) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
     const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T);
     const float X = dev_x(p, s, d, t);
@@ -160,19 +172,27 @@ __global__ void fwd_dev(DP p, St s, St nx, float *XD) {
     if (p.kind[d] == 2) {
       const int e = d - (p.G + p.D + p.B), d1 = d - (e & 1), h = e >> 1;
       const float x1 = (e & 1) ? dev_x(p, s, d1, t) : X, x2 = (e & 1) ? X : dev_x(p, s, d1 + 1, t);
-      const float f = fminf(fmaxf(0.5f * (x2 - x1), -p.hvdc_u[h]), p.hvdc_u[h]);
+      const float z = 0.5f * (x2 - x1), u = p.hvdc_u[h];
+      if (dmask) dmask[i] = clip_code(z, -u, u);
+      const float f = fminf(fmaxf(z, -u), u);
       nx.PD[i] = (e & 1) ? f : -f;
       continue;
     }
     float r;
     if (d < p.G) {
       const float z = (p.rd * X - p.gb[d]) / (2.f * p.ga[d] + p.rd);
+      if (dmask) dmask[i] = clip_code(z, p.gpmin[i], p.gpmax[i]);
       r = fminf(fmaxf(z, p.gpmin[i]), p.gpmax[i]);
     } else {
       const int e = d - p.G;
       const size_t o = (size_t)e * p.T + t;
-      if (p.voll[e] < 0.f) r = -p.load_p[o];
-      else r = fminf(fmaxf((p.rd * X - p.voll[e]) / p.rd, -p.load_p[o]), 0.f);
+      if (p.voll[e] < 0.f) {
+        r = -p.load_p[o];
+      } else {
+        const float z = (p.rd * X - p.voll[e]) / p.rd;
+        if (dmask) dmask[i] = clip_code(z, -p.load_p[o], 0.f);
+        r = fminf(fmaxf(z, -p.load_p[o]), 0.f);
+      }
     }
     nx.PD[i] = r;
   }
@@ -359,8 +379,10 @@ __global__ void bwd_node1(DP p, Adj a, float *A, float *B) {
 }
 
 // the line prox backwards; X1.. hold d/d(x1, x2, y1, y2) for the node gathers
+// lmask (optional): the forward's record of the iteration's line clips,
+// else the unclipped flows are recomputed from state i-1
 __global__ void bwd_line1(DP p, St s, Adj a, const float *A, const float *B, float *X1, float *X2, float *Y1,
-                          float *Y2, float *GU) {
+                          float *Y2, float *GU, const unsigned char *lmask) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
@@ -371,20 +393,25 @@ __global__ void bwd_line1(DP p, St s, Adj a, const float *A, const float *B, flo
     const float lt2 = a.LT2[i] + a.LV2[i] + (p.cth[n2] > 0.f ? B[o2] / p.cth[n2] : 0.f);
     float lx1 = 0.f, lx2 = 0.f, ly1, ly2;
     if (p.out[k] != l) {
-      const LineIn in = line_inputs(p, s, k, l, t);
       const float b = p.b[l], tb = 2.f * b, u = p.lu[l];
       const float den = 2.f * p.rp + p.rt / (tb * b);
-      const float z = (p.rp * (in.x2 - in.x1) + p.rt * (in.y1 - in.y2) / tb) / den;
+      unsigned char code;
+      if (lmask) {
+        code = lmask[i];
+      } else {
+        const LineIn in = line_inputs(p, s, k, l, t);
+        code = clip_code((p.rp * (in.x2 - in.x1) + p.rt * (in.y1 - in.y2) / tb) / den, -u, u);
+      }
       const float lpt = lp + (lt1 - lt2) / tb;     // theta_{1,2} = mid +- p / (2b)
       ly1 = ly2 = 0.5f * (lt1 + lt2);
-      if (z >= -u && z <= u) {
+      if (code == CLIP_IN) {
         lx2 = p.rp * lpt / den;
         lx1 = -lx2;
         const float w = p.rt * lpt / (tb * den);
         ly1 += w;
         ly2 -= w;
       } else {
-        GU[i] += z > u ? lpt : -lpt;
+        GU[i] += code == CLIP_HI ? lpt : -lpt;
       }
     } else {
       ly1 = lt1;
@@ -410,40 +437,51 @@ __device__ __forceinline__ float dev_lpd(const DP &p, const Adj &a, const float 
   return lpd;
 }
 
-__global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL, float *GP, float *XD, float *LPDT) {
+// dmask (optional): the forward's record of the iteration's device clips
+// (the inner-ADMM devices then need no X either: their clipped rows are
+// recorded too); else X is recomputed from state i-1
+__global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL, float *GP, float *XD, float *LPDT,
+                        const unsigned char *dmask) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
     const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T);
     const float lpd = dev_lpd(p, a, A, d, t);
-    const float X = dev_x(p, s, d, t);
+    const float X = dmask ? 0.f : dev_x(p, s, d, t);
     if (p.kind[d] == 1) {
-      XD[i] = X;
+      if (!dmask) XD[i] = X;
       LPDT[i] = lpd;
       continue;
     }
     if (p.kind[d] == 2) {                // HVDC: both terminals' adjoints meet in d/d p2
       const int e = d - (p.G + p.D + p.B), d1 = d - (e & 1), h = e >> 1;
-      const float x1 = (e & 1) ? dev_x(p, s, d1, t) : X, x2 = (e & 1) ? X : dev_x(p, s, d1 + 1, t);
       const float l1 = (e & 1) ? dev_lpd(p, a, A, d1, t) : lpd, l2 = (e & 1) ? lpd : dev_lpd(p, a, A, d1 + 1, t);
-      const float z = 0.5f * (x2 - x1), u = p.hvdc_u[h];
-      const float lz = (z >= -u && z <= u) ? 0.5f * (l2 - l1) : 0.f;
+      const float u = p.hvdc_u[h];
+      unsigned char code;
+      if (dmask) {
+        code = dmask[i];
+      } else {
+        const float x1 = (e & 1) ? dev_x(p, s, d1, t) : X, x2 = (e & 1) ? X : dev_x(p, s, d1 + 1, t);
+        code = clip_code(0.5f * (x2 - x1), -u, u);
+      }
+      const float lz = code == CLIP_IN ? 0.5f * (l2 - l1) : 0.f;
       LX[i] = (e & 1) ? lz : -lz;
       continue;
     }
     float lx = 0.f;
     if (d < p.G) {
       const float den = 2.f * p.ga[d] + p.rd;
-      const float z = (p.rd * X - p.gb[d]) / den;
-      if (z >= p.gpmin[i] && z <= p.gpmax[i]) lx = lpd * p.rd / den;
-      else if (z > p.gpmax[i]) GP[i] += lpd;
+      const unsigned char code = dmask ? dmask[i] : clip_code((p.rd * X - p.gb[d]) / den, p.gpmin[i], p.gpmax[i]);
+      if (code == CLIP_IN) lx = lpd * p.rd / den;
+      else if (code == CLIP_HI) GP[i] += lpd;
     } else {
       const int e = d - p.G;
       const size_t o = (size_t)e * p.T + t;
       if (p.voll[e] < 0.f) {
         GL[o] -= lpd;                    // p = -P
       } else {
-        const float z = (p.rd * X - p.voll[e]) / p.rd;
-        if (z >= -p.load_p[o] && z <= 0.f) lx = lpd;
-        else if (z < -p.load_p[o]) GL[o] -= lpd;
+        const unsigned char code =
+            dmask ? dmask[i] : clip_code((p.rd * X - p.voll[e]) / p.rd, -p.load_p[o], 0.f);
+        if (code == CLIP_IN) lx = lpd;
+        else if (code == CLIP_LO) GL[o] -= lpd;
       }
     }
     LX[i] = lx;
@@ -658,6 +696,7 @@ struct opf_diff {
   // ([K][N_INNER rows of every device], one byte each), for the reverse pass
   float *masks = nullptr;
   size_t masks_cap = 0;
+  size_t record_limit = size_t(4) << 30;   // opf_diff_set_record_limit
 };
 
 namespace {
@@ -805,12 +844,16 @@ St carve_state(const opf_diff *d, float *base) {
   return s;
 }
 
+// mask (optional): the iteration's record for the reverse pass -- the
+// clipped inner rows, then a byte per line item, then one per device step
 void forward_step(const opf_diff *d, const St &s, const St &nx, float *XD, float *DEL,
                   unsigned char *mask = nullptr) {
   const DP &p = d->p;
   const long long nl = (long long)p.Kp * p.L * p.T, nn = (long long)p.Kp * p.N * p.T, ns = (long long)p.S * p.T;
-  fwd_line<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx);
-  fwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, nx, XD);
+  unsigned char *lmask = mask ? mask + (size_t)N_INNER * p.Mtot : nullptr;
+  unsigned char *dmask = mask ? lmask + nl : nullptr;
+  fwd_line<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx, lmask);
+  fwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, nx, XD, dmask);
   if (p.n_inner) fwd_inner<<<p.n_inner, TBI, d->smem_fwd, d->stream>>>(p, s, nx, XD, DEL, d->stage, mask);
   fwd_avg<<<grid_for(nn), TB, 0, d->stream>>>(p, nx);
   fwd_upd_nodes<<<grid_for(nn), TB, 0, d->stream>>>(p, s, nx);
@@ -1133,9 +1176,6 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
 namespace {
 
 // grow one of the kept buffers to n floats (contents not kept)
-// the largest record of clipped inner rows a call keeps (bytes)
-constexpr size_t kMaskBytes = size_t(4) << 30;
-
 cudaError_t ensure(float **buf, size_t *cap, size_t n) {
   if (*buf && *cap >= n) return cudaSuccess;
   if (*buf) cudaFree(*buf);
@@ -1179,11 +1219,12 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   if (e == cudaSuccess) e = ensure(&d->adj, &adj_cap, adj_floats);
   if (e == cudaSuccess) e = ensure(&d->work, &work_cap, work_floats);
   if (e == cudaSuccess) e = ensure(&d->gline, &gl_cap, L);
-  // the forward pass records which inner rows clipped, so that the reverse
-  // pass need not run each iteration's inner ADMM again (while the record
-  // stays within kMaskBytes)
-  const size_t mask_iter = (size_t)N_INNER * MT;
-  const bool rec = grads && p.n_inner > 0 && (size_t)K * mask_iter <= kMaskBytes;
+  // the forward pass records which inner rows clipped and where each line's
+  // and closed-form device's unclipped value lay, so that the reverse pass
+  // need not run each iteration's inner ADMM again nor recompute the prox
+  // inputs (while the record stays within the context's limit)
+  const size_t mask_iter = (size_t)N_INNER * MT + KLT + ST;
+  const bool rec = grads && (size_t)K * mask_iter <= d->record_limit;
   if (e == cudaSuccess && rec) e = ensure(&d->masks, &d->masks_cap, ((size_t)K * mask_iter + 3) / 4);
   if (e != cudaSuccess)
     return dfail(e == cudaErrorMemoryAllocation ? OPF_ENOMEM : OPF_ECUDA, "diff: device allocation failed");
@@ -1251,11 +1292,13 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
     for (int i = hi; e == cudaSuccess && i > lo; --i) {
       const St s = sgst(i - 1 - lo);   // state i - 1
       bwd_node1<<<grid_for(nn), TB, 0, d->stream>>>(p, a, A, Bn);
-      bwd_line1<<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, Bn, X1, X2, Y1, Y2, GU);
-      bwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT);
+      unsigned char *mi = mask_of(i);
+      const unsigned char *lmask = mi ? mi + (size_t)N_INNER * MT : nullptr, *dmask = mi ? lmask + KLT : nullptr;
+      bwd_line1<<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, Bn, X1, X2, Y1, Y2, GU, lmask);
+      bwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT, dmask);
       if (p.n_inner)
         bwd_inner<<<p.n_inner, TBI, d->smem_bwd, d->stream>>>(p, s, a, XD, LPDT, LX, HB, i == K ? 1 : 0,
-                                                             d->stage, mask_of(i));
+                                                             d->stage, mi);
       bwd_node2<<<grid_for(nn), TB, 0, d->stream>>>(p, a, X1, X2, Y1, Y2, LX, Cn, Dn);
       bwd_line2<<<grid_for(nl), TB, 0, d->stream>>>(p, a, Cn, Dn);
       bwd_dev2<<<grid_for(ns), TB, 0, d->stream>>>(p, a, LX, Cn);
@@ -1288,6 +1331,13 @@ opf_status opf_diff_cost_grad_on(opf_diff *d, int32_t K, int32_t on_device, cons
                                  const float *gen_pmax, const float *line_u, double *cost, float *g_load,
                                  float *g_pmax, float *g_u) {
   return cost_grad(d, K, on_device ? 1 : 0, load_p, gen_pmax, line_u, cost, g_load, g_pmax, g_u);
+}
+
+opf_status opf_diff_set_record_limit(opf_diff *d, int64_t bytes) {
+  if (!d) return dfail(OPF_EINVAL, "diff is NULL");
+  if (bytes < 0) return dfail(OPF_EINVAL, "diff: the record limit must be >= 0");
+  d->record_limit = (size_t)bytes;
+  return OPF_OK;
 }
 
 void opf_diff_destroy(opf_diff *d) {

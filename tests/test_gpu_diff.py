@@ -75,13 +75,17 @@ def test_base_case_only_and_single_step():
 
 def test_checkpointing_is_exact():
     """Recomputed segments repeat the forward pass bit for bit, so the
-    gradients do not depend on the checkpoint spacing."""
+    gradients do not depend on the checkpoint spacing, nor on whether the
+    reverse pass reads the forward's record of clipped values or recomputes
+    them (record limit 0; a limit too small for this call)."""
     b = _lib()
-    case = make_case(scale_case(120, 4, 3, seed=8, ramp=True, stor_per_node=0.05, fixed_frac=0.3))
+    case = make_case(scale_case(120, 4, 3, seed=8, ramp=True, stor_per_node=0.05, fixed_frac=0.3, n_hvdc=2))
     outs = []
-    for ckpt in (1, 5, 64):
+    for ckpt, limit in ((1, None), (5, None), (64, None), (1, 0), (5, 0), (5, 1000)):
         d = b.UnrolledCost(case, rho_p=10.0, rho_theta=20.0, checkpoint_every=ckpt)
         try:
+            if limit is not None:
+                d.set_record_limit(limit)
             outs.append(d.cost_grad(37))
         finally:
             d.close()
@@ -89,6 +93,20 @@ def test_checkpointing_is_exact():
         assert f == outs[0][0]
         for k in g:
             np.testing.assert_array_equal(g[k], outs[0][1][k])
+    # the same context switching between the two
+    d = b.UnrolledCost(case, rho_p=10.0, rho_theta=20.0, checkpoint_every=5)
+    try:
+        d.set_record_limit(0)
+        f0, g0 = d.cost_grad(23)
+        d.set_record_limit(1 << 30)
+        f1, g1 = d.cost_grad(23)
+        with pytest.raises(b.OpfError):
+            d.set_record_limit(-1)
+    finally:
+        d.close()
+    assert f0 == f1
+    for k in g0:
+        np.testing.assert_array_equal(g0[k], g1[k])
 
 
 def test_data_arguments_replace_the_case_data():
