@@ -30,7 +30,7 @@ constexpr int N_INNER = 10;   // Appendix D iterations per prox evaluation (Sect
 // one inner-ADMM device: its index among all devices, its constraint shape,
 // and offsets of its inverse system matrix, right-hand side rows and linear cost
 struct IDev {
-  int dev, shape, minv, h, q, bat, pad0, pad1;  // bat: battery index, -1 for a generator
+  int dev, shape, minv, h, q, bat, piv, pad1;  // bat: battery index, -1 for a generator; piv: see DP::piv
 };
 
 // constraint rows A z <= h (eq: = h) of one device kind, in CSR and CSC form
@@ -61,6 +61,13 @@ struct DP {
   const int *arp, *aci, *atp, *ati;
   const float *acv, *atv, *minv, *RH, *Q, *scost;   // RH: right-hand sides of the inner rows
   const unsigned char *aeq;
+  // the register path of the inner ADMM (horizons up to DREG_T): chunk of
+  // steps per lane (0: the shared-memory path), each device's factor at
+  // IDev::piv -- a ramp generator its pivots q [T] and a = 2 omega / q [T],
+  // a battery eight constants (H^-1: i00 i01 i11, g = H^-1 f: gc gd), then
+  // q [T+1] and a = gam / q [T+1] -- and the batteries' efficiencies
+  int reg_c;
+  const float *piv, *beff;
 };
 
 struct St {
@@ -572,6 +579,705 @@ __global__ void __launch_bounds__(TBI) bwd_inner(DP p, St s, Adj a, const float 
   }
 }
 
+// ---------------------------------------------------------------------------
+// The inner ADMM from registers (horizons up to DREG_T steps), one warp per
+// device: lane l holds elements l C .. l C + C - 1 of each vector (steps t of
+// p, c and delta, states of charge s_t), and the solves of M z = r use the
+// structure of M = diag(qd) + omega A'A instead of its inverse: a ramp
+// generator's M is tridiagonal; a battery's reduces, after eliminating p and
+// then (c, delta) step by step (2 x 2 blocks H), to a tridiagonal system in
+// s.  The same solve serves the forward iterations and the reverse pass (M is
+// symmetric).  Every operation is written with its rounding, so the forward
+// pass and a recomputation in the reverse pass repeat each other bit for bit.
+// ---------------------------------------------------------------------------
+constexpr int DREG_T = 127;
+constexpr unsigned FULLM = 0xffffffffu;
+constexpr int RWARPS = TB / 32;   // devices per CTA of the register kernels
+
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// x := M^-1 x for a tridiagonal M with pivots q and a = -off / q (element i
+// = lane C + j, valid while i < n): first-order recurrences composed over
+// each lane's chunk, then across the warp by shuffle scans
+template <int C>
+__device__ __forceinline__ void tri_solve_r(const float (&q)[C], const float (&a)[C], float (&x)[C], int n,
+                                            int lane) {
+  const int i0 = lane * C;
+  float r[C];
+  float Ac = 1.f, Bc = 0.f;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    r[j] = 0.f;
+    if (i0 + j < n) {
+      r[j] = rdiv(x[j], q[j]);
+      const float Ai = (i0 + j == 0) ? 0.f : a[j];
+      Bc = rfma(Ai, Bc, r[j]);
+      Ac = rmul(Ai, Ac);
+    }
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float Ap = __shfl_up_sync(FULLM, Ac, d), Bp = __shfl_up_sync(FULLM, Bc, d);
+    if (lane >= d) {
+      Bc = rfma(Ac, Bp, Bc);
+      Ac = rmul(Ac, Ap);
+    }
+  }
+  float prev = __shfl_up_sync(FULLM, Bc, 1);
+  if (lane == 0) prev = 0.f;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    if (i0 + j < n) {
+      const float Ai = (i0 + j == 0) ? 0.f : a[j];
+      prev = rfma(Ai, prev, r[j]);
+      x[j] = prev;
+    }
+  }
+  Ac = 1.f;
+  Bc = 0.f;
+#pragma unroll
+  for (int j = C - 1; j >= 0; --j) {
+    if (i0 + j < n) {
+      const float Ci = (i0 + j == n - 1) ? 0.f : a[j];
+      Bc = rfma(Ci, Bc, x[j]);
+      Ac = rmul(Ci, Ac);
+    }
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float Ap = __shfl_down_sync(FULLM, Ac, d), Bp = __shfl_down_sync(FULLM, Bc, d);
+    if (lane + d < 32) {
+      Bc = rfma(Ac, Bp, Bc);
+      Ac = rmul(Ac, Ap);
+    }
+  }
+  float nxt = __shfl_down_sync(FULLM, Bc, 1);
+  if (lane == 31) nxt = 0.f;
+#pragma unroll
+  for (int j = C - 1; j >= 0; --j) {
+    if (i0 + j < n) {
+      const float Ci = (i0 + j == n - 1) ? 0.f : a[j];
+      nxt = rfma(Ci, nxt, x[j]);
+      x[j] = nxt;
+    }
+  }
+}
+
+// The register path records which rows clipped as one 64-bit word per lane
+// and inner iteration (bit g C + j: row group g, element j of the lane's
+// chunk), [device][inner iteration][lane]: coalesced stores and loads.
+constexpr size_t RREC_WORDS = (size_t)N_INNER * 32;   // words per device and outer iteration
+
+// bytes of one outer iteration's record of the inner ADMM: the register
+// path's words, or the shared-memory path's byte per row and inner iteration
+__host__ __device__ inline size_t inner_record_bytes(const DP &p) {
+  return p.reg_c ? (size_t)p.n_inner * RREC_WORDS * sizeof(unsigned long long) : (size_t)N_INNER * p.Mtot;
+}
+
+// one inequality row of the inner ADMM: s = alpha + lambda, beta = min(s, 0),
+// lambda = s - beta; bit b of the record says whether beta took s
+__device__ __forceinline__ void ineq_r(float al, float &lam, float &bet, unsigned long long &bits, int b) {
+  const float sv = radd(al, lam);
+  const float bt = fminf(sv, 0.f);
+  if (sv <= 0.f) bits |= 1ull << b;
+  bet = bt;
+  lam = rsub(sv, bt);
+}
+
+// the adjoint of that row: d s = d lambda' + [clipped] (d beta' - d lambda')
+__device__ __forceinline__ float sbar_r(unsigned long long bits, int b, float bb, float lb) {
+  return ((bits >> b) & 1ull) ? radd(lb, rsub(bb, lb)) : lb;
+}
+
+// A battery's constants: omega eta, H^-1 and g = H^-1 f with f = (-omega eta,
+// omega) the coupling of (c_t, delta_t) to s_{t+1} - s_t
+struct StorK {
+  float rho, om, eta, rpo, i00, i01, i11, gc, gd;
+};
+
+// z := M^-1 z for a battery, z = (p, c, delta) at steps t < T, s at j <= T
+// (element e = lane C + j holds step e and state of charge e)
+template <int C>
+__device__ __forceinline__ void stor_solve_r(const StorK &k, const float (&qv)[C], const float (&av)[C],
+                                             float (&zp)[C], float (&zc)[C], float (&zd)[C], float (&zs)[C], int T,
+                                             int lane) {
+  const int t0 = lane * C;
+  const float fc = -rmul(k.om, k.eta), fd = k.om;
+  float u[C], yc[C], yd[C], fy[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    u[j] = yc[j] = yd[j] = fy[j] = 0.f;
+    if (t0 + j < T) {
+      u[j] = rdiv(zp[j], k.rpo);                          // p = u - omega (c - delta) / (rho + omega)
+      const float rc = rsub(zc[j], rmul(k.om, u[j])), rd = radd(zd[j], rmul(k.om, u[j]));
+      yc[j] = rfma(k.i00, rc, rmul(k.i01, rd));             // y = H^-1 r'
+      yd[j] = rfma(k.i01, rc, rmul(k.i11, rd));
+      fy[j] = rfma(fc, yc[j], rmul(fd, yd[j]));
+    }
+  }
+  const float fyp = __shfl_up_sync(FULLM, fy[C - 1], 1);
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int e = t0 + j;
+    if (e <= T) {
+      float r = zs[j];
+      if (e <= T - 1) r = radd(r, fy[j]);
+      if (e >= 1) r = rsub(r, (j == 0) ? fyp : fy[j - 1]);
+      zs[j] = r;
+    }
+  }
+  tri_solve_r<C>(qv, av, zs, T + 1, lane);
+  const float sn = __shfl_down_sync(FULLM, zs[0], 1);
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    if (t0 + j < T) {
+      const float dsv = rsub((j == C - 1) ? sn : zs[j + 1], zs[j]);
+      const float c = rsub(yc[j], rmul(k.gc, dsv)), dl = rsub(yd[j], rmul(k.gd, dsv));
+      zc[j] = c;
+      zd[j] = dl;
+      zp[j] = rsub(u[j], rdiv(rmul(k.om, rsub(c, dl)), k.rpo));
+    }
+  }
+}
+
+// N_INNER forward iterations of a ramp generator from registers.  Rows (offset
+// in the device's block): UP p_t <= pmax_t (t), LO -p_t <= -pmin_t (T + t),
+// RU p_{t+1} - p_t <= R (2T + t), RD p_t - p_{t+1} <= R (3T - 1 + t).  mask:
+// the device's record block (N_INNER x m bytes) or NULL
+template <int C>
+__device__ void ramp_fwd_r(int T, int lane, float rho, float om, float qlin, const float (&x)[C],
+                           const float (&qv)[C], const float (&av)[C], const float (&hU)[C], const float (&hL)[C],
+                           const float (&hRU)[C], const float (&hRD)[C], float (&bU)[C], float (&lU)[C],
+                           float (&bL)[C], float (&lL)[C], float (&bRU)[C], float (&lRU)[C], float (&bRD)[C],
+                           float (&lRD)[C], float (&z)[C], unsigned long long *rec) {
+  const int t0 = lane * C;
+  for (int it = 0; it < N_INNER; ++it) {
+    unsigned long long bits = 0;
+    float wRU[C], wRD[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      wRU[j] = rsub(radd(hRU[j], bRU[j]), lRU[j]);
+      wRD[j] = rsub(radd(hRD[j], bRD[j]), lRD[j]);
+    }
+    const float pRU = __shfl_up_sync(FULLM, wRU[C - 1], 1), pRD = __shfl_up_sync(FULLM, wRD[C - 1], 1);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int t = t0 + j;
+      z[j] = 0.f;
+      if (t < T) {
+        float acc = rsub(rsub(radd(hU[j], bU[j]), lU[j]), rsub(radd(hL[j], bL[j]), lL[j]));   // A'w, w = h + beta - lambda
+        if (t >= 1) acc = radd(acc, rsub(j ? wRU[j - 1] : pRU, j ? wRD[j - 1] : pRD));
+        if (t <= T - 2) acc = rsub(acc, rsub(wRU[j], wRD[j]));
+        z[j] = rfma(rho, x[j], rfma(om, acc, -qlin));                                           // r
+      }
+    }
+    tri_solve_r<C>(qv, av, z, T, lane);
+    const float zn = __shfl_down_sync(FULLM, z[0], 1);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int t = t0 + j;
+      if (t < T) {
+        ineq_r(rsub(z[j], hU[j]), lU[j], bU[j], bits, j);
+        ineq_r(rsub(-z[j], hL[j]), lL[j], bL[j], bits, C + j);
+        if (t < T - 1) {
+          const float znx = (j == C - 1) ? zn : z[j + 1];
+          ineq_r(rsub(rsub(znx, z[j]), hRU[j]), lRU[j], bRU[j], bits, 2 * C + j);
+          ineq_r(rsub(rsub(z[j], znx), hRD[j]), lRD[j], bRD[j], bits, 3 * C + j);
+        }
+      }
+    }
+    if (rec) rec[(size_t)it * 32 + lane] = bits;
+  }
+}
+
+// A battery's rows (offset in the device's block): E1 p + c - delta = 0 (t),
+// E2 s_{t+1} - s_t - eta c + delta = 0 (T + t), E3 s_0 = 0 (2T), s_T = 0
+// (2T + 1), CU c <= P (2T + 2 + t), CL -c <= 0 (3T + 2 + t), DU delta <= P
+// (4T + 2 + t), DL -delta <= 0 (5T + 2 + t), SU s <= E (6T + 2 + j), SL -s <=
+// 0 (7T + 3 + j).  Per element its rows' values; E3's on the lanes that hold
+// s_0 and s_T.
+enum { SE1 = 0, SE2, SCU, SCL, SDU, SDL, SSU, SSL, SGROUPS };
+template <int C>
+struct StorRows {
+  float v[SGROUPS][C];   // per group (SE1 .. SSL) and element
+  float E3a, E3b;
+};
+// offset of group g's row for element e in the battery's block
+__device__ __forceinline__ int srow(int g, int e, int T) { return g * T + (g >= SCU ? 2 : 0) + (g == SSL ? 1 : 0) + e; }
+// whether element e has a row in group g (steps for SE1 .. SDL, states of charge for SSU, SSL)
+__device__ __forceinline__ bool shas(int g, int e, int T) { return g < SSU ? e < T : e <= T; }
+
+template <int C>
+__device__ void stor_fwd_r(int T, int lane, const StorK &k, float cost, float Pm, float Em, const float (&x)[C],
+                           const float (&qv)[C], const float (&av)[C], StorRows<C> &lam, StorRows<C> &bet,
+                           float (&zp)[C], float (&zd)[C], unsigned long long *rec) {
+  const int t0 = lane * C;
+  for (int it = 0; it < N_INNER; ++it) {
+    unsigned long long bits = 0;
+    // w = h + beta - lambda (beta = 0 and h = 0 on the equality rows)
+    float wE2[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) wE2[j] = -lam.v[SE2][j];
+    const float pE2 = __shfl_up_sync(FULLM, wE2[C - 1], 1);
+    float zc[C], zs[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int e = t0 + j;
+      zp[j] = zc[j] = zd[j] = zs[j] = 0.f;
+      if (e < T) {
+        const float wE1 = -lam.v[SE1][j];
+        const float wCU = rsub(radd(Pm, bet.v[SCU][j]), lam.v[SCU][j]), wCL = rsub(bet.v[SCL][j], lam.v[SCL][j]);
+        const float wDU = rsub(radd(Pm, bet.v[SDU][j]), lam.v[SDU][j]), wDL = rsub(bet.v[SDL][j], lam.v[SDL][j]);
+        zp[j] = rfma(k.rho, x[j], rmul(k.om, wE1));
+        zc[j] = rmul(k.om, rsub(radd(rfma(-k.eta, wE2[j], wE1), wCU), wCL));
+        zd[j] = rsub(rmul(k.om, rsub(radd(radd(-wE1, wE2[j]), wDU), wDL)), cost);
+      }
+      if (e <= T) {
+        float as = rsub(rsub(radd(Em, bet.v[SSU][j]), lam.v[SSU][j]), rsub(bet.v[SSL][j], lam.v[SSL][j]));
+        if (e >= 1) as = radd(as, (j == 0) ? pE2 : wE2[j - 1]);
+        if (e <= T - 1) as = rsub(as, wE2[j]);
+        if (e == 0) as = rsub(as, lam.E3a);
+        if (e == T) as = rsub(as, lam.E3b);
+        zs[j] = rmul(k.om, as);
+      }
+    }
+    stor_solve_r<C>(k, qv, av, zp, zc, zd, zs, T, lane);
+    const float sn = __shfl_down_sync(FULLM, zs[0], 1);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int e = t0 + j;
+      if (e < T) {
+        const float snx = (j == C - 1) ? sn : zs[j + 1];
+        lam.v[SE1][j] = radd(rsub(radd(zp[j], zc[j]), zd[j]), lam.v[SE1][j]);                          // equality rows
+        lam.v[SE2][j] = radd(radd(rfma(-k.eta, zc[j], rsub(snx, zs[j])), zd[j]), lam.v[SE2][j]);
+        ineq_r(rsub(zc[j], Pm), lam.v[SCU][j], bet.v[SCU][j], bits, SCU * C + j);
+        ineq_r(-zc[j], lam.v[SCL][j], bet.v[SCL][j], bits, SCL * C + j);
+        ineq_r(rsub(zd[j], Pm), lam.v[SDU][j], bet.v[SDU][j], bits, SDU * C + j);
+        ineq_r(-zd[j], lam.v[SDL][j], bet.v[SDL][j], bits, SDL * C + j);
+      }
+      if (e <= T) {
+        if (e == 0) lam.E3a = radd(zs[j], lam.E3a);
+        if (e == T) lam.E3b = radd(zs[j], lam.E3b);
+        ineq_r(rsub(zs[j], Em), lam.v[SSU][j], bet.v[SSU][j], bits, SSU * C + j);
+        ineq_r(-zs[j], lam.v[SSL][j], bet.v[SSL][j], bits, SSL * C + j);
+      }
+    }
+    if (rec) rec[(size_t)it * 32 + lane] = bits;   // equality rows never clip: their bits stay 0
+  }
+}
+
+// the device's data from the parameters and state i-1 (x: its X)
+struct RDev {
+  int dev, h, bat, piv;
+};
+
+template <int C>
+__device__ void ramp_load(const DP &p, const St &s, const RDev &dv, int T, int lane, float (&x)[C], float (&qv)[C],
+                          float (&av)[C], float (&hU)[C], float (&hL)[C], float (&hRU)[C], float (&hRD)[C],
+                          float (&bU)[C], float (&lU)[C], float (&bL)[C], float (&lL)[C], float (&bRU)[C],
+                          float (&lRU)[C], float (&bRD)[C], float (&lRD)[C], const float *XD) {
+  const int t0 = lane * C;
+  const float *B = s.INS + dv.h, *Lm = s.INS + p.Mtot + dv.h, *Hh = p.RH + dv.h;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int t = t0 + j;
+    const bool in = t < T, rr = t < T - 1;
+    x[j] = in ? XD[(size_t)dv.dev * T + t] : 0.f;
+    qv[j] = in ? p.piv[dv.piv + t] : 1.f;
+    av[j] = in ? p.piv[dv.piv + T + t] : 0.f;
+    hU[j] = in ? Hh[t] : 0.f;
+    hL[j] = in ? Hh[T + t] : 0.f;
+    bU[j] = in ? B[t] : 0.f;
+    lU[j] = in ? Lm[t] : 0.f;
+    bL[j] = in ? B[T + t] : 0.f;
+    lL[j] = in ? Lm[T + t] : 0.f;
+    hRU[j] = rr ? Hh[2 * T + t] : 0.f;
+    hRD[j] = rr ? Hh[3 * T - 1 + t] : 0.f;
+    bRU[j] = rr ? B[2 * T + t] : 0.f;
+    lRU[j] = rr ? Lm[2 * T + t] : 0.f;
+    bRD[j] = rr ? B[3 * T - 1 + t] : 0.f;
+    lRD[j] = rr ? Lm[3 * T - 1 + t] : 0.f;
+  }
+}
+
+template <int C>
+__device__ void stor_load(const DP &p, const St &s, const RDev &dv, int T, int lane, StorK &k, float &cost,
+                          float &Pm, float &Em, float (&x)[C], float (&qv)[C], float (&av)[C], StorRows<C> &lam,
+                          StorRows<C> &bet, const float *XD) {
+  const int t0 = lane * C;
+  const float *B = s.INS + dv.h, *Lm = s.INS + p.Mtot + dv.h, *Hh = p.RH + dv.h;
+  const float *kc = p.piv + dv.piv;
+  k.rho = p.rd;
+  k.om = p.rd;
+  k.eta = p.beff[dv.bat];
+  k.rpo = radd(k.rho, k.om);
+  k.i00 = kc[0];
+  k.i01 = kc[1];
+  k.i11 = kc[2];
+  k.gc = kc[3];
+  k.gd = kc[4];
+  cost = p.scost[dv.bat];
+  Pm = Hh[2 * T + 2];      // the CU rows' right-hand side
+  Em = Hh[6 * T + 2];      // the SU rows'
+  lam.E3a = Lm[2 * T];
+  lam.E3b = Lm[2 * T + 1];
+  bet.E3a = bet.E3b = 0.f;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int e = t0 + j;
+    const bool st = e < T, ss = e <= T;
+    x[j] = st ? XD[(size_t)dv.dev * T + e] : 0.f;
+    qv[j] = ss ? kc[8 + e] : 1.f;
+    av[j] = ss ? kc[8 + (T + 1) + e] : 0.f;
+    lam.v[SE1][j] = st ? Lm[e] : 0.f;
+    lam.v[SE2][j] = st ? Lm[T + e] : 0.f;
+    lam.v[SCU][j] = st ? Lm[2 * T + 2 + e] : 0.f;
+    lam.v[SCL][j] = st ? Lm[3 * T + 2 + e] : 0.f;
+    lam.v[SDU][j] = st ? Lm[4 * T + 2 + e] : 0.f;
+    lam.v[SDL][j] = st ? Lm[5 * T + 2 + e] : 0.f;
+    lam.v[SSU][j] = ss ? Lm[6 * T + 2 + e] : 0.f;
+    lam.v[SSL][j] = ss ? Lm[7 * T + 3 + e] : 0.f;
+    bet.v[SE1][j] = bet.v[SE2][j] = 0.f;
+    bet.v[SCU][j] = st ? B[2 * T + 2 + e] : 0.f;
+    bet.v[SCL][j] = st ? B[3 * T + 2 + e] : 0.f;
+    bet.v[SDU][j] = st ? B[4 * T + 2 + e] : 0.f;
+    bet.v[SDL][j] = st ? B[5 * T + 2 + e] : 0.f;
+    bet.v[SSU][j] = ss ? B[6 * T + 2 + e] : 0.f;
+    bet.v[SSL][j] = ss ? B[7 * T + 3 + e] : 0.f;
+  }
+}
+
+template <int C>
+__device__ __forceinline__ RDev rdev(const DP &p, int w) {
+  const IDev di = p.idev[w];
+  return RDev{di.dev, di.h, di.bat, di.piv};
+}
+
+// step 2 for the inner-ADMM devices from registers, one warp per device
+template <int C>
+__global__ void __launch_bounds__(TB, 1) fwd_inner_r(DP p, St s, St nx, const float *XD, float *DEL,
+                                                     unsigned long long *grec) {
+  const int lane = threadIdx.x & 31, w = blockIdx.x * RWARPS + (threadIdx.x >> 5), T = p.T, t0 = lane * C;
+  if (w >= p.n_inner) return;
+  const RDev dv = rdev<C>(p, w);
+  unsigned long long *mask = grec ? grec + (size_t)w * RREC_WORDS : nullptr;
+  float *Bo = nx.INS + dv.h, *Lo = nx.INS + p.Mtot + dv.h;
+  float x[C], qv[C], av[C];
+  if (dv.bat < 0) {
+    float hU[C], hL[C], hRU[C], hRD[C], bU[C], lU[C], bL[C], lL[C], bRU[C], lRU[C], bRD[C], lRD[C], z[C];
+    ramp_load<C>(p, s, dv, T, lane, x, qv, av, hU, hL, hRU, hRD, bU, lU, bL, lL, bRU, lRU, bRD, lRD, XD);
+    ramp_fwd_r<C>(T, lane, p.rd, p.rd, p.gb[dv.dev], x, qv, av, hU, hL, hRU, hRD, bU, lU, bL, lL, bRU, lRU, bRD,
+                  lRD, z, mask);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int t = t0 + j;
+      if (t < T) {
+        nx.PD[(size_t)dv.dev * T + t] = z[j];
+        Bo[t] = bU[j];
+        Lo[t] = lU[j];
+        Bo[T + t] = bL[j];
+        Lo[T + t] = lL[j];
+      }
+      if (t < T - 1) {
+        Bo[2 * T + t] = bRU[j];
+        Lo[2 * T + t] = lRU[j];
+        Bo[3 * T - 1 + t] = bRD[j];
+        Lo[3 * T - 1 + t] = lRD[j];
+      }
+    }
+  } else {
+    StorK k;
+    float cost, Pm, Em, zp[C], zd[C];
+    StorRows<C> lam, bet;
+    stor_load<C>(p, s, dv, T, lane, k, cost, Pm, Em, x, qv, av, lam, bet, XD);
+    stor_fwd_r<C>(T, lane, k, cost, Pm, Em, x, qv, av, lam, bet, zp, zd, mask);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int e = t0 + j;
+      if (e < T) {
+        nx.PD[(size_t)dv.dev * T + e] = zp[j];
+        DEL[(size_t)dv.bat * T + e] = zd[j];   // discharge, for the cost
+        Bo[e] = 0.f;
+        Lo[e] = lam.v[SE1][j];
+        Bo[T + e] = 0.f;
+        Lo[T + e] = lam.v[SE2][j];
+        Bo[2 * T + 2 + e] = bet.v[SCU][j];
+        Lo[2 * T + 2 + e] = lam.v[SCU][j];
+        Bo[3 * T + 2 + e] = bet.v[SCL][j];
+        Lo[3 * T + 2 + e] = lam.v[SCL][j];
+        Bo[4 * T + 2 + e] = bet.v[SDU][j];
+        Lo[4 * T + 2 + e] = lam.v[SDU][j];
+        Bo[5 * T + 2 + e] = bet.v[SDL][j];
+        Lo[5 * T + 2 + e] = lam.v[SDL][j];
+      }
+      if (e <= T) {
+        Bo[6 * T + 2 + e] = bet.v[SSU][j];
+        Lo[6 * T + 2 + e] = lam.v[SSU][j];
+        Bo[7 * T + 3 + e] = bet.v[SSL][j];
+        Lo[7 * T + 3 + e] = lam.v[SSL][j];
+      }
+      if (e == 0) {
+        Bo[2 * T] = 0.f;
+        Lo[2 * T] = lam.E3a;
+      }
+      if (e == T) {
+        Bo[2 * T + 1] = 0.f;
+        Lo[2 * T + 1] = lam.E3b;
+      }
+    }
+  }
+}
+
+// The inner ADMM backwards from registers, one warp per device: which rows
+// clipped comes from the forward's record (gmask) or, without one, from the
+// forward iterations run again here into `scratch` (one iteration's record);
+// then the N_INNER iterations in reverse, as bwd_inner describes.
+template <int C>
+__global__ void __launch_bounds__(TB, 1) bwd_inner_r(DP p, St s, Adj a, const float *XD, const float *LPDT,
+                                                     float *LX, float *HB, int last, const unsigned long long *grec,
+                                                     unsigned long long *scratch) {
+  const int lane = threadIdx.x & 31, w = blockIdx.x * RWARPS + (threadIdx.x >> 5), T = p.T, t0 = lane * C;
+  if (w >= p.n_inner) return;
+  const RDev dv = rdev<C>(p, w);
+  const float rho = p.rd, om = p.rd;
+  float *BB = a.LINS + dv.h, *LB = a.LINS + p.Mtot + dv.h, *HBd = HB + dv.h;
+  float x[C], qv[C], av[C], xb[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) xb[j] = 0.f;
+  if (dv.bat < 0) {
+    float hU[C], hL[C], hRU[C], hRD[C], bU[C], lU[C], bL[C], lL[C], bRU[C], lRU[C], bRD[C], lRD[C];
+    ramp_load<C>(p, s, dv, T, lane, x, qv, av, hU, hL, hRU, hRD, bU, lU, bL, lL, bRU, lRU, bRD, lRD, XD);
+    const unsigned long long *mask = (grec ? grec : scratch) + (size_t)w * RREC_WORDS;
+    if (!grec) {
+      float z[C];
+      ramp_fwd_r<C>(T, lane, rho, om, p.gb[dv.dev], x, qv, av, hU, hL, hRU, hRD, bU, lU, bL, lL, bRU, lRU, bRD,
+                    lRD, z, scratch + (size_t)w * RREC_WORDS);
+    }
+    // adjoints of (beta, lambda) per row, and of the right-hand sides
+    float ab[4][C], al[4][C], ah[4][C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int t = t0 + j;
+      const bool in = t < T, rr = t < T - 1;
+      const int rows[4] = {t, T + t, 2 * T + t, 3 * T - 1 + t};
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const bool ok = g < 2 ? in : rr;
+        ab[g][j] = ok ? BB[rows[g]] : 0.f;
+        al[g][j] = ok ? LB[rows[g]] : 0.f;
+        ah[g][j] = 0.f;
+      }
+    }
+    unsigned long long mnext = mask[(size_t)(N_INNER - 1) * 32 + lane];
+    for (int it = N_INNER - 1; it >= 0; --it) {
+      const unsigned long long mk = mnext;
+      if (it > 0) mnext = mask[(size_t)(it - 1) * 32 + lane];   // in flight during this iteration
+      float sv[4][C];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const int t = t0 + j;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const bool ok = g < 2 ? t < T : t < T - 1;
+          sv[g][j] = ok ? sbar_r(mk, g * C + j, ab[g][j], al[g][j]) : 0.f;
+          ah[g][j] = rsub(ah[g][j], sv[g][j]);
+        }
+      }
+      const float pRU = __shfl_up_sync(FULLM, sv[2][C - 1], 1), pRD = __shfl_up_sync(FULLM, sv[3][C - 1], 1);
+      float rb[C];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const int t = t0 + j;
+        rb[j] = 0.f;
+        if (t < T) {
+          float acc = rsub(sv[0][j], sv[1][j]);   // A' d s
+          if (t >= 1) acc = radd(acc, rsub(j ? sv[2][j - 1] : pRU, j ? sv[3][j - 1] : pRD));
+          if (t <= T - 2) acc = rsub(acc, rsub(sv[2][j], sv[3][j]));
+          if (it == N_INNER - 1) acc = radd(acc, LPDT[(size_t)dv.dev * T + t]);   // the output p = z_p
+          rb[j] = acc;
+        }
+      }
+      tri_solve_r<C>(qv, av, rb, T, lane);
+      const float rn = __shfl_down_sync(FULLM, rb[0], 1);
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const int t = t0 + j;
+        if (t < T) {
+          xb[j] = rfma(rho, rb[j], xb[j]);
+          const float rnx = (j == C - 1) ? rn : rb[j + 1];
+          float wv[4] = {rmul(om, rb[j]), -rmul(om, rb[j]), 0.f, 0.f};
+          if (t < T - 1) {
+            wv[2] = rmul(om, rsub(rnx, rb[j]));
+            wv[3] = rmul(om, rsub(rb[j], rnx));
+          }
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            ah[g][j] = radd(ah[g][j], wv[g]);
+            ab[g][j] = wv[g];
+            al[g][j] = rsub(sv[g][j], wv[g]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int t = t0 + j;
+      if (t < T) LX[(size_t)dv.dev * T + t] = xb[j];
+      const int rows[4] = {t, T + t, 2 * T + t, 3 * T - 1 + t};
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        if (g < 2 ? t < T : t < T - 1) {
+          BB[rows[g]] = ab[g][j];
+          LB[rows[g]] = al[g][j];
+          HBd[rows[g]] += ah[g][j];
+        }
+      }
+    }
+  } else {
+    StorK k;
+    float cost, Pm, Em;
+    StorRows<C> lam, bet;
+    stor_load<C>(p, s, dv, T, lane, k, cost, Pm, Em, x, qv, av, lam, bet, XD);
+    const unsigned long long *mask = (grec ? grec : scratch) + (size_t)w * RREC_WORDS;
+    if (!grec) {
+      float zp[C], zd[C];
+      stor_fwd_r<C>(T, lane, k, cost, Pm, Em, x, qv, av, lam, bet, zp, zd, scratch + (size_t)w * RREC_WORDS);
+    }
+    const float dcost = last ? cost : 0.f;
+    // per row group: adjoints of beta (ab), lambda (al), the right-hand side (ah)
+    StorRows<C> ab, al, ah;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int e = t0 + j;
+#pragma unroll
+      for (int g = 0; g < SGROUPS; ++g) {
+        const bool ok = shas(g, e, T);
+        ab.v[g][j] = ok ? BB[srow(g, e, T)] : 0.f;
+        al.v[g][j] = ok ? LB[srow(g, e, T)] : 0.f;
+        ah.v[g][j] = 0.f;
+      }
+    }
+    ab.E3a = BB[2 * T];
+    ab.E3b = BB[2 * T + 1];
+    al.E3a = LB[2 * T];
+    al.E3b = LB[2 * T + 1];
+    ah.E3a = ah.E3b = 0.f;
+    unsigned long long mnext = mask[(size_t)(N_INNER - 1) * 32 + lane];
+    for (int it = N_INNER - 1; it >= 0; --it) {
+      const unsigned long long mk = mnext;
+      if (it > 0) mnext = mask[(size_t)(it - 1) * 32 + lane];   // in flight during this iteration
+      StorRows<C> sv;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const int e = t0 + j;
+#pragma unroll
+        for (int g = 0; g < SGROUPS; ++g) {
+          sv.v[g][j] = shas(g, e, T) ? sbar_r(mk, g * C + j, ab.v[g][j], al.v[g][j]) : 0.f;
+          ah.v[g][j] = rsub(ah.v[g][j], sv.v[g][j]);
+        }
+      }
+      sv.E3a = al.E3a;   // equality rows never clip
+      sv.E3b = al.E3b;
+      ah.E3a = rsub(ah.E3a, sv.E3a);
+      ah.E3b = rsub(ah.E3b, sv.E3b);
+      const float pE2 = __shfl_up_sync(FULLM, sv.v[SE2][C - 1], 1);
+      float zp[C], zc[C], zd[C], zs[C];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const int e = t0 + j;
+        zp[j] = zc[j] = zd[j] = zs[j] = 0.f;
+        if (e < T) {   // A' d s, and the outputs' adjoints on the last inner iterate
+          zp[j] = sv.v[SE1][j];
+          zc[j] = rsub(radd(rfma(-k.eta, sv.v[SE2][j], sv.v[SE1][j]), sv.v[SCU][j]), sv.v[SCL][j]);
+          zd[j] = rsub(radd(radd(-sv.v[SE1][j], sv.v[SE2][j]), sv.v[SDU][j]), sv.v[SDL][j]);
+          if (it == N_INNER - 1) {
+            zp[j] = radd(zp[j], LPDT[(size_t)dv.dev * T + e]);
+            zd[j] = radd(zd[j], dcost);
+          }
+        }
+        if (e <= T) {
+          float as = rsub(sv.v[SSU][j], sv.v[SSL][j]);
+          if (e >= 1) as = radd(as, (j == 0) ? pE2 : sv.v[SE2][j - 1]);
+          if (e <= T - 1) as = rsub(as, sv.v[SE2][j]);
+          if (e == 0) as = radd(as, sv.E3a);
+          if (e == T) as = radd(as, sv.E3b);
+          zs[j] = as;
+        }
+      }
+      stor_solve_r<C>(k, qv, av, zp, zc, zd, zs, T, lane);
+      const float sn = __shfl_down_sync(FULLM, zs[0], 1);
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const int e = t0 + j;
+        float wv[SGROUPS];
+#pragma unroll
+        for (int g = 0; g < SGROUPS; ++g) wv[g] = 0.f;
+        if (e < T) {
+          xb[j] = rfma(rho, zp[j], xb[j]);
+          const float snx = (j == C - 1) ? sn : zs[j + 1];
+          wv[0] = rmul(om, rsub(radd(zp[j], zc[j]), zd[j]));
+          wv[1] = rmul(om, radd(rfma(-k.eta, zc[j], rsub(snx, zs[j])), zd[j]));
+          wv[2] = rmul(om, zc[j]);
+          wv[3] = -rmul(om, zc[j]);
+          wv[4] = rmul(om, zd[j]);
+          wv[5] = -rmul(om, zd[j]);
+        }
+        if (e <= T) {
+          wv[6] = rmul(om, zs[j]);
+          wv[7] = -rmul(om, zs[j]);
+        }
+#pragma unroll
+        for (int g = 0; g < SGROUPS; ++g) {
+          if (shas(g, e, T)) {
+            ah.v[g][j] = radd(ah.v[g][j], wv[g]);
+            ab.v[g][j] = wv[g];
+            al.v[g][j] = rsub(sv.v[g][j], wv[g]);
+          }
+        }
+        if (e == 0) {
+          const float w3 = rmul(om, zs[j]);
+          ah.E3a = radd(ah.E3a, w3);
+          ab.E3a = w3;
+          al.E3a = rsub(sv.E3a, w3);
+        }
+        if (e == T) {
+          const float w3 = rmul(om, zs[j]);
+          ah.E3b = radd(ah.E3b, w3);
+          ab.E3b = w3;
+          al.E3b = rsub(sv.E3b, w3);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int e = t0 + j;
+      if (e < T) LX[(size_t)dv.dev * T + e] = xb[j];
+#pragma unroll
+      for (int g = 0; g < SGROUPS; ++g) {
+        if (shas(g, e, T)) {
+          BB[srow(g, e, T)] = ab.v[g][j];
+          LB[srow(g, e, T)] = al.v[g][j];
+          HBd[srow(g, e, T)] += ah.v[g][j];
+        }
+      }
+      if (e == 0) {
+        BB[2 * T] = ab.E3a;
+        LB[2 * T] = al.E3a;
+        HBd[2 * T] += ah.E3a;
+      }
+      if (e == T) {
+        BB[2 * T + 1] = ab.E3b;
+        LB[2 * T + 1] = al.E3b;
+        HBd[2 * T + 1] += ah.E3b;
+      }
+    }
+  }
+}
+
 // gathers at the nodes: C = d/d pbar (old), D = d/d theta_bar (old); u's adjoint
 __global__ void bwd_node2(DP p, Adj a, const float *X1, const float *X2, const float *Y1, const float *Y2,
                           const float *LX, float *C, float *Dt) {
@@ -697,6 +1403,7 @@ struct opf_diff {
   float *masks = nullptr;
   size_t masks_cap = 0;
   size_t record_limit = size_t(4) << 30;   // opf_diff_set_record_limit
+  unsigned char *mask1 = nullptr;           // one iteration's inner record, for a reverse pass without one
 };
 
 namespace {
@@ -827,6 +1534,38 @@ bool spd_inverse(const Rows &r, const std::vector<double> &qd, double omega, std
   return true;
 }
 
+// Thomas pivots of a tridiagonal matrix with diagonal d_end at both ends,
+// d_mid inside and off-diagonal off (FP64, stored as FP32), then the solve's
+// coefficients a = -off / q
+void tri_pivots(int n, double d_end, double d_mid, double off, std::vector<float> &out) {
+  std::vector<double> q(n);
+  for (int i = 0; i < n; ++i) {
+    const double d = (i == 0 || i == n - 1) ? d_end : d_mid;
+    q[i] = i == 0 ? d : d - off * off / q[i - 1];
+  }
+  for (int i = 0; i < n; ++i) out.push_back((float)q[i]);
+  for (int i = 0; i < n; ++i) out.push_back((float)(-off / q[i]));
+}
+
+// A battery's factor for the register path (omega = rho' = rd): with p
+// eliminated, the 2 x 2 block H of (c_t, delta_t) and its inverse, the
+// coupling f = (-omega eta, omega) of (c_t, delta_t) to s_{t+1} - s_t and
+// g = H^-1 f, and the tridiagonal system of s whose neighbours couple with
+// gam = omega - f'g: eight constants (i00 i01 i11 gc gd, three unused), then
+// the pivots and coefficients of the s system
+void stor_factor(int T, double rd, double eta, std::vector<float> &out) {
+  const double rho = rd, om = rd;
+  const double kap = rho * om / (rho + om);
+  const double h00 = kap + 2.0 * om + om * eta * eta, h01 = -kap - om * eta, h11 = kap + 3.0 * om;
+  const double det = h00 * h11 - h01 * h01;
+  const double i00 = h11 / det, i01 = -h01 / det, i11 = h00 / det;
+  const double fc = -om * eta, fd = om;
+  const double gc = i00 * fc + i01 * fd, gd = i01 * fc + i11 * fd;
+  const double gam = om - (fc * gc + fd * gd);
+  for (double v : {i00, i01, i11, gc, gd, 0.0, 0.0, 0.0}) out.push_back((float)v);
+  tri_pivots(T + 1, 3.0 * om + gam, 2.0 * om + 2.0 * gam, -gam, out);
+}
+
 St carve_state(const opf_diff *d, float *base) {
   const size_t KLT = (size_t)d->Kp * d->L * d->T, KNT = (size_t)d->Kp * d->N * d->T, ST = (size_t)d->S * d->T;
   St s;
@@ -850,11 +1589,21 @@ void forward_step(const opf_diff *d, const St &s, const St &nx, float *XD, float
                   unsigned char *mask = nullptr) {
   const DP &p = d->p;
   const long long nl = (long long)p.Kp * p.L * p.T, nn = (long long)p.Kp * p.N * p.T, ns = (long long)p.S * p.T;
-  unsigned char *lmask = mask ? mask + (size_t)N_INNER * p.Mtot : nullptr;
+  unsigned char *lmask = mask ? mask + inner_record_bytes(p) : nullptr;
   unsigned char *dmask = mask ? lmask + nl : nullptr;
+  unsigned long long *rrec = reinterpret_cast<unsigned long long *>(mask);
   fwd_line<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx, lmask);
   fwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, nx, XD, dmask);
-  if (p.n_inner) fwd_inner<<<p.n_inner, TBI, d->smem_fwd, d->stream>>>(p, s, nx, XD, DEL, d->stage, mask);
+  if (p.n_inner) {
+    const int g = (p.n_inner + RWARPS - 1) / RWARPS;
+    switch (p.reg_c) {
+      case 1: fwd_inner_r<1><<<g, TB, 0, d->stream>>>(p, s, nx, XD, DEL, rrec); break;
+      case 2: fwd_inner_r<2><<<g, TB, 0, d->stream>>>(p, s, nx, XD, DEL, rrec); break;
+      case 3: fwd_inner_r<3><<<g, TB, 0, d->stream>>>(p, s, nx, XD, DEL, rrec); break;
+      case 4: fwd_inner_r<4><<<g, TB, 0, d->stream>>>(p, s, nx, XD, DEL, rrec); break;
+      default: fwd_inner<<<p.n_inner, TBI, d->smem_fwd, d->stream>>>(p, s, nx, XD, DEL, d->stage, mask); break;
+    }
+  }
   fwd_avg<<<grid_for(nn), TB, 0, d->stream>>>(p, nx);
   fwd_upd_nodes<<<grid_for(nn), TB, 0, d->stream>>>(p, s, nx);
   fwd_upd_lines<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx);
@@ -1006,6 +1755,7 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
     shapes.push_back(s);
     return (int)shapes.size() - 1;
   };
+  std::vector<float> piv;   // the register path's factors (DP::piv)
   bool ok = true;
   int hoff = 0;
   if (T > 1 && net->gen_ramp) {
@@ -1023,6 +1773,9 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
       di.bat = -1;
       std::vector<double> qd(T, 2.0 * net->gen_a[g] + rd);   // 2 a + rho' on every step (all are power)
       ok = spd_inverse(rr, qd, rd, minv);
+      // the register path's factor: M = (qd + 2 omega) I + 2 omega D'D
+      di.piv = (int)piv.size();
+      tri_pivots(T, qd[0] + 4.0 * rd, qd[0] + 6.0 * rd, -2.0 * rd, piv);
       for (int t = 0; t < T; ++t) qv.push_back((float)net->gen_b[g]);
       hoff += rr.m;
       kind[g] = 1;
@@ -1046,6 +1799,8 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
         it = by_eff.emplace(eff, std::make_pair(sh, mo)).first;
       }
       IDev di{};
+      di.piv = (int)piv.size();
+      stor_factor(T, rd, eff, piv);
       di.dev = G + D + bt;
       di.shape = it->second.first;
       di.minv = it->second.second;
@@ -1138,6 +1893,13 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   U(&p.aeq, aeq);
   U(&p.minv, minv);
   U(&p.Q, qv);
+  U(&p.piv, piv);
+  {
+    std::vector<float> be(B);
+    for (int bt = 0; bt < B; ++bt) be[bt] = (float)net->stor_eff[bt];
+    U(&p.beff, be);
+  }
+  p.reg_c = T <= DREG_T ? (T + 32) / 32 : 0;   // chunk of T + 1 elements over 32 lanes
   U(&p.scost, d->scost);
   std::vector<float> hu(H);
   for (int h = 0; h < H; ++h) hu[h] = (float)net->hvdc_u[h];
@@ -1148,6 +1910,7 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   U(&p.lu, d->lu);
   if (e == cudaSuccess) e = dalloc(d->allocs, &d->RH, (size_t)d->Mtot);
   p.RH = d->RH;
+  if (e == cudaSuccess) e = dalloc(d->allocs, &d->mask1, inner_record_bytes(p));
   if (e == cudaSuccess && d->Mtot) {
     // right-hand sides of the inner rows; a call rewrites the capacity rows
     // of the ramp-limited generators from its capacity data (set_ramp_rhs)
@@ -1223,7 +1986,7 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   // and closed-form device's unclipped value lay, so that the reverse pass
   // need not run each iteration's inner ADMM again nor recompute the prox
   // inputs (while the record stays within the context's limit)
-  const size_t mask_iter = (size_t)N_INNER * MT + KLT + ST;
+  const size_t mask_iter = (inner_record_bytes(p) + KLT + ST + 255) & ~size_t(255);
   const bool rec = grads && (size_t)K * mask_iter <= d->record_limit;
   if (e == cudaSuccess && rec) e = ensure(&d->masks, &d->masks_cap, ((size_t)K * mask_iter + 3) / 4);
   if (e != cudaSuccess)
@@ -1293,12 +2056,23 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
       const St s = sgst(i - 1 - lo);   // state i - 1
       bwd_node1<<<grid_for(nn), TB, 0, d->stream>>>(p, a, A, Bn);
       unsigned char *mi = mask_of(i);
-      const unsigned char *lmask = mi ? mi + (size_t)N_INNER * MT : nullptr, *dmask = mi ? lmask + KLT : nullptr;
+      const unsigned char *lmask = mi ? mi + inner_record_bytes(p) : nullptr, *dmask = mi ? lmask + KLT : nullptr;
       bwd_line1<<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, Bn, X1, X2, Y1, Y2, GU, lmask);
       bwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT, dmask);
-      if (p.n_inner)
-        bwd_inner<<<p.n_inner, TBI, d->smem_bwd, d->stream>>>(p, s, a, XD, LPDT, LX, HB, i == K ? 1 : 0,
-                                                             d->stage, mi);
+      if (p.n_inner) {
+        const int g = (p.n_inner + RWARPS - 1) / RWARPS, lst = i == K ? 1 : 0;
+        unsigned long long *m1 = reinterpret_cast<unsigned long long *>(d->mask1);
+        const unsigned long long *rr = reinterpret_cast<const unsigned long long *>(mi);
+        switch (p.reg_c) {
+          case 1: bwd_inner_r<1><<<g, TB, 0, d->stream>>>(p, s, a, XD, LPDT, LX, HB, lst, rr, m1); break;
+          case 2: bwd_inner_r<2><<<g, TB, 0, d->stream>>>(p, s, a, XD, LPDT, LX, HB, lst, rr, m1); break;
+          case 3: bwd_inner_r<3><<<g, TB, 0, d->stream>>>(p, s, a, XD, LPDT, LX, HB, lst, rr, m1); break;
+          case 4: bwd_inner_r<4><<<g, TB, 0, d->stream>>>(p, s, a, XD, LPDT, LX, HB, lst, rr, m1); break;
+          default:
+            bwd_inner<<<p.n_inner, TBI, d->smem_bwd, d->stream>>>(p, s, a, XD, LPDT, LX, HB, lst, d->stage, mi);
+            break;
+        }
+      }
       bwd_node2<<<grid_for(nn), TB, 0, d->stream>>>(p, a, X1, X2, Y1, Y2, LX, Cn, Dn);
       bwd_line2<<<grid_for(nl), TB, 0, d->stream>>>(p, a, Cn, Dn);
       bwd_dev2<<<grid_for(ns), TB, 0, d->stream>>>(p, a, LX, Cn);

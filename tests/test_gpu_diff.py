@@ -142,6 +142,15 @@ def test_inner_admm_devices_match_autograd():
     _check(case, 30, ckpt=4)                       # T = 1: batteries only
 
 
+@pytest.mark.parametrize("T", [31, 32, 70, 127, 130])
+def test_inner_admm_horizons_match_autograd(T):
+    """The inner ADMM from registers at one to four steps per lane (the chunk
+    boundaries of T + 1 = 32, 33 and 128 states of charge), and beyond 127
+    steps through the shared-memory path with the system's inverse."""
+    case = make_case(scale_case(12, T, 1, seed=40 + T, ramp=True, stor_per_node=0.3, fixed_frac=0.3))
+    _check(case, 15, ckpt=4)
+
+
 def test_hvdc_links_match_autograd():
     case = make_case(scale_case(40, 6, 2, seed=7, ramp=True, stor_per_node=0.1, fixed_frac=0.3, n_hvdc=2))
     _check(case, 40, ckpt=9)
