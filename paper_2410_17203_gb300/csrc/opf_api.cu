@@ -717,6 +717,7 @@ opf_status create_impl(const opf_network *net, int32_t T, const opf_contingencie
   p.n_hvdc = c->H;
   p.hvdc0 = G + D + c->B;
   p.node_grid = c->plan.node_grid;
+  p.dsum_lean = c->plan.dsum_lean;
   p.eps = opt.eps;
   p.mu = opt.mu;
   p.gamma = opt.gamma;
@@ -778,7 +779,7 @@ opf_status create_impl(const opf_network *net, int32_t T, const opf_contingencie
       for (int j = lptr[n], q = 0; j < lptr[n + 1] && q < 4; ++j, ++q) code[q] = lcsr[j].x;
       rec[3 * n] = make_int4(fbits(cnt_p[n]), fbits(cnt_th[n]), fbits(rcnt_p[n]), fbits(rcnt_th[n]));
       rec[3 * n + 1] = make_int4(code[0], code[1], code[2], code[3]);
-      rec[3 * n + 2] = make_int4(tptr[n], tptr[n + 1], dptr[n + 1] - dptr[n], 0);
+      rec[3 * n + 2] = make_int4(tptr[n], tptr[n + 1], dptr[n + 1] - dptr[n], dptr[n]);
     }
     up(p.nrec, rec);
   }

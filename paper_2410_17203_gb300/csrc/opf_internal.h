@@ -91,7 +91,7 @@ struct Params {
   const float *rcnt_p, *rcnt_th;   // their reciprocals (0 for a node without line terminals)
   // per node, 3 int4: (cnt_p, cnt_th, rcnt_p, rcnt_th as float bits), the first
   // four line-terminal codes 2*l + end (-1 = none), (tcode begin, end of the
-  // rest, device count, 0)
+  // rest, device count, first of the node's entries in dcsr_idx)
   const int4 *nrec;
   const int *tcode;                // line-terminal codes beyond the first four per node,
                                    // each node's list padded to a multiple of 4 with -1
@@ -123,6 +123,7 @@ struct Params {
   // scratch
   double *partials;  // [node_grid][NSLOT] per-CTA residual partial sums of the node kernel
   int node_grid;     // CTAs of the node kernel (partial-sum slots)
+  int dsum_lean;     // IterPlan::dsum_lean
   DevScalars *sc;
   // options
   double eps, mu, gamma, tol;
@@ -163,6 +164,8 @@ struct IterPlan {
   int n_slabs, slab_k;  // contingency slabs of the line / node kernels, slab_k contingencies each
   size_t inner_smem;
   int inner_c;     // register chunk of the inner-ADMM kernel (0: shared-memory path)
+  int dsum_lean;   // 1: the passes without residuals sum device powers themselves (dsum only where
+                   // residuals are formed); for instances whose device chain the line pass cannot hide
 };
 
 // A batch of instances: the CTA schedules of each batch kernel, concatenated

@@ -1011,7 +1011,9 @@ __device__ __forceinline__ void line_item(const Params &p, int old, int nw, int 
 // res = 0: the iteration's residuals are not read, so the node sums skip the
 // inputs only they need (old p and theta_bar rows, the device Welford state)
 // and their accumulation; the relaxed variant always needs the mean change.
-template <int VW, bool RELAX, int NB = 4>
+// ILD: where the pass forms no residuals, whether it sums the device powers
+// itself (0 never, 1 always, 2 as Params::dsum_lean says)
+template <int VW, bool RELAX, int NB = 4, int ILD = 2>
 __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int k, int n, int toff, float fsu,
                                           float *acc, bool res) {
   const int T = p.T;
@@ -1025,8 +1027,20 @@ __device__ __forceinline__ void node_item(const Params &p, int old, int nw, int 
   FV<VW> go;
   if (res) go = ldv_cs<VW>(p.THBAR[old] + on);
   // device terminals first: the sum and the Welford state after them, the
-  // same in every contingency
-  FV<VW> sp = ldv<VW>(p.DSP + os), st;
+  // same in every contingency -- from dsum_kernel, or (dsum_lean, where no
+  // residuals are formed) summed here over the node's devices in its order
+  FV<VW> sp, st;
+  if (res || ILD == 0 || (ILD == 2 && !p.dsum_lean)) {
+    sp = ldv<VW>(p.DSP + os);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VW; ++e) sp.v[e] = 0.f;
+    for (int j = r2.w; j < r2.w + r2.z; ++j) {
+      const FV<VW> pd = ldv<VW>(p.PD + (size_t)p.dcsr_idx[j] * T + toff);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) sp.v[e] += pd.v[e];
+    }
+  }
   Welf<VW> wdp, wth;
   Welf2<VW> wrx;   // RELAX: (Theta_new, Theta_new - Theta_old) over the line terminals
   if constexpr (RELAX) wrx.reset();
@@ -1312,12 +1326,16 @@ __device__ __forceinline__ void inner_body(const Params &p, unsigned bid, unsign
 // ---------------------------------------------------------------------------
 // dsum: per (node, VW time steps), the sum of the node's device powers and
 // the Welford state of their changes, in device order (the node sums of
-// every contingency start from it)
+// every contingency start from it), on the iterations that form residuals
+// (and every iteration of the over-relaxed form)
 // ---------------------------------------------------------------------------
 template <int VW>
 __device__ __forceinline__ void dsum_body(const Params &p, unsigned bid, unsigned nblk) {
   const Iter q = iter_scalars(p);
   if (q.skip) return;
+  // with dsum_lean the node passes that form no residuals sum the device
+  // powers themselves
+  if (p.dsum_lean && !q.res && p.alpha == 1.f) return;
   const int T = p.T, TV = T / VW;
   const unsigned n_items = (unsigned)p.N * (unsigned)TV;
   for (unsigned item = bid * BLOCK + threadIdx.x; item < n_items; item += nblk * BLOCK) {
@@ -1375,7 +1393,7 @@ __device__ __forceinline__ void line_body(const Params &p, int k0, int k1, unsig
 // LEAN: the variant for iterations that form no residuals (it returns at
 // once on the others); the general variant returns at once on those when a
 // lean launch covers them.
-template <int VW, bool RELAX, bool LEAN = false>
+template <int VW, bool RELAX, bool LEAN = false, int ILD = 2>
 __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int first, unsigned bid,
                                           unsigned nblk, bool lean_split = false) {
   __shared__ double red[WARPS][NSLOT];
@@ -1399,7 +1417,7 @@ __device__ __forceinline__ void node_body(const Params &p, int k0, int k1, int f
   ix.set(item, KK, TV);
   dx.set(stride, KK, TV);
   for (; item < n; item += stride, ix.step(dx, KK, TV))
-    node_item<VW, RELAX, LEAN ? NODE_LEAN_NB : 4>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.fsu, acc,
+    node_item<VW, RELAX, LEAN ? NODE_LEAN_NB : 4, ILD>(p, q.old, q.nw, k0 + ix.b, ix.a, ix.c * VW, q.fsu, acc,
                                                   LEAN ? false : q.res != 0);
   if constexpr (!LEAN) {
     if (!q.res) return;   // nothing reads this iteration's partial sums
@@ -1586,8 +1604,10 @@ __global__ void __launch_bounds__(BLOCK, RELAX ? 1 : NODE_MIN_CTAS) node_kernel(
 }
 
 // the residual-free node pass: fewer live values, more CTAs per SM
+// ILD: the plan's dsum_lean, fixed at compile time for this pass
+template <int ILD>
 __global__ void __launch_bounds__(BLOCK, NODE_LEAN_CTAS) node_kernel_lean(Params p, int k0, int k1, int first) {
-  node_body<NODE_VW, false, true>(p, k0, k1, first, blockIdx.x, gridDim.x);
+  node_body<NODE_VW, false, true, ILD>(p, k0, k1, first, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(BLOCK) decide_kernel(Params p, int n_part) { decide_body(p, n_part); }
@@ -1971,7 +1991,7 @@ int opfk_plan(const Params &p, IterPlan *plan) {
     return -1;
   const bool vn = (p.T % NODE_VW == 0);
   const int gn = vn ? resident_grid(node_kernel<NODE_VW, false>, 0) : resident_grid(node_kernel<1, false>, 0);
-  const int gl = vn ? resident_grid(node_kernel_lean, 0) : 0;
+  const int gl = vn ? resident_grid(node_kernel_lean<0>, 0) : 0;
   const int gx = v4 ? resident_grid(xs_kernel<4>, 0) : resident_grid(xs_kernel<1>, 0);
   const int gd = v2 ? resident_grid(dsum_kernel<2>, 0) : resident_grid(dsum_kernel<1>, 0);
   if (gn < 1 || gx < 1 || gd < 1) return -1;
@@ -2006,9 +2026,16 @@ int opfk_plan(const Params &p, IterPlan *plan) {
     // memory: one CTA on every other SM while its rounds fit in 70 % of it
     // (0.741 -> 0.706 at the same size).
     const double line_us = (double)p.Kp * p.L * p.T * 32.0 / 6.5e6;
+    plan->dsum_lean = 0;
     if (ic) {
       const int max_rounds = (int)std::floor(0.5 * line_us / (0.13 * p.T));
       if (max_rounds >= 2) plan->inner_grid = (plan->inner_grid + max_rounds - 1) / max_rounds;
+      // a line pass too short to hide the device chain (xs, inner, dsum):
+      // shorten the chain by summing device powers in the node passes that
+      // form no residuals (2k buses, T = 24: 35.5 -> 34.0 us per iteration;
+      // at 10k, where the chain is hidden, the extra loads of the node pass
+      // cost more than dsum: 0.697 -> 0.701 ms)
+      else plan->dsum_lean = 1;
     } else {
       int dev = 0, sms = 0;
       if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -2069,7 +2096,8 @@ static int iteration_enqueue(const Params &p, const IterPlan &plan, void *main_s
       // one of the two returns at once: the general pass forms residuals,
       // the lean one runs the iterations that need none
       node_kernel<NODE_VW, false><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
-      node_kernel_lean<<<plan.lean_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
+      if (p.dsum_lean) node_kernel_lean<1><<<plan.lean_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
+      else node_kernel_lean<0><<<plan.lean_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
     }
     else if (!rx) node_kernel<1, false><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
     else if (vn) node_kernel<NODE_VW, true><<<plan.node_grid, BLOCK, 0, sm>>>(p, k0, k1, s == 0);
