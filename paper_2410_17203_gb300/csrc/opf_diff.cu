@@ -886,7 +886,7 @@ __device__ void ramp_load(const DP &p, const St &s, const RDev &dv, int T, int l
   for (int j = 0; j < C; ++j) {
     const int t = t0 + j;
     const bool in = t < T, rr = t < T - 1;
-    x[j] = in ? XD[(size_t)dv.dev * T + t] : 0.f;
+    x[j] = (in && XD) ? XD[(size_t)dv.dev * T + t] : 0.f;
     qv[j] = in ? p.piv[dv.piv + t] : 1.f;
     av[j] = in ? p.piv[dv.piv + T + t] : 0.f;
     hU[j] = in ? Hh[t] : 0.f;
@@ -930,7 +930,7 @@ __device__ void stor_load(const DP &p, const St &s, const RDev &dv, int T, int l
   for (int j = 0; j < C; ++j) {
     const int e = t0 + j;
     const bool st = e < T, ss = e <= T;
-    x[j] = st ? XD[(size_t)dv.dev * T + e] : 0.f;
+    x[j] = (st && XD) ? XD[(size_t)dv.dev * T + e] : 0.f;
     qv[j] = ss ? kc[8 + e] : 1.f;
     av[j] = ss ? kc[8 + (T + 1) + e] : 0.f;
     lam.v[SE1][j] = st ? Lm[e] : 0.f;
@@ -951,7 +951,6 @@ __device__ void stor_load(const DP &p, const St &s, const RDev &dv, int T, int l
   }
 }
 
-template <int C>
 __device__ __forceinline__ RDev rdev(const DP &p, int w) {
   const IDev di = p.idev[w];
   return RDev{di.dev, di.h, di.bat, di.piv};
@@ -963,7 +962,7 @@ __global__ void __launch_bounds__(TB, 1) fwd_inner_r(DP p, St s, St nx, const fl
                                                      unsigned long long *grec) {
   const int lane = threadIdx.x & 31, w = blockIdx.x * RWARPS + (threadIdx.x >> 5), T = p.T, t0 = lane * C;
   if (w >= p.n_inner) return;
-  const RDev dv = rdev<C>(p, w);
+  const RDev dv = rdev(p, w);
   unsigned long long *mask = grec ? grec + (size_t)w * RREC_WORDS : nullptr;
   float *Bo = nx.INS + dv.h, *Lo = nx.INS + p.Mtot + dv.h;
   float x[C], qv[C], av[C];
@@ -1042,7 +1041,7 @@ __global__ void __launch_bounds__(TB, 1) bwd_inner_r(DP p, St s, Adj a, const fl
                                                      unsigned long long *scratch) {
   const int lane = threadIdx.x & 31, w = blockIdx.x * RWARPS + (threadIdx.x >> 5), T = p.T, t0 = lane * C;
   if (w >= p.n_inner) return;
-  const RDev dv = rdev<C>(p, w);
+  const RDev dv = rdev(p, w);
   const float rho = p.rd, om = p.rd;
   float *BB = a.LINS + dv.h, *LB = a.LINS + p.Mtot + dv.h, *HBd = HB + dv.h;
   float x[C], qv[C], av[C], xb[C];
@@ -1050,7 +1049,9 @@ __global__ void __launch_bounds__(TB, 1) bwd_inner_r(DP p, St s, Adj a, const fl
   for (int j = 0; j < C; ++j) xb[j] = 0.f;
   if (dv.bat < 0) {
     float hU[C], hL[C], hRU[C], hRD[C], bU[C], lU[C], bL[C], lL[C], bRU[C], lRU[C], bRD[C], lRD[C];
-    ramp_load<C>(p, s, dv, T, lane, x, qv, av, hU, hL, hRU, hRD, bU, lU, bL, lL, bRU, lRU, bRD, lRD, XD);
+    // X (and the state) only to run the forward iterations again
+    ramp_load<C>(p, s, dv, T, lane, x, qv, av, hU, hL, hRU, hRD, bU, lU, bL, lL, bRU, lRU, bRD, lRD,
+                 grec ? nullptr : XD);
     const unsigned long long *mask = (grec ? grec : scratch) + (size_t)w * RREC_WORDS;
     if (!grec) {
       float z[C];
@@ -1141,7 +1142,7 @@ __global__ void __launch_bounds__(TB, 1) bwd_inner_r(DP p, St s, Adj a, const fl
     StorK k;
     float cost, Pm, Em;
     StorRows<C> lam, bet;
-    stor_load<C>(p, s, dv, T, lane, k, cost, Pm, Em, x, qv, av, lam, bet, XD);
+    stor_load<C>(p, s, dv, T, lane, k, cost, Pm, Em, x, qv, av, lam, bet, grec ? nullptr : XD);
     const unsigned long long *mask = (grec ? grec : scratch) + (size_t)w * RREC_WORDS;
     if (!grec) {
       float zp[C], zd[C];
