@@ -404,9 +404,9 @@ def batched_vs_plain(stream, args):
     cycles has its penalties fixed and goes on; one that stops falling at
     fixed penalties stops with OPF_ESTALLED."""
     import torch
-    from paper_2410_17203_gb300 import (BATCH_LAYOUTS, opf_batch_autotune, opf_batch_create, opf_batch_destroy,
-                                        opf_batch_iterate, opf_batch_stopped, opf_create, opf_destroy,
-                                        opf_get_info, opf_iterate, opf_reset)
+    from paper_2410_17203_gb300 import (BATCH_LAYOUTS, opf_batch_autotune, opf_batch_compact, opf_batch_create,
+                                        opf_batch_destroy, opf_batch_iterate, opf_batch_stopped, opf_create,
+                                        opf_destroy, opf_get_info, opf_iterate, opf_reset)
     cases = batch_instances(args.batched)
     opts = dict(adapt_every=10, eps=1e-4, stall_window=args.stall_window)
     chunk = args.ttt_chunk
@@ -436,12 +436,16 @@ def batched_vs_plain(stream, args):
     t0 = time.perf_counter()
     choice, layout_ms = opf_batch_autotune(b, steps=20)    # from the zero state, which it restores
     t_tune = time.perf_counter() - t0
-    done = 0
+    done, sched, n_compact = 0, len(batch), 0
     while done < args.ttt_max:
         opf_batch_iterate(b, chunk)
         done += chunk
-        if sum(opf_batch_stopped(b)) == len(batch):
+        stopped = sum(opf_batch_stopped(b))
+        if stopped == len(batch):
             break
+        if len(batch) - stopped <= 0.75 * sched:        # schedule the running instances only
+            sched = opf_batch_compact(b)
+            n_compact += 1
     t_batch = time.perf_counter() - t0
     infos = [opf_get_info(h) for h in batch]
     its_batch = [int(i["iterations"]) for i in infos]
@@ -457,6 +461,7 @@ def batched_vs_plain(stream, args):
             "converged_after_fixing_penalties": n_frozen_conv,
             "iterations_total": int(sum(its_plain)),
             "iterations_equal": its_plain == its_batch,
+            "compactions": n_compact,
             "autotune": {"seconds": t_tune, "chosen": BATCH_LAYOUTS[choice],
                          "ms_per_batch_iteration": dict(zip(BATCH_LAYOUTS, layout_ms))},
             "workload": "buses log-uniform [100, 5000], T in {1, 24, 48}, K in 0..20, seed 3"}
@@ -466,17 +471,20 @@ def batch_solve(handles, args):
     """Iterate a batch of contexts until every instance has stopped
     (converged, stalled) or the iteration cap; returns (iterations per
     instance, converged flags, seconds including the autotuner)."""
-    from paper_2410_17203_gb300 import (opf_batch_autotune, opf_batch_create, opf_batch_destroy,
-                                        opf_batch_iterate, opf_batch_stopped, opf_get_info)
+    from paper_2410_17203_gb300 import (opf_batch_autotune, opf_batch_compact, opf_batch_create,
+                                        opf_batch_destroy, opf_batch_iterate, opf_batch_stopped, opf_get_info)
     b = opf_batch_create(handles)
     t0 = time.perf_counter()
     opf_batch_autotune(b, steps=20)
-    done = 0
+    done, sched = 0, len(handles)
     while done < args.ttt_max:
         opf_batch_iterate(b, args.ttt_chunk)
         done += args.ttt_chunk
-        if sum(opf_batch_stopped(b)) == len(handles):
+        stopped = sum(opf_batch_stopped(b))
+        if stopped == len(handles):
             break
+        if len(handles) - stopped <= 0.75 * sched:      # schedule the running instances only
+            sched = opf_batch_compact(b)
     dt = time.perf_counter() - t0
     its = [int(opf_get_info(h)["iterations"]) for h in handles]
     conv = [bool(opf_get_info(h)["converged"]) for h in handles]

@@ -366,6 +366,18 @@ void opf_batch_destroy(opf_batch *batch);
 #define OPF_BATCH_LAYOUTS 6
 opf_status opf_batch_autotune(opf_batch *batch, int32_t steps, int32_t *choice, double *ms_each);
 
+/* Drop the batch's stopped instances (converged, stalled, error) from its
+ * schedule, so that later steps launch CTAs for the running ones only (a
+ * batch's last steps often run one or two instances while the stopped ones'
+ * CTAs would still be scheduled).  The layout in force keeps its order and
+ * CTA split, restricted to the running instances, so iterates do not change,
+ * not even the residuals' last bits; counts and queries still cover every
+ * instance, and an instance once dropped is not iterated again by this batch.
+ * n_scheduled (may be NULL) receives the number of instances still
+ * scheduled.  Synchronizes; a later opf_batch_autotune schedules every
+ * instance again. */
+opf_status opf_batch_compact(opf_batch *batch, int32_t *n_scheduled);
+
 /* Export / import the full state (warm start, checkpoint and resume,
  * Section 3.4).  Import recomputes the node averages from p and theta and
  * projects v onto v_bar = 0 per node (Appendix C); it clears a sticky

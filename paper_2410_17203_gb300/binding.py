@@ -89,7 +89,7 @@ EXPORTS = ["opf_default_options", "opf_create", "opf_create_slice", "opf_slice_e
            "opf_destroy", "opf_status_str", "opf_last_error", "opf_abi_version",
            "opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_stopped",
            "opf_batch_destroy",
-           "opf_batch_autotune",
+           "opf_batch_autotune", "opf_batch_compact",
            "opf_wsnet_param_count", "opf_wsnet_create", "opf_wsnet_get_params", "opf_wsnet_set_params",
            "opf_wsnet_forward", "opf_wsnet_gradient", "opf_wsnet_train_step", "opf_wsnet_destroy",
            "opf_diff_create", "opf_diff_cost_grad", "opf_diff_cost_grad_on", "opf_diff_set_record_limit",
@@ -149,8 +149,9 @@ def load_library(path=None):
     lib.opf_batch_destroy.argtypes = [C.c_void_p]
     lib.opf_batch_destroy.restype = None
     lib.opf_batch_autotune.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), F64P]
+    lib.opf_batch_compact.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
     for name in ("opf_batch_create", "opf_batch_iterate", "opf_batch_converged", "opf_batch_stopped",
-                 "opf_batch_autotune"):
+                 "opf_batch_autotune", "opf_batch_compact"):
         getattr(lib, name).restype = C.c_int
     lib.opf_wsnet_param_count.argtypes = [C.c_int32]
     lib.opf_wsnet_param_count.restype = C.c_int64
@@ -498,6 +499,14 @@ def opf_batch_autotune(b, steps=20):
     ms = (C.c_double * len(BATCH_LAYOUTS))()
     _check(load_library().opf_batch_autotune(b, int(steps), C.byref(choice), ms), "opf_batch_autotune")
     return choice.value, list(ms)
+
+
+def opf_batch_compact(b):
+    """Drop the stopped instances from the batch's schedule (the iterates do
+    not change); returns how many instances it still schedules."""
+    n = C.c_int32(0)
+    _check(load_library().opf_batch_compact(b, C.byref(n)), "opf_batch_compact")
+    return n.value
 
 
 def opf_batch_converged(b):

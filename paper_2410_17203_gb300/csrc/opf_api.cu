@@ -1135,6 +1135,11 @@ struct opf_batch {
   opfk::BatchPlan plan{};
   long long sched_cap = 0;    // schedule entries d_sched holds (the longest layout)
   cudaGraphExec_t g_one = nullptr, g_many = nullptr;
+  // the layout in force (opf_batch_autotune) and how many instances it
+  // schedules (all, or those still running after opf_batch_compact)
+  std::vector<int> lay_order;  // instance order; empty: as given
+  int lay_interleave = 0, lay_div = 1;
+  int n_sched = 0;
 };
 
 namespace {
@@ -1169,9 +1174,10 @@ opf_status build_batch_graph(opf_batch *b, int iters, cudaGraphExec_t *out) {
   return OPF_OK;
 }
 
-// Build the schedule of layout `lay` into d_sched and drop the graphs of the
+// Build the schedule of the n_sched instances that `lay` lists (lay.order;
+// NULL: every instance as given) into d_sched and drop the graphs of the
 // previous one (rebuilt on the next iteration).  Waits for the batch stream.
-opf_status set_batch_layout(opf_batch *b, const opfk::BatchLayout &lay) {
+opf_status schedule_batch(opf_batch *b, int n_sched, const opfk::BatchLayout &lay) {
   const int n = (int)b->ctx.size();
   std::vector<Params> hp(n);
   std::vector<opfk::IterPlan> plans(n);
@@ -1181,10 +1187,10 @@ opf_status set_batch_layout(opf_batch *b, const opfk::BatchLayout &lay) {
   }
   long long len = 0;
   opfk::BatchPlan bp{};
-  if (opfk_batch_plan(hp.data(), plans.data(), n, lay, nullptr, 0, &len, &bp) != 0 || len > b->sched_cap)
+  if (opfk_batch_plan(hp.data(), plans.data(), n_sched, lay, nullptr, 0, &len, &bp) != 0 || len > b->sched_cap)
     return fail(OPF_ECUDA, "batch schedule");
   std::vector<int> sched(4 * (size_t)std::max(len, 1LL));
-  if (opfk_batch_plan(hp.data(), plans.data(), n, lay, sched.data(), len, &len, &bp) != 0)
+  if (opfk_batch_plan(hp.data(), plans.data(), n_sched, lay, sched.data(), len, &len, &bp) != 0)
     return fail(OPF_ECUDA, "batch schedule");
   CK(cudaStreamSynchronize(b->stream));
   if (b->g_one) cudaGraphExecDestroy(b->g_one);
@@ -1195,7 +1201,18 @@ opf_status set_batch_layout(opf_batch *b, const opfk::BatchLayout &lay) {
   for (int i = 0; i < n; ++i) hp[i].node_grid = opfk_batch_node_blocks(plans[i], lay.div);
   CK(cudaMemcpy(b->d_params, hp.data(), n * sizeof(Params), cudaMemcpyHostToDevice));
   b->plan = bp;
+  b->n_sched = n_sched;
   return OPF_OK;
+}
+
+// Apply layout `lay` to every instance and keep it for opf_batch_compact.
+opf_status set_batch_layout(opf_batch *b, const opfk::BatchLayout &lay) {
+  const int n = (int)b->ctx.size();
+  if (lay.order) b->lay_order.assign(lay.order, lay.order + n);
+  else b->lay_order.clear();
+  b->lay_interleave = lay.interleave;
+  b->lay_div = lay.div;
+  return schedule_batch(b, n, lay);
 }
 
 opf_status ensure_batch_graphs(opf_batch *b) {
@@ -1253,6 +1270,7 @@ opf_status opf_batch_create(opf_ctx *const *ctxs, int32_t n, opf_batch **out) {
   if (st == OPF_OK && opfk_batch_plan(hp.data(), plans.data(), n, lay, sched.data(), len, &len, &b->plan) != 0)
     st = fail(OPF_ECUDA, "batch schedule");
   b->sched_cap = len;
+  b->n_sched = n;
   int lo = 0, hi = 0;
   cudaError_t e = st == OPF_OK ? cudaDeviceGetStreamPriorityRange(&lo, &hi) : cudaSuccess;
   if (st == OPF_OK) {
@@ -1404,6 +1422,33 @@ opf_status opf_batch_stopped(opf_batch *b, int32_t *n_converged, int32_t *n_stal
   if (n_converged) *n_converged = nc;
   if (n_stalled) *n_stalled = ns;
   if (n_error) *n_error = ne;
+  return OPF_OK;
+}
+
+opf_status opf_batch_compact(opf_batch *b, int32_t *n_scheduled) {
+  if (!b) return fail(OPF_EINVAL, "batch is NULL");
+  // which instances still run, after the work queued so far
+  CK(cudaStreamSynchronize(b->stream));
+  const int n = (int)b->ctx.size();
+  std::vector<char> run(n, 0);
+  for (int i = 0; i < n; ++i) {
+    DevScalars sc;
+    CK(cudaMemcpy(&sc, b->ctx[i]->P.sc, sizeof(sc), cudaMemcpyDeviceToHost));
+    if (sc.status) b->ctx[i]->host_status = sc.status;
+    run[i] = (sc.stop == 0 && sc.status == 0) ? 1 : 0;
+  }
+  // the layout in force, restricted to them (the same order and CTA split)
+  std::vector<int> order;
+  for (int j = 0; j < n; ++j) {
+    const int i = b->lay_order.empty() ? j : b->lay_order[j];
+    if (run[i]) order.push_back(i);
+  }
+  if ((int)order.size() != b->n_sched) {
+    const opfk::BatchLayout lay{order.data(), b->lay_interleave, b->lay_div};
+    const opf_status st = schedule_batch(b, (int)order.size(), lay);
+    if (st != OPF_OK) return st;
+  }
+  if (n_scheduled) *n_scheduled = (int32_t)order.size();
   return OPF_OK;
 }
 

@@ -81,6 +81,46 @@ def test_mixed_horizons_equal_single_instance_iterates():
             s.close()
 
 
+def test_compaction_keeps_iterates_and_drops_stopped_instances():
+    """opf_batch_compact after some instances have stopped (here: converged
+    early at a loose tolerance): the schedule keeps the running ones, whose
+    iterates stay bit for bit those of single-instance runs (layout, CTA
+    split and residual partial sums unchanged), and the stopped ones keep
+    their state."""
+    from paper_2410_17203_gb300 import (Solver, opf_batch_autotune, opf_batch_compact, opf_batch_create,
+                                        opf_batch_destroy, opf_batch_iterate, opf_batch_stopped)
+    cases = [make_case("tiny"), make_case(scale_case(150, 24, 6, seed=21)), make_case(scale_case(90, 7, 3, seed=22)),
+             make_case(scale_case(80, 12, 2, seed=27, n_hvdc=3))]
+    # the tiny case converges within the first 300 iterations at this tolerance
+    opts = [dict(adapt_every=10, eps=1e-2, rho_theta=10.0)] + [dict(adapt_every=10, eps=0.0)] * 3
+    bs = [Solver(c, o) for c, o in zip(cases, opts)]
+    ss = [Solver(c, o) for c, o in zip(cases, opts)]
+    b = opf_batch_create([s.h for s in bs])
+    try:
+        opf_batch_autotune(b, steps=3)
+        assert opf_batch_compact(b) == 4          # nothing stopped yet
+        opf_batch_iterate(b, 300)
+        assert opf_batch_stopped(b)[0] == 1
+        assert opf_batch_compact(b) == 3
+        frozen = bs[0].state()
+        opf_batch_iterate(b, 37)
+        for s in ss:
+            s.iterate(337)
+        np.testing.assert_equal(bs[0].state(), frozen)
+        stopped_at = bs[0].get_info()["iterations"]
+        assert stopped_at == ss[0].get_info()["iterations"] and stopped_at < 300
+        for sb, s1 in zip(bs[1:], ss[1:]):
+            a, c = sb.state(), s1.state()
+            for k in a:
+                np.testing.assert_array_equal(a[k], c[k], err_msg=k)
+            assert sb.get_info()["iterations"] == 337
+            np.testing.assert_array_equal(sb.residuals(), s1.residuals())
+    finally:
+        opf_batch_destroy(b)
+        for s in bs + ss:
+            s.close()
+
+
 def test_converged_instances_stay_stopped():
     from paper_2410_17203_gb300 import (Solver, opf_batch_converged, opf_batch_create,
                                         opf_batch_destroy, opf_batch_iterate)
