@@ -16,7 +16,8 @@ iterations and the solution download are inside the timed region.
 the eps = 1e-4 test of Eq. (converge) with the adaptive penalty, through the C
 ABI: the instance cold, the instance with every load scaled by
 lognormal(0, 0.05) cold, and that perturbed instance warm-started from the
-first solution (Section 3.4); and the instance cold with over-relaxation
+first solution (Section 3.4) kept on the device, and again imported from host
+memory inside the timed region; and the instance cold with over-relaxation
 alpha = 1.5 (Section 3.6; ``--ttt-alpha``).
 
 ``--adjoint K``: wall time of the cost gradient after K unrolled iterations
@@ -325,9 +326,10 @@ def reference_arm(args):
     return 0
 
 
-def solve_to_tolerance(case, stream, args, opts=None, state=None):
+def solve_to_tolerance(case, stream, args, opts=None, state=None, state_on_device=False):
     """Iterate to eps = 1e-4 through the C ABI; wall time includes the state
-    import of a warm start.  Returns (info, seconds, handle)."""
+    import of a warm start (host arrays, or CUDA tensors with
+    state_on_device).  Returns (info, seconds, handle)."""
     import torch
     from paper_2410_17203_gb300 import opf_create, opf_get_info, opf_iterate, opf_set_state
     o = dict(adapt_every=10, eps=1e-4)
@@ -336,7 +338,7 @@ def solve_to_tolerance(case, stream, args, opts=None, state=None):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     if state is not None:
-        opf_set_state(h, state)
+        opf_set_state(h, state, on_device=state_on_device)
     done = 0
     while done < args.ttt_max:
         opf_iterate(h, args.ttt_chunk)
@@ -356,9 +358,17 @@ def time_to_tolerance(case, stream, args):
                 "seconds": dt, "residuals": [float(x) for x in opf_residuals(h)[:2]],
                 "tolerance": info["tolerance"]}
 
+    import torch
+    from paper_2410_17203_gb300 import state_shapes
+
     info, dt, h = solve_to_tolerance(case, stream, args)
     out = {"eps": 1e-4, "cold": entry(info, dt, h)}
     state = opf_get_state(h)
+    # the same solution kept on the device (in HBM, as a solver that keeps its
+    # previous solution would)
+    dstate = {k: torch.zeros(sh, dtype=torch.float32, device="cuda") for k, sh in state_shapes(info).items()}
+    opf_get_state(h, on_device=True, out=dstate)
+    torch.cuda.synchronize()
     rho = (info["rho_p"], info["rho_theta"])
     opf_destroy(h)
     # the same network with every load scaled by lognormal(0, 0.05) per step
@@ -369,8 +379,14 @@ def time_to_tolerance(case, stream, args):
     out["perturbed_cold"] = entry(info, dt, h)
     opf_destroy(h)
     info, dt, h = solve_to_tolerance(pert, stream, args, opts=dict(rho_p=rho[0], rho_theta=rho[1]),
-                                     state=state)
+                                     state=dstate, state_on_device=True)
     out["perturbed_warm"] = entry(info, dt, h)
+    out["perturbed_warm"]["state"] = "the previous solution on the device"
+    opf_destroy(h)
+    info, dt, h = solve_to_tolerance(pert, stream, args, opts=dict(rho_p=rho[0], rho_theta=rho[1]),
+                                     state=state)
+    out["perturbed_warm_host_state"] = entry(info, dt, h)
+    out["perturbed_warm_host_state"]["state"] = "the previous solution in host memory (imported in the timed region)"
     opf_destroy(h)
     out["perturbation"] = "load_p x lognormal(0, 0.05) per (load, step), seed 12345"
     if args.ttt_alpha != 1.0:
