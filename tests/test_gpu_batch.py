@@ -121,6 +121,33 @@ def test_compaction_keeps_iterates_and_drops_stopped_instances():
             s.close()
 
 
+def test_compaction_when_every_instance_has_stopped_and_after_autotune():
+    """A batch whose instances have all stopped compacts to an empty schedule
+    (later steps change nothing); opf_batch_autotune schedules every
+    instance again."""
+    from paper_2410_17203_gb300 import (Solver, opf_batch_autotune, opf_batch_compact, opf_batch_create,
+                                        opf_batch_destroy, opf_batch_iterate, opf_batch_stopped)
+    opts = dict(adapt_every=10, eps=1e-2, rho_theta=10.0)
+    solvers = [Solver(make_case("tiny"), opts), Solver(make_case("tiny"), dict(opts, rho_theta=5.0))]
+    b = opf_batch_create([s.h for s in solvers])
+    try:
+        opf_batch_iterate(b, 600)
+        assert opf_batch_stopped(b)[0] == 2
+        assert opf_batch_compact(b) == 0
+        before = [s.state() for s in solvers]
+        its = [s.get_info()["iterations"] for s in solvers]
+        opf_batch_iterate(b, 50)
+        for s, st, it in zip(solvers, before, its):
+            np.testing.assert_equal(s.state(), st)
+            assert s.get_info()["iterations"] == it
+        opf_batch_autotune(b, steps=2)          # leaves the stopped instances as they are
+        assert opf_batch_compact(b) == 0
+    finally:
+        opf_batch_destroy(b)
+        for s in solvers:
+            s.close()
+
+
 def test_converged_instances_stay_stopped():
     from paper_2410_17203_gb300 import (Solver, opf_batch_converged, opf_batch_create,
                                         opf_batch_destroy, opf_batch_iterate)
