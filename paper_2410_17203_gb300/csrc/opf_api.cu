@@ -26,6 +26,9 @@ thread_local char g_err[512];
 
 opf_status fail(opf_status s, const char *msg) {
   snprintf(g_err, sizeof(g_err), "%s", msg);
+  // the failure is returned here; clear the runtime's (non-sticky) last error
+  // so that a later call's launch check does not report it a second time
+  if (s == OPF_ECUDA || s == OPF_ENOMEM) (void)cudaGetLastError();
   return s;
 }
 
@@ -1296,7 +1299,9 @@ opf_status opf_batch_create(opf_ctx *const *ctxs, int32_t n, opf_batch **out) {
 opf_status opf_batch_iterate(opf_batch *b, int32_t n_iters) {
   if (!b) return fail(OPF_EINVAL, "batch is NULL");
   if (n_iters < 0) return fail(OPF_EINVAL, "n_iters must be >= 0");
-  if (n_iters == 0) return OPF_OK;
+  // nothing to do with no iterations, or when opf_batch_compact found every
+  // instance stopped (a stopped instance does not move)
+  if (n_iters == 0 || b->n_sched == 0) return OPF_OK;
   const opf_status gs = ensure_batch_graphs(b);
   if (gs != OPF_OK) return gs;
   // after each instance's queued work ...

@@ -2262,7 +2262,7 @@ int opfk_batch_enqueue(const Params *d_params, const int *d_sched, const BatchPl
     if (bp.count[BK_NODE4]) node_kernel_b<4, true><<<bp.count[BK_NODE4], BLOCK, 0, sm>>>(d_params, at(BK_NODE4));
     if (bp.count[BK_NODE1]) node_kernel_b<1, true><<<bp.count[BK_NODE1], BLOCK, 0, sm>>>(d_params, at(BK_NODE1));
   }
-  decide_kernel_b<<<bp.count[BK_DECIDE], BLOCK, 0, sm>>>(d_params, at(BK_DECIDE));
+  if (bp.count[BK_DECIDE]) decide_kernel_b<<<bp.count[BK_DECIDE], BLOCK, 0, sm>>>(d_params, at(BK_DECIDE));
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
