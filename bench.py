@@ -20,9 +20,9 @@ first solution (Section 3.4) kept on the device, and again imported from host
 memory inside the timed region; and the instance cold with over-relaxation
 alpha = 1.5 (Section 3.6; ``--ttt-alpha``).
 
-``--adjoint K``: wall time of the cost gradient after K unrolled iterations
-(include/opf_diff.h) on the 2k instance, checkpoints every 20 iterations and
-every state kept.
+``--adjoint K`` (default 200, 0 to skip): wall time of the cost gradient
+after K unrolled iterations (include/opf_diff.h) on the 2k instance,
+checkpoints every 20 iterations and every state kept.
 
 ``--impl reference`` times the FP64 oracle on the host cores instead; each
 step is one oracle iteration on a bounded sample of the instance (the 10k
@@ -908,8 +908,8 @@ def main():
                          "(0 = skip)")
     ap.add_argument("--stall-window", type=int, default=3000,
                     help="stall rule of the batched solves (include/opf.h opf_options.stall_window; 0 = off)")
-    ap.add_argument("--adjoint", type=int, default=0,
-                    help="also time the cost gradient after this many unrolled iterations on the 2k instance")
+    ap.add_argument("--adjoint", type=int, default=200,
+                    help="also time the cost gradient after this many unrolled iterations on the 2k instance (0 = skip)")
     ap.add_argument("--_oracle-child", dest="oracle_child", default=None)
     args = ap.parse_args()
     if args.oracle_child:

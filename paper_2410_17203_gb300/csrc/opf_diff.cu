@@ -90,21 +90,24 @@ __device__ __forceinline__ size_t ni(const DP &p, int k, int n, int t) { return 
 // forward (Section 3.2)
 // ---------------------------------------------------------------------------
 
-// node averages (Eq. average-op) of the terminal values of a state
-__global__ void fwd_avg(DP p, St s) {
+// node averages (Eq. average-op) of the terminal values of the new state nx,
+// and the price update u' = u + pbar' (step 3) from the old state s
+__global__ void fwd_avg(DP p, St s, St nx) {
   GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
     float sp = 0.f, st = 0.f;
-    for (int j = p.dptr[n]; j < p.dptr[n + 1]; ++j) sp += s.PD[(size_t)p.didx[j] * p.T + t];
+    for (int j = p.dptr[n]; j < p.dptr[n + 1]; ++j) sp += nx.PD[(size_t)p.didx[j] * p.T + t];
     for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
       const int c = p.lcode[j], l = c >> 1;
-      const float v = s.P[li(p, k, l, t)];
+      const float v = nx.P[li(p, k, l, t)];
       sp += (c & 1) ? v : -v;
-      st += (c & 1) ? s.TH2[li(p, k, l, t)] : s.TH1[li(p, k, l, t)];
+      st += (c & 1) ? nx.TH2[li(p, k, l, t)] : nx.TH1[li(p, k, l, t)];
     }
-    s.PB[i] = sp / p.cnt[n];
-    s.TBR[i] = p.cth[n] > 0.f ? st / p.cth[n] : 0.f;
+    const float pb = sp / p.cnt[n];
+    nx.PB[i] = pb;
+    nx.TBR[i] = p.cth[n] > 0.f ? st / p.cth[n] : 0.f;
+    nx.U[i] = s.U[i] + pb;
   }
 }
 
@@ -121,6 +124,25 @@ __device__ __forceinline__ LineIn line_inputs(const DP &p, const St &s, int k, i
   r.y1 = s.TBR[o1] - s.V1[o];                  // theta_bar - v
   r.y2 = s.TBR[o2] - s.V2[o];
   return r;
+}
+
+// The prox inputs that decide a clip, each rounding written out, so that the
+// reverse pass's recomputation (without a record) takes the forward's
+// decisions whatever the compiler contracts elsewhere: the line prox's
+// denominator 2 rho_p + rho_theta / (2 b^2) and unclipped flow (Section 4.2),
+// a generator's and a curtailable load's unclipped power (Section 4.1)
+__device__ __forceinline__ float line_den(const DP &p, float b, float tb) {
+  return __fadd_rn(__fmul_rn(2.f, p.rp), p.rt / (tb * b));
+}
+__device__ __forceinline__ float line_z(const DP &p, const LineIn &in, float tb, float den) {
+  return __fadd_rn(__fmul_rn(p.rp, in.x2 - in.x1), __fmul_rn(p.rt, in.y1 - in.y2) / tb) / den;
+}
+__device__ __forceinline__ float gen_den(const DP &p, int d) { return __fadd_rn(__fmul_rn(2.f, p.ga[d]), p.rd); }
+__device__ __forceinline__ float gen_z(const DP &p, int d, float X) {
+  return __fsub_rn(__fmul_rn(p.rd, X), p.gb[d]) / gen_den(p, d);
+}
+__device__ __forceinline__ float load_z(const DP &p, int e, float X) {
+  return __fsub_rn(__fmul_rn(p.rd, X), p.voll[e]) / p.rd;
 }
 
 // where an unclipped value z lies against [lo, hi]: 0 inside, 1 above, 2
@@ -140,8 +162,7 @@ __global__ void fwd_line(DP p, St s, St nx, unsigned char *lmask) {
     const LineIn in = line_inputs(p, s, k, l, t);
     if (p.out[k] != l) {
       const float b = p.b[l], tb = 2.f * b, u = p.lu[l];
-      const float den = 2.f * p.rp + p.rt / (tb * b);
-      const float z = (p.rp * (in.x2 - in.x1) + p.rt * (in.y1 - in.y2) / tb) / den;
+      const float z = line_z(p, in, tb, line_den(p, b, tb));
       if (lmask) lmask[i] = clip_code(z, -u, u);
       const float p2 = fminf(fmaxf(z, -u), u);
       const float mid = 0.5f * (in.y1 + in.y2);
@@ -159,6 +180,7 @@ __global__ void fwd_line(DP p, St s, St nx, unsigned char *lmask) {
 __device__ __forceinline__ float dev_x(const DP &p, const St &s, int d, int t) {
   const int n = p.dnode[d];
   float sum = 0.f;
+#pragma unroll 4
   for (int k = 0; k < p.Kp; ++k) sum += s.PB[ni(p, k, n, t)] + s.U[ni(p, k, n, t)];
   return s.PD[(size_t)d * p.T + t] - sum / (float)p.Kp;   // p_d - avg_k(pbar + u)
 }
@@ -187,7 +209,7 @@ __global__ void fwd_dev(DP p, St s, St nx, float *XD, unsigned char *dmask) {
     }
     float r;
     if (d < p.G) {
-      const float z = (p.rd * X - p.gb[d]) / (2.f * p.ga[d] + p.rd);
+      const float z = gen_z(p, d, X);
       if (dmask) dmask[i] = clip_code(z, p.gpmin[i], p.gpmax[i]);
       r = fminf(fmaxf(z, p.gpmin[i]), p.gpmax[i]);
     } else {
@@ -196,7 +218,7 @@ __global__ void fwd_dev(DP p, St s, St nx, float *XD, unsigned char *dmask) {
       if (p.voll[e] < 0.f) {
         r = -p.load_p[o];
       } else {
-        const float z = (p.rd * X - p.voll[e]) / p.rd;
+        const float z = load_z(p, e, X);
         if (dmask) dmask[i] = clip_code(z, -p.load_p[o], 0.f);
         r = fminf(fmaxf(z, -p.load_p[o]), 0.f);
       }
@@ -350,11 +372,8 @@ __global__ void __launch_bounds__(TBI) fwd_inner(DP p, St s, St nx, const float 
   }
 }
 
-// step 3: u += pbar, v += theta - theta_bar (after fwd_avg of the new state)
-__global__ void fwd_upd_nodes(DP p, St s, St nx) {
-  GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) nx.U[i] = s.U[i] + nx.PB[i];
-}
-
+// step 3 for the lines: v += theta - theta_bar (after fwd_avg of the new
+// state; fwd_avg updates u)
 __global__ void fwd_upd_lines(DP p, St s, St nx) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
     const unsigned q = i / (unsigned)p.T;
@@ -369,129 +388,162 @@ __global__ void fwd_upd_lines(DP p, St s, St nx) {
 // adjoint of state i-1; s is state i-1
 // ---------------------------------------------------------------------------
 
-// adjoints of the new node averages through u' = u + pbar' and
-// v' = v + theta' - theta_bar': A = d/d pbar', B = d/d theta_bar'
-__global__ void bwd_node1(DP p, Adj a, float *A, float *B) {
+// The reverse pass of iteration i runs in two halves.  The first: the
+// adjoints of the new node averages, the line prox and the device proxes
+// transposed (bwd_node1, bwd_line1, bwd_dev), then the inner ADMM.  The
+// second: gathers at the nodes and their scatter back to the line and device
+// values (bwd_node2, bwd_line2, bwd_dev2).  Each second-half kernel also runs
+// iteration i-1's first-half step on the same item when `nxt` is set, so a
+// reverse iteration takes four launches instead of seven; the arithmetic is
+// the same device functions either way, so the results are the same bit for
+// bit.  The adjoint of the new pbar' through u' = u + pbar' is u's adjoint
+// itself: the kernels read it from a.LU (as `A`) before bwd_node2 adds to it.
+
+// B = d/d theta_bar' through v' = v + theta' - theta_bar' at node item
+// (k, n, t): minus the v adjoints of the node's line terminals
+__device__ __forceinline__ float node_b(const DP &p, const Adj &a, int k, int n, int t) {
+  float s = 0.f;
+  for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
+    const int c = p.lcode[j];
+    s += (c & 1) ? a.LV2[li(p, k, c >> 1, t)] : a.LV1[li(p, k, c >> 1, t)];
+  }
+  return -s;
+}
+
+__global__ void bwd_node1(DP p, Adj a, float *B) {
   GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
-    float s = 0.f;
-    for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
-      const int c = p.lcode[j];
-      s += (c & 1) ? a.LV2[li(p, k, c >> 1, t)] : a.LV1[li(p, k, c >> 1, t)];
-    }
-    A[i] = a.LU[i];
-    B[i] = -s;
+    B[i] = node_b(p, a, k, n, t);
   }
 }
 
-// the line prox backwards; X1.. hold d/d(x1, x2, y1, y2) for the node gathers
-// lmask (optional): the forward's record of the iteration's line clips,
-// else the unclipped flows are recomputed from state i-1
+// the line prox backwards at item i = (k, l, t), given the adjoints of the
+// step's outputs p, theta_1, theta_2 (lp0, lt10, lt20); X1.. receive
+// d/d(x1, x2, y1, y2) for the node gathers.  lmask (optional): the forward's
+// record of the iteration's line clips, else the unclipped flow is
+// recomputed from the step's input state s
+__device__ __forceinline__ void line_back(const DP &p, const St &s, const Adj &a, const float *A, const float *B,
+                                          float *X1, float *X2, float *Y1, float *Y2, float *GU,
+                                          const unsigned char *lmask, unsigned i, int k, int l, int t, float lp0,
+                                          float lt10, float lt20) {
+  const int n1 = p.n1[l], n2 = p.n2[l];
+  const size_t o1 = ni(p, k, n1, t), o2 = ni(p, k, n2, t);
+  const float lp = lp0 - A[o1] / p.cnt[n1] + A[o2] / p.cnt[n2];
+  const float lt1 = lt10 + a.LV1[i] + (p.cth[n1] > 0.f ? B[o1] / p.cth[n1] : 0.f);
+  const float lt2 = lt20 + a.LV2[i] + (p.cth[n2] > 0.f ? B[o2] / p.cth[n2] : 0.f);
+  float lx1 = 0.f, lx2 = 0.f, ly1, ly2;
+  if (p.out[k] != l) {
+    const float b = p.b[l], tb = 2.f * b, u = p.lu[l];
+    const float den = line_den(p, b, tb);
+    const unsigned char code = lmask ? lmask[i] : clip_code(line_z(p, line_inputs(p, s, k, l, t), tb, den), -u, u);
+    const float lpt = lp + (lt1 - lt2) / tb;     // theta_{1,2} = mid +- p / (2b)
+    const float half = __fmul_rn(0.5f, lt1 + lt2);
+    ly1 = ly2 = half;
+    if (code == CLIP_IN) {
+      lx2 = p.rp * lpt / den;
+      lx1 = -lx2;
+      const float w = p.rt * lpt / (tb * den);
+      ly1 = __fadd_rn(half, w);
+      ly2 = __fsub_rn(half, w);
+    } else {
+      GU[i] += code == CLIP_HI ? lpt : -lpt;
+    }
+  } else {
+    ly1 = lt1;
+    ly2 = lt2;
+  }
+  X1[i] = lx1;
+  X2[i] = lx2;
+  Y1[i] = ly1;
+  Y2[i] = ly2;
+  a.LP[i] = lx2 - lx1;                   // x1 = -p - ..., x2 = p - ...
+  a.LV1[i] -= ly1;                       // v enters y = theta_bar - v, and v' = v + ...
+  a.LV2[i] -= ly2;
+}
+
 __global__ void bwd_line1(DP p, St s, Adj a, const float *A, const float *B, float *X1, float *X2, float *Y1,
                           float *Y2, float *GU, const unsigned char *lmask) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
-    const int n1 = p.n1[l], n2 = p.n2[l];
-    const size_t o1 = ni(p, k, n1, t), o2 = ni(p, k, n2, t);
-    const float lp = a.LP[i] - A[o1] / p.cnt[n1] + A[o2] / p.cnt[n2];
-    const float lt1 = a.LT1[i] + a.LV1[i] + (p.cth[n1] > 0.f ? B[o1] / p.cth[n1] : 0.f);
-    const float lt2 = a.LT2[i] + a.LV2[i] + (p.cth[n2] > 0.f ? B[o2] / p.cth[n2] : 0.f);
-    float lx1 = 0.f, lx2 = 0.f, ly1, ly2;
-    if (p.out[k] != l) {
-      const float b = p.b[l], tb = 2.f * b, u = p.lu[l];
-      const float den = 2.f * p.rp + p.rt / (tb * b);
-      unsigned char code;
-      if (lmask) {
-        code = lmask[i];
-      } else {
-        const LineIn in = line_inputs(p, s, k, l, t);
-        code = clip_code((p.rp * (in.x2 - in.x1) + p.rt * (in.y1 - in.y2) / tb) / den, -u, u);
-      }
-      const float lpt = lp + (lt1 - lt2) / tb;     // theta_{1,2} = mid +- p / (2b)
-      ly1 = ly2 = 0.5f * (lt1 + lt2);
-      if (code == CLIP_IN) {
-        lx2 = p.rp * lpt / den;
-        lx1 = -lx2;
-        const float w = p.rt * lpt / (tb * den);
-        ly1 += w;
-        ly2 -= w;
-      } else {
-        GU[i] += code == CLIP_HI ? lpt : -lpt;
-      }
-    } else {
-      ly1 = lt1;
-      ly2 = lt2;
-    }
-    X1[i] = lx1;
-    X2[i] = lx2;
-    Y1[i] = ly1;
-    Y2[i] = ly2;
-    a.LP[i] = lx2 - lx1;                 // x1 = -p - ..., x2 = p - ...
-    a.LV1[i] -= ly1;                     // v enters y = theta_bar - v, and v' = v + ...
-    a.LV2[i] -= ly2;
+    line_back(p, s, a, A, B, X1, X2, Y1, Y2, GU, lmask, i, k, l, t, a.LP[i], a.LT1[i], a.LT2[i]);
   }
 }
 
-// the closed-form device proxes backwards; LX = d/dX per device.  For an
-// inner-ADMM device the kernel records X and the adjoint of its output for
-// bwd_inner.
-__device__ __forceinline__ float dev_lpd(const DP &p, const Adj &a, const float *A, int d, int t) {
+// lpd + sum over contingencies of V at device d's node, divided by the
+// node's terminal count (the k-average's adjoint)
+__device__ __forceinline__ float add_node_k(const DP &p, const float *V, int d, int t, float lpd) {
   const int n = p.dnode[d];
-  float lpd = a.LPD[(size_t)d * p.T + t];
-  for (int k = 0; k < p.Kp; ++k) lpd += A[ni(p, k, n, t)] / p.cnt[n];
+#pragma unroll 4
+  for (int k = 0; k < p.Kp; ++k) lpd += V[ni(p, k, n, t)] / p.cnt[n];
   return lpd;
 }
 
+// the closed-form device proxes backwards at item i = (d, t), given the
+// adjoint of the device's new power (lpd) and, for an HVDC terminal, its
+// partner's (lpd_o); LX = d/dX per device.  An inner-ADMM device records
+// the adjoint of its output for bwd_inner (and, without a record, X).
 // dmask (optional): the forward's record of the iteration's device clips
 // (the inner-ADMM devices then need no X either: their clipped rows are
-// recorded too); else X is recomputed from state i-1
+// recorded too); else X is recomputed from the step's input state s
+__device__ __forceinline__ void dev_back(const DP &p, const St &s, float *LX, float *GL, float *GP, float *XD,
+                                         float *LPDT, const unsigned char *dmask, unsigned i, int d, int t, float lpd,
+                                         float lpd_o) {
+  const float X = dmask ? 0.f : dev_x(p, s, d, t);
+  if (p.kind[d] == 1) {
+    if (!dmask) XD[i] = X;
+    LPDT[i] = lpd;
+    return;
+  }
+  if (p.kind[d] == 2) {                  // HVDC: both terminals' adjoints meet in d/d p2
+    const int e = d - (p.G + p.D + p.B), d1 = d - (e & 1), h = e >> 1;
+    const float l1 = (e & 1) ? lpd_o : lpd, l2 = (e & 1) ? lpd : lpd_o;
+    const float u = p.hvdc_u[h];
+    unsigned char code;
+    if (dmask) {
+      code = dmask[i];
+    } else {
+      const float x1 = (e & 1) ? dev_x(p, s, d1, t) : X, x2 = (e & 1) ? X : dev_x(p, s, d1 + 1, t);
+      code = clip_code(0.5f * (x2 - x1), -u, u);
+    }
+    const float lz = code == CLIP_IN ? 0.5f * (l2 - l1) : 0.f;
+    LX[i] = (e & 1) ? lz : -lz;
+    return;
+  }
+  float lx = 0.f;
+  if (d < p.G) {
+    const unsigned char code = dmask ? dmask[i] : clip_code(gen_z(p, d, X), p.gpmin[i], p.gpmax[i]);
+    if (code == CLIP_IN) lx = lpd * p.rd / gen_den(p, d);
+    else if (code == CLIP_HI) GP[i] += lpd;
+  } else {
+    const int e = d - p.G;
+    const size_t o = (size_t)e * p.T + t;
+    if (p.voll[e] < 0.f) {
+      GL[o] -= lpd;                      // p = -P
+    } else {
+      const unsigned char code = dmask ? dmask[i] : clip_code(load_z(p, e, X), -p.load_p[o], 0.f);
+      if (code == CLIP_IN) lx = lpd;
+      else if (code == CLIP_LO) GL[o] -= lpd;
+    }
+  }
+  LX[i] = lx;
+}
+
+// the HVDC partner of terminal d (its index), or -1
+__device__ __forceinline__ int hvdc_partner(const DP &p, int d) {
+  if (p.kind[d] != 2) return -1;
+  const int e = d - (p.G + p.D + p.B);
+  return (e & 1) ? d - 1 : d + 1;
+}
+
 __global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL, float *GP, float *XD, float *LPDT,
                         const unsigned char *dmask) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
-    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T);
-    const float lpd = dev_lpd(p, a, A, d, t);
-    const float X = dmask ? 0.f : dev_x(p, s, d, t);
-    if (p.kind[d] == 1) {
-      if (!dmask) XD[i] = X;
-      LPDT[i] = lpd;
-      continue;
-    }
-    if (p.kind[d] == 2) {                // HVDC: both terminals' adjoints meet in d/d p2
-      const int e = d - (p.G + p.D + p.B), d1 = d - (e & 1), h = e >> 1;
-      const float l1 = (e & 1) ? dev_lpd(p, a, A, d1, t) : lpd, l2 = (e & 1) ? lpd : dev_lpd(p, a, A, d1 + 1, t);
-      const float u = p.hvdc_u[h];
-      unsigned char code;
-      if (dmask) {
-        code = dmask[i];
-      } else {
-        const float x1 = (e & 1) ? dev_x(p, s, d1, t) : X, x2 = (e & 1) ? X : dev_x(p, s, d1 + 1, t);
-        code = clip_code(0.5f * (x2 - x1), -u, u);
-      }
-      const float lz = code == CLIP_IN ? 0.5f * (l2 - l1) : 0.f;
-      LX[i] = (e & 1) ? lz : -lz;
-      continue;
-    }
-    float lx = 0.f;
-    if (d < p.G) {
-      const float den = 2.f * p.ga[d] + p.rd;
-      const unsigned char code = dmask ? dmask[i] : clip_code((p.rd * X - p.gb[d]) / den, p.gpmin[i], p.gpmax[i]);
-      if (code == CLIP_IN) lx = lpd * p.rd / den;
-      else if (code == CLIP_HI) GP[i] += lpd;
-    } else {
-      const int e = d - p.G;
-      const size_t o = (size_t)e * p.T + t;
-      if (p.voll[e] < 0.f) {
-        GL[o] -= lpd;                    // p = -P
-      } else {
-        const unsigned char code =
-            dmask ? dmask[i] : clip_code((p.rd * X - p.voll[e]) / p.rd, -p.load_p[o], 0.f);
-        if (code == CLIP_IN) lx = lpd;
-        else if (code == CLIP_LO) GL[o] -= lpd;
-      }
-    }
-    LX[i] = lx;
+    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T), d2 = hvdc_partner(p, d);
+    const float lpd = add_node_k(p, A, d, t, a.LPD[i]);
+    const float lpd_o = d2 < 0 ? 0.f : add_node_k(p, A, d2, t, a.LPD[(size_t)d2 * p.T + t]);
+    dev_back(p, s, LX, GL, GP, XD, LPDT, dmask, i, d, t, lpd, lpd_o);
   }
 }
 
@@ -1279,9 +1331,11 @@ __global__ void __launch_bounds__(TB, 1) bwd_inner_r(DP p, St s, Adj a, const fl
   }
 }
 
-// gathers at the nodes: C = d/d pbar (old), D = d/d theta_bar (old); u's adjoint
+// gathers at the nodes: C = d/d pbar (old), D = d/d theta_bar (old); u's
+// adjoint.  nxt: also iteration i-1's B (bwd_node1: the v adjoints are final
+// after bwd_line1 of iteration i)
 __global__ void bwd_node2(DP p, Adj a, const float *X1, const float *X2, const float *Y1, const float *Y2,
-                          const float *LX, float *C, float *Dt) {
+                          const float *LX, float *C, float *Dt, float *B, int nxt) {
   GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
@@ -1297,28 +1351,49 @@ __global__ void bwd_node2(DP p, Adj a, const float *X1, const float *X2, const f
     C[i] = -sx - sd;                     // x = ... - pbar - u, X = ... - avg_k(pbar + u)
     a.LU[i] += -sx - sd;
     Dt[i] = sy;                          // y = theta_bar - v
+    if (nxt) B[i] = node_b(p, a, k, n, t);
   }
 }
 
-// the old node averages back onto the old line values and device powers
-__global__ void bwd_line2(DP p, Adj a, const float *C, const float *Dt) {
+// the old node averages back onto the old line values; nxt: then iteration
+// i-1's line prox backwards on the same item (bwd_line1), from state s and
+// record lmask of that iteration
+__global__ void bwd_line2(DP p, St s, Adj a, const float *C, const float *Dt, const float *A, const float *B,
+                          float *X1, float *X2, float *Y1, float *Y2, float *GU, const unsigned char *lmask, int nxt) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
     const int n1 = p.n1[l], n2 = p.n2[l];
     const size_t o1 = ni(p, k, n1, t), o2 = ni(p, k, n2, t);
-    a.LP[i] += -C[o1] / p.cnt[n1] + C[o2] / p.cnt[n2];
-    a.LT1[i] = p.cth[n1] > 0.f ? Dt[o1] / p.cth[n1] : 0.f;
-    a.LT2[i] = p.cth[n2] > 0.f ? Dt[o2] / p.cth[n2] : 0.f;
+    const float lp = a.LP[i] + (-C[o1] / p.cnt[n1] + C[o2] / p.cnt[n2]);
+    const float lt1 = p.cth[n1] > 0.f ? Dt[o1] / p.cth[n1] : 0.f;
+    const float lt2 = p.cth[n2] > 0.f ? Dt[o2] / p.cth[n2] : 0.f;
+    if (nxt) {
+      line_back(p, s, a, A, B, X1, X2, Y1, Y2, GU, lmask, i, k, l, t, lp, lt1, lt2);
+    } else {
+      a.LP[i] = lp;
+      a.LT1[i] = lt1;
+      a.LT2[i] = lt2;
+    }
   }
 }
 
-__global__ void bwd_dev2(DP p, Adj a, const float *LX, const float *C) {
+// ... and onto the old device powers (LX: this iteration's d/dX); nxt: then
+// iteration i-1's device proxes backwards on the same item (bwd_dev), into
+// LXn, from state s and record dmask of that iteration.  An HVDC terminal
+// recomputes its partner's adjoint from the same inputs.
+__global__ void bwd_dev2(DP p, St s, Adj a, const float *LX, const float *C, const float *A, float *LXn, float *GL,
+                         float *GP, float *XD, float *LPDT, const unsigned char *dmask, int nxt) {
   GRID_STRIDE(i, (long long)p.S * p.T) {
-    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T), n = p.dnode[d];
-    float s = LX[i];
-    for (int k = 0; k < p.Kp; ++k) s += C[ni(p, k, n, t)] / p.cnt[n];
-    a.LPD[i] = s;
+    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T);
+    const float lpd = add_node_k(p, C, d, t, LX[i]);
+    a.LPD[i] = lpd;
+    if (nxt) {
+      const int d2 = hvdc_partner(p, d);
+      const size_t o2 = (size_t)d2 * p.T + t;
+      const float lpd_o = d2 < 0 ? 0.f : add_node_k(p, A, d2, t, add_node_k(p, C, d2, t, LX[o2]));
+      dev_back(p, s, LXn, GL, GP, XD, LPDT, dmask, i, d, t, add_node_k(p, A, d, t, lpd), lpd_o);
+    }
   }
 }
 
@@ -1605,8 +1680,7 @@ void forward_step(const opf_diff *d, const St &s, const St &nx, float *XD, float
       default: fwd_inner<<<p.n_inner, TBI, d->smem_fwd, d->stream>>>(p, s, nx, XD, DEL, d->stage, mask); break;
     }
   }
-  fwd_avg<<<grid_for(nn), TB, 0, d->stream>>>(p, nx);
-  fwd_upd_nodes<<<grid_for(nn), TB, 0, d->stream>>>(p, s, nx);
+  fwd_avg<<<grid_for(nn), TB, 0, d->stream>>>(p, s, nx);
   fwd_upd_lines<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx);
 }
 
@@ -1968,18 +2042,19 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   else DCK(cudaMemcpyAsync(const_cast<float *>(p.lu), d->lu.data(), L * 4, cudaMemcpyHostToDevice, d->stream));
   // the capacity rows of the ramp-limited generators' inner problems
   if (p.n_inner) set_ramp_rhs<<<grid_for((long long)p.n_inner * T), TB, 0, d->stream>>>(p, d->RH);
-  // states: checkpoints 0, C, 2C, ... and one segment of C + 1 states
+  // states: checkpoints 0, C, 2C, ... and room for a segment's C - 1
+  // recomputed states (at least the forward pass's two alternating ones)
   const int C = std::min(d->ckpt, K);
   const int n_ck = K / C + 1;
   const size_t SF = d->state_floats;
   const size_t KLT = (size_t)d->Kp * d->L * T, KNT = (size_t)d->Kp * d->N * T, ST = (size_t)d->S * T;
   const size_t MT = (size_t)d->Mtot;
   const size_t adj_floats = 5 * KLT + ST + KNT + 2 * MT;
-  const size_t work_floats = 5 * KLT + 4 * KNT + 3 * ST + DT + GT + MT + BT;
+  const size_t work_floats = 5 * KLT + 3 * KNT + 4 * ST + DT + GT + MT + BT;
   const bool grads = g_load || g_pmax || g_u;
   size_t adj_cap = d->adj ? adj_floats : 0, work_cap = d->work ? work_floats : 0, gl_cap = d->gline ? L : 0;
   cudaError_t e = ensure(&d->ck, &d->ck_cap, (size_t)n_ck * SF);
-  if (e == cudaSuccess) e = ensure(&d->seg, &d->seg_cap, (size_t)(grads ? C + 1 : 2) * SF);
+  if (e == cudaSuccess) e = ensure(&d->seg, &d->seg_cap, (size_t)(grads ? std::max(C, 2) : 2) * SF);
   if (e == cudaSuccess) e = ensure(&d->adj, &adj_cap, adj_floats);
   if (e == cudaSuccess) e = ensure(&d->work, &work_cap, work_floats);
   if (e == cudaSuccess) e = ensure(&d->gline, &gl_cap, L);
@@ -1996,7 +2071,7 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   auto mask_of = [&](int i) { return masks ? masks + (size_t)(i - 1) * mask_iter : nullptr; };   // iteration i
   float *ck = d->ck, *seg = d->seg, *adj = d->adj, *work = d->work;
   float *X1 = work, *X2 = X1 + KLT, *Y1 = X2 + KLT, *Y2 = Y1 + KLT, *GU = Y2 + KLT;
-  float *A = GU + KLT, *Bn = A + KNT, *Cn = Bn + KNT, *Dn = Cn + KNT, *LX = Dn + KNT, *XD = LX + ST;
+  float *Bn = GU + KLT, *Cn = Bn + KNT, *Dn = Cn + KNT, *LX0 = Dn + KNT, *LX1 = LX0 + ST, *XD = LX1 + ST;
   float *LPDT = XD + ST, *GL = LPDT + ST, *GP = GL + DT, *HB = GP + GT, *DEL = HB + MT;
   auto ckst = [&](int j) { return carve_state(d, ck + (size_t)j * SF); };
   auto sgst = [&](int j) { return carve_state(d, seg + (size_t)j * SF); };
@@ -2048,18 +2123,25 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   if (e == cudaSuccess) e = cudaMemsetAsync(GL, 0, (DT + GT + MT) * 4, d->stream);
   if (e == cudaSuccess) bwd_init<<<grid_for((long long)ST), TB, 0, d->stream>>>(p, cur, a, GL);
   const long long nl = (long long)KLT, nn = (long long)KNT, ns = (long long)ST;
+  // d/d pbar' is u's adjoint itself (u' = u + pbar'), read before bwd_node2 adds to it
+  const float *A = a.LU;
+  bool primed = false;   // iteration i's first half already ran, fused into iteration i+1's second half
   for (int hi = K; e == cudaSuccess && hi > 0;) {
-    // segment (lo, hi]: recompute states lo .. hi - 1 from checkpoint lo
+    // segment (lo, hi]: states lo + 1 .. hi - 1 recomputed from checkpoint lo
+    // (read in place)
     const int lo = ((hi - 1) / C) * C;
-    e = cudaMemcpyAsync(seg, ck + (size_t)(lo / C) * SF, SF * 4, cudaMemcpyDeviceToDevice, d->stream);
-    for (int i = lo + 1; e == cudaSuccess && i < hi; ++i) forward_step(d, sgst(i - 1 - lo), sgst(i - lo), XD, DEL);
+    auto state = [&](int j) { return j == lo ? ckst(lo / C) : sgst(j - lo); };   // state j, lo <= j < hi
+    for (int i = lo + 1; e == cudaSuccess && i < hi; ++i) forward_step(d, state(i - 1), sgst(i - lo), XD, DEL);
     for (int i = hi; e == cudaSuccess && i > lo; --i) {
-      const St s = sgst(i - 1 - lo);   // state i - 1
-      bwd_node1<<<grid_for(nn), TB, 0, d->stream>>>(p, a, A, Bn);
+      const St s = state(i - 1);
       unsigned char *mi = mask_of(i);
-      const unsigned char *lmask = mi ? mi + inner_record_bytes(p) : nullptr, *dmask = mi ? lmask + KLT : nullptr;
-      bwd_line1<<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, Bn, X1, X2, Y1, Y2, GU, lmask);
-      bwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT, dmask);
+      float *LX = (i & 1) ? LX1 : LX0, *LXn = (i & 1) ? LX0 : LX1;   // d/dX of iterations i and i - 1
+      if (!primed) {
+        const unsigned char *lmask = mi ? mi + inner_record_bytes(p) : nullptr, *dmask = mi ? lmask + KLT : nullptr;
+        bwd_node1<<<grid_for(nn), TB, 0, d->stream>>>(p, a, Bn);
+        bwd_line1<<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, Bn, X1, X2, Y1, Y2, GU, lmask);
+        bwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT, dmask);
+      }
       if (p.n_inner) {
         const int g = (p.n_inner + RWARPS - 1) / RWARPS, lst = i == K ? 1 : 0;
         unsigned long long *m1 = reinterpret_cast<unsigned long long *>(d->mask1);
@@ -2074,9 +2156,16 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
             break;
         }
       }
-      bwd_node2<<<grid_for(nn), TB, 0, d->stream>>>(p, a, X1, X2, Y1, Y2, LX, Cn, Dn);
-      bwd_line2<<<grid_for(nl), TB, 0, d->stream>>>(p, a, Cn, Dn);
-      bwd_dev2<<<grid_for(ns), TB, 0, d->stream>>>(p, a, LX, Cn);
+      // iteration i - 1's first half joins this second half when what it
+      // reads is at hand: its record, or its input state i - 2 in this segment
+      unsigned char *mp = i > 1 ? mask_of(i - 1) : nullptr;
+      const int nxt = i > 1 && (mp || i - 2 >= lo) ? 1 : 0;
+      const St sp = nxt && i - 2 >= lo ? state(i - 2) : s;   // read only without a record
+      const unsigned char *lmp = mp ? mp + inner_record_bytes(p) : nullptr, *dmp = mp ? lmp + KLT : nullptr;
+      bwd_node2<<<grid_for(nn), TB, 0, d->stream>>>(p, a, X1, X2, Y1, Y2, LX, Cn, Dn, Bn, nxt);
+      bwd_line2<<<grid_for(nl), TB, 0, d->stream>>>(p, sp, a, Cn, Dn, A, Bn, X1, X2, Y1, Y2, GU, lmp, nxt);
+      bwd_dev2<<<grid_for(ns), TB, 0, d->stream>>>(p, sp, a, LX, Cn, A, LXn, GL, GP, XD, LPDT, dmp, nxt);
+      primed = nxt != 0;
     }
     hi = lo;
     if (e == cudaSuccess) e = cudaGetLastError();
