@@ -23,7 +23,8 @@
 
 namespace {
 
-constexpr int TB = 256;       // threads per CTA of the element-wise kernels
+constexpr int TB = 256;       // threads per CTA of the element-wise kernels (eight per SM: they wait
+                              // on gathers, so they are held to 32 registers for the most warps)
 constexpr int TBI = 128;      // threads per CTA of the inner-ADMM kernels (one CTA per device)
 constexpr int N_INNER = 10;   // Appendix D iterations per prox evaluation (Section 4.5)
 
@@ -86,13 +87,46 @@ __device__ __forceinline__ size_t ni(const DP &p, int k, int n, int t) { return 
 #define GRID_STRIDE(i, n) \
   for (unsigned i = blockIdx.x * TB + threadIdx.x, n_##i = (unsigned)(n); i < n_##i; i += gridDim.x * TB)
 
+// The device kernels give each device step (d, t) a group of KL lanes, which
+// split its sums over the K+1 contingencies: lane j takes k = j, j + KL, ...,
+// and the partial sums meet in a butterfly whose pattern is fixed (so the
+// result is the same wherever it is formed; floating-point addition is
+// commutative, so every lane ends with the same total).  Without the split a
+// device kernel ran about 200 CTAs of threads each walking 21 contingencies
+// one load after another.  The loop trip count is the same for the lanes of
+// a group.
+constexpr int KL = 8;
+#define GROUP_STRIDE(i, n)                                                                   \
+  for (unsigned i = (blockIdx.x * TB + threadIdx.x) / KL, n_##i = (unsigned)(n); i < n_##i; \
+       i += gridDim.x * (TB / KL))
+
+__device__ __forceinline__ unsigned group_mask() { return 0xFFu << ((threadIdx.x & 31) & ~(KL - 1)); }
+
+// sum over the contingencies of V (and W, when not NULL) at node n, step t,
+// split over the group's lanes (lane j = threadIdx.x % KL)
+__device__ __forceinline__ float ksum(const DP &p, const float *V, const float *W, int n, int t) {
+  const int j = threadIdx.x & (KL - 1);
+  float s = 0.f;
+  if (W) {
+#pragma unroll 3
+    for (int k = j; k < p.Kp; k += KL) s += V[ni(p, k, n, t)] + W[ni(p, k, n, t)];
+  } else {
+#pragma unroll 3
+    for (int k = j; k < p.Kp; k += KL) s += V[ni(p, k, n, t)];
+  }
+  const unsigned gm = group_mask();
+#pragma unroll
+  for (int o = KL / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gm, s, o);
+  return s;
+}
+
 // ---------------------------------------------------------------------------
 // forward (Section 3.2)
 // ---------------------------------------------------------------------------
 
 // node averages (Eq. average-op) of the terminal values of the new state nx,
 // and the price update u' = u + pbar' (step 3) from the old state s
-__global__ void fwd_avg(DP p, St s, St nx) {
+__global__ void __launch_bounds__(TB, 8) fwd_avg(DP p, St s, St nx) {
   GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
@@ -155,7 +189,7 @@ __device__ __forceinline__ unsigned char clip_code(float z, float lo, float hi) 
 
 // step 1: line prox (Section 4.2); outaged lines decouple.  lmask (optional):
 // the iteration's record of where each line's unclipped flow lay
-__global__ void fwd_line(DP p, St s, St nx, unsigned char *lmask) {
+__global__ void __launch_bounds__(TB, 8) fwd_line(DP p, St s, St nx, unsigned char *lmask) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
@@ -177,12 +211,16 @@ __global__ void fwd_line(DP p, St s, St nx, unsigned char *lmask) {
   }
 }
 
+// a device's prox input X = p_d - avg_k(pbar + u) (every lane of the group)
 __device__ __forceinline__ float dev_x(const DP &p, const St &s, int d, int t) {
-  const int n = p.dnode[d];
-  float sum = 0.f;
-#pragma unroll 4
-  for (int k = 0; k < p.Kp; ++k) sum += s.PB[ni(p, k, n, t)] + s.U[ni(p, k, n, t)];
-  return s.PD[(size_t)d * p.T + t] - sum / (float)p.Kp;   // p_d - avg_k(pbar + u)
+  return s.PD[(size_t)d * p.T + t] - ksum(p, s.PB, s.U, p.dnode[d], t) / (float)p.Kp;
+}
+
+// the HVDC partner of terminal d (its index), or -1
+__device__ __forceinline__ int hvdc_partner(const DP &p, int d) {
+  if (p.kind[d] != 2) return -1;
+  const int e = d - (p.G + p.D + p.B);
+  return (e & 1) ? d - 1 : d + 1;
 }
 
 // step 2: devices shared by all contingencies, weight (K+1) rho_p; the
@@ -190,17 +228,18 @@ __device__ __forceinline__ float dev_x(const DP &p, const St &s, int d, int t) {
 // evaluates its link's prox p2 = clip((x2 - x1)/2, -u, u), p1 = -p2.
 // dmask (optional): the iteration's record of where each closed-form
 // device's unclipped power lay
-__global__ void fwd_dev(DP p, St s, St nx, float *XD, unsigned char *dmask) {
-  GRID_STRIDE(i, (long long)p.S * p.T) {
-    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T);
-    const float X = dev_x(p, s, d, t);
+__global__ void __launch_bounds__(TB, 8) fwd_dev(DP p, St s, St nx, float *XD, unsigned char *dmask) {
+  GROUP_STRIDE(i, (long long)p.S * p.T) {
+    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T), d2 = hvdc_partner(p, d);
+    const float X = dev_x(p, s, d, t), Xo = d2 < 0 ? 0.f : dev_x(p, s, d2, t);
+    if (threadIdx.x & (KL - 1)) continue;   // the group's first lane writes
     if (p.kind[d] == 1) {
       XD[i] = X;
       continue;
     }
     if (p.kind[d] == 2) {
-      const int e = d - (p.G + p.D + p.B), d1 = d - (e & 1), h = e >> 1;
-      const float x1 = (e & 1) ? dev_x(p, s, d1, t) : X, x2 = (e & 1) ? X : dev_x(p, s, d1 + 1, t);
+      const int e = d - (p.G + p.D + p.B), h = e >> 1;
+      const float x1 = (e & 1) ? Xo : X, x2 = (e & 1) ? X : Xo;
       const float z = 0.5f * (x2 - x1), u = p.hvdc_u[h];
       if (dmask) dmask[i] = clip_code(z, -u, u);
       const float f = fminf(fmaxf(z, -u), u);
@@ -374,7 +413,7 @@ __global__ void __launch_bounds__(TBI) fwd_inner(DP p, St s, St nx, const float 
 
 // step 3 for the lines: v += theta - theta_bar (after fwd_avg of the new
 // state; fwd_avg updates u)
-__global__ void fwd_upd_lines(DP p, St s, St nx) {
+__global__ void __launch_bounds__(TB, 8) fwd_upd_lines(DP p, St s, St nx) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
@@ -391,13 +430,16 @@ __global__ void fwd_upd_lines(DP p, St s, St nx) {
 // The reverse pass of iteration i runs in two halves.  The first: the
 // adjoints of the new node averages, the line prox and the device proxes
 // transposed (bwd_node1, bwd_line1, bwd_dev), then the inner ADMM.  The
-// second: gathers at the nodes and their scatter back to the line and device
-// values (bwd_node2, bwd_line2, bwd_dev2).  Each second-half kernel also runs
+// second: gathers at the nodes (bwd_node2 for the line terms, on a second
+// stream beside the inner ADMM, which it does not touch; bwd_node3 for the
+// device terms after it) and their scatter back to the line and device
+// values (bwd_line2, and bwd_dev2 beside it on the second stream: their
+// writes are disjoint).  bwd_node2, bwd_line2 and bwd_dev2 also run
 // iteration i-1's first-half step on the same item when `nxt` is set, so a
-// reverse iteration takes four launches instead of seven; the arithmetic is
+// reverse iteration takes five launches instead of seven; the arithmetic is
 // the same device functions either way, so the results are the same bit for
 // bit.  The adjoint of the new pbar' through u' = u + pbar' is u's adjoint
-// itself: the kernels read it from a.LU (as `A`) before bwd_node2 adds to it.
+// itself: the kernels read it from a.LU (as `A`) before bwd_node3 adds to it.
 
 // B = d/d theta_bar' through v' = v + theta' - theta_bar' at node item
 // (k, n, t): minus the v adjoints of the node's line terminals
@@ -410,7 +452,7 @@ __device__ __forceinline__ float node_b(const DP &p, const Adj &a, int k, int n,
   return -s;
 }
 
-__global__ void bwd_node1(DP p, Adj a, float *B) {
+__global__ void __launch_bounds__(TB, 8) bwd_node1(DP p, Adj a, float *B) {
   GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
@@ -419,12 +461,12 @@ __global__ void bwd_node1(DP p, Adj a, float *B) {
 }
 
 // the line prox backwards at item i = (k, l, t), given the adjoints of the
-// step's outputs p, theta_1, theta_2 (lp0, lt10, lt20); X1.. receive
-// d/d(x1, x2, y1, y2) for the node gathers.  lmask (optional): the forward's
+// step's outputs p, theta_1, theta_2 (lp0, lt10, lt20); X2, Y1, Y2 receive
+// d/d(x2, y1, y2) for the node gathers (d/d x1 = -d/d x2).  lmask (optional): the forward's
 // record of the iteration's line clips, else the unclipped flow is
 // recomputed from the step's input state s
 __device__ __forceinline__ void line_back(const DP &p, const St &s, const Adj &a, const float *A, const float *B,
-                                          float *X1, float *X2, float *Y1, float *Y2, float *GU,
+                                          float *X2, float *Y1, float *Y2, float *GU,
                                           const unsigned char *lmask, unsigned i, int k, int l, int t, float lp0,
                                           float lt10, float lt20) {
   const int n1 = p.n1[l], n2 = p.n2[l];
@@ -453,7 +495,6 @@ __device__ __forceinline__ void line_back(const DP &p, const St &s, const Adj &a
     ly1 = lt1;
     ly2 = lt2;
   }
-  X1[i] = lx1;
   X2[i] = lx2;
   Y1[i] = ly1;
   Y2[i] = ly2;
@@ -462,22 +503,20 @@ __device__ __forceinline__ void line_back(const DP &p, const St &s, const Adj &a
   a.LV2[i] -= ly2;
 }
 
-__global__ void bwd_line1(DP p, St s, Adj a, const float *A, const float *B, float *X1, float *X2, float *Y1,
-                          float *Y2, float *GU, const unsigned char *lmask) {
+__global__ void __launch_bounds__(TB, 8) bwd_line1(DP p, St s, Adj a, const float *A, const float *B, float *X2,
+                                                   float *Y1, float *Y2, float *GU, const unsigned char *lmask) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
-    line_back(p, s, a, A, B, X1, X2, Y1, Y2, GU, lmask, i, k, l, t, a.LP[i], a.LT1[i], a.LT2[i]);
+    line_back(p, s, a, A, B, X2, Y1, Y2, GU, lmask, i, k, l, t, a.LP[i], a.LT1[i], a.LT2[i]);
   }
 }
 
-// lpd + sum over contingencies of V at device d's node, divided by the
-// node's terminal count (the k-average's adjoint)
+// lpd + the sum over contingencies of V at device d's node, divided by the
+// node's terminal count (the k-average's adjoint; every lane of the group)
 __device__ __forceinline__ float add_node_k(const DP &p, const float *V, int d, int t, float lpd) {
   const int n = p.dnode[d];
-#pragma unroll 4
-  for (int k = 0; k < p.Kp; ++k) lpd += V[ni(p, k, n, t)] / p.cnt[n];
-  return lpd;
+  return lpd + ksum(p, V, nullptr, n, t) / p.cnt[n];
 }
 
 // the closed-form device proxes backwards at item i = (d, t), given the
@@ -486,25 +525,25 @@ __device__ __forceinline__ float add_node_k(const DP &p, const float *V, int d, 
 // the adjoint of its output for bwd_inner (and, without a record, X).
 // dmask (optional): the forward's record of the iteration's device clips
 // (the inner-ADMM devices then need no X either: their clipped rows are
-// recorded too); else X is recomputed from the step's input state s
-__device__ __forceinline__ void dev_back(const DP &p, const St &s, float *LX, float *GL, float *GP, float *XD,
-                                         float *LPDT, const unsigned char *dmask, unsigned i, int d, int t, float lpd,
-                                         float lpd_o) {
-  const float X = dmask ? 0.f : dev_x(p, s, d, t);
+// recorded too); else the caller passes X (and the HVDC partner's, Xo)
+// recomputed from the step's input state.  One lane per device step.
+__device__ __forceinline__ void dev_back(const DP &p, float *LX, float *GL, float *GP, float *XD, float *LPDT,
+                                         const unsigned char *dmask, unsigned i, int d, int t, float lpd, float lpd_o,
+                                         float X, float Xo) {
   if (p.kind[d] == 1) {
     if (!dmask) XD[i] = X;
     LPDT[i] = lpd;
     return;
   }
   if (p.kind[d] == 2) {                  // HVDC: both terminals' adjoints meet in d/d p2
-    const int e = d - (p.G + p.D + p.B), d1 = d - (e & 1), h = e >> 1;
+    const int e = d - (p.G + p.D + p.B), h = e >> 1;
     const float l1 = (e & 1) ? lpd_o : lpd, l2 = (e & 1) ? lpd : lpd_o;
     const float u = p.hvdc_u[h];
     unsigned char code;
     if (dmask) {
       code = dmask[i];
     } else {
-      const float x1 = (e & 1) ? dev_x(p, s, d1, t) : X, x2 = (e & 1) ? X : dev_x(p, s, d1 + 1, t);
+      const float x1 = (e & 1) ? Xo : X, x2 = (e & 1) ? X : Xo;
       code = clip_code(0.5f * (x2 - x1), -u, u);
     }
     const float lz = code == CLIP_IN ? 0.5f * (l2 - l1) : 0.f;
@@ -530,20 +569,14 @@ __device__ __forceinline__ void dev_back(const DP &p, const St &s, float *LX, fl
   LX[i] = lx;
 }
 
-// the HVDC partner of terminal d (its index), or -1
-__device__ __forceinline__ int hvdc_partner(const DP &p, int d) {
-  if (p.kind[d] != 2) return -1;
-  const int e = d - (p.G + p.D + p.B);
-  return (e & 1) ? d - 1 : d + 1;
-}
-
 __global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL, float *GP, float *XD, float *LPDT,
                         const unsigned char *dmask) {
-  GRID_STRIDE(i, (long long)p.S * p.T) {
+  GROUP_STRIDE(i, (long long)p.S * p.T) {
     const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T), d2 = hvdc_partner(p, d);
     const float lpd = add_node_k(p, A, d, t, a.LPD[i]);
     const float lpd_o = d2 < 0 ? 0.f : add_node_k(p, A, d2, t, a.LPD[(size_t)d2 * p.T + t]);
-    dev_back(p, s, LX, GL, GP, XD, LPDT, dmask, i, d, t, lpd, lpd_o);
+    const float X = dmask ? 0.f : dev_x(p, s, d, t), Xo = (dmask || d2 < 0) ? 0.f : dev_x(p, s, d2, t);
+    if (!(threadIdx.x & (KL - 1))) dev_back(p, LX, GL, GP, XD, LPDT, dmask, i, d, t, lpd, lpd_o, X, Xo);
   }
 }
 
@@ -1331,35 +1364,49 @@ __global__ void __launch_bounds__(TB, 1) bwd_inner_r(DP p, St s, Adj a, const fl
   }
 }
 
-// gathers at the nodes: C = d/d pbar (old), D = d/d theta_bar (old); u's
-// adjoint.  nxt: also iteration i-1's B (bwd_node1: the v adjoints are final
-// after bwd_line1 of iteration i)
-__global__ void bwd_node2(DP p, Adj a, const float *X1, const float *X2, const float *Y1, const float *Y2,
-                          const float *LX, float *C, float *Dt, float *B, int nxt) {
+// gathers at the nodes of the line terms: C = -sum of the terminals' d/d x
+// (completed by bwd_node3), D = d/d theta_bar (old).  nxt: also iteration
+// i-1's B (bwd_node1: the v adjoints are final after bwd_line1 of iteration
+// i).  It reads nothing the inner ADMM writes, and runs beside it.
+__global__ void __launch_bounds__(TB, 8) bwd_node2(DP p, Adj a, const float *X2, const float *Y1, const float *Y2,
+                                                   float *C, float *Dt, float *B, int nxt) {
   GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
-    float sx = 0.f, sy = 0.f, sd = 0.f;
+    float sx = 0.f, sy = 0.f;
     for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
       const int c = p.lcode[j];
       const size_t o = li(p, k, c >> 1, t);
-      sx += (c & 1) ? X2[o] : X1[o];
+      sx += (c & 1) ? X2[o] : -X2[o];
       sy += (c & 1) ? Y2[o] : Y1[o];
     }
-    for (int j = p.dptr[n]; j < p.dptr[n + 1]; ++j) sd += LX[(size_t)p.didx[j] * p.T + t];
-    sd /= (float)p.Kp;
-    C[i] = -sx - sd;                     // x = ... - pbar - u, X = ... - avg_k(pbar + u)
-    a.LU[i] += -sx - sd;
+    C[i] = -sx;
     Dt[i] = sy;                          // y = theta_bar - v
     if (nxt) B[i] = node_b(p, a, k, n, t);
+  }
+}
+
+// ... and of the devices' terms once the inner ADMM is done: C = d/d pbar
+// (old) = -sx - avg_k(the node's devices' d/dX) (x = ... - pbar - u, X = ...
+// - avg_k(pbar + u)), which is also u's adjoint's increment
+__global__ void __launch_bounds__(TB, 8) bwd_node3(DP p, Adj a, const float *LX, float *C) {
+  GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
+    const unsigned q = i / (unsigned)p.T;
+    const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N);
+    float sd = 0.f;
+    for (int j = p.dptr[n]; j < p.dptr[n + 1]; ++j) sd += LX[(size_t)p.didx[j] * p.T + t];
+    sd /= (float)p.Kp;
+    const float c = C[i] - sd;
+    C[i] = c;
+    a.LU[i] += c;
   }
 }
 
 // the old node averages back onto the old line values; nxt: then iteration
 // i-1's line prox backwards on the same item (bwd_line1), from state s and
 // record lmask of that iteration
-__global__ void bwd_line2(DP p, St s, Adj a, const float *C, const float *Dt, const float *A, const float *B,
-                          float *X1, float *X2, float *Y1, float *Y2, float *GU, const unsigned char *lmask, int nxt) {
+__global__ void __launch_bounds__(TB, 8) bwd_line2(DP p, St s, Adj a, const float *C, const float *Dt, const float *A, const float *B,
+                          float *X2, float *Y1, float *Y2, float *GU, const unsigned char *lmask, int nxt) {
   GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
@@ -1369,7 +1416,7 @@ __global__ void bwd_line2(DP p, St s, Adj a, const float *C, const float *Dt, co
     const float lt1 = p.cth[n1] > 0.f ? Dt[o1] / p.cth[n1] : 0.f;
     const float lt2 = p.cth[n2] > 0.f ? Dt[o2] / p.cth[n2] : 0.f;
     if (nxt) {
-      line_back(p, s, a, A, B, X1, X2, Y1, Y2, GU, lmask, i, k, l, t, lp, lt1, lt2);
+      line_back(p, s, a, A, B, X2, Y1, Y2, GU, lmask, i, k, l, t, lp, lt1, lt2);
     } else {
       a.LP[i] = lp;
       a.LT1[i] = lt1;
@@ -1382,17 +1429,20 @@ __global__ void bwd_line2(DP p, St s, Adj a, const float *C, const float *Dt, co
 // iteration i-1's device proxes backwards on the same item (bwd_dev), into
 // LXn, from state s and record dmask of that iteration.  An HVDC terminal
 // recomputes its partner's adjoint from the same inputs.
-__global__ void bwd_dev2(DP p, St s, Adj a, const float *LX, const float *C, const float *A, float *LXn, float *GL,
+__global__ void __launch_bounds__(TB, 8) bwd_dev2(DP p, St s, Adj a, const float *LX, const float *C, const float *A, float *LXn, float *GL,
                          float *GP, float *XD, float *LPDT, const unsigned char *dmask, int nxt) {
-  GRID_STRIDE(i, (long long)p.S * p.T) {
+  GROUP_STRIDE(i, (long long)p.S * p.T) {
     const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T);
+    const bool lead = !(threadIdx.x & (KL - 1));
     const float lpd = add_node_k(p, C, d, t, LX[i]);
-    a.LPD[i] = lpd;
+    if (lead) a.LPD[i] = lpd;
     if (nxt) {
       const int d2 = hvdc_partner(p, d);
       const size_t o2 = (size_t)d2 * p.T + t;
       const float lpd_o = d2 < 0 ? 0.f : add_node_k(p, A, d2, t, add_node_k(p, C, d2, t, LX[o2]));
-      dev_back(p, s, LXn, GL, GP, XD, LPDT, dmask, i, d, t, add_node_k(p, A, d, t, lpd), lpd_o);
+      const float lpdn = add_node_k(p, A, d, t, lpd);
+      const float X = dmask ? 0.f : dev_x(p, s, d, t), Xo = (dmask || d2 < 0) ? 0.f : dev_x(p, s, d2, t);
+      if (lead) dev_back(p, LXn, GL, GP, XD, LPDT, dmask, i, d, t, lpdn, lpd_o, X, Xo);
     }
   }
 }
@@ -1458,6 +1508,10 @@ size_t bwd_inner_smem(int T, int n, int m, int nnz, int level) {
 struct opf_diff {
   int N = 0, L = 0, T = 0, Kp = 0, G = 0, D = 0, B = 0, H = 0, S = 0, ckpt = 1;
   cudaStream_t stream = nullptr;
+  // the reverse pass runs the node gathers of the line terms here, beside
+  // the inner ADMM on `stream` (created by the first gradient call)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   DP p{};
   std::vector<float> ga, gb, voll, load_p, gpmax, lu, scost;  // host copies (cost and defaults)
   std::vector<double> gpmin, ramp, sP, sdur;                 // right-hand sides of the inner rows
@@ -1669,7 +1723,7 @@ void forward_step(const opf_diff *d, const St &s, const St &nx, float *XD, float
   unsigned char *dmask = mask ? lmask + nl : nullptr;
   unsigned long long *rrec = reinterpret_cast<unsigned long long *>(mask);
   fwd_line<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx, lmask);
-  fwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, nx, XD, dmask);
+  fwd_dev<<<grid_for(ns * KL), TB, 0, d->stream>>>(p, s, nx, XD, dmask);
   if (p.n_inner) {
     const int g = (p.n_inner + RWARPS - 1) / RWARPS;
     switch (p.reg_c) {
@@ -2050,7 +2104,7 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   const size_t KLT = (size_t)d->Kp * d->L * T, KNT = (size_t)d->Kp * d->N * T, ST = (size_t)d->S * T;
   const size_t MT = (size_t)d->Mtot;
   const size_t adj_floats = 5 * KLT + ST + KNT + 2 * MT;
-  const size_t work_floats = 5 * KLT + 3 * KNT + 4 * ST + DT + GT + MT + BT;
+  const size_t work_floats = 4 * KLT + 3 * KNT + 4 * ST + DT + GT + MT + BT;
   const bool grads = g_load || g_pmax || g_u;
   size_t adj_cap = d->adj ? adj_floats : 0, work_cap = d->work ? work_floats : 0, gl_cap = d->gline ? L : 0;
   cudaError_t e = ensure(&d->ck, &d->ck_cap, (size_t)n_ck * SF);
@@ -2070,7 +2124,7 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   unsigned char *masks = rec ? reinterpret_cast<unsigned char *>(d->masks) : nullptr;
   auto mask_of = [&](int i) { return masks ? masks + (size_t)(i - 1) * mask_iter : nullptr; };   // iteration i
   float *ck = d->ck, *seg = d->seg, *adj = d->adj, *work = d->work;
-  float *X1 = work, *X2 = X1 + KLT, *Y1 = X2 + KLT, *Y2 = Y1 + KLT, *GU = Y2 + KLT;
+  float *X2 = work, *Y1 = X2 + KLT, *Y2 = Y1 + KLT, *GU = Y2 + KLT;
   float *Bn = GU + KLT, *Cn = Bn + KNT, *Dn = Cn + KNT, *LX0 = Dn + KNT, *LX1 = LX0 + ST, *XD = LX1 + ST;
   float *LPDT = XD + ST, *GL = LPDT + ST, *GP = GL + DT, *HB = GP + GT, *DEL = HB + MT;
   auto ckst = [&](int j) { return carve_state(d, ck + (size_t)j * SF); };
@@ -2108,6 +2162,13 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
     *cost = f;
   }
   if (!grads) return OPF_OK;
+  {
+    cudaError_t ce = cudaSuccess;
+    if (!d->aux) ce = cudaStreamCreateWithFlags(&d->aux, cudaStreamNonBlocking);
+    if (ce == cudaSuccess && !d->ev_fork) ce = cudaEventCreateWithFlags(&d->ev_fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess && !d->ev_join) ce = cudaEventCreateWithFlags(&d->ev_join, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return dfail(OPF_ECUDA, cudaGetErrorString(ce));
+  }
   // reverse pass
   Adj a;
   a.LP = adj;
@@ -2139,9 +2200,19 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
       if (!primed) {
         const unsigned char *lmask = mi ? mi + inner_record_bytes(p) : nullptr, *dmask = mi ? lmask + KLT : nullptr;
         bwd_node1<<<grid_for(nn), TB, 0, d->stream>>>(p, a, Bn);
-        bwd_line1<<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, Bn, X1, X2, Y1, Y2, GU, lmask);
-        bwd_dev<<<grid_for(ns), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT, dmask);
+        bwd_line1<<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, Bn, X2, Y1, Y2, GU, lmask);
+        bwd_dev<<<grid_for(ns * KL), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT, dmask);
       }
+      // iteration i - 1's first half joins this second half when what it
+      // reads is at hand: its record, or its input state i - 2 in this segment
+      unsigned char *mp = i > 1 ? mask_of(i - 1) : nullptr;
+      const int nxt = i > 1 && (mp || i - 2 >= lo) ? 1 : 0;
+      // the node gathers of the line terms beside the inner ADMM
+      if (e == cudaSuccess) e = cudaEventRecord(d->ev_fork, d->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(d->aux, d->ev_fork, 0);
+      if (e != cudaSuccess) break;
+      bwd_node2<<<grid_for(nn), TB, 0, d->aux>>>(p, a, X2, Y1, Y2, Cn, Dn, Bn, nxt);
+      e = cudaEventRecord(d->ev_join, d->aux);
       if (p.n_inner) {
         const int g = (p.n_inner + RWARPS - 1) / RWARPS, lst = i == K ? 1 : 0;
         unsigned long long *m1 = reinterpret_cast<unsigned long long *>(d->mask1);
@@ -2156,15 +2227,19 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
             break;
         }
       }
-      // iteration i - 1's first half joins this second half when what it
-      // reads is at hand: its record, or its input state i - 2 in this segment
-      unsigned char *mp = i > 1 ? mask_of(i - 1) : nullptr;
-      const int nxt = i > 1 && (mp || i - 2 >= lo) ? 1 : 0;
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(d->stream, d->ev_join, 0);
+      if (e != cudaSuccess) break;
       const St sp = nxt && i - 2 >= lo ? state(i - 2) : s;   // read only without a record
       const unsigned char *lmp = mp ? mp + inner_record_bytes(p) : nullptr, *dmp = mp ? lmp + KLT : nullptr;
-      bwd_node2<<<grid_for(nn), TB, 0, d->stream>>>(p, a, X1, X2, Y1, Y2, LX, Cn, Dn, Bn, nxt);
-      bwd_line2<<<grid_for(nl), TB, 0, d->stream>>>(p, sp, a, Cn, Dn, A, Bn, X1, X2, Y1, Y2, GU, lmp, nxt);
-      bwd_dev2<<<grid_for(ns), TB, 0, d->stream>>>(p, sp, a, LX, Cn, A, LXn, GL, GP, XD, LPDT, dmp, nxt);
+      bwd_node3<<<grid_for(nn), TB, 0, d->stream>>>(p, a, LX, Cn);
+      // the scatters to the devices beside those to the lines (disjoint writes)
+      e = cudaEventRecord(d->ev_fork, d->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(d->aux, d->ev_fork, 0);
+      if (e != cudaSuccess) break;
+      bwd_dev2<<<grid_for(ns * KL), TB, 0, d->aux>>>(p, sp, a, LX, Cn, A, LXn, GL, GP, XD, LPDT, dmp, nxt);
+      e = cudaEventRecord(d->ev_join, d->aux);
+      bwd_line2<<<grid_for(nl), TB, 0, d->stream>>>(p, sp, a, Cn, Dn, A, Bn, X2, Y1, Y2, GU, lmp, nxt);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(d->stream, d->ev_join, 0);
       primed = nxt != 0;
     }
     hi = lo;
@@ -2207,6 +2282,10 @@ opf_status opf_diff_set_record_limit(opf_diff *d, int64_t bytes) {
 void opf_diff_destroy(opf_diff *d) {
   if (!d) return;
   cudaStreamSynchronize(d->stream);
+  if (d->aux) cudaStreamSynchronize(d->aux);
+  if (d->ev_fork) cudaEventDestroy(d->ev_fork);
+  if (d->ev_join) cudaEventDestroy(d->ev_join);
+  if (d->aux) cudaStreamDestroy(d->aux);
   for (void *q : d->allocs) cudaFree(q);
   for (float *q : {d->ck, d->seg, d->adj, d->work, d->gline, d->masks})
     if (q) cudaFree(q);
