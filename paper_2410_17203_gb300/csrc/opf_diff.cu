@@ -2107,17 +2107,17 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   const size_t work_floats = 4 * KLT + 3 * KNT + 4 * ST + DT + GT + MT + BT;
   const bool grads = g_load || g_pmax || g_u;
   size_t adj_cap = d->adj ? adj_floats : 0, work_cap = d->work ? work_floats : 0, gl_cap = d->gline ? L : 0;
-  cudaError_t e = ensure(&d->ck, &d->ck_cap, (size_t)n_ck * SF);
-  if (e == cudaSuccess) e = ensure(&d->seg, &d->seg_cap, (size_t)(grads ? std::max(C, 2) : 2) * SF);
-  if (e == cudaSuccess) e = ensure(&d->adj, &adj_cap, adj_floats);
-  if (e == cudaSuccess) e = ensure(&d->work, &work_cap, work_floats);
-  if (e == cudaSuccess) e = ensure(&d->gline, &gl_cap, L);
   // the forward pass records which inner rows clipped and where each line's
   // and closed-form device's unclipped value lay, so that the reverse pass
   // need not run each iteration's inner ADMM again nor recompute the prox
-  // inputs (while the record stays within the context's limit)
+  // inputs, nor the states (while the record stays within the context's limit)
   const size_t mask_iter = (inner_record_bytes(p) + KLT + ST + 255) & ~size_t(255);
   const bool rec = grads && (size_t)K * mask_iter <= d->record_limit;
+  cudaError_t e = ensure(&d->ck, &d->ck_cap, (size_t)n_ck * SF);
+  if (e == cudaSuccess) e = ensure(&d->seg, &d->seg_cap, (size_t)(grads && !rec ? std::max(C, 2) : 2) * SF);
+  if (e == cudaSuccess) e = ensure(&d->adj, &adj_cap, adj_floats);
+  if (e == cudaSuccess) e = ensure(&d->work, &work_cap, work_floats);
+  if (e == cudaSuccess) e = ensure(&d->gline, &gl_cap, L);
   if (e == cudaSuccess && rec) e = ensure(&d->masks, &d->masks_cap, ((size_t)K * mask_iter + 3) / 4);
   if (e != cudaSuccess)
     return dfail(e == cudaErrorMemoryAllocation ? OPF_ENOMEM : OPF_ECUDA, "diff: device allocation failed");
@@ -2189,10 +2189,13 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   bool primed = false;   // iteration i's first half already ran, fused into iteration i+1's second half
   for (int hi = K; e == cudaSuccess && hi > 0;) {
     // segment (lo, hi]: states lo + 1 .. hi - 1 recomputed from checkpoint lo
-    // (read in place)
+    // (read in place).  With the record the reverse pass reads no state (the
+    // clips, and the inner rows that clipped, are all it needs), so nothing
+    // is recomputed and every kernel is handed checkpoint lo, unread.
     const int lo = ((hi - 1) / C) * C;
-    auto state = [&](int j) { return j == lo ? ckst(lo / C) : sgst(j - lo); };   // state j, lo <= j < hi
-    for (int i = lo + 1; e == cudaSuccess && i < hi; ++i) forward_step(d, state(i - 1), sgst(i - lo), XD, DEL);
+    auto state = [&](int j) { return (j == lo || masks) ? ckst(lo / C) : sgst(j - lo); };   // state j, lo <= j < hi
+    for (int i = lo + 1; e == cudaSuccess && !masks && i < hi; ++i)
+      forward_step(d, state(i - 1), sgst(i - lo), XD, DEL);
     for (int i = hi; e == cudaSuccess && i > lo; --i) {
       const St s = state(i - 1);
       unsigned char *mi = mask_of(i);

@@ -76,8 +76,9 @@ def test_base_case_only_and_single_step():
 def test_checkpointing_is_exact():
     """Recomputed segments repeat the forward pass bit for bit, so the
     gradients do not depend on the checkpoint spacing, nor on whether the
-    reverse pass reads the forward's record of clipped values or recomputes
-    them (record limit 0; a limit too small for this call)."""
+    reverse pass reads the forward's record of clipped values (and then no
+    state, so nothing is recomputed) or recomputes them (record limit 0; a
+    limit too small for this call)."""
     b = _lib()
     case = make_case(scale_case(120, 4, 3, seed=8, ramp=True, stor_per_node=0.05, fixed_frac=0.3, n_hvdc=2))
     outs = []
