@@ -49,6 +49,9 @@ struct DP {
   const int *lptr, *lcode;             // node -> line terminal codes 2 l + end (end 1: terminal 2)
   const int *dptr, *didx;              // node -> devices
   const float *cnt, *cth;              // terminals at a node: all, line (0: none)
+  // the reverse pass's factors: 1 / cnt, 1 / cth (0 for none) [N]; per line
+  // 1 / (2b), rho_p / den, rho_theta / (2b den) [3][L]
+  const float *icnt, *icth, *lfac;
   const int *dnode;                    // device node [S]
   const int *kind;                     // [S] 0: closed-form prox, 1: inner ADMM, 2: HVDC terminal
   const float *hvdc_u;                 // [H]
@@ -471,21 +474,21 @@ __device__ __forceinline__ void line_back(const DP &p, const St &s, const Adj &a
                                           float lt10, float lt20) {
   const int n1 = p.n1[l], n2 = p.n2[l];
   const size_t o1 = ni(p, k, n1, t), o2 = ni(p, k, n2, t);
-  const float lp = lp0 - A[o1] / p.cnt[n1] + A[o2] / p.cnt[n2];
-  const float lt1 = lt10 + a.LV1[i] + (p.cth[n1] > 0.f ? B[o1] / p.cth[n1] : 0.f);
-  const float lt2 = lt20 + a.LV2[i] + (p.cth[n2] > 0.f ? B[o2] / p.cth[n2] : 0.f);
+  const float lp = fmaf(A[o2], p.icnt[n2], fmaf(-A[o1], p.icnt[n1], lp0));
+  const float lt1 = fmaf(B[o1], p.icth[n1], __fadd_rn(lt10, a.LV1[i]));
+  const float lt2 = fmaf(B[o2], p.icth[n2], __fadd_rn(lt20, a.LV2[i]));
   float lx1 = 0.f, lx2 = 0.f, ly1, ly2;
   if (p.out[k] != l) {
     const float b = p.b[l], tb = 2.f * b, u = p.lu[l];
     const float den = line_den(p, b, tb);
     const unsigned char code = lmask ? lmask[i] : clip_code(line_z(p, line_inputs(p, s, k, l, t), tb, den), -u, u);
-    const float lpt = lp + (lt1 - lt2) / tb;     // theta_{1,2} = mid +- p / (2b)
+    const float lpt = fmaf(lt1 - lt2, p.lfac[l], lp);     // theta_{1,2} = mid +- p / (2b)
     const float half = __fmul_rn(0.5f, lt1 + lt2);
     ly1 = ly2 = half;
     if (code == CLIP_IN) {
-      lx2 = p.rp * lpt / den;
+      lx2 = __fmul_rn(lpt, p.lfac[p.L + l]);
       lx1 = -lx2;
-      const float w = p.rt * lpt / (tb * den);
+      const float w = __fmul_rn(lpt, p.lfac[2 * p.L + l]);
       ly1 = __fadd_rn(half, w);
       ly2 = __fsub_rn(half, w);
     } else {
@@ -516,7 +519,7 @@ __global__ void __launch_bounds__(TB, 8) bwd_line1(DP p, St s, Adj a, const floa
 // node's terminal count (the k-average's adjoint; every lane of the group)
 __device__ __forceinline__ float add_node_k(const DP &p, const float *V, int d, int t, float lpd) {
   const int n = p.dnode[d];
-  return lpd + ksum(p, V, nullptr, n, t) / p.cnt[n];
+  return fmaf(ksum(p, V, nullptr, n, t), p.icnt[n], lpd);
 }
 
 // the closed-form device proxes backwards at item i = (d, t), given the
@@ -1412,9 +1415,9 @@ __global__ void __launch_bounds__(TB, 8) bwd_line2(DP p, St s, Adj a, const floa
     const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
     const int n1 = p.n1[l], n2 = p.n2[l];
     const size_t o1 = ni(p, k, n1, t), o2 = ni(p, k, n2, t);
-    const float lp = a.LP[i] + (-C[o1] / p.cnt[n1] + C[o2] / p.cnt[n2]);
-    const float lt1 = p.cth[n1] > 0.f ? Dt[o1] / p.cth[n1] : 0.f;
-    const float lt2 = p.cth[n2] > 0.f ? Dt[o2] / p.cth[n2] : 0.f;
+    const float lp = __fadd_rn(a.LP[i], fmaf(C[o2], p.icnt[n2], -__fmul_rn(C[o1], p.icnt[n1])));
+    const float lt1 = __fmul_rn(Dt[o1], p.icth[n1]);
+    const float lt2 = __fmul_rn(Dt[o2], p.icth[n2]);
     if (nxt) {
       line_back(p, s, a, A, B, X2, Y1, Y2, GU, lmask, i, k, l, t, lp, lt1, lt2);
     } else {
@@ -2005,6 +2008,22 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   U(&p.didx, didx);
   U(&p.cnt, cnt);
   U(&p.cth, cth);
+  {
+    std::vector<float> ic(N), ih(N), lf(3 * (size_t)L);
+    for (int n = 0; n < N; ++n) {
+      ic[n] = (float)(1.0 / cnt[n]);
+      ih[n] = cth[n] > 0.f ? (float)(1.0 / cth[n]) : 0.f;
+    }
+    for (int l = 0; l < L; ++l) {
+      const double bl = b[l], tb = 2.0 * bl, den = 2.0 * rho_p + rho_theta / (tb * bl);
+      lf[l] = (float)(1.0 / tb);
+      lf[L + l] = (float)(rho_p / den);
+      lf[2 * (size_t)L + l] = (float)(rho_theta / (tb * den));
+    }
+    U(&p.icnt, ic);
+    U(&p.icth, ih);
+    U(&p.lfac, lf);
+  }
   U(&p.dnode, dnode);
   U(&p.kind, kind);
   U(&p.ga, d->ga);
