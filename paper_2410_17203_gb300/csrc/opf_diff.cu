@@ -102,6 +102,12 @@ constexpr int KL = 8;
 #define GROUP_STRIDE(i, n)                                                                   \
   for (unsigned i = (blockIdx.x * TB + threadIdx.x) / KL, n_##i = (unsigned)(n); i < n_##i; \
        i += gridDim.x * (TB / KL))
+// the same loops over blocks bid of nb (a kernel whose blocks take two roles)
+#define GRID_STRIDE_B(i, n, bid, nb) \
+  for (unsigned i = (bid) * TB + threadIdx.x, n_##i = (unsigned)(n); i < n_##i; i += (nb) * TB)
+#define GROUP_STRIDE_B(i, n, bid, nb)                                                   \
+  for (unsigned i = ((bid) * TB + threadIdx.x) / KL, n_##i = (unsigned)(n); i < n_##i; \
+       i += (nb) * (TB / KL))
 
 __device__ __forceinline__ unsigned group_mask() { return 0xFFu << ((threadIdx.x & 31) & ~(KL - 1)); }
 
@@ -128,7 +134,8 @@ __device__ __forceinline__ float ksum(const DP &p, const float *V, const float *
 // ---------------------------------------------------------------------------
 
 // node averages (Eq. average-op) of the terminal values of the new state nx,
-// and the price update u' = u + pbar' (step 3) from the old state s
+// and the price updates u' = u + pbar', v' = v + theta' - theta_bar' (step
+// 3) from the old state s
 __global__ void __launch_bounds__(TB, 8) fwd_avg(DP p, St s, St nx) {
   GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
     const unsigned q = i / (unsigned)p.T;
@@ -142,9 +149,18 @@ __global__ void __launch_bounds__(TB, 8) fwd_avg(DP p, St s, St nx) {
       st += (c & 1) ? nx.TH2[li(p, k, l, t)] : nx.TH1[li(p, k, l, t)];
     }
     const float pb = sp / p.cnt[n];
+    const float tbr = p.cth[n] > 0.f ? st / p.cth[n] : 0.f;
     nx.PB[i] = pb;
-    nx.TBR[i] = p.cth[n] > 0.f ? st / p.cth[n] : 0.f;
+    nx.TBR[i] = tbr;
     nx.U[i] = s.U[i] + pb;
+    // v' = v + theta' - theta_bar' of the node's line terminals (each
+    // terminal belongs to one node, so every v entry is written once)
+    for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
+      const int c = p.lcode[j];
+      const size_t o = li(p, k, c >> 1, t);
+      if (c & 1) nx.V2[o] = s.V2[o] + nx.TH2[o] - tbr;
+      else nx.V1[o] = s.V1[o] + nx.TH1[o] - tbr;
+    }
   }
 }
 
@@ -414,17 +430,6 @@ __global__ void __launch_bounds__(TBI) fwd_inner(DP p, St s, St nx, const float 
   }
 }
 
-// step 3 for the lines: v += theta - theta_bar (after fwd_avg of the new
-// state; fwd_avg updates u)
-__global__ void __launch_bounds__(TB, 8) fwd_upd_lines(DP p, St s, St nx) {
-  GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
-    const unsigned q = i / (unsigned)p.T;
-    const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
-    nx.V1[i] = s.V1[i] + nx.TH1[i] - nx.TBR[ni(p, k, p.n1[l], t)];
-    nx.V2[i] = s.V2[i] + nx.TH2[i] - nx.TBR[ni(p, k, p.n2[l], t)];
-  }
-}
-
 // ---------------------------------------------------------------------------
 // reverse pass of one iteration: the adjoint of state i in `a` becomes the
 // adjoint of state i-1; s is state i-1
@@ -436,10 +441,9 @@ __global__ void __launch_bounds__(TB, 8) fwd_upd_lines(DP p, St s, St nx) {
 // second: gathers at the nodes (bwd_node2 for the line terms, on a second
 // stream beside the inner ADMM, which it does not touch; bwd_node3 for the
 // device terms after it) and their scatter back to the line and device
-// values (bwd_line2, and bwd_dev2 beside it on the second stream: their
-// writes are disjoint).  bwd_node2, bwd_line2 and bwd_dev2 also run
-// iteration i-1's first-half step on the same item when `nxt` is set, so a
-// reverse iteration takes five launches instead of seven; the arithmetic is
+// values (bwd_scatter, one launch for both).  bwd_node2 and bwd_scatter also
+// run iteration i-1's first-half step on the same item when `nxt` is set, so
+// a reverse iteration takes four launches instead of seven; the arithmetic is
 // the same device functions either way, so the results are the same bit for
 // bit.  The adjoint of the new pbar' through u' = u + pbar' is u's adjoint
 // itself: the kernels read it from a.LU (as `A`) before bwd_node3 adds to it.
@@ -1405,21 +1409,32 @@ __global__ void __launch_bounds__(TB, 8) bwd_node3(DP p, Adj a, const float *LX,
   }
 }
 
+// The scatters of one reverse iteration, as one launch whose first
+// dev_blocks blocks take the device items and the rest the line items (their
+// writes are disjoint; the device items, fewer and waiting longer on their
+// sums, start first).
+struct Scatter {
+  const float *C, *Dt, *A, *B, *LX;   // node gathers, u's adjoint, B of iteration i-1, this iteration's d/dX
+  float *X2, *Y1, *Y2, *GU;           // iteration i-1's line terms
+  float *LXn, *GL, *GP, *XD, *LPDT;   // iteration i-1's device terms
+  const unsigned char *lmask, *dmask; // iteration i-1's record (or NULL)
+};
+
 // the old node averages back onto the old line values; nxt: then iteration
 // i-1's line prox backwards on the same item (bwd_line1), from state s and
 // record lmask of that iteration
-__global__ void __launch_bounds__(TB, 8) bwd_line2(DP p, St s, Adj a, const float *C, const float *Dt, const float *A, const float *B,
-                          float *X2, float *Y1, float *Y2, float *GU, const unsigned char *lmask, int nxt) {
-  GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
+__device__ __forceinline__ void line2_part(const DP &p, const St &s, const Adj &a, const Scatter &g, int nxt,
+                                           unsigned bid, unsigned nb) {
+  GRID_STRIDE_B(i, (long long)p.Kp * p.L * p.T, bid, nb) {
     const unsigned q = i / (unsigned)p.T;
     const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
     const int n1 = p.n1[l], n2 = p.n2[l];
     const size_t o1 = ni(p, k, n1, t), o2 = ni(p, k, n2, t);
-    const float lp = __fadd_rn(a.LP[i], fmaf(C[o2], p.icnt[n2], -__fmul_rn(C[o1], p.icnt[n1])));
-    const float lt1 = __fmul_rn(Dt[o1], p.icth[n1]);
-    const float lt2 = __fmul_rn(Dt[o2], p.icth[n2]);
+    const float lp = __fadd_rn(a.LP[i], fmaf(g.C[o2], p.icnt[n2], -__fmul_rn(g.C[o1], p.icnt[n1])));
+    const float lt1 = __fmul_rn(g.Dt[o1], p.icth[n1]);
+    const float lt2 = __fmul_rn(g.Dt[o2], p.icth[n2]);
     if (nxt) {
-      line_back(p, s, a, A, B, X2, Y1, Y2, GU, lmask, i, k, l, t, lp, lt1, lt2);
+      line_back(p, s, a, g.A, g.B, g.X2, g.Y1, g.Y2, g.GU, g.lmask, i, k, l, t, lp, lt1, lt2);
     } else {
       a.LP[i] = lp;
       a.LT1[i] = lt1;
@@ -1432,22 +1447,27 @@ __global__ void __launch_bounds__(TB, 8) bwd_line2(DP p, St s, Adj a, const floa
 // iteration i-1's device proxes backwards on the same item (bwd_dev), into
 // LXn, from state s and record dmask of that iteration.  An HVDC terminal
 // recomputes its partner's adjoint from the same inputs.
-__global__ void __launch_bounds__(TB, 8) bwd_dev2(DP p, St s, Adj a, const float *LX, const float *C, const float *A, float *LXn, float *GL,
-                         float *GP, float *XD, float *LPDT, const unsigned char *dmask, int nxt) {
-  GROUP_STRIDE(i, (long long)p.S * p.T) {
+__device__ __forceinline__ void dev2_part(const DP &p, const St &s, const Adj &a, const Scatter &g, int nxt,
+                                          unsigned bid, unsigned nb) {
+  GROUP_STRIDE_B(i, (long long)p.S * p.T, bid, nb) {
     const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T);
     const bool lead = !(threadIdx.x & (KL - 1));
-    const float lpd = add_node_k(p, C, d, t, LX[i]);
+    const float lpd = add_node_k(p, g.C, d, t, g.LX[i]);
     if (lead) a.LPD[i] = lpd;
     if (nxt) {
       const int d2 = hvdc_partner(p, d);
       const size_t o2 = (size_t)d2 * p.T + t;
-      const float lpd_o = d2 < 0 ? 0.f : add_node_k(p, A, d2, t, add_node_k(p, C, d2, t, LX[o2]));
-      const float lpdn = add_node_k(p, A, d, t, lpd);
-      const float X = dmask ? 0.f : dev_x(p, s, d, t), Xo = (dmask || d2 < 0) ? 0.f : dev_x(p, s, d2, t);
-      if (lead) dev_back(p, LXn, GL, GP, XD, LPDT, dmask, i, d, t, lpdn, lpd_o, X, Xo);
+      const float lpd_o = d2 < 0 ? 0.f : add_node_k(p, g.A, d2, t, add_node_k(p, g.C, d2, t, g.LX[o2]));
+      const float lpdn = add_node_k(p, g.A, d, t, lpd);
+      const float X = g.dmask ? 0.f : dev_x(p, s, d, t), Xo = (g.dmask || d2 < 0) ? 0.f : dev_x(p, s, d2, t);
+      if (lead) dev_back(p, g.LXn, g.GL, g.GP, g.XD, g.LPDT, g.dmask, i, d, t, lpdn, lpd_o, X, Xo);
     }
   }
+}
+
+__global__ void __launch_bounds__(TB, 8) bwd_scatter(DP p, St s, Adj a, Scatter g, int nxt, int dev_blocks) {
+  if ((int)blockIdx.x < dev_blocks) dev2_part(p, s, a, g, nxt, blockIdx.x, dev_blocks);
+  else line2_part(p, s, a, g, nxt, blockIdx.x - dev_blocks, gridDim.x - dev_blocks);
 }
 
 // d f / d p_d at the last iterate, and f's direct dependence on P (the
@@ -1738,7 +1758,6 @@ void forward_step(const opf_diff *d, const St &s, const St &nx, float *XD, float
     }
   }
   fwd_avg<<<grid_for(nn), TB, 0, d->stream>>>(p, s, nx);
-  fwd_upd_lines<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx);
 }
 
 }  // namespace
@@ -2254,14 +2273,11 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
       const St sp = nxt && i - 2 >= lo ? state(i - 2) : s;   // read only without a record
       const unsigned char *lmp = mp ? mp + inner_record_bytes(p) : nullptr, *dmp = mp ? lmp + KLT : nullptr;
       bwd_node3<<<grid_for(nn), TB, 0, d->stream>>>(p, a, LX, Cn);
-      // the scatters to the devices beside those to the lines (disjoint writes)
-      e = cudaEventRecord(d->ev_fork, d->stream);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(d->aux, d->ev_fork, 0);
-      if (e != cudaSuccess) break;
-      bwd_dev2<<<grid_for(ns * KL), TB, 0, d->aux>>>(p, sp, a, LX, Cn, A, LXn, GL, GP, XD, LPDT, dmp, nxt);
-      e = cudaEventRecord(d->ev_join, d->aux);
-      bwd_line2<<<grid_for(nl), TB, 0, d->stream>>>(p, sp, a, Cn, Dn, A, Bn, X2, Y1, Y2, GU, lmp, nxt);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(d->stream, d->ev_join, 0);
+      {
+        const Scatter g{Cn, Dn, A, Bn, LX, X2, Y1, Y2, GU, LXn, GL, GP, XD, LPDT, lmp, dmp};
+        const int db = grid_for(ns * KL);
+        bwd_scatter<<<db + grid_for(nl), TB, 0, d->stream>>>(p, sp, a, g, nxt, db);
+      }
       primed = nxt != 0;
     }
     hi = lo;
