@@ -13,8 +13,12 @@
  * and its gradient with respect to the load power P [D][T], the generator
  * capacity pmax [G][T] and the line limits u [L], by a hand-written reverse
  * pass over the iterations (adjoint kernels of the line prox, the device
- * proxes, the node averages and the price updates).  The forward states are
- * kept every `checkpoint_every` iterations and recomputed in between.
+ * proxes, the node averages and the price updates).  The forward pass keeps
+ * a record of its clipping decisions (opf_diff_set_record_limit); the reverse
+ * pass then reads no state.  Without the record the forward states are kept
+ * every `checkpoint_every` iterations and recomputed in between.  A call
+ * uses the context's stream and a second stream of its own, created by the
+ * first gradient call; it returns after both are done.
  *
  * Every device type is covered.  Ramp-limited generators (T > 1) and
  * batteries take their prox from 10 iterations of the Appendix D inner ADMM
@@ -72,10 +76,11 @@ opf_status opf_diff_cost_grad_on(opf_diff *d, int32_t K, int32_t on_device, cons
  * the forward pass: per iteration, which inner-ADMM rows clipped (one byte
  * per row and inner iteration) and where each line's and closed-form
  * device's unclipped value lay (one byte per line item and device step).
- * With the record the reverse pass runs no inner iteration and recomputes no
- * prox input; a call whose record would exceed the limit (and every call
- * after a limit of 0) recomputes them from the states instead, with the same
- * result bit for bit.  Default 4 GiB.  OPF_EINVAL for d NULL or bytes < 0. */
+ * With the record the reverse pass runs no inner iteration, recomputes no
+ * prox input and no state; a call whose record would exceed the limit (and
+ * every call after a limit of 0) recomputes them from the checkpointed
+ * states instead, with the same result bit for bit.  Default 4 GiB.
+ * OPF_EINVAL for d NULL or bytes < 0. */
 opf_status opf_diff_set_record_limit(opf_diff *d, int64_t bytes);
 
 void opf_diff_destroy(opf_diff *d);
