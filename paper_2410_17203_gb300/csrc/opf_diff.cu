@@ -2291,7 +2291,12 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   if (e == cudaSuccess && g_pmax) e = cudaMemcpyAsync(g_pmax, GP, GT * 4, out_kind, d->stream);
   if (e == cudaSuccess && g_u) e = cudaMemcpyAsync(g_u, d->gline, L * 4, out_kind, d->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
-  if (e != cudaSuccess) return dfail(OPF_ECUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    // a failed fork or join may leave work queued on the second stream
+    cudaStreamSynchronize(d->stream);
+    cudaStreamSynchronize(d->aux);
+    return dfail(OPF_ECUDA, cudaGetErrorString(e));
+  }
   return OPF_OK;
 }
 
