@@ -27,6 +27,8 @@
  *     terminal carries -p.
  *   - All GPU work is enqueued on the stream given in opf_options; functions
  *     that return data synchronize that stream.
+ *   - A context lives on the device that is current when it is created;
+ *     calls on it are made with that device current.
  */
 #ifndef OPF_H_
 #define OPF_H_

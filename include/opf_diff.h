@@ -32,7 +32,9 @@
  * bound 0.
  *
  * Arrays are in the caller's numbering and layout (opf.h); host pointers
- * (opf_diff_cost_grad_on also takes device pointers).  The computation runs
+ * (opf_diff_cost_grad_on also takes device pointers).  A context lives on
+ * the device current at opf_diff_create; calls on it are made with that
+ * device current.  The computation runs
  * in FP32 on the device; the cost is summed in FP64, and so is the line-limit
  * gradient over contingencies and steps.
  */
