@@ -25,6 +25,7 @@ namespace {
 
 constexpr int TB = 256;       // threads per CTA of the element-wise kernels (eight per SM: they wait
                               // on gathers, so they are held to 32 registers for the most warps)
+constexpr int VW4_CTAS = 4;   // ... the line and node kernels on four steps per thread: more registers
 constexpr int TBI = 128;      // threads per CTA of the inner-ADMM kernels (one CTA per device)
 constexpr int N_INNER = 10;   // Appendix D iterations per prox evaluation (Section 4.5)
 
@@ -133,33 +134,123 @@ __device__ __forceinline__ float ksum(const DP &p, const float *V, const float *
 // forward (Section 3.2)
 // ---------------------------------------------------------------------------
 
+// The line and node kernels take VW consecutive time steps per thread: 4
+// when T is a multiple of 4 (then every row offset is a multiple of 4 floats
+// and every array starts on a 16-byte boundary, so rows move as 128-bit
+// loads and stores and an item's index arithmetic is shared by its steps),
+// else 1.  Each step's arithmetic is the same whatever VW.
+template <int VW>
+struct Vf {
+  float x[VW];
+};
+template <int VW>
+__device__ __forceinline__ Vf<VW> ldv(const float *q) {
+  Vf<VW> r;
+  if constexpr (VW == 4) {
+    const float4 f = *reinterpret_cast<const float4 *>(q);
+    r.x[0] = f.x;
+    r.x[1] = f.y;
+    r.x[2] = f.z;
+    r.x[3] = f.w;
+  } else {
+    r.x[0] = *q;
+  }
+  return r;
+}
+template <int VW>
+__device__ __forceinline__ void stv(float *q, const Vf<VW> &v) {
+  if constexpr (VW == 4) *reinterpret_cast<float4 *>(q) = make_float4(v.x[0], v.x[1], v.x[2], v.x[3]);
+  else *q = v.x[0];
+}
+template <int VW>
+struct Vb {
+  unsigned char x[VW];
+};
+template <int VW>
+__device__ __forceinline__ Vb<VW> ldb(const unsigned char *q) {
+  Vb<VW> r;
+  if constexpr (VW == 4) {
+    const uchar4 c = *reinterpret_cast<const uchar4 *>(q);
+    r.x[0] = c.x;
+    r.x[1] = c.y;
+    r.x[2] = c.z;
+    r.x[3] = c.w;
+  } else {
+    r.x[0] = *q;
+  }
+  return r;
+}
+template <int VW>
+__device__ __forceinline__ void stb(unsigned char *q, const Vb<VW> &v) {
+  if constexpr (VW == 4) *reinterpret_cast<uchar4 *>(q) = make_uchar4(v.x[0], v.x[1], v.x[2], v.x[3]);
+  else *q = v.x[0];
+}
+
+// item i of a [Kp][M][T / VW] field (M lines or nodes): its row (k, m), its
+// first step t0 and its offset in the [Kp][M][T] arrays
+struct Item {
+  int k, m, t0;
+  size_t o;
+};
+template <int VW>
+__device__ __forceinline__ Item item_of(unsigned i, int M, int T) {
+  const unsigned TV = (unsigned)(T / VW), q = i / TV;
+  Item r;
+  r.t0 = (int)(i - q * TV) * VW;
+  r.m = (int)(q % (unsigned)M);
+  r.k = (int)(q / (unsigned)M);
+  r.o = (size_t)i * VW;
+  return r;
+}
+
 // node averages (Eq. average-op) of the terminal values of the new state nx,
 // and the price updates u' = u + pbar', v' = v + theta' - theta_bar' (step
 // 3) from the old state s
-__global__ void __launch_bounds__(TB, 8) fwd_avg(DP p, St s, St nx) {
-  GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
-    const unsigned q = i / (unsigned)p.T;
-    const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
-    float sp = 0.f, st = 0.f;
-    for (int j = p.dptr[n]; j < p.dptr[n + 1]; ++j) sp += nx.PD[(size_t)p.didx[j] * p.T + t];
-    for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
-      const int c = p.lcode[j], l = c >> 1;
-      const float v = nx.P[li(p, k, l, t)];
-      sp += (c & 1) ? v : -v;
-      st += (c & 1) ? nx.TH2[li(p, k, l, t)] : nx.TH1[li(p, k, l, t)];
+template <int VW>
+__global__ void __launch_bounds__(TB, VW == 4 ? VW4_CTAS : 8) fwd_avg(DP p, St s, St nx) {
+  GRID_STRIDE(i, (long long)p.Kp * p.N * (p.T / VW)) {
+    const Item it = item_of<VW>(i, p.N, p.T);
+    const int n = it.m, k = it.k, t0 = it.t0;
+    float sp[VW], st[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) sp[e] = st[e] = 0.f;
+    for (int j = p.dptr[n]; j < p.dptr[n + 1]; ++j) {
+      const Vf<VW> v = ldv<VW>(nx.PD + (size_t)p.didx[j] * p.T + t0);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) sp[e] += v.x[e];
     }
-    const float pb = sp / p.cnt[n];
-    const float tbr = p.cth[n] > 0.f ? st / p.cth[n] : 0.f;
-    nx.PB[i] = pb;
-    nx.TBR[i] = tbr;
-    nx.U[i] = s.U[i] + pb;
+    for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
+      const int c = p.lcode[j];
+      const size_t ol = li(p, k, c >> 1, t0);
+      const Vf<VW> v = ldv<VW>(nx.P + ol), th = ldv<VW>(((c & 1) ? nx.TH2 : nx.TH1) + ol);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        sp[e] += (c & 1) ? v.x[e] : -v.x[e];
+        st[e] += th.x[e];
+      }
+    }
+    const Vf<VW> u = ldv<VW>(s.U + it.o);
+    Vf<VW> pb, tbr, un;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      pb.x[e] = sp[e] / p.cnt[n];
+      tbr.x[e] = p.cth[n] > 0.f ? st[e] / p.cth[n] : 0.f;
+      un.x[e] = u.x[e] + pb.x[e];
+    }
+    stv<VW>(nx.PB + it.o, pb);
+    stv<VW>(nx.TBR + it.o, tbr);
+    stv<VW>(nx.U + it.o, un);
     // v' = v + theta' - theta_bar' of the node's line terminals (each
     // terminal belongs to one node, so every v entry is written once)
     for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
       const int c = p.lcode[j];
-      const size_t o = li(p, k, c >> 1, t);
-      if (c & 1) nx.V2[o] = s.V2[o] + nx.TH2[o] - tbr;
-      else nx.V1[o] = s.V1[o] + nx.TH1[o] - tbr;
+      const size_t ol = li(p, k, c >> 1, t0);
+      float *V = (c & 1) ? nx.V2 : nx.V1;
+      const Vf<VW> v = ldv<VW>(((c & 1) ? s.V2 : s.V1) + ol), th = ldv<VW>(((c & 1) ? nx.TH2 : nx.TH1) + ol);
+      Vf<VW> w;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) w.x[e] = v.x[e] + th.x[e] - tbr.x[e];
+      stv<VW>(V + ol, w);
     }
   }
 }
@@ -208,25 +299,44 @@ __device__ __forceinline__ unsigned char clip_code(float z, float lo, float hi) 
 
 // step 1: line prox (Section 4.2); outaged lines decouple.  lmask (optional):
 // the iteration's record of where each line's unclipped flow lay
-__global__ void __launch_bounds__(TB, 8) fwd_line(DP p, St s, St nx, unsigned char *lmask) {
-  GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
-    const unsigned q = i / (unsigned)p.T;
-    const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
-    const LineIn in = line_inputs(p, s, k, l, t);
+template <int VW>
+__global__ void __launch_bounds__(TB, VW == 4 ? VW4_CTAS : 8) fwd_line(DP p, St s, St nx, unsigned char *lmask) {
+  GRID_STRIDE(i, (long long)p.Kp * p.L * (p.T / VW)) {
+    const Item it = item_of<VW>(i, p.L, p.T);
+    const int l = it.m, k = it.k;
+    const size_t o = it.o, o1 = ni(p, k, p.n1[l], it.t0), o2 = ni(p, k, p.n2[l], it.t0);
+    const Vf<VW> P = ldv<VW>(s.P + o), PB1 = ldv<VW>(s.PB + o1), U1 = ldv<VW>(s.U + o1);
+    const Vf<VW> PB2 = ldv<VW>(s.PB + o2), U2 = ldv<VW>(s.U + o2), TB1 = ldv<VW>(s.TBR + o1);
+    const Vf<VW> TB2 = ldv<VW>(s.TBR + o2), V1 = ldv<VW>(s.V1 + o), V2 = ldv<VW>(s.V2 + o);
+    Vf<VW> np, t1, t2;
     if (p.out[k] != l) {
-      const float b = p.b[l], tb = 2.f * b, u = p.lu[l];
-      const float z = line_z(p, in, tb, line_den(p, b, tb));
-      if (lmask) lmask[i] = clip_code(z, -u, u);
-      const float p2 = fminf(fmaxf(z, -u), u);
-      const float mid = 0.5f * (in.y1 + in.y2);
-      nx.P[i] = p2;
-      nx.TH1[i] = mid + p2 / tb;
-      nx.TH2[i] = mid - p2 / tb;
+      const float b = p.b[l], tb = 2.f * b, u = p.lu[l], den = line_den(p, b, tb);
+      Vb<VW> code;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        // the prox inputs as line_inputs forms them
+        const LineIn in{-P.x[e] - PB1.x[e] - U1.x[e], P.x[e] - PB2.x[e] - U2.x[e], TB1.x[e] - V1.x[e],
+                        TB2.x[e] - V2.x[e]};
+        const float z = line_z(p, in, tb, den);
+        code.x[e] = clip_code(z, -u, u);
+        const float p2 = fminf(fmaxf(z, -u), u);
+        const float mid = 0.5f * (in.y1 + in.y2);
+        np.x[e] = p2;
+        t1.x[e] = mid + p2 / tb;
+        t2.x[e] = mid - p2 / tb;
+      }
+      if (lmask) stb<VW>(lmask + o, code);
     } else {
-      nx.P[i] = 0.f;
-      nx.TH1[i] = in.y1;
-      nx.TH2[i] = in.y2;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        np.x[e] = 0.f;
+        t1.x[e] = TB1.x[e] - V1.x[e];
+        t2.x[e] = TB2.x[e] - V2.x[e];
+      }
     }
+    stv<VW>(nx.P + o, np);
+    stv<VW>(nx.TH1 + o, t1);
+    stv<VW>(nx.TH2 + o, t2);
   }
 }
 
@@ -449,82 +559,102 @@ __global__ void __launch_bounds__(TBI) fwd_inner(DP p, St s, St nx, const float 
 // itself: the kernels read it from a.LU (as `A`) before bwd_node3 adds to it.
 
 // B = d/d theta_bar' through v' = v + theta' - theta_bar' at node item
-// (k, n, t): minus the v adjoints of the node's line terminals
-__device__ __forceinline__ float node_b(const DP &p, const Adj &a, int k, int n, int t) {
-  float s = 0.f;
+// (k, n, t0 ..): minus the v adjoints of the node's line terminals
+template <int VW>
+__device__ __forceinline__ Vf<VW> node_b(const DP &p, const Adj &a, int k, int n, int t0) {
+  Vf<VW> s;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) s.x[e] = 0.f;
   for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
     const int c = p.lcode[j];
-    s += (c & 1) ? a.LV2[li(p, k, c >> 1, t)] : a.LV1[li(p, k, c >> 1, t)];
+    const Vf<VW> v = ldv<VW>(((c & 1) ? a.LV2 : a.LV1) + li(p, k, c >> 1, t0));
+#pragma unroll
+    for (int e = 0; e < VW; ++e) s.x[e] += v.x[e];
   }
-  return -s;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) s.x[e] = -s.x[e];
+  return s;
 }
 
-__global__ void __launch_bounds__(TB, 8) bwd_node1(DP p, Adj a, float *B) {
-  GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
-    const unsigned q = i / (unsigned)p.T;
-    const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
-    B[i] = node_b(p, a, k, n, t);
+template <int VW>
+__global__ void __launch_bounds__(TB, VW == 4 ? VW4_CTAS : 8) bwd_node1(DP p, Adj a, float *B) {
+  GRID_STRIDE(i, (long long)p.Kp * p.N * (p.T / VW)) {
+    const Item it = item_of<VW>(i, p.N, p.T);
+    stv<VW>(B + it.o, node_b<VW>(p, a, it.k, it.m, it.t0));
   }
 }
 
-// the line prox backwards at item i = (k, l, t), given the adjoints of the
-// step's outputs p, theta_1, theta_2 (lp0, lt10, lt20); X2, Y1, Y2 receive
-// d/d(x2, y1, y2) for the node gathers (d/d x1 = -d/d x2).  lmask (optional): the forward's
-// record of the iteration's line clips, else the unclipped flow is
-// recomputed from the step's input state s
-__device__ __forceinline__ void line_back(const DP &p, const St &s, const Adj &a, const float *A, const float *B,
-                                          float *X2, float *Y1, float *Y2, float *GU,
-                                          const unsigned char *lmask, unsigned i, int k, int l, int t, float lp0,
-                                          float lt10, float lt20) {
-  const int n1 = p.n1[l], n2 = p.n2[l];
-  const size_t o1 = ni(p, k, n1, t), o2 = ni(p, k, n2, t);
-  const float lp = fmaf(A[o2], p.icnt[n2], fmaf(-A[o1], p.icnt[n1], lp0));
-  const float lt1 = fmaf(B[o1], p.icth[n1], __fadd_rn(lt10, a.LV1[i]));
-  const float lt2 = fmaf(B[o2], p.icth[n2], __fadd_rn(lt20, a.LV2[i]));
-  float lx1 = 0.f, lx2 = 0.f, ly1, ly2;
-  if (p.out[k] != l) {
-    const float b = p.b[l], tb = 2.f * b, u = p.lu[l];
-    const float den = line_den(p, b, tb);
-    const unsigned char code = lmask ? lmask[i] : clip_code(line_z(p, line_inputs(p, s, k, l, t), tb, den), -u, u);
-    const float lpt = fmaf(lt1 - lt2, p.lfac[l], lp);     // theta_{1,2} = mid +- p / (2b)
-    const float half = __fmul_rn(0.5f, lt1 + lt2);
-    ly1 = ly2 = half;
-    if (code == CLIP_IN) {
-      lx2 = __fmul_rn(lpt, p.lfac[p.L + l]);
-      lx1 = -lx2;
-      const float w = __fmul_rn(lpt, p.lfac[2 * p.L + l]);
-      ly1 = __fadd_rn(half, w);
-      ly2 = __fsub_rn(half, w);
+// the line prox backwards at item `it` (line it.m, contingency it.k, steps
+// it.t0 ..), given the adjoints of the step's outputs p, theta_1, theta_2
+// (lp0, lt10, lt20) and A at the two ends (A1, A2); X2, Y1, Y2 receive
+// d/d(x2, y1, y2) for the node gathers (d/d x1 = -d/d x2).  lmask
+// (optional): the forward's record of the iteration's line clips, else the
+// unclipped flow is recomputed from the step's input state s
+template <int VW>
+__device__ __forceinline__ void line_back(const DP &p, const St &s, const Adj &a, const Vf<VW> &A1,
+                                          const Vf<VW> &A2, const float *B, float *X2, float *Y1, float *Y2,
+                                          float *GU, const unsigned char *lmask, const Item &it, const Vf<VW> &lp0,
+                                          const Vf<VW> &lt10, const Vf<VW> &lt20) {
+  const int l = it.m, k = it.k, n1 = p.n1[l], n2 = p.n2[l];
+  const size_t o = it.o, o1 = ni(p, k, n1, it.t0), o2 = ni(p, k, n2, it.t0);
+  const float ic1 = p.icnt[n1], ic2 = p.icnt[n2], ih1 = p.icth[n1], ih2 = p.icth[n2];
+  const Vf<VW> B1 = ldv<VW>(B + o1), B2 = ldv<VW>(B + o2), LV1 = ldv<VW>(a.LV1 + o), LV2 = ldv<VW>(a.LV2 + o);
+  const bool act = p.out[k] != l;
+  Vb<VW> code;
+  if (act && lmask) code = ldb<VW>(lmask + o);
+  Vf<VW> x2, y1, y2, lpn, v1, v2;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    const float lp = fmaf(A2.x[e], ic2, fmaf(-A1.x[e], ic1, lp0.x[e]));
+    const float lt1 = fmaf(B1.x[e], ih1, __fadd_rn(lt10.x[e], LV1.x[e]));
+    const float lt2 = fmaf(B2.x[e], ih2, __fadd_rn(lt20.x[e], LV2.x[e]));
+    float lx1 = 0.f, lx2 = 0.f, ly1, ly2;
+    if (act) {
+      const float b = p.b[l], tb = 2.f * b, u = p.lu[l];
+      const unsigned char cd =
+          lmask ? code.x[e] : clip_code(line_z(p, line_inputs(p, s, k, l, it.t0 + e), tb, line_den(p, b, tb)), -u, u);
+      const float lpt = fmaf(lt1 - lt2, p.lfac[l], lp);     // theta_{1,2} = mid +- p / (2b)
+      const float half = __fmul_rn(0.5f, lt1 + lt2);
+      ly1 = ly2 = half;
+      if (cd == CLIP_IN) {
+        lx2 = __fmul_rn(lpt, p.lfac[p.L + l]);
+        lx1 = -lx2;
+        const float w = __fmul_rn(lpt, p.lfac[2 * p.L + l]);
+        ly1 = __fadd_rn(half, w);
+        ly2 = __fsub_rn(half, w);
+      } else {
+        GU[o + e] += cd == CLIP_HI ? lpt : -lpt;
+      }
     } else {
-      GU[i] += code == CLIP_HI ? lpt : -lpt;
+      ly1 = lt1;
+      ly2 = lt2;
     }
-  } else {
-    ly1 = lt1;
-    ly2 = lt2;
+    x2.x[e] = lx2;
+    y1.x[e] = ly1;
+    y2.x[e] = ly2;
+    lpn.x[e] = lx2 - lx1;                // x1 = -p - ..., x2 = p - ...
+    v1.x[e] = LV1.x[e] - ly1;            // v enters y = theta_bar - v, and v' = v + ...
+    v2.x[e] = LV2.x[e] - ly2;
   }
-  X2[i] = lx2;
-  Y1[i] = ly1;
-  Y2[i] = ly2;
-  a.LP[i] = lx2 - lx1;                   // x1 = -p - ..., x2 = p - ...
-  a.LV1[i] -= ly1;                       // v enters y = theta_bar - v, and v' = v + ...
-  a.LV2[i] -= ly2;
+  stv<VW>(X2 + o, x2);
+  stv<VW>(Y1 + o, y1);
+  stv<VW>(Y2 + o, y2);
+  stv<VW>(a.LP + o, lpn);
+  stv<VW>(a.LV1 + o, v1);
+  stv<VW>(a.LV2 + o, v2);
 }
 
-__global__ void __launch_bounds__(TB, 8) bwd_line1(DP p, St s, Adj a, const float *A, const float *B, float *X2,
+template <int VW>
+__global__ void __launch_bounds__(TB, VW == 4 ? VW4_CTAS : 8) bwd_line1(DP p, St s, Adj a, const float *A, const float *B, float *X2,
                                                    float *Y1, float *Y2, float *GU, const unsigned char *lmask) {
-  GRID_STRIDE(i, (long long)p.Kp * p.L * p.T) {
-    const unsigned q = i / (unsigned)p.T;
-    const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
-    line_back(p, s, a, A, B, X2, Y1, Y2, GU, lmask, i, k, l, t, a.LP[i], a.LT1[i], a.LT2[i]);
+  GRID_STRIDE(i, (long long)p.Kp * p.L * (p.T / VW)) {
+    const Item it = item_of<VW>(i, p.L, p.T);
+    const size_t o1 = ni(p, it.k, p.n1[it.m], it.t0), o2 = ni(p, it.k, p.n2[it.m], it.t0);
+    line_back<VW>(p, s, a, ldv<VW>(A + o1), ldv<VW>(A + o2), B, X2, Y1, Y2, GU, lmask, it, ldv<VW>(a.LP + it.o),
+                  ldv<VW>(a.LT1 + it.o), ldv<VW>(a.LT2 + it.o));
   }
 }
 
-// lpd + the sum over contingencies of V at device d's node, divided by the
-// node's terminal count (the k-average's adjoint; every lane of the group)
-__device__ __forceinline__ float add_node_k(const DP &p, const float *V, int d, int t, float lpd) {
-  const int n = p.dnode[d];
-  return fmaf(ksum(p, V, nullptr, n, t), p.icnt[n], lpd);
-}
 
 // the closed-form device proxes backwards at item i = (d, t), given the
 // adjoint of the device's new power (lpd) and, for an HVDC terminal, its
@@ -576,14 +706,80 @@ __device__ __forceinline__ void dev_back(const DP &p, float *LX, float *GL, floa
   LX[i] = lx;
 }
 
+// The reverse device kernels on VW steps per lane group: ksum and dev_x for
+// steps t0 .. t0 + VW - 1, each step summed in the same order as the
+// one-step forms (so the results are the same step by step), and
+// add_node_kv: lpd + the sum over contingencies of V at device d's node
+// divided by the node's terminal count (the k-average's adjoint)
+template <int VW>
+__device__ __forceinline__ Vf<VW> ksumv(const DP &p, const float *V, const float *W, int n, int t0) {
+  const int j = threadIdx.x & (KL - 1);
+  Vf<VW> s;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) s.x[e] = 0.f;
+#pragma unroll 3
+  for (int k = j; k < p.Kp; k += KL) {
+    const Vf<VW> v = ldv<VW>(V + ni(p, k, n, t0));
+    if (W) {
+      const Vf<VW> w = ldv<VW>(W + ni(p, k, n, t0));
+#pragma unroll
+      for (int e = 0; e < VW; ++e) s.x[e] += v.x[e] + w.x[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < VW; ++e) s.x[e] += v.x[e];
+    }
+  }
+  const unsigned gm = group_mask();
+#pragma unroll
+  for (int o = KL / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) s.x[e] += __shfl_xor_sync(gm, s.x[e], o);
+  return s;
+}
+template <int VW>
+__device__ __forceinline__ Vf<VW> dev_xv(const DP &p, const St &s, int d, int t0) {
+  const Vf<VW> pd = ldv<VW>(s.PD + (size_t)d * p.T + t0), k = ksumv<VW>(p, s.PB, s.U, p.dnode[d], t0);
+  Vf<VW> r;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) r.x[e] = pd.x[e] - k.x[e] / (float)p.Kp;
+  return r;
+}
+template <int VW>
+__device__ __forceinline__ Vf<VW> add_node_kv(const DP &p, const float *V, int d, int t0, const Vf<VW> &lpd) {
+  const int n = p.dnode[d];
+  const Vf<VW> k = ksumv<VW>(p, V, nullptr, n, t0);
+  Vf<VW> r;
+#pragma unroll
+  for (int e = 0; e < VW; ++e) r.x[e] = fmaf(k.x[e], p.icnt[n], lpd.x[e]);
+  return r;
+}
+
+// device item i of a [S][T / VW] field: device d, first step t0, offset
+// d T + t0 = i VW
+template <int VW>
+__device__ __forceinline__ void dev_item(unsigned i, int T, int &d, int &t0) {
+  const unsigned TV = (unsigned)(T / VW);
+  d = (int)(i / TV);
+  t0 = (int)(i - (unsigned)d * TV) * VW;
+}
+
+template <int VW>
 __global__ void bwd_dev(DP p, St s, Adj a, const float *A, float *LX, float *GL, float *GP, float *XD, float *LPDT,
                         const unsigned char *dmask) {
-  GROUP_STRIDE(i, (long long)p.S * p.T) {
-    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T), d2 = hvdc_partner(p, d);
-    const float lpd = add_node_k(p, A, d, t, a.LPD[i]);
-    const float lpd_o = d2 < 0 ? 0.f : add_node_k(p, A, d2, t, a.LPD[(size_t)d2 * p.T + t]);
-    const float X = dmask ? 0.f : dev_x(p, s, d, t), Xo = (dmask || d2 < 0) ? 0.f : dev_x(p, s, d2, t);
-    if (!(threadIdx.x & (KL - 1))) dev_back(p, LX, GL, GP, XD, LPDT, dmask, i, d, t, lpd, lpd_o, X, Xo);
+  GROUP_STRIDE(i, (long long)p.S * (p.T / VW)) {
+    int d, t0;
+    dev_item<VW>(i, p.T, d, t0);
+    const int d2 = hvdc_partner(p, d);
+    const size_t o = (size_t)i * VW, o2 = (size_t)d2 * p.T + t0;
+    const Vf<VW> lpd = add_node_kv<VW>(p, A, d, t0, ldv<VW>(a.LPD + o));
+    Vf<VW> lpd_o{}, X{}, Xo{};
+    if (d2 >= 0) lpd_o = add_node_kv<VW>(p, A, d2, t0, ldv<VW>(a.LPD + o2));
+    if (!dmask) X = dev_xv<VW>(p, s, d, t0);
+    if (!dmask && d2 >= 0) Xo = dev_xv<VW>(p, s, d2, t0);
+    if (!(threadIdx.x & (KL - 1)))
+#pragma unroll
+      for (int e = 0; e < VW; ++e)
+        dev_back(p, LX, GL, GP, XD, LPDT, dmask, (unsigned)(o + e), d, t0 + e, lpd.x[e], lpd_o.x[e], X.x[e], Xo.x[e]);
   }
 }
 
@@ -766,8 +962,11 @@ constexpr size_t RREC_WORDS = (size_t)N_INNER * 32;   // words per device and ou
 
 // bytes of one outer iteration's record of the inner ADMM: the register
 // path's words, or the shared-memory path's byte per row and inner iteration
+// (a multiple of 16 bytes: the line record that follows it is read 4 bytes
+// at a time)
 __host__ __device__ inline size_t inner_record_bytes(const DP &p) {
-  return p.reg_c ? (size_t)p.n_inner * RREC_WORDS * sizeof(unsigned long long) : (size_t)N_INNER * p.Mtot;
+  const size_t b = p.reg_c ? (size_t)p.n_inner * RREC_WORDS * sizeof(unsigned long long) : (size_t)N_INNER * p.Mtot;
+  return (b + 15) & ~size_t(15);
 }
 
 // one inequality row of the inner ADMM: s = alpha + lambda, beta = min(s, 0),
@@ -1375,37 +1574,62 @@ __global__ void __launch_bounds__(TB, 1) bwd_inner_r(DP p, St s, Adj a, const fl
 // (completed by bwd_node3), D = d/d theta_bar (old).  nxt: also iteration
 // i-1's B (bwd_node1: the v adjoints are final after bwd_line1 of iteration
 // i).  It reads nothing the inner ADMM writes, and runs beside it.
-__global__ void __launch_bounds__(TB, 8) bwd_node2(DP p, Adj a, const float *X2, const float *Y1, const float *Y2,
+template <int VW>
+__global__ void __launch_bounds__(TB, VW == 4 ? VW4_CTAS : 8) bwd_node2(DP p, Adj a, const float *X2, const float *Y1, const float *Y2,
                                                    float *C, float *Dt, float *B, int nxt) {
-  GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
-    const unsigned q = i / (unsigned)p.T;
-    const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N), k = (int)(q / (unsigned)p.N);
-    float sx = 0.f, sy = 0.f;
+  GRID_STRIDE(i, (long long)p.Kp * p.N * (p.T / VW)) {
+    const Item it = item_of<VW>(i, p.N, p.T);
+    const int n = it.m;
+    float sx[VW], sy[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) sx[e] = sy[e] = 0.f;
     for (int j = p.lptr[n]; j < p.lptr[n + 1]; ++j) {
       const int c = p.lcode[j];
-      const size_t o = li(p, k, c >> 1, t);
-      sx += (c & 1) ? X2[o] : -X2[o];
-      sy += (c & 1) ? Y2[o] : Y1[o];
+      const size_t o = li(p, it.k, c >> 1, it.t0);
+      const Vf<VW> x = ldv<VW>(X2 + o), y = ldv<VW>(((c & 1) ? Y2 : Y1) + o);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        sx[e] += (c & 1) ? x.x[e] : -x.x[e];
+        sy[e] += y.x[e];
+      }
     }
-    C[i] = -sx;
-    Dt[i] = sy;                          // y = theta_bar - v
-    if (nxt) B[i] = node_b(p, a, k, n, t);
+    Vf<VW> cv, dv;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      cv.x[e] = -sx[e];
+      dv.x[e] = sy[e];                   // y = theta_bar - v
+    }
+    stv<VW>(C + it.o, cv);
+    stv<VW>(Dt + it.o, dv);
+    if (nxt) stv<VW>(B + it.o, node_b<VW>(p, a, it.k, n, it.t0));
   }
 }
 
 // ... and of the devices' terms once the inner ADMM is done: C = d/d pbar
 // (old) = -sx - avg_k(the node's devices' d/dX) (x = ... - pbar - u, X = ...
 // - avg_k(pbar + u)), which is also u's adjoint's increment
-__global__ void __launch_bounds__(TB, 8) bwd_node3(DP p, Adj a, const float *LX, float *C) {
-  GRID_STRIDE(i, (long long)p.Kp * p.N * p.T) {
-    const unsigned q = i / (unsigned)p.T;
-    const int t = (int)(i - q * (unsigned)p.T), n = (int)(q % (unsigned)p.N);
-    float sd = 0.f;
-    for (int j = p.dptr[n]; j < p.dptr[n + 1]; ++j) sd += LX[(size_t)p.didx[j] * p.T + t];
-    sd /= (float)p.Kp;
-    const float c = C[i] - sd;
-    C[i] = c;
-    a.LU[i] += c;
+template <int VW>
+__global__ void __launch_bounds__(TB, VW == 4 ? VW4_CTAS : 8) bwd_node3(DP p, Adj a, const float *LX, float *C) {
+  GRID_STRIDE(i, (long long)p.Kp * p.N * (p.T / VW)) {
+    const Item it = item_of<VW>(i, p.N, p.T);
+    const int n = it.m;
+    float sd[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) sd[e] = 0.f;
+    for (int j = p.dptr[n]; j < p.dptr[n + 1]; ++j) {
+      const Vf<VW> v = ldv<VW>(LX + (size_t)p.didx[j] * p.T + it.t0);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) sd[e] += v.x[e];
+    }
+    const Vf<VW> c0 = ldv<VW>(C + it.o), u = ldv<VW>(a.LU + it.o);
+    Vf<VW> cv, un;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      cv.x[e] = c0.x[e] - sd[e] / (float)p.Kp;
+      un.x[e] = u.x[e] + cv.x[e];
+    }
+    stv<VW>(C + it.o, cv);
+    stv<VW>(a.LU + it.o, un);
   }
 }
 
@@ -1423,22 +1647,30 @@ struct Scatter {
 // the old node averages back onto the old line values; nxt: then iteration
 // i-1's line prox backwards on the same item (bwd_line1), from state s and
 // record lmask of that iteration
+template <int VW>
 __device__ __forceinline__ void line2_part(const DP &p, const St &s, const Adj &a, const Scatter &g, int nxt,
                                            unsigned bid, unsigned nb) {
-  GRID_STRIDE_B(i, (long long)p.Kp * p.L * p.T, bid, nb) {
-    const unsigned q = i / (unsigned)p.T;
-    const int t = (int)(i - q * (unsigned)p.T), l = (int)(q % (unsigned)p.L), k = (int)(q / (unsigned)p.L);
-    const int n1 = p.n1[l], n2 = p.n2[l];
-    const size_t o1 = ni(p, k, n1, t), o2 = ni(p, k, n2, t);
-    const float lp = __fadd_rn(a.LP[i], fmaf(g.C[o2], p.icnt[n2], -__fmul_rn(g.C[o1], p.icnt[n1])));
-    const float lt1 = __fmul_rn(g.Dt[o1], p.icth[n1]);
-    const float lt2 = __fmul_rn(g.Dt[o2], p.icth[n2]);
+  GRID_STRIDE_B(i, (long long)p.Kp * p.L * (p.T / VW), bid, nb) {
+    const Item it = item_of<VW>(i, p.L, p.T);
+    const int n1 = p.n1[it.m], n2 = p.n2[it.m];
+    const size_t o1 = ni(p, it.k, n1, it.t0), o2 = ni(p, it.k, n2, it.t0);
+    const float ic1 = p.icnt[n1], ic2 = p.icnt[n2], ih1 = p.icth[n1], ih2 = p.icth[n2];
+    const Vf<VW> C1 = ldv<VW>(g.C + o1), C2 = ldv<VW>(g.C + o2), D1 = ldv<VW>(g.Dt + o1), D2 = ldv<VW>(g.Dt + o2);
+    const Vf<VW> lp0 = ldv<VW>(a.LP + it.o);
+    Vf<VW> lp, lt1, lt2;
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      lp.x[e] = __fadd_rn(lp0.x[e], fmaf(C2.x[e], ic2, -__fmul_rn(C1.x[e], ic1)));
+      lt1.x[e] = __fmul_rn(D1.x[e], ih1);
+      lt2.x[e] = __fmul_rn(D2.x[e], ih2);
+    }
     if (nxt) {
-      line_back(p, s, a, g.A, g.B, g.X2, g.Y1, g.Y2, g.GU, g.lmask, i, k, l, t, lp, lt1, lt2);
+      line_back<VW>(p, s, a, ldv<VW>(g.A + o1), ldv<VW>(g.A + o2), g.B, g.X2, g.Y1, g.Y2, g.GU, g.lmask, it, lp,
+                    lt1, lt2);
     } else {
-      a.LP[i] = lp;
-      a.LT1[i] = lt1;
-      a.LT2[i] = lt2;
+      stv<VW>(a.LP + it.o, lp);
+      stv<VW>(a.LT1 + it.o, lt1);
+      stv<VW>(a.LT2 + it.o, lt2);
     }
   }
 }
@@ -1447,27 +1679,37 @@ __device__ __forceinline__ void line2_part(const DP &p, const St &s, const Adj &
 // iteration i-1's device proxes backwards on the same item (bwd_dev), into
 // LXn, from state s and record dmask of that iteration.  An HVDC terminal
 // recomputes its partner's adjoint from the same inputs.
+template <int VW>
 __device__ __forceinline__ void dev2_part(const DP &p, const St &s, const Adj &a, const Scatter &g, int nxt,
                                           unsigned bid, unsigned nb) {
-  GROUP_STRIDE_B(i, (long long)p.S * p.T, bid, nb) {
-    const int d = (int)(i / (unsigned)p.T), t = (int)(i - (unsigned)d * (unsigned)p.T);
+  GROUP_STRIDE_B(i, (long long)p.S * (p.T / VW), bid, nb) {
+    int d, t0;
+    dev_item<VW>(i, p.T, d, t0);
+    const size_t o = (size_t)i * VW;
     const bool lead = !(threadIdx.x & (KL - 1));
-    const float lpd = add_node_k(p, g.C, d, t, g.LX[i]);
-    if (lead) a.LPD[i] = lpd;
+    const Vf<VW> lpd = add_node_kv<VW>(p, g.C, d, t0, ldv<VW>(g.LX + o));
+    if (lead) stv<VW>(a.LPD + o, lpd);
     if (nxt) {
       const int d2 = hvdc_partner(p, d);
-      const size_t o2 = (size_t)d2 * p.T + t;
-      const float lpd_o = d2 < 0 ? 0.f : add_node_k(p, g.A, d2, t, add_node_k(p, g.C, d2, t, g.LX[o2]));
-      const float lpdn = add_node_k(p, g.A, d, t, lpd);
-      const float X = g.dmask ? 0.f : dev_x(p, s, d, t), Xo = (g.dmask || d2 < 0) ? 0.f : dev_x(p, s, d2, t);
-      if (lead) dev_back(p, g.LXn, g.GL, g.GP, g.XD, g.LPDT, g.dmask, i, d, t, lpdn, lpd_o, X, Xo);
+      const size_t o2 = (size_t)d2 * p.T + t0;
+      Vf<VW> lpd_o{}, X{}, Xo{};
+      if (d2 >= 0) lpd_o = add_node_kv<VW>(p, g.A, d2, t0, add_node_kv<VW>(p, g.C, d2, t0, ldv<VW>(g.LX + o2)));
+      const Vf<VW> lpdn = add_node_kv<VW>(p, g.A, d, t0, lpd);
+      if (!g.dmask) X = dev_xv<VW>(p, s, d, t0);
+      if (!g.dmask && d2 >= 0) Xo = dev_xv<VW>(p, s, d2, t0);
+      if (lead)
+#pragma unroll
+        for (int e = 0; e < VW; ++e)
+          dev_back(p, g.LXn, g.GL, g.GP, g.XD, g.LPDT, g.dmask, (unsigned)(o + e), d, t0 + e, lpdn.x[e], lpd_o.x[e],
+                   X.x[e], Xo.x[e]);
     }
   }
 }
 
-__global__ void __launch_bounds__(TB, 8) bwd_scatter(DP p, St s, Adj a, Scatter g, int nxt, int dev_blocks) {
-  if ((int)blockIdx.x < dev_blocks) dev2_part(p, s, a, g, nxt, blockIdx.x, dev_blocks);
-  else line2_part(p, s, a, g, nxt, blockIdx.x - dev_blocks, gridDim.x - dev_blocks);
+template <int VW>
+__global__ void __launch_bounds__(TB, VW == 4 ? VW4_CTAS : 8) bwd_scatter(DP p, St s, Adj a, Scatter g, int nxt, int dev_blocks) {
+  if ((int)blockIdx.x < dev_blocks) dev2_part<VW>(p, s, a, g, nxt, blockIdx.x, dev_blocks);
+  else line2_part<VW>(p, s, a, g, nxt, blockIdx.x - dev_blocks, gridDim.x - dev_blocks);
 }
 
 // d f / d p_d at the last iterate, and f's direct dependence on P (the
@@ -1745,7 +1987,9 @@ void forward_step(const opf_diff *d, const St &s, const St &nx, float *XD, float
   unsigned char *lmask = mask ? mask + inner_record_bytes(p) : nullptr;
   unsigned char *dmask = mask ? lmask + nl : nullptr;
   unsigned long long *rrec = reinterpret_cast<unsigned long long *>(mask);
-  fwd_line<<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx, lmask);
+  const bool v4 = p.T % 4 == 0;   // four steps per thread in the line and node kernels
+  if (v4) fwd_line<4><<<grid_for(nl / 4), TB, 0, d->stream>>>(p, s, nx, lmask);
+  else fwd_line<1><<<grid_for(nl), TB, 0, d->stream>>>(p, s, nx, lmask);
   fwd_dev<<<grid_for(ns * KL), TB, 0, d->stream>>>(p, s, nx, XD, dmask);
   if (p.n_inner) {
     const int g = (p.n_inner + RWARPS - 1) / RWARPS;
@@ -1757,7 +2001,8 @@ void forward_step(const opf_diff *d, const St &s, const St &nx, float *XD, float
       default: fwd_inner<<<p.n_inner, TBI, d->smem_fwd, d->stream>>>(p, s, nx, XD, DEL, d->stage, mask); break;
     }
   }
-  fwd_avg<<<grid_for(nn), TB, 0, d->stream>>>(p, s, nx);
+  if (v4) fwd_avg<4><<<grid_for(nn / 4), TB, 0, d->stream>>>(p, s, nx);
+  else fwd_avg<1><<<grid_for(nn), TB, 0, d->stream>>>(p, s, nx);
 }
 
 }  // namespace
@@ -2096,7 +2341,10 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
     delete d;
     return dfail(OPF_ECUDA, cudaGetErrorString(e));
   }
-  d->state_floats = 5 * (size_t)d->Kp * L * T + (size_t)d->S * T + 3 * (size_t)d->Kp * N * T + 2 * (size_t)d->Mtot;
+  // padded to 64 floats, so that every state in a buffer of states starts on
+  // a 256-byte boundary (the line and node kernels move 16-byte rows)
+  d->state_floats = (5 * (size_t)d->Kp * L * T + (size_t)d->S * T + 3 * (size_t)d->Kp * N * T + 2 * (size_t)d->Mtot +
+                     63) & ~size_t(63);
   *out = d;
   return OPF_OK;
 }
@@ -2224,6 +2472,7 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   const long long nl = (long long)KLT, nn = (long long)KNT, ns = (long long)ST;
   // d/d pbar' is u's adjoint itself (u' = u + pbar'), read before bwd_node2 adds to it
   const float *A = a.LU;
+  const bool v4 = T % 4 == 0;   // four steps per thread in the line and node kernels
   bool primed = false;   // iteration i's first half already ran, fused into iteration i+1's second half
   for (int hi = K; e == cudaSuccess && hi > 0;) {
     // segment (lo, hi]: states lo + 1 .. hi - 1 recomputed from checkpoint lo
@@ -2240,9 +2489,15 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
       float *LX = (i & 1) ? LX1 : LX0, *LXn = (i & 1) ? LX0 : LX1;   // d/dX of iterations i and i - 1
       if (!primed) {
         const unsigned char *lmask = mi ? mi + inner_record_bytes(p) : nullptr, *dmask = mi ? lmask + KLT : nullptr;
-        bwd_node1<<<grid_for(nn), TB, 0, d->stream>>>(p, a, Bn);
-        bwd_line1<<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, Bn, X2, Y1, Y2, GU, lmask);
-        bwd_dev<<<grid_for(ns * KL), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT, dmask);
+        if (v4) {
+          bwd_node1<4><<<grid_for(nn / 4), TB, 0, d->stream>>>(p, a, Bn);
+          bwd_line1<4><<<grid_for(nl / 4), TB, 0, d->stream>>>(p, s, a, A, Bn, X2, Y1, Y2, GU, lmask);
+        } else {
+          bwd_node1<1><<<grid_for(nn), TB, 0, d->stream>>>(p, a, Bn);
+          bwd_line1<1><<<grid_for(nl), TB, 0, d->stream>>>(p, s, a, A, Bn, X2, Y1, Y2, GU, lmask);
+        }
+        if (v4) bwd_dev<4><<<grid_for(ns / 4 * KL), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT, dmask);
+        else bwd_dev<1><<<grid_for(ns * KL), TB, 0, d->stream>>>(p, s, a, A, LX, GL, GP, XD, LPDT, dmask);
       }
       // iteration i - 1's first half joins this second half when what it
       // reads is at hand: its record, or its input state i - 2 in this segment
@@ -2252,7 +2507,8 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
       if (e == cudaSuccess) e = cudaEventRecord(d->ev_fork, d->stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(d->aux, d->ev_fork, 0);
       if (e != cudaSuccess) break;
-      bwd_node2<<<grid_for(nn), TB, 0, d->aux>>>(p, a, X2, Y1, Y2, Cn, Dn, Bn, nxt);
+      if (v4) bwd_node2<4><<<grid_for(nn / 4), TB, 0, d->aux>>>(p, a, X2, Y1, Y2, Cn, Dn, Bn, nxt);
+      else bwd_node2<1><<<grid_for(nn), TB, 0, d->aux>>>(p, a, X2, Y1, Y2, Cn, Dn, Bn, nxt);
       e = cudaEventRecord(d->ev_join, d->aux);
       if (p.n_inner) {
         const int g = (p.n_inner + RWARPS - 1) / RWARPS, lst = i == K ? 1 : 0;
@@ -2272,11 +2528,13 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
       if (e != cudaSuccess) break;
       const St sp = nxt && i - 2 >= lo ? state(i - 2) : s;   // read only without a record
       const unsigned char *lmp = mp ? mp + inner_record_bytes(p) : nullptr, *dmp = mp ? lmp + KLT : nullptr;
-      bwd_node3<<<grid_for(nn), TB, 0, d->stream>>>(p, a, LX, Cn);
+      if (v4) bwd_node3<4><<<grid_for(nn / 4), TB, 0, d->stream>>>(p, a, LX, Cn);
+      else bwd_node3<1><<<grid_for(nn), TB, 0, d->stream>>>(p, a, LX, Cn);
       {
         const Scatter g{Cn, Dn, A, Bn, LX, X2, Y1, Y2, GU, LXn, GL, GP, XD, LPDT, lmp, dmp};
-        const int db = grid_for(ns * KL);
-        bwd_scatter<<<db + grid_for(nl), TB, 0, d->stream>>>(p, sp, a, g, nxt, db);
+        const int db = grid_for(ns / (v4 ? 4 : 1) * KL);
+        if (v4) bwd_scatter<4><<<db + grid_for(nl / 4), TB, 0, d->stream>>>(p, sp, a, g, nxt, db);
+        else bwd_scatter<1><<<db + grid_for(nl), TB, 0, d->stream>>>(p, sp, a, g, nxt, db);
       }
       primed = nxt != 0;
     }
