@@ -61,6 +61,9 @@ struct DP {
   const float *load_p, *gpmax, *lu;    // data: [D][T], [G][T], [L]
   // inner ADMM (Appendix D)
   int n_inner, Mtot;                   // devices, rows over all devices
+  int n_inode;                         // nodes with an inner-ADMM device: inode [n_inode], hasin [N]
+  const int *inode;
+  const unsigned char *hasin;
   const IDev *idev;
   const Shape *shape;
   const int *arp, *aci, *atp, *ati;
@@ -548,15 +551,16 @@ __global__ void __launch_bounds__(TBI) fwd_inner(DP p, St s, St nx, const float 
 // The reverse pass of iteration i runs in two halves.  The first: the
 // adjoints of the new node averages, the line prox and the device proxes
 // transposed (bwd_node1, bwd_line1, bwd_dev), then the inner ADMM.  The
-// second: gathers at the nodes (bwd_node2 for the line terms, on a second
-// stream beside the inner ADMM, which it does not touch; bwd_node3 for the
-// device terms after it) and their scatter back to the line and device
+// second: gathers at the nodes (bwd_node2, on a second stream beside the
+// inner ADMM, which it does not touch, complete at the nodes without an
+// inner-ADMM device; bwd_node3 after it for the others) and their scatter back to the line and device
 // values (bwd_scatter, one launch for both).  bwd_node2 and bwd_scatter also
 // run iteration i-1's first-half step on the same item when `nxt` is set, so
 // a reverse iteration takes four launches instead of seven; the arithmetic is
 // the same device functions either way, so the results are the same bit for
 // bit.  The adjoint of the new pbar' through u' = u + pbar' is u's adjoint
-// itself: the kernels read it from a.LU (as `A`) before bwd_node3 adds to it.
+// itself: the kernels read it from a.LU (as `A`) before bwd_node2 (or
+// bwd_node3, at the nodes with an inner-ADMM device) adds the increment.
 
 // B = d/d theta_bar' through v' = v + theta' - theta_bar' at node item
 // (k, n, t0 ..): minus the v adjoints of the node's line terminals
@@ -1570,13 +1574,31 @@ __global__ void __launch_bounds__(TB, 1) bwd_inner_r(DP p, St s, Adj a, const fl
   }
 }
 
-// gathers at the nodes of the line terms: C = -sum of the terminals' d/d x
-// (completed by bwd_node3), D = d/d theta_bar (old).  nxt: also iteration
-// i-1's B (bwd_node1: the v adjoints are final after bwd_line1 of iteration
-// i).  It reads nothing the inner ADMM writes, and runs beside it.
+// C = d/d pbar (old) = -sx - avg_k(the node's devices' d/dX) (x = ... -
+// pbar - u, X = ... - avg_k(pbar + u)), which is also u's adjoint's
+// increment: the line terms sx and the device terms, sd = the sum of the
+// node's devices' d/dX at steps t0 ..
 template <int VW>
-__global__ void __launch_bounds__(TB, VW == 4 ? VW4_CTAS : 8) bwd_node2(DP p, Adj a, const float *X2, const float *Y1, const float *Y2,
-                                                   float *C, float *Dt, float *B, int nxt) {
+__device__ __forceinline__ void node_sd(const DP &p, const float *LX, int n, int t0, float (&sd)[VW]) {
+#pragma unroll
+  for (int e = 0; e < VW; ++e) sd[e] = 0.f;
+  for (int j = p.dptr[n]; j < p.dptr[n + 1]; ++j) {
+    const Vf<VW> v = ldv<VW>(LX + (size_t)p.didx[j] * p.T + t0);
+#pragma unroll
+    for (int e = 0; e < VW; ++e) sd[e] += v.x[e];
+  }
+}
+
+// gathers at the nodes: D = d/d theta_bar (old), and C, complete (with u's
+// adjoint's increment) at a node without an inner-ADMM device, else its line
+// terms -sx, completed by bwd_node3 once the inner ADMM is done.  nxt: also
+// iteration i-1's B (bwd_node1: the v adjoints are final after bwd_line1 of
+// iteration i).  It reads nothing the inner ADMM writes (LX only of the
+// other devices), and runs beside it.
+template <int VW>
+__global__ void __launch_bounds__(TB, VW == 4 ? VW4_CTAS : 8) bwd_node2(DP p, Adj a, const float *X2, const float *Y1,
+                                                                       const float *Y2, const float *LX, float *C,
+                                                                       float *Dt, float *B, int nxt) {
   GRID_STRIDE(i, (long long)p.Kp * p.N * (p.T / VW)) {
     const Item it = item_of<VW>(i, p.N, p.T);
     const int n = it.m;
@@ -1599,37 +1621,43 @@ __global__ void __launch_bounds__(TB, VW == 4 ? VW4_CTAS : 8) bwd_node2(DP p, Ad
       cv.x[e] = -sx[e];
       dv.x[e] = sy[e];                   // y = theta_bar - v
     }
+    if (!p.hasin[n]) {
+      float sd[VW];
+      node_sd<VW>(p, LX, n, it.t0, sd);
+      const Vf<VW> u = ldv<VW>(a.LU + it.o);
+      Vf<VW> un;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        cv.x[e] = cv.x[e] - sd[e] / (float)p.Kp;
+        un.x[e] = u.x[e] + cv.x[e];
+      }
+      stv<VW>(a.LU + it.o, un);
+    }
     stv<VW>(C + it.o, cv);
     stv<VW>(Dt + it.o, dv);
     if (nxt) stv<VW>(B + it.o, node_b<VW>(p, a, it.k, n, it.t0));
   }
 }
 
-// ... and of the devices' terms once the inner ADMM is done: C = d/d pbar
-// (old) = -sx - avg_k(the node's devices' d/dX) (x = ... - pbar - u, X = ...
-// - avg_k(pbar + u)), which is also u's adjoint's increment
+// ... and at the nodes with an inner-ADMM device, once it is done (items
+// (k, m, t0 ..) of the nodes inode[m])
 template <int VW>
 __global__ void __launch_bounds__(TB, VW == 4 ? VW4_CTAS : 8) bwd_node3(DP p, Adj a, const float *LX, float *C) {
-  GRID_STRIDE(i, (long long)p.Kp * p.N * (p.T / VW)) {
-    const Item it = item_of<VW>(i, p.N, p.T);
-    const int n = it.m;
+  GRID_STRIDE(i, (long long)p.Kp * p.n_inode * (p.T / VW)) {
+    const Item it = item_of<VW>(i, p.n_inode, p.T);
+    const int n = p.inode[it.m];
+    const size_t o = ni(p, it.k, n, it.t0);
     float sd[VW];
-#pragma unroll
-    for (int e = 0; e < VW; ++e) sd[e] = 0.f;
-    for (int j = p.dptr[n]; j < p.dptr[n + 1]; ++j) {
-      const Vf<VW> v = ldv<VW>(LX + (size_t)p.didx[j] * p.T + it.t0);
-#pragma unroll
-      for (int e = 0; e < VW; ++e) sd[e] += v.x[e];
-    }
-    const Vf<VW> c0 = ldv<VW>(C + it.o), u = ldv<VW>(a.LU + it.o);
+    node_sd<VW>(p, LX, n, it.t0, sd);
+    const Vf<VW> c0 = ldv<VW>(C + o), u = ldv<VW>(a.LU + o);
     Vf<VW> cv, un;
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
       cv.x[e] = c0.x[e] - sd[e] / (float)p.Kp;
       un.x[e] = u.x[e] + cv.x[e];
     }
-    stv<VW>(C + it.o, cv);
-    stv<VW>(a.LU + it.o, un);
+    stv<VW>(C + o, cv);
+    stv<VW>(a.LU + o, un);
   }
 }
 
@@ -2290,6 +2318,17 @@ opf_status opf_diff_create(const opf_network *net, int32_t T, const opf_continge
   }
   U(&p.dnode, dnode);
   U(&p.kind, kind);
+  {
+    std::vector<unsigned char> hasin(N, 0);
+    for (int s2 = 0; s2 < d->S; ++s2)
+      if (kind[s2] == 1) hasin[dnode[s2]] = 1;
+    std::vector<int> inode;
+    for (int n = 0; n < N; ++n)
+      if (hasin[n]) inode.push_back(n);
+    p.n_inode = (int)inode.size();
+    U(&p.hasin, hasin);
+    U(&p.inode, inode);
+  }
   U(&p.ga, d->ga);
   U(&p.gb, d->gb);
   U(&p.gpmin, gpmin);
@@ -2507,8 +2546,8 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
       if (e == cudaSuccess) e = cudaEventRecord(d->ev_fork, d->stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(d->aux, d->ev_fork, 0);
       if (e != cudaSuccess) break;
-      if (v4) bwd_node2<4><<<grid_for(nn / 4), TB, 0, d->aux>>>(p, a, X2, Y1, Y2, Cn, Dn, Bn, nxt);
-      else bwd_node2<1><<<grid_for(nn), TB, 0, d->aux>>>(p, a, X2, Y1, Y2, Cn, Dn, Bn, nxt);
+      if (v4) bwd_node2<4><<<grid_for(nn / 4), TB, 0, d->aux>>>(p, a, X2, Y1, Y2, LX, Cn, Dn, Bn, nxt);
+      else bwd_node2<1><<<grid_for(nn), TB, 0, d->aux>>>(p, a, X2, Y1, Y2, LX, Cn, Dn, Bn, nxt);
       e = cudaEventRecord(d->ev_join, d->aux);
       if (p.n_inner) {
         const int g = (p.n_inner + RWARPS - 1) / RWARPS, lst = i == K ? 1 : 0;
@@ -2528,8 +2567,9 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
       if (e != cudaSuccess) break;
       const St sp = nxt && i - 2 >= lo ? state(i - 2) : s;   // read only without a record
       const unsigned char *lmp = mp ? mp + inner_record_bytes(p) : nullptr, *dmp = mp ? lmp + KLT : nullptr;
-      if (v4) bwd_node3<4><<<grid_for(nn / 4), TB, 0, d->stream>>>(p, a, LX, Cn);
-      else bwd_node3<1><<<grid_for(nn), TB, 0, d->stream>>>(p, a, LX, Cn);
+      const long long ni3 = (long long)p.Kp * p.n_inode * T;   // items of the nodes with inner-ADMM devices
+      if (ni3 && v4) bwd_node3<4><<<grid_for(ni3 / 4), TB, 0, d->stream>>>(p, a, LX, Cn);
+      else if (ni3) bwd_node3<1><<<grid_for(ni3), TB, 0, d->stream>>>(p, a, LX, Cn);
       {
         const Scatter g{Cn, Dn, A, Bn, LX, X2, Y1, Y2, GU, LXn, GL, GP, XD, LPDT, lmp, dmp};
         const int db = grid_for(ns / (v4 ? 4 : 1) * KL);
