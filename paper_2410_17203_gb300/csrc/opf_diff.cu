@@ -2509,7 +2509,8 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
   if (e == cudaSuccess) e = cudaMemsetAsync(GL, 0, (DT + GT + MT) * 4, d->stream);
   if (e == cudaSuccess) bwd_init<<<grid_for((long long)ST), TB, 0, d->stream>>>(p, cur, a, GL);
   const long long nl = (long long)KLT, nn = (long long)KNT, ns = (long long)ST;
-  // d/d pbar' is u's adjoint itself (u' = u + pbar'), read before bwd_node2 adds to it
+  // d/d pbar' is u's adjoint itself (u' = u + pbar'), read before bwd_node2 or
+  // bwd_node3 adds the iteration's increment to it
   const float *A = a.LU;
   const bool v4 = T % 4 == 0;   // four steps per thread in the line and node kernels
   bool primed = false;   // iteration i's first half already ran, fused into iteration i+1's second half
@@ -2542,7 +2543,8 @@ opf_status cost_grad(opf_diff *d, int32_t K, int on_device, const float *load_p,
       // reads is at hand: its record, or its input state i - 2 in this segment
       unsigned char *mp = i > 1 ? mask_of(i - 1) : nullptr;
       const int nxt = i > 1 && (mp || i - 2 >= lo) ? 1 : 0;
-      // the node gathers of the line terms beside the inner ADMM
+      // the node gathers beside the inner ADMM (at the nodes with its devices,
+      // only the line terms; bwd_node3 adds the device terms after it)
       if (e == cudaSuccess) e = cudaEventRecord(d->ev_fork, d->stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(d->aux, d->ev_fork, 0);
       if (e != cudaSuccess) break;
