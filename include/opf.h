@@ -376,8 +376,8 @@ opf_status opf_batch_autotune(opf_batch *batch, int32_t steps, int32_t *choice, 
  * not even the residuals' last bits; counts and queries still cover every
  * instance, and an instance once dropped is not iterated again by this batch.
  * n_scheduled (may be NULL) receives the number of instances still
- * scheduled.  Synchronizes; a later opf_batch_autotune schedules every
- * instance again. */
+ * scheduled; with none, opf_batch_iterate does nothing.  Synchronizes; a
+ * later opf_batch_autotune schedules every instance again. */
 opf_status opf_batch_compact(opf_batch *batch, int32_t *n_scheduled);
 
 /* Export / import the full state (warm start, checkpoint and resume,
